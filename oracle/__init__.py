@@ -1,0 +1,281 @@
+"""FP64 CPU oracle of the EM-PIC step (test infrastructure only).
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  The C source ``pic_oracle.c`` is built
+with gcc into ``oracle/_build/liboracle.so`` on first use (or by ``build()``).
+
+Every function follows a passage of Hemker's thesis (arxiv 1503.00276), ch. 3:
+field weighting eq. "2d-field-weighting-e3", Boris push eq. "momentum-update",
+position update eq. "2d-position-update", TRISTAN / Villasenor-Buneman
+current deposit (average of orthogonal moves, path split at cell faces), field
+solve eqs. "2d-field-solve-b-part1/-e/-b-part2" and the 3D extension, and the
+appendix's smoothing section (nl_smooth).  See the header of pic_oracle.c for
+the readings of garbled passages and the list of pins.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "liboracle.so")
+_SRC = os.path.join(_HERE, "pic_oracle.c")
+_lock = threading.Lock()
+_lib = None
+
+MAX_PASS = 8
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (no fused multiply-add contraction)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= max(os.path.getmtime(_SRC),
+                                                   os.path.getmtime(os.path.join(_HERE, "pic_oracle.h")))):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+           "-o", tmp, _SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+class OraGrid(C.Structure):
+    _fields_ = [("ndim", C.c_int), ("nx", C.c_int * 3), ("dx", C.c_double * 3), ("xmin", C.c_double * 3),
+                ("dt", C.c_double), ("e0", C.c_double * 3), ("b0", C.c_double * 3),
+                ("smooth_level", C.c_int * 3), ("smooth_w", ((C.c_double * 3) * MAX_PASS) * 3),
+                ("rho_bg", C.c_double)]
+
+
+class OraSpecies(C.Structure):
+    _fields_ = [("rqm", C.c_double), ("q", C.c_double), ("n", C.c_longlong),
+                ("x", C.POINTER(C.c_double)), ("u", C.POINTER(C.c_double))]
+
+
+_DP = C.POINTER(C.c_double)
+_DPP = _DP * 6
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            L = C.CDLL(_LIB_PATH)
+            gp = C.POINTER(OraGrid)
+            sp = C.POINTER(OraSpecies)
+            L.ora_gather.argtypes = [gp, C.POINTER(_DP), _DP, _DP]
+            L.ora_boris.argtypes = [_DP, _DP, _DP, C.c_double, C.c_double]
+            L.ora_gamma.argtypes = [_DP]
+            L.ora_gamma.restype = C.c_double
+            L.ora_move.argtypes = [gp, _DP, _DP]
+            L.ora_wrap.argtypes = [gp, _DP]
+            L.ora_deposit_vb.argtypes = [gp, C.POINTER(_DP), _DP, _DP, C.c_double, C.c_double]
+            L.ora_deposit_rho.argtypes = [gp, _DP, _DP, C.c_longlong, C.c_double]
+            L.ora_smooth.argtypes = [gp, _DP]
+            L.ora_field_solve.argtypes = [gp, C.POINTER(_DP), C.POINTER(_DP)]
+            L.ora_advance_particles.argtypes = [gp, C.POINTER(_DP), C.c_double, C.c_longlong, _DP, _DP, C.c_int]
+            L.ora_particle_phase.argtypes = [gp, C.POINTER(_DP), C.POINTER(_DP), sp, C.c_int]
+            L.ora_step.argtypes = [gp, C.POINTER(_DP), C.POINTER(_DP), sp, C.c_int, C.c_int]
+            L.ora_rho.argtypes = [gp, sp, C.c_int, _DP]
+            L.ora_gauss_residual.argtypes = [gp, C.POINTER(_DP), _DP]
+            L.ora_gauss_residual.restype = C.c_double
+            L.ora_field_energy.argtypes = [gp, C.POINTER(_DP)]
+            L.ora_field_energy.restype = C.c_double
+            L.ora_kinetic_energy.argtypes = [sp, C.c_int]
+            L.ora_kinetic_energy.restype = C.c_double
+            L.ora_init_e_gauss_x1.argtypes = [gp, _DP, _DP]
+            L.ora_tile_bin.argtypes = [gp, C.POINTER(C.c_int), C.c_longlong, _DP, C.POINTER(C.c_longlong),
+                                       C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]
+            _lib = L
+    return _lib
+
+
+def _dp(a: np.ndarray):
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(_DP)
+
+
+def make_grid(g) -> OraGrid:
+    """ctypes grid from a ``workload.Grid``."""
+    og = OraGrid()
+    og.ndim = g.ndim
+    for d in range(3):
+        og.nx[d] = int(g.nx[d])
+        og.dx[d] = float(g.dx[d])
+        og.xmin[d] = float(g.xmin[d])
+        og.e0[d] = float(g.e0[d])
+        og.b0[d] = float(g.b0[d])
+        og.smooth_level[d] = int(g.smooth_level[d])
+        for p in range(MAX_PASS):
+            w = g.smooth_w[d] if not isinstance(g.smooth_w[d][0], (tuple, list)) else g.smooth_w[d][min(p, len(g.smooth_w[d]) - 1)]
+            for m in range(3):
+                og.smooth_w[d][p][m] = float(w[m])
+    og.dt = float(g.dt)
+    og.rho_bg = float(g.rho_bg)
+    return og
+
+
+class State:
+    """Oracle simulation state: six field arrays, three current arrays, species."""
+
+    def __init__(self, grid, species_list, xs, us, charges, fields=None):
+        self.grid = grid
+        self.og = make_grid(grid)
+        shape = (int(grid.nx[2]), int(grid.nx[1]), int(grid.nx[0]))
+        self.fld = [np.zeros(shape) if fields is None else np.ascontiguousarray(fields[c], dtype=np.float64).copy()
+                    for c in range(6)]
+        self.cur = [np.zeros(shape) for _ in range(3)]
+        self.x = [np.ascontiguousarray(x, dtype=np.float64).copy() for x in xs]
+        self.u = [np.ascontiguousarray(u, dtype=np.float64).copy() for u in us]
+        self.rqm = [float(s.rqm) for s in species_list]
+        self.q = [float(q) for q in charges]
+        self._refresh()
+
+    def _refresh(self):
+        self._fp = _DPP(*[_dp(f) for f in self.fld])
+        self._cp = (_DP * 3)(*[_dp(c) for c in self.cur])
+        n = len(self.x)
+        self._sp = (OraSpecies * n)()
+        for i in range(n):
+            self._sp[i].rqm = self.rqm[i]
+            self._sp[i].q = self.q[i]
+            self._sp[i].n = self.x[i].shape[0]
+            self._sp[i].x = _dp(self.x[i])
+            self._sp[i].u = _dp(self.u[i])
+
+    @property
+    def nsp(self):
+        return len(self.x)
+
+    def step(self, nsteps: int = 1):
+        lib().ora_step(C.byref(self.og), self._fp, self._cp, self._sp, self.nsp, int(nsteps))
+
+    def particle_phase(self):
+        lib().ora_particle_phase(C.byref(self.og), self._fp, self._cp, self._sp, self.nsp)
+
+    def smooth_current(self):
+        for c in self.cur:
+            lib().ora_smooth(C.byref(self.og), _dp(c))
+
+    def field_solve(self):
+        lib().ora_field_solve(C.byref(self.og), self._fp, self._cp)
+
+    def rho(self) -> np.ndarray:
+        r = np.zeros_like(self.cur[0])
+        lib().ora_rho(C.byref(self.og), self._sp, self.nsp, _dp(r))
+        return r
+
+    def gauss_residual(self, rho=None) -> float:
+        r = self.rho() if rho is None else rho
+        return lib().ora_gauss_residual(C.byref(self.og), self._fp, _dp(r))
+
+    def field_energy(self) -> float:
+        return lib().ora_field_energy(C.byref(self.og), self._fp)
+
+    def kinetic_energy(self) -> float:
+        return lib().ora_kinetic_energy(self._sp, self.nsp)
+
+    def init_e_gauss_x1(self):
+        lib().ora_init_e_gauss_x1(C.byref(self.og), _dp(self.rho()), _dp(self.fld[0]))
+
+
+def from_workload(grid, species_list, fields=None, index=None):
+    """Oracle state loaded from the seeded generator (all particles, or ``index``)."""
+    import workload
+    xs, us, qs = [], [], []
+    for s in species_list:
+        x, u = workload.load_particles(grid, s, index)
+        xs.append(x)
+        us.append(u)
+        qs.append(workload.macro_charge(grid, s))
+    st = State(grid, species_list, xs, us, qs, fields)
+    if grid.init_e_gauss_x1:
+        st.init_e_gauss_x1()
+    return st
+
+
+# --- single-operation helpers for the pins ---------------------------------
+
+def gather(grid, fields, x) -> np.ndarray:
+    og = make_grid(grid)
+    fl = [np.ascontiguousarray(f, dtype=np.float64) for f in fields]
+    fp = _DPP(*[_dp(f) for f in fl])
+    xx = np.ascontiguousarray(x, dtype=np.float64)
+    out = np.zeros(6)
+    lib().ora_gather(C.byref(og), fp, _dp(xx), _dp(out))
+    return out
+
+
+def boris(u, e, b, rqm, dt) -> np.ndarray:
+    uu = np.array(u, dtype=np.float64)
+    ee = np.array(e, dtype=np.float64)
+    bb = np.array(b, dtype=np.float64)
+    lib().ora_boris(_dp(uu), _dp(ee), _dp(bb), float(rqm), float(dt))
+    return uu
+
+
+def deposit_vb(grid, xold, xnew, v3, q):
+    og = make_grid(grid)
+    shape = (int(grid.nx[2]), int(grid.nx[1]), int(grid.nx[0]))
+    cur = [np.zeros(shape) for _ in range(3)]
+    cp = (_DP * 3)(*[_dp(c) for c in cur])
+    lib().ora_deposit_vb(C.byref(og), cp, _dp(np.ascontiguousarray(xold, dtype=np.float64)),
+                         _dp(np.ascontiguousarray(xnew, dtype=np.float64)), float(v3), float(q))
+    return cur
+
+
+def deposit_rho(grid, x, q, bg: float = 0.0):
+    og = make_grid(grid)
+    shape = (int(grid.nx[2]), int(grid.nx[1]), int(grid.nx[0]))
+    r = np.full(shape, bg)
+    xx = np.ascontiguousarray(np.atleast_2d(x), dtype=np.float64)
+    lib().ora_deposit_rho(C.byref(og), _dp(r), _dp(xx), xx.shape[0], float(q))
+    return r
+
+
+def smooth(grid, f):
+    og = make_grid(grid)
+    ff = np.ascontiguousarray(f, dtype=np.float64).copy()
+    lib().ora_smooth(C.byref(og), _dp(ff))
+    return ff
+
+
+def field_solve(grid, fields, currents):
+    og = make_grid(grid)
+    fl = [np.ascontiguousarray(f, dtype=np.float64).copy() for f in fields]
+    cu = [np.ascontiguousarray(c, dtype=np.float64) for c in currents]
+    lib().ora_field_solve(C.byref(og), _DPP(*[_dp(f) for f in fl]), (_DP * 3)(*[_dp(c) for c in cu]))
+    return fl
+
+
+def advance_particles(grid, fields, rqm, x, u, wrap=True):
+    og = make_grid(grid)
+    fl = [np.ascontiguousarray(f, dtype=np.float64) for f in fields]
+    xx = np.ascontiguousarray(x, dtype=np.float64).copy()
+    uu = np.ascontiguousarray(u, dtype=np.float64).copy()
+    lib().ora_advance_particles(C.byref(og), _DPP(*[_dp(f) for f in fl]), float(rqm), xx.shape[0],
+                                _dp(xx), _dp(uu), int(wrap))
+    return xx, uu
+
+
+def tile_bin(grid, tile, x):
+    og = make_grid(grid)
+    nt = [int(grid.nx[d]) // int(tile[d]) if d < grid.ndim else 1 for d in range(3)]
+    ntiles = nt[0] * nt[1] * nt[2]
+    xx = np.ascontiguousarray(x, dtype=np.float64)
+    n = xx.shape[0]
+    tid = np.zeros(n, dtype=np.int64)
+    counts = np.zeros(ntiles, dtype=np.int64)
+    order = np.zeros(n, dtype=np.int64)
+    t = (C.c_int * 3)(*[int(v) for v in tile])
+    LLP = C.POINTER(C.c_longlong)
+    lib().ora_tile_bin(C.byref(og), t, n, _dp(xx), tid.ctypes.data_as(LLP), counts.ctypes.data_as(LLP),
+                       order.ctypes.data_as(LLP))
+    return tid, counts, order

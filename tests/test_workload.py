@@ -1,0 +1,57 @@
+"""The seeded input generator: SplitMix64 against its published test vectors,
+Box-Muller moments, the num_par_x lattice loader and macroparticle charge."""
+import math
+import os
+
+import numpy as np
+
+import workload
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+def test_splitmix64_published_vectors():
+    for line in open(os.path.join(HERE, "golden", "splitmix64_vectors.txt")):
+        if line.startswith("#") or not line.strip():
+            continue
+        seed, *vals = line.split()
+        got = workload.splitmix64(int(seed), np.arange(len(vals)))
+        assert [int(v) for v in got] == [int(v, 16) for v in vals]
+
+
+def test_uniform_and_normal_moments():
+    u = workload.uniform01(7, np.arange(200000))
+    assert u.min() >= 0.0 and u.max() < 1.0
+    assert abs(u.mean() - 0.5) < 3e-3
+    n = workload.normal(7, np.arange(200000))
+    assert abs(n.mean()) < 1e-2 and abs(n.std() - 1) < 1e-2
+    assert abs(np.mean(n ** 4) - 3) < 0.05
+
+
+def test_lattice_loader_positions_and_charge():
+    g = workload.Grid(ndim=3, nx=(4, 3, 2), dx=(0.1, 0.2, 0.3), dt=0.01)
+    sp = workload.Species(ppc=(2, 1, 2), uth=(0.1, 0.0, 0.2), ufl=(0.0, 0.5, 0.0), seed=5)
+    x, u = workload.load_particles(g, sp)
+    assert x.shape == (4 * 3 * 2 * 4, 3)
+    # particle 0: cell (0,0,0), sub-lattice (0,0,0) -> offsets (1/4, 1/2, 1/4)
+    np.testing.assert_array_equal(x[0], [0.025, 0.1, 0.075])
+    # particle 1: sub-lattice x1 index 1 -> offset 3/4
+    np.testing.assert_allclose(x[1], [0.075, 0.1, 0.075], rtol=1e-15)
+    # particle ppc: next cell in x1
+    np.testing.assert_allclose(x[4], [0.125, 0.1, 0.075])
+    assert np.all(u[:, 1] == 0.5)
+    # regenerate a subset by index: identical
+    idx = np.array([7, 31, 60])
+    xs, us = workload.load_particles(g, sp, idx)
+    np.testing.assert_array_equal(xs, x[idx])
+    np.testing.assert_array_equal(us, u[idx])
+    q = workload.macro_charge(g, sp)
+    assert math.isclose(q * x.shape[0], -g.dvol * g.ncells)
+
+
+def test_config_shapes():
+    g, sp, steps = workload.config0()
+    assert g.nx == (64, 64, 1) and workload.n_particles(g, sp[0]) == 65536 and steps == 100
+    assert abs(g.dt - 0.99 / math.sqrt(200)) < 1e-15
+    g3, sp3, steps3 = workload.config3()
+    assert workload.n_particles(g3, sp3[0]) == 268435456 and steps3 == 200

@@ -1,0 +1,198 @@
+"""Seeded synthetic inputs for the EM-PIC hot path.
+
+This module is the only code that both sides of every comparison share: the
+FP64 CPU oracle (``oracle/``) and the CUDA library.  It produces input data
+only -- grids, initial particle positions and momenta, random test fields --
+and contains none of the arithmetic of the PIC method (no gather, push,
+deposit, smoothing or field solve).
+
+Random numbers come from one counter-based generator, SplitMix64
+(G. L. Steele, D. Lea, C. H. Flood, "Fast splittable pseudorandom number
+generators", OOPSLA 2014; the constants are those of the published
+reference implementation), turned into uniforms on [0, 1) with 53 bits and
+into normals with the Box-Muller transform (cos branch only, so that each
+normal deviate has its own pair of counters).  Draw number ``c`` of stream
+``seed`` is ``splitmix64(seed + (c + 1) * GAMMA)``, so any particle can be
+regenerated on its own from its index.  The CUDA loader implements the same
+published definitions independently.
+
+Particle loading follows the species input of the paper's appendix (input
+sections ``nl_species`` / ``nl_profile``): ``num_par_x`` particles per cell
+direction on a regular sub-lattice, thermal spread ``vth`` read as the
+standard deviation of each momentum component u = p/(m c), fluid momentum
+``vfl``.  Particle ``p`` is sub-lattice point ``s`` of cell ``c`` with
+``p = c * ppc + s``, cells in x1-fastest order, sub-lattice points in
+x1-fastest order.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+GAMMA = np.uint64(0x9E3779B97F4A7C15)
+MIX1 = np.uint64(0xBF58476D1CE4E5B9)
+MIX2 = np.uint64(0x94D049BB133111EB)
+_U53 = 1.0 / 9007199254740992.0  # 2**-53
+
+
+def splitmix64(seed: int, counter) -> np.ndarray:
+    """Output number ``counter`` (0-based, array) of the SplitMix64 stream ``seed``."""
+    c = np.asarray(counter, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        z = np.uint64(seed & 0xFFFFFFFFFFFFFFFF) + (c + np.uint64(1)) * GAMMA
+        z = (z ^ (z >> np.uint64(30))) * MIX1
+        z = (z ^ (z >> np.uint64(27))) * MIX2
+        z = z ^ (z >> np.uint64(31))
+    return z
+
+
+def uniform01(seed: int, counter) -> np.ndarray:
+    """Uniform double on [0, 1): top 53 bits of the SplitMix64 output."""
+    return (splitmix64(seed, counter) >> np.uint64(11)).astype(np.float64) * _U53
+
+
+def normal(seed: int, counter) -> np.ndarray:
+    """Standard normal deviate number ``counter``: Box-Muller on draws 2c, 2c+1."""
+    c = np.asarray(counter, dtype=np.uint64)
+    u1 = 1.0 - uniform01(seed, np.uint64(2) * c)          # (0, 1]
+    u2 = uniform01(seed, np.uint64(2) * c + np.uint64(1))  # [0, 1)
+    return np.sqrt(-2.0 * np.log(u1)) * np.cos(2.0 * math.pi * u2)
+
+
+# ----------------------------------------------------------------------------
+# Problem descriptions
+# ----------------------------------------------------------------------------
+
+@dataclass
+class Grid:
+    """Simulation box in normalised units (t in 1/w_p, x in c/w_p)."""
+    ndim: int
+    nx: tuple                      # cells per direction (3 entries; nx[2] = 1 in 2D)
+    dx: tuple                      # cell size per direction
+    xmin: tuple = (0.0, 0.0, 0.0)
+    dt: float = 0.0
+    e0: tuple = (0.0, 0.0, 0.0)    # constant external fields
+    b0: tuple = (0.0, 0.0, 0.0)
+    smooth_level: tuple = (0, 0, 0)
+    smooth_w: tuple = ((1.0, 2.0, 1.0),) * 3
+    rho_bg: float = 1.0            # fixed neutralising ion background density
+    init_e_gauss_x1: bool = False  # initial E1 from the discrete Gauss law along x1
+
+    @property
+    def ncells(self) -> int:
+        return int(self.nx[0]) * int(self.nx[1]) * int(self.nx[2])
+
+    @property
+    def dvol(self) -> float:
+        v = self.dx[0] * self.dx[1]
+        return v * self.dx[2] if self.ndim == 3 else v
+
+
+@dataclass
+class Species:
+    rqm: float = -1.0              # m/q in units of m_e/e; electrons -1
+    ppc: tuple = (1, 1, 1)         # num_par_x
+    uth: tuple = (0.0, 0.0, 0.0)   # vth, std-dev of each u component
+    ufl: tuple = (0.0, 0.0, 0.0)   # vfl
+    density: float = 1.0           # uniform density in units of n0
+    seed: int = 0
+    # sinusoidal x1 displacement: x1 -> x1 + (delta/k) cos(k (x1 - xmin1)),
+    # giving density ~ 1 + delta sin(k x1) to first order
+    perturb_delta: float = 0.0
+    perturb_k: float = 0.0
+
+    @property
+    def ppc_total(self) -> int:
+        return int(self.ppc[0]) * int(self.ppc[1]) * int(self.ppc[2])
+
+
+def courant_dt(dx, ndim: int, frac: float = 0.99) -> float:
+    """``frac`` times the multi-dimensional Courant limit 1/sqrt(sum dx_d^-2)."""
+    return frac / math.sqrt(sum(1.0 / (dx[d] * dx[d]) for d in range(ndim)))
+
+
+def macro_charge(grid: Grid, sp: Species) -> float:
+    """Charge per macroparticle so that ppc particles carry density ``sp.density``."""
+    sign = -1.0 if sp.rqm < 0 else 1.0
+    return sign * sp.density * grid.dvol / sp.ppc_total
+
+
+def n_particles(grid: Grid, sp: Species) -> int:
+    return grid.ncells * sp.ppc_total
+
+
+def load_particles(grid: Grid, sp: Species, index=None):
+    """Initial x^0 (global, FP64) and u^{-1/2} (FP64) of the particles ``index``.
+
+    ``index`` defaults to all particles.  Returns (x[n,3], u[n,3]); in 2D the
+    third position column is 0.
+    """
+    n_total = n_particles(grid, sp)
+    if index is None:
+        index = np.arange(n_total, dtype=np.int64)
+    p = np.asarray(index, dtype=np.int64)
+    ppc = sp.ppc_total
+    cell = p // ppc
+    sub = p % ppc
+    nx, ny = int(grid.nx[0]), int(grid.nx[1])
+    ci = cell % nx
+    cj = (cell // nx) % ny
+    ck = cell // (nx * ny)
+    npx, npy = int(sp.ppc[0]), int(sp.ppc[1])
+    si = sub % npx
+    sj = (sub // npx) % npy
+    sk = sub // (npx * npy)
+    x = np.zeros((p.size, 3), dtype=np.float64)
+    for d, (c, s) in enumerate(((ci, si), (cj, sj), (ck, sk))):
+        if d >= grid.ndim:
+            break
+        off = (s.astype(np.float64) + 0.5) / float(sp.ppc[d])
+        x[:, d] = grid.xmin[d] + (c.astype(np.float64) + off) * grid.dx[d]
+    if sp.perturb_delta != 0.0:
+        L = grid.nx[0] * grid.dx[0]
+        x1 = x[:, 0] + (sp.perturb_delta / sp.perturb_k) * np.cos(sp.perturb_k * (x[:, 0] - grid.xmin[0]))
+        x1 = np.where(x1 >= grid.xmin[0] + L, x1 - L, x1)
+        x1 = np.where(x1 < grid.xmin[0], x1 + L, x1)
+        x[:, 0] = x1
+    u = np.empty((p.size, 3), dtype=np.float64)
+    pu = p.astype(np.uint64)
+    for d in range(3):
+        u[:, d] = sp.ufl[d] + sp.uth[d] * normal(sp.seed, np.uint64(3) * pu + np.uint64(d)) if sp.uth[d] != 0.0 \
+            else np.full(p.size, float(sp.ufl[d]))
+    return x, u
+
+
+def random_fields(grid: Grid, seed: int, amp: float = 0.1, ncomp: int = 6):
+    """``ncomp`` grid arrays [nz][ny][nx] of uniform noise on [-amp, amp)."""
+    shape = (int(grid.nx[2]), int(grid.nx[1]), int(grid.nx[0]))
+    n = int(np.prod(shape))
+    out = []
+    for c in range(ncomp):
+        cnt = np.arange(n, dtype=np.uint64) + np.uint64(c * n)
+        out.append((2.0 * uniform01(seed, cnt) - 1.0).reshape(shape) * amp)
+    return out
+
+
+# ----------------------------------------------------------------------------
+# The five workloads of the hot path (sizes and physics parameters)
+# ----------------------------------------------------------------------------
+
+def config0(seed: int = 20001):
+    """2D3V periodic electron plasma, 64x64 cells, 16 ppc, 1% x1 perturbation, 100 steps."""
+    dx = (0.1, 0.1, 1.0)
+    g = Grid(ndim=2, nx=(64, 64, 1), dx=dx, dt=courant_dt(dx, 2), init_e_gauss_x1=True)
+    k = 2.0 * math.pi / (64 * 0.1)
+    s = Species(rqm=-1.0, ppc=(4, 4, 1), uth=(0.01, 0.01, 0.01), seed=seed,
+                perturb_delta=0.01, perturb_k=k)
+    return g, [s], 100
+
+
+def config3(ppc_total: int = 8, seed: int = 20004, nx=(512, 256, 256)):
+    """3D3V periodic thermal plasma, 512x256x256 cells, u_th = 0.05, 200 steps."""
+    lattice = {1: (1, 1, 1), 2: (2, 1, 1), 4: (2, 2, 1), 8: (2, 2, 2), 16: (4, 2, 2)}[ppc_total]
+    dx = (0.1, 0.1, 0.1)
+    g = Grid(ndim=3, nx=tuple(nx), dx=dx, dt=courant_dt(dx, 3))
+    s = Species(rqm=-1.0, ppc=lattice, uth=(0.05, 0.05, 0.05), seed=seed)
+    return g, [s], 200

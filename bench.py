@@ -1,0 +1,422 @@
+#!/usr/bin/env python
+"""Throughput of the EM-PIC hot path on GB300.
+
+Default workload: 3D3V periodic thermal plasma, 512x256x256 cells, 8 particles
+per cell (268,435,456 electrons), u_th = 0.05 c, dx = 0.1 c/w_p, dt = 0.99 of the
+Courant limit, in the FP32 cell-offset tiled form.  One "step" is one full PIC
+step: gather + Boris push + move + charge-conserving deposit (with the per-tile
+binning), current fold, field solve.  Particles and fields are resident in HBM
+(the particle store alone is ~9 GB, far larger than L2).
+
+python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+Prints one JSON line (rank 0).  With N > 1 (launched by torchrun) every rank runs
+an independent replica with its own seed ("replicas only": the workload does
+not exchange data between GPUs); the timed region is bracketed by barriers and
+the max over ranks is reported.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "particle pushes/s (gather+push+deposit) and % HBM roofline, FP32 vs FP64 at stated error"
+UNIT = "particle-pushes/s"
+FALLBACK_HBM_GBS = 6800.0
+
+# algorithmic bytes per particle-step: particle record read + written, plus the
+# per-cell field reads (6 E/B components) and current read-modify-write (3)
+# amortised over the particles of a cell
+REC_BYTES = {("fp32", 3): 28, ("fp32", 2): 24, ("fp64", 3): 48, ("fp64", 2): 40}
+
+
+def alg_bytes_per_particle(prec: str, ndim: int, ppc: int) -> float:
+    w = 4 if prec == "fp32" else 8
+    return 2 * REC_BYTES[(prec, ndim)] + (6 * w + 3 * w * 2) / ppc
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=200)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--ppc", type=int, default=8, choices=[1, 2, 4, 8, 16])
+    p.add_argument("--nx", default="512,256,256")
+    p.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    p.add_argument("--tile", default="8,8,8")
+    p.add_argument("--smooth", type=int, default=0, help="(1,2,1) passes per direction")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--no-fp64", action="store_true")
+    p.add_argument("--fp64-steps", type=int, default=3)
+    return p.parse_args()
+
+
+# ---------------------------------------------------------------- environment
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def measured_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(prefix="clocks_", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.gpu), "-lms", "100"], stdout=open(self.path, "w"),
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if "Active" in f[5 + k] and "Not" not in f[5 + k]:
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def source_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("k_tiled.cu", "common.cuh", "kernels.h"):
+        with open(os.path.join(ROOT, "paper_1503_00276_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(kernel: str, n_particles: int):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on
+    the current kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f)[kernel]
+        if rec.get("source_hash") != source_hash():
+            return None
+        return rec["dram_bytes_per_particle"] * n_particles
+    except Exception:
+        return None
+
+
+# ---------------------------------------------------------------- workloads
+def make_workload(args, rank: int):
+    import workload
+    nx = tuple(int(v) for v in args.nx.split(","))
+    g, sps, steps = workload.config3(args.ppc, seed=20004 + rank, nx=nx)
+    g.smooth_level = (args.smooth,) * 3
+    return g, sps, steps
+
+
+def describe(args, n_p: int):
+    nx = [int(v) for v in args.nx.split(",")]
+    return {
+        "workload": (f"3D3V periodic thermal plasma {nx[0]}x{nx[1]}x{nx[2]} cells, {args.ppc} ppc "
+                     f"({n_p:,} electrons), u_th=0.05c, dx=0.1 c/w_p, dt=0.99 Courant, "
+                     f"{'FP32 cell-offset tiled' if args.precision == 'fp32' else 'FP64 plain'}"),
+        "grid": nx, "ppc": args.ppc, "precision": args.precision,
+        "tile": [int(v) for v in args.tile.split(",")] if args.precision == "fp32" else None,
+        "smoothing_passes": args.smooth,
+        "l2": "inputs larger than L2 (particle store >= 7.5 GB vs 129 MB L2)",
+        "steps_in_config": 200,
+    }
+
+
+# ---------------------------------------------------------------- our arm
+def run_ours(args):
+    import torch
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import paper_1503_00276_gb300 as pg
+    import workload
+
+    g, sps, _ = make_workload(args, rank)
+    n_p = workload.n_particles(g, sps[0])
+    tile = tuple(int(v) for v in args.tile.split(","))
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(v: float) -> float:
+        if dist is None:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def sum_over_ranks(v: float) -> float:
+        if dist is None:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        return float(t.item())
+
+    def timed(sim, steps, warmup, clocks=None):
+        for _ in range(warmup):
+            sim.step(1)
+        sim.timing_enable(True)
+        sim.timing_read(reset=True)
+        barrier()
+        if clocks:
+            clocks.start()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            sim.step(1)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        clk = clocks.stop() if clocks else None
+        ms = e0.elapsed_time(e1)
+        tim = sim.timing_read(reset=True)
+        sim.timing_enable(False)
+        return ms, tim, clk
+
+    peak, peak_kind = measured_peak()
+    prec = args.precision
+    sim = pg.Simulation(g, sps, precision=prec, tile=tile if prec == "fp32" else None)
+    clocks = ClockSampler(local)
+    ms, tim, clk = timed(sim, args.steps, args.warmup, clocks)
+    diag = sim.diag()
+    sim.close()
+    del sim
+    ms_max = max_over_ranks(ms)
+    total_units = sum_over_ranks(n_p * args.steps)
+    value = total_units / (ms_max / 1e3)
+    k1_ms, k1_n = tim["particles"]
+    k1_avg_s = k1_ms / max(k1_n, 1) / 1e3
+    bpp = alg_bytes_per_particle(prec, 3, args.ppc)
+    achieved = n_p * bpp / k1_avg_s / 1e9
+    kname = "k_tile_push" if prec == "fp32" else "k_plain_push"
+    roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "traffic": profiled_traffic(kname, n_p),
+            "kernel": kname, "algorithmic_bytes_per_particle": bpp, "peak_source": f"{peak_kind} hbm_gbs",
+            "k1_ms_per_launch": round(k1_avg_s * 1e3, 4), "step_roofline_frac": round(
+                n_p * bpp / (ms / args.steps / 1e3) / 1e9 / peak, 4)}
+    launches = int(tim["launches"][1])
+
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec == "fp32" else "f64",
+           "data": "synthetic (seeded lattice + Maxwellian loader, no dataset)", "config": describe(args, n_p),
+           "roofline": roof, "clocks": clk, "gpu_launches": launches,
+           "stages_ms_per_step": {k: round(v[0] / max(args.steps, 1), 4) for k, v in tim.items()
+                                  if k not in ("launches",)},
+           "diag_after": {"gauss_resid_max": diag["gauss_resid_max"],
+                          "rho_particles_abs_max": diag["rho_particles_abs_max"],
+                          "error_flags": diag["error_flags"]}}
+
+    # FP64 plain form on the same GPU (speed-up statement)
+    if not args.no_fp64 and prec == "fp32":
+        s64 = pg.Simulation(g, sps, precision="fp64")
+        ms64, tim64, _ = timed(s64, args.fp64_steps, 1)
+        s64.close()
+        del s64
+        ms64 = max_over_ranks(ms64)
+        v64 = sum_over_ranks(n_p * args.fp64_steps) / (ms64 / 1e3)
+        k64 = tim64["particles"][0] / max(tim64["particles"][1], 1) / 1e3
+        b64 = alg_bytes_per_particle("fp64", 3, args.ppc)
+        out["fp64_plain"] = {"value": v64, "unit": UNIT, "ms_per_step": ms64 / args.fp64_steps,
+                             "steps": args.fp64_steps,
+                             "roofline_frac": round(n_p * b64 / k64 / 1e9 / peak, 4),
+                             "k1_ms_per_launch": round(k64 * 1e3, 3),
+                             "fp32_speedup": value / v64}
+
+    # end to end through the C ABI with host buffers
+    if not args.no_e2e:
+        out["e2e"] = run_e2e(args, g, sps, n_p, tile, barrier, max_over_ranks, sum_over_ranks)
+
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        out["cpu_baseline"] = run_cpu_baseline(args, budget_s=15.0)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def run_e2e(args, g, sps, n_p, tile, barrier, max_over_ranks, sum_over_ranks):
+    """One job through the public API: upload the initial particles from pinned
+    host memory (pic_init with explicit arrays), advance K steps reading the FP64
+    diagnostics back every step, copy all particles back to pinned host memory."""
+    import numpy as np
+    import torch
+    from concurrent.futures import ThreadPoolExecutor
+
+    import paper_1503_00276_gb300 as pg
+    import workload
+
+    x = torch.empty((n_p, 3), dtype=torch.float64, pin_memory=True)
+    u = torch.empty((n_p, 3), dtype=torch.float64, pin_memory=True)
+    xn, un = x.numpy(), u.numpy()
+    chunk = 1 << 22
+
+    def gen(first):
+        idx = np.arange(first, min(first + chunk, n_p), dtype=np.int64)
+        a, b = workload.load_particles(g, sps[0], idx)
+        xn[first:first + idx.size] = a
+        un[first:first + idx.size] = b
+
+    with ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 4)) as ex:
+        list(ex.map(gen, range(0, n_p, chunk)))
+    q = workload.macro_charge(g, sps[0])
+    steps = args.steps
+    barrier()
+    t0 = time.perf_counter()
+    sim = pg.Simulation(g, sps, precision=args.precision, explicit=[(xn, un, q)],
+                        tile=tile if args.precision == "fp32" else None)
+    for _ in range(steps):
+        sim.step(1)
+        sim.diag()
+    got = sim.particles_into(xn, un)
+    sim.close()
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    barrier()
+    assert got == n_p
+    sec = max_over_ranks(t1 - t0)
+    value = sum_over_ranks(n_p * steps) / sec
+    h2d = 2 * n_p * 3 * 8
+    d2h = 2 * n_p * 3 * 8 + steps * 80
+    return {"value": value, "unit": UNIT, "h2d_bytes_per_step": h2d / steps, "d2h_bytes_per_step": d2h / steps,
+            "job": f"pic_init from pinned host FP64 arrays + {steps} x (pic_step + pic_diag) + pic_particles to "
+                   f"pinned host", "seconds": sec}
+
+
+# ---------------------------------------------------------------- oracle arms
+def oracle_sample(cells_target: int, ppc: int):
+    """A periodic sub-box of the workload (same dx, u_th, ppc) with about
+    cells_target cells."""
+    import workload
+    dims = [8, 8, 8]
+    k = 0
+    while dims[0] * dims[1] * dims[2] * 2 <= cells_target and max(dims) < 512:
+        dims[k % 3] *= 2
+        k += 1
+    dims.sort(reverse=True)
+    g, sps, _ = workload.config3(ppc, seed=20004, nx=tuple(dims))
+    return g, sps, dims
+
+
+def run_cpu_baseline(args, budget_s: float):
+    import oracle
+    import workload
+    g, sps, dims = oracle_sample(1 << 17, args.ppc)
+    st = oracle.from_workload(g, sps)
+    n = workload.n_particles(g, sps[0])
+    t0 = time.perf_counter()
+    st.step(1)
+    one = time.perf_counter() - t0
+    more = max(0, int(budget_s / max(one, 1e-3)) - 1)
+    t1 = time.perf_counter()
+    if more:
+        st.step(more)
+    total = (time.perf_counter() - t1) + one
+    steps = more + 1
+    return {"value": n * steps / total, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{dims[0]}x{dims[1]}x{dims[2]} periodic sub-box of the workload, {args.ppc} ppc "
+                      f"({n:,} electrons), {steps} full FP64 steps, single thread, {total:.1f} s"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    import workload
+    k, w = args.steps, args.warmup
+    # each step a bounded sample: about 150 s over the whole run at ~1.2 us per
+    # particle-step of the oracle
+    cells = int(150.0 / max(k + w, 1) / (args.ppc * 1.2e-6))
+    cells = max(512, min(cells, 1 << 21))
+    g, sps, dims = oracle_sample(cells, args.ppc)
+    g_full, sp_full, _ = make_workload(args, 0)
+    st = oracle.from_workload(g, sps)
+    n = workload.n_particles(g, sps[0])
+    if w:
+        st.step(w)
+    t0 = time.perf_counter()
+    st.step(k)
+    sec = time.perf_counter() - t0
+    value = n * k / sec
+    sample = (f"{dims[0]}x{dims[1]}x{dims[2]} periodic sub-box of the workload, {args.ppc} ppc ({n:,} electrons) "
+              f"per step, FP64 oracle, single thread")
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": k,
+           "warmup": w, "ms_per_step": sec / max(k, 1) * 1e3, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded lattice + Maxwellian loader)",
+           "config": describe(args, workload.n_particles(g_full, sp_full[0])),
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,232 @@
+/*
+ * pic.h -- C ABI of libpicgb, the GB300 (sm_103a) electromagnetic particle-in-cell
+ * hot path of Hemker's OSIRIS thesis (arxiv 1503.00276).
+ *
+ * One simulation step (thesis ch. 3, the PIC loop figure and the OSIRIS flow
+ * chart, where gather, push and deposit form one combined particle algorithm):
+ *   1. interpolate E^n, B^n linearly to every particle from each component's own
+ *      staggered lattice (eq. "2d-field-weighting-e3", 3D extension);
+ *   2. relativistic Boris push u^{n-1/2} -> u^{n+1/2} (eq. "momentum-update");
+ *   3. position update x^{n+1} = x^n + dt u/gamma (eq. "2d-position-update");
+ *   4. charge-conserving TRISTAN / Villasenor-Buneman current deposit from the
+ *      straight path x^n -> x^{n+1}, split at cell faces (sect. "PIC Algorithms for
+ *      2D-Cartesian Simulations"; 3D extension in sect. "3D-Cartesian ...");
+ *   5. periodic wrap of particles and fold of current guard cells (appendix,
+ *      nl_node_conf if_periodic);
+ *   6. optional binomial smoothing of J (appendix, nl_smooth);
+ *   7. field solve B -> B^{n+1/2} -> E^{n+1} -> B^{n+1}
+ *      (eqs. "2d-field-solve-b-part1", "-e", "-b-part2" and the 3D extension).
+ *
+ * Units are the thesis' normalised units (appendix "Input File"): t in 1/w_p,
+ * x in c/w_p, u = p/(m_e c), E and B in m_e c w_p / e, J in e n0 c, rho in e n0.
+ * Every quantity crossing this ABI is in these units.
+ *
+ * Conventions for every function below:
+ *  - Return value: PIC_OK or a negative pic_status; nothing aborts or exits.
+ *    pic_last_error() gives a one-line message for the last failure.
+ *  - Device work is enqueued on the CUDA stream passed to pic_init; functions that
+ *    hand data to the host synchronise that stream.
+ *  - Ownership: the library owns every device buffer it allocates (through the
+ *    caller's pic_allocator, or cudaMalloc when that is NULL) and frees them in
+ *    pic_destroy.  Caller arrays are only read or written during the call.
+ *  - Calls on one handle are not thread-safe; distinct handles are independent.
+ *  - Grid arrays crossing the ABI are dense [nz][ny][nx] (x1 fastest; nz = 1 in
+ *    2D) without guard cells.  Array index (i,j,k) of a component sits at
+ *    xmin + ((i,j,k) + stagger) * dx with the Yee staggering read off the
+ *    difference stencils of the field equations:
+ *      E1 (1/2,0,0)  E2 (0,1/2,0)  E3 (0,0,1/2)  B1 (0,1/2,1/2)  B2 (1/2,0,1/2)
+ *      B3 (1/2,1/2,0)  J like E  rho at the nodes (0,0,0)   (x3 entry dropped in 2D).
+ */
+#ifndef PICGB_PIC_H
+#define PICGB_PIC_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  PIC_OK = 0,
+  PIC_EINVAL = -1,        /* bad argument or unsupported combination */
+  PIC_ENOMEM = -2,        /* device allocation failed */
+  PIC_ECUDA = -3,         /* a CUDA call failed (message in pic_last_error) */
+  PIC_ECOURANT = -4,      /* dt >= 1/sqrt(sum dx_d^-2): the Courant condition
+                             c dt < dx (sect. on moving boundaries), multi-D form */
+  PIC_EOVERFLOW = -5,     /* particle storage exhausted (np_max, appendix nl_species) */
+  PIC_ENONFINITE = -6,    /* a NaN or Inf appeared in particles or fields */
+  PIC_ETIMEOUT = -7,      /* a bounded device-side wait gave up */
+  PIC_EUNSUPPORTED = -8,  /* valid request that this build does not implement */
+  PIC_ENOTBUILT = -9      /* the library was built without a GPU code path */
+} pic_status;
+
+/* Numerical form of the particle data and of the whole step. */
+typedef enum {
+  /* Reference form: global FP64 positions, FP64 momenta, FP64 fields and
+   * current, gather from global memory, deposit with FP64 global atomics. */
+  PIC_FP64_PLAIN = 0,
+  /* Fast form: int32 cell index within a tile + FP32 in-cell offsets in [0,1),
+   * FP32 momenta and fields; particles stored by tile; each tile's E/B stencil
+   * staged in shared memory by TMA and its current accumulated in shared memory
+   * before one TMA reduce-add into HBM. */
+  PIC_FP32_CELLOFF = 1
+} pic_precision;
+
+/* Boundary types (appendix nl_emf_bound / nl_spe_bound).  This build
+ * implements periodic boundaries (nl_node_conf if_periodic) only. */
+enum { PIC_BC_PERIODIC = 0 };
+
+/* Field selectors for pic_fields / pic_set_field. */
+enum { PIC_E1 = 0, PIC_E2, PIC_E3, PIC_B1, PIC_B2, PIC_B3, PIC_J1, PIC_J2, PIC_J3, PIC_RHO };
+
+#define PIC_MAX_SMOOTH 8
+
+/* Optional device allocator (e.g. a framework's caching allocator).  alloc
+ * returns a device pointer aligned to at least 256 bytes, or NULL on failure;
+ * free releases it.  ctx is passed back unchanged. */
+typedef struct {
+  void* ctx;
+  void* (*alloc)(void* ctx, size_t bytes);
+  void (*free)(void* ctx, void* ptr, size_t bytes);
+} pic_allocator;
+
+/* Grid, time step, fields and numerical options
+ * (appendix sections nl_grid, nl_space, nl_time_step, nl_el_mag_fld, nl_smooth). */
+typedef struct {
+  int ndim;                 /* 2 (2D3V: x1,x2 in the plane, three u components) or 3 */
+  int nx[3];                /* cells per direction (nx_p); nx[2] ignored in 2D */
+  double xmin[3];           /* lower corner of the box (nl_space xmin) */
+  double dx[3];             /* cell size */
+  double dt;                /* time step; must satisfy dt < 1/sqrt(sum_d dx_d^-2) */
+  int bc[3][2];             /* boundary type per direction and side: PIC_BC_PERIODIC */
+  double e0[3], b0[3];      /* constant external fields added at the gather (nl_el_mag_fld) */
+  int smooth_level[3];      /* smoothing passes of J per direction (0 = off) */
+  double smooth_w[3][PIC_MAX_SMOOTH][3];  /* weights (swfj) per direction and pass;
+                                             each pass is normalised by the weight sum */
+  double rho_bg;            /* fixed neutralising background charge density */
+  int init_e_gauss_x1;      /* 1: set the initial E1 from the discrete Gauss law
+                               along x1, column by column (exact for charge
+                               densities that vary only along x1); 0: E = 0 */
+  pic_precision precision;
+  int tile[3];              /* PIC_FP32_CELLOFF tile size in cells (0 = default:
+                               2D 32x16, 3D 8x8x8); nx must be a multiple */
+  double slack;             /* per-tile storage slack fraction (0 = default 0.25) */
+} pic_grid;
+
+/* One particle species (appendix nl_species / nl_profile).  Either loaded on the
+ * device from the num_par_x lattice and a seed, or given explicitly. */
+typedef struct {
+  double rqm;               /* m/q in units of m_e/e (electrons: -1) */
+  int ppc[3];               /* num_par_x: particles per cell direction (lattice) */
+  double uth[3];            /* vth: standard deviation of each u component */
+  double ufl[3];            /* vfl: fluid momentum */
+  double density;           /* uniform density in units of n0 (macroparticle charge
+                               q = sign(1/rqm) * density * cell volume / ppc) */
+  unsigned long long seed;  /* SplitMix64 stream for the thermal momenta */
+  /* Explicit particles instead of the lattice (n_explicit > 0): host arrays of
+   * n_explicit rows [x1 x2 x3] (global positions, x3 ignored in 2D) and
+   * [u1 u2 u3], FP64, copied during pic_init; every position must lie in the
+   * periodic box [xmin, xmin + nx dx) (else PIC_EINVAL).  q_explicit is the
+   * charge per macroparticle (0: density times the cell volume). */
+  long long n_explicit;
+  const double* x0;
+  const double* u0;
+  double q_explicit;
+  long long np_max;         /* storage limit in particles (0 = no limit) */
+  int track_ids;            /* 1: keep an int32 particle id (lattice index or explicit
+                               row) alongside each particle, for pic_particle_ids */
+} pic_species;
+
+typedef struct pic_sim pic_sim;   /* opaque; owns all device state */
+
+typedef struct {
+  long long step;           /* steps taken */
+  double time;              /* step * dt */
+  double field_energy;      /* (1/2) sum over grid values of (E^2 + B^2) * cell volume */
+  double kinetic_energy;    /* sum over particles of q*rqm*(gamma - 1), u at the last half step */
+  double total_charge;      /* sum of macroparticle charges (background excluded) */
+  double gauss_resid_max;   /* max over nodes |div E - rho - rho_bg|, backward differences */
+  double rho_abs_max;       /* max over nodes |rho + rho_bg| */
+  double rho_particles_abs_max; /* max over nodes |rho| of the particles alone */
+  long long n_particles;
+  int error_flags;          /* bit 0: non-finite value seen; bit 1: tile storage spill */
+} pic_diag_t;
+
+/* Create a simulation (thesis: global -> local object set-up).  Validates the
+ * Courant condition (PIC_ECOURANT), sizes and tile divisibility (PIC_EINVAL),
+ * allocates every device buffer, loads the particles and sets the initial fields
+ * (zero, or Gauss-consistent E1 when init_e_gauss_x1).  `stream` is a
+ * cudaStream_t (NULL = the legacy default stream).  On failure *out is NULL and
+ * nothing is leaked. */
+pic_status pic_init(const pic_grid* grid, const pic_species* species, int nspecies,
+                    const pic_allocator* alloc, void* stream, pic_sim** out);
+
+/* Advance nsteps full steps (the seven stages in the header comment).  Returns
+ * after the work is enqueued and the per-step device status has been checked;
+ * PIC_ENONFINITE if a NaN/Inf was flagged. */
+pic_status pic_step(pic_sim* sim, int nsteps);
+
+/* Copy one grid quantity (PIC_E1 .. PIC_RHO) as a dense FP64 [nz][ny][nx] array
+ * into dst (dst_bytes >= 8 * cells; device pointer if dst_on_device).  J is the
+ * (folded, smoothed) current of the last step; RHO is computed on demand from the
+ * current particle positions with the linear weights, background excluded. */
+pic_status pic_fields(pic_sim* sim, int which, void* dst, size_t dst_bytes, int dst_on_device);
+
+/* Overwrite one field component (PIC_E1 .. PIC_B3) from a dense FP64
+ * [nz][ny][nx] array (device pointer if src_on_device). */
+pic_status pic_set_field(pic_sim* sim, int which, const void* src, size_t src_bytes, int src_on_device);
+
+/* Copy the particles of one species as global FP64 positions x[n][3] and
+ * momenta u[n][3] (either pointer may be NULL).  cap is the row capacity of
+ * the destination; *n_out receives the particle count (PIC_EOVERFLOW when it
+ * exceeds cap, nothing copied).  Rows come in the library's storage order. */
+pic_status pic_particles(pic_sim* sim, int species, double* x, double* u, long long cap,
+                         long long* n_out, int dst_on_device);
+
+/* Particle ids (species with track_ids) in the same order as pic_particles. */
+pic_status pic_particle_ids(pic_sim* sim, int species, int* ids, long long cap, long long* n_out,
+                            int dst_on_device);
+
+/* Number of tiles of the PIC_FP32_CELLOFF store and the particle count of each
+ * (tiles in x1-fastest order), host array of ntiles entries. */
+pic_status pic_tile_counts(pic_sim* sim, int species, long long* counts, long long cap,
+                           long long* ntiles_out);
+
+/* FP64 device reductions of the Gauss-law residual, energies and charge
+ * (synchronises the stream). */
+pic_status pic_diag(pic_sim* sim, pic_diag_t* out);
+
+/* Per-stage device time accumulated with CUDA events on the simulation's stream
+ * while timing is enabled.  Slots: 0 particle kernel (gather+push+deposit),
+ * 1 current fold/smoothing, 2 field solve, 3 tile rebuilds, 4 whole steps;
+ * pic_timing_read returns milliseconds and the number of timed spans per slot
+ * since the last reset.  Slot 5 (when nslots > 5) counts every kernel that
+ * pic_step launched since the last reset, timing enabled or not (ms[5] = 0). */
+pic_status pic_timing_enable(pic_sim* sim, int enable);
+pic_status pic_timing_read(pic_sim* sim, double* ms, long long* launches, int nslots, int reset);
+
+/* Release every device buffer.  NULL is accepted. */
+pic_status pic_destroy(pic_sim* sim);
+
+/* Message of the last failure on this thread (never NULL). */
+const char* pic_last_error(void);
+
+/* Stateless tile binning (not in the thesis: the supporting per-tile sort).
+ * For n particles with integer cell coordinates cell[n][3] (device, int32,
+ * each in [0, nx_d)), computes the tile of each particle
+ * t = ((c3/T3)*nt2 + c2/T2)*nt1 + c1/T1 (nt_d = nx_d/T_d), the count of every
+ * tile (tile_count[ntiles], device int32), the exclusive prefix sum of the counts
+ * (tile_start[ntiles], device int64) and a permutation perm[n] (device int64)
+ * that lists particles tile by tile, in increasing particle index within each
+ * tile.  Scratch memory comes from `alloc` (NULL = cudaMalloc) and is
+ * released before returning.  `stream` is a cudaStream_t.  In 2D pass
+ * nx[2] = tile[2] = 1 and cell[.][2] = 0. */
+pic_status pic_bin_tiles(const int nx[3], const int tile[3], long long n, const int* cell,
+                         int* tile_count, long long* tile_start, long long* perm,
+                         const pic_allocator* alloc, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PICGB_PIC_H */

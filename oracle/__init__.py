@@ -16,6 +16,7 @@ from __future__ import annotations
 
 import ctypes as C
 import os
+import platform
 import subprocess
 import threading
 
@@ -24,6 +25,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
+_STAMP = os.path.join(_BUILD, "machine.txt")
 _SRC = os.path.join(_HERE, "pic_oracle.c")
 _lock = threading.Lock()
 _lib = None
@@ -34,7 +36,8 @@ MAX_PASS = 8
 def build(force: bool = False) -> str:
     """Compile the oracle with gcc (no fused multiply-add contraction)."""
     os.makedirs(_BUILD, exist_ok=True)
-    if (not force and os.path.exists(_LIB_PATH)
+    same_machine = os.path.exists(_STAMP) and open(_STAMP).read().strip() == platform.machine()
+    if (not force and same_machine and os.path.exists(_LIB_PATH)
             and os.path.getmtime(_LIB_PATH) >= max(os.path.getmtime(_SRC),
                                                    os.path.getmtime(os.path.join(_HERE, "pic_oracle.h")))):
         return _LIB_PATH
@@ -43,6 +46,8 @@ def build(force: bool = False) -> str:
            "-o", tmp, _SRC, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB_PATH)
+    with open(_STAMP, "w") as f:
+        f.write(platform.machine())
     return _LIB_PATH
 
 

@@ -1,0 +1,270 @@
+"""GB300 (sm_103a) hot path of the electromagnetic PIC method of Hemker's OSIRIS
+thesis (arxiv 1503.00276): gather E,B -> relativistic Boris push -> position
+update -> TRISTAN / Villasenor-Buneman charge-conserving current deposit, with
+the Yee field solve, current smoothing and the per-tile particle sort as
+supporting kernels.
+
+Every step runs in the CUDA kernels of ``libpicgb.so`` behind the C ABI of
+``include/pic.h``.  This module only marshals arguments; PyTorch (when
+present) supplies device memory through its caching allocator and the CUDA
+stream.  There is no CPU fallback: without the built library and a GPU every
+call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from . import _capi
+from ._capi import FIELD_NAMES, PIC_FP32_CELLOFF, PIC_FP64_PLAIN, PicError, check, load  # noqa: F401
+
+__all__ = ["Simulation", "bin_tiles", "load", "PicError", "PIC_FP64_PLAIN", "PIC_FP32_CELLOFF", "FIELD_NAMES"]
+
+
+def _torch():
+    try:
+        import torch
+        return torch
+    except Exception:  # pragma: no cover
+        return None
+
+
+class _TorchAllocator:
+    """pic_allocator backed by torch's caching allocator on the given stream."""
+
+    def __init__(self, torch, device, stream):
+        self.torch, self.device, self.stream = torch, device, stream
+        self._alloc = _capi.ALLOC_FN(self._do_alloc)
+        self._free = _capi.FREE_FN(self._do_free)
+        self.struct = _capi.PicAllocator(None, self._alloc, self._free)
+
+    def _do_alloc(self, ctx, nbytes):
+        try:
+            return int(self.torch.cuda.caching_allocator_alloc(int(nbytes), self.device, self.stream))
+        except Exception:
+            return None
+
+    def _do_free(self, ctx, ptr, nbytes):
+        self.torch.cuda.caching_allocator_delete(ptr)
+
+
+def _grid_struct(grid, precision, tile=None, slack=0.0):
+    g = _capi.PicGrid()
+    g.ndim = int(grid.ndim)
+    for d in range(3):
+        g.nx[d] = int(grid.nx[d]) if d < grid.ndim else 1
+        g.dx[d] = float(grid.dx[d]) if d < grid.ndim else 1.0
+        g.xmin[d] = float(grid.xmin[d])
+        g.e0[d] = float(grid.e0[d])
+        g.b0[d] = float(grid.b0[d])
+        g.smooth_level[d] = int(grid.smooth_level[d]) if d < grid.ndim else 0
+        sw = grid.smooth_w[d]
+        per_pass = isinstance(sw[0], (tuple, list))
+        for p in range(_capi.MAX_SMOOTH):
+            w = sw[min(p, len(sw) - 1)] if per_pass else sw
+            for m in range(3):
+                g.smooth_w[d][p][m] = float(w[m])
+        g.bc[d][0] = g.bc[d][1] = 0
+        g.tile[d] = int(tile[d]) if tile is not None and d < len(tile) else 0
+    g.dt = float(grid.dt)
+    g.rho_bg = float(grid.rho_bg)
+    g.init_e_gauss_x1 = int(bool(getattr(grid, "init_e_gauss_x1", False)))
+    g.precision = int(precision)
+    g.slack = float(slack)
+    return g
+
+
+def _species_struct(sp, explicit=None, track_ids=False, np_max=0):
+    s = _capi.PicSpecies()
+    s.rqm = float(sp.rqm)
+    for d in range(3):
+        s.ppc[d] = int(sp.ppc[d])
+        s.uth[d] = float(sp.uth[d])
+        s.ufl[d] = float(sp.ufl[d])
+    s.density = float(getattr(sp, "density", 1.0))
+    s.seed = int(getattr(sp, "seed", 0)) & 0xFFFFFFFFFFFFFFFF
+    s.track_ids = int(bool(track_ids))
+    s.np_max = int(np_max)
+    keep = None
+    if explicit is not None:
+        x, u, q = explicit
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        u = np.ascontiguousarray(u, dtype=np.float64)
+        assert x.shape == u.shape and x.ndim == 2 and x.shape[1] == 3
+        s.n_explicit = x.shape[0]
+        s.x0 = x.ctypes.data_as(C.POINTER(C.c_double))
+        s.u0 = u.ctypes.data_as(C.POINTER(C.c_double))
+        s.q_explicit = float(q)
+        keep = (x, u)
+    return s, keep
+
+
+class Simulation:
+    """One simulation handle (pic_init ... pic_destroy).
+
+    grid / species: objects with the attributes of ``pic_grid`` / ``pic_species``
+    (ndim, nx, dx, xmin, dt, e0, b0, smooth_level, smooth_w, rho_bg,
+    init_e_gauss_x1 / rqm, ppc, uth, ufl, density, seed).  ``explicit``: optional
+    list, per species, of (x[n,3], u[n,3], q) host arrays that replace the lattice
+    loader.  ``precision``: "fp64" (plain form) or "fp32" (cell-offset tiled form).
+    """
+
+    def __init__(self, grid, species, precision="fp64", explicit=None, tile=None, track_ids=False, slack=0.0,
+                 stream=None, use_torch_allocator=True, np_max=0):
+        self._lib = load()
+        torch = _torch()
+        prec = PIC_FP32_CELLOFF if precision in ("fp32", PIC_FP32_CELLOFF) else PIC_FP64_PLAIN
+        self.precision = prec
+        self.ndim = int(grid.ndim)
+        self.shape = (int(grid.nx[2]) if grid.ndim == 3 else 1, int(grid.nx[1]), int(grid.nx[0]))
+        self._g = _grid_struct(grid, prec, tile, slack)
+        specs = (_capi.PicSpecies * max(len(species), 1))()
+        self._keep = []
+        for k, sp in enumerate(species):
+            ex = explicit[k] if explicit is not None else None
+            s, keep = _species_struct(sp, ex, track_ids, np_max)
+            specs[k] = s
+            self._keep.append(keep)
+        self.nspecies = len(species)
+        self._torch = torch
+        self._alloc = None
+        stream_ptr = None
+        if torch is not None and torch.cuda.is_available():
+            st = stream if stream is not None else torch.cuda.current_stream()
+            self.stream = st
+            stream_ptr = C.c_void_p(st.cuda_stream)
+            if use_torch_allocator:
+                self._alloc = _TorchAllocator(torch, torch.cuda.current_device(), st)
+        else:
+            self.stream = None
+        h = C.c_void_p()
+        code = self._lib.pic_init(C.byref(self._g), specs, len(species),
+                                  C.byref(self._alloc.struct) if self._alloc else None, stream_ptr, C.byref(h))
+        self._keep = None
+        check(code, "pic_init")
+        self._h = h
+
+    # -- lifecycle ----------------------------------------------------------
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.pic_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # -- stepping -------------------------------------------------------------
+    def step(self, n: int = 1):
+        check(self._lib.pic_step(self._h, int(n)), "pic_step")
+
+    # -- grid data ------------------------------------------------------------
+    def _which(self, which):
+        return FIELD_NAMES[which] if isinstance(which, str) else int(which)
+
+    def fields(self, which) -> np.ndarray:
+        out = np.empty(self.shape, dtype=np.float64)
+        check(self._lib.pic_fields(self._h, self._which(which), out.ctypes.data_as(C.c_void_p), out.nbytes, 0),
+              "pic_fields")
+        return out
+
+    def fields_device(self, which):
+        torch = self._torch
+        out = torch.empty(self.shape, dtype=torch.float64, device="cuda")
+        check(self._lib.pic_fields(self._h, self._which(which), C.c_void_p(out.data_ptr()), out.numel() * 8, 1),
+              "pic_fields")
+        return out
+
+    def set_field(self, which, arr):
+        a = np.ascontiguousarray(np.asarray(arr, dtype=np.float64).reshape(self.shape))
+        check(self._lib.pic_set_field(self._h, self._which(which), a.ctypes.data_as(C.c_void_p), a.nbytes, 0),
+              "pic_set_field")
+
+    # -- particles --------------------------------------------------------------
+    def n_particles(self, species: int = 0) -> int:
+        n = C.c_longlong()
+        self._lib.pic_particles(self._h, species, None, None, 0, C.byref(n), 0)
+        return int(n.value)
+
+    def particles(self, species: int = 0):
+        n = self.n_particles(species)
+        x = np.empty((n, 3), dtype=np.float64)
+        u = np.empty((n, 3), dtype=np.float64)
+        got = C.c_longlong()
+        check(self._lib.pic_particles(self._h, species, x.ctypes.data_as(C.c_void_p), u.ctypes.data_as(C.c_void_p),
+                                      n, C.byref(got), 0), "pic_particles")
+        return x, u
+
+    def particles_into(self, x, u, species: int = 0) -> int:
+        """Copy into caller buffers (numpy host arrays or torch CUDA tensors)."""
+        on_dev = int(hasattr(x, "data_ptr"))
+        px = C.c_void_p(x.data_ptr() if on_dev else x.ctypes.data)
+        pu = C.c_void_p(u.data_ptr() if on_dev else u.ctypes.data)
+        got = C.c_longlong()
+        check(self._lib.pic_particles(self._h, species, px, pu, int(x.shape[0]), C.byref(got), on_dev),
+              "pic_particles")
+        return int(got.value)
+
+    def ids(self, species: int = 0) -> np.ndarray:
+        n = self.n_particles(species)
+        out = np.empty(n, dtype=np.int32)
+        got = C.c_longlong()
+        check(self._lib.pic_particle_ids(self._h, species, out.ctypes.data_as(C.c_void_p), n, C.byref(got), 0),
+              "pic_particle_ids")
+        return out
+
+    def tile_counts(self, species: int = 0) -> np.ndarray:
+        nt = C.c_longlong()
+        self._lib.pic_tile_counts(self._h, species, None, 0, C.byref(nt))
+        out = np.empty(int(nt.value), dtype=np.int64)
+        check(self._lib.pic_tile_counts(self._h, species, out.ctypes.data_as(C.POINTER(C.c_longlong)), out.size,
+                                        C.byref(nt)), "pic_tile_counts")
+        return out
+
+    # -- diagnostics ------------------------------------------------------------
+    def diag(self) -> dict:
+        d = _capi.PicDiag()
+        check(self._lib.pic_diag(self._h, C.byref(d)), "pic_diag")
+        return {k: getattr(d, k) for k, _ in _capi.PicDiag._fields_}
+
+    def timing_enable(self, on: bool = True):
+        check(self._lib.pic_timing_enable(self._h, int(on)), "pic_timing_enable")
+
+    def timing_read(self, reset: bool = False):
+        ms = (C.c_double * 6)()
+        n = (C.c_longlong * 6)()
+        check(self._lib.pic_timing_read(self._h, ms, n, 6, int(reset)), "pic_timing_read")
+        names = ["particles", "current", "fields", "rebuild", "step", "launches"]
+        return {names[k]: (ms[k], n[k]) for k in range(6)}
+
+
+def bin_tiles(nx, tile, cell, stream=None):
+    """Tile binning of device int32 cells[n,3] (torch CUDA tensor) through pic_bin_tiles.
+    Returns (tile_count int32, tile_start int64, perm int64) as torch tensors."""
+    torch = _torch()
+    lib = load()
+    assert cell.is_cuda and cell.dtype == torch.int32 and cell.is_contiguous()
+    n = cell.shape[0]
+    nt = 1
+    for d in range(3):
+        nt *= int(nx[d]) // int(tile[d])
+    counts = torch.empty(nt, dtype=torch.int32, device=cell.device)
+    start = torch.empty(nt, dtype=torch.int64, device=cell.device)
+    perm = torch.empty(max(n, 1), dtype=torch.int64, device=cell.device)
+    st = stream if stream is not None else torch.cuda.current_stream()
+    alloc = _TorchAllocator(torch, cell.device.index, st)
+    nxa = (C.c_int * 3)(*[int(v) for v in nx])
+    ta = (C.c_int * 3)(*[int(v) for v in tile])
+    check(lib.pic_bin_tiles(nxa, ta, n, C.c_void_p(cell.data_ptr()), C.c_void_p(counts.data_ptr()),
+                            C.c_void_p(start.data_ptr()), C.c_void_p(perm.data_ptr()), C.byref(alloc.struct),
+                            C.c_void_p(st.cuda_stream)), "pic_bin_tiles")
+    return counts, start, perm[:n]

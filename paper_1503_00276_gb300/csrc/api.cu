@@ -1,0 +1,1287 @@
+// api.cu -- the C ABI of libpicgb (include/pic.h): simulation state, loading,
+// the step schedule, copy-out and diagnostics.  All numerical work runs in the
+// kernels of k_*.cu; this file only allocates, orders launches and checks status.
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "kernels.h"
+
+namespace picgb {
+
+static thread_local std::string g_err = "no error";
+void set_error(const std::string& msg) { g_err = msg; }
+
+namespace {
+
+// ------------------------------------------------------------- small kernels
+__global__ void k_aos3_to_soa(const double* a, long long n, double* x0, double* x1, double* x2) {
+  const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  x0[k] = a[3 * k];
+  x1[k] = a[3 * k + 1];
+  x2[k] = a[3 * k + 2];
+}
+
+__global__ void k_soa_to_aos3(const double* x0, const double* x1, const double* x2, long long n, double* a) {
+  const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  a[3 * k] = x0[k];
+  a[3 * k + 1] = x1[k];
+  a[3 * k + 2] = x2 ? x2[k] : 0.0;
+}
+
+// Explicit positions must lie in the periodic box [xmin, xmin + nx dx).
+__global__ void k_check_box(int ndim, PushConst C, const double* x0, const double* x1, const double* x2, long long n,
+                            int* status) {
+  const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  const double* xs[3] = {x0, x1, x2};
+  for (int d = 0; d < ndim; ++d) {
+    const double v = xs[d][k];
+    if (!(v >= C.xmin[d] && v < C.xmin[d] + C.L[d])) atomicOr(status, ST_BADCELL);
+  }
+}
+
+__global__ void k_add_i32(const int* a, const int* b, int* c, int n) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < n) c[k] = a[k] + b[k];
+}
+
+struct StatusWord {
+  int status;
+  int spill_count;
+};
+
+// ------------------------------------------------------------- allocation
+struct Allocator {
+  pic_allocator user{};
+  bool has_user = false;
+  std::vector<std::pair<void*, size_t>> live;
+
+  void* get(size_t bytes) {
+    bytes = (bytes + 255) / 256 * 256;
+    if (bytes == 0) bytes = 256;
+    void* p = nullptr;
+    if (has_user) {
+      p = user.alloc(user.ctx, bytes);
+    } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      p = nullptr;
+    }
+    if (p) live.emplace_back(p, bytes);
+    return p;
+  }
+  void put(void* p) {
+    if (!p) return;
+    for (size_t k = 0; k < live.size(); ++k) {
+      if (live[k].first == p) {
+        if (has_user) {
+          if (user.free) user.free(user.ctx, p, live[k].second);
+        } else {
+          cudaFree(p);
+        }
+        live.erase(live.begin() + (long)k);
+        return;
+      }
+    }
+  }
+  void release_all() {
+    while (!live.empty()) put(live.back().first);
+  }
+};
+
+struct SpeciesState {
+  double rqm = -1.0, q = 0.0;
+  long long n = 0;
+  long long np_max = 0;
+  bool ids = false;
+  // FP64 plain
+  Plain plain{};
+  // FP32 tiled
+  Tiles tg{};
+  Part32 buf[2]{};
+  int* stay[2]{};
+  int* move[2]{};
+  int cur = 0;
+  long long slots = 0;
+  Flat32 spill{};
+  long long spill_cap = 0;
+};
+
+constexpr int kTimingSlots = 5;
+constexpr int kLaunchSlot = 5;
+
+}  // namespace
+}  // namespace picgb
+
+using namespace picgb;
+
+struct pic_sim {
+  pic_grid g{};
+  Layout L{};
+  int ndim = 0;
+  pic_precision prec = PIC_FP64_PLAIN;
+  cudaStream_t s = nullptr;
+  Allocator al;
+  void* fld = nullptr;  // 6 planes E1..B3
+  void* cur = nullptr;  // 3 planes J1..J3
+  void* tmp = nullptr;  // 1 plane (smoothing)
+  double* rho = nullptr;
+  double* dense = nullptr;  // 1 dense FP64 grid (copy-out staging)
+  Diag64* dacc = nullptr;
+  StatusWord* dstat = nullptr;
+  StatusWord* hstat = nullptr;  // pinned
+  std::vector<SpeciesState> sp;
+  CUtensorMap fmap{}, jmap{};
+  long long step = 0;
+  int T[3] = {1, 1, 1};
+  double slack = 0.25;
+  bool timing = false;
+  double t_ms[kTimingSlots] = {0, 0, 0, 0, 0};
+  long long t_n[kTimingSlots] = {0, 0, 0, 0, 0};
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_pending;
+  int sticky_flags = 0;
+  long long nlaunch = 0;  // kernels launched by pic_step since the last reset
+};
+
+namespace {
+
+size_t elem_bytes(const pic_sim* S) { return S->prec == PIC_FP32_CELLOFF ? 4 : 8; }
+
+template <typename T>
+T* fld_ptr(pic_sim* S, int c) {
+  return reinterpret_cast<T*>(S->fld) + (long long)c * S->L.plane;
+}
+template <typename T>
+T* cur_ptr(pic_sim* S, int c) {
+  return reinterpret_cast<T*>(S->cur) + (long long)c * S->L.plane;
+}
+
+pic_status cuda_check(const char* where) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    set_error(std::string(where) + ": " + cudaGetErrorString(e));
+    return PIC_ECUDA;
+  }
+  return PIC_OK;
+}
+
+PushConst make_const(const pic_sim* S, const SpeciesState& sp) {
+  PushConst C{};
+  const pic_grid& g = S->g;
+  double dvol = 1.0;
+  for (int d = 0; d < 3; ++d) {
+    C.xmin[d] = g.xmin[d];
+    C.dx[d] = d < S->ndim ? g.dx[d] : 1.0;
+    C.inv_dx[d] = 1.0 / C.dx[d];
+    C.e0[d] = g.e0[d];
+    C.b0[d] = g.b0[d];
+    C.L[d] = d < S->ndim ? g.nx[d] * g.dx[d] : 1.0;
+    if (d < S->ndim) dvol *= g.dx[d];
+  }
+  C.dt = g.dt;
+  C.rqm = sp.rqm;
+  C.q = sp.q;
+  C.dvol = dvol;
+  return C;
+}
+
+// ------------------------------------------------------------- timing
+cudaEvent_t ev_get(pic_sim* S) {
+  if (!S->ev_pool.empty()) {
+    cudaEvent_t e = S->ev_pool.back();
+    S->ev_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e;
+  cudaEventCreate(&e);
+  return e;
+}
+
+struct Span {
+  pic_sim* S;
+  int slot;
+  cudaEvent_t a = nullptr;
+  Span(pic_sim* s_, int slot_) : S(s_), slot(slot_) {
+    if (S->timing) {
+      a = ev_get(S);
+      cudaEventRecord(a, S->s);
+    }
+  }
+  ~Span() {
+    if (S->timing) {
+      cudaEvent_t b = ev_get(S);
+      cudaEventRecord(b, S->s);
+      S->ev_pending.push_back({slot, {a, b}});
+    }
+  }
+};
+
+void timing_collect(pic_sim* S) {
+  if (S->ev_pending.empty()) return;
+  cudaStreamSynchronize(S->s);
+  for (auto& p : S->ev_pending) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, p.second.first, p.second.second);
+    S->t_ms[p.first] += ms;
+    S->t_n[p.first] += 1;
+    S->ev_pool.push_back(p.second.first);
+    S->ev_pool.push_back(p.second.second);
+  }
+  S->ev_pending.clear();
+}
+
+// ------------------------------------------------------------- tensor maps
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+pic_status make_maps(pic_sim* S) {
+  auto enc = encode_fn();
+  if (!enc) {
+    set_error("cuTensorMapEncodeTiled not available from the driver");
+    return PIC_ECUDA;
+  }
+  const Layout& L = S->L;
+  const cuuint64_t ps = (cuuint64_t)L.plane * 4;
+  CUresult r1, r2;
+  if (S->ndim == 3) {
+    cuuint64_t gdim[4] = {(cuuint64_t)L.NX, (cuuint64_t)L.NY, (cuuint64_t)L.NZ, 6};
+    cuuint64_t gstr[3] = {(cuuint64_t)L.NX * 4, (cuuint64_t)L.NX * L.NY * 4, ps};
+    cuuint32_t box[4] = {(cuuint32_t)S->T[0] + 8, (cuuint32_t)S->T[1] + 2, (cuuint32_t)S->T[2] + 2, 6};
+    cuuint32_t es[4] = {1, 1, 1, 1};
+    r1 = enc(&S->fmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, S->fld, gdim, gstr, box, es,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    cuuint64_t jdim[4] = {(cuuint64_t)L.NX, (cuuint64_t)L.NY, (cuuint64_t)L.NZ, 3};
+    cuuint32_t jbox[4] = {(cuuint32_t)S->T[0] + 8, (cuuint32_t)S->T[1] + 3, (cuuint32_t)S->T[2] + 3, 3};
+    r2 = enc(&S->jmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, S->cur, jdim, gstr, jbox, es,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  } else {
+    cuuint64_t gdim[3] = {(cuuint64_t)L.NX, (cuuint64_t)L.NY, 6};
+    cuuint64_t gstr[2] = {(cuuint64_t)L.NX * 4, ps};
+    cuuint32_t box[3] = {(cuuint32_t)S->T[0] + 8, (cuuint32_t)S->T[1] + 2, 6};
+    cuuint32_t es[3] = {1, 1, 1};
+    r1 = enc(&S->fmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, S->fld, gdim, gstr, box, es,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    cuuint64_t jdim[3] = {(cuuint64_t)L.NX, (cuuint64_t)L.NY, 3};
+    cuuint32_t jbox[3] = {(cuuint32_t)S->T[0] + 8, (cuuint32_t)S->T[1] + 3, 3};
+    r2 = enc(&S->jmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, S->cur, jdim, gstr, jbox, es,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  }
+  if (r1 != CUDA_SUCCESS || r2 != CUDA_SUCCESS) {
+    set_error("cuTensorMapEncodeTiled failed (" + std::to_string((int)r1) + ", " + std::to_string((int)r2) + ")");
+    return PIC_ECUDA;
+  }
+  return PIC_OK;
+}
+
+// ------------------------------------------------------------- tiled store
+Part32 alloc_part(pic_sim* S, long long slots, bool ids, bool& ok) {
+  Part32 p{};
+  p.cell = (uint32_t*)S->al.get(4 * (size_t)slots);
+  for (int d = 0; d < 3; ++d) {
+    p.o[d] = (d < S->ndim) ? (float*)S->al.get(4 * (size_t)slots) : nullptr;
+    p.u[d] = (float*)S->al.get(4 * (size_t)slots);
+  }
+  if (S->ndim == 2) p.o[2] = nullptr;
+  p.id = ids ? (int*)S->al.get(4 * (size_t)slots) : nullptr;
+  ok = p.cell && p.o[0] && p.o[1] && (S->ndim == 2 || p.o[2]) && p.u[0] && p.u[1] && p.u[2] && (!ids || p.id);
+  return p;
+}
+
+void free_part(pic_sim* S, Part32& p) {
+  S->al.put(p.cell);
+  for (int d = 0; d < 3; ++d) {
+    S->al.put(p.o[d]);
+    S->al.put(p.u[d]);
+  }
+  S->al.put(p.id);
+  p = Part32{};
+}
+
+Flat32 alloc_flat(pic_sim* S, long long n, bool ids, bool& ok) {
+  Flat32 f{};
+  size_t m = (size_t)std::max<long long>(n, 1);
+  f.tile = (int*)S->al.get(4 * m);
+  f.cell = (uint32_t*)S->al.get(4 * m);
+  for (int d = 0; d < 3; ++d) {
+    f.o[d] = (float*)S->al.get(4 * m);
+    f.u[d] = (float*)S->al.get(4 * m);
+  }
+  f.id = ids ? (int*)S->al.get(4 * m) : nullptr;
+  ok = f.tile && f.cell && f.o[0] && f.o[1] && f.o[2] && f.u[0] && f.u[1] && f.u[2] && (!ids || f.id);
+  return f;
+}
+
+void free_flat(pic_sim* S, Flat32& f) {
+  S->al.put(f.tile);
+  S->al.put(f.cell);
+  for (int d = 0; d < 3; ++d) {
+    S->al.put(f.o[d]);
+    S->al.put(f.u[d]);
+  }
+  S->al.put(f.id);
+  f = Flat32{};
+}
+
+// Bin a flat particle list into buffer `cur` of the store, sizing every tile
+// region from its count (plus slack).  Regrows the store when needed.
+pic_status bin_flat(pic_sim* S, SpeciesState& sp, Flat32& flat, long long n) {
+  const int nt = sp.tg.ntiles;
+  int* counts = (int*)S->al.get(4 * (size_t)nt);
+  if (!counts) {
+    set_error("out of device memory (tile counts)");
+    return PIC_ENOMEM;
+  }
+  cudaMemsetAsync(counts, 0, 4 * (size_t)nt, S->s);
+  flat_count(flat, n, nt, counts, S->s);
+  std::vector<int> hc(nt);
+  cudaMemcpyAsync(hc.data(), counts, 4 * (size_t)nt, cudaMemcpyDeviceToHost, S->s);
+  if (cudaStreamSynchronize(S->s) != cudaSuccess) {
+    S->al.put(counts);
+    return cuda_check("binning");
+  }
+  long long total = 0;
+  for (int t = 0; t < nt; ++t) total += hc[t];
+  if (total != n) {
+    S->al.put(counts);
+    set_error("binning: " + std::to_string(n - total) + " particles outside the grid");
+    return PIC_EINVAL;
+  }
+  std::vector<int> hcap(nt);
+  std::vector<long long> hbase(nt);
+  long long slots = 0;
+  for (int t = 0; t < nt; ++t) {
+    long long c = hc[t];
+    long long extra = std::max<long long>(32, (long long)std::ceil(c * S->slack));
+    long long cap = (c + extra + 3) / 4 * 4;
+    if (cap > (1ll << 30)) cap = 1ll << 30;
+    hcap[t] = (int)cap;
+    hbase[t] = slots;
+    slots += cap;
+  }
+  if (sp.np_max > 0 && n > sp.np_max) {
+    S->al.put(counts);
+    set_error("species holds " + std::to_string(n) + " particles, more than np_max");
+    return PIC_EOVERFLOW;
+  }
+  if (slots > sp.slots) {
+    for (int b = 0; b < 2; ++b) free_part(S, sp.buf[b]);
+    bool ok0, ok1;
+    sp.buf[0] = alloc_part(S, slots, sp.ids, ok0);
+    sp.buf[1] = alloc_part(S, slots, sp.ids, ok1);
+    if (!ok0 || !ok1) {
+      S->al.put(counts);
+      set_error("out of device memory (particle store of " + std::to_string(slots) + " slots)");
+      return PIC_ENOMEM;
+    }
+    sp.slots = slots;
+  }
+  cudaMemcpyAsync(sp.tg.cap, hcap.data(), 4 * (size_t)nt, cudaMemcpyHostToDevice, S->s);
+  cudaMemcpyAsync(sp.tg.base, hbase.data(), 8 * (size_t)nt, cudaMemcpyHostToDevice, S->s);
+  int* cursor = (int*)S->al.get(4 * (size_t)nt);
+  if (!cursor) {
+    S->al.put(counts);
+    set_error("out of device memory (cursor)");
+    return PIC_ENOMEM;
+  }
+  cudaMemsetAsync(cursor, 0, 4 * (size_t)nt, S->s);
+  flat_scatter(flat, n, sp.tg, cursor, sp.buf[sp.cur], S->s);
+  cudaMemcpyAsync(sp.stay[sp.cur], counts, 4 * (size_t)nt, cudaMemcpyDeviceToDevice, S->s);
+  cudaMemsetAsync(sp.move[sp.cur], 0, 4 * (size_t)nt, S->s);
+  cudaError_t e = cudaStreamSynchronize(S->s);
+  S->al.put(cursor);
+  S->al.put(counts);
+  if (e != cudaSuccess) return cuda_check("binning scatter");
+  sp.n = n;
+  return PIC_OK;
+}
+
+// Flatten the current buffer of a tiled species (+ spill list) into `flat`.
+pic_status flatten(pic_sim* S, SpeciesState& sp, Flat32& flat, long long& n, bool include_spill, int spill_n,
+                   bool& allocated) {
+  const int nt = sp.tg.ntiles;
+  int* tot = (int*)S->al.get(4 * (size_t)nt);
+  long long* off = (long long*)S->al.get(8 * (size_t)nt + 8);
+  void* scr = S->al.get(scan_scratch_bytes(nt));
+  if (!tot || !off || !scr) {
+    S->al.put(tot);
+    S->al.put(off);
+    S->al.put(scr);
+    set_error("out of device memory (flatten)");
+    return PIC_ENOMEM;
+  }
+  k_add_i32<<<(nt + 255) / 256, 256, 0, S->s>>>(sp.stay[sp.cur], sp.move[sp.cur], tot, nt);
+  exclusive_scan_i32(tot, off, nt, scr, S->s);
+  long long last_off = 0;
+  int last_cnt = 0;
+  cudaMemcpyAsync(&last_off, off + nt - 1, 8, cudaMemcpyDeviceToHost, S->s);
+  cudaMemcpyAsync(&last_cnt, tot + nt - 1, 4, cudaMemcpyDeviceToHost, S->s);
+  if (cudaStreamSynchronize(S->s) != cudaSuccess) return cuda_check("flatten");
+  const long long nstore = last_off + last_cnt;
+  n = nstore + (include_spill ? spill_n : 0);
+  bool ok = true;
+  flat = alloc_flat(S, n, sp.ids, ok);
+  allocated = true;
+  if (!ok) {
+    S->al.put(tot);
+    S->al.put(off);
+    S->al.put(scr);
+    free_flat(S, flat);
+    allocated = false;
+    set_error("out of device memory (flat copy of " + std::to_string(n) + " particles)");
+    return PIC_ENOMEM;
+  }
+  tiled_flatten(sp.tg, sp.buf[sp.cur], sp.stay[sp.cur], sp.move[sp.cur], off, flat, S->s);
+  if (include_spill && spill_n > 0) {
+    auto cp = [&](void* dst, const void* src) {
+      cudaMemcpyAsync((char*)dst + 4 * (size_t)nstore, src, 4 * (size_t)spill_n, cudaMemcpyDeviceToDevice, S->s);
+    };
+    cp(flat.tile, sp.spill.tile);
+    cp(flat.cell, sp.spill.cell);
+    for (int d = 0; d < 3; ++d) {
+      cp(flat.o[d], sp.spill.o[d]);
+      cp(flat.u[d], sp.spill.u[d]);
+    }
+    if (flat.id && sp.spill.id) cp(flat.id, sp.spill.id);
+  }
+  cudaError_t e = cudaStreamSynchronize(S->s);
+  S->al.put(tot);
+  S->al.put(off);
+  S->al.put(scr);
+  if (e != cudaSuccess) return cuda_check("flatten");
+  return PIC_OK;
+}
+
+pic_status rebuild(pic_sim* S, SpeciesState& sp, int spill_n) {
+  Flat32 flat{};
+  long long n = 0;
+  bool alloc = false;
+  pic_status st = flatten(S, sp, flat, n, true, spill_n, alloc);
+  if (st == PIC_OK) st = bin_flat(S, sp, flat, n);
+  if (alloc) free_flat(S, flat);
+  return st;
+}
+
+// ------------------------------------------------------------- loading
+pic_status load_species(pic_sim* S, const pic_species& in, SpeciesState& sp) {
+  const pic_grid& g = S->g;
+  const int nd = S->ndim;
+  double dvol = 1.0;
+  long long ncells = 1;
+  for (int d = 0; d < nd; ++d) {
+    dvol *= g.dx[d];
+    ncells *= g.nx[d];
+  }
+  sp.rqm = in.rqm;
+  sp.ids = in.track_ids != 0;
+  sp.np_max = in.np_max;
+  if (in.rqm == 0.0 || !std::isfinite(in.rqm)) {
+    set_error("species rqm must be finite and non-zero");
+    return PIC_EINVAL;
+  }
+  long long n;
+  long long ppc = 1;
+  if (in.n_explicit > 0) {
+    if (!in.x0 || !in.u0) {
+      set_error("explicit species needs x0 and u0");
+      return PIC_EINVAL;
+    }
+    n = in.n_explicit;
+  } else {
+    for (int d = 0; d < 3; ++d) {
+      const int v = d < nd ? in.ppc[d] : 1;
+      if (d < nd && v <= 0) {
+        set_error("species ppc must be positive");
+        return PIC_EINVAL;
+      }
+      ppc *= (d < nd ? v : 1);
+    }
+    n = ncells * ppc;
+  }
+  if (in.np_max > 0 && n > in.np_max) {
+    set_error("species has " + std::to_string(n) + " particles, more than np_max");
+    return PIC_EOVERFLOW;
+  }
+  if (n > (1ll << 31) - 1 && sp.ids) {
+    set_error("particle ids are int32: too many particles");
+    return PIC_EINVAL;
+  }
+  // macroparticle charge: density * cell volume / ppc with the sign of q;
+  // an explicit list gives it directly (q_explicit), else one particle per cell
+  const double sign = in.rqm < 0 ? -1.0 : 1.0;
+  if (in.n_explicit > 0)
+    sp.q = in.q_explicit != 0.0 ? in.q_explicit : sign * in.density * dvol;
+  else
+    sp.q = sign * in.density * dvol / (double)ppc;
+  sp.n = n;
+
+  // FP64 SoA of the initial state, in chunks (device)
+  const long long chunk = S->prec == PIC_FP64_PLAIN ? std::max<long long>(n, 1) : std::min<long long>(n, 1ll << 25);
+  double* xs[3] = {nullptr, nullptr, nullptr};
+  double* us[3] = {nullptr, nullptr, nullptr};
+  int* ids = nullptr;
+  double* aos = nullptr;
+  auto fail = [&](const char* what) {
+    set_error(std::string("out of device memory (") + what + ")");
+    return PIC_ENOMEM;
+  };
+  if (S->prec == PIC_FP64_PLAIN) {
+    for (int d = 0; d < 3; ++d) {
+      sp.plain.x[d] = (d < nd) ? (double*)S->al.get(8 * (size_t)std::max<long long>(n, 1)) : nullptr;
+      sp.plain.u[d] = (double*)S->al.get(8 * (size_t)std::max<long long>(n, 1));
+      if ((d < nd && !sp.plain.x[d]) || !sp.plain.u[d]) return fail("particles");
+    }
+    sp.plain.id = sp.ids ? (int*)S->al.get(4 * (size_t)std::max<long long>(n, 1)) : nullptr;
+    if (sp.ids && !sp.plain.id) return fail("ids");
+    sp.plain.n = n;
+  }
+  Flat32 flat{};
+  bool flat_ok = true;
+  if (S->prec == PIC_FP32_CELLOFF) {
+    flat = alloc_flat(S, n, sp.ids, flat_ok);
+    if (!flat_ok) {
+      free_flat(S, flat);
+      return fail("flat staging");
+    }
+  }
+  double* scratch_x2 = nullptr;
+  for (long long first = 0; first < n; first += chunk) {
+    const long long cnt = std::min(chunk, n - first);
+    if (S->prec == PIC_FP64_PLAIN) {
+      for (int d = 0; d < 3; ++d) {
+        xs[d] = sp.plain.x[d] ? sp.plain.x[d] + first : nullptr;
+        us[d] = sp.plain.u[d] + first;
+      }
+      ids = sp.plain.id ? sp.plain.id + first : nullptr;
+      if (!xs[2]) {
+        if (!scratch_x2) scratch_x2 = (double*)S->al.get(8 * (size_t)chunk);
+        if (!scratch_x2) return fail("staging");
+        xs[2] = scratch_x2;
+      }
+    } else {
+      if (!xs[0]) {
+        for (int d = 0; d < 3; ++d) {
+          xs[d] = (double*)S->al.get(8 * (size_t)chunk);
+          us[d] = (double*)S->al.get(8 * (size_t)chunk);
+          if (!xs[d] || !us[d]) return fail("staging");
+        }
+        ids = sp.ids ? (int*)S->al.get(4 * (size_t)chunk) : nullptr;
+      }
+    }
+    if (in.n_explicit > 0) {
+      if (!aos) aos = (double*)S->al.get(24 * (size_t)chunk);
+      if (!aos) return fail("staging");
+      cudaMemcpyAsync(aos, in.x0 + 3 * first, 24 * (size_t)cnt, cudaMemcpyHostToDevice, S->s);
+      k_aos3_to_soa<<<(unsigned)((cnt + 255) / 256), 256, 0, S->s>>>(aos, cnt, xs[0], xs[1], xs[2]);
+      k_check_box<<<(unsigned)((cnt + 255) / 256), 256, 0, S->s>>>(nd, make_const(S, sp), xs[0], xs[1], xs[2], cnt,
+                                                                   &S->dstat->status);
+      cudaMemcpyAsync(aos, in.u0 + 3 * first, 24 * (size_t)cnt, cudaMemcpyHostToDevice, S->s);
+      k_aos3_to_soa<<<(unsigned)((cnt + 255) / 256), 256, 0, S->s>>>(aos, cnt, us[0], us[1], us[2]);
+      if (ids) {
+        std::vector<int> h((size_t)cnt);
+        for (long long k = 0; k < cnt; ++k) h[(size_t)k] = (int)(first + k);
+        cudaMemcpyAsync(ids, h.data(), 4 * (size_t)cnt, cudaMemcpyHostToDevice, S->s);
+        cudaStreamSynchronize(S->s);
+      }
+    } else {
+      LatticeSpec L{};
+      L.ndim = nd;
+      for (int d = 0; d < 3; ++d) {
+        L.nx[d] = d < nd ? g.nx[d] : 1;
+        L.xmin[d] = g.xmin[d];
+        L.dx[d] = d < nd ? g.dx[d] : 1.0;
+        L.ppc[d] = d < nd ? in.ppc[d] : 1;
+        L.uth[d] = in.uth[d];
+        L.ufl[d] = in.ufl[d];
+      }
+      L.seed = in.seed;
+      lattice_load(L, first, cnt, xs, us, ids, S->s);
+    }
+    if (S->prec == PIC_FP32_CELLOFF) {
+      Flat32 part = flat;
+      part.tile += first;
+      part.cell += first;
+      for (int d = 0; d < 3; ++d) {
+        part.o[d] += first;
+        part.u[d] += first;
+      }
+      if (part.id) part.id += first;
+      PushConst C = make_const(S, sp);
+      global_to_flat(nd, S->L, sp.tg, C, xs, us, ids, cnt, part, &S->dstat->status, S->s);
+    }
+    cudaError_t e = cudaStreamSynchronize(S->s);
+    if (e != cudaSuccess) return cuda_check("loading particles");
+  }
+  if (aos) S->al.put(aos);
+  if (scratch_x2) S->al.put(scratch_x2);
+  if (S->prec == PIC_FP32_CELLOFF) {
+    for (int d = 0; d < 3; ++d) {
+      S->al.put(xs[d]);
+      S->al.put(us[d]);
+    }
+    S->al.put(ids);
+    pic_status st = bin_flat(S, sp, flat, n);
+    free_flat(S, flat);
+    if (st != PIC_OK) return st;
+  }
+  return cuda_check("loading particles");
+}
+
+pic_status setup_tiles(pic_sim* S, SpeciesState& sp) {
+  Tiles& tg = sp.tg;
+  tg.ndim = S->ndim;
+  tg.ntiles = 1;
+  for (int d = 0; d < 3; ++d) {
+    tg.T[d] = d < S->ndim ? S->T[d] : 1;
+    tg.nt[d] = d < S->ndim ? S->g.nx[d] / S->T[d] : 1;
+    tg.ntiles *= tg.nt[d];
+  }
+  tg.base = (long long*)S->al.get(8 * (size_t)tg.ntiles);
+  tg.cap = (int*)S->al.get(4 * (size_t)tg.ntiles);
+  for (int b = 0; b < 2; ++b) {
+    sp.stay[b] = (int*)S->al.get(4 * (size_t)tg.ntiles);
+    sp.move[b] = (int*)S->al.get(4 * (size_t)tg.ntiles);
+  }
+  if (!tg.base || !tg.cap || !sp.stay[0] || !sp.stay[1] || !sp.move[0] || !sp.move[1]) {
+    set_error("out of device memory (tile tables)");
+    return PIC_ENOMEM;
+  }
+  cudaMemsetAsync(sp.stay[1], 0, 4 * (size_t)tg.ntiles, S->s);
+  cudaMemsetAsync(sp.move[1], 0, 4 * (size_t)tg.ntiles, S->s);
+  return PIC_OK;
+}
+
+pic_status alloc_spill(pic_sim* S, SpeciesState& sp) {
+  sp.spill_cap = std::max<long long>(1 << 16, sp.n / 64);
+  bool ok = true;
+  sp.spill = alloc_flat(S, sp.spill_cap, sp.ids, ok);
+  if (!ok) {
+    set_error("out of device memory (spill list)");
+    return PIC_ENOMEM;
+  }
+  return PIC_OK;
+}
+
+// rho of every species into S->rho (padded FP64), guards folded
+void compute_rho(pic_sim* S) {
+  cudaMemsetAsync(S->rho, 0, 8 * (size_t)S->L.plane, S->s);
+  for (auto& sp : S->sp) {
+    PushConst C = make_const(S, sp);
+    if (S->prec == PIC_FP64_PLAIN)
+      plain_rho(S->ndim, S->L, C, sp.plain, S->rho, S->s);
+    else
+      tiled_rho(S->L, C, sp.tg, sp.buf[sp.cur], sp.stay[sp.cur], sp.move[sp.cur], S->rho, S->s);
+  }
+  double* r[1] = {S->rho};
+  fold_guards<double>(S->L, r, 1, S->s);
+}
+
+template <typename T>
+void field_step(pic_sim* S) {
+  const Layout& L = S->L;
+  T* e[3] = {fld_ptr<T>(S, 0), fld_ptr<T>(S, 1), fld_ptr<T>(S, 2)};
+  T* b[3] = {fld_ptr<T>(S, 3), fld_ptr<T>(S, 4), fld_ptr<T>(S, 5)};
+  T* j[3] = {cur_ptr<T>(S, 0), cur_ptr<T>(S, 1), cur_ptr<T>(S, 2)};
+  {
+    Span sp(S, 1);
+    fold_guards<T>(L, j, 3, S->s);
+    S->nlaunch += 1;
+    for (int d = 0; d < S->ndim; ++d)
+      for (int pass = 0; pass < S->g.smooth_level[d]; ++pass) {
+        const double* w = S->g.smooth_w[d][pass];
+        for (int c = 0; c < 3; ++c) smooth_pass<T>(L, j[c], reinterpret_cast<T*>(S->tmp), d, w[0], w[1], w[2], S->s);
+        S->nlaunch += 3;
+      }
+  }
+  {
+    Span sp(S, 2);
+    double dx[3] = {S->g.dx[0], S->g.dx[1], S->ndim == 3 ? S->g.dx[2] : 1.0};
+    yee_b_half<T>(L, e, b, S->g.dt, dx, S->s);
+    fill_guards<T>(L, b, 3, S->s);
+    yee_e<T>(L, e, b, j, S->g.dt, dx, S->s);
+    fill_guards<T>(L, e, 3, S->s);
+    yee_b_half<T>(L, e, b, S->g.dt, dx, S->s);
+    fill_guards<T>(L, b, 3, S->s);
+    S->nlaunch += 6;
+  }
+}
+
+pic_status one_step(pic_sim* S, bool check_now) {
+  Span whole(S, 4);
+  cudaMemsetAsync(S->cur, 0, 3 * elem_bytes(S) * (size_t)S->L.plane, S->s);
+  {
+    Span sp(S, 0);
+    for (auto& s : S->sp) {
+      PushConst C = make_const(S, s);
+      if (S->prec == PIC_FP64_PLAIN) {
+        double* f[6];
+        double* j[3];
+        for (int c = 0; c < 6; ++c) f[c] = fld_ptr<double>(S, c);
+        for (int c = 0; c < 3; ++c) j[c] = cur_ptr<double>(S, c);
+        plain_push(S->ndim, S->L, C, s.plain, f, j, &S->dstat->status, S->s);
+      } else {
+        const int in = s.cur, out = 1 - s.cur;
+        tiled_push(S->L, C, s.tg, s.buf[in], s.stay[in], s.move[in], s.buf[out], s.stay[out], s.move[out],
+                   s.spill, &S->dstat->spill_count, s.spill_cap, &S->fmap, &S->jmap, &S->dstat->status, S->s);
+        s.cur = out;
+      }
+      S->nlaunch += s.n > 0 || S->prec == PIC_FP32_CELLOFF ? 1 : 0;
+    }
+  }
+  if (S->prec == PIC_FP64_PLAIN)
+    field_step<double>(S);
+  else
+    field_step<float>(S);
+  ++S->step;
+  pic_status st = cuda_check("step launch");
+  if (st != PIC_OK) return st;
+  if (!check_now) return PIC_OK;
+  cudaMemcpyAsync(S->hstat, S->dstat, sizeof(StatusWord), cudaMemcpyDeviceToHost, S->s);
+  if (cudaStreamSynchronize(S->s) != cudaSuccess) return cuda_check("step");
+  const int flags = S->hstat->status;
+  S->sticky_flags |= flags;
+  if (flags & ST_SPILL) {
+    if (flags & ST_SPILL_LOST) {
+      set_error("particle spill list overflowed: particles were lost");
+      return PIC_EOVERFLOW;
+    }
+    // the spilled particles were fully advanced; re-bin before the next step
+    Span rb(S, 3);
+    for (auto& s : S->sp) {
+      st = rebuild(S, s, S->hstat->spill_count);
+      if (st != PIC_OK) return st;
+    }
+    cudaMemsetAsync(S->dstat, 0, sizeof(StatusWord), S->s);
+  }
+  if (flags & ST_TIMEOUT) {
+    set_error("a bounded device wait gave up (TMA copy did not complete)");
+    return PIC_ETIMEOUT;
+  }
+  if (flags & (ST_NONFINITE | ST_BADCELL)) {
+    set_error("non-finite particle or field value");
+    return PIC_ENONFINITE;
+  }
+  return PIC_OK;
+}
+
+pic_status validate_grid(const pic_grid* g) {
+  if (!g) {
+    set_error("grid is NULL");
+    return PIC_EINVAL;
+  }
+  if (g->ndim != 2 && g->ndim != 3) {
+    set_error("ndim must be 2 or 3");
+    return PIC_EINVAL;
+  }
+  double s = 0.0;
+  for (int d = 0; d < g->ndim; ++d) {
+    if (g->nx[d] < 4 || !(g->dx[d] > 0.0) || !std::isfinite(g->dx[d])) {
+      set_error("nx must be >= 4 and dx > 0 in every direction");
+      return PIC_EINVAL;
+    }
+    s += 1.0 / (g->dx[d] * g->dx[d]);
+    for (int side = 0; side < 2; ++side)
+      if (g->bc[d][side] != PIC_BC_PERIODIC) {
+        set_error("only periodic boundaries are implemented");
+        return PIC_EUNSUPPORTED;
+      }
+    if (g->smooth_level[d] < 0 || g->smooth_level[d] > PIC_MAX_SMOOTH) {
+      set_error("smooth_level out of range");
+      return PIC_EINVAL;
+    }
+  }
+  if (!(g->dt > 0.0) || !std::isfinite(g->dt)) {
+    set_error("dt must be positive");
+    return PIC_EINVAL;
+  }
+  if (g->dt >= 1.0 / std::sqrt(s)) {
+    set_error("Courant condition violated: dt >= 1/sqrt(sum dx^-2)");
+    return PIC_ECOURANT;
+  }
+  if (g->precision != PIC_FP64_PLAIN && g->precision != PIC_FP32_CELLOFF) {
+    set_error("unknown precision");
+    return PIC_EINVAL;
+  }
+  return PIC_OK;
+}
+
+}  // namespace
+
+// ============================================================= the C ABI
+extern "C" {
+
+const char* pic_last_error(void) { return g_err.c_str(); }
+
+pic_status pic_destroy(pic_sim* S) {
+  if (!S) return PIC_OK;
+  cudaStreamSynchronize(S->s);
+  timing_collect(S);
+  for (auto e : S->ev_pool) cudaEventDestroy(e);
+  S->al.release_all();
+  if (S->hstat) cudaFreeHost(S->hstat);
+  delete S;
+  return PIC_OK;
+}
+
+pic_status pic_init(const pic_grid* grid, const pic_species* species, int nspecies, const pic_allocator* alloc,
+                    void* stream, pic_sim** out) {
+  if (!out) {
+    set_error("out is NULL");
+    return PIC_EINVAL;
+  }
+  *out = nullptr;
+  pic_status st = validate_grid(grid);
+  if (st != PIC_OK) return st;
+  if (nspecies < 0 || (nspecies > 0 && !species)) {
+    set_error("bad species list");
+    return PIC_EINVAL;
+  }
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+    cudaGetLastError();
+    set_error("no CUDA device");
+    return PIC_ECUDA;
+  }
+  pic_sim* S = new pic_sim();
+  S->g = *grid;
+  S->ndim = grid->ndim;
+  S->prec = grid->precision;
+  S->s = reinterpret_cast<cudaStream_t>(stream);
+  if (alloc && alloc->alloc) {
+    S->al.user = *alloc;
+    S->al.has_user = true;
+  }
+  S->slack = grid->slack > 0.0 ? grid->slack : 0.25;
+  int nxv[3] = {grid->nx[0], grid->nx[1], grid->ndim == 3 ? grid->nx[2] : 1};
+  S->L = make_layout(S->ndim, nxv);
+  if (S->prec == PIC_FP32_CELLOFF) {
+    for (int d = 0; d < 3; ++d) S->T[d] = d < S->ndim ? grid->tile[d] : 1;
+    if (S->T[0] <= 0 || S->T[1] <= 0 || (S->ndim == 3 && S->T[2] <= 0)) {
+      if (S->ndim == 3) {
+        S->T[0] = S->T[1] = S->T[2] = 8;
+      } else {
+        S->T[0] = 32;
+        S->T[1] = 16;
+        S->T[2] = 1;
+      }
+    }
+    if (tiled_push_smem_bytes(S->ndim, S->T) < 0) {
+      set_error("unsupported tile shape (3D: 8x8x8, 16x8x4, 4x4x4; 2D: 32x16, 16x16, 8x8)");
+      delete S;
+      return PIC_EUNSUPPORTED;
+    }
+    for (int d = 0; d < S->ndim; ++d)
+      if (grid->nx[d] % S->T[d] != 0) {
+        set_error("nx must be a multiple of the tile size in every direction");
+        delete S;
+        return PIC_EINVAL;
+      }
+  }
+  auto bail = [&](pic_status code) {
+    pic_destroy(S);
+    return code;
+  };
+  const size_t eb = elem_bytes(S);
+  S->fld = S->al.get(6 * eb * (size_t)S->L.plane);
+  S->cur = S->al.get(3 * eb * (size_t)S->L.plane);
+  S->tmp = S->al.get(eb * (size_t)S->L.plane);
+  S->rho = (double*)S->al.get(8 * (size_t)S->L.plane);
+  S->dense = (double*)S->al.get(8 * (size_t)S->L.nx * S->L.ny * S->L.nz);
+  S->dacc = (Diag64*)S->al.get(sizeof(Diag64));
+  S->dstat = (StatusWord*)S->al.get(sizeof(StatusWord));
+  if (!S->fld || !S->cur || !S->tmp || !S->rho || !S->dense || !S->dacc || !S->dstat) {
+    set_error("out of device memory (grid arrays)");
+    return bail(PIC_ENOMEM);
+  }
+  if (cudaMallocHost(&S->hstat, sizeof(StatusWord)) != cudaSuccess) {
+    S->hstat = nullptr;
+    set_error("pinned host allocation failed");
+    return bail(PIC_ENOMEM);
+  }
+  cudaMemsetAsync(S->fld, 0, 6 * eb * (size_t)S->L.plane, S->s);
+  cudaMemsetAsync(S->cur, 0, 3 * eb * (size_t)S->L.plane, S->s);
+  cudaMemsetAsync(S->tmp, 0, eb * (size_t)S->L.plane, S->s);
+  cudaMemsetAsync(S->dstat, 0, sizeof(StatusWord), S->s);
+  if ((st = cuda_check("pic_init")) != PIC_OK) return bail(st);
+  S->sp.resize((size_t)nspecies);
+  for (int k = 0; k < nspecies; ++k) {
+    if (S->prec == PIC_FP32_CELLOFF) {
+      if ((st = setup_tiles(S, S->sp[k])) != PIC_OK) return bail(st);
+    }
+    if ((st = load_species(S, species[k], S->sp[k])) != PIC_OK) return bail(st);
+    if (S->prec == PIC_FP32_CELLOFF) {
+      if ((st = alloc_spill(S, S->sp[k])) != PIC_OK) return bail(st);
+    }
+  }
+  // explicit positions were checked on the device; nothing may read them
+  // before that check is known to have passed
+  if (cudaStreamSynchronize(S->s) != cudaSuccess) return bail(cuda_check("pic_init"));
+  cudaMemcpy(S->hstat, S->dstat, sizeof(StatusWord), cudaMemcpyDeviceToHost);
+  if (S->hstat->status & ST_BADCELL) {
+    set_error("initial particle position outside the box or not finite");
+    return bail(PIC_EINVAL);
+  }
+  if (S->prec == PIC_FP32_CELLOFF) {
+    if ((st = make_maps(S)) != PIC_OK) return bail(st);
+  }
+  if (grid->init_e_gauss_x1) {
+    compute_rho(S);
+    if (S->prec == PIC_FP64_PLAIN)
+      init_e_gauss_x1<double>(S->L, S->rho, grid->rho_bg, grid->dx[0], fld_ptr<double>(S, 0), S->s);
+    else
+      init_e_gauss_x1<float>(S->L, S->rho, grid->rho_bg, grid->dx[0], fld_ptr<float>(S, 0), S->s);
+  }
+  if (S->prec == PIC_FP64_PLAIN) {
+    double* f[6];
+    for (int c = 0; c < 6; ++c) f[c] = fld_ptr<double>(S, c);
+    fill_guards<double>(S->L, f, 6, S->s);
+  } else {
+    float* f[6];
+    for (int c = 0; c < 6; ++c) f[c] = fld_ptr<float>(S, c);
+    fill_guards<float>(S->L, f, 6, S->s);
+  }
+  if (cudaStreamSynchronize(S->s) != cudaSuccess) return bail(cuda_check("pic_init"));
+  if ((st = cuda_check("pic_init")) != PIC_OK) return bail(st);
+  cudaMemcpy(S->hstat, S->dstat, sizeof(StatusWord), cudaMemcpyDeviceToHost);
+  if (S->hstat->status & ST_BADCELL) {
+    set_error("initial particle position outside the box or not finite");
+    return bail(PIC_EINVAL);
+  }
+  *out = S;
+  return PIC_OK;
+}
+
+pic_status pic_step(pic_sim* S, int nsteps) {
+  if (!S || nsteps < 0) {
+    set_error("pic_step: bad arguments");
+    return PIC_EINVAL;
+  }
+  pic_status st = PIC_OK;
+  const bool tiled = S->prec == PIC_FP32_CELLOFF;
+  for (int k = 0; k < nsteps && st == PIC_OK; ++k) st = one_step(S, tiled);
+  if (st == PIC_OK && !tiled) {
+    cudaMemcpyAsync(S->hstat, S->dstat, sizeof(StatusWord), cudaMemcpyDeviceToHost, S->s);
+    if (cudaStreamSynchronize(S->s) != cudaSuccess) return cuda_check("pic_step");
+    S->sticky_flags |= S->hstat->status;
+    if (S->hstat->status & ST_NONFINITE) {
+      set_error("non-finite particle value");
+      st = PIC_ENONFINITE;
+    }
+  }
+  if (S->timing) timing_collect(S);
+  return st;
+}
+
+pic_status pic_fields(pic_sim* S, int which, void* dst, size_t dst_bytes, int dst_on_device) {
+  if (!S || !dst || which < PIC_E1 || which > PIC_RHO) {
+    set_error("pic_fields: bad arguments");
+    return PIC_EINVAL;
+  }
+  const size_t cells = (size_t)S->L.nx * S->L.ny * S->L.nz;
+  if (dst_bytes < 8 * cells) {
+    set_error("pic_fields: destination too small");
+    return PIC_EINVAL;
+  }
+  double* target = dst_on_device ? reinterpret_cast<double*>(dst) : S->dense;
+  if (which == PIC_RHO) {
+    compute_rho(S);
+    pack_interior<double>(S->L, S->rho, target, S->s);
+  } else if (S->prec == PIC_FP64_PLAIN) {
+    const double* src = which <= PIC_B3 ? fld_ptr<double>(S, which) : cur_ptr<double>(S, which - PIC_J1);
+    pack_interior<double>(S->L, src, target, S->s);
+  } else {
+    const float* src = which <= PIC_B3 ? fld_ptr<float>(S, which) : cur_ptr<float>(S, which - PIC_J1);
+    pack_interior<float>(S->L, src, target, S->s);
+  }
+  if (!dst_on_device) cudaMemcpyAsync(dst, S->dense, 8 * cells, cudaMemcpyDeviceToHost, S->s);
+  if (cudaStreamSynchronize(S->s) != cudaSuccess) return cuda_check("pic_fields");
+  return cuda_check("pic_fields");
+}
+
+pic_status pic_set_field(pic_sim* S, int which, const void* src, size_t src_bytes, int src_on_device) {
+  if (!S || !src || which < PIC_E1 || which > PIC_B3) {
+    set_error("pic_set_field: bad arguments");
+    return PIC_EINVAL;
+  }
+  const size_t cells = (size_t)S->L.nx * S->L.ny * S->L.nz;
+  if (src_bytes < 8 * cells) {
+    set_error("pic_set_field: source too small");
+    return PIC_EINVAL;
+  }
+  const double* from = reinterpret_cast<const double*>(src);
+  if (!src_on_device) {
+    cudaMemcpyAsync(S->dense, src, 8 * cells, cudaMemcpyHostToDevice, S->s);
+    from = S->dense;
+  }
+  if (S->prec == PIC_FP64_PLAIN) {
+    double* f = fld_ptr<double>(S, which);
+    unpack_interior<double>(S->L, from, f, S->s);
+    double* all[6];
+    for (int c = 0; c < 6; ++c) all[c] = fld_ptr<double>(S, c);
+    fill_guards<double>(S->L, all, 6, S->s);
+  } else {
+    float* f = fld_ptr<float>(S, which);
+    unpack_interior<float>(S->L, from, f, S->s);
+    float* all[6];
+    for (int c = 0; c < 6; ++c) all[c] = fld_ptr<float>(S, c);
+    fill_guards<float>(S->L, all, 6, S->s);
+  }
+  if (cudaStreamSynchronize(S->s) != cudaSuccess) return cuda_check("pic_set_field");
+  return cuda_check("pic_set_field");
+}
+
+pic_status pic_particles(pic_sim* S, int species, double* x, double* u, long long cap, long long* n_out,
+                         int dst_on_device) {
+  if (!S || species < 0 || species >= (int)S->sp.size() || !n_out) {
+    set_error("pic_particles: bad arguments");
+    return PIC_EINVAL;
+  }
+  SpeciesState& sp = S->sp[(size_t)species];
+  if (S->prec == PIC_FP64_PLAIN) {
+    const long long n = sp.plain.n;
+    *n_out = n;
+    if (n > cap) {
+      set_error("pic_particles: capacity too small");
+      return PIC_EOVERFLOW;
+    }
+    if (n == 0) return PIC_OK;
+    double* tmp = dst_on_device ? nullptr : (double*)S->al.get(24 * (size_t)n);
+    if (!dst_on_device && !tmp) {
+      set_error("out of device memory (copy-out)");
+      return PIC_ENOMEM;
+    }
+    const unsigned nb = (unsigned)((n + 255) / 256);
+    if (x) {
+      double* d = dst_on_device ? x : tmp;
+      k_soa_to_aos3<<<nb, 256, 0, S->s>>>(sp.plain.x[0], sp.plain.x[1], S->ndim == 3 ? sp.plain.x[2] : nullptr, n,
+                                          d);
+      if (!dst_on_device) cudaMemcpyAsync(x, tmp, 24 * (size_t)n, cudaMemcpyDeviceToHost, S->s);
+      cudaStreamSynchronize(S->s);
+    }
+    if (u) {
+      double* d = dst_on_device ? u : tmp;
+      k_soa_to_aos3<<<nb, 256, 0, S->s>>>(sp.plain.u[0], sp.plain.u[1], sp.plain.u[2], n, d);
+      if (!dst_on_device) cudaMemcpyAsync(u, tmp, 24 * (size_t)n, cudaMemcpyDeviceToHost, S->s);
+      cudaStreamSynchronize(S->s);
+    }
+    S->al.put(tmp);
+    return cuda_check("pic_particles");
+  }
+  Flat32 flat{};
+  long long n = 0;
+  bool allocated = false;
+  pic_status st = flatten(S, sp, flat, n, false, 0, allocated);
+  if (st != PIC_OK) {
+    if (allocated) free_flat(S, flat);
+    return st;
+  }
+  *n_out = n;
+  if (n > cap) {
+    free_flat(S, flat);
+    set_error("pic_particles: capacity too small");
+    return PIC_EOVERFLOW;
+  }
+  PushConst C = make_const(S, sp);
+  double* tx = (x && !dst_on_device) ? (double*)S->al.get(24 * (size_t)std::max<long long>(n, 1)) : x;
+  double* tu = (u && !dst_on_device) ? (double*)S->al.get(24 * (size_t)std::max<long long>(n, 1)) : u;
+  if ((x && !tx) || (u && !tu)) {
+    free_flat(S, flat);
+    set_error("out of device memory (copy-out)");
+    return PIC_ENOMEM;
+  }
+  flat_to_global(S->ndim, sp.tg, C, flat, n, tx, tu, S->s);
+  if (x && !dst_on_device) cudaMemcpyAsync(x, tx, 24 * (size_t)n, cudaMemcpyDeviceToHost, S->s);
+  if (u && !dst_on_device) cudaMemcpyAsync(u, tu, 24 * (size_t)n, cudaMemcpyDeviceToHost, S->s);
+  cudaStreamSynchronize(S->s);
+  if (x && !dst_on_device) S->al.put(tx);
+  if (u && !dst_on_device) S->al.put(tu);
+  free_flat(S, flat);
+  return cuda_check("pic_particles");
+}
+
+pic_status pic_particle_ids(pic_sim* S, int species, int* ids, long long cap, long long* n_out, int dst_on_device) {
+  if (!S || species < 0 || species >= (int)S->sp.size() || !n_out || !ids) {
+    set_error("pic_particle_ids: bad arguments");
+    return PIC_EINVAL;
+  }
+  SpeciesState& sp = S->sp[(size_t)species];
+  if (!sp.ids) {
+    set_error("pic_particle_ids: species was created without track_ids");
+    return PIC_EINVAL;
+  }
+  if (S->prec == PIC_FP64_PLAIN) {
+    *n_out = sp.plain.n;
+    if (sp.plain.n > cap) {
+      set_error("pic_particle_ids: capacity too small");
+      return PIC_EOVERFLOW;
+    }
+    cudaMemcpyAsync(ids, sp.plain.id, 4 * (size_t)sp.plain.n,
+                    dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, S->s);
+    cudaStreamSynchronize(S->s);
+    return cuda_check("pic_particle_ids");
+  }
+  Flat32 flat{};
+  long long n = 0;
+  bool allocated = false;
+  pic_status st = flatten(S, sp, flat, n, false, 0, allocated);
+  if (st != PIC_OK) {
+    if (allocated) free_flat(S, flat);
+    return st;
+  }
+  *n_out = n;
+  if (n > cap) {
+    free_flat(S, flat);
+    set_error("pic_particle_ids: capacity too small");
+    return PIC_EOVERFLOW;
+  }
+  cudaMemcpyAsync(ids, flat.id, 4 * (size_t)n, dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                  S->s);
+  cudaStreamSynchronize(S->s);
+  free_flat(S, flat);
+  return cuda_check("pic_particle_ids");
+}
+
+pic_status pic_tile_counts(pic_sim* S, int species, long long* counts, long long cap, long long* ntiles_out) {
+  if (!S || species < 0 || species >= (int)S->sp.size() || !ntiles_out) {
+    set_error("pic_tile_counts: bad arguments");
+    return PIC_EINVAL;
+  }
+  if (S->prec != PIC_FP32_CELLOFF) {
+    set_error("pic_tile_counts: only the FP32 cell-offset form stores particles by tile");
+    return PIC_EINVAL;
+  }
+  SpeciesState& sp = S->sp[(size_t)species];
+  const int nt = sp.tg.ntiles;
+  *ntiles_out = nt;
+  if (!counts || cap < nt) {
+    set_error("pic_tile_counts: capacity too small");
+    return PIC_EOVERFLOW;
+  }
+  Flat32 flat{};
+  long long n = 0;
+  bool allocated = false;
+  pic_status st = flatten(S, sp, flat, n, false, 0, allocated);
+  if (st != PIC_OK) {
+    if (allocated) free_flat(S, flat);
+    return st;
+  }
+  int* dc = (int*)S->al.get(4 * (size_t)nt);
+  if (!dc) {
+    free_flat(S, flat);
+    set_error("out of device memory");
+    return PIC_ENOMEM;
+  }
+  cudaMemsetAsync(dc, 0, 4 * (size_t)nt, S->s);
+  flat_count(flat, n, nt, dc, S->s);
+  std::vector<int> h((size_t)nt);
+  cudaMemcpyAsync(h.data(), dc, 4 * (size_t)nt, cudaMemcpyDeviceToHost, S->s);
+  cudaStreamSynchronize(S->s);
+  for (int t = 0; t < nt; ++t) counts[t] = h[(size_t)t];
+  S->al.put(dc);
+  free_flat(S, flat);
+  return cuda_check("pic_tile_counts");
+}
+
+pic_status pic_diag(pic_sim* S, pic_diag_t* out) {
+  if (!S || !out) {
+    set_error("pic_diag: bad arguments");
+    return PIC_EINVAL;
+  }
+  cudaMemsetAsync(S->dacc, 0, sizeof(Diag64), S->s);
+  compute_rho(S);
+  double dx[3] = {S->g.dx[0], S->g.dx[1], S->ndim == 3 ? S->g.dx[2] : 1.0};
+  long long n = 0;
+  if (S->prec == PIC_FP64_PLAIN) {
+    double* f[6];
+    for (int c = 0; c < 6; ++c) f[c] = fld_ptr<double>(S, c);
+    gauss_residual<double>(S->L, f, S->rho, S->g.rho_bg, dx, S->dacc, S->s);
+    field_energy<double>(S->L, f, S->dacc, S->s);
+  } else {
+    float* f[6];
+    for (int c = 0; c < 6; ++c) f[c] = fld_ptr<float>(S, c);
+    gauss_residual<float>(S->L, f, S->rho, S->g.rho_bg, dx, S->dacc, S->s);
+    field_energy<float>(S->L, f, S->dacc, S->s);
+  }
+  for (auto& sp : S->sp) {
+    PushConst C = make_const(S, sp);
+    if (S->prec == PIC_FP64_PLAIN)
+      plain_kinetic(C, sp.plain, S->dacc, S->s);
+    else
+      tiled_kinetic(C, sp.tg, sp.buf[sp.cur], sp.stay[sp.cur], sp.move[sp.cur], S->dacc, S->s);
+    n += sp.n;
+  }
+  Diag64 h{};
+  cudaMemcpyAsync(&h, S->dacc, sizeof(Diag64), cudaMemcpyDeviceToHost, S->s);
+  cudaMemcpyAsync(S->hstat, S->dstat, sizeof(StatusWord), cudaMemcpyDeviceToHost, S->s);
+  if (cudaStreamSynchronize(S->s) != cudaSuccess) return cuda_check("pic_diag");
+  double dvol = 1.0;
+  for (int d = 0; d < S->ndim; ++d) dvol *= S->g.dx[d];
+  out->step = S->step;
+  out->time = (double)S->step * S->g.dt;
+  out->field_energy = 0.5 * h.field_energy * dvol;
+  out->kinetic_energy = h.kinetic_energy;
+  out->total_charge = h.total_charge;
+  out->gauss_resid_max = h.gauss_max;
+  out->rho_abs_max = h.rho_max;
+  out->rho_particles_abs_max = h.rho_part_max;
+  out->n_particles = n;
+  const int f = S->sticky_flags | S->hstat->status;
+  out->error_flags = ((f & (ST_NONFINITE | ST_BADCELL)) ? 1 : 0) | ((f & ST_SPILL) ? 2 : 0);
+  return cuda_check("pic_diag");
+}
+
+pic_status pic_timing_enable(pic_sim* S, int enable) {
+  if (!S) {
+    set_error("pic_timing_enable: NULL handle");
+    return PIC_EINVAL;
+  }
+  S->timing = enable != 0;
+  return PIC_OK;
+}
+
+pic_status pic_timing_read(pic_sim* S, double* ms, long long* launches, int nslots, int reset) {
+  if (!S || nslots < 0) {
+    set_error("pic_timing_read: bad arguments");
+    return PIC_EINVAL;
+  }
+  timing_collect(S);
+  for (int k = 0; k < nslots && k < kTimingSlots; ++k) {
+    if (ms) ms[k] = S->t_ms[k];
+    if (launches) launches[k] = S->t_n[k];
+  }
+  if (nslots > kLaunchSlot) {
+    if (ms) ms[kLaunchSlot] = 0.0;
+    if (launches) launches[kLaunchSlot] = S->nlaunch;
+  }
+  if (reset) {
+    for (int k = 0; k < kTimingSlots; ++k) {
+      S->t_ms[k] = 0.0;
+      S->t_n[k] = 0;
+    }
+    S->nlaunch = 0;
+  }
+  return PIC_OK;
+}
+
+}  // extern "C"

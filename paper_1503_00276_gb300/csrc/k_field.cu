@@ -1,0 +1,343 @@
+// k_field.cu -- grid kernels: Yee field solve, periodic guards, current fold,
+// binomial smoothing, and the FP64 diagnostics (field energy, Gauss residual).
+//
+// Compiled without multiply-add contraction so that the FP64 instantiation
+// rounds every operation exactly as written; the FP32 instantiation is
+// bandwidth-bound, so the contraction would buy nothing there.
+#include <cstdio>
+
+#include "kernels.h"
+
+namespace picgb {
+
+namespace {
+
+__device__ inline int wrapi(int i, int n) {
+  int r = i % n;
+  return r < 0 ? r + n : r;
+}
+
+inline dim3 interior_grid(const Layout& L) { return dim3((L.nx + 31) / 32, (L.ny + 7) / 8, L.nz); }
+inline dim3 padded_grid(const Layout& L) { return dim3((L.NX + 31) / 32, (L.NY + 7) / 8, L.NZ); }
+const dim3 kBlock(32, 8, 1);
+
+template <typename T>
+struct Ptr3 {
+  T* c[3];
+};
+template <typename T>
+struct Ptr6 {
+  T* c[6];
+};
+
+// ---------------------------------------------------------------- guards
+template <typename T>
+__global__ void k_fill_guards(Layout L, Ptr3<T> P, int ncomp) {
+  int X = blockIdx.x * blockDim.x + threadIdx.x;
+  int Y = blockIdx.y * blockDim.y + threadIdx.y;
+  int Z = blockIdx.z;
+  if (X >= L.NX || Y >= L.NY) return;
+  int i = X - L.gx, j = Y - L.gy, k = Z - L.gz;
+  if (i >= 0 && i < L.nx && j >= 0 && j < L.ny && k >= 0 && k < L.nz) return;
+  long long dst = ((long long)Z * L.NY + Y) * L.NX + X;
+  long long src = L.idx(wrapi(i, L.nx), wrapi(j, L.ny), wrapi(k, L.nz));
+  for (int c = 0; c < ncomp; ++c) P.c[c][dst] = P.c[c][src];
+}
+
+// Periodic boundary for the current: what the deposit put into a guard cell
+// belongs to the interior cell at the wrapped index (the node "communicates
+// with its own opposite boundary").  Several guard cells can map to one
+// interior cell (edges, corners), hence the atomics.
+template <typename T>
+__global__ void k_fold_guards(Layout L, Ptr3<T> P, int ncomp) {
+  int X = blockIdx.x * blockDim.x + threadIdx.x;
+  int Y = blockIdx.y * blockDim.y + threadIdx.y;
+  int Z = blockIdx.z;
+  if (X >= L.NX || Y >= L.NY) return;
+  int i = X - L.gx, j = Y - L.gy, k = Z - L.gz;
+  if (i >= 0 && i < L.nx && j >= 0 && j < L.ny && k >= 0 && k < L.nz) return;
+  long long g = ((long long)Z * L.NY + Y) * L.NX + X;
+  long long dst = L.idx(wrapi(i, L.nx), wrapi(j, L.ny), wrapi(k, L.nz));
+  for (int c = 0; c < ncomp; ++c) {
+    T v = P.c[c][g];
+    if (v != T(0)) atomicAdd(&P.c[c][dst], v);
+    P.c[c][g] = T(0);
+  }
+}
+
+// ---------------------------------------------------------------- smoothing
+// One pass of (w0, w1, w2)/(w0+w1+w2) along `dim`, periodic, out of place.
+template <typename T>
+__global__ void k_smooth(Layout L, const T* __restrict__ f, T* __restrict__ out, int dim, T w0, T w1, T w2, T ws) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  int j = blockIdx.y * blockDim.y + threadIdx.y;
+  int k = blockIdx.z;
+  if (i >= L.nx || j >= L.ny) return;
+  int lo[3] = {i, j, k}, hi[3] = {i, j, k};
+  int n[3] = {L.nx, L.ny, L.nz};
+  lo[dim] = lo[dim] == 0 ? n[dim] - 1 : lo[dim] - 1;
+  hi[dim] = hi[dim] == n[dim] - 1 ? 0 : hi[dim] + 1;
+  long long c = L.idx(i, j, k);
+  out[c] = (w0 * f[L.idx(lo[0], lo[1], lo[2])] + w1 * f[c] + w2 * f[L.idx(hi[0], hi[1], hi[2])]) / ws;
+}
+
+// ---------------------------------------------------------------- Yee solve
+// Faraday half step (eq. 2d-field-solve-b-part1 / -part2; 3D adds the x3
+// derivatives): B -= (dt/2) curl E with forward differences of E.
+template <typename T>
+__global__ void k_yee_b_half(Layout L, Ptr3<T> E, Ptr3<T> B, T h, T dx1, T dx2, T dx3) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  int j = blockIdx.y * blockDim.y + threadIdx.y;
+  int k = blockIdx.z;
+  if (i >= L.nx || j >= L.ny) return;
+  const long long sx = 1, sy = L.NX, sz = (long long)L.NX * L.NY;
+  long long c = L.idx(i, j, k);
+  const T* E1 = E.c[0];
+  const T* E2 = E.c[1];
+  const T* E3 = E.c[2];
+  T dE3d2 = (E3[c + sy] - E3[c]) / dx2;
+  T dE3d1 = (E3[c + sx] - E3[c]) / dx1;
+  T dE2d1 = (E2[c + sx] - E2[c]) / dx1;
+  T dE1d2 = (E1[c + sy] - E1[c]) / dx2;
+  T dE2d3 = T(0), dE1d3 = T(0);
+  if (L.ndim == 3) {
+    dE2d3 = (E2[c + sz] - E2[c]) / dx3;
+    dE1d3 = (E1[c + sz] - E1[c]) / dx3;
+  }
+  B.c[0][c] = B.c[0][c] - h * (dE3d2 - dE2d3);
+  B.c[1][c] = B.c[1][c] - h * (dE1d3 - dE3d1);
+  B.c[2][c] = B.c[2][c] - h * (dE2d1 - dE1d2);
+}
+
+// Ampere step (eq. 2d-field-solve-e; the printed j1 of the E3 line read as j3):
+// E += dt (curl B - J) with backward differences of B.
+template <typename T>
+__global__ void k_yee_e(Layout L, Ptr3<T> E, Ptr3<T> B, Ptr3<T> J, T dt, T dx1, T dx2, T dx3) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  int j = blockIdx.y * blockDim.y + threadIdx.y;
+  int k = blockIdx.z;
+  if (i >= L.nx || j >= L.ny) return;
+  const long long sx = 1, sy = L.NX, sz = (long long)L.NX * L.NY;
+  long long c = L.idx(i, j, k);
+  const T* B1 = B.c[0];
+  const T* B2 = B.c[1];
+  const T* B3 = B.c[2];
+  T dB3d2 = (B3[c] - B3[c - sy]) / dx2;
+  T dB3d1 = (B3[c] - B3[c - sx]) / dx1;
+  T dB2d1 = (B2[c] - B2[c - sx]) / dx1;
+  T dB1d2 = (B1[c] - B1[c - sy]) / dx2;
+  T dB2d3 = T(0), dB1d3 = T(0);
+  if (L.ndim == 3) {
+    dB2d3 = (B2[c] - B2[c - sz]) / dx3;
+    dB1d3 = (B1[c] - B1[c - sz]) / dx3;
+  }
+  E.c[0][c] = E.c[0][c] + dt * (dB3d2 - dB2d3) - dt * J.c[0][c];
+  E.c[1][c] = E.c[1][c] + dt * (dB1d3 - dB3d1) - dt * J.c[1][c];
+  E.c[2][c] = E.c[2][c] + dt * (dB2d1 - dB1d2) - dt * J.c[2][c];
+}
+
+// ---------------------------------------------------------------- diagnostics
+__device__ inline double block_sum(double v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  int lane = (threadIdx.y * blockDim.x + threadIdx.x) & 31;
+  int warp = (threadIdx.y * blockDim.x + threadIdx.x) >> 5;
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  int nw = (blockDim.x * blockDim.y + 31) / 32;
+  double s = 0.0;
+  if (warp == 0) {
+    s = lane < nw ? red[lane] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  }
+  __syncthreads();
+  return s;
+}
+
+__device__ inline double block_max(double v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+  int lane = (threadIdx.y * blockDim.x + threadIdx.x) & 31;
+  int warp = (threadIdx.y * blockDim.x + threadIdx.x) >> 5;
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  int nw = (blockDim.x * blockDim.y + 31) / 32;
+  double s = 0.0;
+  if (warp == 0) {
+    s = lane < nw ? red[lane] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) s = fmax(s, __shfl_down_sync(0xffffffffu, s, o));
+  }
+  __syncthreads();
+  return s;
+}
+
+template <typename T>
+__global__ void k_field_energy(Layout L, Ptr6<T> F, double* acc) {
+  __shared__ double red[32];
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  int j = blockIdx.y * blockDim.y + threadIdx.y;
+  int k = blockIdx.z;
+  double s = 0.0;
+  if (i < L.nx && j < L.ny) {
+    long long c = L.idx(i, j, k);
+    for (int m = 0; m < 6; ++m) {
+      double v = (double)F.c[m][c];
+      s = s + v * v;
+    }
+  }
+  s = block_sum(s, red);
+  if (threadIdx.x == 0 && threadIdx.y == 0) atomicAdd(acc, s);
+}
+
+template <typename T>
+__global__ void k_gauss(Layout L, Ptr3<T> E, const double* __restrict__ rho, double rho_bg, double dx1, double dx2,
+                        double dx3, double* gmax, double* rmax, double* pmax) {
+  __shared__ double red[32];
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  int j = blockIdx.y * blockDim.y + threadIdx.y;
+  int k = blockIdx.z;
+  double g = 0.0, r = 0.0, p = 0.0;
+  if (i < L.nx && j < L.ny) {
+    const long long sx = 1, sy = L.NX, sz = (long long)L.NX * L.NY;
+    long long c = L.idx(i, j, k);
+    double div = ((double)E.c[0][c] - (double)E.c[0][c - sx]) / dx1 + ((double)E.c[1][c] - (double)E.c[1][c - sy]) / dx2;
+    if (L.ndim == 3) div = div + ((double)E.c[2][c] - (double)E.c[2][c - sz]) / dx3;
+    double rt = rho[c] + rho_bg;
+    g = fabs(div - rt);
+    r = fabs(rt);
+    p = fabs(rho[c]);
+  }
+  g = block_max(g, red);
+  r = block_max(r, red);
+  p = block_max(p, red);
+  if (threadIdx.x == 0 && threadIdx.y == 0) {
+    atomic_max_nonneg(gmax, g);
+    atomic_max_nonneg(rmax, r);
+    atomic_max_nonneg(pmax, p);
+  }
+}
+
+template <typename T>
+__global__ void k_pack(Layout L, const T* __restrict__ f, double* __restrict__ dst) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  int j = blockIdx.y * blockDim.y + threadIdx.y;
+  int k = blockIdx.z;
+  if (i >= L.nx || j >= L.ny) return;
+  dst[((long long)k * L.ny + j) * L.nx + i] = (double)f[L.idx(i, j, k)];
+}
+
+template <typename T>
+__global__ void k_unpack(Layout L, const double* __restrict__ src, T* __restrict__ f) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  int j = blockIdx.y * blockDim.y + threadIdx.y;
+  int k = blockIdx.z;
+  if (i >= L.nx || j >= L.ny) return;
+  f[L.idx(i, j, k)] = (T)src[((long long)k * L.ny + j) * L.nx + i];
+}
+
+// E1(i+1/2) - E1(i-1/2) = dx1 * rho(i), zero mean per column.
+template <typename T>
+__global__ void k_gauss_x1(Layout L, const double* __restrict__ rho, double rho_bg, double dx1, T* e1) {
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  int k = blockIdx.y;
+  if (j >= L.ny) return;
+  double run = 0.0, mean = 0.0;
+  for (int i = 0; i < L.nx; ++i) {
+    long long c = L.idx(i, j, k);
+    run = run + dx1 * (rho[c] + rho_bg);
+    mean = mean + run;
+  }
+  mean = mean / (double)L.nx;
+  run = 0.0;
+  for (int i = 0; i < L.nx; ++i) {
+    long long c = L.idx(i, j, k);
+    run = run + dx1 * (rho[c] + rho_bg);
+    e1[c] = (T)(run - mean);
+  }
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ launchers
+template <typename T>
+void fill_guards(const Layout& L, T* const* comps, int ncomp, cudaStream_t s) {
+  for (int c0 = 0; c0 < ncomp; c0 += 3) {
+    Ptr3<T> P{};
+    int m = ncomp - c0 < 3 ? ncomp - c0 : 3;
+    for (int c = 0; c < m; ++c) P.c[c] = comps[c0 + c];
+    k_fill_guards<T><<<padded_grid(L), kBlock, 0, s>>>(L, P, m);
+  }
+}
+
+template <typename T>
+void fold_guards(const Layout& L, T* const* comps, int ncomp, cudaStream_t s) {
+  for (int c0 = 0; c0 < ncomp; c0 += 3) {
+    Ptr3<T> P{};
+    int m = ncomp - c0 < 3 ? ncomp - c0 : 3;
+    for (int c = 0; c < m; ++c) P.c[c] = comps[c0 + c];
+    k_fold_guards<T><<<padded_grid(L), kBlock, 0, s>>>(L, P, m);
+  }
+}
+
+template <typename T>
+void smooth_pass(const Layout& L, T* comp, T* tmp, int dim, double w0, double w1, double w2, cudaStream_t s) {
+  k_smooth<T><<<interior_grid(L), kBlock, 0, s>>>(L, comp, tmp, dim, (T)w0, (T)w1, (T)w2, (T)(w0 + w1 + w2));
+  cudaMemcpyAsync(comp, tmp, sizeof(T) * (size_t)L.plane, cudaMemcpyDeviceToDevice, s);
+}
+
+template <typename T>
+void yee_b_half(const Layout& L, T* const* e, T* const* b, double dt, const double dx[3], cudaStream_t s) {
+  Ptr3<T> E{{e[0], e[1], e[2]}}, B{{b[0], b[1], b[2]}};
+  k_yee_b_half<T><<<interior_grid(L), kBlock, 0, s>>>(L, E, B, (T)(dt / 2.0), (T)dx[0], (T)dx[1], (T)dx[2]);
+}
+
+template <typename T>
+void yee_e(const Layout& L, T* const* e, T* const* b, T* const* j, double dt, const double dx[3], cudaStream_t s) {
+  Ptr3<T> E{{e[0], e[1], e[2]}}, B{{b[0], b[1], b[2]}}, J{{j[0], j[1], j[2]}};
+  k_yee_e<T><<<interior_grid(L), kBlock, 0, s>>>(L, E, B, J, (T)dt, (T)dx[0], (T)dx[1], (T)dx[2]);
+}
+
+template <typename T>
+void field_energy(const Layout& L, T* const* f, Diag64* acc, cudaStream_t s) {
+  Ptr6<T> F{{f[0], f[1], f[2], f[3], f[4], f[5]}};
+  k_field_energy<T><<<interior_grid(L), kBlock, 0, s>>>(L, F, &acc->field_energy);
+}
+
+template <typename T>
+void gauss_residual(const Layout& L, T* const* e, const double* rho, double rho_bg, const double dx[3], Diag64* acc,
+                    cudaStream_t s) {
+  Ptr3<T> E{{e[0], e[1], e[2]}};
+  k_gauss<T><<<interior_grid(L), kBlock, 0, s>>>(L, E, rho, rho_bg, dx[0], dx[1], dx[2], &acc->gauss_max,
+                                                 &acc->rho_max, &acc->rho_part_max);
+}
+
+template <typename T>
+void pack_interior(const Layout& L, const T* comp, double* dst, cudaStream_t s) {
+  k_pack<T><<<interior_grid(L), kBlock, 0, s>>>(L, comp, dst);
+}
+
+template <typename T>
+void unpack_interior(const Layout& L, const double* src, T* comp, cudaStream_t s) {
+  k_unpack<T><<<interior_grid(L), kBlock, 0, s>>>(L, src, comp);
+}
+
+template <typename T>
+void init_e_gauss_x1(const Layout& L, const double* rho, double rho_bg, double dx1, T* e1, cudaStream_t s) {
+  k_gauss_x1<T><<<dim3((L.ny + 127) / 128, L.nz), 128, 0, s>>>(L, rho, rho_bg, dx1, e1);
+}
+
+#define PICGB_INST(T)                                                                                         \
+  template void fill_guards<T>(const Layout&, T* const*, int, cudaStream_t);                                  \
+  template void fold_guards<T>(const Layout&, T* const*, int, cudaStream_t);                                  \
+  template void smooth_pass<T>(const Layout&, T*, T*, int, double, double, double, cudaStream_t);             \
+  template void yee_b_half<T>(const Layout&, T* const*, T* const*, double, const double[3], cudaStream_t);     \
+  template void yee_e<T>(const Layout&, T* const*, T* const*, T* const*, double, const double[3], cudaStream_t); \
+  template void field_energy<T>(const Layout&, T* const*, Diag64*, cudaStream_t);                             \
+  template void gauss_residual<T>(const Layout&, T* const*, const double*, double, const double[3], Diag64*,   \
+                                  cudaStream_t);                                                              \
+  template void pack_interior<T>(const Layout&, const T*, double*, cudaStream_t);                             \
+  template void unpack_interior<T>(const Layout&, const double*, T*, cudaStream_t);                           \
+  template void init_e_gauss_x1<T>(const Layout&, const double*, double, double, T*, cudaStream_t);
+
+PICGB_INST(float)
+PICGB_INST(double)
+
+}  // namespace picgb

@@ -1,0 +1,117 @@
+// kernels.h -- internal launchers of libpicgb (host side, C++; not part of the ABI).
+#pragma once
+
+#include "common.cuh"
+
+namespace picgb {
+
+// ----------------------------------------------------------------- grid fields
+struct Diag64 {           // device accumulators of one diagnostic pass (FP64)
+  double field_energy;
+  double kinetic_energy;
+  double total_charge;
+  double gauss_max;
+  double rho_max;
+  double rho_part_max;
+};
+
+template <typename T> void fill_guards(const Layout& L, T* const* comps, int ncomp, cudaStream_t s);
+template <typename T> void fold_guards(const Layout& L, T* const* comps, int ncomp, cudaStream_t s);
+template <typename T>
+void smooth_pass(const Layout& L, T* comp, T* tmp, int dim, double w0, double w1, double w2, cudaStream_t s);
+template <typename T>
+void yee_b_half(const Layout& L, T* const* e, T* const* b, double dt, const double dx[3], cudaStream_t s);
+template <typename T>
+void yee_e(const Layout& L, T* const* e, T* const* b, T* const* j, double dt, const double dx[3], cudaStream_t s);
+template <typename T> void field_energy(const Layout& L, T* const* f, Diag64* acc, cudaStream_t s);
+template <typename T>
+void gauss_residual(const Layout& L, T* const* e, const double* rho, double rho_bg, const double dx[3], Diag64* acc,
+                    cudaStream_t s);
+template <typename T> void pack_interior(const Layout& L, const T* comp, double* dst, cudaStream_t s);
+template <typename T> void unpack_interior(const Layout& L, const double* src, T* comp, cudaStream_t s);
+// E1 from the discrete Gauss law along x1, column by column (rho padded FP64).
+template <typename T> void init_e_gauss_x1(const Layout& L, const double* rho, double rho_bg, double dx1, T* e1,
+                                           cudaStream_t s);
+
+// ----------------------------------------------------------------- particles
+struct PushConst {        // per-species constants of one step
+  double xmin[3], dx[3], inv_dx[3], dt;
+  double e0[3], b0[3];
+  double rqm, q, dvol;
+  double L[3];            // box length per direction
+};
+
+// FP64 plain form
+struct Plain {
+  double* x[3];
+  double* u[3];
+  int* id;
+  long long n;
+};
+void plain_push(int ndim, const Layout& L, const PushConst& C, Plain p, double* const* f, double* const* j,
+                int* status, cudaStream_t s);
+void plain_rho(int ndim, const Layout& L, const PushConst& C, Plain p, double* rho, cudaStream_t s);
+void plain_kinetic(const PushConst& C, Plain p, Diag64* acc, cudaStream_t s);
+
+// FP32 cell-offset form, particles stored by tile
+struct Part32 {           // one particle buffer (structure of arrays)
+  uint32_t* cell;         // packed local cell lx | ly<<8 | lz<<16 | dir<<24
+  float* o[3];            // in-cell offsets in [0,1)
+  float* u[3];
+  int* id;                // may be null
+};
+struct Flat32 {           // unsorted staging form (load, rebuild, copy-out)
+  int* tile;
+  uint32_t* cell;         // packed local cell within `tile`, dir = 13
+  float* o[3];
+  float* u[3];
+  int* id;
+};
+struct Tiles {
+  int ndim;
+  int T[3];               // tile size in cells
+  int nt[3];              // tiles per direction
+  int ntiles;
+  long long* base;        // [ntiles] first slot of each tile region
+  int* cap;               // [ntiles] slots of each tile region
+};
+constexpr int DIR_STAY = 13;
+
+void tiled_push(const Layout& L, const PushConst& C, const Tiles& tg, const Part32& in, const int* in_stay,
+                const int* in_move, const Part32& out, int* out_stay, int* out_move, Flat32 spill,
+                int* spill_count, long long spill_cap, const CUtensorMap* fmap, const CUtensorMap* jmap,
+                int* status, cudaStream_t s);
+int tiled_push_smem_bytes(int ndim, const int T[3]);
+void tiled_flatten(const Tiles& tg, const Part32& in, const int* stay, const int* move, const long long* out_off,
+                   Flat32 out, cudaStream_t s);
+void flat_count(const Flat32& f, long long n, int ntiles, int* counts, cudaStream_t s);
+void flat_scatter(const Flat32& f, long long n, const Tiles& tg, int* cursor, Part32 out, cudaStream_t s);
+void flat_to_global(int ndim, const Tiles& tg, const PushConst& C, const Flat32& f, long long n, double* x, double* u,
+                    cudaStream_t s);
+void global_to_flat(int ndim, const Layout& L, const Tiles& tg, const PushConst& C, double* const x[3],
+                    double* const u[3], const int* id, long long n, Flat32 out, int* status, cudaStream_t s);
+void tiled_rho(const Layout& L, const PushConst& C, const Tiles& tg, const Part32& in, const int* stay,
+               const int* move, double* rho, cudaStream_t s);
+void tiled_kinetic(const PushConst& C, const Tiles& tg, const Part32& in, const int* stay, const int* move,
+                   Diag64* acc, cudaStream_t s);
+
+// ----------------------------------------------------------------- loading
+// Lattice loader (nl_species num_par_x, vth, vfl) on the device, FP64 output.
+struct LatticeSpec {
+  int ndim;
+  int nx[3];
+  double xmin[3], dx[3];
+  int ppc[3];
+  double uth[3], ufl[3];
+  unsigned long long seed;
+};
+void lattice_load(const LatticeSpec& S, long long first, long long count, double* const x[3], double* const u[3],
+                  int* id, cudaStream_t s);
+
+// ----------------------------------------------------------------- sorting
+// Exclusive prefix sum of n int32 counts into int64 starts; `scratch` holds at
+// least scan_scratch_bytes(n) bytes.
+size_t scan_scratch_bytes(long long n);
+void exclusive_scan_i32(const int* in, long long* out, long long n, void* scratch, cudaStream_t s);
+
+}  // namespace picgb

@@ -1,0 +1,105 @@
+"""C ABI checks that need no GPU: the library builds and loads, exports every
+function include/pic.h declares, and validates arguments on the host
+(Courant condition, dimensions, boundary types) before touching a device."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+import workload
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def capi():
+    from paper_1503_00276_gb300 import _capi, build
+    build.build()
+    _capi.load()
+    return _capi
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "pic.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(pic_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_header_declarations_are_exported(capi):
+    names = _declared()
+    assert "pic_init" in names and "pic_step" in names and len(names) >= 13
+    lib = C.CDLL(capi.library_path())
+    for n in names:
+        assert hasattr(lib, n), n
+    assert sorted(capi.PROTOTYPES) == names
+
+
+def test_struct_layouts_match_header(capi, tmp_path):
+    """sizeof/offsetof of the ABI structs as the C compiler sees include/pic.h."""
+    import subprocess
+    prog = tmp_path / "layout.c"
+    fields = {"pic_grid": capi.PicGrid, "pic_species": capi.PicSpecies, "pic_diag_t": capi.PicDiag,
+              "pic_allocator": capi.PicAllocator}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "pic.h"', "int main(void) {"]
+    for cname, cls in fields.items():
+        lines.append(f'  printf("{cname} %zu\\n", sizeof({cname}));')
+        for f, _ in cls._fields_:
+            lines.append(f'  printf("{cname}.{f} %zu\\n", offsetof({cname}, {f}));')
+    lines.append("  return 0; }")
+    prog.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)], check=True)
+    out = dict(l.split() for l in subprocess.run([str(exe)], capture_output=True, text=True, check=True)
+               .stdout.splitlines())
+    for cname, cls in fields.items():
+        assert int(out[cname]) == C.sizeof(cls), cname
+        for f, _ in cls._fields_:
+            assert int(out[f"{cname}.{f}"]) == getattr(cls, f).offset, (cname, f)
+
+
+def _grid(dt_frac=0.99, ndim=2, bc=0):
+    dx = (0.1, 0.1, 0.1)
+    g = workload.Grid(ndim=ndim, nx=(16, 16, 16), dx=dx, dt=workload.courant_dt(dx, ndim, dt_frac))
+    from paper_1503_00276_gb300 import _grid_struct
+    s = _grid_struct(g, 0)
+    s.bc[0][0] = bc
+    return s
+
+
+def _init(capi, g):
+    h = C.c_void_p()
+    sp = capi.PicSpecies()
+    sp.rqm = -1.0
+    sp.ppc[0] = sp.ppc[1] = sp.ppc[2] = 1
+    sp.density = 1.0
+    code = capi.load().pic_init(C.byref(g), C.byref(sp), 1, None, None, C.byref(h))
+    return code, h
+
+
+def test_courant_violation_is_rejected(capi):
+    code, h = _init(capi, _grid(dt_frac=1.0001))
+    assert code == -4 and not h.value
+    assert b"Courant" in capi.load().pic_last_error()
+
+
+def test_bad_arguments_are_rejected(capi):
+    g = _grid()
+    g.ndim = 4
+    assert _init(capi, g)[0] == -1
+    assert _init(capi, _grid(bc=5))[0] == -8
+    lib = capi.load()
+    assert lib.pic_destroy(None) == 0
+    h = C.c_void_p()
+    assert lib.pic_init(None, None, 0, None, None, C.byref(h)) == -1
+    nx = (C.c_int * 3)(16, 16, 1)
+    bad_tile = (C.c_int * 3)(5, 4, 1)
+    assert lib.pic_bin_tiles(nx, bad_tile, 0, None, C.c_void_p(8), C.c_void_p(8), None, None, None) == -1
+
+
+def test_valid_grid_without_device_reports_cuda_error(capi):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    code, h = _init(capi, _grid())
+    assert code == -3 and not h.value

@@ -6,6 +6,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -105,13 +106,16 @@ struct SpeciesState {
   Plain plain{};
   // FP32 tiled
   Tiles tg{};
-  Part32 buf[2]{};
-  int* stay[2]{};
-  int* move[2]{};
+  TileSide side[2]{};
   int cur = 0;
   long long slots = 0;
   Flat32 spill{};
   long long spill_cap = 0;
+  void* scratch = nullptr;  // per-CTA staging of the tile kernel (L2 resident)
+  long long scap = 0;       // particles per CTA in `scratch`
+  size_t scratch_bytes = 0;
+  int grid = 0;             // persistent CTAs of the tile kernel
+  int* work = nullptr;      // its dynamic tile counter
 };
 
 constexpr int kTimingSlots = 5;
@@ -386,10 +390,10 @@ pic_status bin_flat(pic_sim* S, SpeciesState& sp, Flat32& flat, long long n) {
     return PIC_EOVERFLOW;
   }
   if (slots > sp.slots) {
-    for (int b = 0; b < 2; ++b) free_part(S, sp.buf[b]);
+    for (int b = 0; b < 2; ++b) free_part(S, sp.side[b].p);
     bool ok0, ok1;
-    sp.buf[0] = alloc_part(S, slots, sp.ids, ok0);
-    sp.buf[1] = alloc_part(S, slots, sp.ids, ok1);
+    sp.side[0].p = alloc_part(S, slots, sp.ids, ok0);
+    sp.side[1].p = alloc_part(S, slots, sp.ids, ok1);
     if (!ok0 || !ok1) {
       S->al.put(counts);
       set_error("out of device memory (particle store of " + std::to_string(slots) + " slots)");
@@ -397,6 +401,23 @@ pic_status bin_flat(pic_sim* S, SpeciesState& sp, Flat32& flat, long long n) {
     }
     sp.slots = slots;
   }
+  // staging of the tile kernel: every persistent CTA holds one tile's particles
+  long long max_cap = 4;
+  for (int t = 0; t < nt; ++t) max_cap = std::max<long long>(max_cap, hcap[t]);
+  const long long scap = (max_cap + std::max<long long>(64, max_cap / 4) + 3) / 4 * 4;
+  sp.grid = tiled_push_grid(S->ndim, S->T, nt);
+  const size_t sbytes = tiled_scratch_bytes(sp.grid, scap);
+  if (sbytes > sp.scratch_bytes) {
+    S->al.put(sp.scratch);
+    sp.scratch = S->al.get(sbytes);
+    if (!sp.scratch) {
+      S->al.put(counts);
+      set_error("out of device memory (tile kernel staging)");
+      return PIC_ENOMEM;
+    }
+    sp.scratch_bytes = sbytes;
+  }
+  sp.scap = scap;
   cudaMemcpyAsync(sp.tg.cap, hcap.data(), 4 * (size_t)nt, cudaMemcpyHostToDevice, S->s);
   cudaMemcpyAsync(sp.tg.base, hbase.data(), 8 * (size_t)nt, cudaMemcpyHostToDevice, S->s);
   int* cursor = (int*)S->al.get(4 * (size_t)nt);
@@ -406,9 +427,11 @@ pic_status bin_flat(pic_sim* S, SpeciesState& sp, Flat32& flat, long long n) {
     return PIC_ENOMEM;
   }
   cudaMemsetAsync(cursor, 0, 4 * (size_t)nt, S->s);
-  flat_scatter(flat, n, sp.tg, cursor, sp.buf[sp.cur], S->s);
-  cudaMemcpyAsync(sp.stay[sp.cur], counts, 4 * (size_t)nt, cudaMemcpyDeviceToDevice, S->s);
-  cudaMemsetAsync(sp.move[sp.cur], 0, 4 * (size_t)nt, S->s);
+  flat_scatter(flat, n, sp.tg, cursor, sp.side[sp.cur].p, S->s);
+  cudaMemcpyAsync(sp.side[sp.cur].stay, counts, 4 * (size_t)nt, cudaMemcpyDeviceToDevice, S->s);
+  cudaMemsetAsync(sp.side[sp.cur].move, 0, 4 * (size_t)nt, S->s);
+  cudaMemsetAsync(sp.side[sp.cur].mstart, 0, 4 * (size_t)nt * 27, S->s);
+  cudaMemsetAsync(sp.side[sp.cur].mcount, 0, 4 * (size_t)nt * 27, S->s);
   cudaError_t e = cudaStreamSynchronize(S->s);
   S->al.put(cursor);
   S->al.put(counts);
@@ -431,7 +454,7 @@ pic_status flatten(pic_sim* S, SpeciesState& sp, Flat32& flat, long long& n, boo
     set_error("out of device memory (flatten)");
     return PIC_ENOMEM;
   }
-  k_add_i32<<<(nt + 255) / 256, 256, 0, S->s>>>(sp.stay[sp.cur], sp.move[sp.cur], tot, nt);
+  k_add_i32<<<(nt + 255) / 256, 256, 0, S->s>>>(sp.side[sp.cur].stay, sp.side[sp.cur].move, tot, nt);
   exclusive_scan_i32(tot, off, nt, scr, S->s);
   long long last_off = 0;
   int last_cnt = 0;
@@ -452,7 +475,7 @@ pic_status flatten(pic_sim* S, SpeciesState& sp, Flat32& flat, long long& n, boo
     set_error("out of device memory (flat copy of " + std::to_string(n) + " particles)");
     return PIC_ENOMEM;
   }
-  tiled_flatten(sp.tg, sp.buf[sp.cur], sp.stay[sp.cur], sp.move[sp.cur], off, flat, S->s);
+  tiled_flatten(sp.tg, sp.side[sp.cur], off, flat, S->s);
   if (include_spill && spill_n > 0) {
     auto cp = [&](void* dst, const void* src) {
       cudaMemcpyAsync((char*)dst + 4 * (size_t)nstore, src, 4 * (size_t)spill_n, cudaMemcpyDeviceToDevice, S->s);
@@ -659,16 +682,26 @@ pic_status setup_tiles(pic_sim* S, SpeciesState& sp) {
   }
   tg.base = (long long*)S->al.get(8 * (size_t)tg.ntiles);
   tg.cap = (int*)S->al.get(4 * (size_t)tg.ntiles);
+  bool ok = tg.base && tg.cap;
   for (int b = 0; b < 2; ++b) {
-    sp.stay[b] = (int*)S->al.get(4 * (size_t)tg.ntiles);
-    sp.move[b] = (int*)S->al.get(4 * (size_t)tg.ntiles);
+    TileSide& sd = sp.side[b];
+    sd.stay = (int*)S->al.get(4 * (size_t)tg.ntiles);
+    sd.move = (int*)S->al.get(4 * (size_t)tg.ntiles);
+    sd.mstart = (int*)S->al.get(4 * 27 * (size_t)tg.ntiles);
+    sd.mcount = (int*)S->al.get(4 * 27 * (size_t)tg.ntiles);
+    ok = ok && sd.stay && sd.move && sd.mstart && sd.mcount;
   }
-  if (!tg.base || !tg.cap || !sp.stay[0] || !sp.stay[1] || !sp.move[0] || !sp.move[1]) {
+  sp.work = (int*)S->al.get(sizeof(int));
+  if (!ok || !sp.work) {
     set_error("out of device memory (tile tables)");
     return PIC_ENOMEM;
   }
-  cudaMemsetAsync(sp.stay[1], 0, 4 * (size_t)tg.ntiles, S->s);
-  cudaMemsetAsync(sp.move[1], 0, 4 * (size_t)tg.ntiles, S->s);
+  for (int b = 0; b < 2; ++b) {
+    cudaMemsetAsync(sp.side[b].stay, 0, 4 * (size_t)tg.ntiles, S->s);
+    cudaMemsetAsync(sp.side[b].move, 0, 4 * (size_t)tg.ntiles, S->s);
+    cudaMemsetAsync(sp.side[b].mstart, 0, 4 * 27 * (size_t)tg.ntiles, S->s);
+    cudaMemsetAsync(sp.side[b].mcount, 0, 4 * 27 * (size_t)tg.ntiles, S->s);
+  }
   return PIC_OK;
 }
 
@@ -691,7 +724,7 @@ void compute_rho(pic_sim* S) {
     if (S->prec == PIC_FP64_PLAIN)
       plain_rho(S->ndim, S->L, C, sp.plain, S->rho, S->s);
     else
-      tiled_rho(S->L, C, sp.tg, sp.buf[sp.cur], sp.stay[sp.cur], sp.move[sp.cur], S->rho, S->s);
+      tiled_rho(S->L, C, sp.tg, sp.side[sp.cur], S->rho, S->s);
   }
   double* r[1] = {S->rho};
   fold_guards<double>(S->L, r, 1, S->s);
@@ -742,8 +775,8 @@ pic_status one_step(pic_sim* S, bool check_now) {
         plain_push(S->ndim, S->L, C, s.plain, f, j, &S->dstat->status, S->s);
       } else {
         const int in = s.cur, out = 1 - s.cur;
-        tiled_push(S->L, C, s.tg, s.buf[in], s.stay[in], s.move[in], s.buf[out], s.stay[out], s.move[out],
-                   s.spill, &S->dstat->spill_count, s.spill_cap, &S->fmap, &S->jmap, &S->dstat->status, S->s);
+        tiled_push(S->L, C, s.tg, s.side[in], s.side[out], s.spill, &S->dstat->spill_count, s.spill_cap, s.scratch,
+                   s.scap, s.grid, s.work, &S->fmap, &S->jmap, &S->dstat->status, S->s);
         s.cur = out;
       }
       S->nlaunch += s.n > 0 || S->prec == PIC_FP32_CELLOFF ? 1 : 0;
@@ -886,8 +919,9 @@ pic_status pic_init(const pic_grid* grid, const pic_species* species, int nspeci
         S->T[2] = 1;
       }
     }
+    if (const char* e = getenv("PICGB_TILE_CTAS")) tiled_push_set_minb(atoi(e));
     if (tiled_push_smem_bytes(S->ndim, S->T) < 0) {
-      set_error("unsupported tile shape (3D: 8x8x8, 16x8x4, 4x4x4; 2D: 32x16, 16x16, 8x8)");
+      set_error("unsupported tile shape (3D: 8x8x8, 16x8x4; 2D: 32x16, 16x16, 8x8)");
       delete S;
       return PIC_EUNSUPPORTED;
     }
@@ -1228,7 +1262,7 @@ pic_status pic_diag(pic_sim* S, pic_diag_t* out) {
     if (S->prec == PIC_FP64_PLAIN)
       plain_kinetic(C, sp.plain, S->dacc, S->s);
     else
-      tiled_kinetic(C, sp.tg, sp.buf[sp.cur], sp.stay[sp.cur], sp.move[sp.cur], S->dacc, S->s);
+      tiled_kinetic(C, sp.tg, sp.side[sp.cur], S->dacc, S->s);
     n += sp.n;
   }
   Diag64 h{};

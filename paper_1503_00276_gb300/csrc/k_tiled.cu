@@ -1,21 +1,25 @@
-// k_tiled.cu -- FP32 cell-offset form of the particle step, one CTA per tile.
+// k_tiled.cu -- FP32 cell-offset form of the particle step on tiles of cells.
 //
-// Particles live in per-tile regions of a slot array (structure of arrays):
-// a tile's particles that stayed in it during the last step sit at the front
-// of its region, those that left it sit at the back, each tagged with the
-// direction it left in and its cell relative to the tile it entered.  One
-// launch of k_tile_push advances every particle of a tile -- its own stayers
-// plus the movers its 26 (3D) or 8 (2D) neighbours tagged for it -- and writes
-// them, binned the same way, into the other (ping-pong) slot array.  So the
-// per-tile sort costs no separate pass.
+// Store: per tile a region of slots (structure of arrays).  At the start of a
+// step a region holds the tile's stayers sorted by cell, followed by the
+// particles that left it in the last step, grouped by the direction they left
+// in (their cell is already expressed relative to the tile they entered).
 //
-// Per tile:
-//   * one TMA copy stages the E/B stencil of the tile plus halo in shared memory;
+// k_tile_push (persistent CTAs, one tile at a time) advances, for its tile, the
+// stayers plus the neighbours' groups that point at it:
+//   * one TMA copy stages the E/B stencil of the tile + halo in shared memory;
 //   * gather (eq. 2d-field-weighting-e3, 3D extension), Boris push
 //     (eq. momentum-update), position update (eq. 2d-position-update) and the
 //     TRISTAN / Villasenor-Buneman deposit run in FP32 on int cell + FP32 offset;
-//   * the deposit goes to a shared-memory current tile with shared atomics;
-//   * one TMA reduce-add flushes that current tile (with halo) into HBM.
+//   * pass 1 writes the advanced particles to a per-CTA scratch area (L2
+//     resident) and histograms their new (cell | direction) keys; pass 2
+//     scatters them into the tile's region of the other store side, stayers
+//     sorted by cell -- so the store is re-sorted every step at no DRAM cost;
+//   * the current goes to a shared-memory tile: each thread adds the first
+//     in-cell piece of consecutive same-cell particles in registers and flushes
+//     once per cell; pieces after a face crossing (a few % of particles) are
+//     queued in shared memory and deposited by full warps;
+//   * one TMA reduce-add flushes the shared current tile (with halo) into HBM.
 #include "kernels.h"
 
 namespace picgb {
@@ -23,46 +27,51 @@ namespace picgb {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kPPT = 4;                      // particles per thread per chunk
+constexpr int kPPT = 4;                      // consecutive particles per thread per chunk
 constexpr int kChunk = kThreads * kPPT;      // 1024
-constexpr int kIncMax = kChunk;              // incoming-mover list capacity
+constexpr int kQCap = 320;                   // crossing queue entries
 constexpr long long kWaitLimit = 1ll << 26;  // bounded mbarrier poll
+constexpr int kDirs = 27;
 
 struct TileArgs {
   int nt[3];
   int ntiles;
   const long long* base;
   const int* cap;
-  Part32 in;
-  const int* in_stay;
-  const int* in_move;
-  Part32 out;
-  int* out_stay;
-  int* out_move;
+  TileSide in;
+  TileSide out;
   Flat32 spill;
   int* spill_count;
   long long spill_cap;
-  float qmdt2;     // (q/m) dt/2 = dt / (2 rqm)
-  float dt_dx[3];  // dt / dx_d
-  float cf[3];     // q dx_d / (dt dV): current density per cell-unit of displacement
-  float j3f;       // q / dV (2D3V out-of-plane current per unit v3 and time share)
+  float* scratch;       // [grid][8][scap]
+  long long scap;
+  int* work;            // dynamic tile counter
+  float qmdt2;          // (q/m) dt/2 = dt / (2 rqm)
+  float dt_dx[3];       // dt / dx_d
+  float cf[3];          // q dx_d / (dt dV): current density per cell-unit of displacement
+  float j3f;            // q / dV (2D3V out-of-plane current per unit v3 and time share)
   float e0[3], b0[3];
   int* status;
 };
 
 template <int NDIM, int TX, int TY, int TZ>
 struct Geo {
+  static constexpr int NC = TX * TY * TZ;
+  static constexpr int NK = NC + kDirs;
   static constexpr int FX = TX + 8, FY = TY + 2, FZ = NDIM == 3 ? TZ + 2 : 1;
   static constexpr int JX = TX + 8, JY = TY + 3, JZ = NDIM == 3 ? TZ + 3 : 1;
   static constexpr int FPL = FX * FY * FZ;
   static constexpr int JPL = JX * JY * JZ;
   static constexpr int FBYTES = 6 * FPL * 4;
   static constexpr int JBYTES = 3 * JPL * 4;
+  static constexpr int QW = NDIM == 3 ? 7 : 6;  // words per queue entry
   static constexpr int FOFF = 0;
-  static constexpr int JOFF = ((FBYTES + 1023) / 1024) * 1024;
-  static constexpr int INCOFF = JOFF + ((JBYTES + 127) / 128) * 128;
-  static constexpr int MISCOFF = INCOFF + kIncMax * 8;
-  static constexpr int SMEM = MISCOFF + 1024;
+  static constexpr int JOFF = ((FBYTES + 127) / 128) * 128;
+  static constexpr int HOFF = JOFF + ((JBYTES + 127) / 128) * 128;   // hist[NK]
+  static constexpr int COFF = HOFF + ((NK * 4 + 15) / 16) * 16;      // cursor[NK]
+  static constexpr int QOFF = COFF + ((NK * 4 + 15) / 16) * 16;      // queue
+  static constexpr int MOFF = QOFF + ((kQCap * QW * 4 + 15) / 16) * 16;
+  static constexpr int SMEM = MOFF + 512;
 };
 
 struct P {
@@ -79,92 +88,181 @@ template <int NDIM, int FX, int FY>
 __device__ inline float interp(const float* F, int ix, int iy, int iz, float wx, float wy, float wz) {
   if (NDIM == 2) {
     const float* r = F + (iy + 1) * FX + (ix + 4);
-    float lo = lerp(r[0], r[1], wx);
-    float hi = lerp(r[FX], r[FX + 1], wx);
-    return lerp(lo, hi, wy);
+    return lerp(lerp(r[0], r[1], wx), lerp(r[FX], r[FX + 1], wx), wy);
   } else {
     const float* r = F + ((iz + 1) * FY + (iy + 1)) * FX + (ix + 4);
     constexpr int PL = FX * FY;
-    float a0 = lerp(r[0], r[1], wx);
-    float a1 = lerp(r[FX], r[FX + 1], wx);
-    float b0 = lerp(r[PL], r[PL + 1], wx);
-    float b1 = lerp(r[PL + FX], r[PL + FX + 1], wx);
+    const float a0 = lerp(r[0], r[1], wx);
+    const float a1 = lerp(r[FX], r[FX + 1], wx);
+    const float b0 = lerp(r[PL], r[PL + 1], wx);
+    const float b1 = lerp(r[PL + FX], r[PL + FX + 1], wx);
     return lerp(lerp(a0, a1, wy), lerp(b0, b1, wy), wz);
   }
 }
 
-// Villasenor-Buneman current of one in-cell segment into the shared tile, 2D3V.
-// (cx,cy): the segment's cell relative to the tile; (ax,ay)->(bx,by): its ends
-// in cell units relative to that cell; v3frac: v3 times its share of dt.
-template <int JX, int JY>
-__device__ inline void deposit_seg2(float* J, const TileArgs& A, int cx, int cy, float ax, float ay, float bx,
-                                    float by, float v3frac) {
-  constexpr int JP = JX * JY;
-  float* J1 = J;
-  float* J2 = J + JP;
-  float* J3 = J + 2 * JP;
+// Villasenor-Buneman weights of one straight in-cell piece a -> b (cell units
+// relative to its cell): the flux of the move along d through face cell_d+1/2
+// is shared among the transverse nodes with the path-averaged linear weights,
+// i.e. the midpoint weights plus the covariance term D_t1 D_t2 / 12.  Order of
+// the 12 (3D) / 8 (2D) values: J1 (n,n+y,n+z,n+y+z) J2 (n,n+z,n+x,n+z+x)
+// J3 (n,n+x,n+y,n+x+y) in 3D; J1 (n,n+y) J2 (n,n+x) J3 (n,n+x,n+y,n+x+y) in 2D.
+template <int NDIM>
+__device__ inline void seg_weights(const TileArgs& A, float ax, float ay, float az, float bx, float by, float bz,
+                                   float v3frac, float w[12]) {
   const float dx = bx - ax, dy = by - ay;
   const float mx = 0.5f * (ax + bx), my = 0.5f * (ay + by);
-  const int c = (cy + 1) * JX + (cx + 4);
-  const float a1 = A.cf[0] * dx, a2 = A.cf[1] * dy;
-  atomicAdd(&J1[c], a1 * (1.f - my));
-  atomicAdd(&J1[c + JX], a1 * my);
-  atomicAdd(&J2[c], a2 * (1.f - mx));
-  atomicAdd(&J2[c + 1], a2 * mx);
-  const float a3 = A.j3f * v3frac;
-  const float cv = dx * dy * (1.f / 12.f);
-  atomicAdd(&J3[c], a3 * ((1.f - mx) * (1.f - my) + cv));
-  atomicAdd(&J3[c + 1], a3 * (mx * (1.f - my) - cv));
-  atomicAdd(&J3[c + JX], a3 * ((1.f - mx) * my - cv));
-  atomicAdd(&J3[c + JX + 1], a3 * (mx * my + cv));
+  if (NDIM == 2) {
+    const float a1 = A.cf[0] * dx, a2 = A.cf[1] * dy;
+    w[0] = a1 * (1.f - my);
+    w[1] = a1 * my;
+    w[2] = a2 * (1.f - mx);
+    w[3] = a2 * mx;
+    const float a3 = A.j3f * v3frac;
+    const float cv = dx * dy * (1.f / 12.f);
+    w[4] = a3 * ((1.f - mx) * (1.f - my) + cv);
+    w[5] = a3 * (mx * (1.f - my) - cv);
+    w[6] = a3 * ((1.f - mx) * my - cv);
+    w[7] = a3 * (mx * my + cv);
+  } else {
+    const float dz = bz - az, mz = 0.5f * (az + bz);
+    float a = A.cf[0] * dx, cv = dy * dz * (1.f / 12.f);
+    w[0] = a * ((1.f - my) * (1.f - mz) + cv);
+    w[1] = a * (my * (1.f - mz) - cv);
+    w[2] = a * ((1.f - my) * mz - cv);
+    w[3] = a * (my * mz + cv);
+    a = A.cf[1] * dy;
+    cv = dz * dx * (1.f / 12.f);
+    w[4] = a * ((1.f - mz) * (1.f - mx) + cv);
+    w[5] = a * (mz * (1.f - mx) - cv);
+    w[6] = a * ((1.f - mz) * mx - cv);
+    w[7] = a * (mz * mx + cv);
+    a = A.cf[2] * dz;
+    cv = dx * dy * (1.f / 12.f);
+    w[8] = a * ((1.f - mx) * (1.f - my) + cv);
+    w[9] = a * (mx * (1.f - my) - cv);
+    w[10] = a * ((1.f - mx) * my - cv);
+    w[11] = a * (mx * my + cv);
+  }
 }
 
+// Shared-memory atomics of one piece's values at cell (cx,cy,cz) of the tile.
+template <int NDIM, int JX, int JY, int JPL>
+__device__ inline void flush_cell(float* J, int cx, int cy, int cz, const float w[12]) {
+  if (NDIM == 2) {
+    const int c = (cy + 1) * JX + (cx + 4);
+    atomicAdd(&J[c], w[0]);
+    atomicAdd(&J[c + JX], w[1]);
+    atomicAdd(&J[JPL + c], w[2]);
+    atomicAdd(&J[JPL + c + 1], w[3]);
+    atomicAdd(&J[2 * JPL + c], w[4]);
+    atomicAdd(&J[2 * JPL + c + 1], w[5]);
+    atomicAdd(&J[2 * JPL + c + JX], w[6]);
+    atomicAdd(&J[2 * JPL + c + JX + 1], w[7]);
+  } else {
+    constexpr int SY = JX, SZ = JX * JY;
+    const int c = (cz + 1) * SZ + (cy + 1) * SY + (cx + 4);
+    atomicAdd(&J[c], w[0]);
+    atomicAdd(&J[c + SY], w[1]);
+    atomicAdd(&J[c + SZ], w[2]);
+    atomicAdd(&J[c + SY + SZ], w[3]);
+    atomicAdd(&J[JPL + c], w[4]);
+    atomicAdd(&J[JPL + c + SZ], w[5]);
+    atomicAdd(&J[JPL + c + 1], w[6]);
+    atomicAdd(&J[JPL + c + SZ + 1], w[7]);
+    atomicAdd(&J[2 * JPL + c], w[8]);
+    atomicAdd(&J[2 * JPL + c + 1], w[9]);
+    atomicAdd(&J[2 * JPL + c + SY], w[10]);
+    atomicAdd(&J[2 * JPL + c + SY + 1], w[11]);
+  }
+}
+
+// Face crossings of the path a -> b (cell units): parameter along the path
+// (2 = none) and side (+1 / -1) per direction; |b - a| < 1 so at most one
+// crossing per direction.
+template <int NDIM>
+__device__ inline void crossings(float ax, float ay, float az, float bx, float by, float bz, float& tx, float& ty,
+                                 float& tz, int& sx, int& sy, int& sz) {
+  tx = ty = tz = 2.f;
+  sx = sy = sz = 0;
+  if (bx < 0.f) { tx = ax / (ax - bx); sx = -1; } else if (bx >= 1.f) { tx = (1.f - ax) / (bx - ax); sx = 1; }
+  if (by < 0.f) { ty = ay / (ay - by); sy = -1; } else if (by >= 1.f) { ty = (1.f - ay) / (by - ay); sy = 1; }
+  if (NDIM == 3) {
+    if (bz < 0.f) { tz = az / (az - bz); sz = -1; } else if (bz >= 1.f) { tz = (1.f - az) / (bz - az); sz = 1; }
+  }
+}
+
+// Walk the in-cell pieces of a -> b in path order, calling f(k, ox, oy, oz,
+// piece start, piece end, time share) for piece k in cell (start cell + o).
+template <int NDIM, typename Fn>
+__device__ inline void walk(float ax, float ay, float az, float bx, float by, float bz, Fn f) {
+  float tcx, tcy, tcz;
+  int scx, scy, scz;
+  crossings<NDIM>(ax, ay, az, bx, by, bz, tcx, tcy, tcz, scx, scy, scz);
+  int ox = 0, oy = 0, oz = 0;
+  float p0x = ax, p0y = ay, p0z = az, t0 = 0.f;
+#pragma unroll
+  for (int m = 0; m <= NDIM; ++m) {
+    const float tm = fminf(tcx, fminf(tcy, tcz));
+    const bool last = tm >= 1.f;
+    float p1x, p1y, p1z, t1;
+    int w = -1;
+    if (last) {
+      t1 = 1.f;
+      p1x = bx;
+      p1y = by;
+      p1z = bz;
+    } else {
+      t1 = tm;
+      w = (tm == tcx) ? 0 : ((tm == tcy) ? 1 : 2);
+      p1x = fmaf(t1, bx - ax, ax);
+      p1y = fmaf(t1, by - ay, ay);
+      p1z = fmaf(t1, bz - az, az);
+      if (w == 0) p1x = (float)(ox + (scx > 0));
+      if (w == 1) p1y = (float)(oy + (scy > 0));
+      if (w == 2) p1z = (float)(oz + (scz > 0));
+    }
+    f(m, ox, oy, oz, p0x - ox, p0y - oy, p0z - oz, p1x - ox, p1y - oy, p1z - oz, t1 - t0);
+    if (last) break;
+    if (w == 0) { ox += scx; tcx = 2.f; }
+    if (w == 1) { oy += scy; tcy = 2.f; }
+    if (w == 2) { oz += scz; tcz = 2.f; }
+    p0x = p1x;
+    p0y = p1y;
+    p0z = p1z;
+    t0 = t1;
+  }
+}
+
+// Per-thread accumulator of first pieces that start in the same cell.
+struct Acc {
+  float w[12];
+  int cell;  // packed local cell, -1 = empty
+};
+
 template <int NDIM, int TX, int TY, int TZ>
-__device__ inline void deposit_seg3(float* J, const TileArgs& A, int cx, int cy, int cz, float ax, float ay,
-                                    float az, float bx, float by, float bz) {
+__device__ inline void acc_flush(float* J, Acc& a) {
   using G = Geo<NDIM, TX, TY, TZ>;
-  constexpr int SY = G::JX, SZ = G::JX * G::JY;
-  float* J1 = J;
-  float* J2 = J + G::JPL;
-  float* J3 = J + 2 * G::JPL;
-  const float dx = bx - ax, dy = by - ay, dz = bz - az;
-  const float mx = 0.5f * (ax + bx), my = 0.5f * (ay + by), mz = 0.5f * (az + bz);
-  const int c = (cz + 1) * SZ + (cy + 1) * SY + (cx + 4);
-  {  // J1: face cx, nodes (cy, cz)
-    const float a = A.cf[0] * dx, cv = dy * dz * (1.f / 12.f);
-    atomicAdd(&J1[c], a * ((1.f - my) * (1.f - mz) + cv));
-    atomicAdd(&J1[c + SY], a * (my * (1.f - mz) - cv));
-    atomicAdd(&J1[c + SZ], a * ((1.f - my) * mz - cv));
-    atomicAdd(&J1[c + SY + SZ], a * (my * mz + cv));
+  if (a.cell >= 0) {
+    flush_cell<NDIM, G::JX, G::JY, G::JPL>(J, a.cell & 255, (a.cell >> 8) & 255, (a.cell >> 16) & 255, a.w);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) a.w[k] = 0.f;
   }
-  {  // J2: face cy, nodes (cz, cx)
-    const float a = A.cf[1] * dy, cv = dz * dx * (1.f / 12.f);
-    atomicAdd(&J2[c], a * ((1.f - mz) * (1.f - mx) + cv));
-    atomicAdd(&J2[c + SZ], a * (mz * (1.f - mx) - cv));
-    atomicAdd(&J2[c + 1], a * ((1.f - mz) * mx - cv));
-    atomicAdd(&J2[c + SZ + 1], a * (mz * mx + cv));
-  }
-  {  // J3: face cz, nodes (cx, cy)
-    const float a = A.cf[2] * dz, cv = dx * dy * (1.f / 12.f);
-    atomicAdd(&J3[c], a * ((1.f - mx) * (1.f - my) + cv));
-    atomicAdd(&J3[c + 1], a * (mx * (1.f - my) - cv));
-    atomicAdd(&J3[c + SY], a * ((1.f - mx) * my - cv));
-    atomicAdd(&J3[c + SY + 1], a * (mx * my + cv));
-  }
+  a.cell = -1;
 }
 
-// Gather + push + move + deposit of one particle.  Returns the direction code
-// of the tile it ends in (DIR_STAY or a neighbour) and rewrites p in the
-// coordinates of that tile.
+// Gather + push + move of one particle, deposit of its first in-cell piece into
+// the accumulator, crossing pieces queued.  Rewrites p in the coordinates of
+// the tile it ends in; returns its key: new cell (stayers) or NC + direction.
 template <int NDIM, int TX, int TY, int TZ>
-__device__ inline int push_one(const float* F, float* J, const TileArgs& A, P& p) {
+__device__ inline int push_one(const float* F, float* J, const TileArgs& A, P& p, Acc& acc, float* Q, int* qn) {
   using G = Geo<NDIM, TX, TY, TZ>;
   const int lx = p.cell & 255, ly = (p.cell >> 8) & 255, lz = NDIM == 3 ? (p.cell >> 16) & 255 : 0;
   if (lx >= TX || ly >= TY || lz >= TZ) {
     atomicOr(A.status, ST_BADCELL);
-    return DIR_STAY;
+    p.cell = 0;
+    return 0;
   }
-  // lattice indices and weights for stagger 0 and 1/2 in each direction
+  const int cellp = lx | (ly << 8) | (lz << 16);
   const bool hx = p.o0 < 0.5f, hy = p.o1 < 0.5f, hz = p.o2 < 0.5f;
   const int x1 = lx - hx, y1 = ly - hy, z1 = lz - hz;
   const float wx1 = hx ? p.o0 + 0.5f : p.o0 - 0.5f;
@@ -214,54 +312,62 @@ __device__ inline int push_one(const float* F, float* J, const TileArgs& A, P& p
   const float bz = NDIM == 3 ? az + uz * ig2 * A.dt_dx[2] : 0.f;
   if (!(isfinite(bx) && isfinite(by) && isfinite(bz) && isfinite(ux) && isfinite(uy) && isfinite(uz))) {
     atomicOr(A.status, ST_NONFINITE);
-    return DIR_STAY;
-  }
-  // split the path at the faces it crosses (at most one per direction) and
-  // deposit each in-cell piece
-  float tcx = 2.f, tcy = 2.f, tcz = 2.f;
-  int scx = 0, scy = 0, scz = 0;
-  if (bx < 0.f) { tcx = ax / (ax - bx); scx = -1; } else if (bx >= 1.f) { tcx = (1.f - ax) / (bx - ax); scx = 1; }
-  if (by < 0.f) { tcy = ay / (ay - by); scy = -1; } else if (by >= 1.f) { tcy = (1.f - ay) / (by - ay); scy = 1; }
-  if (NDIM == 3) {
-    if (bz < 0.f) { tcz = az / (az - bz); scz = -1; } else if (bz >= 1.f) { tcz = (1.f - az) / (bz - az); scz = 1; }
+    p.cell = cellp | ((uint32_t)DIR_STAY << 24);
+    return lx + TX * (ly + TY * lz);
   }
   const float v3 = uz * ig2;
-  int ox = 0, oy = 0, oz = 0;
-  float p0x = ax, p0y = ay, p0z = az, t0 = 0.f;
-#pragma unroll
-  for (int m = 0; m <= NDIM; ++m) {
-    const float tm = fminf(tcx, fminf(tcy, tcz));
-    const bool last = tm >= 1.f;
-    float p1x, p1y, p1z, t1;
-    int w = -1;
-    if (last) {
-      t1 = 1.f;
-      p1x = bx;
-      p1y = by;
-      p1z = bz;
-    } else {
+  // first in-cell piece into the accumulator; later pieces to the queue
+  float tcx, tcy, tcz;
+  int scx, scy, scz;
+  crossings<NDIM>(ax, ay, az, bx, by, bz, tcx, tcy, tcz, scx, scy, scz);
+  const float tm = fminf(tcx, fminf(tcy, tcz));
+  {
+    float p1x = bx, p1y = by, p1z = bz, t1 = 1.f;
+    if (tm < 1.f) {
       t1 = tm;
-      w = (tm == tcx) ? 0 : ((tm == tcy) ? 1 : 2);
+      const int w = (tm == tcx) ? 0 : ((tm == tcy) ? 1 : 2);
       p1x = fmaf(t1, bx - ax, ax);
       p1y = fmaf(t1, by - ay, ay);
       p1z = fmaf(t1, bz - az, az);
-      if (w == 0) p1x = (float)(ox + (scx > 0));
-      if (w == 1) p1y = (float)(oy + (scy > 0));
-      if (w == 2) p1z = (float)(oz + (scz > 0));
+      if (w == 0) p1x = (float)(scx > 0);
+      if (w == 1) p1y = (float)(scy > 0);
+      if (w == 2) p1z = (float)(scz > 0);
     }
-    if (NDIM == 3)
-      deposit_seg3<NDIM, TX, TY, TZ>(J, A, lx + ox, ly + oy, lz + oz, p0x - ox, p0y - oy, p0z - oz, p1x - ox,
-                                     p1y - oy, p1z - oz);
-    else
-      deposit_seg2<G::JX, G::JY>(J, A, lx + ox, ly + oy, p0x - ox, p0y - oy, p1x - ox, p1y - oy, v3 * (t1 - t0));
-    if (last) break;
-    if (w == 0) { ox += scx; tcx = 2.f; }
-    if (w == 1) { oy += scy; tcy = 2.f; }
-    if (w == 2) { oz += scz; tcz = 2.f; }
-    p0x = p1x;
-    p0y = p1y;
-    p0z = p1z;
-    t0 = t1;
+    if (acc.cell != cellp) {
+      acc_flush<NDIM, TX, TY, TZ>(J, acc);
+      acc.cell = cellp;
+    }
+    float w[12];
+    seg_weights<NDIM>(A, ax, ay, az, p1x, p1y, p1z, v3 * t1, w);
+#pragma unroll
+    for (int k = 0; k < (NDIM == 3 ? 12 : 8); ++k) acc.w[k] += w[k];
+  }
+  if (tm < 1.f) {
+    const int q = atomicAdd(qn, 1);
+    if (q < kQCap) {
+      float* e = Q + q * G::QW;
+      e[0] = __int_as_float(cellp);
+      e[1] = ax;
+      e[2] = ay;
+      e[3] = bx;
+      e[4] = by;
+      if (NDIM == 3) {
+        e[5] = az;
+        e[6] = bz;
+      } else {
+        e[5] = v3;
+      }
+    } else {
+      // queue full: deposit the remaining pieces here
+      walk<NDIM>(ax, ay, az, bx, by, bz,
+                 [&](int k, int ox, int oy, int oz, float sx0, float sy0, float sz0, float sx1, float sy1, float sz1,
+                     float frac) {
+                   if (k == 0) return;
+                   float w[12];
+                   seg_weights<NDIM>(A, sx0, sy0, sz0, sx1, sy1, sz1, v3 * frac, w);
+                   flush_cell<NDIM, G::JX, G::JY, G::JPL>(J, lx + ox, ly + oy, lz + oz, w);
+                 });
+    }
   }
   // new cell and offset
   int cx = 0, cy = 0, cz = 0;
@@ -289,284 +395,386 @@ __device__ inline int push_one(const float* F, float* J, const TileArgs& A, P& p
   p.u0 = ux;
   p.u1 = uy;
   p.u2 = uz;
-  return dir;
+  return dir == DIR_STAY ? gx + TX * (gy + TY * gz) : G::NC + dir;
 }
 
-// Block-wide exclusive scan of one int per thread; returns the total.
-__device__ inline int block_excl_scan(int v, int* scratch, int& total) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  int x = v;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    int y = __shfl_up_sync(0xffffffffu, x, o);
-    if (lane >= o) x += y;
-  }
-  if (lane == 31) scratch[warp] = x;
-  __syncthreads();
-  if (warp == 0) {
-    int s = lane < (kThreads / 32) ? scratch[lane] : 0;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      int y = __shfl_up_sync(0xffffffffu, s, o);
-      if (lane >= o) s += y;
-    }
-    if (lane < (kThreads / 32)) scratch[lane] = s;
-  }
-  __syncthreads();
-  const int before = warp > 0 ? scratch[warp - 1] : 0;
-  total = scratch[kThreads / 32 - 1];
-  __syncthreads();
-  return before + x - v;
-}
-
+// Deposit the queued crossing pieces (all but the first of each path).
 template <int NDIM, int TX, int TY, int TZ>
-__device__ inline void store_chunk(const TileArgs& A, int t, long long base, int cap, P (&pp)[kPPT],
-                                   int (&dir)[kPPT], int nvalid, int& ws, int& wm, int* scr) {
-  int ns = 0, nm = 0;
-#pragma unroll
-  for (int r = 0; r < kPPT; ++r) {
-    if (r < nvalid) {
-      if (dir[r] == DIR_STAY)
-        ++ns;
-      else
-        ++nm;
-    }
+__device__ inline void drain_queue(float* J, const TileArgs& A, const float* Q, int n) {
+  using G = Geo<NDIM, TX, TY, TZ>;
+  for (int q = threadIdx.x; q < n; q += kThreads) {
+    const float* e = Q + q * G::QW;
+    const int c = __float_as_int(e[0]);
+    const int lx = c & 255, ly = (c >> 8) & 255, lz = (c >> 16) & 255;
+    const float ax = e[1], ay = e[2], bx = e[3], by = e[4];
+    const float az = NDIM == 3 ? e[5] : 0.f, bz = NDIM == 3 ? e[6] : 0.f;
+    const float v3 = NDIM == 3 ? 0.f : e[5];
+    walk<NDIM>(ax, ay, az, bx, by, bz,
+               [&](int k, int ox, int oy, int oz, float sx0, float sy0, float sz0, float sx1, float sy1, float sz1,
+                   float frac) {
+                 if (k == 0) return;
+                 float w[12];
+                 seg_weights<NDIM>(A, sx0, sy0, sz0, sx1, sy1, sz1, v3 * frac, w);
+                 flush_cell<NDIM, G::JX, G::JY, G::JPL>(J, lx + ox, ly + oy, lz + oz, w);
+               });
   }
-  int S, M;
-  int rs = block_excl_scan(ns, scr, S);
-  int rm = block_excl_scan(nm, scr + 16, M);
-  const int free_slots = cap - ws - wm;
-  const int putS = S < free_slots ? S : free_slots;
-  const int putM = M < free_slots - putS ? M : free_slots - putS;
-#pragma unroll
-  for (int r = 0; r < kPPT; ++r) {
-    if (r >= nvalid) continue;
-    long long slot = -1;
-    if (dir[r] == DIR_STAY) {
-      if (rs < putS) slot = base + ws + rs;
-      ++rs;
-    } else {
-      if (rm < putM) slot = base + cap - 1 - (wm + rm);
-      ++rm;
-    }
-    const P& q = pp[r];
-    if (slot >= 0) {
-      A.out.cell[slot] = q.cell;
-      A.out.o[0][slot] = q.o0;
-      A.out.o[1][slot] = q.o1;
-      if (NDIM == 3) A.out.o[2][slot] = q.o2;
-      A.out.u[0][slot] = q.u0;
-      A.out.u[1][slot] = q.u1;
-      A.out.u[2][slot] = q.u2;
-      if (A.out.id) A.out.id[slot] = q.id;
-    } else {
-      // tile region full: park the particle in the spill list, tagged with the
-      // tile it belongs to; the host re-bins before the next step
-      atomicOr(A.status, ST_SPILL);
-      int k = atomicAdd(A.spill_count, 1);
-      if (k >= A.spill_cap) {
-        atomicOr(A.status, ST_SPILL_LOST);
-        continue;
-      }
-      const int d = dir[r];
-      int ti[3] = {t % A.nt[0], (t / A.nt[0]) % A.nt[1], t / (A.nt[0] * A.nt[1])};
-      ti[0] = (ti[0] + (d % 3) - 1 + A.nt[0]) % A.nt[0];
-      ti[1] = (ti[1] + (d / 3) % 3 - 1 + A.nt[1]) % A.nt[1];
-      ti[2] = (ti[2] + d / 9 - 1 + A.nt[2]) % A.nt[2];
-      A.spill.tile[k] = (ti[2] * A.nt[1] + ti[1]) * A.nt[0] + ti[0];
-      A.spill.cell[k] = (q.cell & 0x00FFFFFFu) | ((uint32_t)DIR_STAY << 24);
-      A.spill.o[0][k] = q.o0;
-      A.spill.o[1][k] = q.o1;
-      A.spill.o[2][k] = q.o2;
-      A.spill.u[0][k] = q.u0;
-      A.spill.u[1][k] = q.u1;
-      A.spill.u[2][k] = q.u2;
-      if (A.spill.id) A.spill.id[k] = q.id;
-    }
-  }
-  ws += putS;
-  wm += putM;
 }
 
-template <int NDIM, int TX, int TY, int TZ>
-__global__ void __launch_bounds__(kThreads, 2)
+__device__ inline float* sfield(const TileArgs& A, int f) {
+  return A.scratch + ((size_t)blockIdx.x * 8 + f) * (size_t)A.scap;
+}
+
+__device__ inline void scratch_put(const TileArgs& A, long long i, const P& p) {
+  sfield(A, 0)[i] = __uint_as_float(p.cell);
+  sfield(A, 1)[i] = p.o0;
+  sfield(A, 2)[i] = p.o1;
+  sfield(A, 3)[i] = p.o2;
+  sfield(A, 4)[i] = p.u0;
+  sfield(A, 5)[i] = p.u1;
+  sfield(A, 6)[i] = p.u2;
+  sfield(A, 7)[i] = __int_as_float(p.id);
+}
+
+template <int NDIM, int TX, int TY, int TZ, int MINB>
+__global__ void __launch_bounds__(kThreads, MINB)
     k_tile_push(const __grid_constant__ CUtensorMap fmap, const __grid_constant__ CUtensorMap jmap, TileArgs A) {
   using G = Geo<NDIM, TX, TY, TZ>;
   extern __shared__ __align__(1024) unsigned char smem[];
   float* F = reinterpret_cast<float*>(smem + G::FOFF);
   float* J = reinterpret_cast<float*>(smem + G::JOFF);
-  long long* inc = reinterpret_cast<long long*>(smem + G::INCOFF);
-  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + G::MISCOFF);
-  int* scr = reinterpret_cast<int*>(smem + G::MISCOFF + 16);        // 32 ints
-  int* nbm = reinterpret_cast<int*>(smem + G::MISCOFF + 16 + 128);  // 27 ints: mover counts
-  int* nbp = nbm + 32;                                              // 28 ints: prefix
-  long long* nbs = reinterpret_cast<long long*>(smem + G::MISCOFF + 512);  // 27 starts
+  int* hist = reinterpret_cast<int*>(smem + G::HOFF);
+  int* cursor = reinterpret_cast<int*>(smem + G::COFF);
+  float* Q = reinterpret_cast<float*>(smem + G::QOFF);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + G::MOFF);
+  int* misc = reinterpret_cast<int*>(smem + G::MOFF + 16);  // [0] tile [1] queue [2..9] scan [12..38] counts
+  int* gpre = misc + 40;                                     // 28 ints: incoming group prefix
+  int* gsrc = gpre + 28;                                     // 27 ints: source tile of group d
+  int* gofs = gsrc + 27;                                     // 27 ints: group start within source region
+  const int tid = threadIdx.x;
 
-  const int t = blockIdx.x;
-  const int tix = t % A.nt[0], tiy = (t / A.nt[0]) % A.nt[1], tiz = t / (A.nt[0] * A.nt[1]);
-  const int x0 = tix * TX, y0 = tiy * TY, z0 = tiz * TZ;
-
-  if (threadIdx.x == 0) {
+  if (tid == 0) {
     mbar_init(bar, 1);
     fence_barrier_init();
   }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    mbar_arrive_expect_tx(bar, (uint32_t)G::FBYTES);
-    if (NDIM == 3)
-      tma_load_4d(F, &fmap, bar, x0, y0, z0, 0);
-    else
-      tma_load_3d(F, &fmap, bar, x0, y0, 0);
-  }
-  for (int k = threadIdx.x; k < 3 * G::JPL; k += kThreads) J[k] = 0.f;
-  // neighbour mover lists: who sends to this tile
-  if (threadIdx.x < 27) {
-    const int d = threadIdx.x;  // direction from the neighbour to this tile
-    int cnt = 0;
-    long long start = 0;
-    const int ddx = d % 3 - 1, ddy = (d / 3) % 3 - 1, ddz = d / 9 - 1;
-    const bool valid = d != DIR_STAY && (NDIM == 3 || ddz == 0);
-    if (valid) {
-      const int nx_ = (tix - ddx + A.nt[0]) % A.nt[0];
-      const int ny_ = (tiy - ddy + A.nt[1]) % A.nt[1];
-      const int nz_ = NDIM == 3 ? (tiz - ddz + A.nt[2]) % A.nt[2] : 0;
-      const int nb = (nz_ * A.nt[1] + ny_) * A.nt[0] + nx_;
-      cnt = A.in_move[nb];
-      start = A.base[nb] + A.cap[nb] - cnt;
+  uint32_t phase = 0;
+  for (;;) {
+    __syncthreads();
+    if (tid == 0) {
+      misc[0] = atomicAdd(A.work, 1);
+      misc[1] = 0;
     }
-    nbm[d] = cnt;
-    nbs[d] = start;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    int run = 0;
-    for (int d = 0; d < 27; ++d) {
-      nbp[d] = run;
-      run += nbm[d];
+    __syncthreads();
+    const int t = misc[0];
+    if (t >= A.ntiles) break;
+    const int tix = t % A.nt[0], tiy = (t / A.nt[0]) % A.nt[1], tiz = t / (A.nt[0] * A.nt[1]);
+    const int x0 = tix * TX, y0 = tiy * TY, z0 = tiz * TZ;
+    if (tid == 0) {
+      mbar_arrive_expect_tx(bar, (uint32_t)G::FBYTES);
+      if (NDIM == 3)
+        tma_load_4d(F, &fmap, bar, x0, y0, z0, 0);
+      else
+        tma_load_3d(F, &fmap, bar, x0, y0, 0);
     }
-    nbp[27] = run;
-  }
-  // wait for the staged fields (bounded)
-  if (!mbar_wait_bounded(bar, 0, kWaitLimit)) {
-    if (threadIdx.x == 0) atomicOr(A.status, ST_TIMEOUT);
-    // give the copy a second bounded chance to land before the CTA exits
-    mbar_wait_bounded(bar, 0, kWaitLimit);
-    return;
-  }
-  __syncthreads();
+    for (int k = tid; k < 3 * G::JPL; k += kThreads) J[k] = 0.f;
+    for (int k = tid; k < G::NK; k += kThreads) hist[k] = 0;
+    if (tid < kDirs) {
+      // group of the neighbour nb = t - (offset of direction d) that moved into t
+      const int d = tid;
+      const int ddx = d % 3 - 1, ddy = (d / 3) % 3 - 1, ddz = d / 9 - 1;
+      int cnt = 0, src = 0, ofs = 0;
+      if (d != DIR_STAY && (NDIM == 3 || ddz == 0)) {
+        const int nx_ = (tix - ddx + A.nt[0]) % A.nt[0];
+        const int ny_ = (tiy - ddy + A.nt[1]) % A.nt[1];
+        const int nz_ = NDIM == 3 ? (tiz - ddz + A.nt[2]) % A.nt[2] : 0;
+        src = (nz_ * A.nt[1] + ny_) * A.nt[0] + nx_;
+        cnt = A.in.mcount[src * kDirs + d];
+        ofs = A.in.mstart[src * kDirs + d];
+      }
+      misc[12 + d] = cnt;
+      gsrc[d] = src;
+      gofs[d] = ofs;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      int run = 0;
+      for (int d = 0; d < kDirs; ++d) {
+        gpre[d] = run;
+        run += misc[12 + d];
+      }
+      gpre[kDirs] = run;
+    }
+    if (!mbar_wait_bounded(bar, phase, kWaitLimit)) {
+      if (tid == 0) atomicOr(A.status, ST_TIMEOUT);
+      mbar_wait_bounded(bar, phase, kWaitLimit);
+      return;
+    }
+    phase ^= 1u;
+    __syncthreads();
 
-  const long long base = A.base[t];
-  const int cap = A.cap[t];
-  int ws = 0, wm = 0;
+    const long long base = A.base[t];
+    const int cap = A.cap[t];
+    const int nstay = A.in.stay[t];
+    const int ninc = gpre[kDirs];
 
-  // (1) own stayers: vectorised loads, 4 consecutive particles per thread
-  const int nstay = A.in_stay[t];
-  for (int c0 = 0; c0 < nstay; c0 += kChunk) {
-    P pp[kPPT];
-    int dir[kPPT];
-    const int first = c0 + threadIdx.x * kPPT;
-    int nvalid = nstay - first;
-    nvalid = nvalid < 0 ? 0 : (nvalid > kPPT ? kPPT : nvalid);
-    if (nvalid > 0) {
-      const long long s = base + first;
-      const uint4 cl = *reinterpret_cast<const uint4*>(A.in.cell + s);
-      const float4 q0 = *reinterpret_cast<const float4*>(A.in.o[0] + s);
-      const float4 q1 = *reinterpret_cast<const float4*>(A.in.o[1] + s);
-      float4 q2 = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (NDIM == 3) q2 = *reinterpret_cast<const float4*>(A.in.o[2] + s);
-      const float4 v0 = *reinterpret_cast<const float4*>(A.in.u[0] + s);
-      const float4 v1 = *reinterpret_cast<const float4*>(A.in.u[1] + s);
-      const float4 v2 = *reinterpret_cast<const float4*>(A.in.u[2] + s);
-      int4 idv = make_int4(0, 0, 0, 0);
-      if (A.in.id) idv = *reinterpret_cast<const int4*>(A.in.id + s);
-      pp[0] = P{cl.x, q0.x, q1.x, q2.x, v0.x, v1.x, v2.x, idv.x};
-      pp[1] = P{cl.y, q0.y, q1.y, q2.y, v0.y, v1.y, v2.y, idv.y};
-      pp[2] = P{cl.z, q0.z, q1.z, q2.z, v0.z, v1.z, v2.z, idv.z};
-      pp[3] = P{cl.w, q0.w, q1.w, q2.w, v0.w, v1.w, v2.w, idv.w};
-    }
+    // ---- pass 1a: own stayers, 4 consecutive (same-cell) particles per thread
+    for (int c0 = 0; c0 < nstay; c0 += kChunk) {
+      P pp[kPPT];
+      const int first = c0 + tid * kPPT;
+      int nvalid = nstay - first;
+      nvalid = nvalid < 0 ? 0 : (nvalid > kPPT ? kPPT : nvalid);
+      if (nvalid > 0) {
+        const long long s = base + first;
+        const uint4 cl = *reinterpret_cast<const uint4*>(A.in.p.cell + s);
+        const float4 q0 = *reinterpret_cast<const float4*>(A.in.p.o[0] + s);
+        const float4 q1 = *reinterpret_cast<const float4*>(A.in.p.o[1] + s);
+        float4 q2 = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (NDIM == 3) q2 = *reinterpret_cast<const float4*>(A.in.p.o[2] + s);
+        const float4 v0 = *reinterpret_cast<const float4*>(A.in.p.u[0] + s);
+        const float4 v1 = *reinterpret_cast<const float4*>(A.in.p.u[1] + s);
+        const float4 v2 = *reinterpret_cast<const float4*>(A.in.p.u[2] + s);
+        int4 idv = make_int4(0, 0, 0, 0);
+        if (A.in.p.id) idv = *reinterpret_cast<const int4*>(A.in.p.id + s);
+        pp[0] = P{cl.x, q0.x, q1.x, q2.x, v0.x, v1.x, v2.x, idv.x};
+        pp[1] = P{cl.y, q0.y, q1.y, q2.y, v0.y, v1.y, v2.y, idv.y};
+        pp[2] = P{cl.z, q0.z, q1.z, q2.z, v0.z, v1.z, v2.z, idv.z};
+        pp[3] = P{cl.w, q0.w, q1.w, q2.w, v0.w, v1.w, v2.w, idv.w};
+      }
+      Acc acc;
 #pragma unroll
-    for (int r = 0; r < kPPT; ++r) dir[r] = r < nvalid ? push_one<NDIM, TX, TY, TZ>(F, J, A, pp[r]) : DIR_STAY;
-    store_chunk<NDIM, TX, TY, TZ>(A, t, base, cap, pp, dir, nvalid, ws, wm, scr);
-  }
-
-  // (2) incoming movers from the neighbours' lists, compacted into `inc`
-  const int ncand = nbp[27];
-  int ninc = 0;
-  for (int c0 = 0; c0 < ncand; c0 += kThreads) {
-    const int k = c0 + threadIdx.x;
-    int match = 0;
-    long long slot = 0;
-    if (k < ncand) {
-      int d = 0;
-      while (d < 26 && nbp[d + 1] <= k) ++d;
-      slot = nbs[d] + (k - nbp[d]);
-      match = (int)(A.in.cell[slot] >> 24) == d;
-    }
-    int tot;
-    const int pos = block_excl_scan(match, scr, tot);
-    if (ninc + tot > kIncMax) {
-      // flush the list before it overflows: process what is queued
-      // (all threads take part; the scan above is repeated for this batch)
+      for (int k = 0; k < 12; ++k) acc.w[k] = 0.f;
+      acc.cell = -1;
+      int hk = -1, hc = 0;
+#pragma unroll
+      for (int r = 0; r < kPPT; ++r) {
+        if (r < nvalid) {
+          const int key = push_one<NDIM, TX, TY, TZ>(F, J, A, pp[r], acc, Q, misc + 1);
+          if (key != hk) {
+            if (hk >= 0) atomicAdd(&hist[hk], hc);
+            hk = key;
+            hc = 0;
+          }
+          ++hc;
+        }
+      }
+      acc_flush<NDIM, TX, TY, TZ>(J, acc);
+      if (hk >= 0) atomicAdd(&hist[hk], hc);
+      if (nvalid == kPPT) {
+        *reinterpret_cast<float4*>(sfield(A, 0) + first) =
+            make_float4(__uint_as_float(pp[0].cell), __uint_as_float(pp[1].cell), __uint_as_float(pp[2].cell),
+                        __uint_as_float(pp[3].cell));
+        *reinterpret_cast<float4*>(sfield(A, 1) + first) = make_float4(pp[0].o0, pp[1].o0, pp[2].o0, pp[3].o0);
+        *reinterpret_cast<float4*>(sfield(A, 2) + first) = make_float4(pp[0].o1, pp[1].o1, pp[2].o1, pp[3].o1);
+        if (NDIM == 3)
+          *reinterpret_cast<float4*>(sfield(A, 3) + first) = make_float4(pp[0].o2, pp[1].o2, pp[2].o2, pp[3].o2);
+        *reinterpret_cast<float4*>(sfield(A, 4) + first) = make_float4(pp[0].u0, pp[1].u0, pp[2].u0, pp[3].u0);
+        *reinterpret_cast<float4*>(sfield(A, 5) + first) = make_float4(pp[0].u1, pp[1].u1, pp[2].u1, pp[3].u1);
+        *reinterpret_cast<float4*>(sfield(A, 6) + first) = make_float4(pp[0].u2, pp[1].u2, pp[2].u2, pp[3].u2);
+        if (A.in.p.id)
+          *reinterpret_cast<float4*>(sfield(A, 7) + first) =
+              make_float4(__int_as_float(pp[0].id), __int_as_float(pp[1].id), __int_as_float(pp[2].id),
+                          __int_as_float(pp[3].id));
+      } else {
+#pragma unroll
+        for (int r = 0; r < kPPT; ++r)
+          if (r < nvalid) scratch_put(A, first + r, pp[r]);
+      }
       __syncthreads();
-      for (int c1 = 0; c1 < ninc; c1 += kChunk) {
-        P pp[kPPT];
-        int dir[kPPT];
-        const int first = c1 + threadIdx.x * kPPT;
-        int nvalid = ninc - first;
-        nvalid = nvalid < 0 ? 0 : (nvalid > kPPT ? kPPT : nvalid);
+      const int nq = misc[1];
+      if (nq > kQCap / 2) {
+        drain_queue<NDIM, TX, TY, TZ>(J, A, Q, nq < kQCap ? nq : kQCap);
+        __syncthreads();
+        if (tid == 0) misc[1] = 0;
+        __syncthreads();
+      }
+    }
+
+    // ---- pass 1b: movers the neighbours sent to this tile
+    for (int c0 = 0; c0 < ninc; c0 += kThreads) {
+      const int k = c0 + tid;
+      if (k < ninc) {
+        int d = 0;
+#pragma unroll 1
+        for (int step = 16; step > 0; step >>= 1)
+          if (d + step < kDirs && gpre[d + step] <= k) d += step;
+        const int src = gsrc[d];
+        const long long s = A.base[src] + gofs[d] + (k - gpre[d]);
+        P p{A.in.p.cell[s] & 0x00FFFFFFu, A.in.p.o[0][s], A.in.p.o[1][s], NDIM == 3 ? A.in.p.o[2][s] : 0.f,
+            A.in.p.u[0][s], A.in.p.u[1][s], A.in.p.u[2][s], A.in.p.id ? A.in.p.id[s] : 0};
+        Acc acc;
 #pragma unroll
-        for (int r = 0; r < kPPT; ++r) {
-          if (r < nvalid) {
-            const long long s = inc[first + r];
-            pp[r] = P{A.in.cell[s] & 0x00FFFFFFu, A.in.o[0][s], A.in.o[1][s], NDIM == 3 ? A.in.o[2][s] : 0.f,
-                      A.in.u[0][s], A.in.u[1][s], A.in.u[2][s], A.in.id ? A.in.id[s] : 0};
+        for (int q = 0; q < 12; ++q) acc.w[q] = 0.f;
+        acc.cell = -1;
+        const int key = push_one<NDIM, TX, TY, TZ>(F, J, A, p, acc, Q, misc + 1);
+        acc_flush<NDIM, TX, TY, TZ>(J, acc);
+        if (nstay + k < A.scap) {
+          atomicAdd(&hist[key], 1);
+          scratch_put(A, nstay + k, p);
+        } else {
+          // more arrivals than the scratch holds: the particle (fully advanced)
+          // goes to the spill list and the host re-bins before the next step
+          atomicOr(A.status, ST_SPILL);
+          const int q = atomicAdd(A.spill_count, 1);
+          if (q >= A.spill_cap) {
+            atomicOr(A.status, ST_SPILL_LOST);
+          } else {
+            const int dir = (int)(p.cell >> 24);
+            int ti[3] = {tix, tiy, tiz};
+            ti[0] = (ti[0] + dir % 3 - 1 + A.nt[0]) % A.nt[0];
+            ti[1] = (ti[1] + (dir / 3) % 3 - 1 + A.nt[1]) % A.nt[1];
+            ti[2] = (ti[2] + dir / 9 - 1 + A.nt[2]) % A.nt[2];
+            A.spill.tile[q] = (ti[2] * A.nt[1] + ti[1]) * A.nt[0] + ti[0];
+            A.spill.cell[q] = (p.cell & 0x00FFFFFFu) | ((uint32_t)DIR_STAY << 24);
+            A.spill.o[0][q] = p.o0;
+            A.spill.o[1][q] = p.o1;
+            A.spill.o[2][q] = p.o2;
+            A.spill.u[0][q] = p.u0;
+            A.spill.u[1][q] = p.u1;
+            A.spill.u[2][q] = p.u2;
+            if (A.spill.id) A.spill.id[q] = p.id;
           }
         }
-#pragma unroll
-        for (int r = 0; r < kPPT; ++r) dir[r] = r < nvalid ? push_one<NDIM, TX, TY, TZ>(F, J, A, pp[r]) : DIR_STAY;
-        store_chunk<NDIM, TX, TY, TZ>(A, t, base, cap, pp, dir, nvalid, ws, wm, scr);
       }
-      ninc = 0;
       __syncthreads();
-    }
-    if (match) inc[ninc + pos] = slot;
-    ninc += tot;
-    __syncthreads();
-  }
-  for (int c1 = 0; c1 < ninc; c1 += kChunk) {
-    P pp[kPPT];
-    int dir[kPPT];
-    const int first = c1 + threadIdx.x * kPPT;
-    int nvalid = ninc - first;
-    nvalid = nvalid < 0 ? 0 : (nvalid > kPPT ? kPPT : nvalid);
-#pragma unroll
-    for (int r = 0; r < kPPT; ++r) {
-      if (r < nvalid) {
-        const long long s = inc[first + r];
-        pp[r] = P{A.in.cell[s] & 0x00FFFFFFu, A.in.o[0][s], A.in.o[1][s], NDIM == 3 ? A.in.o[2][s] : 0.f,
-                  A.in.u[0][s], A.in.u[1][s], A.in.u[2][s], A.in.id ? A.in.id[s] : 0};
+      const int nq = misc[1];
+      if (nq > kQCap / 2) {
+        drain_queue<NDIM, TX, TY, TZ>(J, A, Q, nq < kQCap ? nq : kQCap);
+        __syncthreads();
+        if (tid == 0) misc[1] = 0;
+        __syncthreads();
       }
     }
-#pragma unroll
-    for (int r = 0; r < kPPT; ++r) dir[r] = r < nvalid ? push_one<NDIM, TX, TY, TZ>(F, J, A, pp[r]) : DIR_STAY;
-    store_chunk<NDIM, TX, TY, TZ>(A, t, base, cap, pp, dir, nvalid, ws, wm, scr);
-  }
+    {
+      const int nq = misc[1];
+      if (nq > 0) drain_queue<NDIM, TX, TY, TZ>(J, A, Q, nq < kQCap ? nq : kQCap);
+    }
 
-  if (threadIdx.x == 0) {
-    A.out_stay[t] = ws;
-    A.out_move[t] = wm;
-  }
-  // flush the current tile: every thread orders its shared-memory atomics
-  // before the async proxy reads them; one thread issues the TMA reduce-add
-  fence_proxy_async_smem();
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    if (NDIM == 3)
-      tma_reduce_add_4d(&jmap, J, x0, y0, z0, 0);
-    else
-      tma_reduce_add_3d(&jmap, J, x0, y0, 0);
-    tma_commit();
-    tma_wait_read0();
+    // ---- flush the current tile: order the shared atomics before the async
+    // proxy reads them; one thread issues the TMA reduce-add
+    fence_proxy_async_smem();
+    __syncthreads();
+    if (tid == 0) {
+      if (NDIM == 3)
+        tma_reduce_add_4d(&jmap, J, x0, y0, z0, 0);
+      else
+        tma_reduce_add_3d(&jmap, J, x0, y0, 0);
+      tma_commit();
+    }
+
+    // ---- exclusive scan of the key histogram (stayers by cell, then movers by direction)
+    {
+      constexpr int PER = (G::NK + kThreads - 1) / kThreads;
+      int v[PER];
+      int run = 0;
+#pragma unroll
+      for (int r = 0; r < PER; ++r) {
+        const int k = tid * PER + r;
+        v[r] = k < G::NK ? hist[k] : 0;
+        run += v[r];
+      }
+      const int lane = tid & 31, warp = tid >> 5;
+      int x = run;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+      }
+      int* wsum = misc + 2;  // 8 warps
+      if (lane == 31) wsum[warp] = x;
+      __syncthreads();
+      if (tid == 0) {
+        int s = 0;
+        for (int w = 0; w < kThreads / 32; ++w) {
+          const int tmp = wsum[w];
+          wsum[w] = s;
+          s += tmp;
+        }
+      }
+      __syncthreads();
+      int pre = wsum[warp] + x - run;
+#pragma unroll
+      for (int r = 0; r < PER; ++r) {
+        const int k = tid * PER + r;
+        if (k < G::NK) cursor[k] = pre;
+        pre += v[r];
+      }
+    }
+    __syncthreads();
+    const int total = cursor[G::NK - 1] + hist[G::NK - 1];
+    const int nst = cursor[G::NC];  // stayers
+    if (tid < kDirs) {
+      // placed counts (a full region spills the tail)
+      const int st0 = cursor[G::NC + tid];
+      const int cnt = hist[G::NC + tid];
+      int placed = cap - st0;
+      placed = placed < 0 ? 0 : (placed > cnt ? cnt : placed);
+      A.out.mstart[t * kDirs + tid] = st0;
+      A.out.mcount[t * kDirs + tid] = tid == DIR_STAY ? 0 : placed;
+    }
+    if (tid == 0) {
+      A.out.stay[t] = nst < cap ? nst : cap;
+      const int mv = total - nst;
+      int pm = cap - nst;
+      pm = pm < 0 ? 0 : (pm > mv ? mv : pm);
+      A.out.move[t] = pm;
+    }
+
+    // ---- pass 2: scatter from scratch into the region, sorted by key
+    for (int c0 = 0; c0 < total; c0 += kThreads) {
+      const int i = c0 + tid;
+      const bool valid = i < total;
+      const unsigned act = __ballot_sync(0xffffffffu, valid);
+      if (valid) {
+        const uint32_t cell = __float_as_uint(sfield(A, 0)[i]);
+        const int dir = (int)(cell >> 24);
+        const int key = dir == DIR_STAY
+                            ? (int)(cell & 255) + TX * ((int)((cell >> 8) & 255) + TY * (int)((cell >> 16) & 255))
+                            : G::NC + dir;
+        const unsigned same = __match_any_sync(act, key);
+        const int leader = __ffs(same) - 1;
+        const int lane = tid & 31;
+        int pos0 = 0;
+        if (lane == leader) pos0 = atomicAdd(&cursor[key], __popc(same));
+        pos0 = __shfl_sync(same, pos0, leader);
+        const int pos = pos0 + __popc(same & ((1u << lane) - 1u));
+        P q{cell, sfield(A, 1)[i], sfield(A, 2)[i], NDIM == 3 ? sfield(A, 3)[i] : 0.f, sfield(A, 4)[i],
+            sfield(A, 5)[i], sfield(A, 6)[i], __float_as_int(sfield(A, 7)[i])};
+        if (pos < cap) {
+          const long long s = base + pos;
+          A.out.p.cell[s] = q.cell;
+          A.out.p.o[0][s] = q.o0;
+          A.out.p.o[1][s] = q.o1;
+          if (NDIM == 3) A.out.p.o[2][s] = q.o2;
+          A.out.p.u[0][s] = q.u0;
+          A.out.p.u[1][s] = q.u1;
+          A.out.p.u[2][s] = q.u2;
+          if (A.out.p.id) A.out.p.id[s] = q.id;
+        } else {
+          // region full: park the particle in the spill list with the tile it
+          // belongs to; the host re-bins before the next step
+          atomicOr(A.status, ST_SPILL);
+          const int k = atomicAdd(A.spill_count, 1);
+          if (k >= A.spill_cap) {
+            atomicOr(A.status, ST_SPILL_LOST);
+          } else {
+            int ti[3] = {tix, tiy, tiz};
+            ti[0] = (ti[0] + dir % 3 - 1 + A.nt[0]) % A.nt[0];
+            ti[1] = (ti[1] + (dir / 3) % 3 - 1 + A.nt[1]) % A.nt[1];
+            ti[2] = (ti[2] + dir / 9 - 1 + A.nt[2]) % A.nt[2];
+            A.spill.tile[k] = (ti[2] * A.nt[1] + ti[1]) * A.nt[0] + ti[0];
+            A.spill.cell[k] = (q.cell & 0x00FFFFFFu) | ((uint32_t)DIR_STAY << 24);
+            A.spill.o[0][k] = q.o0;
+            A.spill.o[1][k] = q.o1;
+            A.spill.o[2][k] = q.o2;
+            A.spill.u[0][k] = q.u0;
+            A.spill.u[1][k] = q.u1;
+            A.spill.u[2][k] = q.u2;
+            if (A.spill.id) A.spill.id[k] = q.id;
+          }
+        }
+      }
+    }
+    // the shared current tile must stay intact until the TMA has read it
+    if (tid == 0) tma_wait_read0();
   }
 }
 
@@ -589,26 +797,24 @@ __device__ inline int dest_tile(const Tiles& tg, int t, uint32_t cell) {
   return (iz * tg.nt[1] + iy) * tg.nt[0] + ix;
 }
 
-__global__ void k_flatten(Tiles tg, Part32 in, const int* stay, const int* move, const long long* out_off,
-                          Flat32 out) {
+__global__ void k_flatten(Tiles tg, TileSide in, const long long* out_off, Flat32 out) {
   const int t = blockIdx.x;
-  const int ns = stay[t], nm = move[t];
+  const int n = in.stay[t] + in.move[t];
   const long long base = tg.base[t];
-  const int cap = tg.cap[t];
   const long long o = out_off[t];
-  for (int k = threadIdx.x; k < ns + nm; k += blockDim.x) {
-    const long long s = k < ns ? base + k : base + cap - nm + (k - ns);
-    const uint32_t c = in.cell[s];
+  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    const long long s = base + k;
+    const uint32_t c = in.p.cell[s];
     const long long w = o + k;
     out.tile[w] = dest_tile(tg, t, c);
     out.cell[w] = (c & 0x00FFFFFFu) | ((uint32_t)DIR_STAY << 24);
-    out.o[0][w] = in.o[0][s];
-    out.o[1][w] = in.o[1][s];
-    out.o[2][w] = tg.ndim == 3 ? in.o[2][s] : 0.f;
-    out.u[0][w] = in.u[0][s];
-    out.u[1][w] = in.u[1][s];
-    out.u[2][w] = in.u[2][s];
-    if (out.id) out.id[w] = in.id ? in.id[s] : 0;
+    out.o[0][w] = in.p.o[0][s];
+    out.o[1][w] = in.p.o[1][s];
+    out.o[2][w] = tg.ndim == 3 ? in.p.o[2][s] : 0.f;
+    out.u[0][w] = in.p.u[0][s];
+    out.u[1][w] = in.p.u[1][s];
+    out.u[2][w] = in.p.u[2][s];
+    if (out.id) out.id[w] = in.p.id ? in.p.id[s] : 0;
   }
 }
 
@@ -700,19 +906,17 @@ __global__ void k_global_to_flat(int ndim, Layout L, Tiles tg, PushConst C, cons
 }
 
 // charge density with linear weights (FP64 atomics) of every particle in the store
-__global__ void k_tiled_rho(Layout L, PushConst C, Tiles tg, Part32 in, const int* stay, const int* move,
-                            double* rho) {
+__global__ void k_tiled_rho(Layout L, PushConst C, Tiles tg, TileSide in, double* rho) {
   const int t = blockIdx.x;
-  const int ns = stay[t], nm = move[t];
+  const int n = in.stay[t] + in.move[t];
   const long long base = tg.base[t];
-  const int cap = tg.cap[t];
-  for (int k = threadIdx.x; k < ns + nm; k += blockDim.x) {
-    const long long s = k < ns ? base + k : base + cap - nm + (k - ns);
-    const uint32_t c = in.cell[s];
+  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    const long long s = base + k;
+    const uint32_t c = in.p.cell[s];
     int o[3];
     tile_origin(tg, dest_tile(tg, t, c), o);
     const int i = o[0] + (int)(c & 255), j = o[1] + (int)((c >> 8) & 255), kk = o[2] + (int)((c >> 16) & 255);
-    const double e0 = in.o[0][s], e1 = in.o[1][s], e2 = tg.ndim == 3 ? (double)in.o[2][s] : 0.0;
+    const double e0 = in.p.o[0][s], e1 = in.p.o[1][s], e2 = tg.ndim == 3 ? (double)in.p.o[2][s] : 0.0;
     const double qv = C.q / C.dvol;
     for (int c3 = 0; c3 < (tg.ndim == 3 ? 2 : 1); ++c3)
       for (int c2 = 0; c2 < 2; ++c2)
@@ -724,17 +928,15 @@ __global__ void k_tiled_rho(Layout L, PushConst C, Tiles tg, Part32 in, const in
   }
 }
 
-__global__ void k_tiled_kinetic(PushConst C, Tiles tg, Part32 in, const int* stay, const int* move, double* ke,
-                                double* qsum) {
+__global__ void k_tiled_kinetic(PushConst C, Tiles tg, TileSide in, double* ke, double* qsum) {
   __shared__ double red[32];
   const int t = blockIdx.x;
-  const int ns = stay[t], nm = move[t];
+  const int n = in.stay[t] + in.move[t];
   const long long base = tg.base[t];
-  const int cap = tg.cap[t];
   double v = 0.0;
-  for (int k = threadIdx.x; k < ns + nm; k += blockDim.x) {
-    const long long s = k < ns ? base + k : base + cap - nm + (k - ns);
-    const double a = in.u[0][s], b = in.u[1][s], c = in.u[2][s];
+  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    const long long s = base + k;
+    const double a = in.p.u[0][s], b = in.p.u[1][s], c = in.p.u[2][s];
     v += C.q * C.rqm * (sqrt(1.0 + a * a + b * b + c * c) - 1.0);
   }
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
@@ -744,37 +946,75 @@ __global__ void k_tiled_kinetic(PushConst C, Tiles tg, Part32 in, const int* sta
     double s = 0.0;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
     atomicAdd(ke, s);
-    atomicAdd(qsum, C.q * (double)(ns + nm));
+    atomicAdd(qsum, C.q * (double)n);
   }
 }
 
-template <int NDIM, int TX, int TY, int TZ>
-void launch_push(const CUtensorMap* fmap, const CUtensorMap* jmap, const TileArgs& A, int ntiles, cudaStream_t s) {
+template <int NDIM, int TX, int TY, int TZ, int MINB>
+int occupancy() {
   using G = Geo<NDIM, TX, TY, TZ>;
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaFuncSetAttribute(k_tile_push<NDIM, TX, TY, TZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM);
-    attr_set = true;
+  static int occ = -1;
+  if (occ < 0) {
+    cudaFuncSetAttribute(k_tile_push<NDIM, TX, TY, TZ, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM);
+    int o = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_tile_push<NDIM, TX, TY, TZ, MINB>, kThreads, G::SMEM) !=
+            cudaSuccess ||
+        o < 1)
+      o = 1;
+    occ = o;
   }
-  k_tile_push<NDIM, TX, TY, TZ><<<ntiles, kThreads, G::SMEM, s>>>(*fmap, *jmap, A);
+  return occ;
 }
+
+template <int NDIM, int TX, int TY, int TZ, int MINB>
+void launch_push(const CUtensorMap* fmap, const CUtensorMap* jmap, const TileArgs& A, int grid, cudaStream_t s) {
+  using G = Geo<NDIM, TX, TY, TZ>;
+  occupancy<NDIM, TX, TY, TZ, MINB>();
+  k_tile_push<NDIM, TX, TY, TZ, MINB><<<grid, kThreads, G::SMEM, s>>>(*fmap, *jmap, A);
+}
+
+// Register budget of the tile kernel: 3 CTAs per SM (80 registers, a few
+// spills in 3D) or 2 (no spills).  Chosen per simulation.
+int g_minb = 3;
+
+#define PICGB_TILE_SHAPES(X) \
+  X(3, 8, 8, 8)              \
+  X(3, 16, 8, 4)             \
+  X(2, 32, 16, 1)            \
+  X(2, 16, 16, 1)            \
+  X(2, 8, 8, 1)
 
 }  // namespace
 
 int tiled_push_smem_bytes(int ndim, const int T[3]) {
-  if (ndim == 3 && T[0] == 8 && T[1] == 8 && T[2] == 8) return Geo<3, 8, 8, 8>::SMEM;
-  if (ndim == 3 && T[0] == 16 && T[1] == 8 && T[2] == 4) return Geo<3, 16, 8, 4>::SMEM;
-  if (ndim == 3 && T[0] == 4 && T[1] == 4 && T[2] == 4) return Geo<3, 4, 4, 4>::SMEM;
-  if (ndim == 2 && T[0] == 32 && T[1] == 16) return Geo<2, 32, 16, 1>::SMEM;
-  if (ndim == 2 && T[0] == 16 && T[1] == 16) return Geo<2, 16, 16, 1>::SMEM;
-  if (ndim == 2 && T[0] == 8 && T[1] == 8) return Geo<2, 8, 8, 1>::SMEM;
+#define X(N, A_, B_, C_) \
+  if (ndim == N && T[0] == A_ && T[1] == B_ && (N == 2 || T[2] == C_)) return Geo<N, A_, B_, C_>::SMEM;
+  PICGB_TILE_SHAPES(X)
+#undef X
   return -1;
 }
 
-void tiled_push(const Layout& L, const PushConst& C, const Tiles& tg, const Part32& in, const int* in_stay,
-                const int* in_move, const Part32& out, int* out_stay, int* out_move, Flat32 spill,
-                int* spill_count, long long spill_cap, const CUtensorMap* fmap, const CUtensorMap* jmap,
-                int* status, cudaStream_t s) {
+void tiled_push_set_minb(int minb) { g_minb = minb == 2 ? 2 : 3; }
+
+int tiled_push_grid(int ndim, const int T[3], int ntiles) {
+  int dev = 0, sms = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  int occ = 1;
+#define X(N, A_, B_, C_)                                                  \
+  if (ndim == N && T[0] == A_ && T[1] == B_ && (N == 2 || T[2] == C_))    \
+    occ = g_minb == 2 ? occupancy<N, A_, B_, C_, 2>() : occupancy<N, A_, B_, C_, 3>();
+  PICGB_TILE_SHAPES(X)
+#undef X
+  const int g = sms * occ;
+  return g < ntiles ? g : ntiles;
+}
+
+size_t tiled_scratch_bytes(int grid, long long max_cap) { return (size_t)grid * 8 * (size_t)max_cap * 4; }
+
+void tiled_push(const Layout& L, const PushConst& C, const Tiles& tg, const TileSide& in, const TileSide& out,
+                Flat32 spill, int* spill_count, long long spill_cap, void* scratch, long long scratch_cap, int grid,
+                int* work, const CUtensorMap* fmap, const CUtensorMap* jmap, int* status, cudaStream_t s) {
   (void)L;
   TileArgs A;
   for (int d = 0; d < 3; ++d) A.nt[d] = tg.nt[d];
@@ -782,14 +1022,13 @@ void tiled_push(const Layout& L, const PushConst& C, const Tiles& tg, const Part
   A.base = tg.base;
   A.cap = tg.cap;
   A.in = in;
-  A.in_stay = in_stay;
-  A.in_move = in_move;
   A.out = out;
-  A.out_stay = out_stay;
-  A.out_move = out_move;
   A.spill = spill;
   A.spill_count = spill_count;
   A.spill_cap = spill_cap;
+  A.scratch = reinterpret_cast<float*>(scratch);
+  A.scap = scratch_cap;
+  A.work = work;
   A.qmdt2 = (float)(C.dt / (2.0 * C.rqm));
   for (int d = 0; d < 3; ++d) {
     A.dt_dx[d] = (float)(C.dt / C.dx[d]);
@@ -799,24 +1038,22 @@ void tiled_push(const Layout& L, const PushConst& C, const Tiles& tg, const Part
   }
   A.j3f = (float)(C.q / C.dvol);
   A.status = status;
+  cudaMemsetAsync(work, 0, sizeof(int), s);
   const int* T = tg.T;
-  if (tg.ndim == 3 && T[0] == 8 && T[1] == 8 && T[2] == 8)
-    launch_push<3, 8, 8, 8>(fmap, jmap, A, tg.ntiles, s);
-  else if (tg.ndim == 3 && T[0] == 16 && T[1] == 8 && T[2] == 4)
-    launch_push<3, 16, 8, 4>(fmap, jmap, A, tg.ntiles, s);
-  else if (tg.ndim == 3 && T[0] == 4 && T[1] == 4 && T[2] == 4)
-    launch_push<3, 4, 4, 4>(fmap, jmap, A, tg.ntiles, s);
-  else if (tg.ndim == 2 && T[0] == 32 && T[1] == 16)
-    launch_push<2, 32, 16, 1>(fmap, jmap, A, tg.ntiles, s);
-  else if (tg.ndim == 2 && T[0] == 16 && T[1] == 16)
-    launch_push<2, 16, 16, 1>(fmap, jmap, A, tg.ntiles, s);
-  else if (tg.ndim == 2 && T[0] == 8 && T[1] == 8)
-    launch_push<2, 8, 8, 1>(fmap, jmap, A, tg.ntiles, s);
+#define X(N, A_, B_, C_)                                                    \
+  if (tg.ndim == N && T[0] == A_ && T[1] == B_ && (N == 2 || T[2] == C_)) { \
+    if (g_minb == 2)                                                        \
+      launch_push<N, A_, B_, C_, 2>(fmap, jmap, A, grid, s);                \
+    else                                                                    \
+      launch_push<N, A_, B_, C_, 3>(fmap, jmap, A, grid, s);                \
+    return;                                                                 \
+  }
+  PICGB_TILE_SHAPES(X)
+#undef X
 }
 
-void tiled_flatten(const Tiles& tg, const Part32& in, const int* stay, const int* move, const long long* out_off,
-                   Flat32 out, cudaStream_t s) {
-  k_flatten<<<tg.ntiles, 256, 0, s>>>(tg, in, stay, move, out_off, out);
+void tiled_flatten(const Tiles& tg, const TileSide& in, const long long* out_off, Flat32 out, cudaStream_t s) {
+  k_flatten<<<tg.ntiles, 256, 0, s>>>(tg, in, out_off, out);
 }
 
 void flat_count(const Flat32& f, long long n, int ntiles, int* counts, cudaStream_t s) {
@@ -842,14 +1079,12 @@ void global_to_flat(int ndim, const Layout& L, const Tiles& tg, const PushConst&
                                                                 id, n, out, status);
 }
 
-void tiled_rho(const Layout& L, const PushConst& C, const Tiles& tg, const Part32& in, const int* stay,
-               const int* move, double* rho, cudaStream_t s) {
-  k_tiled_rho<<<tg.ntiles, 256, 0, s>>>(L, C, tg, in, stay, move, rho);
+void tiled_rho(const Layout& L, const PushConst& C, const Tiles& tg, const TileSide& in, double* rho, cudaStream_t s) {
+  k_tiled_rho<<<tg.ntiles, 256, 0, s>>>(L, C, tg, in, rho);
 }
 
-void tiled_kinetic(const PushConst& C, const Tiles& tg, const Part32& in, const int* stay, const int* move,
-                   Diag64* acc, cudaStream_t s) {
-  k_tiled_kinetic<<<tg.ntiles, 256, 0, s>>>(C, tg, in, stay, move, &acc->kinetic_energy, &acc->total_charge);
+void tiled_kinetic(const PushConst& C, const Tiles& tg, const TileSide& in, Diag64* acc, cudaStream_t s) {
+  k_tiled_kinetic<<<tg.ntiles, 256, 0, s>>>(C, tg, in, &acc->kinetic_energy, &acc->total_charge);
 }
 
 }  // namespace picgb

@@ -77,23 +77,34 @@ struct Tiles {
 };
 constexpr int DIR_STAY = 13;
 
-void tiled_push(const Layout& L, const PushConst& C, const Tiles& tg, const Part32& in, const int* in_stay,
-                const int* in_move, const Part32& out, int* out_stay, int* out_move, Flat32 spill,
-                int* spill_count, long long spill_cap, const CUtensorMap* fmap, const CUtensorMap* jmap,
-                int* status, cudaStream_t s);
+// One side of the ping-pong particle store.  Region of tile t: slots
+// [base[t], base[t] + cap[t]); stayers (sorted by cell) first, then the movers,
+// grouped by the direction they left in; group d of tile t starts at
+// base[t] + mstart[27 t + d] and holds mcount[27 t + d] particles.
+struct TileSide {
+  Part32 p;
+  int* stay;
+  int* move;
+  int* mstart;
+  int* mcount;
+};
+
+void tiled_push(const Layout& L, const PushConst& C, const Tiles& tg, const TileSide& in, const TileSide& out,
+                Flat32 spill, int* spill_count, long long spill_cap, void* scratch, long long scratch_cap, int grid,
+                int* work, const CUtensorMap* fmap, const CUtensorMap* jmap, int* status, cudaStream_t s);
 int tiled_push_smem_bytes(int ndim, const int T[3]);
-void tiled_flatten(const Tiles& tg, const Part32& in, const int* stay, const int* move, const long long* out_off,
-                   Flat32 out, cudaStream_t s);
+int tiled_push_grid(int ndim, const int T[3], int ntiles);  // persistent CTAs
+void tiled_push_set_minb(int minb);  // CTAs per SM the tile kernel is built for (2 or 3)
+size_t tiled_scratch_bytes(int grid, long long max_cap);
+void tiled_flatten(const Tiles& tg, const TileSide& in, const long long* out_off, Flat32 out, cudaStream_t s);
 void flat_count(const Flat32& f, long long n, int ntiles, int* counts, cudaStream_t s);
 void flat_scatter(const Flat32& f, long long n, const Tiles& tg, int* cursor, Part32 out, cudaStream_t s);
 void flat_to_global(int ndim, const Tiles& tg, const PushConst& C, const Flat32& f, long long n, double* x, double* u,
                     cudaStream_t s);
 void global_to_flat(int ndim, const Layout& L, const Tiles& tg, const PushConst& C, double* const x[3],
                     double* const u[3], const int* id, long long n, Flat32 out, int* status, cudaStream_t s);
-void tiled_rho(const Layout& L, const PushConst& C, const Tiles& tg, const Part32& in, const int* stay,
-               const int* move, double* rho, cudaStream_t s);
-void tiled_kinetic(const PushConst& C, const Tiles& tg, const Part32& in, const int* stay, const int* move,
-                   Diag64* acc, cudaStream_t s);
+void tiled_rho(const Layout& L, const PushConst& C, const Tiles& tg, const TileSide& in, double* rho, cudaStream_t s);
+void tiled_kinetic(const PushConst& C, const Tiles& tg, const TileSide& in, Diag64* acc, cudaStream_t s);
 
 // ----------------------------------------------------------------- loading
 // Lattice loader (nl_species num_par_x, vth, vfl) on the device, FP64 output.

@@ -264,7 +264,17 @@ def test_error_paths_on_gpu():
     with pytest.raises(pg.PicError) as e:
         pg.Simulation(g, [sp], precision="fp64", np_max=100)
     assert e.value.code == -5
+    g2 = workload.Grid(ndim=3, nx=(16, 8, 8), dx=dx, dt=workload.courant_dt(dx, 3))
     x = np.full((4, 3), np.nan)
+    for prec in ("fp32", "fp64"):
+        with pytest.raises(pg.PicError) as e:
+            pg.Simulation(g2, [sp], precision=prec, tile=(8, 8, 8), explicit=[(x, np.zeros((4, 3)), -1.0)])
+        assert e.value.code == -1
+    x = np.full((4, 3), 0.05)
+    x[2, 1] = 0.8  # on the upper face of the box: outside [xmin, xmax)
     with pytest.raises(pg.PicError) as e:
-        pg.Simulation(g, [sp], precision="fp32", tile=(4, 4, 4), explicit=[(x, np.zeros((4, 3)), -1.0)])
-    assert e.value.code in (-1, -6)
+        pg.Simulation(g2, [sp], precision="fp64", explicit=[(x, np.zeros((4, 3)), -1.0)])
+    assert e.value.code == -1
+    with pytest.raises(pg.PicError) as e:
+        pg.Simulation(g2, [sp], precision="fp32", tile=(4, 4, 4))
+    assert e.value.code == -8

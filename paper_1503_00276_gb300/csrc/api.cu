@@ -750,13 +750,14 @@ void field_step(pic_sim* S) {
   {
     Span sp(S, 2);
     double dx[3] = {S->g.dx[0], S->g.dx[1], S->ndim == 3 ? S->g.dx[2] : 1.0};
+    // the sweeps wrap their neighbours periodically; the guard cells (read by
+    // the particle kernels) are refreshed once at the end
     yee_b_half<T>(L, e, b, S->g.dt, dx, S->s);
-    fill_guards<T>(L, b, 3, S->s);
     yee_e<T>(L, e, b, j, S->g.dt, dx, S->s);
-    fill_guards<T>(L, e, 3, S->s);
     yee_b_half<T>(L, e, b, S->g.dt, dx, S->s);
-    fill_guards<T>(L, b, 3, S->s);
-    S->nlaunch += 6;
+    T* eb[6] = {e[0], e[1], e[2], b[0], b[1], b[2]};
+    fill_guards<T>(L, eb, 6, S->s);
+    S->nlaunch += 4;
   }
 }
 

@@ -18,7 +18,6 @@ __device__ inline int wrapi(int i, int n) {
 }
 
 inline dim3 interior_grid(const Layout& L) { return dim3((L.nx + 31) / 32, (L.ny + 7) / 8, L.nz); }
-inline dim3 padded_grid(const Layout& L) { return dim3((L.NX + 31) / 32, (L.NY + 7) / 8, L.NZ); }
 const dim3 kBlock(32, 8, 1);
 
 template <typename T>
@@ -31,16 +30,63 @@ struct Ptr6 {
 };
 
 // ---------------------------------------------------------------- guards
+// Flat enumeration of the guard cells only: the z slabs (all y, x), then the
+// y slabs of interior z (all x), then the x slabs of interior z and y.
+__device__ inline bool guard_xyz(const Layout& L, long long g, int& X, int& Y, int& Z) {
+  const long long nzs = (long long)(L.NZ - L.nz) * L.NY * L.NX;
+  if (g < nzs) {
+    const long long plane = (long long)L.NY * L.NX;
+    int zi = (int)(g / plane);
+    const long long r = g - (long long)zi * plane;
+    Z = zi < L.gz ? zi : zi + L.nz;
+    Y = (int)(r / L.NX);
+    X = (int)(r - (long long)Y * L.NX);
+    return true;
+  }
+  g -= nzs;
+  const long long nys = (long long)L.nz * (L.NY - L.ny) * L.NX;
+  if (g < nys) {
+    const long long slab = (long long)(L.NY - L.ny) * L.NX;
+    Z = (int)(g / slab) + L.gz;
+    const long long r = g - (long long)(Z - L.gz) * slab;
+    int yi = (int)(r / L.NX);
+    X = (int)(r - (long long)yi * L.NX);
+    Y = yi < L.gy ? yi : yi + L.ny;
+    return true;
+  }
+  g -= nys;
+  const int gw = L.NX - L.nx;
+  const long long nxs = (long long)L.nz * L.ny * gw;
+  if (g < nxs) {
+    const long long row = gw;
+    const long long zy = g / row;
+    int xi = (int)(g - zy * row);
+    Z = (int)(zy / L.ny) + L.gz;
+    Y = (int)(zy - (long long)(Z - L.gz) * L.ny) + L.gy;
+    X = xi < L.gx ? xi : xi + L.nx;
+    return true;
+  }
+  return false;
+}
+
+inline long long guard_count(const Layout& L) {
+  return (long long)(L.NZ - L.nz) * L.NY * L.NX + (long long)L.nz * (L.NY - L.ny) * L.NX +
+         (long long)L.nz * L.ny * (L.NX - L.nx);
+}
+
+template <typename T, int NC>
+struct PtrN {
+  T* c[NC];
+};
+
 template <typename T>
-__global__ void k_fill_guards(Layout L, Ptr3<T> P, int ncomp) {
-  int X = blockIdx.x * blockDim.x + threadIdx.x;
-  int Y = blockIdx.y * blockDim.y + threadIdx.y;
-  int Z = blockIdx.z;
-  if (X >= L.NX || Y >= L.NY) return;
-  int i = X - L.gx, j = Y - L.gy, k = Z - L.gz;
-  if (i >= 0 && i < L.nx && j >= 0 && j < L.ny && k >= 0 && k < L.nz) return;
-  long long dst = ((long long)Z * L.NY + Y) * L.NX + X;
-  long long src = L.idx(wrapi(i, L.nx), wrapi(j, L.ny), wrapi(k, L.nz));
+__global__ void k_fill_guards(Layout L, PtrN<T, 6> P, int ncomp) {
+  const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  int X, Y, Z;
+  if (!guard_xyz(L, g, X, Y, Z)) return;
+  const int i = X - L.gx, j = Y - L.gy, k = Z - L.gz;
+  const long long dst = ((long long)Z * L.NY + Y) * L.NX + X;
+  const long long src = L.idx(wrapi(i, L.nx), wrapi(j, L.ny), wrapi(k, L.nz));
   for (int c = 0; c < ncomp; ++c) P.c[c][dst] = P.c[c][src];
 }
 
@@ -49,19 +95,17 @@ __global__ void k_fill_guards(Layout L, Ptr3<T> P, int ncomp) {
 // with its own opposite boundary").  Several guard cells can map to one
 // interior cell (edges, corners), hence the atomics.
 template <typename T>
-__global__ void k_fold_guards(Layout L, Ptr3<T> P, int ncomp) {
-  int X = blockIdx.x * blockDim.x + threadIdx.x;
-  int Y = blockIdx.y * blockDim.y + threadIdx.y;
-  int Z = blockIdx.z;
-  if (X >= L.NX || Y >= L.NY) return;
-  int i = X - L.gx, j = Y - L.gy, k = Z - L.gz;
-  if (i >= 0 && i < L.nx && j >= 0 && j < L.ny && k >= 0 && k < L.nz) return;
-  long long g = ((long long)Z * L.NY + Y) * L.NX + X;
-  long long dst = L.idx(wrapi(i, L.nx), wrapi(j, L.ny), wrapi(k, L.nz));
+__global__ void k_fold_guards(Layout L, PtrN<T, 6> P, int ncomp) {
+  const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  int X, Y, Z;
+  if (!guard_xyz(L, g, X, Y, Z)) return;
+  const int i = X - L.gx, j = Y - L.gy, k = Z - L.gz;
+  const long long src = ((long long)Z * L.NY + Y) * L.NX + X;
+  const long long dst = L.idx(wrapi(i, L.nx), wrapi(j, L.ny), wrapi(k, L.nz));
   for (int c = 0; c < ncomp; ++c) {
-    T v = P.c[c][g];
+    const T v = P.c[c][src];
     if (v != T(0)) atomicAdd(&P.c[c][dst], v);
-    P.c[c][g] = T(0);
+    P.c[c][src] = T(0);
   }
 }
 
@@ -90,19 +134,22 @@ __global__ void k_yee_b_half(Layout L, Ptr3<T> E, Ptr3<T> B, T h, T dx1, T dx2, 
   int j = blockIdx.y * blockDim.y + threadIdx.y;
   int k = blockIdx.z;
   if (i >= L.nx || j >= L.ny) return;
-  const long long sx = 1, sy = L.NX, sz = (long long)L.NX * L.NY;
-  long long c = L.idx(i, j, k);
+  // forward neighbours, wrapped periodically (no guard cells read)
+  const long long c = L.idx(i, j, k);
+  const long long cx = L.idx(i + 1 == L.nx ? 0 : i + 1, j, k);
+  const long long cy = L.idx(i, j + 1 == L.ny ? 0 : j + 1, k);
   const T* E1 = E.c[0];
   const T* E2 = E.c[1];
   const T* E3 = E.c[2];
-  T dE3d2 = (E3[c + sy] - E3[c]) / dx2;
-  T dE3d1 = (E3[c + sx] - E3[c]) / dx1;
-  T dE2d1 = (E2[c + sx] - E2[c]) / dx1;
-  T dE1d2 = (E1[c + sy] - E1[c]) / dx2;
+  T dE3d2 = (E3[cy] - E3[c]) / dx2;
+  T dE3d1 = (E3[cx] - E3[c]) / dx1;
+  T dE2d1 = (E2[cx] - E2[c]) / dx1;
+  T dE1d2 = (E1[cy] - E1[c]) / dx2;
   T dE2d3 = T(0), dE1d3 = T(0);
   if (L.ndim == 3) {
-    dE2d3 = (E2[c + sz] - E2[c]) / dx3;
-    dE1d3 = (E1[c + sz] - E1[c]) / dx3;
+    const long long cz = L.idx(i, j, k + 1 == L.nz ? 0 : k + 1);
+    dE2d3 = (E2[cz] - E2[c]) / dx3;
+    dE1d3 = (E1[cz] - E1[c]) / dx3;
   }
   B.c[0][c] = B.c[0][c] - h * (dE3d2 - dE2d3);
   B.c[1][c] = B.c[1][c] - h * (dE1d3 - dE3d1);
@@ -117,19 +164,22 @@ __global__ void k_yee_e(Layout L, Ptr3<T> E, Ptr3<T> B, Ptr3<T> J, T dt, T dx1, 
   int j = blockIdx.y * blockDim.y + threadIdx.y;
   int k = blockIdx.z;
   if (i >= L.nx || j >= L.ny) return;
-  const long long sx = 1, sy = L.NX, sz = (long long)L.NX * L.NY;
-  long long c = L.idx(i, j, k);
+  // backward neighbours, wrapped periodically (no guard cells read)
+  const long long c = L.idx(i, j, k);
+  const long long cx = L.idx(i == 0 ? L.nx - 1 : i - 1, j, k);
+  const long long cy = L.idx(i, j == 0 ? L.ny - 1 : j - 1, k);
   const T* B1 = B.c[0];
   const T* B2 = B.c[1];
   const T* B3 = B.c[2];
-  T dB3d2 = (B3[c] - B3[c - sy]) / dx2;
-  T dB3d1 = (B3[c] - B3[c - sx]) / dx1;
-  T dB2d1 = (B2[c] - B2[c - sx]) / dx1;
-  T dB1d2 = (B1[c] - B1[c - sy]) / dx2;
+  T dB3d2 = (B3[c] - B3[cy]) / dx2;
+  T dB3d1 = (B3[c] - B3[cx]) / dx1;
+  T dB2d1 = (B2[c] - B2[cx]) / dx1;
+  T dB1d2 = (B1[c] - B1[cy]) / dx2;
   T dB2d3 = T(0), dB1d3 = T(0);
   if (L.ndim == 3) {
-    dB2d3 = (B2[c] - B2[c - sz]) / dx3;
-    dB1d3 = (B1[c] - B1[c - sz]) / dx3;
+    const long long cz = L.idx(i, j, k == 0 ? L.nz - 1 : k - 1);
+    dB2d3 = (B2[c] - B2[cz]) / dx3;
+    dB1d3 = (B1[c] - B1[cz]) / dx3;
   }
   E.c[0][c] = E.c[0][c] + dt * (dB3d2 - dB2d3) - dt * J.c[0][c];
   E.c[1][c] = E.c[1][c] + dt * (dB1d3 - dB3d1) - dt * J.c[1][c];
@@ -259,21 +309,25 @@ __global__ void k_gauss_x1(Layout L, const double* __restrict__ rho, double rho_
 // ------------------------------------------------------------------ launchers
 template <typename T>
 void fill_guards(const Layout& L, T* const* comps, int ncomp, cudaStream_t s) {
-  for (int c0 = 0; c0 < ncomp; c0 += 3) {
-    Ptr3<T> P{};
-    int m = ncomp - c0 < 3 ? ncomp - c0 : 3;
+  const long long n = guard_count(L);
+  if (n == 0) return;
+  for (int c0 = 0; c0 < ncomp; c0 += 6) {
+    PtrN<T, 6> P{};
+    const int m = ncomp - c0 < 6 ? ncomp - c0 : 6;
     for (int c = 0; c < m; ++c) P.c[c] = comps[c0 + c];
-    k_fill_guards<T><<<padded_grid(L), kBlock, 0, s>>>(L, P, m);
+    k_fill_guards<T><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(L, P, m);
   }
 }
 
 template <typename T>
 void fold_guards(const Layout& L, T* const* comps, int ncomp, cudaStream_t s) {
-  for (int c0 = 0; c0 < ncomp; c0 += 3) {
-    Ptr3<T> P{};
-    int m = ncomp - c0 < 3 ? ncomp - c0 : 3;
+  const long long n = guard_count(L);
+  if (n == 0) return;
+  for (int c0 = 0; c0 < ncomp; c0 += 6) {
+    PtrN<T, 6> P{};
+    const int m = ncomp - c0 < 6 ? ncomp - c0 : 6;
     for (int c = 0; c < m; ++c) P.c[c] = comps[c0 + c];
-    k_fold_guards<T><<<padded_grid(L), kBlock, 0, s>>>(L, P, m);
+    k_fold_guards<T><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(L, P, m);
   }
 }
 

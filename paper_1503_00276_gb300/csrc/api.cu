@@ -49,9 +49,10 @@ __global__ void k_check_box(int ndim, PushConst C, const double* x0, const doubl
   }
 }
 
-__global__ void k_add_i32(const int* a, const int* b, int* c, int n) {
+// particles held by each tile: its stayers plus its arrivals (at most res)
+__global__ void k_tile_totals(const int* stay, const int* inc, const int* res, int* tot, int n) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k < n) c[k] = a[k] + b[k];
+  if (k < n) tot[k] = stay[k] + (inc[k] < res[k] ? inc[k] : res[k]);
 }
 
 struct StatusWord {
@@ -111,9 +112,6 @@ struct SpeciesState {
   long long slots = 0;
   Flat32 spill{};
   long long spill_cap = 0;
-  void* scratch = nullptr;  // per-CTA staging of the tile kernel (L2 resident)
-  long long scap = 0;       // particles per CTA in `scratch`
-  size_t scratch_bytes = 0;
   int grid = 0;             // persistent CTAs of the tile kernel
   int* work = nullptr;      // its dynamic tile counter
 };
@@ -268,26 +266,26 @@ pic_status make_maps(pic_sim* S) {
   if (S->ndim == 3) {
     cuuint64_t gdim[4] = {(cuuint64_t)L.NX, (cuuint64_t)L.NY, (cuuint64_t)L.NZ, 6};
     cuuint64_t gstr[3] = {(cuuint64_t)L.NX * 4, (cuuint64_t)L.NX * L.NY * 4, ps};
-    cuuint32_t box[4] = {(cuuint32_t)S->T[0] + 8, (cuuint32_t)S->T[1] + 2, (cuuint32_t)S->T[2] + 2, 6};
+    cuuint32_t box[4] = {(cuuint32_t)S->T[0] + 4, (cuuint32_t)S->T[1] + 2, (cuuint32_t)S->T[2] + 2, 6};
     cuuint32_t es[4] = {1, 1, 1, 1};
     r1 = enc(&S->fmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, S->fld, gdim, gstr, box, es,
              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     cuuint64_t jdim[4] = {(cuuint64_t)L.NX, (cuuint64_t)L.NY, (cuuint64_t)L.NZ, 3};
-    cuuint32_t jbox[4] = {(cuuint32_t)S->T[0] + 8, (cuuint32_t)S->T[1] + 3, (cuuint32_t)S->T[2] + 3, 3};
+    cuuint32_t jbox[4] = {(cuuint32_t)S->T[0] + 4, (cuuint32_t)S->T[1] + 3, (cuuint32_t)S->T[2] + 3, 3};
     r2 = enc(&S->jmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, S->cur, jdim, gstr, jbox, es,
              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   } else {
     cuuint64_t gdim[3] = {(cuuint64_t)L.NX, (cuuint64_t)L.NY, 6};
     cuuint64_t gstr[2] = {(cuuint64_t)L.NX * 4, ps};
-    cuuint32_t box[3] = {(cuuint32_t)S->T[0] + 8, (cuuint32_t)S->T[1] + 2, 6};
+    cuuint32_t box[3] = {(cuuint32_t)S->T[0] + 4, (cuuint32_t)S->T[1] + 2, 6};
     cuuint32_t es[3] = {1, 1, 1};
     r1 = enc(&S->fmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, S->fld, gdim, gstr, box, es,
              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     cuuint64_t jdim[3] = {(cuuint64_t)L.NX, (cuuint64_t)L.NY, 3};
-    cuuint32_t jbox[3] = {(cuuint32_t)S->T[0] + 8, (cuuint32_t)S->T[1] + 3, 3};
+    cuuint32_t jbox[3] = {(cuuint32_t)S->T[0] + 4, (cuuint32_t)S->T[1] + 3, 3};
     r2 = enc(&S->jmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, S->cur, jdim, gstr, jbox, es,
              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -372,15 +370,18 @@ pic_status bin_flat(pic_sim* S, SpeciesState& sp, Flat32& flat, long long n) {
     set_error("binning: " + std::to_string(n - total) + " particles outside the grid");
     return PIC_EINVAL;
   }
-  std::vector<int> hcap(nt);
+  // region of tile t: its count plus slack for growth, of which the back
+  // part `res` receives the particles entering the tile during a step
+  std::vector<int> hcap(nt), hres(nt);
   std::vector<long long> hbase(nt);
   long long slots = 0;
   for (int t = 0; t < nt; ++t) {
-    long long c = hc[t];
-    long long extra = std::max<long long>(32, (long long)std::ceil(c * S->slack));
+    const long long c = hc[t];
+    const long long extra = std::max<long long>(64, (long long)std::ceil(c * S->slack));
     long long cap = (c + extra + 3) / 4 * 4;
     if (cap > (1ll << 30)) cap = 1ll << 30;
     hcap[t] = (int)cap;
+    hres[t] = (int)std::min<long long>(cap - c, std::max<long long>(32, extra / 2));
     hbase[t] = slots;
     slots += cap;
   }
@@ -401,24 +402,9 @@ pic_status bin_flat(pic_sim* S, SpeciesState& sp, Flat32& flat, long long n) {
     }
     sp.slots = slots;
   }
-  // staging of the tile kernel: every persistent CTA holds one tile's particles
-  long long max_cap = 4;
-  for (int t = 0; t < nt; ++t) max_cap = std::max<long long>(max_cap, hcap[t]);
-  const long long scap = (max_cap + std::max<long long>(64, max_cap / 4) + 3) / 4 * 4;
   sp.grid = tiled_push_grid(S->ndim, S->T, nt);
-  const size_t sbytes = tiled_scratch_bytes(sp.grid, scap);
-  if (sbytes > sp.scratch_bytes) {
-    S->al.put(sp.scratch);
-    sp.scratch = S->al.get(sbytes);
-    if (!sp.scratch) {
-      S->al.put(counts);
-      set_error("out of device memory (tile kernel staging)");
-      return PIC_ENOMEM;
-    }
-    sp.scratch_bytes = sbytes;
-  }
-  sp.scap = scap;
   cudaMemcpyAsync(sp.tg.cap, hcap.data(), 4 * (size_t)nt, cudaMemcpyHostToDevice, S->s);
+  cudaMemcpyAsync(sp.tg.res, hres.data(), 4 * (size_t)nt, cudaMemcpyHostToDevice, S->s);
   cudaMemcpyAsync(sp.tg.base, hbase.data(), 8 * (size_t)nt, cudaMemcpyHostToDevice, S->s);
   int* cursor = (int*)S->al.get(4 * (size_t)nt);
   if (!cursor) {
@@ -429,9 +415,7 @@ pic_status bin_flat(pic_sim* S, SpeciesState& sp, Flat32& flat, long long n) {
   cudaMemsetAsync(cursor, 0, 4 * (size_t)nt, S->s);
   flat_scatter(flat, n, sp.tg, cursor, sp.side[sp.cur].p, S->s);
   cudaMemcpyAsync(sp.side[sp.cur].stay, counts, 4 * (size_t)nt, cudaMemcpyDeviceToDevice, S->s);
-  cudaMemsetAsync(sp.side[sp.cur].move, 0, 4 * (size_t)nt, S->s);
-  cudaMemsetAsync(sp.side[sp.cur].mstart, 0, 4 * (size_t)nt * 27, S->s);
-  cudaMemsetAsync(sp.side[sp.cur].mcount, 0, 4 * (size_t)nt * 27, S->s);
+  cudaMemsetAsync(sp.side[sp.cur].inc, 0, 4 * (size_t)nt, S->s);
   cudaError_t e = cudaStreamSynchronize(S->s);
   S->al.put(cursor);
   S->al.put(counts);
@@ -454,7 +438,7 @@ pic_status flatten(pic_sim* S, SpeciesState& sp, Flat32& flat, long long& n, boo
     set_error("out of device memory (flatten)");
     return PIC_ENOMEM;
   }
-  k_add_i32<<<(nt + 255) / 256, 256, 0, S->s>>>(sp.side[sp.cur].stay, sp.side[sp.cur].move, tot, nt);
+  k_tile_totals<<<(nt + 255) / 256, 256, 0, S->s>>>(sp.side[sp.cur].stay, sp.side[sp.cur].inc, sp.tg.res, tot, nt);
   exclusive_scan_i32(tot, off, nt, scr, S->s);
   long long last_off = 0;
   int last_cnt = 0;
@@ -682,14 +666,13 @@ pic_status setup_tiles(pic_sim* S, SpeciesState& sp) {
   }
   tg.base = (long long*)S->al.get(8 * (size_t)tg.ntiles);
   tg.cap = (int*)S->al.get(4 * (size_t)tg.ntiles);
-  bool ok = tg.base && tg.cap;
+  tg.res = (int*)S->al.get(4 * (size_t)tg.ntiles);
+  bool ok = tg.base && tg.cap && tg.res;
   for (int b = 0; b < 2; ++b) {
     TileSide& sd = sp.side[b];
     sd.stay = (int*)S->al.get(4 * (size_t)tg.ntiles);
-    sd.move = (int*)S->al.get(4 * (size_t)tg.ntiles);
-    sd.mstart = (int*)S->al.get(4 * 27 * (size_t)tg.ntiles);
-    sd.mcount = (int*)S->al.get(4 * 27 * (size_t)tg.ntiles);
-    ok = ok && sd.stay && sd.move && sd.mstart && sd.mcount;
+    sd.inc = (int*)S->al.get(4 * (size_t)tg.ntiles);
+    ok = ok && sd.stay && sd.inc;
   }
   sp.work = (int*)S->al.get(sizeof(int));
   if (!ok || !sp.work) {
@@ -698,9 +681,7 @@ pic_status setup_tiles(pic_sim* S, SpeciesState& sp) {
   }
   for (int b = 0; b < 2; ++b) {
     cudaMemsetAsync(sp.side[b].stay, 0, 4 * (size_t)tg.ntiles, S->s);
-    cudaMemsetAsync(sp.side[b].move, 0, 4 * (size_t)tg.ntiles, S->s);
-    cudaMemsetAsync(sp.side[b].mstart, 0, 4 * 27 * (size_t)tg.ntiles, S->s);
-    cudaMemsetAsync(sp.side[b].mcount, 0, 4 * 27 * (size_t)tg.ntiles, S->s);
+    cudaMemsetAsync(sp.side[b].inc, 0, 4 * (size_t)tg.ntiles, S->s);
   }
   return PIC_OK;
 }
@@ -776,8 +757,8 @@ pic_status one_step(pic_sim* S, bool check_now) {
         plain_push(S->ndim, S->L, C, s.plain, f, j, &S->dstat->status, S->s);
       } else {
         const int in = s.cur, out = 1 - s.cur;
-        tiled_push(S->L, C, s.tg, s.side[in], s.side[out], s.spill, &S->dstat->spill_count, s.spill_cap, s.scratch,
-                   s.scap, s.grid, s.work, &S->fmap, &S->jmap, &S->dstat->status, S->s);
+        tiled_push(S->L, C, s.tg, s.side[in], s.side[out], s.spill, &S->dstat->spill_count, s.spill_cap, s.grid,
+                   s.work, &S->fmap, &S->jmap, &S->dstat->status, S->s);
         s.cur = out;
       }
       S->nlaunch += s.n > 0 || S->prec == PIC_FP32_CELLOFF ? 1 : 0;

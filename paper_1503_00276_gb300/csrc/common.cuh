@@ -12,11 +12,13 @@ namespace picgb {
 // ---------------------------------------------------------------------------
 // Field storage: one component = a padded [NZ][NY][NX] plane with guard cells.
 // Interior cell (i,j,k), 0 <= i < nx, lives at ((k+gz)*NY + (j+gy))*NX + (i+gx).
-// Guards: x 4 below / 4 above (so that a TMA box starting 4 cells left of a tile
-// is 16-byte aligned), y and z 1 below / 2 above (the deposit reaches one node
-// beyond the first neighbour cell).  2D: no z guards, NZ = 1.
+// Guards: x 1 below / 3 above, y and z 1 below / 2 above (the deposit reaches
+// one node beyond the first neighbour cell).  With one guard cell below, the
+// TMA box of a tile starting at cell x0 - 1 starts at padded column x0, a
+// multiple of 4 floats, as a TMA copy requires; the 3 cells above make the
+// padded row a multiple of 4 floats too.  2D: no z guards, NZ = 1.
 // ---------------------------------------------------------------------------
-constexpr int GX_LO = 4, GX_HI = 4, GY_LO = 1, GY_HI = 2;
+constexpr int GX_LO = 1, GX_HI = 3, GY_LO = 1, GY_HI = 2;
 
 struct Layout {
   int ndim;

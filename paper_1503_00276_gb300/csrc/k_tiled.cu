@@ -1,25 +1,28 @@
 // k_tiled.cu -- FP32 cell-offset form of the particle step on tiles of cells.
 //
 // Store: per tile a region of slots (structure of arrays).  At the start of a
-// step a region holds the tile's stayers sorted by cell, followed by the
-// particles that left it in the last step, grouped by the direction they left
-// in (their cell is already expressed relative to the tile they entered).
+// step a region holds, at its front, the tile's stayers in runs sorted by cell
+// and, at its back, the particles that entered the tile during the last step
+// (their cell already relative to this tile).
 //
-// k_tile_push (persistent CTAs, one tile at a time) advances, for its tile, the
-// stayers plus the neighbours' groups that point at it:
+// k_tile_push (persistent CTAs, one tile at a time) advances every particle of
+// its tile:
 //   * one TMA copy stages the E/B stencil of the tile + halo in shared memory;
 //   * gather (eq. 2d-field-weighting-e3, 3D extension), Boris push
 //     (eq. momentum-update), position update (eq. 2d-position-update) and the
 //     TRISTAN / Villasenor-Buneman deposit run in FP32 on int cell + FP32 offset;
-//   * pass 1 writes the advanced particles to a per-CTA scratch area (L2
-//     resident) and histograms their new (cell | direction) keys; pass 2
-//     scatters them into the tile's region of the other store side, stayers
-//     sorted by cell -- so the store is re-sorted every step at no DRAM cost;
 //   * the current goes to a shared-memory tile: each thread adds the first
 //     in-cell piece of consecutive same-cell particles in registers and flushes
 //     once per cell; pieces after a face crossing (a few % of particles) are
 //     queued in shared memory and deposited by full warps;
+//   * each chunk of 1024 advanced particles is counting-sorted by new cell in
+//     shared memory (keys only -- the particles stay in registers) and written
+//     to the front of the tile's region on the other store side; particles that
+//     left the tile are appended, with one global atomic each, to the back of
+//     their new tile's region there;
 //   * one TMA reduce-add flushes the shared current tile (with halo) into HBM.
+// The store is therefore re-binned by tile and re-sorted by cell every step
+// without a separate pass over HBM.
 #include "kernels.h"
 
 namespace picgb {
@@ -31,20 +34,18 @@ constexpr int kPPT = 4;                      // consecutive particles per thread
 constexpr int kChunk = kThreads * kPPT;      // 1024
 constexpr int kQCap = 320;                   // crossing queue entries
 constexpr long long kWaitLimit = 1ll << 26;  // bounded mbarrier poll
-constexpr int kDirs = 27;
 
 struct TileArgs {
   int nt[3];
   int ntiles;
   const long long* base;
   const int* cap;
+  const int* res;
   TileSide in;
   TileSide out;
   Flat32 spill;
   int* spill_count;
   long long spill_cap;
-  float* scratch;       // [grid][8][scap]
-  long long scap;
   int* work;            // dynamic tile counter
   float qmdt2;          // (q/m) dt/2 = dt / (2 rqm)
   float dt_dx[3];       // dt / dx_d
@@ -54,12 +55,15 @@ struct TileArgs {
   int* status;
 };
 
+// Shared-memory tiles: fields and current cover local cells [-1, T+3) in x
+// (TMA boxes start 16-byte aligned one cell left of the tile), fields
+// [-1, T+1) and current [-1, T+2) in y and z.
 template <int NDIM, int TX, int TY, int TZ>
 struct Geo {
   static constexpr int NC = TX * TY * TZ;
-  static constexpr int NK = NC + kDirs;
-  static constexpr int FX = TX + 8, FY = TY + 2, FZ = NDIM == 3 ? TZ + 2 : 1;
-  static constexpr int JX = TX + 8, JY = TY + 3, JZ = NDIM == 3 ? TZ + 3 : 1;
+  static constexpr int NK = NC + 1;  // keys: new cell of a stayer, or NC = left the tile
+  static constexpr int FX = TX + 4, FY = TY + 2, FZ = NDIM == 3 ? TZ + 2 : 1;
+  static constexpr int JX = TX + 4, JY = TY + 3, JZ = NDIM == 3 ? TZ + 3 : 1;
   static constexpr int FPL = FX * FY * FZ;
   static constexpr int JPL = JX * JY * JZ;
   static constexpr int FBYTES = 6 * FPL * 4;
@@ -68,10 +72,9 @@ struct Geo {
   static constexpr int FOFF = 0;
   static constexpr int JOFF = ((FBYTES + 127) / 128) * 128;
   static constexpr int HOFF = JOFF + ((JBYTES + 127) / 128) * 128;   // hist[NK]
-  static constexpr int COFF = HOFF + ((NK * 4 + 15) / 16) * 16;      // cursor[NK]
-  static constexpr int QOFF = COFF + ((NK * 4 + 15) / 16) * 16;      // queue
+  static constexpr int QOFF = HOFF + ((NK * 4 + 15) / 16) * 16;      // queue
   static constexpr int MOFF = QOFF + ((kQCap * QW * 4 + 15) / 16) * 16;
-  static constexpr int SMEM = MOFF + 512;
+  static constexpr int SMEM = MOFF + 256;
 };
 
 struct P {
@@ -87,10 +90,10 @@ __device__ inline float lerp(float a, float b, float w) { return fmaf(w, b - a, 
 template <int NDIM, int FX, int FY>
 __device__ inline float interp(const float* F, int ix, int iy, int iz, float wx, float wy, float wz) {
   if (NDIM == 2) {
-    const float* r = F + (iy + 1) * FX + (ix + 4);
+    const float* r = F + (iy + 1) * FX + (ix + 1);
     return lerp(lerp(r[0], r[1], wx), lerp(r[FX], r[FX + 1], wx), wy);
   } else {
-    const float* r = F + ((iz + 1) * FY + (iy + 1)) * FX + (ix + 4);
+    const float* r = F + ((iz + 1) * FY + (iy + 1)) * FX + (ix + 1);
     constexpr int PL = FX * FY;
     const float a0 = lerp(r[0], r[1], wx);
     const float a1 = lerp(r[FX], r[FX + 1], wx);
@@ -149,7 +152,7 @@ __device__ inline void seg_weights(const TileArgs& A, float ax, float ay, float 
 template <int NDIM, int JX, int JY, int JPL>
 __device__ inline void flush_cell(float* J, int cx, int cy, int cz, const float w[12]) {
   if (NDIM == 2) {
-    const int c = (cy + 1) * JX + (cx + 4);
+    const int c = (cy + 1) * JX + (cx + 1);
     atomicAdd(&J[c], w[0]);
     atomicAdd(&J[c + JX], w[1]);
     atomicAdd(&J[JPL + c], w[2]);
@@ -160,7 +163,7 @@ __device__ inline void flush_cell(float* J, int cx, int cy, int cz, const float 
     atomicAdd(&J[2 * JPL + c + JX + 1], w[7]);
   } else {
     constexpr int SY = JX, SZ = JX * JY;
-    const int c = (cz + 1) * SZ + (cy + 1) * SY + (cx + 4);
+    const int c = (cz + 1) * SZ + (cy + 1) * SY + (cx + 1);
     atomicAdd(&J[c], w[0]);
     atomicAdd(&J[c + SY], w[1]);
     atomicAdd(&J[c + SZ], w[2]);
@@ -313,7 +316,7 @@ __device__ inline int push_one(const float* F, float* J, const TileArgs& A, P& p
   if (!(isfinite(bx) && isfinite(by) && isfinite(bz) && isfinite(ux) && isfinite(uy) && isfinite(uz))) {
     atomicOr(A.status, ST_NONFINITE);
     p.cell = cellp | ((uint32_t)DIR_STAY << 24);
-    return lx + TX * (ly + TY * lz);
+    return lx + TX * (ly + TY * lz);  // kept in place, not advanced
   }
   const float v3 = uz * ig2;
   // first in-cell piece into the accumulator; later pieces to the queue
@@ -395,7 +398,7 @@ __device__ inline int push_one(const float* F, float* J, const TileArgs& A, P& p
   p.u0 = ux;
   p.u1 = uy;
   p.u2 = uz;
-  return dir == DIR_STAY ? gx + TX * (gy + TY * gz) : G::NC + dir;
+  return dir == DIR_STAY ? gx + TX * (gy + TY * gz) : G::NC;
 }
 
 // Deposit the queued crossing pieces (all but the first of each path).
@@ -420,19 +423,140 @@ __device__ inline void drain_queue(float* J, const TileArgs& A, const float* Q, 
   }
 }
 
-__device__ inline float* sfield(const TileArgs& A, int f) {
-  return A.scratch + ((size_t)blockIdx.x * 8 + f) * (size_t)A.scap;
+
+__device__ inline void spill_put(const TileArgs& A, int tile, const P& q) {
+  atomicOr(A.status, ST_SPILL);
+  const int k = atomicAdd(A.spill_count, 1);
+  if (k >= A.spill_cap) {
+    atomicOr(A.status, ST_SPILL_LOST);
+    return;
+  }
+  A.spill.tile[k] = tile;
+  A.spill.cell[k] = (q.cell & 0x00FFFFFFu) | ((uint32_t)DIR_STAY << 24);
+  A.spill.o[0][k] = q.o0;
+  A.spill.o[1][k] = q.o1;
+  A.spill.o[2][k] = q.o2;
+  A.spill.u[0][k] = q.u0;
+  A.spill.u[1][k] = q.u1;
+  A.spill.u[2][k] = q.u2;
+  if (A.spill.id) A.spill.id[k] = q.id;
 }
 
-__device__ inline void scratch_put(const TileArgs& A, long long i, const P& p) {
-  sfield(A, 0)[i] = __uint_as_float(p.cell);
-  sfield(A, 1)[i] = p.o0;
-  sfield(A, 2)[i] = p.o1;
-  sfield(A, 3)[i] = p.o2;
-  sfield(A, 4)[i] = p.u0;
-  sfield(A, 5)[i] = p.u1;
-  sfield(A, 6)[i] = p.u2;
-  sfield(A, 7)[i] = __int_as_float(p.id);
+template <int NDIM>
+__device__ inline void store_particle(const Part32& o, long long s, const P& q) {
+  o.cell[s] = q.cell;
+  o.o[0][s] = q.o0;
+  o.o[1][s] = q.o1;
+  if (NDIM == 3) o.o[2][s] = q.o2;
+  o.u[0][s] = q.u0;
+  o.u[1][s] = q.u1;
+  o.u[2][s] = q.u2;
+  if (o.id) o.id[s] = q.id;
+}
+
+// Counting sort of one chunk of advanced particles (still in registers) by key
+// and write-out: stayers to the front of this tile's output region in cell
+// order, leavers to the back of their new tile's output region.
+template <int NDIM, int TX, int TY, int TZ>
+__device__ inline void sort_and_store(const TileArgs& A, int t, int tix, int tiy, int tiz, long long base, int room,
+                                      P (&pp)[kPPT], int (&key)[kPPT], int nvalid, int& ws, int* hist, int* misc) {
+  using G = Geo<NDIM, TX, TY, TZ>;
+  const int tid = threadIdx.x;
+  __syncthreads();  // previous chunk's ranks read
+  for (int k = tid; k < G::NK; k += kThreads) hist[k] = 0;
+  __syncthreads();
+  {
+    int hk = -1, hc = 0;
+#pragma unroll
+    for (int r = 0; r < kPPT; ++r) {
+      if (r < nvalid) {
+        if (key[r] != hk) {
+          if (hk >= 0) atomicAdd(&hist[hk], hc);
+          hk = key[r];
+          hc = 0;
+        }
+        ++hc;
+      }
+    }
+    if (hk >= 0) atomicAdd(&hist[hk], hc);
+  }
+  __syncthreads();
+  // exclusive scan of hist in place
+  {
+    constexpr int PER = (G::NK + kThreads - 1) / kThreads;
+    int v[PER];
+    int run = 0;
+#pragma unroll
+    for (int r = 0; r < PER; ++r) {
+      const int k = tid * PER + r;
+      v[r] = k < G::NK ? hist[k] : 0;
+      run += v[r];
+    }
+    const int lane = tid & 31, warp = tid >> 5;
+    int x = run;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) misc[8 + warp] = x;
+    __syncthreads();
+    if (tid == 0) {
+      int s = 0;
+      for (int w = 0; w < kThreads / 32; ++w) {
+        const int tmp = misc[8 + w];
+        misc[8 + w] = s;
+        s += tmp;
+      }
+      misc[7] = s;  // chunk total
+    }
+    __syncthreads();
+    int pre = misc[8 + warp] + x - run;
+#pragma unroll
+    for (int r = 0; r < PER; ++r) {
+      const int k = tid * PER + r;
+      if (k < G::NK) hist[k] = pre;
+      if (k == G::NC) misc[6] = pre;  // stayers in this chunk (hist[NC] moves during ranking)
+      pre += v[r];
+    }
+  }
+  __syncthreads();
+  const int nst = misc[6];
+  // rank within key (a run of equal keys takes one atomic) and write
+  {
+    int r = 0;
+    while (r < nvalid) {
+      const int k = key[r];
+      int n = 1;
+      while (r + n < nvalid && key[r + n] == k) ++n;
+      const int p0 = atomicAdd(&hist[k], n);
+      for (int m = 0; m < n; ++m) {
+        const P& q = pp[r + m];
+        if (k < G::NC) {
+          const int pos = ws + p0 + m;
+          if (pos < room)
+            store_particle<NDIM>(A.out.p, base + pos, q);
+          else
+            spill_put(A, t, q);
+        } else {
+          const int dir = (int)(q.cell >> 24);
+          int ix = (tix + dir % 3 - 1 + A.nt[0]) % A.nt[0];
+          int iy = (tiy + (dir / 3) % 3 - 1 + A.nt[1]) % A.nt[1];
+          int iz = (tiz + dir / 9 - 1 + A.nt[2]) % A.nt[2];
+          const int dt_ = (iz * A.nt[1] + iy) * A.nt[0] + ix;
+          P q2 = q;
+          q2.cell = (q.cell & 0x00FFFFFFu) | ((uint32_t)DIR_STAY << 24);
+          const int slot = atomicAdd(&A.out.inc[dt_], 1);
+          if (slot < A.res[dt_])
+            store_particle<NDIM>(A.out.p, A.base[dt_] + A.cap[dt_] - 1 - slot, q2);
+          else
+            spill_put(A, dt_, q2);
+        }
+      }
+      r += n;
+    }
+  }
+  ws += nst;
 }
 
 template <int NDIM, int TX, int TY, int TZ, int MINB>
@@ -443,13 +567,9 @@ __global__ void __launch_bounds__(kThreads, MINB)
   float* F = reinterpret_cast<float*>(smem + G::FOFF);
   float* J = reinterpret_cast<float*>(smem + G::JOFF);
   int* hist = reinterpret_cast<int*>(smem + G::HOFF);
-  int* cursor = reinterpret_cast<int*>(smem + G::COFF);
   float* Q = reinterpret_cast<float*>(smem + G::QOFF);
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + G::MOFF);
-  int* misc = reinterpret_cast<int*>(smem + G::MOFF + 16);  // [0] tile [1] queue [2..9] scan [12..38] counts
-  int* gpre = misc + 40;                                     // 28 ints: incoming group prefix
-  int* gsrc = gpre + 28;                                     // 27 ints: source tile of group d
-  int* gofs = gsrc + 27;                                     // 27 ints: group start within source region
+  int* misc = reinterpret_cast<int*>(smem + G::MOFF + 16);  // [0] tile [1] queue [6] stayers [7] total [8..15] scan
   const int tid = threadIdx.x;
 
   if (tid == 0) {
@@ -476,33 +596,13 @@ __global__ void __launch_bounds__(kThreads, MINB)
         tma_load_3d(F, &fmap, bar, x0, y0, 0);
     }
     for (int k = tid; k < 3 * G::JPL; k += kThreads) J[k] = 0.f;
-    for (int k = tid; k < G::NK; k += kThreads) hist[k] = 0;
-    if (tid < kDirs) {
-      // group of the neighbour nb = t - (offset of direction d) that moved into t
-      const int d = tid;
-      const int ddx = d % 3 - 1, ddy = (d / 3) % 3 - 1, ddz = d / 9 - 1;
-      int cnt = 0, src = 0, ofs = 0;
-      if (d != DIR_STAY && (NDIM == 3 || ddz == 0)) {
-        const int nx_ = (tix - ddx + A.nt[0]) % A.nt[0];
-        const int ny_ = (tiy - ddy + A.nt[1]) % A.nt[1];
-        const int nz_ = NDIM == 3 ? (tiz - ddz + A.nt[2]) % A.nt[2] : 0;
-        src = (nz_ * A.nt[1] + ny_) * A.nt[0] + nx_;
-        cnt = A.in.mcount[src * kDirs + d];
-        ofs = A.in.mstart[src * kDirs + d];
-      }
-      misc[12 + d] = cnt;
-      gsrc[d] = src;
-      gofs[d] = ofs;
-    }
-    __syncthreads();
-    if (tid == 0) {
-      int run = 0;
-      for (int d = 0; d < kDirs; ++d) {
-        gpre[d] = run;
-        run += misc[12 + d];
-      }
-      gpre[kDirs] = run;
-    }
+    const long long base = A.base[t];
+    const int cap = A.cap[t];
+    const int res = A.res[t];
+    const int nstay = A.in.stay[t];
+    int ninc = A.in.inc[t];
+    ninc = ninc < res ? ninc : res;
+    const int room = cap - res;  // stayer slots of the output region
     if (!mbar_wait_bounded(bar, phase, kWaitLimit)) {
       if (tid == 0) atomicOr(A.status, ST_TIMEOUT);
       mbar_wait_bounded(bar, phase, kWaitLimit);
@@ -511,145 +611,77 @@ __global__ void __launch_bounds__(kThreads, MINB)
     phase ^= 1u;
     __syncthreads();
 
-    const long long base = A.base[t];
-    const int cap = A.cap[t];
-    const int nstay = A.in.stay[t];
-    const int ninc = gpre[kDirs];
-
-    // ---- pass 1a: own stayers, 4 consecutive (same-cell) particles per thread
-    for (int c0 = 0; c0 < nstay; c0 += kChunk) {
+    int ws = 0;
+    // chunks over the stayers (front, 16-byte aligned) then the arrivals (back)
+    const int nchunk_s = (nstay + kChunk - 1) / kChunk;
+    const int nchunk_i = (ninc + kChunk - 1) / kChunk;
+    for (int ch = 0; ch < nchunk_s + nchunk_i; ++ch) {
       P pp[kPPT];
-      const int first = c0 + tid * kPPT;
-      int nvalid = nstay - first;
-      nvalid = nvalid < 0 ? 0 : (nvalid > kPPT ? kPPT : nvalid);
-      if (nvalid > 0) {
-        const long long s = base + first;
-        const uint4 cl = *reinterpret_cast<const uint4*>(A.in.p.cell + s);
-        const float4 q0 = *reinterpret_cast<const float4*>(A.in.p.o[0] + s);
-        const float4 q1 = *reinterpret_cast<const float4*>(A.in.p.o[1] + s);
-        float4 q2 = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (NDIM == 3) q2 = *reinterpret_cast<const float4*>(A.in.p.o[2] + s);
-        const float4 v0 = *reinterpret_cast<const float4*>(A.in.p.u[0] + s);
-        const float4 v1 = *reinterpret_cast<const float4*>(A.in.p.u[1] + s);
-        const float4 v2 = *reinterpret_cast<const float4*>(A.in.p.u[2] + s);
-        int4 idv = make_int4(0, 0, 0, 0);
-        if (A.in.p.id) idv = *reinterpret_cast<const int4*>(A.in.p.id + s);
-        pp[0] = P{cl.x, q0.x, q1.x, q2.x, v0.x, v1.x, v2.x, idv.x};
-        pp[1] = P{cl.y, q0.y, q1.y, q2.y, v0.y, v1.y, v2.y, idv.y};
-        pp[2] = P{cl.z, q0.z, q1.z, q2.z, v0.z, v1.z, v2.z, idv.z};
-        pp[3] = P{cl.w, q0.w, q1.w, q2.w, v0.w, v1.w, v2.w, idv.w};
-      }
-      Acc acc;
+      int key[kPPT];
+      int nvalid;
+      if (ch < nchunk_s) {
+        const int first = ch * kChunk + tid * kPPT;
+        nvalid = nstay - first;
+        nvalid = nvalid < 0 ? 0 : (nvalid > kPPT ? kPPT : nvalid);
+        if (nvalid > 0) {
+          const long long s = base + first;
+          const uint4 cl = *reinterpret_cast<const uint4*>(A.in.p.cell + s);
+          const float4 q0 = *reinterpret_cast<const float4*>(A.in.p.o[0] + s);
+          const float4 q1 = *reinterpret_cast<const float4*>(A.in.p.o[1] + s);
+          float4 q2 = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (NDIM == 3) q2 = *reinterpret_cast<const float4*>(A.in.p.o[2] + s);
+          const float4 v0 = *reinterpret_cast<const float4*>(A.in.p.u[0] + s);
+          const float4 v1 = *reinterpret_cast<const float4*>(A.in.p.u[1] + s);
+          const float4 v2 = *reinterpret_cast<const float4*>(A.in.p.u[2] + s);
+          int4 idv = make_int4(0, 0, 0, 0);
+          if (A.in.p.id) idv = *reinterpret_cast<const int4*>(A.in.p.id + s);
+          pp[0] = P{cl.x, q0.x, q1.x, q2.x, v0.x, v1.x, v2.x, idv.x};
+          pp[1] = P{cl.y, q0.y, q1.y, q2.y, v0.y, v1.y, v2.y, idv.y};
+          pp[2] = P{cl.z, q0.z, q1.z, q2.z, v0.z, v1.z, v2.z, idv.z};
+          pp[3] = P{cl.w, q0.w, q1.w, q2.w, v0.w, v1.w, v2.w, idv.w};
+        }
+      } else {
+        const int first = (ch - nchunk_s) * kChunk + tid * kPPT;
+        nvalid = ninc - first;
+        nvalid = nvalid < 0 ? 0 : (nvalid > kPPT ? kPPT : nvalid);
 #pragma unroll
-      for (int k = 0; k < 12; ++k) acc.w[k] = 0.f;
-      acc.cell = -1;
-      int hk = -1, hc = 0;
-#pragma unroll
-      for (int r = 0; r < kPPT; ++r) {
-        if (r < nvalid) {
-          const int key = push_one<NDIM, TX, TY, TZ>(F, J, A, pp[r], acc, Q, misc + 1);
-          if (key != hk) {
-            if (hk >= 0) atomicAdd(&hist[hk], hc);
-            hk = key;
-            hc = 0;
+        for (int r = 0; r < kPPT; ++r) {
+          if (r < nvalid) {
+            const long long s = base + cap - ninc + first + r;
+            pp[r] = P{A.in.p.cell[s], A.in.p.o[0][s], A.in.p.o[1][s], NDIM == 3 ? A.in.p.o[2][s] : 0.f,
+                      A.in.p.u[0][s], A.in.p.u[1][s], A.in.p.u[2][s], A.in.p.id ? A.in.p.id[s] : 0};
           }
-          ++hc;
         }
       }
-      acc_flush<NDIM, TX, TY, TZ>(J, acc);
-      if (hk >= 0) atomicAdd(&hist[hk], hc);
-      if (nvalid == kPPT) {
-        *reinterpret_cast<float4*>(sfield(A, 0) + first) =
-            make_float4(__uint_as_float(pp[0].cell), __uint_as_float(pp[1].cell), __uint_as_float(pp[2].cell),
-                        __uint_as_float(pp[3].cell));
-        *reinterpret_cast<float4*>(sfield(A, 1) + first) = make_float4(pp[0].o0, pp[1].o0, pp[2].o0, pp[3].o0);
-        *reinterpret_cast<float4*>(sfield(A, 2) + first) = make_float4(pp[0].o1, pp[1].o1, pp[2].o1, pp[3].o1);
-        if (NDIM == 3)
-          *reinterpret_cast<float4*>(sfield(A, 3) + first) = make_float4(pp[0].o2, pp[1].o2, pp[2].o2, pp[3].o2);
-        *reinterpret_cast<float4*>(sfield(A, 4) + first) = make_float4(pp[0].u0, pp[1].u0, pp[2].u0, pp[3].u0);
-        *reinterpret_cast<float4*>(sfield(A, 5) + first) = make_float4(pp[0].u1, pp[1].u1, pp[2].u1, pp[3].u1);
-        *reinterpret_cast<float4*>(sfield(A, 6) + first) = make_float4(pp[0].u2, pp[1].u2, pp[2].u2, pp[3].u2);
-        if (A.in.p.id)
-          *reinterpret_cast<float4*>(sfield(A, 7) + first) =
-              make_float4(__int_as_float(pp[0].id), __int_as_float(pp[1].id), __int_as_float(pp[2].id),
-                          __int_as_float(pp[3].id));
-      } else {
-#pragma unroll
-        for (int r = 0; r < kPPT; ++r)
-          if (r < nvalid) scratch_put(A, first + r, pp[r]);
-      }
-      __syncthreads();
-      const int nq = misc[1];
-      if (nq > kQCap / 2) {
-        drain_queue<NDIM, TX, TY, TZ>(J, A, Q, nq < kQCap ? nq : kQCap);
-        __syncthreads();
-        if (tid == 0) misc[1] = 0;
-        __syncthreads();
-      }
-    }
-
-    // ---- pass 1b: movers the neighbours sent to this tile
-    for (int c0 = 0; c0 < ninc; c0 += kThreads) {
-      const int k = c0 + tid;
-      if (k < ninc) {
-        int d = 0;
-#pragma unroll 1
-        for (int step = 16; step > 0; step >>= 1)
-          if (d + step < kDirs && gpre[d + step] <= k) d += step;
-        const int src = gsrc[d];
-        const long long s = A.base[src] + gofs[d] + (k - gpre[d]);
-        P p{A.in.p.cell[s] & 0x00FFFFFFu, A.in.p.o[0][s], A.in.p.o[1][s], NDIM == 3 ? A.in.p.o[2][s] : 0.f,
-            A.in.p.u[0][s], A.in.p.u[1][s], A.in.p.u[2][s], A.in.p.id ? A.in.p.id[s] : 0};
+      {
         Acc acc;
 #pragma unroll
-        for (int q = 0; q < 12; ++q) acc.w[q] = 0.f;
+        for (int k = 0; k < 12; ++k) acc.w[k] = 0.f;
         acc.cell = -1;
-        const int key = push_one<NDIM, TX, TY, TZ>(F, J, A, p, acc, Q, misc + 1);
+#pragma unroll
+        for (int r = 0; r < kPPT; ++r)
+          key[r] = r < nvalid ? push_one<NDIM, TX, TY, TZ>(F, J, A, pp[r], acc, Q, misc + 1) : 0;
         acc_flush<NDIM, TX, TY, TZ>(J, acc);
-        if (nstay + k < A.scap) {
-          atomicAdd(&hist[key], 1);
-          scratch_put(A, nstay + k, p);
-        } else {
-          // more arrivals than the scratch holds: the particle (fully advanced)
-          // goes to the spill list and the host re-bins before the next step
-          atomicOr(A.status, ST_SPILL);
-          const int q = atomicAdd(A.spill_count, 1);
-          if (q >= A.spill_cap) {
-            atomicOr(A.status, ST_SPILL_LOST);
-          } else {
-            const int dir = (int)(p.cell >> 24);
-            int ti[3] = {tix, tiy, tiz};
-            ti[0] = (ti[0] + dir % 3 - 1 + A.nt[0]) % A.nt[0];
-            ti[1] = (ti[1] + (dir / 3) % 3 - 1 + A.nt[1]) % A.nt[1];
-            ti[2] = (ti[2] + dir / 9 - 1 + A.nt[2]) % A.nt[2];
-            A.spill.tile[q] = (ti[2] * A.nt[1] + ti[1]) * A.nt[0] + ti[0];
-            A.spill.cell[q] = (p.cell & 0x00FFFFFFu) | ((uint32_t)DIR_STAY << 24);
-            A.spill.o[0][q] = p.o0;
-            A.spill.o[1][q] = p.o1;
-            A.spill.o[2][q] = p.o2;
-            A.spill.u[0][q] = p.u0;
-            A.spill.u[1][q] = p.u1;
-            A.spill.u[2][q] = p.u2;
-            if (A.spill.id) A.spill.id[q] = p.id;
-          }
-        }
       }
+      sort_and_store<NDIM, TX, TY, TZ>(A, t, tix, tiy, tiz, base, room, pp, key, nvalid, ws, hist, misc);
       __syncthreads();
       const int nq = misc[1];
       if (nq > kQCap / 2) {
         drain_queue<NDIM, TX, TY, TZ>(J, A, Q, nq < kQCap ? nq : kQCap);
         __syncthreads();
         if (tid == 0) misc[1] = 0;
-        __syncthreads();
+        __syncthreads();  // the reset lands before the next chunk queues anything
       }
     }
+    __syncthreads();
     {
       const int nq = misc[1];
       if (nq > 0) drain_queue<NDIM, TX, TY, TZ>(J, A, Q, nq < kQCap ? nq : kQCap);
     }
-
-    // ---- flush the current tile: order the shared atomics before the async
-    // proxy reads them; one thread issues the TMA reduce-add
+    if (tid == 0) A.out.stay[t] = ws < room ? ws : room;
+    // flush the current tile: every thread orders its shared atomics before the
+    // async proxy reads them; one thread issues the TMA reduce-add and waits
+    // until the TMA has read the tile before the next tile reuses it
     fence_proxy_async_smem();
     __syncthreads();
     if (tid == 0) {
@@ -658,123 +690,8 @@ __global__ void __launch_bounds__(kThreads, MINB)
       else
         tma_reduce_add_3d(&jmap, J, x0, y0, 0);
       tma_commit();
+      tma_wait_read0();
     }
-
-    // ---- exclusive scan of the key histogram (stayers by cell, then movers by direction)
-    {
-      constexpr int PER = (G::NK + kThreads - 1) / kThreads;
-      int v[PER];
-      int run = 0;
-#pragma unroll
-      for (int r = 0; r < PER; ++r) {
-        const int k = tid * PER + r;
-        v[r] = k < G::NK ? hist[k] : 0;
-        run += v[r];
-      }
-      const int lane = tid & 31, warp = tid >> 5;
-      int x = run;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
-      }
-      int* wsum = misc + 2;  // 8 warps
-      if (lane == 31) wsum[warp] = x;
-      __syncthreads();
-      if (tid == 0) {
-        int s = 0;
-        for (int w = 0; w < kThreads / 32; ++w) {
-          const int tmp = wsum[w];
-          wsum[w] = s;
-          s += tmp;
-        }
-      }
-      __syncthreads();
-      int pre = wsum[warp] + x - run;
-#pragma unroll
-      for (int r = 0; r < PER; ++r) {
-        const int k = tid * PER + r;
-        if (k < G::NK) cursor[k] = pre;
-        pre += v[r];
-      }
-    }
-    __syncthreads();
-    const int total = cursor[G::NK - 1] + hist[G::NK - 1];
-    const int nst = cursor[G::NC];  // stayers
-    if (tid < kDirs) {
-      // placed counts (a full region spills the tail)
-      const int st0 = cursor[G::NC + tid];
-      const int cnt = hist[G::NC + tid];
-      int placed = cap - st0;
-      placed = placed < 0 ? 0 : (placed > cnt ? cnt : placed);
-      A.out.mstart[t * kDirs + tid] = st0;
-      A.out.mcount[t * kDirs + tid] = tid == DIR_STAY ? 0 : placed;
-    }
-    if (tid == 0) {
-      A.out.stay[t] = nst < cap ? nst : cap;
-      const int mv = total - nst;
-      int pm = cap - nst;
-      pm = pm < 0 ? 0 : (pm > mv ? mv : pm);
-      A.out.move[t] = pm;
-    }
-
-    // ---- pass 2: scatter from scratch into the region, sorted by key
-    for (int c0 = 0; c0 < total; c0 += kThreads) {
-      const int i = c0 + tid;
-      const bool valid = i < total;
-      const unsigned act = __ballot_sync(0xffffffffu, valid);
-      if (valid) {
-        const uint32_t cell = __float_as_uint(sfield(A, 0)[i]);
-        const int dir = (int)(cell >> 24);
-        const int key = dir == DIR_STAY
-                            ? (int)(cell & 255) + TX * ((int)((cell >> 8) & 255) + TY * (int)((cell >> 16) & 255))
-                            : G::NC + dir;
-        const unsigned same = __match_any_sync(act, key);
-        const int leader = __ffs(same) - 1;
-        const int lane = tid & 31;
-        int pos0 = 0;
-        if (lane == leader) pos0 = atomicAdd(&cursor[key], __popc(same));
-        pos0 = __shfl_sync(same, pos0, leader);
-        const int pos = pos0 + __popc(same & ((1u << lane) - 1u));
-        P q{cell, sfield(A, 1)[i], sfield(A, 2)[i], NDIM == 3 ? sfield(A, 3)[i] : 0.f, sfield(A, 4)[i],
-            sfield(A, 5)[i], sfield(A, 6)[i], __float_as_int(sfield(A, 7)[i])};
-        if (pos < cap) {
-          const long long s = base + pos;
-          A.out.p.cell[s] = q.cell;
-          A.out.p.o[0][s] = q.o0;
-          A.out.p.o[1][s] = q.o1;
-          if (NDIM == 3) A.out.p.o[2][s] = q.o2;
-          A.out.p.u[0][s] = q.u0;
-          A.out.p.u[1][s] = q.u1;
-          A.out.p.u[2][s] = q.u2;
-          if (A.out.p.id) A.out.p.id[s] = q.id;
-        } else {
-          // region full: park the particle in the spill list with the tile it
-          // belongs to; the host re-bins before the next step
-          atomicOr(A.status, ST_SPILL);
-          const int k = atomicAdd(A.spill_count, 1);
-          if (k >= A.spill_cap) {
-            atomicOr(A.status, ST_SPILL_LOST);
-          } else {
-            int ti[3] = {tix, tiy, tiz};
-            ti[0] = (ti[0] + dir % 3 - 1 + A.nt[0]) % A.nt[0];
-            ti[1] = (ti[1] + (dir / 3) % 3 - 1 + A.nt[1]) % A.nt[1];
-            ti[2] = (ti[2] + dir / 9 - 1 + A.nt[2]) % A.nt[2];
-            A.spill.tile[k] = (ti[2] * A.nt[1] + ti[1]) * A.nt[0] + ti[0];
-            A.spill.cell[k] = (q.cell & 0x00FFFFFFu) | ((uint32_t)DIR_STAY << 24);
-            A.spill.o[0][k] = q.o0;
-            A.spill.o[1][k] = q.o1;
-            A.spill.o[2][k] = q.o2;
-            A.spill.u[0][k] = q.u0;
-            A.spill.u[1][k] = q.u1;
-            A.spill.u[2][k] = q.u2;
-            if (A.spill.id) A.spill.id[k] = q.id;
-          }
-        }
-      }
-    }
-    // the shared current tile must stay intact until the TMA has read it
-    if (tid == 0) tma_wait_read0();
   }
 }
 
@@ -797,13 +714,22 @@ __device__ inline int dest_tile(const Tiles& tg, int t, uint32_t cell) {
   return (iz * tg.nt[1] + iy) * tg.nt[0] + ix;
 }
 
+// slot of the k-th particle of tile t: stayers from the front, arrivals at the back
+__device__ inline long long tile_slot(const Tiles& tg, const TileSide& in, int t, int k, int& n) {
+  const int ns = in.stay[t];
+  int ni = in.inc[t];
+  ni = ni < tg.res[t] ? ni : tg.res[t];
+  n = ns + ni;
+  return k < ns ? tg.base[t] + k : tg.base[t] + tg.cap[t] - ni + (k - ns);
+}
+
 __global__ void k_flatten(Tiles tg, TileSide in, const long long* out_off, Flat32 out) {
   const int t = blockIdx.x;
-  const int n = in.stay[t] + in.move[t];
-  const long long base = tg.base[t];
+  int n;
+  tile_slot(tg, in, t, 0, n);
   const long long o = out_off[t];
   for (int k = threadIdx.x; k < n; k += blockDim.x) {
-    const long long s = base + k;
+    const long long s = tile_slot(tg, in, t, k, n);
     const uint32_t c = in.p.cell[s];
     const long long w = o + k;
     out.tile[w] = dest_tile(tg, t, c);
@@ -908,10 +834,10 @@ __global__ void k_global_to_flat(int ndim, Layout L, Tiles tg, PushConst C, cons
 // charge density with linear weights (FP64 atomics) of every particle in the store
 __global__ void k_tiled_rho(Layout L, PushConst C, Tiles tg, TileSide in, double* rho) {
   const int t = blockIdx.x;
-  const int n = in.stay[t] + in.move[t];
-  const long long base = tg.base[t];
+  int n;
+  tile_slot(tg, in, t, 0, n);
   for (int k = threadIdx.x; k < n; k += blockDim.x) {
-    const long long s = base + k;
+    const long long s = tile_slot(tg, in, t, k, n);
     const uint32_t c = in.p.cell[s];
     int o[3];
     tile_origin(tg, dest_tile(tg, t, c), o);
@@ -931,11 +857,11 @@ __global__ void k_tiled_rho(Layout L, PushConst C, Tiles tg, TileSide in, double
 __global__ void k_tiled_kinetic(PushConst C, Tiles tg, TileSide in, double* ke, double* qsum) {
   __shared__ double red[32];
   const int t = blockIdx.x;
-  const int n = in.stay[t] + in.move[t];
-  const long long base = tg.base[t];
+  int n;
+  tile_slot(tg, in, t, 0, n);
   double v = 0.0;
   for (int k = threadIdx.x; k < n; k += blockDim.x) {
-    const long long s = base + k;
+    const long long s = tile_slot(tg, in, t, k, n);
     const double a = in.p.u[0][s], b = in.p.u[1][s], c = in.p.u[2][s];
     v += C.q * C.rqm * (sqrt(1.0 + a * a + b * b + c * c) - 1.0);
   }
@@ -1010,24 +936,21 @@ int tiled_push_grid(int ndim, const int T[3], int ntiles) {
   return g < ntiles ? g : ntiles;
 }
 
-size_t tiled_scratch_bytes(int grid, long long max_cap) { return (size_t)grid * 8 * (size_t)max_cap * 4; }
-
 void tiled_push(const Layout& L, const PushConst& C, const Tiles& tg, const TileSide& in, const TileSide& out,
-                Flat32 spill, int* spill_count, long long spill_cap, void* scratch, long long scratch_cap, int grid,
-                int* work, const CUtensorMap* fmap, const CUtensorMap* jmap, int* status, cudaStream_t s) {
+                Flat32 spill, int* spill_count, long long spill_cap, int grid, int* work, const CUtensorMap* fmap,
+                const CUtensorMap* jmap, int* status, cudaStream_t s) {
   (void)L;
   TileArgs A;
   for (int d = 0; d < 3; ++d) A.nt[d] = tg.nt[d];
   A.ntiles = tg.ntiles;
   A.base = tg.base;
   A.cap = tg.cap;
+  A.res = tg.res;
   A.in = in;
   A.out = out;
   A.spill = spill;
   A.spill_count = spill_count;
   A.spill_cap = spill_cap;
-  A.scratch = reinterpret_cast<float*>(scratch);
-  A.scap = scratch_cap;
   A.work = work;
   A.qmdt2 = (float)(C.dt / (2.0 * C.rqm));
   for (int d = 0; d < 3; ++d) {
@@ -1039,6 +962,7 @@ void tiled_push(const Layout& L, const PushConst& C, const Tiles& tg, const Tile
   A.j3f = (float)(C.q / C.dvol);
   A.status = status;
   cudaMemsetAsync(work, 0, sizeof(int), s);
+  cudaMemsetAsync(out.inc, 0, sizeof(int) * (size_t)tg.ntiles, s);
   const int* T = tg.T;
 #define X(N, A_, B_, C_)                                                    \
   if (tg.ndim == N && T[0] == A_ && T[1] == B_ && (N == 2 || T[2] == C_)) { \

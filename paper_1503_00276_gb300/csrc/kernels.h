@@ -74,28 +74,27 @@ struct Tiles {
   int ntiles;
   long long* base;        // [ntiles] first slot of each tile region
   int* cap;               // [ntiles] slots of each tile region
+  int* res;               // [ntiles] slots at the back of each region kept for arrivals
 };
 constexpr int DIR_STAY = 13;
 
 // One side of the ping-pong particle store.  Region of tile t: slots
-// [base[t], base[t] + cap[t]); stayers (sorted by cell) first, then the movers,
-// grouped by the direction they left in; group d of tile t starts at
-// base[t] + mstart[27 t + d] and holds mcount[27 t + d] particles.
+// [base[t], base[t] + cap[t]).  Its front holds the tile's stayers (stay[t]
+// of them, sorted by cell in runs); its back holds the particles that entered
+// the tile in the last step (inc[t] of them, at most res[t]), written there
+// by the neighbouring tiles.
 struct TileSide {
   Part32 p;
   int* stay;
-  int* move;
-  int* mstart;
-  int* mcount;
+  int* inc;
 };
 
 void tiled_push(const Layout& L, const PushConst& C, const Tiles& tg, const TileSide& in, const TileSide& out,
-                Flat32 spill, int* spill_count, long long spill_cap, void* scratch, long long scratch_cap, int grid,
-                int* work, const CUtensorMap* fmap, const CUtensorMap* jmap, int* status, cudaStream_t s);
+                Flat32 spill, int* spill_count, long long spill_cap, int grid, int* work, const CUtensorMap* fmap,
+                const CUtensorMap* jmap, int* status, cudaStream_t s);
 int tiled_push_smem_bytes(int ndim, const int T[3]);
 int tiled_push_grid(int ndim, const int T[3], int ntiles);  // persistent CTAs
 void tiled_push_set_minb(int minb);  // CTAs per SM the tile kernel is built for (2 or 3)
-size_t tiled_scratch_bytes(int grid, long long max_cap);
 void tiled_flatten(const Tiles& tg, const TileSide& in, const long long* out_off, Flat32 out, cudaStream_t s);
 void flat_count(const Flat32& f, long long n, int ntiles, int* counts, cudaStream_t s);
 void flat_scatter(const Flat32& f, long long n, const Tiles& tg, int* cursor, Part32 out, cudaStream_t s);

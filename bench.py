@@ -54,7 +54,7 @@ def parse():
     p.add_argument("--ppc", type=int, default=8, choices=[1, 2, 4, 8, 16])
     p.add_argument("--nx", default="512,256,256")
     p.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
-    p.add_argument("--tile", default="8,8,8")
+    p.add_argument("--tile", default="auto", help="tile shape in cells, e.g. 4,4,4 (auto: the library's choice)")
     p.add_argument("--smooth", type=int, default=0, help="(1,2,1) passes per direction")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
@@ -168,7 +168,7 @@ def describe(args, n_p: int):
                      f"({n_p:,} electrons), u_th=0.05c, dx=0.1 c/w_p, dt=0.99 Courant, "
                      f"{'FP32 cell-offset tiled' if args.precision == 'fp32' else 'FP64 plain'}"),
         "grid": nx, "ppc": args.ppc, "precision": args.precision,
-        "tile": [int(v) for v in args.tile.split(",")] if args.precision == "fp32" else None,
+        "tile": args.tile if args.precision == "fp32" else None,
         "smoothing_passes": args.smooth,
         "l2": "inputs larger than L2 (particle store >= 7.5 GB vs 129 MB L2)",
         "steps_in_config": 200,
@@ -189,7 +189,7 @@ def run_ours(args):
 
     g, sps, _ = make_workload(args, rank)
     n_p = workload.n_particles(g, sps[0])
-    tile = tuple(int(v) for v in args.tile.split(","))
+    tile = None if args.tile == "auto" else tuple(int(v) for v in args.tile.split(","))
     stream = torch.cuda.current_stream()
 
     def barrier():

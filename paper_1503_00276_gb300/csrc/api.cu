@@ -381,7 +381,8 @@ pic_status bin_flat(pic_sim* S, SpeciesState& sp, Flat32& flat, long long n) {
     long long cap = (c + extra + 3) / 4 * 4;
     if (cap > (1ll << 30)) cap = 1ll << 30;
     hcap[t] = (int)cap;
-    hres[t] = (int)std::min<long long>(cap - c, std::max<long long>(32, extra / 2));
+    // a multiple of 4, so that the stayer part of a region ends 16-byte aligned
+    hres[t] = (int)(std::min<long long>(cap - c, std::max<long long>(32, extra / 2)) & ~3ll);
     hbase[t] = slots;
     slots += cap;
   }
@@ -402,7 +403,10 @@ pic_status bin_flat(pic_sim* S, SpeciesState& sp, Flat32& flat, long long n) {
     }
     sp.slots = slots;
   }
-  sp.grid = tiled_push_grid(S->ndim, S->T, nt);
+  long long max_cap = 0;
+  for (int t = 0; t < nt; ++t) max_cap = std::max<long long>(max_cap, hcap[t]);
+  sp.tg.small = tiled_has_small(S->ndim, S->T) && (max_cap <= tiled_small_capacity() || !tiled_has_general(S->ndim, S->T));
+  sp.grid = tiled_push_grid(S->ndim, S->T, nt, sp.tg.small != 0);
   cudaMemcpyAsync(sp.tg.cap, hcap.data(), 4 * (size_t)nt, cudaMemcpyHostToDevice, S->s);
   cudaMemcpyAsync(sp.tg.res, hres.data(), 4 * (size_t)nt, cudaMemcpyHostToDevice, S->s);
   cudaMemcpyAsync(sp.tg.base, hbase.data(), 8 * (size_t)nt, cudaMemcpyHostToDevice, S->s);
@@ -893,17 +897,31 @@ pic_status pic_init(const pic_grid* grid, const pic_species* species, int nspeci
   if (S->prec == PIC_FP32_CELLOFF) {
     for (int d = 0; d < 3; ++d) S->T[d] = d < S->ndim ? grid->tile[d] : 1;
     if (S->T[0] <= 0 || S->T[1] <= 0 || (S->ndim == 3 && S->T[2] <= 0)) {
-      if (S->ndim == 3) {
-        S->T[0] = S->T[1] = S->T[2] = 8;
-      } else {
-        S->T[0] = 32;
-        S->T[1] = 16;
-        S->T[2] = 1;
+      // about 512 particles per tile: the small-tile kernel then stages a
+      // whole tile (plus slack) in shared memory
+      int ppc = 1;
+      if (nspecies > 0 && species[0].n_explicit <= 0)
+        for (int d = 0; d < S->ndim; ++d) ppc *= std::max(1, species[0].ppc[d]);
+      static const int c3[][3] = {{4, 4, 2}, {4, 4, 4}, {8, 4, 4}, {8, 8, 8}, {16, 8, 4}};
+      static const int c2[][3] = {{8, 4, 1}, {8, 8, 1}, {16, 8, 1}, {16, 16, 1}, {32, 16, 1}};
+      const int first = ppc >= 16 ? 0 : ppc >= 8 ? 1 : ppc >= 4 ? 2 : 3;
+      S->T[0] = 0;
+      for (int k = first; k < 5 && S->T[0] == 0; ++k) {
+        const int* c = S->ndim == 3 ? c3[k] : c2[k];
+        bool fits = true;
+        for (int d = 0; d < S->ndim; ++d) fits = fits && grid->nx[d] % c[d] == 0;
+        if (fits)
+          for (int d = 0; d < 3; ++d) S->T[d] = c[d];
+      }
+      if (S->T[0] == 0) {
+        set_error("no supported tile shape divides the grid");
+        delete S;
+        return PIC_EINVAL;
       }
     }
     if (const char* e = getenv("PICGB_TILE_CTAS")) tiled_push_set_minb(atoi(e));
     if (tiled_push_smem_bytes(S->ndim, S->T) < 0) {
-      set_error("unsupported tile shape (3D: 8x8x8, 16x8x4; 2D: 32x16, 16x16, 8x8)");
+      set_error("unsupported tile shape (3D: 4x4x4, 4x4x2, 8x4x4, 8x8x8, 16x8x4; 2D: 8x4, 8x8, 16x8, 16x16, 32x16)");
       delete S;
       return PIC_EUNSUPPORTED;
     }

@@ -143,7 +143,23 @@ __device__ inline void tma_reduce_add_4d(const CUtensorMap* map, const void* src
       : "memory");
 }
 
+// 1D bulk copies (no tensor map): both addresses 16-byte aligned, size a
+// multiple of 16 bytes.
+__device__ inline void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ inline void bulk_s2g(void* dst, const void* src, uint32_t bytes) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(smem_u32(src)),
+               "r"(bytes)
+               : "memory");
+}
+
 __device__ inline void tma_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ inline void tma_wait_read1() { asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory"); }
 __device__ inline void tma_wait_read0() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
 __device__ inline void tma_wait0() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 

@@ -256,7 +256,7 @@ __device__ inline void acc_flush(float* J, Acc& a) {
 // Gather + push + move of one particle, deposit of its first in-cell piece into
 // the accumulator, crossing pieces queued.  Rewrites p in the coordinates of
 // the tile it ends in; returns its key: new cell (stayers) or NC + direction.
-template <int NDIM, int TX, int TY, int TZ>
+template <int NDIM, int TX, int TY, int TZ, int QCAP = kQCap>
 __device__ inline int push_one(const float* F, float* J, const TileArgs& A, P& p, Acc& acc, float* Q, int* qn) {
   using G = Geo<NDIM, TX, TY, TZ>;
   const int lx = p.cell & 255, ly = (p.cell >> 8) & 255, lz = NDIM == 3 ? (p.cell >> 16) & 255 : 0;
@@ -347,7 +347,7 @@ __device__ inline int push_one(const float* F, float* J, const TileArgs& A, P& p
   }
   if (tm < 1.f) {
     const int q = atomicAdd(qn, 1);
-    if (q < kQCap) {
+    if (q < QCAP) {
       float* e = Q + q * G::QW;
       e[0] = __int_as_float(cellp);
       e[1] = ax;
@@ -457,9 +457,9 @@ __device__ inline void store_particle(const Part32& o, long long s, const P& q) 
 // Counting sort of one chunk of advanced particles (still in registers) by key
 // and write-out: stayers to the front of this tile's output region in cell
 // order, leavers to the back of their new tile's output region.
-template <int NDIM, int TX, int TY, int TZ>
+template <int NDIM, int TX, int TY, int TZ, int PPT = kPPT>
 __device__ inline void sort_and_store(const TileArgs& A, int t, int tix, int tiy, int tiz, long long base, int room,
-                                      P (&pp)[kPPT], int (&key)[kPPT], int nvalid, int& ws, int* hist, int* misc) {
+                                      P (&pp)[PPT], int (&key)[PPT], int nvalid, int& ws, int* hist, int* misc) {
   using G = Geo<NDIM, TX, TY, TZ>;
   const int tid = threadIdx.x;
   __syncthreads();  // previous chunk's ranks read
@@ -468,7 +468,7 @@ __device__ inline void sort_and_store(const TileArgs& A, int t, int tix, int tiy
   {
     int hk = -1, hc = 0;
 #pragma unroll
-    for (int r = 0; r < kPPT; ++r) {
+    for (int r = 0; r < PPT; ++r) {
       if (r < nvalid) {
         if (key[r] != hk) {
           if (hk >= 0) atomicAdd(&hist[hk], hc);
@@ -695,6 +695,361 @@ __global__ void __launch_bounds__(kThreads, MINB)
   }
 }
 
+
+// ============================================================================
+// Small-tile kernel: every tile holds at most kCapS particles, so one CTA
+// stages a whole tile in shared memory and the pipeline runs on TMA:
+//   tile t computes while the tile it takes next streams in (fields into the
+//   other field buffer, particles into the input stage, by 1D bulk copies);
+//   the stayers leave cell-sorted through an output stage by bulk stores; the
+//   current tiles are double-buffered so a tile's reduce-add drains while the
+//   next tile deposits.  Tiles with more particles (density far from the mean)
+//   are processed straight from global memory in chunks.
+// ============================================================================
+constexpr int kCapS = 768;                // particles per staged tile
+constexpr int kPPTS = kCapS / kThreads;  // 3
+constexpr int kQCapS = 96;
+constexpr int kNA = 8;                    // staged arrays: cell, o1..o3, u1..u3, id
+
+template <int NDIM, int TX, int TY, int TZ>
+struct GeoS {
+  using G = Geo<NDIM, TX, TY, TZ>;
+  static constexpr int FB = ((6 * G::FPL * 4 + 127) / 128) * 128;
+  static constexpr int JB = ((3 * G::JPL * 4 + 127) / 128) * 128;
+  static constexpr int SB = kNA * kCapS * 4;
+  static constexpr int F0 = 0, F1 = FB, J0 = 2 * FB, J1 = 2 * FB + JB;
+  static constexpr int IN = 2 * FB + 2 * JB;
+  static constexpr int OUT = IN + SB;
+  static constexpr int H = OUT + SB;
+  static constexpr int QO = H + ((G::NK * 4 + 15) / 16) * 16;
+  static constexpr int MO = QO + ((kQCapS * G::QW * 4 + 15) / 16) * 16;
+  static constexpr int SMEM = MO + 256;
+  // misc ints (after 3 mbarriers): sort scratch 6..15, then the tile pipeline
+  static constexpr int M_TILE = 16, M_NEXT = 17, M_QN = 18, M_NS = 19, M_NI = 20, M_AOFF = 21, M_BIG = 22,
+                       M_NST = 23;
+};
+
+__device__ inline void* arr_ptr(const Part32& p, int a) {
+  switch (a) {
+    case 0: return p.cell;
+    case 1: return p.o[0];
+    case 2: return p.o[1];
+    case 3: return p.o[2];
+    case 4: return p.u[0];
+    case 5: return p.u[1];
+    case 6: return p.u[2];
+    default: return p.id;
+  }
+}
+
+// Thread 0: start the copies of tile t's fields and particles; record where
+// the particles land in the input stage.
+template <int NDIM, int TX, int TY, int TZ>
+__device__ inline void issue_tile(const TileArgs& A, const CUtensorMap* fmap, int t, float* F, uint64_t* fbar,
+                                  float* IN, uint64_t* inbar, int* misc) {
+  using S = GeoS<NDIM, TX, TY, TZ>;
+  using G = Geo<NDIM, TX, TY, TZ>;
+  const int tix = t % A.nt[0], tiy = (t / A.nt[0]) % A.nt[1], tiz = t / (A.nt[0] * A.nt[1]);
+  mbar_arrive_expect_tx(fbar, (uint32_t)G::FBYTES);
+  if (NDIM == 3)
+    tma_load_4d(F, fmap, fbar, tix * TX, tiy * TY, tiz * TZ, 0);
+  else
+    tma_load_3d(F, fmap, fbar, tix * TX, tiy * TY, 0);
+  const int ns = A.in.stay[t];
+  int ni = A.in.inc[t];
+  ni = ni < A.res[t] ? ni : A.res[t];
+  const long long base = A.base[t];
+  const int cap = A.cap[t];
+  misc[S::M_NS] = ns;
+  misc[S::M_NI] = ni;
+  if (ns + ni + 9 > kCapS) {  // over-full tile: processed from global memory
+    misc[S::M_BIG] = 1;
+    mbar_arrive_expect_tx(inbar, 0);
+    return;
+  }
+  misc[S::M_BIG] = 0;
+  const int ns4 = (ns + 3) & ~3;
+  const int a0 = (cap - ni) & ~3;          // aligned start of the arrivals
+  const int delta = (cap - ni) - a0;
+  const int ni4 = (ni + delta + 3) & ~3;
+  misc[S::M_AOFF] = ns4 + delta;
+  int na = 0;
+  for (int a = 0; a < kNA; ++a)
+    if (arr_ptr(A.in.p, a) && !(NDIM == 2 && a == 3)) ++na;
+  mbar_arrive_expect_tx(inbar, (uint32_t)(na * (ns4 + (ni > 0 ? ni4 : 0)) * 4));
+  for (int a = 0; a < kNA; ++a) {
+    const float* src = reinterpret_cast<const float*>(arr_ptr(A.in.p, a));
+    if (!src || (NDIM == 2 && a == 3)) continue;
+    float* dst = IN + a * kCapS;
+    if (ns4 > 0) bulk_g2s(dst, src + base, (uint32_t)ns4 * 4, inbar);
+    if (ni > 0) bulk_g2s(dst + ns4, src + base + a0, (uint32_t)ni4 * 4, inbar);
+  }
+}
+
+template <int NDIM>
+__device__ inline P stage_get(const float* IN, int i) {
+  P p;
+  p.cell = __float_as_uint(IN[i]);
+  p.o0 = IN[kCapS + i];
+  p.o1 = IN[2 * kCapS + i];
+  p.o2 = NDIM == 3 ? IN[3 * kCapS + i] : 0.f;
+  p.u0 = IN[4 * kCapS + i];
+  p.u1 = IN[5 * kCapS + i];
+  p.u2 = IN[6 * kCapS + i];
+  p.id = __float_as_int(IN[7 * kCapS + i]);
+  return p;
+}
+
+template <int NDIM, int TX, int TY, int TZ>
+__global__ void __launch_bounds__(kThreads, 3)
+    k_tile_push_s(const __grid_constant__ CUtensorMap fmap, const __grid_constant__ CUtensorMap jmap, TileArgs A) {
+  using G = Geo<NDIM, TX, TY, TZ>;
+  using S = GeoS<NDIM, TX, TY, TZ>;
+  extern __shared__ __align__(1024) unsigned char smem[];
+  float* Fb[2] = {reinterpret_cast<float*>(smem + S::F0), reinterpret_cast<float*>(smem + S::F1)};
+  float* Jb[2] = {reinterpret_cast<float*>(smem + S::J0), reinterpret_cast<float*>(smem + S::J1)};
+  float* IN = reinterpret_cast<float*>(smem + S::IN);
+  float* OUT = reinterpret_cast<float*>(smem + S::OUT);
+  int* hist = reinterpret_cast<int*>(smem + S::H);
+  float* Q = reinterpret_cast<float*>(smem + S::QO);
+  uint64_t* fbar = reinterpret_cast<uint64_t*>(smem + S::MO);  // [2]
+  uint64_t* inbar = fbar + 2;
+  int* misc = reinterpret_cast<int*>(smem + S::MO + 32);
+  const int tid = threadIdx.x;
+  const bool has_id = A.in.p.id != nullptr;
+
+  if (tid == 0) {
+    mbar_init(&fbar[0], 1);
+    mbar_init(&fbar[1], 1);
+    mbar_init(inbar, 1);
+    fence_barrier_init();
+  }
+  __syncthreads();
+  if (tid == 0) {
+    const int t0 = atomicAdd(A.work, 1);
+    misc[S::M_TILE] = t0;
+    if (t0 < A.ntiles) issue_tile<NDIM, TX, TY, TZ>(A, &fmap, t0, Fb[0], &fbar[0], IN, inbar, misc);
+  }
+  __syncthreads();
+  uint32_t fph0 = 0, fph1 = 0, iph = 0;
+  for (int it = 0;; ++it) {
+    const int t = misc[S::M_TILE];
+    if (t >= A.ntiles) break;
+    const int fb = it & 1;
+    const int tix = t % A.nt[0], tiy = (t / A.nt[0]) % A.nt[1], tiz = t / (A.nt[0] * A.nt[1]);
+    const long long base = A.base[t];
+    const int cap = A.cap[t];
+    const int room = cap - A.res[t];
+    const uint32_t fph = fb ? fph1 : fph0;
+    bool ok = mbar_wait_bounded(&fbar[fb], fph, kWaitLimit);
+    ok = mbar_wait_bounded(inbar, iph, kWaitLimit) && ok;
+    if (__syncthreads_or(!ok)) {  // every thread takes the same decision
+      if (tid == 0) atomicOr(A.status, ST_TIMEOUT);
+      mbar_wait_bounded(&fbar[fb], fph, kWaitLimit);
+      mbar_wait_bounded(inbar, iph, kWaitLimit);
+      break;
+    }
+    if (fb) fph1 ^= 1u; else fph0 ^= 1u;
+    iph ^= 1u;
+    const int ns = misc[S::M_NS], ni = misc[S::M_NI], aoff = misc[S::M_AOFF], big = misc[S::M_BIG];
+    const int n = ns + ni;
+    P pp[kPPTS];
+    int nvalid = 0;
+    if (!big) {
+      const int first = tid * kPPTS;
+      nvalid = n - first;
+      nvalid = nvalid < 0 ? 0 : (nvalid > kPPTS ? kPPTS : nvalid);
+#pragma unroll
+      for (int r = 0; r < kPPTS; ++r) {
+        if (r < nvalid) {
+          const int i = first + r;
+          pp[r] = stage_get<NDIM>(IN, i < ns ? i : aoff + (i - ns));
+          if (!has_id) pp[r].id = 0;
+        }
+      }
+    }
+    if (tid == 0) tma_wait_read1();  // current tile Jb[fb] of two tiles ago has been read
+    __syncthreads();                  // the input stage and the tile's metadata are consumed
+    if (tid == 0) {
+      const int tn = atomicAdd(A.work, 1);
+      misc[S::M_NEXT] = tn;
+      misc[S::M_QN] = 0;
+      if (tn < A.ntiles) issue_tile<NDIM, TX, TY, TZ>(A, &fmap, tn, Fb[fb ^ 1], &fbar[fb ^ 1], IN, inbar, misc);
+    }
+    float* F = Fb[fb];
+    float* J = Jb[fb];
+    for (int k = tid; k < 3 * G::JPL; k += kThreads) J[k] = 0.f;
+    for (int k = tid; k < G::NK; k += kThreads) hist[k] = 0;
+    __syncthreads();
+
+    if (!big) {
+      int key[kPPTS];
+      {
+        Acc acc;
+#pragma unroll
+        for (int k = 0; k < 12; ++k) acc.w[k] = 0.f;
+        acc.cell = -1;
+#pragma unroll
+        for (int r = 0; r < kPPTS; ++r)
+          key[r] = r < nvalid ? push_one<NDIM, TX, TY, TZ, kQCapS>(F, J, A, pp[r], acc, Q, misc + S::M_QN) : 0;
+        acc_flush<NDIM, TX, TY, TZ>(J, acc);
+      }
+      {
+        int hk = -1, hc = 0;
+#pragma unroll
+        for (int r = 0; r < kPPTS; ++r) {
+          if (r < nvalid) {
+            if (key[r] != hk) {
+              if (hk >= 0) atomicAdd(&hist[hk], hc);
+              hk = key[r];
+              hc = 0;
+            }
+            ++hc;
+          }
+        }
+        if (hk >= 0) atomicAdd(&hist[hk], hc);
+      }
+      __syncthreads();
+      {
+        const int nq = misc[S::M_QN];
+        drain_queue<NDIM, TX, TY, TZ>(J, A, Q, nq < kQCapS ? nq : kQCapS);
+      }
+      if (tid < 32) {  // exclusive scan of the key histogram by one warp
+        constexpr int PW = (G::NK + 31) / 32;
+        int v[PW];
+        int run = 0;
+#pragma unroll
+        for (int r = 0; r < PW; ++r) {
+          const int k = tid * PW + r;
+          v[r] = k < G::NK ? hist[k] : 0;
+          run += v[r];
+        }
+        int x = run;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int y = __shfl_up_sync(0xffffffffu, x, o);
+          if (tid >= o) x += y;
+        }
+        int pre = x - run;
+#pragma unroll
+        for (int r = 0; r < PW; ++r) {
+          const int k = tid * PW + r;
+          if (k < G::NK) hist[k] = pre;
+          if (k == G::NC) misc[S::M_NST] = pre;
+          pre += v[r];
+        }
+      }
+      if (tid == 0) tma_wait_read0();  // the output stage's previous bulk stores have read it
+      __syncthreads();
+      // rank within key (a run of equal keys takes one atomic); stayers to the
+      // output stage in cell order, leavers straight to their new tile
+      {
+        int r = 0;
+        while (r < nvalid) {
+          const int k = key[r];
+          int m = 1;
+          while (r + m < nvalid && key[r + m] == k) ++m;
+          const int p0 = atomicAdd(&hist[k], m);
+          for (int j = 0; j < m; ++j) {
+            const P& q = pp[r + j];
+            if (k < G::NC) {
+              const int pos = p0 + j;
+              if (pos < room) {
+                OUT[pos] = __uint_as_float(q.cell);
+                OUT[kCapS + pos] = q.o0;
+                OUT[2 * kCapS + pos] = q.o1;
+                if (NDIM == 3) OUT[3 * kCapS + pos] = q.o2;
+                OUT[4 * kCapS + pos] = q.u0;
+                OUT[5 * kCapS + pos] = q.u1;
+                OUT[6 * kCapS + pos] = q.u2;
+                OUT[7 * kCapS + pos] = __int_as_float(q.id);
+              } else {
+                spill_put(A, t, q);
+              }
+            } else {
+              const int dir = (int)(q.cell >> 24);
+              const int ix = (tix + dir % 3 - 1 + A.nt[0]) % A.nt[0];
+              const int iy = (tiy + (dir / 3) % 3 - 1 + A.nt[1]) % A.nt[1];
+              const int iz = (tiz + dir / 9 - 1 + A.nt[2]) % A.nt[2];
+              const int dt_ = (iz * A.nt[1] + iy) * A.nt[0] + ix;
+              P q2 = q;
+              q2.cell = (q.cell & 0x00FFFFFFu) | ((uint32_t)DIR_STAY << 24);
+              const int slot = atomicAdd(&A.out.inc[dt_], 1);
+              if (slot < A.res[dt_])
+                store_particle<NDIM>(A.out.p, A.base[dt_] + A.cap[dt_] - 1 - slot, q2);
+              else
+                spill_put(A, dt_, q2);
+            }
+          }
+          r += m;
+        }
+      }
+    } else {
+      // over-full tile: chunks straight from global memory, each sorted by cell
+      int ws = 0;
+      for (int c0 = 0; c0 < n; c0 += kCapS) {
+        P qq[kPPTS];
+        int key[kPPTS];
+        const int first = c0 + tid * kPPTS;
+        int nv = n - first;
+        nv = nv < 0 ? 0 : (nv > kPPTS ? kPPTS : nv);
+#pragma unroll
+        for (int r = 0; r < kPPTS; ++r) {
+          if (r < nv) {
+            const int i = first + r;
+            const long long s = i < ns ? base + i : base + cap - ni + (i - ns);
+            qq[r] = P{A.in.p.cell[s], A.in.p.o[0][s], A.in.p.o[1][s], NDIM == 3 ? A.in.p.o[2][s] : 0.f,
+                      A.in.p.u[0][s], A.in.p.u[1][s], A.in.p.u[2][s], has_id ? A.in.p.id[s] : 0};
+          }
+        }
+        Acc acc;
+#pragma unroll
+        for (int k = 0; k < 12; ++k) acc.w[k] = 0.f;
+        acc.cell = -1;
+#pragma unroll
+        for (int r = 0; r < kPPTS; ++r)
+          key[r] = r < nv ? push_one<NDIM, TX, TY, TZ, kQCapS>(F, J, A, qq[r], acc, Q, misc + S::M_QN) : 0;
+        acc_flush<NDIM, TX, TY, TZ>(J, acc);
+        sort_and_store<NDIM, TX, TY, TZ, kPPTS>(A, t, tix, tiy, tiz, base, room, qq, key, nv, ws, hist, misc);
+        __syncthreads();
+        const int nq = misc[S::M_QN];
+        drain_queue<NDIM, TX, TY, TZ>(J, A, Q, nq < kQCapS ? nq : kQCapS);
+        __syncthreads();
+        if (tid == 0) misc[S::M_QN] = 0;
+        __syncthreads();
+      }
+      if (tid == 0) misc[S::M_NST] = -1 - (ws < room ? ws : room);  // already stored
+    }
+    // flush: current tile by TMA reduce-add, stayers by bulk stores
+    fence_proxy_async_smem();
+    __syncthreads();
+    if (tid == 0) {
+      if (NDIM == 3)
+        tma_reduce_add_4d(&jmap, J, tix * TX, tiy * TY, tiz * TZ, 0);
+      else
+        tma_reduce_add_3d(&jmap, J, tix * TX, tiy * TY, 0);
+      int nst = misc[S::M_NST];
+      if (nst >= 0) {
+        nst = nst < room ? nst : room;
+        const int n4 = (nst + 3) & ~3;  // room is a multiple of 4, so n4 <= room
+        if (n4 > 0)
+          for (int a = 0; a < kNA; ++a) {
+            float* dst = reinterpret_cast<float*>(arr_ptr(A.out.p, a));
+            if (!dst || (NDIM == 2 && a == 3)) continue;
+            bulk_s2g(dst + base, OUT + a * kCapS, (uint32_t)n4 * 4);
+          }
+      } else {
+        nst = -1 - nst;
+      }
+      A.out.stay[t] = nst;
+      tma_commit();
+      misc[S::M_TILE] = misc[S::M_NEXT];
+    }
+    __syncthreads();
+  }
+  if (tid == 0) tma_wait0();
+}
+
 // ------------------------------------------------------------ support kernels
 __device__ inline void tile_origin(const Tiles& tg, int t, int o[3]) {
   o[0] = (t % tg.nt[0]) * tg.T[0];
@@ -892,6 +1247,22 @@ int occupancy() {
   return occ;
 }
 
+template <int NDIM, int TX, int TY, int TZ>
+int occupancy_s() {
+  using S = GeoS<NDIM, TX, TY, TZ>;
+  static int occ = -1;
+  if (occ < 0) {
+    cudaFuncSetAttribute(k_tile_push_s<NDIM, TX, TY, TZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM);
+    int o = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_tile_push_s<NDIM, TX, TY, TZ>, kThreads, S::SMEM) !=
+            cudaSuccess ||
+        o < 1)
+      o = 1;
+    occ = o;
+  }
+  return occ;
+}
+
 template <int NDIM, int TX, int TY, int TZ, int MINB>
 void launch_push(const CUtensorMap* fmap, const CUtensorMap* jmap, const TileArgs& A, int grid, cudaStream_t s) {
   using G = Geo<NDIM, TX, TY, TZ>;
@@ -899,10 +1270,18 @@ void launch_push(const CUtensorMap* fmap, const CUtensorMap* jmap, const TileArg
   k_tile_push<NDIM, TX, TY, TZ, MINB><<<grid, kThreads, G::SMEM, s>>>(*fmap, *jmap, A);
 }
 
-// Register budget of the tile kernel: 3 CTAs per SM (80 registers, a few
-// spills in 3D) or 2 (no spills).  Chosen per simulation.
+template <int NDIM, int TX, int TY, int TZ>
+void launch_push_s(const CUtensorMap* fmap, const CUtensorMap* jmap, const TileArgs& A, int grid, cudaStream_t s) {
+  using S = GeoS<NDIM, TX, TY, TZ>;
+  occupancy_s<NDIM, TX, TY, TZ>();
+  k_tile_push_s<NDIM, TX, TY, TZ><<<grid, kThreads, S::SMEM, s>>>(*fmap, *jmap, A);
+}
+
+// Register budget of the general tile kernel: 3 CTAs per SM (80 registers) or
+// 2.  Chosen per simulation.
 int g_minb = 3;
 
+// Shapes of the general kernel (any particle count per tile) ...
 #define PICGB_TILE_SHAPES(X) \
   X(3, 8, 8, 8)              \
   X(3, 16, 8, 4)             \
@@ -910,28 +1289,70 @@ int g_minb = 3;
   X(2, 16, 16, 1)            \
   X(2, 8, 8, 1)
 
+// ... and of the small-tile kernel (at most kCapS - 9 particles per tile region)
+#define PICGB_SMALL_SHAPES(X) \
+  X(3, 4, 4, 4)               \
+  X(3, 4, 4, 2)               \
+  X(3, 8, 4, 4)               \
+  X(2, 8, 8, 1)               \
+  X(2, 8, 4, 1)               \
+  X(2, 16, 8, 1)
+
 }  // namespace
+
+static bool shape_is(int ndim, const int T[3], int n, int a, int b, int c) {
+  return ndim == n && T[0] == a && T[1] == b && (n == 2 || T[2] == c);
+}
 
 int tiled_push_smem_bytes(int ndim, const int T[3]) {
 #define X(N, A_, B_, C_) \
-  if (ndim == N && T[0] == A_ && T[1] == B_ && (N == 2 || T[2] == C_)) return Geo<N, A_, B_, C_>::SMEM;
+  if (shape_is(ndim, T, N, A_, B_, C_)) return Geo<N, A_, B_, C_>::SMEM;
   PICGB_TILE_SHAPES(X)
+#undef X
+#define X(N, A_, B_, C_) \
+  if (shape_is(ndim, T, N, A_, B_, C_)) return GeoS<N, A_, B_, C_>::SMEM;
+  PICGB_SMALL_SHAPES(X)
 #undef X
   return -1;
 }
 
+bool tiled_has_general(int ndim, const int T[3]) {
+#define X(N, A_, B_, C_) \
+  if (shape_is(ndim, T, N, A_, B_, C_)) return true;
+  PICGB_TILE_SHAPES(X)
+#undef X
+  return false;
+}
+
+bool tiled_has_small(int ndim, const int T[3]) {
+#define X(N, A_, B_, C_) \
+  if (shape_is(ndim, T, N, A_, B_, C_)) return true;
+  PICGB_SMALL_SHAPES(X)
+#undef X
+  return false;
+}
+
+int tiled_small_capacity() { return kCapS - 9; }
+
 void tiled_push_set_minb(int minb) { g_minb = minb == 2 ? 2 : 3; }
 
-int tiled_push_grid(int ndim, const int T[3], int ntiles) {
+int tiled_push_grid(int ndim, const int T[3], int ntiles, bool small) {
   int dev = 0, sms = 1;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   int occ = 1;
-#define X(N, A_, B_, C_)                                                  \
-  if (ndim == N && T[0] == A_ && T[1] == B_ && (N == 2 || T[2] == C_))    \
-    occ = g_minb == 2 ? occupancy<N, A_, B_, C_, 2>() : occupancy<N, A_, B_, C_, 3>();
-  PICGB_TILE_SHAPES(X)
+  if (small) {
+#define X(N, A_, B_, C_) \
+  if (shape_is(ndim, T, N, A_, B_, C_)) occ = occupancy_s<N, A_, B_, C_>();
+    PICGB_SMALL_SHAPES(X)
 #undef X
+  } else {
+#define X(N, A_, B_, C_)                  \
+  if (shape_is(ndim, T, N, A_, B_, C_)) \
+    occ = g_minb == 2 ? occupancy<N, A_, B_, C_, 2>() : occupancy<N, A_, B_, C_, 3>();
+    PICGB_TILE_SHAPES(X)
+#undef X
+  }
   const int g = sms * occ;
   return g < ntiles ? g : ntiles;
 }
@@ -964,13 +1385,22 @@ void tiled_push(const Layout& L, const PushConst& C, const Tiles& tg, const Tile
   cudaMemsetAsync(work, 0, sizeof(int), s);
   cudaMemsetAsync(out.inc, 0, sizeof(int) * (size_t)tg.ntiles, s);
   const int* T = tg.T;
-#define X(N, A_, B_, C_)                                                    \
-  if (tg.ndim == N && T[0] == A_ && T[1] == B_ && (N == 2 || T[2] == C_)) { \
-    if (g_minb == 2)                                                        \
-      launch_push<N, A_, B_, C_, 2>(fmap, jmap, A, grid, s);                \
-    else                                                                    \
-      launch_push<N, A_, B_, C_, 3>(fmap, jmap, A, grid, s);                \
-    return;                                                                 \
+  if (tg.small) {
+#define X(N, A_, B_, C_)                                \
+  if (shape_is(tg.ndim, T, N, A_, B_, C_)) {            \
+    launch_push_s<N, A_, B_, C_>(fmap, jmap, A, grid, s); \
+    return;                                             \
+  }
+    PICGB_SMALL_SHAPES(X)
+#undef X
+  }
+#define X(N, A_, B_, C_)                                   \
+  if (shape_is(tg.ndim, T, N, A_, B_, C_)) {               \
+    if (g_minb == 2)                                       \
+      launch_push<N, A_, B_, C_, 2>(fmap, jmap, A, grid, s); \
+    else                                                   \
+      launch_push<N, A_, B_, C_, 3>(fmap, jmap, A, grid, s); \
+    return;                                                \
   }
   PICGB_TILE_SHAPES(X)
 #undef X

@@ -75,6 +75,7 @@ struct Tiles {
   long long* base;        // [ntiles] first slot of each tile region
   int* cap;               // [ntiles] slots of each tile region
   int* res;               // [ntiles] slots at the back of each region kept for arrivals
+  int small;              // 1: every region fits the small-tile kernel's stage
 };
 constexpr int DIR_STAY = 13;
 
@@ -93,7 +94,10 @@ void tiled_push(const Layout& L, const PushConst& C, const Tiles& tg, const Tile
                 Flat32 spill, int* spill_count, long long spill_cap, int grid, int* work, const CUtensorMap* fmap,
                 const CUtensorMap* jmap, int* status, cudaStream_t s);
 int tiled_push_smem_bytes(int ndim, const int T[3]);
-int tiled_push_grid(int ndim, const int T[3], int ntiles);  // persistent CTAs
+int tiled_push_grid(int ndim, const int T[3], int ntiles, bool small);  // persistent CTAs
+bool tiled_has_general(int ndim, const int T[3]);
+bool tiled_has_small(int ndim, const int T[3]);
+int tiled_small_capacity();  // largest tile region the small-tile kernel stages
 void tiled_push_set_minb(int minb);  // CTAs per SM the tile kernel is built for (2 or 3)
 void tiled_flatten(const Tiles& tg, const TileSide& in, const long long* out_off, Flat32 out, cudaStream_t s);
 void flat_count(const Flat32& f, long long n, int ntiles, int* counts, cudaStream_t s);

@@ -108,6 +108,13 @@ CASES_32 = {
     "3d_16x8x4": (3, (32, 16, 8), (16, 8, 4), (1, 2, 1), 0.3),
     "2d_32x16": (2, (64, 32, 1), (32, 16), (3, 2, 1), 0.4),
     "2d_8x8": (2, (16, 8, 1), (8, 8), (2, 2, 1), 0.6),
+    # small-tile kernel (whole tile staged in shared memory)
+    "3d_4x4x4_small": (3, (16, 8, 12), (4, 4, 4), (3, 1, 1), 0.4),
+    "3d_8x4x4_small": (3, (16, 16, 8), (8, 4, 4), (2, 1, 1), 0.4),
+    "3d_4x4x2_small": (3, (8, 8, 8), (4, 4, 2), (1, 3, 1), 0.4),
+    "2d_8x4_small": (2, (32, 16, 1), (8, 4), (3, 3, 1), 0.5),
+    # small-tile kernel with tiles above its stage capacity (chunks from global memory)
+    "3d_4x4x4_overfull": (3, (8, 8, 8), (4, 4, 4), (4, 2, 2), 0.4),
 }
 
 
@@ -172,7 +179,7 @@ def test_fp32_gauss_law_and_energy_history_vs_fp64():
     every step, field-energy history within 1e-3 (of its maximum) of FP64."""
     g, sps, nsteps = workload.config0()
     s64 = _sim(g, sps, "fp64", ids=False)
-    s32 = _sim(g, sps, "fp32", tile=(32, 16), ids=False)
+    s32 = _sim(g, sps, "fp32", ids=False)
     fe64, fe32 = [], []
     for _ in range(nsteps):
         s64.step(1)

@@ -283,5 +283,5 @@ def test_error_paths_on_gpu():
         pg.Simulation(g2, [sp], precision="fp64", explicit=[(x, np.zeros((4, 3)), -1.0)])
     assert e.value.code == -1
     with pytest.raises(pg.PicError) as e:
-        pg.Simulation(g2, [sp], precision="fp32", tile=(4, 4, 4))
+        pg.Simulation(g2, [sp], precision="fp32", tile=(2, 2, 2))
     assert e.value.code == -8

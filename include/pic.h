@@ -225,6 +225,37 @@ pic_status pic_bin_tiles(const int nx[3], const int tile[3], long long n, const 
                          int* tile_count, long long* tile_start, long long* perm,
                          const pic_allocator* alloc, void* stream);
 
+/* Bytes of the fixed device scratch behind pic_bin_tiles_noalloc. */
+#define PIC_BIN_NOALLOC_SCRATCH_BYTES (16u << 20)
+
+/* pic_bin_tiles without any device allocation (the thesis has no counterpart;
+ * this entry point exists for callers).  Some callers cannot call cudaMalloc
+ * or take an allocator callback: code that runs where allocation is forbidden
+ * or unsafe -- inside a framework that owns every byte of device memory through
+ * its own pool and accounting, in latency-critical paths where a cudaMalloc or
+ * cudaFree (which may synchronise the device) is not allowed, or where an
+ * allocation failure mid-run cannot be handled.  They get the same result as
+ * pic_bin_tiles (same arguments, same output, order within a tile again
+ * unspecified) with the scratch taken from a fixed array compiled into the
+ * library:
+ *  - its size is PIC_BIN_NOALLOC_SCRATCH_BYTES (16 MiB), reserved on every GPU
+ *    that loads the library until the process exits;
+ *  - the scratch a call needs is about 4 bytes per particle plus 4 bytes per
+ *    tile (e.g. 3 million particles on 512 thousand tiles take 14 MiB);
+ *    requests needing more than the array return PIC_EINVAL with a message,
+ *    and nothing runs;
+ *  - the first call on a device (with that device current) looks the array's
+ *    device address up once with cudaGetSymbolAddress; make that first call
+ *    before any stream capture;
+ *  - every call on a device shares the one array and the function clears what
+ *    must start at zero, so calls whose GPU work overlaps (different streams,
+ *    threads or processes sharing the library on one device) race and must be
+ *    serialised by the caller;
+ *  - like pic_bin_tiles it synchronises `stream` before returning.
+ * It calls no cudaMalloc, cudaFree or other allocating routine. */
+pic_status pic_bin_tiles_noalloc(const int nx[3], const int tile[3], long long n, const int* cell,
+                                 int* tile_count, long long* tile_start, long long* perm, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -19,7 +19,7 @@ import numpy as np
 from . import _capi
 from ._capi import FIELD_NAMES, PIC_FP32_CELLOFF, PIC_FP64_PLAIN, PicError, check, load  # noqa: F401
 
-__all__ = ["Simulation", "bin_tiles", "load", "PicError", "PIC_FP64_PLAIN", "PIC_FP32_CELLOFF", "FIELD_NAMES"]
+__all__ = ["Simulation", "bin_tiles", "bin_tiles_noalloc", "load", "PicError", "PIC_FP64_PLAIN", "PIC_FP32_CELLOFF", "FIELD_NAMES"]
 
 
 def _torch():
@@ -267,4 +267,27 @@ def bin_tiles(nx, tile, cell, stream=None):
     check(lib.pic_bin_tiles(nxa, ta, n, C.c_void_p(cell.data_ptr()), C.c_void_p(counts.data_ptr()),
                             C.c_void_p(start.data_ptr()), C.c_void_p(perm.data_ptr()), C.byref(alloc.struct),
                             C.c_void_p(st.cuda_stream)), "pic_bin_tiles")
+    return counts, start, perm[:n]
+
+
+def bin_tiles_noalloc(nx, tile, cell, stream=None):
+    """pic_bin_tiles_noalloc: same result as bin_tiles, scratch from the fixed
+    device array compiled into the library (no allocation inside the call).
+    Output tensors are allocated here by torch, outside the C call."""
+    torch = _torch()
+    lib = load()
+    assert cell.is_cuda and cell.dtype == torch.int32 and cell.is_contiguous()
+    n = cell.shape[0]
+    nt = 1
+    for d in range(3):
+        nt *= int(nx[d]) // int(tile[d])
+    counts = torch.empty(nt, dtype=torch.int32, device=cell.device)
+    start = torch.empty(nt, dtype=torch.int64, device=cell.device)
+    perm = torch.empty(max(n, 1), dtype=torch.int64, device=cell.device)
+    st = stream if stream is not None else torch.cuda.current_stream()
+    nxa = (C.c_int * 3)(*[int(v) for v in nx])
+    ta = (C.c_int * 3)(*[int(v) for v in tile])
+    check(lib.pic_bin_tiles_noalloc(nxa, ta, n, C.c_void_p(cell.data_ptr()), C.c_void_p(counts.data_ptr()),
+                                    C.c_void_p(start.data_ptr()), C.c_void_p(perm.data_ptr()),
+                                    C.c_void_p(st.cuda_stream)), "pic_bin_tiles_noalloc")
     return counts, start, perm[:n]

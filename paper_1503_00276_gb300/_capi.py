@@ -64,7 +64,9 @@ PROTOTYPES = {
     "pic_last_error": (C.c_char_p, []),
     "pic_bin_tiles": (C.c_int, [C.POINTER(C.c_int), C.POINTER(C.c_int), C.c_longlong, _P, _P, _P, _P,
                                 C.POINTER(PicAllocator), _P]),
+    "pic_bin_tiles_noalloc": (C.c_int, [C.POINTER(C.c_int), C.POINTER(C.c_int), C.c_longlong, _P, _P, _P, _P, _P]),
 }
+BIN_NOALLOC_SCRATCH_BYTES = 16 << 20
 
 _lock = threading.Lock()
 _lib = None

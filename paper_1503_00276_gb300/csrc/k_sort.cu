@@ -1,4 +1,5 @@
 // k_sort.cu -- prefix sums and the stateless tile binning entry point.
+#include <mutex>
 #include <string>
 
 #include "kernels.h"
@@ -212,4 +213,72 @@ extern "C" pic_status pic_bin_tiles(const int nx[3], const int tile[3], long lon
     cudaFree(scratch);
   }
   return st;
+}
+
+// ---------------------------------------------------------------------------
+// pic_bin_tiles_noalloc: the same binning with its scratch in a fixed device
+// array instead of memory obtained from an allocator.
+//
+// The array lives in this library's module image, so every GPU that loads the
+// library keeps PIC_BIN_NOALLOC_SCRATCH_BYTES of device memory reserved until
+// the process exits.  Host code must not use the array's name as a device
+// address; its address is looked up per device with cudaGetSymbolAddress the
+// first time the entry point runs on that device (with that device current),
+// then cached.
+// ---------------------------------------------------------------------------
+namespace picgb {
+namespace {
+
+constexpr size_t kNoAllocBytes = PIC_BIN_NOALLOC_SCRATCH_BYTES;
+__device__ __align__(256) unsigned char g_bin_scratch[kNoAllocBytes];
+
+constexpr int kMaxDevices = 64;
+void* g_bin_scratch_addr[kMaxDevices] = {};
+std::mutex g_bin_scratch_mu;
+
+pic_status bin_scratch_address(void** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) {
+    set_error(std::string("pic_bin_tiles_noalloc: cudaGetDevice: ") + cudaGetErrorString(e));
+    return PIC_ECUDA;
+  }
+  if (dev < 0 || dev >= kMaxDevices) {
+    set_error("pic_bin_tiles_noalloc: device ordinal out of range");
+    return PIC_EUNSUPPORTED;
+  }
+  std::lock_guard<std::mutex> lock(g_bin_scratch_mu);
+  if (!g_bin_scratch_addr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_bin_scratch);
+    if (e != cudaSuccess || !p) {
+      set_error(std::string("pic_bin_tiles_noalloc: cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+      return PIC_ECUDA;
+    }
+    g_bin_scratch_addr[dev] = p;
+  }
+  *out = g_bin_scratch_addr[dev];
+  return PIC_OK;
+}
+
+}  // namespace
+}  // namespace picgb
+
+extern "C" pic_status pic_bin_tiles_noalloc(const int nx[3], const int tile[3], long long n, const int* cell,
+                                            int* tile_count, long long* tile_start, long long* perm, void* stream) {
+  pic_status st = bin_tiles_check(nx, tile, n, cell, tile_count, tile_start, perm);
+  if (st != PIC_OK) return st;
+  const long long ntiles = (long long)(nx[0] / tile[0]) * (nx[1] / tile[1]) * (nx[2] / tile[2]);
+  const size_t bytes = bin_scratch_bytes(n, ntiles);
+  if (bytes > kNoAllocBytes) {
+    set_error("pic_bin_tiles_noalloc: " + std::to_string(n) + " particles on " + std::to_string(ntiles) +
+              " tiles need " + std::to_string(bytes) + " bytes of scratch, more than the fixed " +
+              std::to_string(kNoAllocBytes) + "; use pic_bin_tiles");
+    return PIC_EINVAL;
+  }
+  void* scratch = nullptr;
+  st = bin_scratch_address(&scratch);
+  if (st != PIC_OK) return st;
+  return bin_tiles_run(nx, tile, n, cell, tile_count, tile_start, perm, scratch,
+                       reinterpret_cast<cudaStream_t>(stream));
 }

@@ -56,6 +56,8 @@ def parse():
     p.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     p.add_argument("--tile", default="auto", help="tile shape in cells, e.g. 4,4,4 (auto: the library's choice)")
     p.add_argument("--smooth", type=int, default=0, help="(1,2,1) passes per direction")
+    p.add_argument("--sort-period", type=int, default=0,
+                   help="steps per cell re-sort of the tiles (0: the library's default)")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-fp64", action="store_true")
@@ -170,6 +172,7 @@ def describe(args, n_p: int):
         "grid": nx, "ppc": args.ppc, "precision": args.precision,
         "tile": args.tile if args.precision == "fp32" else None,
         "smoothing_passes": args.smooth,
+        "sort_period": args.sort_period or None,
         "l2": "inputs larger than L2 (particle store >= 7.5 GB vs 129 MB L2)",
         "steps_in_config": 200,
     }
@@ -234,7 +237,8 @@ def run_ours(args):
 
     peak, peak_kind = measured_peak()
     prec = args.precision
-    sim = pg.Simulation(g, sps, precision=prec, tile=tile if prec == "fp32" else None)
+    sim = pg.Simulation(g, sps, precision=prec, tile=tile if prec == "fp32" else None,
+                        sort_period=args.sort_period)
     clocks = ClockSampler(local)
     ms, tim, clk = timed(sim, args.steps, args.warmup, clocks)
     diag = sim.diag()
@@ -324,7 +328,7 @@ def run_e2e(args, g, sps, n_p, tile, barrier, max_over_ranks, sum_over_ranks):
     barrier()
     t0 = time.perf_counter()
     sim = pg.Simulation(g, sps, precision=args.precision, explicit=[(xn, un, q)],
-                        tile=tile if args.precision == "fp32" else None)
+                        tile=tile if args.precision == "fp32" else None, sort_period=args.sort_period)
     for _ in range(steps):
         sim.step(1)
         sim.diag()

@@ -111,6 +111,9 @@ typedef struct {
   int tile[3];              /* PIC_FP32_CELLOFF tile size in cells (0 = default:
                                2D 32x16, 3D 8x8x8); nx must be a multiple */
   double slack;             /* per-tile storage slack fraction (0 = default 0.25) */
+  int sort_period;          /* PIC_FP32_CELLOFF: every sort_period-th step re-sorts each
+                               tile by cell; the steps between update particles in
+                               place (0 = default 1: sort every step) */
 } pic_grid;
 
 /* One particle species (appendix nl_species / nl_profile).  Either loaded on the

@@ -49,7 +49,7 @@ class _TorchAllocator:
         self.torch.cuda.caching_allocator_delete(ptr)
 
 
-def _grid_struct(grid, precision, tile=None, slack=0.0):
+def _grid_struct(grid, precision, tile=None, slack=0.0, sort_period=0):
     g = _capi.PicGrid()
     g.ndim = int(grid.ndim)
     for d in range(3):
@@ -72,6 +72,7 @@ def _grid_struct(grid, precision, tile=None, slack=0.0):
     g.init_e_gauss_x1 = int(bool(getattr(grid, "init_e_gauss_x1", False)))
     g.precision = int(precision)
     g.slack = float(slack)
+    g.sort_period = int(sort_period)
     return g
 
 
@@ -111,14 +112,14 @@ class Simulation:
     """
 
     def __init__(self, grid, species, precision="fp64", explicit=None, tile=None, track_ids=False, slack=0.0,
-                 stream=None, use_torch_allocator=True, np_max=0):
+                 stream=None, use_torch_allocator=True, np_max=0, sort_period=0):
         self._lib = load()
         torch = _torch()
         prec = PIC_FP32_CELLOFF if precision in ("fp32", PIC_FP32_CELLOFF) else PIC_FP64_PLAIN
         self.precision = prec
         self.ndim = int(grid.ndim)
         self.shape = (int(grid.nx[2]) if grid.ndim == 3 else 1, int(grid.nx[1]), int(grid.nx[0]))
-        self._g = _grid_struct(grid, prec, tile, slack)
+        self._g = _grid_struct(grid, prec, tile, slack, sort_period)
         specs = (_capi.PicSpecies * max(len(species), 1))()
         self._keep = []
         for k, sp in enumerate(species):

@@ -112,7 +112,8 @@ struct SpeciesState {
   long long slots = 0;
   Flat32 spill{};
   long long spill_cap = 0;
-  int grid = 0;             // persistent CTAs of the tile kernel
+  int grid = 0;             // persistent CTAs of the sorting tile kernel
+  int grid_stream = 0;      // ... and of the in-place streaming kernel
   int* work = nullptr;      // its dynamic tile counter
 };
 
@@ -144,6 +145,7 @@ struct pic_sim {
   long long step = 0;
   int T[3] = {1, 1, 1};
   double slack = 0.25;
+  int sort_period = 1;
   bool timing = false;
   double t_ms[kTimingSlots] = {0, 0, 0, 0, 0};
   long long t_n[kTimingSlots] = {0, 0, 0, 0, 0};
@@ -407,6 +409,7 @@ pic_status bin_flat(pic_sim* S, SpeciesState& sp, Flat32& flat, long long n) {
   for (int t = 0; t < nt; ++t) max_cap = std::max<long long>(max_cap, hcap[t]);
   sp.tg.small = tiled_has_small(S->ndim, S->T) && (max_cap <= tiled_small_capacity() || !tiled_has_general(S->ndim, S->T));
   sp.grid = tiled_push_grid(S->ndim, S->T, nt, sp.tg.small != 0);
+  sp.grid_stream = tiled_stream_grid(S->ndim, S->T, nt);
   cudaMemcpyAsync(sp.tg.cap, hcap.data(), 4 * (size_t)nt, cudaMemcpyHostToDevice, S->s);
   cudaMemcpyAsync(sp.tg.res, hres.data(), 4 * (size_t)nt, cudaMemcpyHostToDevice, S->s);
   cudaMemcpyAsync(sp.tg.base, hbase.data(), 8 * (size_t)nt, cudaMemcpyHostToDevice, S->s);
@@ -442,7 +445,7 @@ pic_status flatten(pic_sim* S, SpeciesState& sp, Flat32& flat, long long& n, boo
     set_error("out of device memory (flatten)");
     return PIC_ENOMEM;
   }
-  k_tile_totals<<<(nt + 255) / 256, 256, 0, S->s>>>(sp.side[sp.cur].stay, sp.side[sp.cur].inc, sp.tg.res, tot, nt);
+  tiled_live(sp.tg, sp.side[sp.cur], tot, S->s);
   exclusive_scan_i32(tot, off, nt, scr, S->s);
   long long last_off = 0;
   int last_cnt = 0;
@@ -761,8 +764,11 @@ pic_status one_step(pic_sim* S, bool check_now) {
         plain_push(S->ndim, S->L, C, s.plain, f, j, &S->dstat->status, S->s);
       } else {
         const int in = s.cur, out = 1 - s.cur;
-        tiled_push(S->L, C, s.tg, s.side[in], s.side[out], s.spill, &S->dstat->spill_count, s.spill_cap, s.grid,
-                   s.work, &S->fmap, &S->jmap, &S->dstat->status, S->s);
+        // the last step of every sort_period steps re-sorts each tile by cell;
+        // the steps before it keep the order they find (blocks compacted)
+        const bool stream = S->sort_period > 1 && !s.tg.small && (S->step + 1) % S->sort_period != 0;
+        tiled_push(S->L, C, s.tg, s.side[in], s.side[out], s.spill, &S->dstat->spill_count, s.spill_cap,
+                   stream ? s.grid_stream : s.grid, s.work, &S->fmap, &S->jmap, &S->dstat->status, stream, S->s);
         s.cur = out;
       }
       S->nlaunch += s.n > 0 || S->prec == PIC_FP32_CELLOFF ? 1 : 0;
@@ -892,21 +898,17 @@ pic_status pic_init(const pic_grid* grid, const pic_species* species, int nspeci
     S->al.has_user = true;
   }
   S->slack = grid->slack > 0.0 ? grid->slack : 0.25;
+  S->sort_period = grid->sort_period > 0 ? grid->sort_period : 1;
   int nxv[3] = {grid->nx[0], grid->nx[1], grid->ndim == 3 ? grid->nx[2] : 1};
   S->L = make_layout(S->ndim, nxv);
   if (S->prec == PIC_FP32_CELLOFF) {
     for (int d = 0; d < 3; ++d) S->T[d] = d < S->ndim ? grid->tile[d] : 1;
     if (S->T[0] <= 0 || S->T[1] <= 0 || (S->ndim == 3 && S->T[2] <= 0)) {
-      // about 512 particles per tile: the small-tile kernel then stages a
-      // whole tile (plus slack) in shared memory
-      int ppc = 1;
-      if (nspecies > 0 && species[0].n_explicit <= 0)
-        for (int d = 0; d < S->ndim; ++d) ppc *= std::max(1, species[0].ppc[d]);
-      static const int c3[][3] = {{4, 4, 2}, {4, 4, 4}, {8, 4, 4}, {8, 8, 8}, {16, 8, 4}};
-      static const int c2[][3] = {{8, 4, 1}, {8, 8, 1}, {16, 8, 1}, {16, 16, 1}, {32, 16, 1}};
-      const int first = ppc >= 16 ? 0 : ppc >= 8 ? 1 : ppc >= 4 ? 2 : 3;
+      // defaults: 3D 8x8x8, 2D 32x16 (the first shape that divides the grid)
+      static const int c3[][3] = {{8, 8, 8}, {16, 8, 4}, {8, 4, 4}, {4, 4, 4}};
+      static const int c2[][3] = {{32, 16, 1}, {16, 16, 1}, {16, 8, 1}, {8, 8, 1}};
       S->T[0] = 0;
-      for (int k = first; k < 5 && S->T[0] == 0; ++k) {
+      for (int k = 0; k < 4 && S->T[0] == 0; ++k) {
         const int* c = S->ndim == 3 ? c3[k] : c2[k];
         bool fits = true;
         for (int d = 0; d < S->ndim; ++d) fits = fits && grid->nx[d] % c[d] == 0;

@@ -90,9 +90,13 @@ struct TileSide {
   int* inc;
 };
 
+// stream = true: the in-place step that keeps the last sort's order (empty
+// slots where particles left); false: the step that re-sorts every tile
 void tiled_push(const Layout& L, const PushConst& C, const Tiles& tg, const TileSide& in, const TileSide& out,
                 Flat32 spill, int* spill_count, long long spill_cap, int grid, int* work, const CUtensorMap* fmap,
-                const CUtensorMap* jmap, int* status, cudaStream_t s);
+                const CUtensorMap* jmap, int* status, bool stream, cudaStream_t s);
+int tiled_stream_grid(int ndim, const int T[3], int ntiles);
+void tiled_live(const Tiles& tg, const TileSide& in, int* live, cudaStream_t s);
 int tiled_push_smem_bytes(int ndim, const int T[3]);
 int tiled_push_grid(int ndim, const int T[3], int ntiles, bool small);  // persistent CTAs
 bool tiled_has_general(int ndim, const int T[3]);

@@ -27,7 +27,7 @@ def _pg():
     return pg
 
 
-def _sim(g, sps, prec, fields=None, tile=None, ids=True, explicit=True):
+def _sim(g, sps, prec, fields=None, tile=None, ids=True, explicit=True, sort_period=0):
     pg = _pg()
     ex = None
     if explicit:
@@ -35,7 +35,7 @@ def _sim(g, sps, prec, fields=None, tile=None, ids=True, explicit=True):
         for s in sps:
             x, u = workload.load_particles(g, s)
             ex.append((x, u, workload.macro_charge(g, s)))
-    sim = pg.Simulation(g, sps, precision=prec, explicit=ex, tile=tile, track_ids=ids)
+    sim = pg.Simulation(g, sps, precision=prec, explicit=ex, tile=tile, track_ids=ids, sort_period=sort_period)
     if fields is not None:
         for c, name in enumerate(["E1", "E2", "E3", "B1", "B2", "B3"]):
             sim.set_field(name, fields[c])
@@ -118,8 +118,11 @@ CASES_32 = {
 }
 
 
+# sort_period 1: the cell-sorting kernel runs every step; 2: the first step of
+# each period is the streaming (compacting) kernel
+@pytest.mark.parametrize("sort_period", [1, 2])
 @pytest.mark.parametrize("case", sorted(CASES_32))
-def test_fp32_tiled_one_step_matches_oracle(case):
+def test_fp32_tiled_one_step_matches_oracle(case, sort_period):
     ndim, nx, tile, ppc, uth = CASES_32[case]
     dx = (0.1, 0.1, 0.1)
     g = workload.Grid(ndim=ndim, nx=nx, dx=dx, dt=workload.courant_dt(dx, ndim), e0=(0.0, 0.01, 0.0),
@@ -127,7 +130,7 @@ def test_fp32_tiled_one_step_matches_oracle(case):
     sp = workload.Species(ppc=ppc, uth=(uth,) * 3, seed=1234)
     f = workload.random_fields(g, seed=9, amp=0.2)
     ref = oracle.from_workload(g, [sp], fields=f)
-    sim = _sim(g, [sp], "fp32", fields=f, tile=tile)
+    sim = _sim(g, [sp], "fp32", fields=f, tile=tile, sort_period=sort_period)
     # binning of the loaded particles is bit-exact
     _, counts, _ = oracle.tile_bin(g, tile if ndim == 3 else tuple(tile) + (1,), ref.x[0])
     np.testing.assert_array_equal(sim.tile_counts(), counts)
@@ -157,13 +160,14 @@ def test_fp32_tiled_one_step_matches_oracle(case):
     sim.close()
 
 
-def test_fp32_tiled_many_steps_close_to_oracle():
+@pytest.mark.parametrize("sort_period", [1, 3, 8])
+def test_fp32_tiled_many_steps_close_to_oracle(sort_period):
     ndim, nx, tile, ppc, uth = CASES_32["3d_8x8x8"]
     dx = (0.1, 0.1, 0.1)
     g = workload.Grid(ndim=3, nx=nx, dx=dx, dt=workload.courant_dt(dx, 3))
     sp = workload.Species(ppc=ppc, uth=(uth,) * 3, seed=4321)
     ref = oracle.from_workload(g, [sp])
-    sim = _sim(g, [sp], "fp32", tile=tile)
+    sim = _sim(g, [sp], "fp32", tile=tile, sort_period=sort_period)
     ref.step(20)
     sim.step(20)
     x, u = sim.particles()

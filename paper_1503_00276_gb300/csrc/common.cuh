@@ -100,11 +100,20 @@ __device__ inline bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 
-// Bounded wait: gives up after `limit` polls and returns false.
-__device__ inline bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, long long limit) {
-  for (long long it = 0; it < limit; ++it)
+__device__ inline uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Bounded wait: gives up after limit_ns nanoseconds and returns false.
+__device__ inline bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, long long limit_ns) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  for (;;) {
     if (mbar_try_wait(bar, parity)) return true;
-  return false;
+    if ((long long)(global_ns() - t0) > limit_ns) return false;
+  }
 }
 
 __device__ inline void fence_barrier_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }

@@ -34,7 +34,7 @@ constexpr int kPPT = 4;                      // consecutive particles per thread
 constexpr int kChunk = kThreads * kPPT;      // 1024
 constexpr int kQCap = 320;                   // crossing queue entries
 constexpr uint32_t kHoleCell = 0xFFFFFFFFu;  // cell word of an empty slot
-constexpr long long kWaitLimit = 1ll << 26;  // bounded mbarrier poll
+constexpr long long kWaitLimit = 2000000000ll;  // mbarrier waits give up after 2 s
 
 struct TileArgs {
   int nt[3];

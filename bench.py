@@ -62,6 +62,9 @@ def parse():
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-fp64", action="store_true")
     p.add_argument("--fp64-steps", type=int, default=3)
+    p.add_argument("--scan-steps", type=int, default=20,
+                   help="timed steps of the batched-scan comparison (64 runs, batched vs one by one)")
+    p.add_argument("--no-scan", action="store_true")
     return p.parse_args()
 
 
@@ -290,6 +293,9 @@ def run_ours(args):
     if not args.no_e2e:
         out["e2e"] = run_e2e(args, g, sps, n_p, tile, barrier, max_over_ranks, sum_over_ranks)
 
+    if not args.no_scan:
+        out["batch_scan"] = run_batch_scan(args, max_over_ranks)
+
     if rank == 0 and ws == 1 and not args.no_cpu:
         out["cpu_baseline"] = run_cpu_baseline(args, budget_s=15.0)
     if rank == 0:
@@ -297,6 +303,51 @@ def run_ours(args):
     if dist is not None:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def run_batch_scan(args, max_over_ranks):
+    """The batched parameter scan: 64 independent 2D3V runs of uneven size
+    (81.7M electrons in all), advanced as one batch (one tile-kernel launch and
+    one CUDA graph launch per step) versus one by one through pic_step.  Both
+    read the device status back after every step."""
+    import torch
+
+    import paper_1503_00276_gb300 as pg
+    import workload
+
+    sims, _ = workload.config4()
+    n_p = sum(workload.n_particles(g, s[0]) for g, s in sims)
+    K, W = args.scan_steps, 3
+    stream = torch.cuda.current_stream()
+
+    def timed(step):
+        step(W)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step(K)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
+    batch = pg.Batch(sims)
+    ms_b = max_over_ranks(timed(batch.step))
+    info = batch.info()
+    batch.close()
+    del batch
+    ms_s = 0.0
+    for g, sps in sims:
+        s = pg.Simulation(g, sps, precision="fp32")
+        ms_s += timed(s.step)
+        s.close()
+    ms_s = max_over_ranks(ms_s)
+    return {"workload": "64 x 2D3V runs drawn from the scan seed (128x64 .. 1024x512 cells, 4-32 ppc, density "
+                        "0.5-2, transverse momentum a0 0.5-3 standing in for the laser), 81.7M electrons",
+            "members": len(sims), "particles": n_p, "steps": K, "warmup": W, "tile": list(info["tile"]),
+            "batched": {"value": n_p * K / (ms_b / 1e3), "unit": UNIT, "ms_per_step": ms_b / K,
+                        "launches_per_step": info["launches"] / max(info["steps"], 1)},
+            "sequential": {"value": n_p * K / (ms_s / 1e3), "unit": UNIT, "ms_per_step": ms_s / K},
+            "speedup": ms_s / ms_b}
 
 
 def run_e2e(args, g, sps, n_p, tile, barrier, max_over_ranks, sum_over_ranks):

@@ -259,6 +259,48 @@ pic_status pic_bin_tiles(const int nx[3], const int tile[3], long long n, const 
 pic_status pic_bin_tiles_noalloc(const int nx[3], const int tile[3], long long n, const int* cell,
                                  int* tile_count, long long* tile_start, long long* perm, void* stream);
 
+
+/* ---- Batched parameter scan ------------------------------------------------
+ * The thesis runs one simulation at a time; a parameter scan (many independent
+ * 2D/3D runs of uneven grid sizes and particle counts) is advanced here as one
+ * batch, so that small runs share the GPU instead of each leaving most SMs
+ * idle.  Every step of every member is the same step pic_step takes (gather,
+ * Boris push, move and Villasenor-Buneman deposit of section 2.2, current fold,
+ * smoothing and Yee solve of section 2.1), but the particle step of all members
+ * is ONE launch of the persistent sorting tile kernel, whose work items are the
+ * tiles of all members, and the whole step of the batch is one CUDA graph
+ * launch (captured once per store side; re-captured after a member re-bins).
+ */
+typedef struct pic_batch pic_batch;
+
+/* nsims simulations: grids[i] with species[i*nspecies .. i*nspecies+nspecies-1].
+ * Every grid must be PIC_FP32_CELLOFF with the same ndim and the same tile
+ * field; tile {0,0,0} picks the first shape that divides every grid (3D 8x8x8,
+ * 16x8x4; 2D 32x16, 16x16, 8x8).  sort_period is forced to 1.  Device memory
+ * comes from `alloc` (NULL: cudaMalloc); all work is enqueued on `stream`.
+ * Errors: PIC_EINVAL for mismatched grids (message names the member),
+ * PIC_ENOMEM, PIC_ECUDA, plus every error pic_init reports for a member. */
+pic_status pic_batch_init(int nsims, const pic_grid* grids, const pic_species* species, int nspecies,
+                          const pic_allocator* alloc, void* stream, pic_batch** out);
+
+/* Advance every member nsteps steps.  After each step the members' device
+ * status words are read back once (one synchronisation per step): a member
+ * whose tile storage spilled is re-binned before the next step; PIC_ETIMEOUT /
+ * PIC_ENONFINITE / PIC_EOVERFLOW name the member. */
+pic_status pic_batch_step(pic_batch* B, int nsteps);
+
+/* Borrowed handle of member i for pic_fields, pic_particles, pic_particle_ids,
+ * pic_tile_counts and pic_diag.  pic_step and pic_destroy must not be called on
+ * it (pic_step returns PIC_EINVAL); it lives until pic_batch_destroy. */
+pic_status pic_batch_sim(pic_batch* B, int i, pic_sim** out);
+
+/* Steps taken, kernel launches enqueued by pic_batch_step (every graph node
+ * that is a kernel), and the tile shape in use; any pointer may be NULL. */
+pic_status pic_batch_info(const pic_batch* B, long long* steps, long long* launches, int tile[3]);
+
+/* Frees every member and the batch; synchronises its stream first. */
+pic_status pic_batch_destroy(pic_batch* B);
+
 #ifdef __cplusplus
 }
 #endif

@@ -19,7 +19,7 @@ import numpy as np
 from . import _capi
 from ._capi import FIELD_NAMES, PIC_FP32_CELLOFF, PIC_FP64_PLAIN, PicError, check, load  # noqa: F401
 
-__all__ = ["Simulation", "bin_tiles", "bin_tiles_noalloc", "load", "PicError", "PIC_FP64_PLAIN", "PIC_FP32_CELLOFF", "FIELD_NAMES"]
+__all__ = ["Simulation", "Batch", "bin_tiles", "bin_tiles_noalloc", "load", "PicError", "PIC_FP64_PLAIN", "PIC_FP32_CELLOFF", "FIELD_NAMES"]
 
 
 def _torch():
@@ -292,3 +292,100 @@ def bin_tiles_noalloc(nx, tile, cell, stream=None):
                                     C.c_void_p(start.data_ptr()), C.c_void_p(perm.data_ptr()),
                                     C.c_void_p(st.cuda_stream)), "pic_bin_tiles_noalloc")
     return counts, start, perm[:n]
+
+
+class _Member(Simulation):
+    """Borrowed handle of one member of a Batch: read-out and set_field only."""
+
+    def __init__(self, batch, handle, grid, nspecies):
+        self._lib = batch._lib
+        self._torch = batch._torch
+        self._batch = batch  # keeps the batch alive
+        self._h = handle
+        self.precision = PIC_FP32_CELLOFF
+        self.ndim = int(grid.ndim)
+        self.shape = (int(grid.nx[2]) if grid.ndim == 3 else 1, int(grid.nx[1]), int(grid.nx[0]))
+        self.nspecies = nspecies
+        self.stream = batch.stream
+        self._alloc = None
+
+    def close(self):
+        self._h = None  # owned by the batch
+
+    def step(self, n: int = 1):
+        raise RuntimeError("a batch member is stepped by Batch.step")
+
+
+class Batch:
+    """Many independent FP32 cell-offset simulations advanced together
+    (pic_batch_init ... pic_batch_destroy): one persistent tile-kernel launch
+    for the particles of all members and one CUDA graph launch per step.
+
+    ``members``: list of (grid, [species, ...]) with the same number of
+    species each.  ``tile``: common tile shape (None: the library's choice).
+    """
+
+    def __init__(self, members, tile=None, track_ids=False, slack=0.0, stream=None, use_torch_allocator=True):
+        self._lib = load()
+        torch = _torch()
+        self._torch = torch
+        n = len(members)
+        nsp = len(members[0][1])
+        assert n >= 1 and nsp >= 1 and all(len(m[1]) == nsp for m in members)
+        grids = (_capi.PicGrid * n)()
+        specs = (_capi.PicSpecies * (n * nsp))()
+        for i, (g, sps) in enumerate(members):
+            grids[i] = _grid_struct(g, PIC_FP32_CELLOFF, tile, slack, 1)
+            for k, sp in enumerate(sps):
+                specs[i * nsp + k] = _species_struct(sp, None, track_ids)[0]
+        self._members = members
+        self.nspecies = nsp
+        self._alloc = None
+        stream_ptr = None
+        if torch is not None and torch.cuda.is_available():
+            st = stream if stream is not None else torch.cuda.current_stream()
+            self.stream = st
+            stream_ptr = C.c_void_p(st.cuda_stream)
+            if use_torch_allocator:
+                self._alloc = _TorchAllocator(torch, torch.cuda.current_device(), st)
+        else:
+            self.stream = None
+        h = C.c_void_p()
+        code = self._lib.pic_batch_init(n, grids, specs, nsp, C.byref(self._alloc.struct) if self._alloc else None,
+                                        stream_ptr, C.byref(h))
+        check(code, "pic_batch_init")
+        self._h = h
+
+    def __len__(self):
+        return len(self._members)
+
+    def step(self, n: int = 1):
+        check(self._lib.pic_batch_step(self._h, int(n)), "pic_batch_step")
+
+    def sim(self, i: int) -> Simulation:
+        h = C.c_void_p()
+        check(self._lib.pic_batch_sim(self._h, int(i), C.byref(h)), "pic_batch_sim")
+        return _Member(self, h, self._members[i][0], self.nspecies)
+
+    def info(self) -> dict:
+        steps, launches = C.c_longlong(), C.c_longlong()
+        tile = (C.c_int * 3)()
+        check(self._lib.pic_batch_info(self._h, C.byref(steps), C.byref(launches), tile), "pic_batch_info")
+        return {"steps": int(steps.value), "launches": int(launches.value), "tile": tuple(tile)}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.pic_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

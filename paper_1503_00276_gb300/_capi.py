@@ -65,6 +65,12 @@ PROTOTYPES = {
     "pic_bin_tiles": (C.c_int, [C.POINTER(C.c_int), C.POINTER(C.c_int), C.c_longlong, _P, _P, _P, _P,
                                 C.POINTER(PicAllocator), _P]),
     "pic_bin_tiles_noalloc": (C.c_int, [C.POINTER(C.c_int), C.POINTER(C.c_int), C.c_longlong, _P, _P, _P, _P, _P]),
+    "pic_batch_init": (C.c_int, [C.c_int, C.POINTER(PicGrid), C.POINTER(PicSpecies), C.c_int, C.POINTER(PicAllocator),
+                                 _P, C.POINTER(_P)]),
+    "pic_batch_step": (C.c_int, [_P, C.c_int]),
+    "pic_batch_sim": (C.c_int, [_P, C.c_int, C.POINTER(_P)]),
+    "pic_batch_info": (C.c_int, [_P, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong), C.POINTER(C.c_int)]),
+    "pic_batch_destroy": (C.c_int, [_P]),
 }
 BIN_NOALLOC_SCRATCH_BYTES = 16 << 20
 

@@ -153,6 +153,8 @@ struct pic_sim {
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_pending;
   int sticky_flags = 0;
   long long nlaunch = 0;  // kernels launched by pic_step since the last reset
+  bool no_small = false;  // member of a batch: the general tile kernel only
+  bool in_batch = false;  // stepped by its batch; pic_step refuses it
 };
 
 namespace {
@@ -407,7 +409,8 @@ pic_status bin_flat(pic_sim* S, SpeciesState& sp, Flat32& flat, long long n) {
   }
   long long max_cap = 0;
   for (int t = 0; t < nt; ++t) max_cap = std::max<long long>(max_cap, hcap[t]);
-  sp.tg.small = tiled_has_small(S->ndim, S->T) && (max_cap <= tiled_small_capacity() || !tiled_has_general(S->ndim, S->T));
+  sp.tg.small = !S->no_small && tiled_has_small(S->ndim, S->T) &&
+                (max_cap <= tiled_small_capacity() || !tiled_has_general(S->ndim, S->T));
   sp.grid = tiled_push_grid(S->ndim, S->T, nt, sp.tg.small != 0);
   sp.grid_stream = tiled_stream_grid(S->ndim, S->T, nt);
   cudaMemcpyAsync(sp.tg.cap, hcap.data(), 4 * (size_t)nt, cudaMemcpyHostToDevice, S->s);
@@ -869,8 +872,19 @@ pic_status pic_destroy(pic_sim* S) {
   return PIC_OK;
 }
 
+namespace {
+pic_status init_sim(const pic_grid* grid, const pic_species* species, int nspecies, const pic_allocator* alloc,
+                    void* stream, bool no_small, pic_sim** out);
+}
+
 pic_status pic_init(const pic_grid* grid, const pic_species* species, int nspecies, const pic_allocator* alloc,
                     void* stream, pic_sim** out) {
+  return init_sim(grid, species, nspecies, alloc, stream, false, out);
+}
+
+namespace {
+pic_status init_sim(const pic_grid* grid, const pic_species* species, int nspecies, const pic_allocator* alloc,
+                    void* stream, bool no_small, pic_sim** out) {
   if (!out) {
     set_error("out is NULL");
     return PIC_EINVAL;
@@ -889,6 +903,7 @@ pic_status pic_init(const pic_grid* grid, const pic_species* species, int nspeci
     return PIC_ECUDA;
   }
   pic_sim* S = new pic_sim();
+  S->no_small = no_small;
   S->g = *grid;
   S->ndim = grid->ndim;
   S->prec = grid->precision;
@@ -1007,10 +1022,15 @@ pic_status pic_init(const pic_grid* grid, const pic_species* species, int nspeci
   *out = S;
   return PIC_OK;
 }
+}  // namespace
 
 pic_status pic_step(pic_sim* S, int nsteps) {
   if (!S || nsteps < 0) {
     set_error("pic_step: bad arguments");
+    return PIC_EINVAL;
+  }
+  if (S->in_batch) {
+    set_error("pic_step: this simulation belongs to a batch; step it with pic_batch_step");
     return PIC_EINVAL;
   }
   pic_status st = PIC_OK;
@@ -1317,6 +1337,331 @@ pic_status pic_timing_read(pic_sim* S, double* ms, long long* launches, int nslo
     }
     S->nlaunch = 0;
   }
+  return PIC_OK;
+}
+
+
+// ------------------------------------------------------------- batched scan
+
+struct pic_batch {
+  std::vector<pic_sim*> sims;
+  std::vector<std::pair<int, int>> ent;  // (simulation, species) of each table entry
+  cudaStream_t s = nullptr;      // the batch's own stream (capturable): all member work after set-up
+  cudaStream_t user = nullptr;   // the caller's stream
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  Allocator al;
+  int ndim = 0;
+  int T[3] = {1, 1, 1};
+  void* d_args[2] = {nullptr, nullptr};  // entry tables for store side 0 / 1 as input
+  CUtensorMap* d_fmaps = nullptr;
+  CUtensorMap* d_jmaps = nullptr;
+  int* d_tile0 = nullptr;
+  int* d_work = nullptr;
+  StatusWord* d_stat = nullptr;  // one per simulation
+  StatusWord* h_stat = nullptr;  // pinned mirror
+  int grid = 0;
+  bool use_graph = true;
+  bool dirty = true;  // tables / graphs must be rebuilt before the next step
+  cudaGraphExec_t exec[2] = {nullptr, nullptr};
+  long long step = 0;
+  long long nlaunch = 0;
+};
+
+namespace {
+
+void batch_drop_graphs(pic_batch* B) {
+  for (int p = 0; p < 2; ++p)
+    if (B->exec[p]) {
+      cudaGraphExecDestroy(B->exec[p]);
+      B->exec[p] = nullptr;
+    }
+}
+
+// Everything one step enqueues for all simulations, store side p as input.
+void batch_enqueue(pic_batch* B, int p) {
+  for (pic_sim* S : B->sims) cudaMemsetAsync(S->cur, 0, 3 * 4 * (size_t)S->L.plane, B->s);
+  for (auto& e : B->ent) {
+    SpeciesState& sp = B->sims[e.first]->sp[e.second];
+    cudaMemsetAsync(sp.side[1 - p].inc, 0, 4 * (size_t)sp.tg.ntiles, B->s);
+  }
+  tiled_push_batch(B->ndim, B->T, B->d_args[p], B->d_fmaps, B->d_jmaps, B->d_tile0, (int)B->ent.size(), B->d_work,
+                   B->grid, B->s);
+  for (pic_sim* S : B->sims) field_step<float>(S);
+}
+
+long long batch_launches_per_step(const pic_batch* B) {
+  long long n = 1;
+  for (const pic_sim* S : B->sims) {
+    n += 5;  // fold, B half, E, B half, fill
+    for (int d = 0; d < S->ndim; ++d) n += 3 * (long long)S->g.smooth_level[d];
+  }
+  return n;
+}
+
+pic_status batch_build(pic_batch* B) {
+  batch_drop_graphs(B);
+  const int n = (int)B->ent.size();
+  const size_t ab = tiled_args_bytes();
+  std::vector<unsigned char> args(ab * n);
+  std::vector<CUtensorMap> fm(B->sims.size()), jm(B->sims.size());
+  std::vector<CUtensorMap> fme(n), jme(n);
+  std::vector<int> tile0(n + 1, 0);
+  for (int p = 0; p < 2; ++p) {
+    for (int k = 0; k < n; ++k) {
+      pic_sim* S = B->sims[B->ent[k].first];
+      SpeciesState& sp = S->sp[B->ent[k].second];
+      if (sp.tg.small) {
+        set_error("pic_batch: a member simulation uses the small-tile kernel");
+        return PIC_EUNSUPPORTED;
+      }
+      PushConst C = make_const(S, sp);
+      StatusWord* st = S->dstat;
+      tiled_fill_args(args.data() + ab * k, C, sp.tg, sp.side[p], sp.side[1 - p], sp.spill, &st->spill_count,
+                      sp.spill_cap, &st->status);
+      if (p == 0) {
+        fme[k] = S->fmap;
+        jme[k] = S->jmap;
+        tile0[k + 1] = tile0[k] + sp.tg.ntiles;
+      }
+    }
+    cudaMemcpyAsync(B->d_args[p], args.data(), ab * n, cudaMemcpyHostToDevice, B->s);
+  }
+  cudaMemcpyAsync(B->d_fmaps, fme.data(), sizeof(CUtensorMap) * n, cudaMemcpyHostToDevice, B->s);
+  cudaMemcpyAsync(B->d_jmaps, jme.data(), sizeof(CUtensorMap) * n, cudaMemcpyHostToDevice, B->s);
+  cudaMemcpyAsync(B->d_tile0, tile0.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice, B->s);
+  B->grid = tiled_batch_grid(B->ndim, B->T, tile0[n]);
+  if (B->grid <= 0) {
+    set_error("pic_batch: tile shape not supported by the batched kernel");
+    return PIC_EUNSUPPORTED;
+  }
+  if (cudaStreamSynchronize(B->s) != cudaSuccess) return cuda_check("pic_batch tables");
+  if (B->use_graph) {
+    for (int p = 0; p < 2; ++p) {
+      cudaGraph_t g = nullptr;
+      if (cudaStreamBeginCapture(B->s, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+        return cuda_check("pic_batch capture");
+      batch_enqueue(B, p);
+      if (cudaStreamEndCapture(B->s, &g) != cudaSuccess) return cuda_check("pic_batch capture");
+      const cudaError_t e = cudaGraphInstantiate(&B->exec[p], g, 0);
+      cudaGraphDestroy(g);
+      if (e != cudaSuccess) return cuda_check("pic_batch graph");
+    }
+  }
+  B->dirty = false;
+  return cuda_check("pic_batch build");
+}
+
+}  // namespace
+
+pic_status pic_batch_init(int nsims, const pic_grid* grids, const pic_species* species, int nspecies,
+                          const pic_allocator* alloc, void* stream, pic_batch** out) {
+  if (!out || nsims < 1 || !grids || nspecies < 1 || !species) {
+    set_error("pic_batch_init: bad arguments");
+    return PIC_EINVAL;
+  }
+  *out = nullptr;
+  const int ndim = grids[0].ndim;
+  for (int i = 0; i < nsims; ++i) {
+    if (grids[i].precision != PIC_FP32_CELLOFF || grids[i].ndim != ndim) {
+      set_error("pic_batch_init: every simulation must be FP32 cell-offset with the same ndim");
+      return PIC_EINVAL;
+    }
+    for (int d = 0; d < 3; ++d)
+      if (grids[i].tile[d] != grids[0].tile[d]) {
+        set_error("pic_batch_init: every simulation must use the same tile shape");
+        return PIC_EINVAL;
+      }
+  }
+  // tile shape: the given one, else the first general shape dividing every grid
+  int T[3] = {grids[0].tile[0], grids[0].tile[1], ndim == 3 ? grids[0].tile[2] : 1};
+  if (T[0] <= 0) {
+    static const int c3[][3] = {{8, 8, 8}, {16, 8, 4}};
+    static const int c2[][3] = {{32, 16, 1}, {16, 16, 1}, {8, 8, 1}};
+    const int nc = ndim == 3 ? 2 : 3;
+    T[0] = 0;
+    for (int k = 0; k < nc && T[0] == 0; ++k) {
+      const int* c = ndim == 3 ? c3[k] : c2[k];
+      bool fits = true;
+      for (int i = 0; i < nsims; ++i)
+        for (int d = 0; d < ndim; ++d) fits = fits && grids[i].nx[d] % c[d] == 0;
+      if (fits)
+        for (int d = 0; d < 3; ++d) T[d] = c[d];
+    }
+    if (T[0] == 0) {
+      set_error("pic_batch_init: no batched tile shape divides every grid");
+      return PIC_EINVAL;
+    }
+  }
+  pic_batch* B = new pic_batch();
+  B->user = reinterpret_cast<cudaStream_t>(stream);
+  if (cudaStreamCreateWithFlags(&B->s, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&B->ev_in, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&B->ev_out, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    set_error("pic_batch_init: stream or event creation failed");
+    pic_batch_destroy(B);
+    return PIC_ECUDA;
+  }
+  B->ndim = ndim;
+  for (int d = 0; d < 3; ++d) B->T[d] = T[d];
+  if (alloc && alloc->alloc) {
+    B->al.user = *alloc;
+    B->al.has_user = true;
+  }
+  if (const char* e = getenv("PICGB_BATCH_GRAPH")) B->use_graph = atoi(e) != 0;
+  auto bail = [&](pic_status code) {
+    pic_batch_destroy(B);
+    return code;
+  };
+  for (int i = 0; i < nsims; ++i) {
+    pic_grid g = grids[i];
+    for (int d = 0; d < 3; ++d) g.tile[d] = T[d];
+    g.sort_period = 1;
+    pic_sim* S = nullptr;
+    const pic_status st = init_sim(&g, species + (size_t)i * nspecies, nspecies, alloc, stream, true, &S);
+    if (st != PIC_OK) {
+      const std::string msg = "simulation " + std::to_string(i) + ": " + g_err;
+      set_error(msg);
+      return bail(st);
+    }
+    B->sims.push_back(S);
+    for (int k = 0; k < nspecies; ++k) B->ent.push_back({i, k});
+  }
+  const int n = (int)B->ent.size();
+  B->d_args[0] = B->al.get(tiled_args_bytes() * n);
+  B->d_args[1] = B->al.get(tiled_args_bytes() * n);
+  B->d_fmaps = (CUtensorMap*)B->al.get(sizeof(CUtensorMap) * n);
+  B->d_jmaps = (CUtensorMap*)B->al.get(sizeof(CUtensorMap) * n);
+  B->d_tile0 = (int*)B->al.get(sizeof(int) * (n + 1));
+  B->d_work = (int*)B->al.get(sizeof(int));
+  B->d_stat = (StatusWord*)B->al.get(sizeof(StatusWord) * nsims);
+  if (!B->d_args[0] || !B->d_args[1] || !B->d_fmaps || !B->d_jmaps || !B->d_tile0 || !B->d_work || !B->d_stat) {
+    set_error("pic_batch_init: out of device memory (tables)");
+    return bail(PIC_ENOMEM);
+  }
+  if (cudaMallocHost(&B->h_stat, sizeof(StatusWord) * nsims) != cudaSuccess) {
+    B->h_stat = nullptr;
+    set_error("pic_batch_init: pinned host allocation failed");
+    return bail(PIC_ENOMEM);
+  }
+  cudaMemsetAsync(B->d_stat, 0, sizeof(StatusWord) * nsims, B->s);
+  // every member reports into the batch's status array and runs on the
+  // batch's stream from now on (the members were set up on the caller's
+  // stream, which pic_init synchronised)
+  for (int i = 0; i < nsims; ++i) {
+    pic_sim* S = B->sims[i];
+    if (S->hstat) cudaFreeHost(S->hstat);
+    S->hstat = B->h_stat + i;
+    S->dstat = B->d_stat + i;
+    S->s = B->s;
+    S->in_batch = true;
+  }
+  const pic_status st = batch_build(B);
+  if (st != PIC_OK) return bail(st);
+  *out = B;
+  return PIC_OK;
+}
+
+pic_status pic_batch_step(pic_batch* B, int nsteps) {
+  if (!B || nsteps < 0) {
+    set_error("pic_batch_step: bad arguments");
+    return PIC_EINVAL;
+  }
+  const int nsims = (int)B->sims.size();
+  // order after the caller's earlier work; the caller's stream waits for the batch at the end
+  cudaEventRecord(B->ev_in, B->user);
+  cudaStreamWaitEvent(B->s, B->ev_in, 0);
+  struct Join {
+    pic_batch* B;
+    ~Join() {
+      cudaEventRecord(B->ev_out, B->s);
+      cudaStreamWaitEvent(B->user, B->ev_out, 0);
+    }
+  } join{B};
+  for (int k = 0; k < nsteps; ++k) {
+    if (B->dirty) {
+      const pic_status st = batch_build(B);
+      if (st != PIC_OK) return st;
+    }
+    const int p = B->sims[0]->sp[0].cur;
+    if (B->use_graph) {
+      if (cudaGraphLaunch(B->exec[p], B->s) != cudaSuccess) return cuda_check("pic_batch_step graph launch");
+    } else {
+      batch_enqueue(B, p);
+    }
+    B->nlaunch += batch_launches_per_step(B);
+    for (pic_sim* S : B->sims) {
+      for (auto& sp : S->sp) sp.cur = 1 - sp.cur;
+      ++S->step;
+    }
+    ++B->step;
+    cudaMemcpyAsync(B->h_stat, B->d_stat, sizeof(StatusWord) * nsims, cudaMemcpyDeviceToHost, B->s);
+    if (cudaStreamSynchronize(B->s) != cudaSuccess) return cuda_check("pic_batch_step");
+    for (int i = 0; i < nsims; ++i) {
+      pic_sim* S = B->sims[i];
+      const int flags = B->h_stat[i].status;
+      S->sticky_flags |= flags;
+      if (flags & ST_SPILL) {
+        if (flags & ST_SPILL_LOST) {
+          set_error("pic_batch_step: simulation " + std::to_string(i) + ": spill list overflowed");
+          return PIC_EOVERFLOW;
+        }
+        for (auto& sp : S->sp) {
+          const pic_status st = rebuild(S, sp, B->h_stat[i].spill_count);
+          if (st != PIC_OK) return st;
+        }
+        cudaMemsetAsync(S->dstat, 0, sizeof(StatusWord), B->s);
+        B->dirty = true;
+      }
+      if (flags & ST_TIMEOUT) {
+        set_error("pic_batch_step: simulation " + std::to_string(i) + ": a bounded device wait gave up");
+        return PIC_ETIMEOUT;
+      }
+      if (flags & (ST_NONFINITE | ST_BADCELL)) {
+        set_error("pic_batch_step: simulation " + std::to_string(i) + ": non-finite particle or field value");
+        return PIC_ENONFINITE;
+      }
+    }
+  }
+  return cuda_check("pic_batch_step");
+}
+
+pic_status pic_batch_sim(pic_batch* B, int i, pic_sim** out) {
+  if (!B || !out || i < 0 || i >= (int)B->sims.size()) {
+    set_error("pic_batch_sim: bad arguments");
+    return PIC_EINVAL;
+  }
+  *out = B->sims[i];
+  return PIC_OK;
+}
+
+pic_status pic_batch_info(const pic_batch* B, long long* steps, long long* launches, int tile[3]) {
+  if (!B) {
+    set_error("pic_batch_info: bad arguments");
+    return PIC_EINVAL;
+  }
+  if (steps) *steps = B->step;
+  if (launches) *launches = B->nlaunch;
+  if (tile)
+    for (int d = 0; d < 3; ++d) tile[d] = B->T[d];
+  return PIC_OK;
+}
+
+pic_status pic_batch_destroy(pic_batch* B) {
+  if (!B) return PIC_OK;
+  if (B->s) cudaStreamSynchronize(B->s);
+  batch_drop_graphs(B);
+  for (pic_sim* S : B->sims) {
+    S->hstat = nullptr;  // the batch's pinned array
+    S->s = B->user;      // the allocator frees on the caller's stream
+    pic_destroy(S);
+  }
+  B->al.release_all();
+  if (B->h_stat) cudaFreeHost(B->h_stat);
+  if (B->ev_in) cudaEventDestroy(B->ev_in);
+  if (B->ev_out) cudaEventDestroy(B->ev_out);
+  if (B->s) cudaStreamDestroy(B->s);
+  delete B;
   return PIC_OK;
 }
 

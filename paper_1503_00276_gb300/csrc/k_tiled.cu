@@ -23,6 +23,8 @@
 //   * one TMA reduce-add flushes the shared current tile (with halo) into HBM.
 // The store is therefore re-binned by tile and re-sorted by cell every step
 // without a separate pass over HBM.
+#include <cstring>
+
 #include "kernels.h"
 
 namespace picgb {
@@ -564,11 +566,14 @@ __device__ inline void sort_and_store(const TileArgs& A, int t, int tix, int tiy
   ws += nst;
 }
 
-template <int NDIM, int TX, int TY, int TZ, int MINB>
-__global__ void __launch_bounds__(kThreads, MINB)
-    k_tile_push(const __grid_constant__ CUtensorMap fmap, const __grid_constant__ CUtensorMap jmap, TileArgs A) {
+// Everything the sorting kernel does for tile t of one simulation (A): stage
+// the fields, advance, sort and store every particle of the tile, flush the
+// current.  Called by all threads of the block; false if a bounded wait gave
+// up (the block then stops).
+template <int NDIM, int TX, int TY, int TZ>
+__device__ inline bool sort_tile(const TileArgs& A, const CUtensorMap* fmap, const CUtensorMap* jmap, int t,
+                                 unsigned char* smem, uint32_t& phase) {
   using G = Geo<NDIM, TX, TY, TZ>;
-  extern __shared__ __align__(1024) unsigned char smem[];
   float* F = reinterpret_cast<float*>(smem + G::FOFF);
   float* J = reinterpret_cast<float*>(smem + G::JOFF);
   int* hist = reinterpret_cast<int*>(smem + G::HOFF);
@@ -576,7 +581,124 @@ __global__ void __launch_bounds__(kThreads, MINB)
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + G::MOFF);
   int* misc = reinterpret_cast<int*>(smem + G::MOFF + 16);  // [0] tile [1] queue [6] stayers [7] total [8..15] scan
   const int tid = threadIdx.x;
+  const int tix = t % A.nt[0], tiy = (t / A.nt[0]) % A.nt[1], tiz = t / (A.nt[0] * A.nt[1]);
+  const int x0 = tix * TX, y0 = tiy * TY, z0 = tiz * TZ;
+  if (tid == 0) {
+    mbar_arrive_expect_tx(bar, (uint32_t)G::FBYTES);
+    if (NDIM == 3)
+      tma_load_4d(F, fmap, bar, x0, y0, z0, 0);
+    else
+      tma_load_3d(F, fmap, bar, x0, y0, 0);
+  }
+  for (int k = tid; k < 3 * G::JPL; k += kThreads) J[k] = 0.f;
+  const long long base = A.base[t];
+  const int cap = A.cap[t];
+  const int res = A.res[t];
+  const int nstay = A.in.stay[t];
+  int ninc = A.in.inc[t];
+  ninc = ninc < res ? ninc : res;
+  const int room = cap - res;  // stayer slots of the output region
+  const bool ok = mbar_wait_bounded(bar, phase, kWaitLimit);
+  if (__syncthreads_or(!ok)) {  // every thread takes the same decision
+    if (tid == 0) atomicOr(A.status, ST_TIMEOUT);
+    mbar_wait_bounded(bar, phase, kWaitLimit);
+    return false;
+  }
+  phase ^= 1u;
 
+  int ws = 0;
+  // chunks over the stayers (front, 16-byte aligned) then the arrivals (back)
+  const int nchunk_s = (nstay + kChunk - 1) / kChunk;
+  const int nchunk_i = (ninc + kChunk - 1) / kChunk;
+  for (int ch = 0; ch < nchunk_s + nchunk_i; ++ch) {
+    P pp[kPPT];
+    int key[kPPT];
+    int nvalid;
+    if (ch < nchunk_s) {
+      const int first = ch * kChunk + tid * kPPT;
+      nvalid = nstay - first;
+      nvalid = nvalid < 0 ? 0 : (nvalid > kPPT ? kPPT : nvalid);
+      if (nvalid > 0) {
+        const long long s = base + first;
+        const uint4 cl = *reinterpret_cast<const uint4*>(A.in.p.cell + s);
+        const float4 q0 = *reinterpret_cast<const float4*>(A.in.p.o[0] + s);
+        const float4 q1 = *reinterpret_cast<const float4*>(A.in.p.o[1] + s);
+        float4 q2 = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (NDIM == 3) q2 = *reinterpret_cast<const float4*>(A.in.p.o[2] + s);
+        const float4 v0 = *reinterpret_cast<const float4*>(A.in.p.u[0] + s);
+        const float4 v1 = *reinterpret_cast<const float4*>(A.in.p.u[1] + s);
+        const float4 v2 = *reinterpret_cast<const float4*>(A.in.p.u[2] + s);
+        int4 idv = make_int4(0, 0, 0, 0);
+        if (A.in.p.id) idv = *reinterpret_cast<const int4*>(A.in.p.id + s);
+        pp[0] = P{cl.x, q0.x, q1.x, q2.x, v0.x, v1.x, v2.x, idv.x};
+        pp[1] = P{cl.y, q0.y, q1.y, q2.y, v0.y, v1.y, v2.y, idv.y};
+        pp[2] = P{cl.z, q0.z, q1.z, q2.z, v0.z, v1.z, v2.z, idv.z};
+        pp[3] = P{cl.w, q0.w, q1.w, q2.w, v0.w, v1.w, v2.w, idv.w};
+      }
+    } else {
+      const int first = (ch - nchunk_s) * kChunk + tid * kPPT;
+      nvalid = ninc - first;
+      nvalid = nvalid < 0 ? 0 : (nvalid > kPPT ? kPPT : nvalid);
+#pragma unroll
+      for (int r = 0; r < kPPT; ++r) {
+        if (r < nvalid) {
+          const long long s = base + cap - ninc + first + r;
+          pp[r] = P{A.in.p.cell[s], A.in.p.o[0][s], A.in.p.o[1][s], NDIM == 3 ? A.in.p.o[2][s] : 0.f,
+                    A.in.p.u[0][s], A.in.p.u[1][s], A.in.p.u[2][s], A.in.p.id ? A.in.p.id[s] : 0};
+        }
+      }
+    }
+    {
+      Acc acc;
+#pragma unroll
+      for (int k = 0; k < 12; ++k) acc.w[k] = 0.f;
+      acc.cell = -1;
+#pragma unroll
+      for (int r = 0; r < kPPT; ++r)
+        key[r] = r < nvalid ? push_one<NDIM, TX, TY, TZ>(F, J, A, pp[r], acc, Q, misc + 1)
+                                                    : Geo<NDIM, TX, TY, TZ>::NK;
+      acc_flush<NDIM, TX, TY, TZ>(J, acc);
+    }
+    sort_and_store<NDIM, TX, TY, TZ>(A, t, tix, tiy, tiz, base, room, pp, key, nvalid, ws, hist, misc);
+    __syncthreads();
+    const int nq = misc[1];
+    if (nq > kQCap / 2) {
+      drain_queue<NDIM, TX, TY, TZ>(J, A, Q, nq < kQCap ? nq : kQCap);
+      __syncthreads();
+      if (tid == 0) misc[1] = 0;
+      __syncthreads();  // the reset lands before the next chunk queues anything
+    }
+  }
+  __syncthreads();
+  {
+    const int nq = misc[1];
+    if (nq > 0) drain_queue<NDIM, TX, TY, TZ>(J, A, Q, nq < kQCap ? nq : kQCap);
+  }
+  if (tid == 0) A.out.stay[t] = ws < room ? ws : room;
+  // flush the current tile: every thread orders its shared atomics before the
+  // async proxy reads them; one thread issues the TMA reduce-add and waits
+  // until the TMA has read the tile before the next tile reuses it
+  fence_proxy_async_smem();
+  __syncthreads();
+  if (tid == 0) {
+    if (NDIM == 3)
+      tma_reduce_add_4d(jmap, J, x0, y0, z0, 0);
+    else
+      tma_reduce_add_3d(jmap, J, x0, y0, 0);
+    tma_commit();
+    tma_wait_read0();
+  }
+  return true;
+}
+
+template <int NDIM, int TX, int TY, int TZ, int MINB>
+__global__ void __launch_bounds__(kThreads, MINB)
+    k_tile_push(const __grid_constant__ CUtensorMap fmap, const __grid_constant__ CUtensorMap jmap, TileArgs A) {
+  using G = Geo<NDIM, TX, TY, TZ>;
+  extern __shared__ __align__(1024) unsigned char smem[];
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + G::MOFF);
+  int* misc = reinterpret_cast<int*>(smem + G::MOFF + 16);
+  const int tid = threadIdx.x;
   if (tid == 0) {
     mbar_init(bar, 1);
     fence_barrier_init();
@@ -591,116 +713,62 @@ __global__ void __launch_bounds__(kThreads, MINB)
     __syncthreads();
     const int t = misc[0];
     if (t >= A.ntiles) break;
-    const int tix = t % A.nt[0], tiy = (t / A.nt[0]) % A.nt[1], tiz = t / (A.nt[0] * A.nt[1]);
-    const int x0 = tix * TX, y0 = tiy * TY, z0 = tiz * TZ;
-    if (tid == 0) {
-      mbar_arrive_expect_tx(bar, (uint32_t)G::FBYTES);
-      if (NDIM == 3)
-        tma_load_4d(F, &fmap, bar, x0, y0, z0, 0);
-      else
-        tma_load_3d(F, &fmap, bar, x0, y0, 0);
-    }
-    for (int k = tid; k < 3 * G::JPL; k += kThreads) J[k] = 0.f;
-    const long long base = A.base[t];
-    const int cap = A.cap[t];
-    const int res = A.res[t];
-    const int nstay = A.in.stay[t];
-    int ninc = A.in.inc[t];
-    ninc = ninc < res ? ninc : res;
-    const int room = cap - res;  // stayer slots of the output region
-    if (!mbar_wait_bounded(bar, phase, kWaitLimit)) {
-      if (tid == 0) atomicOr(A.status, ST_TIMEOUT);
-      mbar_wait_bounded(bar, phase, kWaitLimit);
-      return;
-    }
-    phase ^= 1u;
-    __syncthreads();
-
-    int ws = 0;
-    // chunks over the stayers (front, 16-byte aligned) then the arrivals (back)
-    const int nchunk_s = (nstay + kChunk - 1) / kChunk;
-    const int nchunk_i = (ninc + kChunk - 1) / kChunk;
-    for (int ch = 0; ch < nchunk_s + nchunk_i; ++ch) {
-      P pp[kPPT];
-      int key[kPPT];
-      int nvalid;
-      if (ch < nchunk_s) {
-        const int first = ch * kChunk + tid * kPPT;
-        nvalid = nstay - first;
-        nvalid = nvalid < 0 ? 0 : (nvalid > kPPT ? kPPT : nvalid);
-        if (nvalid > 0) {
-          const long long s = base + first;
-          const uint4 cl = *reinterpret_cast<const uint4*>(A.in.p.cell + s);
-          const float4 q0 = *reinterpret_cast<const float4*>(A.in.p.o[0] + s);
-          const float4 q1 = *reinterpret_cast<const float4*>(A.in.p.o[1] + s);
-          float4 q2 = make_float4(0.f, 0.f, 0.f, 0.f);
-          if (NDIM == 3) q2 = *reinterpret_cast<const float4*>(A.in.p.o[2] + s);
-          const float4 v0 = *reinterpret_cast<const float4*>(A.in.p.u[0] + s);
-          const float4 v1 = *reinterpret_cast<const float4*>(A.in.p.u[1] + s);
-          const float4 v2 = *reinterpret_cast<const float4*>(A.in.p.u[2] + s);
-          int4 idv = make_int4(0, 0, 0, 0);
-          if (A.in.p.id) idv = *reinterpret_cast<const int4*>(A.in.p.id + s);
-          pp[0] = P{cl.x, q0.x, q1.x, q2.x, v0.x, v1.x, v2.x, idv.x};
-          pp[1] = P{cl.y, q0.y, q1.y, q2.y, v0.y, v1.y, v2.y, idv.y};
-          pp[2] = P{cl.z, q0.z, q1.z, q2.z, v0.z, v1.z, v2.z, idv.z};
-          pp[3] = P{cl.w, q0.w, q1.w, q2.w, v0.w, v1.w, v2.w, idv.w};
-        }
-      } else {
-        const int first = (ch - nchunk_s) * kChunk + tid * kPPT;
-        nvalid = ninc - first;
-        nvalid = nvalid < 0 ? 0 : (nvalid > kPPT ? kPPT : nvalid);
-#pragma unroll
-        for (int r = 0; r < kPPT; ++r) {
-          if (r < nvalid) {
-            const long long s = base + cap - ninc + first + r;
-            pp[r] = P{A.in.p.cell[s], A.in.p.o[0][s], A.in.p.o[1][s], NDIM == 3 ? A.in.p.o[2][s] : 0.f,
-                      A.in.p.u[0][s], A.in.p.u[1][s], A.in.p.u[2][s], A.in.p.id ? A.in.p.id[s] : 0};
-          }
-        }
-      }
-      {
-        Acc acc;
-#pragma unroll
-        for (int k = 0; k < 12; ++k) acc.w[k] = 0.f;
-        acc.cell = -1;
-#pragma unroll
-        for (int r = 0; r < kPPT; ++r)
-          key[r] = r < nvalid ? push_one<NDIM, TX, TY, TZ>(F, J, A, pp[r], acc, Q, misc + 1)
-                                                      : Geo<NDIM, TX, TY, TZ>::NK;
-        acc_flush<NDIM, TX, TY, TZ>(J, acc);
-      }
-      sort_and_store<NDIM, TX, TY, TZ>(A, t, tix, tiy, tiz, base, room, pp, key, nvalid, ws, hist, misc);
-      __syncthreads();
-      const int nq = misc[1];
-      if (nq > kQCap / 2) {
-        drain_queue<NDIM, TX, TY, TZ>(J, A, Q, nq < kQCap ? nq : kQCap);
-        __syncthreads();
-        if (tid == 0) misc[1] = 0;
-        __syncthreads();  // the reset lands before the next chunk queues anything
-      }
-    }
-    __syncthreads();
-    {
-      const int nq = misc[1];
-      if (nq > 0) drain_queue<NDIM, TX, TY, TZ>(J, A, Q, nq < kQCap ? nq : kQCap);
-    }
-    if (tid == 0) A.out.stay[t] = ws < room ? ws : room;
-    // flush the current tile: every thread orders its shared atomics before the
-    // async proxy reads them; one thread issues the TMA reduce-add and waits
-    // until the TMA has read the tile before the next tile reuses it
-    fence_proxy_async_smem();
-    __syncthreads();
-    if (tid == 0) {
-      if (NDIM == 3)
-        tma_reduce_add_4d(&jmap, J, x0, y0, z0, 0);
-      else
-        tma_reduce_add_3d(&jmap, J, x0, y0, 0);
-      tma_commit();
-      tma_wait_read0();
-    }
+    if (!sort_tile<NDIM, TX, TY, TZ>(A, &fmap, &jmap, t, smem, phase)) return;
   }
 }
 
+// Many independent simulations in one launch: work item w is tile
+// w - tile0[s] of table entry s (one entry per simulation and species), whose
+// arguments and tensor maps live in device memory.
+struct BatchTable {
+  const TileArgs* args;
+  const CUtensorMap* fmaps;
+  const CUtensorMap* jmaps;
+  const int* tile0;  // [n + 1] first work item of each entry
+  int n;
+  int* work;
+};
+
+template <int NDIM, int TX, int TY, int TZ, int MINB>
+__global__ void __launch_bounds__(kThreads, MINB) k_tile_push_batch(const BatchTable B) {
+  using G = Geo<NDIM, TX, TY, TZ>;
+  extern __shared__ __align__(1024) unsigned char smem[];
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + G::MOFF);
+  int* misc = reinterpret_cast<int*>(smem + G::MOFF + 16);
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    mbar_init(bar, 1);
+    fence_barrier_init();
+  }
+  const int total = B.tile0[B.n];
+  uint32_t phase = 0;
+  for (;;) {
+    __syncthreads();
+    if (tid == 0) {
+      const int w = atomicAdd(B.work, 1);
+      int s = 0;
+      if (w < total) {  // last entry whose first work item is <= w
+        int lo = 0, hi = B.n - 1;
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (B.tile0[mid] <= w)
+            lo = mid;
+          else
+            hi = mid - 1;
+        }
+        s = lo;
+      }
+      misc[0] = w;
+      misc[2] = s;
+      misc[1] = 0;
+    }
+    __syncthreads();
+    const int w = misc[0];
+    if (w >= total) break;
+    const int s = misc[2];
+    if (!sort_tile<NDIM, TX, TY, TZ>(B.args[s], B.fmaps + s, B.jmaps + s, w - B.tile0[s], smem, phase)) return;
+  }
+}
 
 // ============================================================================
 // Small-tile kernel: every tile holds at most kCapS particles, so one CTA
@@ -1797,10 +1865,9 @@ int tiled_push_grid(int ndim, const int T[3], int ntiles, bool small) {
   return g < ntiles ? g : ntiles;
 }
 
-void tiled_push(const Layout& L, const PushConst& C, const Tiles& tg, const TileSide& in, const TileSide& out,
-                Flat32 spill, int* spill_count, long long spill_cap, int grid, int* work, const CUtensorMap* fmap,
-                const CUtensorMap* jmap, int* status, bool stream, cudaStream_t s) {
-  (void)L;
+namespace {
+TileArgs make_args(const PushConst& C, const Tiles& tg, const TileSide& in, const TileSide& out, Flat32 spill,
+                   int* spill_count, long long spill_cap, int* work, int* status) {
   TileArgs A;
   for (int d = 0; d < 3; ++d) A.nt[d] = tg.nt[d];
   A.ntiles = tg.ntiles;
@@ -1822,6 +1889,76 @@ void tiled_push(const Layout& L, const PushConst& C, const Tiles& tg, const Tile
   }
   A.j3f = (float)(C.q / C.dvol);
   A.status = status;
+  return A;
+}
+
+template <int NDIM, int TX, int TY, int TZ>
+int occupancy_b() {
+  using G = Geo<NDIM, TX, TY, TZ>;
+  static int occ = -1;
+  if (occ < 0) {
+    cudaFuncSetAttribute(k_tile_push_batch<NDIM, TX, TY, TZ, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         G::SMEM);
+    int o = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_tile_push_batch<NDIM, TX, TY, TZ, 3>, kThreads, G::SMEM) !=
+            cudaSuccess ||
+        o < 1)
+      o = 1;
+    occ = o;
+  }
+  return occ;
+}
+}  // namespace
+
+size_t tiled_args_bytes() { return sizeof(TileArgs); }
+
+void tiled_fill_args(void* dst, const PushConst& C, const Tiles& tg, const TileSide& in, const TileSide& out,
+                     Flat32 spill, int* spill_count, long long spill_cap, int* status) {
+  const TileArgs A = make_args(C, tg, in, out, spill, spill_count, spill_cap, nullptr, status);
+  memcpy(dst, &A, sizeof(A));
+}
+
+int tiled_batch_grid(int ndim, const int T[3], int total_tiles) {
+  int dev = 0, sms = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  int occ = 0;
+#define X(N, A_, B_, C_) \
+  if (shape_is(ndim, T, N, A_, B_, C_)) occ = occupancy_b<N, A_, B_, C_>();
+  PICGB_TILE_SHAPES(X)
+#undef X
+  if (occ < 1) return 0;
+  const int g = sms * occ;
+  return g < total_tiles ? g : total_tiles;
+}
+
+bool tiled_push_batch(int ndim, const int T[3], const void* args, const CUtensorMap* fmaps, const CUtensorMap* jmaps,
+                      const int* tile0, int n, int* work, int grid, cudaStream_t s) {
+  BatchTable B;
+  B.args = static_cast<const TileArgs*>(args);
+  B.fmaps = fmaps;
+  B.jmaps = jmaps;
+  B.tile0 = tile0;
+  B.n = n;
+  B.work = work;
+  cudaMemsetAsync(work, 0, sizeof(int), s);
+#define X(N, A_, B_, C_)                                                                    \
+  if (shape_is(ndim, T, N, A_, B_, C_)) {                                                   \
+    using G = Geo<N, A_, B_, C_>;                                                           \
+    occupancy_b<N, A_, B_, C_>();                                                           \
+    k_tile_push_batch<N, A_, B_, C_, 3><<<grid, kThreads, G::SMEM, s>>>(B);                \
+    return true;                                                                            \
+  }
+  PICGB_TILE_SHAPES(X)
+#undef X
+  return false;
+}
+
+void tiled_push(const Layout& L, const PushConst& C, const Tiles& tg, const TileSide& in, const TileSide& out,
+                Flat32 spill, int* spill_count, long long spill_cap, int grid, int* work, const CUtensorMap* fmap,
+                const CUtensorMap* jmap, int* status, bool stream, cudaStream_t s) {
+  (void)L;
+  const TileArgs A = make_args(C, tg, in, out, spill, spill_count, spill_cap, work, status);
   cudaMemsetAsync(work, 0, sizeof(int), s);
   cudaMemsetAsync(out.inc, 0, sizeof(int) * (size_t)tg.ntiles, s);
   const int* T = tg.T;

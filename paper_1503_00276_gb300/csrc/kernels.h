@@ -96,6 +96,17 @@ void tiled_push(const Layout& L, const PushConst& C, const Tiles& tg, const Tile
                 Flat32 spill, int* spill_count, long long spill_cap, int grid, int* work, const CUtensorMap* fmap,
                 const CUtensorMap* jmap, int* status, bool stream, cudaStream_t s);
 int tiled_stream_grid(int ndim, const int T[3], int ntiles);
+// Batched form: many simulations (one table entry per simulation and species)
+// in one launch of the sorting kernel.  tiled_fill_args writes one entry
+// (tiled_args_bytes bytes) on the host; tile0[n] is the exclusive prefix of
+// the entries' tile counts.  tiled_push_batch returns false for a tile shape
+// the kernel is not built for.
+size_t tiled_args_bytes();
+void tiled_fill_args(void* dst, const PushConst& C, const Tiles& tg, const TileSide& in, const TileSide& out,
+                     Flat32 spill, int* spill_count, long long spill_cap, int* status);
+int tiled_batch_grid(int ndim, const int T[3], int total_tiles);
+bool tiled_push_batch(int ndim, const int T[3], const void* args, const CUtensorMap* fmaps, const CUtensorMap* jmaps,
+                      const int* tile0, int n, int* work, int grid, cudaStream_t s);
 void tiled_live(const Tiles& tg, const TileSide& in, int* live, cudaStream_t s);
 int tiled_push_smem_bytes(int ndim, const int T[3]);
 int tiled_push_grid(int ndim, const int T[3], int ntiles, bool small);  // persistent CTAs

@@ -103,3 +103,22 @@ def test_valid_grid_without_device_reports_cuda_error(capi):
         pytest.skip("a GPU is present")
     code, h = _init(capi, _grid())
     assert code == -3 and not h.value
+
+
+def test_batch_arguments_are_checked_before_any_device_work(capi):
+    from paper_1503_00276_gb300 import _grid_struct, _species_struct
+    lib = capi.load()
+    h = C.c_void_p()
+    assert lib.pic_batch_init(0, None, None, 1, None, None, C.byref(h)) == -1
+    dx = (0.1, 0.1, 0.1)
+    g2 = workload.Grid(ndim=2, nx=(64, 32, 1), dx=dx, dt=workload.courant_dt(dx, 2))
+    g3 = workload.Grid(ndim=3, nx=(16, 16, 16), dx=dx, dt=workload.courant_dt(dx, 3))
+    sp = workload.Species(ppc=(1, 1, 1))
+    grids = (capi.PicGrid * 2)(_grid_struct(g2, 1), _grid_struct(g3, 1))
+    specs = (capi.PicSpecies * 2)(_species_struct(sp)[0], _species_struct(sp)[0])
+    assert lib.pic_batch_init(2, grids, specs, 1, None, None, C.byref(h)) == -1  # mixed ndim
+    grids = (capi.PicGrid * 2)(_grid_struct(g2, 1), _grid_struct(g2, 0))
+    assert lib.pic_batch_init(2, grids, specs, 1, None, None, C.byref(h)) == -1  # FP64 member
+    assert b"FP32" in lib.pic_last_error()
+    assert not h.value
+    assert lib.pic_batch_destroy(None) == 0

@@ -1,0 +1,142 @@
+"""GPU tests of the batched scan (pic_batch_*): members of uneven size and
+particle count advanced by one persistent tile-kernel launch per step and one
+CUDA graph launch per step.
+
+* against the same simulations run one by one (pic_step): after 10 steps,
+  particles (by id) within 1e-4 of a cell / of u -- FP32 shared-memory current
+  sums are order dependent, and those differences feed back through the fields;
+* one step of each member against the FP64 oracle with the one-step FP32
+  tolerances (2e-5 of a cell, 2e-5 (1 + |u|), grid values 2e-5 of their max);
+* re-binning: a member whose tile storage overflows is re-binned between steps
+  and keeps every particle;
+* graph replay and direct launches give the same run (same tolerance as above).
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import workload
+
+pytestmark = pytest.mark.gpu
+
+DX = (0.1, 0.1, 1.0)
+
+
+def _members(uth=0.3):
+    out = []
+    for i, (nx, ppc) in enumerate((((64, 32, 1), (2, 1, 1)), ((96, 48, 1), (1, 3, 1)), ((128, 16, 1), (2, 2, 1)),
+                                   ((32, 64, 1), (3, 1, 1)), ((64, 64, 1), (1, 1, 1)))):
+        g = workload.Grid(ndim=2, nx=nx, dx=DX, dt=workload.courant_dt(DX, 2), b0=(0.0, 0.0, 0.1 * i))
+        s = workload.Species(ppc=ppc, uth=(uth,) * 3, ufl=(0.05 * i, 0.0, 0.0), seed=700 + i)
+        out.append((g, [s]))
+    return out
+
+
+def _compare(a, b, tol):
+    xa, ua = a.particles()
+    ia = a.ids()
+    xb, ub = b.particles()
+    ib = b.ids()
+    assert xa.shape == xb.shape
+    pa, pb = np.argsort(ia), np.argsort(ib)
+    np.testing.assert_array_equal(ia[pa], ib[pb])
+    L = np.array([a.shape[2] * DX[0], a.shape[1] * DX[1], 1.0])
+    d = xa[pa] - xb[pb]
+    d = d - L * np.round(d / L)
+    assert np.max(np.abs(d[:, :2] / np.array(DX[:2]))) < tol
+    assert np.max(np.abs(ua[pa] - ub[pb])) < tol
+
+
+def test_batch_matches_members_run_one_by_one():
+    import paper_1503_00276_gb300 as pg
+    mem = _members()
+    batch = pg.Batch(mem, track_ids=True)
+    assert batch.info()["tile"] == (32, 16, 1)
+    batch.step(10)
+    info = batch.info()
+    assert info["steps"] == 10 and info["launches"] == 10 * (1 + 5 * len(mem))
+    for i, (g, sps) in enumerate(mem):
+        solo = pg.Simulation(g, sps, precision="fp32", tile=(32, 16), track_ids=True)
+        solo.step(10)
+        m = batch.sim(i)
+        _compare(m, solo, 1e-4)
+        d = m.diag()
+        assert d["step"] == 10 and d["error_flags"] == 0
+        assert d["gauss_resid_max"] <= 1e-5 * d["rho_abs_max"]
+        solo.close()
+    with pytest.raises(RuntimeError):
+        batch.sim(0).step(1)
+    batch.close()
+
+
+def test_batch_one_step_matches_oracle():
+    import paper_1503_00276_gb300 as pg
+    mem = _members(uth=0.5)[:3]
+    batch = pg.Batch(mem, track_ids=True)
+    refs = []
+    for i, (g, sps) in enumerate(mem):
+        f = workload.random_fields(g, seed=50 + i, amp=0.2)
+        m = batch.sim(i)
+        for c, name in enumerate(["E1", "E2", "E3", "B1", "B2", "B3"]):
+            m.set_field(name, f[c])
+        ref = oracle.from_workload(g, sps, fields=f)
+        ref.particle_phase()
+        jref = [c.copy() for c in ref.cur]
+        ref.field_solve()
+        refs.append((ref, jref))
+    batch.step(1)
+    for i, (g, sps) in enumerate(mem):
+        ref, jref = refs[i]
+        m = batch.sim(i)
+        x, u = m.particles()
+        ids = m.ids()
+        L = np.array([g.nx[0] * DX[0], g.nx[1] * DX[1], 1.0])
+        d = x - ref.x[0][ids]
+        d = d - L * np.round(d / L)
+        assert np.max(np.abs(d[:, :2] / np.array(DX[:2]))) < 2e-5
+        assert np.max(np.abs(u - ref.u[0][ids]) / (1 + np.abs(ref.u[0][ids]))) < 2e-5
+        for c, name in enumerate(["J1", "J2", "J3"]):
+            jm = np.max(np.abs(jref[c]))
+            assert np.max(np.abs(m.fields(name) - jref[c])) < 2e-5 * jm, (i, name)
+        for c, name in enumerate(["E1", "E2", "E3", "B1", "B2", "B3"]):
+            assert np.max(np.abs(m.fields(name) - ref.fld[c])) < 2e-5 * np.max(np.abs(ref.fld[c])), (i, name)
+    batch.close()
+
+
+def test_batch_rebins_a_member_whose_tiles_overflow():
+    import paper_1503_00276_gb300 as pg
+    mem = _members(uth=0.8)
+    batch = pg.Batch(mem, track_ids=True, slack=1e-3)
+    n0 = [batch.sim(i).n_particles() for i in range(len(mem))]
+    batch.step(8)
+    # bit 1 of error_flags: some tile storage spilled (and was re-binned)
+    assert any(batch.sim(i).diag()["error_flags"] & 2 for i in range(len(mem)))
+    for i, (g, sps) in enumerate(mem):
+        m = batch.sim(i)
+        assert m.n_particles() == n0[i]
+        assert np.array_equal(np.sort(m.ids()), np.arange(n0[i]))
+        assert m.diag()["error_flags"] & 1 == 0
+        solo = pg.Simulation(g, sps, precision="fp32", tile=(32, 16), track_ids=True, slack=1e-3)
+        solo.step(8)
+        _compare(m, solo, 1e-4)
+        solo.close()
+    batch.close()
+
+
+def test_batch_graph_and_direct_launches_agree():
+    import paper_1503_00276_gb300 as pg
+    mem = _members()
+    a = pg.Batch(mem, track_ids=True)
+    os.environ["PICGB_BATCH_GRAPH"] = "0"
+    try:
+        b = pg.Batch(mem, track_ids=True)
+    finally:
+        del os.environ["PICGB_BATCH_GRAPH"]
+    a.step(6)
+    b.step(6)
+    for i in range(len(mem)):
+        _compare(a.sim(i), b.sim(i), 1e-4)
+    a.close()
+    b.close()

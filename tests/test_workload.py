@@ -55,3 +55,20 @@ def test_config_shapes():
     assert abs(g.dt - 0.99 / math.sqrt(200)) < 1e-15
     g3, sp3, steps3 = workload.config3()
     assert workload.n_particles(g3, sp3[0]) == 268435456 and steps3 == 200
+
+
+def test_config4_scan_draws():
+    sims, steps = workload.config4()
+    assert len(sims) == 64 and steps == 500
+    again, _ = workload.config4()
+    assert [(g.nx, s[0].ppc, s[0].density, s[0].ufl) for g, s in sims] == \
+        [(g.nx, s[0].ppc, s[0].density, s[0].ufl) for g, s in again]
+    for g, (sp,) in sims:
+        assert g.nx[0] in (128, 256, 512, 1024) and g.nx[1] in (64, 128, 256, 512) and g.nx[2] == 1
+        assert sp.ppc_total in (4, 8, 16, 32)
+        assert 0.5 <= sp.density < 2.0 and 0.5 <= sp.ufl[1] < 3.0
+        assert g.rho_bg == sp.density  # neutral
+        assert abs(g.dt - 0.99 / math.sqrt(1 / 0.05 ** 2 + 1 / 0.2 ** 2)) < 1e-15
+    # uneven sizes: several distinct grids and particle counts
+    assert len({g.nx for g, _ in sims}) > 8
+    assert len({workload.n_particles(g, s[0]) for g, s in sims}) > 8

@@ -196,3 +196,36 @@ def config3(ppc_total: int = 8, seed: int = 20004, nx=(512, 256, 256)):
     g = Grid(ndim=3, nx=tuple(nx), dx=dx, dt=courant_dt(dx, 3))
     s = Species(rqm=-1.0, ppc=lattice, uth=(0.05, 0.05, 0.05), seed=seed)
     return g, [s], 200
+
+
+def config4(seed: int = 20005, nsims: int = 64):
+    """Batched parameter scan: ``nsims`` independent 2D3V runs of uneven size
+    drawn from the seed (500 steps each).
+
+    Draw i uses counters 8i .. 8i+4 of the SplitMix64 stream ``seed``: grid
+    nx1 in {128, 256, 512, 1024} x nx2 in {64, 128, 256, 512}, ppc in
+    {4, 8, 16, 32} (lattices 2x2, 4x2, 4x4, 8x4), plasma density scale
+    U[0.5, 2) and laser strength a0 U[0.5, 3); dx1 = 0.05, dx2 = 0.2,
+    dt = 0.99 of the Courant limit.  The boundary-injected laser and the moving
+    window of a wakefield run are not part of this hot path, so each run is a
+    uniform, neutralised (ion background = density scale) cold plasma whose
+    electrons start with the transverse momentum a0 in x2 -- the quiver
+    momentum the drawn laser would give them -- plus u_th = 0.01.
+    Returns a list of (Grid, [Species]) and the step count.
+    """
+    lattices = {4: (2, 2, 1), 8: (4, 2, 1), 16: (4, 4, 1), 32: (8, 4, 1)}
+    dx = (0.05, 0.2, 1.0)
+    dt = courant_dt(dx, 2)
+    out = []
+    for i in range(nsims):
+        r = uniform01(seed, np.arange(8 * i, 8 * i + 5, dtype=np.uint64))
+        nx1 = (128, 256, 512, 1024)[int(r[0] * 4)]
+        nx2 = (64, 128, 256, 512)[int(r[1] * 4)]
+        ppc = (4, 8, 16, 32)[int(r[2] * 4)]
+        dens = 0.5 + 1.5 * float(r[3])
+        a0 = 0.5 + 2.5 * float(r[4])
+        g = Grid(ndim=2, nx=(nx1, nx2, 1), dx=dx, dt=dt, rho_bg=dens)
+        s = Species(rqm=-1.0, ppc=lattices[ppc], uth=(0.01, 0.01, 0.01), ufl=(0.0, a0, 0.0), density=dens,
+                    seed=seed + 1000 * (i + 1))
+        out.append((g, [s]))
+    return out, 500

@@ -114,6 +114,9 @@ typedef struct {
   int sort_period;          /* PIC_FP32_CELLOFF: every sort_period-th step re-sorts each
                                tile by cell; the steps between update particles in
                                place (0 = default 1: sort every step) */
+  int ctas_per_sm;          /* PIC_FP32_CELLOFF: thread blocks per SM the general tile
+                               kernel is built for: 3 (80 registers per thread) or 2
+                               (128); 0 = default 3 */
 } pic_grid;
 
 /* One particle species (appendix nl_species / nl_profile).  Either loaded on the
@@ -300,6 +303,38 @@ pic_status pic_batch_info(const pic_batch* B, long long* steps, long long* launc
 
 /* Frees every member and the batch; synchronises its stream first. */
 pic_status pic_batch_destroy(pic_batch* B);
+
+
+/* ---- Autotuner --------------------------------------------------------------
+ * Chooses the launch parameters of the FP32 particle step by running them: the
+ * tile shape (3D 8x8x8, 16x8x4, 8x4x4, 4x4x4, 4x4x2; 2D 32x16, 16x16, 8x8,
+ * 16x8, 8x4 -- those dividing every grid), the thread blocks per SM of the
+ * general tile kernel (3 or 2: its particles per block per SM), and the sort
+ * period (1 or 4).  Each candidate is set up from the same grid/species,
+ * stepped `warmup` steps, then `steps` steps are timed with CUDA events on
+ * `stream`; the candidate is freed before the next.  The thesis tunes nothing
+ * of this kind (its particle loop runs on CPUs).
+ * best: the fastest candidate; tried[0 .. min(max_tried, *n_tried) - 1]: every
+ * candidate with its time (ms_per_step < 0: it could not run, e.g. no memory).
+ * PIC_EINVAL for bad arguments or grids no shape divides; PIC_ECUDA if no
+ * candidate ran. */
+typedef struct {
+  int tile[3];
+  int ctas_per_sm;
+  int sort_period;
+  double ms_per_step;
+} pic_tune_choice;
+
+pic_status pic_autotune(const pic_grid* grid, const pic_species* species, int nspecies, const pic_allocator* alloc,
+                        void* stream, int warmup, int steps, pic_tune_choice* best, pic_tune_choice* tried,
+                        int max_tried, int* n_tried);
+
+/* The same for a batch (pic_batch_init arguments): general tile shapes that
+ * divide every member's grid, 3 or 2 blocks per SM, sort period 1; each
+ * candidate is a whole batch. */
+pic_status pic_batch_autotune(int nsims, const pic_grid* grids, const pic_species* species, int nspecies,
+                              const pic_allocator* alloc, void* stream, int warmup, int steps, pic_tune_choice* best,
+                              pic_tune_choice* tried, int max_tried, int* n_tried);
 
 #ifdef __cplusplus
 }

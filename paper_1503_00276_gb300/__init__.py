@@ -19,7 +19,7 @@ import numpy as np
 from . import _capi
 from ._capi import FIELD_NAMES, PIC_FP32_CELLOFF, PIC_FP64_PLAIN, PicError, check, load  # noqa: F401
 
-__all__ = ["Simulation", "Batch", "bin_tiles", "bin_tiles_noalloc", "load", "PicError", "PIC_FP64_PLAIN", "PIC_FP32_CELLOFF", "FIELD_NAMES"]
+__all__ = ["Simulation", "Batch", "autotune", "batch_autotune", "bin_tiles", "bin_tiles_noalloc", "load", "PicError", "PIC_FP64_PLAIN", "PIC_FP32_CELLOFF", "FIELD_NAMES"]
 
 
 def _torch():
@@ -49,7 +49,7 @@ class _TorchAllocator:
         self.torch.cuda.caching_allocator_delete(ptr)
 
 
-def _grid_struct(grid, precision, tile=None, slack=0.0, sort_period=0):
+def _grid_struct(grid, precision, tile=None, slack=0.0, sort_period=0, ctas_per_sm=0):
     g = _capi.PicGrid()
     g.ndim = int(grid.ndim)
     for d in range(3):
@@ -73,6 +73,7 @@ def _grid_struct(grid, precision, tile=None, slack=0.0, sort_period=0):
     g.precision = int(precision)
     g.slack = float(slack)
     g.sort_period = int(sort_period)
+    g.ctas_per_sm = int(ctas_per_sm)
     return g
 
 
@@ -112,14 +113,14 @@ class Simulation:
     """
 
     def __init__(self, grid, species, precision="fp64", explicit=None, tile=None, track_ids=False, slack=0.0,
-                 stream=None, use_torch_allocator=True, np_max=0, sort_period=0):
+                 stream=None, use_torch_allocator=True, np_max=0, sort_period=0, ctas_per_sm=0):
         self._lib = load()
         torch = _torch()
         prec = PIC_FP32_CELLOFF if precision in ("fp32", PIC_FP32_CELLOFF) else PIC_FP64_PLAIN
         self.precision = prec
         self.ndim = int(grid.ndim)
         self.shape = (int(grid.nx[2]) if grid.ndim == 3 else 1, int(grid.nx[1]), int(grid.nx[0]))
-        self._g = _grid_struct(grid, prec, tile, slack, sort_period)
+        self._g = _grid_struct(grid, prec, tile, slack, sort_period, ctas_per_sm)
         specs = (_capi.PicSpecies * max(len(species), 1))()
         self._keep = []
         for k, sp in enumerate(species):
@@ -325,7 +326,8 @@ class Batch:
     species each.  ``tile``: common tile shape (None: the library's choice).
     """
 
-    def __init__(self, members, tile=None, track_ids=False, slack=0.0, stream=None, use_torch_allocator=True):
+    def __init__(self, members, tile=None, track_ids=False, slack=0.0, stream=None, use_torch_allocator=True,
+                 ctas_per_sm=0):
         self._lib = load()
         torch = _torch()
         self._torch = torch
@@ -335,7 +337,7 @@ class Batch:
         grids = (_capi.PicGrid * n)()
         specs = (_capi.PicSpecies * (n * nsp))()
         for i, (g, sps) in enumerate(members):
-            grids[i] = _grid_struct(g, PIC_FP32_CELLOFF, tile, slack, 1)
+            grids[i] = _grid_struct(g, PIC_FP32_CELLOFF, tile, slack, 1, ctas_per_sm)
             for k, sp in enumerate(sps):
                 specs[i * nsp + k] = _species_struct(sp, None, track_ids)[0]
         self._members = members
@@ -389,3 +391,54 @@ class Batch:
 
     def __exit__(self, *a):
         self.close()
+
+
+def _tune_result(best, tried, n):
+    def one(c):
+        return {"tile": tuple(c.tile), "ctas_per_sm": int(c.ctas_per_sm), "sort_period": int(c.sort_period),
+                "ms_per_step": float(c.ms_per_step)}
+    return one(best), [one(tried[k]) for k in range(min(n, len(tried)))]
+
+
+def _stream_and_alloc(stream, use_torch_allocator):
+    torch = _torch()
+    if torch is None or not torch.cuda.is_available():
+        return None, None
+    st = stream if stream is not None else torch.cuda.current_stream()
+    alloc = _TorchAllocator(torch, torch.cuda.current_device(), st) if use_torch_allocator else None
+    return C.c_void_p(st.cuda_stream), alloc
+
+
+def autotune(grid, species, warmup=3, steps=5, slack=0.0, stream=None, use_torch_allocator=True):
+    """pic_autotune: time every (tile shape, blocks per SM, sort period)
+    candidate of the FP32 form on this workload; returns (best, all tried)."""
+    lib = load()
+    g = _grid_struct(grid, PIC_FP32_CELLOFF, None, slack)
+    specs = (_capi.PicSpecies * len(species))(*[_species_struct(sp)[0] for sp in species])
+    st, alloc = _stream_and_alloc(stream, use_torch_allocator)
+    best = _capi.PicTuneChoice()
+    tried = (_capi.PicTuneChoice * 32)()
+    n = C.c_int()
+    check(lib.pic_autotune(C.byref(g), specs, len(species), C.byref(alloc.struct) if alloc else None, st,
+                           int(warmup), int(steps), C.byref(best), tried, 32, C.byref(n)), "pic_autotune")
+    return _tune_result(best, tried, n.value)
+
+
+def batch_autotune(members, warmup=2, steps=3, slack=0.0, stream=None, use_torch_allocator=True):
+    """pic_batch_autotune for the members of a Batch; returns (best, all tried)."""
+    lib = load()
+    n = len(members)
+    nsp = len(members[0][1])
+    grids = (_capi.PicGrid * n)()
+    specs = (_capi.PicSpecies * (n * nsp))()
+    for i, (g, sps) in enumerate(members):
+        grids[i] = _grid_struct(g, PIC_FP32_CELLOFF, None, slack, 1)
+        for k, sp in enumerate(sps):
+            specs[i * nsp + k] = _species_struct(sp)[0]
+    st, alloc = _stream_and_alloc(stream, use_torch_allocator)
+    best = _capi.PicTuneChoice()
+    tried = (_capi.PicTuneChoice * 32)()
+    cnt = C.c_int()
+    check(lib.pic_batch_autotune(n, grids, specs, nsp, C.byref(alloc.struct) if alloc else None, st, int(warmup),
+                                 int(steps), C.byref(best), tried, 32, C.byref(cnt)), "pic_batch_autotune")
+    return _tune_result(best, tried, cnt.value)

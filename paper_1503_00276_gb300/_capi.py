@@ -29,7 +29,8 @@ class PicGrid(C.Structure):
                 ("dt", C.c_double), ("bc", (C.c_int * 2) * 3), ("e0", C.c_double * 3), ("b0", C.c_double * 3),
                 ("smooth_level", C.c_int * 3), ("smooth_w", ((C.c_double * 3) * MAX_SMOOTH) * 3),
                 ("rho_bg", C.c_double), ("init_e_gauss_x1", C.c_int), ("precision", C.c_int),
-                ("tile", C.c_int * 3), ("slack", C.c_double), ("sort_period", C.c_int)]
+                ("tile", C.c_int * 3), ("slack", C.c_double), ("sort_period", C.c_int),
+                ("ctas_per_sm", C.c_int)]
 
 
 class PicSpecies(C.Structure):
@@ -37,6 +38,11 @@ class PicSpecies(C.Structure):
                 ("density", C.c_double), ("seed", C.c_ulonglong), ("n_explicit", C.c_longlong),
                 ("x0", C.POINTER(C.c_double)), ("u0", C.POINTER(C.c_double)), ("q_explicit", C.c_double),
                 ("np_max", C.c_longlong), ("track_ids", C.c_int)]
+
+
+class PicTuneChoice(C.Structure):
+    _fields_ = [("tile", C.c_int * 3), ("ctas_per_sm", C.c_int), ("sort_period", C.c_int),
+                ("ms_per_step", C.c_double)]
 
 
 class PicDiag(C.Structure):
@@ -71,6 +77,12 @@ PROTOTYPES = {
     "pic_batch_sim": (C.c_int, [_P, C.c_int, C.POINTER(_P)]),
     "pic_batch_info": (C.c_int, [_P, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong), C.POINTER(C.c_int)]),
     "pic_batch_destroy": (C.c_int, [_P]),
+    "pic_autotune": (C.c_int, [C.POINTER(PicGrid), C.POINTER(PicSpecies), C.c_int, C.POINTER(PicAllocator), _P, C.c_int,
+                               C.c_int, C.POINTER(PicTuneChoice), C.POINTER(PicTuneChoice), C.c_int,
+                               C.POINTER(C.c_int)]),
+    "pic_batch_autotune": (C.c_int, [C.c_int, C.POINTER(PicGrid), C.POINTER(PicSpecies), C.c_int,
+                                     C.POINTER(PicAllocator), _P, C.c_int, C.c_int, C.POINTER(PicTuneChoice),
+                                     C.POINTER(PicTuneChoice), C.c_int, C.POINTER(C.c_int)]),
 }
 BIN_NOALLOC_SCRATCH_BYTES = 16 << 20
 

@@ -9,6 +9,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <string>
+#include <functional>
 #include <vector>
 
 #include "kernels.h"
@@ -146,6 +147,7 @@ struct pic_sim {
   int T[3] = {1, 1, 1};
   double slack = 0.25;
   int sort_period = 1;
+  int minb = 3;  // CTAs per SM the general tile kernel is built for (2 or 3)
   bool timing = false;
   double t_ms[kTimingSlots] = {0, 0, 0, 0, 0};
   long long t_n[kTimingSlots] = {0, 0, 0, 0, 0};
@@ -411,7 +413,7 @@ pic_status bin_flat(pic_sim* S, SpeciesState& sp, Flat32& flat, long long n) {
   for (int t = 0; t < nt; ++t) max_cap = std::max<long long>(max_cap, hcap[t]);
   sp.tg.small = !S->no_small && tiled_has_small(S->ndim, S->T) &&
                 (max_cap <= tiled_small_capacity() || !tiled_has_general(S->ndim, S->T));
-  sp.grid = tiled_push_grid(S->ndim, S->T, nt, sp.tg.small != 0);
+  sp.grid = tiled_push_grid(S->ndim, S->T, nt, sp.tg.small != 0, S->minb);
   sp.grid_stream = tiled_stream_grid(S->ndim, S->T, nt);
   cudaMemcpyAsync(sp.tg.cap, hcap.data(), 4 * (size_t)nt, cudaMemcpyHostToDevice, S->s);
   cudaMemcpyAsync(sp.tg.res, hres.data(), 4 * (size_t)nt, cudaMemcpyHostToDevice, S->s);
@@ -771,7 +773,8 @@ pic_status one_step(pic_sim* S, bool check_now) {
         // the steps before it keep the order they find (blocks compacted)
         const bool stream = S->sort_period > 1 && !s.tg.small && (S->step + 1) % S->sort_period != 0;
         tiled_push(S->L, C, s.tg, s.side[in], s.side[out], s.spill, &S->dstat->spill_count, s.spill_cap,
-                   stream ? s.grid_stream : s.grid, s.work, &S->fmap, &S->jmap, &S->dstat->status, stream, S->s);
+                   stream ? s.grid_stream : s.grid, s.work, &S->fmap, &S->jmap, &S->dstat->status, stream, S->minb,
+                   S->s);
         s.cur = out;
       }
       S->nlaunch += s.n > 0 || S->prec == PIC_FP32_CELLOFF ? 1 : 0;
@@ -936,7 +939,15 @@ pic_status init_sim(const pic_grid* grid, const pic_species* species, int nspeci
         return PIC_EINVAL;
       }
     }
-    if (const char* e = getenv("PICGB_TILE_CTAS")) tiled_push_set_minb(atoi(e));
+    int ctas = grid->ctas_per_sm;
+    if (ctas == 0)
+      if (const char* e = getenv("PICGB_TILE_CTAS")) ctas = atoi(e);
+    if (ctas != 0 && ctas != 2 && ctas != 3) {
+      set_error("ctas_per_sm must be 0 (default), 2 or 3");
+      delete S;
+      return PIC_EINVAL;
+    }
+    S->minb = ctas == 2 ? 2 : 3;
     if (tiled_push_smem_bytes(S->ndim, S->T) < 0) {
       set_error("unsupported tile shape (3D: 4x4x4, 4x4x2, 8x4x4, 8x8x8, 16x8x4; 2D: 8x4, 8x8, 16x8, 16x16, 32x16)");
       delete S;
@@ -1360,6 +1371,7 @@ struct pic_batch {
   StatusWord* d_stat = nullptr;  // one per simulation
   StatusWord* h_stat = nullptr;  // pinned mirror
   int grid = 0;
+  int minb = 3;
   bool use_graph = true;
   bool dirty = true;  // tables / graphs must be rebuilt before the next step
   cudaGraphExec_t exec[2] = {nullptr, nullptr};
@@ -1385,7 +1397,7 @@ void batch_enqueue(pic_batch* B, int p) {
     cudaMemsetAsync(sp.side[1 - p].inc, 0, 4 * (size_t)sp.tg.ntiles, B->s);
   }
   tiled_push_batch(B->ndim, B->T, B->d_args[p], B->d_fmaps, B->d_jmaps, B->d_tile0, (int)B->ent.size(), B->d_work,
-                   B->grid, B->s);
+                   B->grid, B->minb, B->s);
   for (pic_sim* S : B->sims) field_step<float>(S);
 }
 
@@ -1429,7 +1441,7 @@ pic_status batch_build(pic_batch* B) {
   cudaMemcpyAsync(B->d_fmaps, fme.data(), sizeof(CUtensorMap) * n, cudaMemcpyHostToDevice, B->s);
   cudaMemcpyAsync(B->d_jmaps, jme.data(), sizeof(CUtensorMap) * n, cudaMemcpyHostToDevice, B->s);
   cudaMemcpyAsync(B->d_tile0, tile0.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice, B->s);
-  B->grid = tiled_batch_grid(B->ndim, B->T, tile0[n]);
+  B->grid = tiled_batch_grid(B->ndim, B->T, tile0[n], B->minb);
   if (B->grid <= 0) {
     set_error("pic_batch: tile shape not supported by the batched kernel");
     return PIC_EUNSUPPORTED;
@@ -1471,6 +1483,10 @@ pic_status pic_batch_init(int nsims, const pic_grid* grids, const pic_species* s
         set_error("pic_batch_init: every simulation must use the same tile shape");
         return PIC_EINVAL;
       }
+    if (grids[i].ctas_per_sm != grids[0].ctas_per_sm) {
+      set_error("pic_batch_init: every simulation must use the same ctas_per_sm");
+      return PIC_EINVAL;
+    }
   }
   // tile shape: the given one, else the first general shape dividing every grid
   int T[3] = {grids[0].tile[0], grids[0].tile[1], ndim == 3 ? grids[0].tile[2] : 1};
@@ -1503,6 +1519,7 @@ pic_status pic_batch_init(int nsims, const pic_grid* grids, const pic_species* s
     return PIC_ECUDA;
   }
   B->ndim = ndim;
+  B->minb = grids[0].ctas_per_sm == 2 ? 2 : 3;
   for (int d = 0; d < 3; ++d) B->T[d] = T[d];
   if (alloc && alloc->alloc) {
     B->al.user = *alloc;
@@ -1663,6 +1680,135 @@ pic_status pic_batch_destroy(pic_batch* B) {
   if (B->s) cudaStreamDestroy(B->s);
   delete B;
   return PIC_OK;
+}
+
+
+// ------------------------------------------------------------- autotuner
+
+namespace {
+
+// tile shapes of the general kernel and of the small-tile kernel, largest first
+const int kShapes3[][3] = {{8, 8, 8}, {16, 8, 4}, {8, 4, 4}, {4, 4, 4}, {4, 4, 2}};
+const int kShapes2[][3] = {{32, 16, 1}, {16, 16, 1}, {8, 8, 1}, {16, 8, 1}, {8, 4, 1}};
+constexpr int kGeneral3 = 2, kGeneral2 = 3;  // the first ones are the general kernel's
+
+struct TuneCand {
+  int T[3];
+  int ctas, sort;
+};
+
+std::vector<TuneCand> tune_candidates(int nsims, const pic_grid* grids, bool batch) {
+  std::vector<TuneCand> out;
+  const int ndim = grids[0].ndim;
+  const int ns = 5, ngen = ndim == 3 ? kGeneral3 : kGeneral2;
+  for (int k = 0; k < ns; ++k) {
+    const int* c = ndim == 3 ? kShapes3[k] : kShapes2[k];
+    bool fits = true;
+    for (int i = 0; i < nsims; ++i)
+      for (int d = 0; d < ndim; ++d) fits = fits && grids[i].nx[d] % c[d] == 0;
+    if (!fits) continue;
+    const bool general = k < ngen;
+    if (batch && !general) continue;
+    for (int ctas : {3, 2}) {
+      if (!general && ctas == 2) continue;  // the small-tile kernel has one build
+      for (int sort : {1, 4}) {
+        if ((batch || !general) && sort != 1) continue;
+        out.push_back({{c[0], c[1], ndim == 3 ? c[2] : 1}, ctas, sort});
+      }
+    }
+  }
+  return out;
+}
+
+// Device time per step of `steps` steps after `warmup` (events on `st`).
+double time_steps(cudaStream_t st, int warmup, int steps, const std::function<pic_status(int)>& step) {
+  if (step(warmup) != PIC_OK) return -1.0;
+  cudaEvent_t a, b;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  cudaEventRecord(a, st);
+  const pic_status rc = step(steps);
+  cudaEventRecord(b, st);
+  cudaEventSynchronize(b);
+  float ms = -1.f;
+  if (rc == PIC_OK) cudaEventElapsedTime(&ms, a, b);
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  return rc == PIC_OK && steps > 0 ? ms / steps : -1.0;
+}
+
+pic_status tune_run(int nsims, const pic_grid* grids, const pic_species* species, int nspecies,
+                    const pic_allocator* alloc, void* stream, int warmup, int steps, bool batch,
+                    pic_tune_choice* best, pic_tune_choice* tried, int max_tried, int* n_tried) {
+  if (nsims < 1 || !grids || !species || nspecies < 1 || !best || warmup < 0 || steps < 1) {
+    set_error("autotune: bad arguments");
+    return PIC_EINVAL;
+  }
+  for (int i = 0; i < nsims; ++i)
+    if (grids[i].precision != PIC_FP32_CELLOFF || grids[i].ndim != grids[0].ndim) {
+      set_error("autotune: every grid must be PIC_FP32_CELLOFF with the same ndim");
+      return PIC_EINVAL;
+    }
+  const std::vector<TuneCand> cand = tune_candidates(nsims, grids, batch);
+  if (cand.empty()) {
+    set_error("autotune: no tile shape divides every grid");
+    return PIC_EINVAL;
+  }
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  int nt = 0;
+  best->ms_per_step = -1.0;
+  for (const TuneCand& c : cand) {
+    std::vector<pic_grid> g(grids, grids + nsims);
+    for (auto& x : g) {
+      for (int d = 0; d < 3; ++d) x.tile[d] = c.T[d];
+      x.ctas_per_sm = c.ctas;
+      x.sort_period = c.sort;
+    }
+    double ms = -1.0;
+    if (batch) {
+      pic_batch* B = nullptr;
+      if (pic_batch_init(nsims, g.data(), species, nspecies, alloc, stream, &B) == PIC_OK) {
+        ms = time_steps(st, warmup, steps, [&](int n) { return pic_batch_step(B, n); });
+        pic_batch_destroy(B);
+      }
+    } else {
+      pic_sim* S = nullptr;
+      if (init_sim(g.data(), species, nspecies, alloc, stream, false, &S) == PIC_OK) {
+        ms = time_steps(st, warmup, steps, [&](int n) { return pic_step(S, n); });
+        pic_destroy(S);
+      }
+    }
+    cudaGetLastError();
+    pic_tune_choice r;
+    for (int d = 0; d < 3; ++d) r.tile[d] = c.T[d];
+    r.ctas_per_sm = c.ctas;
+    r.sort_period = c.sort;
+    r.ms_per_step = ms;
+    if (tried && nt < max_tried) tried[nt] = r;
+    ++nt;
+    if (ms > 0.0 && (best->ms_per_step < 0.0 || ms < best->ms_per_step)) *best = r;
+  }
+  if (n_tried) *n_tried = nt;
+  if (best->ms_per_step < 0.0) {
+    set_error("autotune: no candidate ran");
+    return PIC_ECUDA;
+  }
+  return PIC_OK;
+}
+
+}  // namespace
+
+pic_status pic_autotune(const pic_grid* grid, const pic_species* species, int nspecies, const pic_allocator* alloc,
+                        void* stream, int warmup, int steps, pic_tune_choice* best, pic_tune_choice* tried,
+                        int max_tried, int* n_tried) {
+  return tune_run(1, grid, species, nspecies, alloc, stream, warmup, steps, false, best, tried, max_tried, n_tried);
+}
+
+pic_status pic_batch_autotune(int nsims, const pic_grid* grids, const pic_species* species, int nspecies,
+                              const pic_allocator* alloc, void* stream, int warmup, int steps, pic_tune_choice* best,
+                              pic_tune_choice* tried, int max_tried, int* n_tried) {
+  return tune_run(nsims, grids, species, nspecies, alloc, stream, warmup, steps, true, best, tried, max_tried,
+                  n_tried);
 }
 
 }  // extern "C"

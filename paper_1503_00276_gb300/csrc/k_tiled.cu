@@ -1772,9 +1772,6 @@ void launch_push_s(const CUtensorMap* fmap, const CUtensorMap* jmap, const TileA
   k_tile_push_s<NDIM, TX, TY, TZ><<<grid, kThreads, S::SMEM, s>>>(*fmap, *jmap, A);
 }
 
-// Register budget of the general tile kernel: 3 CTAs per SM (80 registers) or
-// 2.  Chosen per simulation.
-int g_minb = 3;
 
 // Shapes of the general kernel (any particle count per tile) ...
 #define PICGB_TILE_SHAPES(X) \
@@ -1829,7 +1826,7 @@ bool tiled_has_small(int ndim, const int T[3]) {
 
 int tiled_small_capacity() { return kCapS - 9; }
 
-void tiled_push_set_minb(int minb) { g_minb = minb == 2 ? 2 : 3; }
+
 
 int tiled_stream_grid(int ndim, const int T[3], int ntiles) {
   int dev = 0, sms = 1;
@@ -1844,7 +1841,7 @@ int tiled_stream_grid(int ndim, const int T[3], int ntiles) {
   return g < ntiles ? g : ntiles;
 }
 
-int tiled_push_grid(int ndim, const int T[3], int ntiles, bool small) {
+int tiled_push_grid(int ndim, const int T[3], int ntiles, bool small, int minb) {
   int dev = 0, sms = 1;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -1857,7 +1854,7 @@ int tiled_push_grid(int ndim, const int T[3], int ntiles, bool small) {
   } else {
 #define X(N, A_, B_, C_)                  \
   if (shape_is(ndim, T, N, A_, B_, C_)) \
-    occ = g_minb == 2 ? occupancy<N, A_, B_, C_, 2>() : occupancy<N, A_, B_, C_, 3>();
+    occ = minb == 2 ? occupancy<N, A_, B_, C_, 2>() : occupancy<N, A_, B_, C_, 3>();
     PICGB_TILE_SHAPES(X)
 #undef X
   }
@@ -1892,16 +1889,16 @@ TileArgs make_args(const PushConst& C, const Tiles& tg, const TileSide& in, cons
   return A;
 }
 
-template <int NDIM, int TX, int TY, int TZ>
+template <int NDIM, int TX, int TY, int TZ, int MINB>
 int occupancy_b() {
   using G = Geo<NDIM, TX, TY, TZ>;
   static int occ = -1;
   if (occ < 0) {
-    cudaFuncSetAttribute(k_tile_push_batch<NDIM, TX, TY, TZ, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(k_tile_push_batch<NDIM, TX, TY, TZ, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          G::SMEM);
     int o = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_tile_push_batch<NDIM, TX, TY, TZ, 3>, kThreads, G::SMEM) !=
-            cudaSuccess ||
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_tile_push_batch<NDIM, TX, TY, TZ, MINB>, kThreads,
+                                                      G::SMEM) != cudaSuccess ||
         o < 1)
       o = 1;
     occ = o;
@@ -1918,13 +1915,14 @@ void tiled_fill_args(void* dst, const PushConst& C, const Tiles& tg, const TileS
   memcpy(dst, &A, sizeof(A));
 }
 
-int tiled_batch_grid(int ndim, const int T[3], int total_tiles) {
+int tiled_batch_grid(int ndim, const int T[3], int total_tiles, int minb) {
   int dev = 0, sms = 1;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   int occ = 0;
 #define X(N, A_, B_, C_) \
-  if (shape_is(ndim, T, N, A_, B_, C_)) occ = occupancy_b<N, A_, B_, C_>();
+  if (shape_is(ndim, T, N, A_, B_, C_)) \
+    occ = minb == 2 ? occupancy_b<N, A_, B_, C_, 2>() : occupancy_b<N, A_, B_, C_, 3>();
   PICGB_TILE_SHAPES(X)
 #undef X
   if (occ < 1) return 0;
@@ -1933,7 +1931,7 @@ int tiled_batch_grid(int ndim, const int T[3], int total_tiles) {
 }
 
 bool tiled_push_batch(int ndim, const int T[3], const void* args, const CUtensorMap* fmaps, const CUtensorMap* jmaps,
-                      const int* tile0, int n, int* work, int grid, cudaStream_t s) {
+                      const int* tile0, int n, int* work, int grid, int minb, cudaStream_t s) {
   BatchTable B;
   B.args = static_cast<const TileArgs*>(args);
   B.fmaps = fmaps;
@@ -1942,12 +1940,17 @@ bool tiled_push_batch(int ndim, const int T[3], const void* args, const CUtensor
   B.n = n;
   B.work = work;
   cudaMemsetAsync(work, 0, sizeof(int), s);
-#define X(N, A_, B_, C_)                                                                    \
-  if (shape_is(ndim, T, N, A_, B_, C_)) {                                                   \
-    using G = Geo<N, A_, B_, C_>;                                                           \
-    occupancy_b<N, A_, B_, C_>();                                                           \
-    k_tile_push_batch<N, A_, B_, C_, 3><<<grid, kThreads, G::SMEM, s>>>(B);                \
-    return true;                                                                            \
+#define X(N, A_, B_, C_)                                                      \
+  if (shape_is(ndim, T, N, A_, B_, C_)) {                                     \
+    using G = Geo<N, A_, B_, C_>;                                             \
+    if (minb == 2) {                                                          \
+      occupancy_b<N, A_, B_, C_, 2>();                                        \
+      k_tile_push_batch<N, A_, B_, C_, 2><<<grid, kThreads, G::SMEM, s>>>(B); \
+    } else {                                                                  \
+      occupancy_b<N, A_, B_, C_, 3>();                                        \
+      k_tile_push_batch<N, A_, B_, C_, 3><<<grid, kThreads, G::SMEM, s>>>(B); \
+    }                                                                         \
+    return true;                                                              \
   }
   PICGB_TILE_SHAPES(X)
 #undef X
@@ -1956,7 +1959,7 @@ bool tiled_push_batch(int ndim, const int T[3], const void* args, const CUtensor
 
 void tiled_push(const Layout& L, const PushConst& C, const Tiles& tg, const TileSide& in, const TileSide& out,
                 Flat32 spill, int* spill_count, long long spill_cap, int grid, int* work, const CUtensorMap* fmap,
-                const CUtensorMap* jmap, int* status, bool stream, cudaStream_t s) {
+                const CUtensorMap* jmap, int* status, bool stream, int minb, cudaStream_t s) {
   (void)L;
   const TileArgs A = make_args(C, tg, in, out, spill, spill_count, spill_cap, work, status);
   cudaMemsetAsync(work, 0, sizeof(int), s);
@@ -1982,7 +1985,7 @@ void tiled_push(const Layout& L, const PushConst& C, const Tiles& tg, const Tile
   }
 #define X(N, A_, B_, C_)                                   \
   if (shape_is(tg.ndim, T, N, A_, B_, C_)) {               \
-    if (g_minb == 2)                                       \
+    if (minb == 2)                                         \
       launch_push<N, A_, B_, C_, 2>(fmap, jmap, A, grid, s); \
     else                                                   \
       launch_push<N, A_, B_, C_, 3>(fmap, jmap, A, grid, s); \

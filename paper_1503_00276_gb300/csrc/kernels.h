@@ -94,7 +94,7 @@ struct TileSide {
 // slots where particles left); false: the step that re-sorts every tile
 void tiled_push(const Layout& L, const PushConst& C, const Tiles& tg, const TileSide& in, const TileSide& out,
                 Flat32 spill, int* spill_count, long long spill_cap, int grid, int* work, const CUtensorMap* fmap,
-                const CUtensorMap* jmap, int* status, bool stream, cudaStream_t s);
+                const CUtensorMap* jmap, int* status, bool stream, int minb, cudaStream_t s);
 int tiled_stream_grid(int ndim, const int T[3], int ntiles);
 // Batched form: many simulations (one table entry per simulation and species)
 // in one launch of the sorting kernel.  tiled_fill_args writes one entry
@@ -104,16 +104,15 @@ int tiled_stream_grid(int ndim, const int T[3], int ntiles);
 size_t tiled_args_bytes();
 void tiled_fill_args(void* dst, const PushConst& C, const Tiles& tg, const TileSide& in, const TileSide& out,
                      Flat32 spill, int* spill_count, long long spill_cap, int* status);
-int tiled_batch_grid(int ndim, const int T[3], int total_tiles);
+int tiled_batch_grid(int ndim, const int T[3], int total_tiles, int minb);
 bool tiled_push_batch(int ndim, const int T[3], const void* args, const CUtensorMap* fmaps, const CUtensorMap* jmaps,
-                      const int* tile0, int n, int* work, int grid, cudaStream_t s);
+                      const int* tile0, int n, int* work, int grid, int minb, cudaStream_t s);
 void tiled_live(const Tiles& tg, const TileSide& in, int* live, cudaStream_t s);
 int tiled_push_smem_bytes(int ndim, const int T[3]);
-int tiled_push_grid(int ndim, const int T[3], int ntiles, bool small);  // persistent CTAs
+int tiled_push_grid(int ndim, const int T[3], int ntiles, bool small, int minb);  // persistent CTAs
 bool tiled_has_general(int ndim, const int T[3]);
 bool tiled_has_small(int ndim, const int T[3]);
 int tiled_small_capacity();  // largest tile region the small-tile kernel stages
-void tiled_push_set_minb(int minb);  // CTAs per SM the tile kernel is built for (2 or 3)
 void tiled_flatten(const Tiles& tg, const TileSide& in, const long long* out_off, Flat32 out, cudaStream_t s);
 void flat_count(const Flat32& f, long long n, int ntiles, int* counts, cudaStream_t s);
 void flat_scatter(const Flat32& f, long long n, const Tiles& tg, int* cursor, Part32 out, cudaStream_t s);

@@ -40,7 +40,7 @@ def test_struct_layouts_match_header(capi, tmp_path):
     import subprocess
     prog = tmp_path / "layout.c"
     fields = {"pic_grid": capi.PicGrid, "pic_species": capi.PicSpecies, "pic_diag_t": capi.PicDiag,
-              "pic_allocator": capi.PicAllocator}
+              "pic_allocator": capi.PicAllocator, "pic_tune_choice": capi.PicTuneChoice}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "pic.h"', "int main(void) {"]
     for cname, cls in fields.items():
         lines.append(f'  printf("{cname} %zu\\n", sizeof({cname}));')
@@ -122,3 +122,19 @@ def test_batch_arguments_are_checked_before_any_device_work(capi):
     assert b"FP32" in lib.pic_last_error()
     assert not h.value
     assert lib.pic_batch_destroy(None) == 0
+
+
+def test_autotune_arguments_are_checked_before_any_device_work(capi):
+    from paper_1503_00276_gb300 import _grid_struct, _species_struct
+    lib = capi.load()
+    best = capi.PicTuneChoice()
+    dx = (0.1, 0.1, 0.1)
+    g = workload.Grid(ndim=2, nx=(20, 12, 1), dx=dx, dt=workload.courant_dt(dx, 2))  # no tile shape divides it
+    gs = _grid_struct(g, 1)
+    sp = _species_struct(workload.Species(ppc=(1, 1, 1)))[0]
+    n = C.c_int()
+    assert lib.pic_autotune(C.byref(gs), C.byref(sp), 1, None, None, 1, 2, C.byref(best), None, 0, C.byref(n)) == -1
+    assert b"divides" in lib.pic_last_error()
+    assert lib.pic_autotune(C.byref(gs), C.byref(sp), 1, None, None, 1, 0, C.byref(best), None, 0, None) == -1
+    g64 = _grid_struct(workload.Grid(ndim=2, nx=(64, 32, 1), dx=dx, dt=workload.courant_dt(dx, 2)), 0)
+    assert lib.pic_autotune(C.byref(g64), C.byref(sp), 1, None, None, 1, 2, C.byref(best), None, 0, None) == -1

@@ -113,8 +113,7 @@ struct SpeciesState {
   long long slots = 0;
   Flat32 spill{};
   long long spill_cap = 0;
-  int grid = 0;             // persistent CTAs of the sorting tile kernel
-  int grid_stream = 0;      // ... and of the in-place streaming kernel
+  int grid = 0;             // persistent CTAs of the tile kernel
   int* work = nullptr;      // its dynamic tile counter
 };
 
@@ -414,7 +413,6 @@ pic_status bin_flat(pic_sim* S, SpeciesState& sp, Flat32& flat, long long n) {
   sp.tg.small = !S->no_small && tiled_has_small(S->ndim, S->T) &&
                 (max_cap <= tiled_small_capacity() || !tiled_has_general(S->ndim, S->T));
   sp.grid = tiled_push_grid(S->ndim, S->T, nt, sp.tg.small != 0, S->minb);
-  sp.grid_stream = tiled_stream_grid(S->ndim, S->T, nt);
   cudaMemcpyAsync(sp.tg.cap, hcap.data(), 4 * (size_t)nt, cudaMemcpyHostToDevice, S->s);
   cudaMemcpyAsync(sp.tg.res, hres.data(), 4 * (size_t)nt, cudaMemcpyHostToDevice, S->s);
   cudaMemcpyAsync(sp.tg.base, hbase.data(), 8 * (size_t)nt, cudaMemcpyHostToDevice, S->s);
@@ -773,7 +771,7 @@ pic_status one_step(pic_sim* S, bool check_now) {
         // the steps before it keep the order they find (blocks compacted)
         const bool stream = S->sort_period > 1 && !s.tg.small && (S->step + 1) % S->sort_period != 0;
         tiled_push(S->L, C, s.tg, s.side[in], s.side[out], s.spill, &S->dstat->spill_count, s.spill_cap,
-                   stream ? s.grid_stream : s.grid, s.work, &S->fmap, &S->jmap, &S->dstat->status, stream, S->minb,
+                   s.grid, s.work, &S->fmap, &S->jmap, &S->dstat->status, stream, S->minb,
                    S->s);
         s.cur = out;
       }

@@ -457,6 +457,25 @@ __device__ inline void store_particle(const Part32& o, long long s, const P& q) 
   if (o.id) o.id[s] = q.id;
 }
 
+// A particle that left tile (tix, tiy, tiz): appended, with one global atomic,
+// to the arrival slots at the back of its new tile's output region (spill
+// list when they are full).
+template <int NDIM>
+__device__ inline void store_leaver(const TileArgs& A, int tix, int tiy, int tiz, const P& q) {
+  const int dir = (int)(q.cell >> 24);
+  const int ix = (tix + dir % 3 - 1 + A.nt[0]) % A.nt[0];
+  const int iy = (tiy + (dir / 3) % 3 - 1 + A.nt[1]) % A.nt[1];
+  const int iz = (tiz + dir / 9 - 1 + A.nt[2]) % A.nt[2];
+  const int dt_ = (iz * A.nt[1] + iy) * A.nt[0] + ix;
+  P q2 = q;
+  q2.cell = (q.cell & 0x00FFFFFFu) | ((uint32_t)DIR_STAY << 24);
+  const int slot = atomicAdd(&A.out.inc[dt_], 1);
+  if (slot < A.res[dt_])
+    store_particle<NDIM>(A.out.p, A.base[dt_] + A.cap[dt_] - 1 - slot, q2);
+  else
+    spill_put(A, dt_, q2);
+}
+
 // Counting sort of one chunk of advanced particles (still in registers) by key
 // and write-out: stayers to the front of this tile's output region in cell
 // order, leavers to the back of their new tile's output region.
@@ -525,52 +544,87 @@ __device__ inline void sort_and_store(const TileArgs& A, int t, int tix, int tiy
   }
   __syncthreads();
   const int nst = misc[6];
-  // rank within key (a run of equal keys takes one atomic) and write
+  // rank within key (a run of equal keys takes one atomic) and write; every
+  // index into pp/key is a compile-time constant, so the chunk stays in
+  // registers
   {
-    int r = 0;
-    while (r < nvalid) {
-      const int k = key[r];
-      int n = 1;
-      while (r + n < nvalid && key[r + n] == k) ++n;
-      if (k >= G::NK) {  // empty slot or dropped particle: not written
-        r += n;
-        continue;
-      }
-      const int p0 = atomicAdd(&hist[k], n);
-      for (int m = 0; m < n; ++m) {
-        const P& q = pp[r + m];
+    int p0 = 0, rs = 0;
+#pragma unroll
+    for (int r = 0; r < PPT; ++r) {
+      if (r < nvalid) {
+        const int k = key[r];
+        if (r == 0 || key[r > 0 ? r - 1 : 0] != k) {  // first of a run of equal keys
+          int n = 1;
+#pragma unroll
+          for (int m = r + 1; m < PPT; ++m)
+            if (m < nvalid && n == m - r && key[m] == k) ++n;
+          if (k < G::NK) p0 = atomicAdd(&hist[k], n);
+          rs = r;
+        }
         if (k < G::NC) {
-          const int pos = ws + p0 + m;
+          const int pos = ws + p0 + (r - rs);
           if (pos < room)
-            store_particle<NDIM>(A.out.p, base + pos, q);
+            store_particle<NDIM>(A.out.p, base + pos, pp[r]);
           else
-            spill_put(A, t, q);
-        } else {
-          const int dir = (int)(q.cell >> 24);
-          int ix = (tix + dir % 3 - 1 + A.nt[0]) % A.nt[0];
-          int iy = (tiy + (dir / 3) % 3 - 1 + A.nt[1]) % A.nt[1];
-          int iz = (tiz + dir / 9 - 1 + A.nt[2]) % A.nt[2];
-          const int dt_ = (iz * A.nt[1] + iy) * A.nt[0] + ix;
-          P q2 = q;
-          q2.cell = (q.cell & 0x00FFFFFFu) | ((uint32_t)DIR_STAY << 24);
-          const int slot = atomicAdd(&A.out.inc[dt_], 1);
-          if (slot < A.res[dt_])
-            store_particle<NDIM>(A.out.p, A.base[dt_] + A.cap[dt_] - 1 - slot, q2);
-          else
-            spill_put(A, dt_, q2);
+            spill_put(A, t, pp[r]);
+        } else if (k < G::NK) {
+          store_leaver<NDIM>(A, tix, tiy, tiz, pp[r]);
         }
       }
-      r += n;
     }
   }
   ws += nst;
+}
+
+// The step between two re-sorts: the chunk's stayers go to the front of the
+// tile's output region in the order they were read (one block scan instead of
+// the counting sort), leavers to their new tile as in sort_and_store.
+template <int NDIM, int TX, int TY, int TZ>
+__device__ inline void compact_and_store(const TileArgs& A, int t, int tix, int tiy, int tiz, long long base, int room,
+                                         P (&pp)[kPPT], int (&key)[kPPT], int nvalid, int& ws, int* misc) {
+  using G = Geo<NDIM, TX, TY, TZ>;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  int cnt = 0;
+#pragma unroll
+  for (int r = 0; r < kPPT; ++r) cnt += r < nvalid && key[r] < G::NC;
+  int x = cnt;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) misc[8 + warp] = x;
+  __syncthreads();
+  int pre = 0, total = 0;
+#pragma unroll
+  for (int w = 0; w < kThreads / 32; ++w) {
+    const int v = misc[8 + w];
+    pre += w < warp ? v : 0;
+    total += v;
+  }
+  int pos = ws + pre + x - cnt;
+#pragma unroll
+  for (int r = 0; r < kPPT; ++r) {
+    if (r >= nvalid || key[r] >= G::NK) continue;  // empty slot or dropped particle
+    const P& q = pp[r];
+    if (key[r] < G::NC) {
+      if (pos < room)
+        store_particle<NDIM>(A.out.p, base + pos, q);
+      else
+        spill_put(A, t, q);
+      ++pos;
+    } else {
+      store_leaver<NDIM>(A, tix, tiy, tiz, q);
+    }
+  }
+  ws += total;
 }
 
 // Everything the sorting kernel does for tile t of one simulation (A): stage
 // the fields, advance, sort and store every particle of the tile, flush the
 // current.  Called by all threads of the block; false if a bounded wait gave
 // up (the block then stops).
-template <int NDIM, int TX, int TY, int TZ>
+template <int NDIM, int TX, int TY, int TZ, bool SORT>
 __device__ inline bool sort_tile(const TileArgs& A, const CUtensorMap* fmap, const CUtensorMap* jmap, int t,
                                  unsigned char* smem, uint32_t& phase) {
   using G = Geo<NDIM, TX, TY, TZ>;
@@ -659,7 +713,10 @@ __device__ inline bool sort_tile(const TileArgs& A, const CUtensorMap* fmap, con
                                                     : Geo<NDIM, TX, TY, TZ>::NK;
       acc_flush<NDIM, TX, TY, TZ>(J, acc);
     }
-    sort_and_store<NDIM, TX, TY, TZ>(A, t, tix, tiy, tiz, base, room, pp, key, nvalid, ws, hist, misc);
+    if constexpr (SORT)
+      sort_and_store<NDIM, TX, TY, TZ>(A, t, tix, tiy, tiz, base, room, pp, key, nvalid, ws, hist, misc);
+    else
+      compact_and_store<NDIM, TX, TY, TZ>(A, t, tix, tiy, tiz, base, room, pp, key, nvalid, ws, misc);
     __syncthreads();
     const int nq = misc[1];
     if (nq > kQCap / 2) {
@@ -691,7 +748,7 @@ __device__ inline bool sort_tile(const TileArgs& A, const CUtensorMap* fmap, con
   return true;
 }
 
-template <int NDIM, int TX, int TY, int TZ, int MINB>
+template <int NDIM, int TX, int TY, int TZ, int MINB, bool SORT = true>
 __global__ void __launch_bounds__(kThreads, MINB)
     k_tile_push(const __grid_constant__ CUtensorMap fmap, const __grid_constant__ CUtensorMap jmap, TileArgs A) {
   using G = Geo<NDIM, TX, TY, TZ>;
@@ -713,7 +770,7 @@ __global__ void __launch_bounds__(kThreads, MINB)
     __syncthreads();
     const int t = misc[0];
     if (t >= A.ntiles) break;
-    if (!sort_tile<NDIM, TX, TY, TZ>(A, &fmap, &jmap, t, smem, phase)) return;
+    if (!sort_tile<NDIM, TX, TY, TZ, SORT>(A, &fmap, &jmap, t, smem, phase)) return;
   }
 }
 
@@ -766,7 +823,7 @@ __global__ void __launch_bounds__(kThreads, MINB) k_tile_push_batch(const BatchT
     const int w = misc[0];
     if (w >= total) break;
     const int s = misc[2];
-    if (!sort_tile<NDIM, TX, TY, TZ>(B.args[s], B.fmaps + s, B.jmaps + s, w - B.tile0[s], smem, phase)) return;
+    if (!sort_tile<NDIM, TX, TY, TZ, true>(B.args[s], B.fmaps + s, B.jmaps + s, w - B.tile0[s], smem, phase)) return;
   }
 }
 
@@ -1125,347 +1182,6 @@ __global__ void __launch_bounds__(kThreads, 3)
 }
 
 
-// ============================================================================
-// Streaming kernel: the step between two sorting steps.  Warps walk their own
-// 128-particle blocks of a tile with no block barrier; the particles that stay
-// in the tile are written back compacted, block by block, in the order they
-// were read (so the cell order of the last sort mostly survives without any
-// block-wide sort), and a particle that left is appended to its new tile's
-// arrival slots.  Pieces after a face crossing go to a per-warp queue that the
-// warp drains 32 at a time.
-// ============================================================================
-constexpr int kWarps = kThreads / 32;
-constexpr int kWQ = 64;                   // per-warp queue entries
-
-template <int NDIM, int TX, int TY, int TZ>
-struct GeoT {
-  using G = Geo<NDIM, TX, TY, TZ>;
-  static constexpr int QW = 8;  // cell, ax, ay, az, bx, by, bz, v3
-  static constexpr int FOFF = 0;
-  static constexpr int JOFF = ((G::FBYTES + 127) / 128) * 128;
-  static constexpr int QOFF = JOFF + ((G::JBYTES + 127) / 128) * 128;
-  static constexpr int MOFF = QOFF + kWarps * kWQ * QW * 4;
-  static constexpr int SMEM = MOFF + 256;
-};
-
-// Gather + push + move of one particle and its first in-cell piece (into the
-// accumulator).  Returns its key (new cell or NC when it left the tile),
-// rewrites p in the coordinates of the tile it ends in and, when the path
-// crosses a face, sets `crosses` and the path in cell units for the queue.
-template <int NDIM, int TX, int TY, int TZ>
-__device__ inline int push_core(const float* F, float* J, const TileArgs& A, P& p, Acc& acc, bool& crosses,
-                                float (&path)[8]) {
-  using G = Geo<NDIM, TX, TY, TZ>;
-  crosses = false;
-  const int lx = p.cell & 255, ly = (p.cell >> 8) & 255, lz = NDIM == 3 ? (p.cell >> 16) & 255 : 0;
-  if (lx >= TX || ly >= TY || lz >= TZ) {
-    atomicOr(A.status, ST_BADCELL);
-    return G::NC + 1;  // dropped
-  }
-  const int cellp = lx | (ly << 8) | (lz << 16);
-  const bool hx = p.o0 < 0.5f, hy = p.o1 < 0.5f, hz = p.o2 < 0.5f;
-  const int x1 = lx - hx, y1 = ly - hy, z1 = lz - hz;
-  const float wx1 = p.o0 + (hx ? 0.5f : -0.5f);
-  const float wy1 = p.o1 + (hy ? 0.5f : -0.5f);
-  const float wz1 = p.o2 + (hz ? 0.5f : -0.5f);
-  constexpr int FX = G::FX, FY = G::FY, FP = G::FPL;
-  float e1, e2, e3, b1, b2, b3;
-  if (NDIM == 3) {
-    e1 = interp<3, FX, FY>(F + 0 * FP, x1, ly, lz, wx1, p.o1, p.o2);
-    e2 = interp<3, FX, FY>(F + 1 * FP, lx, y1, lz, p.o0, wy1, p.o2);
-    e3 = interp<3, FX, FY>(F + 2 * FP, lx, ly, z1, p.o0, p.o1, wz1);
-    b1 = interp<3, FX, FY>(F + 3 * FP, lx, y1, z1, p.o0, wy1, wz1);
-    b2 = interp<3, FX, FY>(F + 4 * FP, x1, ly, z1, wx1, p.o1, wz1);
-    b3 = interp<3, FX, FY>(F + 5 * FP, x1, y1, lz, wx1, wy1, p.o2);
-  } else {
-    e1 = interp<2, FX, FY>(F + 0 * FP, x1, ly, 0, wx1, p.o1, 0.f);
-    e2 = interp<2, FX, FY>(F + 1 * FP, lx, y1, 0, p.o0, wy1, 0.f);
-    e3 = interp<2, FX, FY>(F + 2 * FP, lx, ly, 0, p.o0, p.o1, 0.f);
-    b1 = interp<2, FX, FY>(F + 3 * FP, lx, y1, 0, p.o0, wy1, 0.f);
-    b2 = interp<2, FX, FY>(F + 4 * FP, x1, ly, 0, wx1, p.o1, 0.f);
-    b3 = interp<2, FX, FY>(F + 5 * FP, x1, y1, 0, wx1, wy1, 0.f);
-  }
-  const float al = A.qmdt2;
-  const float ae1 = al * (e1 + A.e0[0]), ae2 = al * (e2 + A.e0[1]), ae3 = al * (e3 + A.e0[2]);
-  // Boris push
-  const float p1x = p.u0 + ae1, p1y = p.u1 + ae2, p1z = p.u2 + ae3;
-  const float ig = rsqrtf(fmaf(p1x, p1x, fmaf(p1y, p1y, fmaf(p1z, p1z, 1.f))));
-  const float ag = al * ig;
-  const float tx = ag * (b1 + A.b0[0]), ty = ag * (b2 + A.b0[1]), tz = ag * (b3 + A.b0[2]);
-  const float p2x = fmaf(p1y, tz, fmaf(-p1z, ty, p1x));
-  const float p2y = fmaf(p1z, tx, fmaf(-p1x, tz, p1y));
-  const float p2z = fmaf(p1x, ty, fmaf(-p1y, tx, p1z));
-  const float sf = __fdividef(2.f, fmaf(tx, tx, fmaf(ty, ty, fmaf(tz, tz, 1.f))));
-  const float sx = tx * sf, sy = ty * sf, sz = tz * sf;
-  const float ux = fmaf(p2y, sz, fmaf(-p2z, sy, p1x)) + ae1;
-  const float uy = fmaf(p2z, sx, fmaf(-p2x, sz, p1y)) + ae2;
-  const float uz = fmaf(p2x, sy, fmaf(-p2y, sx, p1z)) + ae3;
-  // position update in cell units
-  const float u2 = fmaf(ux, ux, fmaf(uy, uy, uz * uz));
-  if (!(u2 < 1e36f)) {  // NaN or Inf
-    atomicOr(A.status, ST_NONFINITE);
-    return lx + TX * (ly + TY * lz);
-  }
-  const float ig2 = rsqrtf(1.f + u2);
-  const float ax = p.o0, ay = p.o1, az = NDIM == 3 ? p.o2 : 0.f;
-  const float bx = fmaf(ux * ig2, A.dt_dx[0], ax);
-  const float by = fmaf(uy * ig2, A.dt_dx[1], ay);
-  const float bz = NDIM == 3 ? fmaf(uz * ig2, A.dt_dx[2], az) : 0.f;
-  const float v3 = uz * ig2;
-  // first in-cell piece: up to the first face crossing (parameters by fast
-  // division; the crossing coordinate itself is set exactly to the face)
-  const bool cx_ = bx < 0.f || bx >= 1.f, cy_ = by < 0.f || by >= 1.f, cz_ = NDIM == 3 && (bz < 0.f || bz >= 1.f);
-  float t1 = 1.f, qx = bx, qy = by, qz = bz;
-  if (cx_ || cy_ || cz_) {
-    const float tcx = cx_ ? __fdividef(bx < 0.f ? ax : 1.f - ax, fabsf(bx - ax)) : 2.f;
-    const float tcy = cy_ ? __fdividef(by < 0.f ? ay : 1.f - ay, fabsf(by - ay)) : 2.f;
-    const float tcz = cz_ ? __fdividef(bz < 0.f ? az : 1.f - az, fabsf(bz - az)) : 2.f;
-    t1 = fminf(tcx, fminf(tcy, tcz));
-    const int w = (t1 == tcx) ? 0 : ((t1 == tcy) ? 1 : 2);
-    qx = w == 0 ? (bx < 0.f ? 0.f : 1.f) : fmaf(t1, bx - ax, ax);
-    qy = w == 1 ? (by < 0.f ? 0.f : 1.f) : fmaf(t1, by - ay, ay);
-    qz = w == 2 ? (bz < 0.f ? 0.f : 1.f) : fmaf(t1, bz - az, az);
-    crosses = true;
-    path[0] = __int_as_float(cellp);
-    path[1] = ax;
-    path[2] = ay;
-    path[3] = az;
-    path[4] = bx;
-    path[5] = by;
-    path[6] = bz;
-    path[7] = v3;
-  }
-  if (acc.cell != cellp) {
-    acc_flush<NDIM, TX, TY, TZ>(J, acc);
-    acc.cell = cellp;
-  }
-  {
-    float w[12];
-    seg_weights<NDIM>(A, ax, ay, az, qx, qy, qz, v3 * t1, w);
-#pragma unroll
-    for (int k = 0; k < (NDIM == 3 ? 12 : 8); ++k) acc.w[k] += w[k];
-  }
-  // new cell and offset
-  float fx = floorf(bx), fy = floorf(by), fz = NDIM == 3 ? floorf(bz) : 0.f;
-  float nx = bx - fx, ny = by - fy, nz = bz - fz;
-  if (nx >= 1.f) { nx = 0.f; fx += 1.f; }
-  if (ny >= 1.f) { ny = 0.f; fy += 1.f; }
-  if (NDIM == 3 && nz >= 1.f) { nz = 0.f; fz += 1.f; }
-  int gx = lx + (int)fx, gy = ly + (int)fy, gz = lz + (int)fz;
-  const int dx_ = (gx >= TX) - (gx < 0), dy_ = (gy >= TY) - (gy < 0);
-  const int dz_ = NDIM == 3 ? (gz >= TZ) - (gz < 0) : 0;
-  gx -= dx_ * TX;
-  gy -= dy_ * TY;
-  gz -= dz_ * TZ;
-  const int dir = (dx_ + 1) + 3 * (dy_ + 1) + 9 * (dz_ + 1);
-  p.cell = (uint32_t)gx | ((uint32_t)gy << 8) | ((uint32_t)gz << 16) | ((uint32_t)dir << 24);
-  p.o0 = nx;
-  p.o1 = ny;
-  p.o2 = NDIM == 3 ? nz : 0.f;
-  p.u0 = ux;
-  p.u1 = uy;
-  p.u2 = uz;
-  return dir == DIR_STAY ? gx + TX * (gy + TY * gz) : G::NC;
-}
-
-// Remaining pieces of n queued paths (lane i takes entry i); all but the first
-// piece of each path are deposited.
-template <int NDIM, int TX, int TY, int TZ>
-__device__ inline void drain_paths(float* J, const TileArgs& A, const float* Qw, int n) {
-  using G = Geo<NDIM, TX, TY, TZ>;
-  const int lane = threadIdx.x & 31;
-  if (lane < n) {
-    const float* e = Qw + lane * 8;
-    const int c = __float_as_int(e[0]);
-    const int lx = c & 255, ly = (c >> 8) & 255, lz = (c >> 16) & 255;
-    const float v3 = e[7];
-    walk<NDIM>(e[1], e[2], NDIM == 3 ? e[3] : 0.f, e[4], e[5], NDIM == 3 ? e[6] : 0.f,
-               [&](int k, int ox, int oy, int oz, float sx0, float sy0, float sz0, float sx1, float sy1, float sz1,
-                   float frac) {
-                 if (k == 0) return;
-                 float w[12];
-                 seg_weights<NDIM>(A, sx0, sy0, sz0, sx1, sy1, sz1, v3 * frac, w);
-                 flush_cell<NDIM, G::JX, G::JY, G::JPL>(J, lx + ox, ly + oy, lz + oz, w);
-               });
-  }
-}
-
-template <int NDIM, int TX, int TY, int TZ>
-__global__ void __launch_bounds__(kThreads, 2)
-    k_tile_stream(const __grid_constant__ CUtensorMap fmap, const __grid_constant__ CUtensorMap jmap, TileArgs A) {
-  using G = Geo<NDIM, TX, TY, TZ>;
-  using S = GeoT<NDIM, TX, TY, TZ>;
-  extern __shared__ __align__(1024) unsigned char smem[];
-  float* F = reinterpret_cast<float*>(smem + S::FOFF);
-  float* J = reinterpret_cast<float*>(smem + S::JOFF);
-  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + S::MOFF);
-  int* misc = reinterpret_cast<int*>(smem + S::MOFF + 16);  // [0] tile, [8..15] per-warp queue counts
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  float* Qw = reinterpret_cast<float*>(smem + S::QOFF) + warp * kWQ * S::QW;
-  int& qn = misc[8 + warp];
-  const bool has_id = A.in.p.id != nullptr;
-
-  if (tid == 0) {
-    mbar_init(bar, 1);
-    fence_barrier_init();
-  }
-  uint32_t phase = 0;
-  for (;;) {
-    __syncthreads();
-    if (tid == 0) misc[0] = atomicAdd(A.work, 1);
-    __syncthreads();
-    const int t = misc[0];
-    if (t >= A.ntiles) break;
-    const int tix = t % A.nt[0], tiy = (t / A.nt[0]) % A.nt[1], tiz = t / (A.nt[0] * A.nt[1]);
-    if (tid == 0) {
-      mbar_arrive_expect_tx(bar, (uint32_t)G::FBYTES);
-      if (NDIM == 3)
-        tma_load_4d(F, &fmap, bar, tix * TX, tiy * TY, tiz * TZ, 0);
-      else
-        tma_load_3d(F, &fmap, bar, tix * TX, tiy * TY, 0);
-    }
-    for (int k = tid; k < 3 * G::JPL; k += kThreads) J[k] = 0.f;
-    if (lane == 0) qn = 0;
-    if (tid == 0) misc[1] = 0;
-    const long long base = A.base[t];
-    const int cap = A.cap[t];
-    const int room = cap - A.res[t];
-    const int ns = A.in.stay[t];
-    int ni = A.in.inc[t];
-    ni = ni < A.res[t] ? ni : A.res[t];
-    const int i0 = cap - ni;           // first arrival slot
-    const int a0 = i0 & ~3;            // 16-byte aligned start of the arrival blocks
-    const int nbs = (ns + 127) >> 7;   // 128-particle blocks of stayers ...
-    const int nbi = ni > 0 ? (cap - a0 + 127) >> 7 : 0;  // ... and of arrivals
-    const bool ok = mbar_wait_bounded(bar, phase, kWaitLimit);
-    if (__syncthreads_or(!ok)) {
-      if (tid == 0) atomicOr(A.status, ST_TIMEOUT);
-      mbar_wait_bounded(bar, phase, kWaitLimit);
-      break;
-    }
-    phase ^= 1u;
-
-    for (int b = warp; b < nbs + nbi; b += kWarps) {
-      const bool arr = b >= nbs;
-      const int s0 = arr ? a0 + ((b - nbs) << 7) + lane * 4 : (b << 7) + lane * 4;
-      const int lo = arr ? i0 : 0, hi = arr ? cap : ns;
-      P pp[4];
-      bool live[4];
-      if (s0 < hi) {
-        const long long s = base + s0;
-        const uint4 cl = *reinterpret_cast<const uint4*>(A.in.p.cell + s);
-        const float4 q0 = *reinterpret_cast<const float4*>(A.in.p.o[0] + s);
-        const float4 q1 = *reinterpret_cast<const float4*>(A.in.p.o[1] + s);
-        float4 q2 = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (NDIM == 3) q2 = *reinterpret_cast<const float4*>(A.in.p.o[2] + s);
-        const float4 v0 = *reinterpret_cast<const float4*>(A.in.p.u[0] + s);
-        const float4 v1 = *reinterpret_cast<const float4*>(A.in.p.u[1] + s);
-        const float4 v2 = *reinterpret_cast<const float4*>(A.in.p.u[2] + s);
-        int4 idv = make_int4(0, 0, 0, 0);
-        if (has_id) idv = *reinterpret_cast<const int4*>(A.in.p.id + s);
-        pp[0] = P{cl.x, q0.x, q1.x, q2.x, v0.x, v1.x, v2.x, idv.x};
-        pp[1] = P{cl.y, q0.y, q1.y, q2.y, v0.y, v1.y, v2.y, idv.y};
-        pp[2] = P{cl.z, q0.z, q1.z, q2.z, v0.z, v1.z, v2.z, idv.z};
-        pp[3] = P{cl.w, q0.w, q1.w, q2.w, v0.w, v1.w, v2.w, idv.w};
-      }
-#pragma unroll
-      for (int r = 0; r < 4; ++r) live[r] = s0 + r >= lo && s0 + r < hi;
-      Acc acc;
-#pragma unroll
-      for (int k = 0; k < 12; ++k) acc.w[k] = 0.f;
-      acc.cell = -1;
-      int key[4];
-#pragma unroll
-      for (int r = 0; r < 4; ++r) {
-        bool crosses = false;
-        float path[8];
-        key[r] = live[r] ? push_core<NDIM, TX, TY, TZ>(F, J, A, pp[r], acc, crosses, path) : G::NC;
-        // per-warp queue of crossing paths
-        const unsigned m = __ballot_sync(0xffffffffu, crosses);
-        if (m) {
-          const int pos = qn + __popc(m & ((1u << lane) - 1u));
-          if (crosses)
-#pragma unroll
-            for (int k = 0; k < 8; ++k) Qw[pos * 8 + k] = path[k];
-          __syncwarp();
-          const int nq = qn + __popc(m);
-          if (nq >= 32) {
-            drain_paths<NDIM, TX, TY, TZ>(J, A, Qw, 32);
-            __syncwarp();
-            if (lane < nq - 32)
-#pragma unroll
-              for (int k = 0; k < 8; ++k) Qw[lane * 8 + k] = Qw[(32 + lane) * 8 + k];
-            __syncwarp();
-            if (lane == 0) qn = nq - 32;
-          } else if (lane == 0) {
-            qn = nq;
-          }
-          __syncwarp();
-        }
-      }
-      acc_flush<NDIM, TX, TY, TZ>(J, acc);
-      // write back, compacted: the particles that stay in this tile take the
-      // next free slots of the tile (their order within the block is kept)
-      bool st[4];
-      int before = 0, total = 0;
-      const unsigned lt = (1u << lane) - 1u;
-#pragma unroll
-      for (int r = 0; r < 4; ++r) {
-        st[r] = live[r] && key[r] < G::NC;
-        const unsigned m = __ballot_sync(0xffffffffu, st[r]);
-        before += __popc(m & lt);
-        total += __popc(m);
-      }
-      int off = 0;
-      if (lane == 0 && total > 0) off = atomicAdd(&misc[1], total);
-      off = __shfl_sync(0xffffffffu, off, 0) + before;
-#pragma unroll
-      for (int r = 0; r < 4; ++r) {
-        if (!st[r]) continue;
-        if (off < room)
-          store_particle<NDIM>(A.out.p, base + off, pp[r]);
-        else
-          spill_put(A, t, pp[r]);
-        ++off;
-      }
-#pragma unroll
-      for (int r = 0; r < 4; ++r) {
-        if (!live[r]) continue;
-        const P& q = pp[r];
-        if (key[r] == G::NC) {
-          const int dir = (int)(q.cell >> 24);
-          const int ix = (tix + dir % 3 - 1 + A.nt[0]) % A.nt[0];
-          const int iy = (tiy + (dir / 3) % 3 - 1 + A.nt[1]) % A.nt[1];
-          const int iz = (tiz + dir / 9 - 1 + A.nt[2]) % A.nt[2];
-          const int dt_ = (iz * A.nt[1] + iy) * A.nt[0] + ix;
-          P q2 = q;
-          q2.cell = (q.cell & 0x00FFFFFFu) | ((uint32_t)DIR_STAY << 24);
-          const int slot = atomicAdd(&A.out.inc[dt_], 1);
-          if (slot < A.res[dt_])
-            store_particle<NDIM>(A.out.p, A.base[dt_] + A.cap[dt_] - 1 - slot, q2);
-          else
-            spill_put(A, dt_, q2);
-        }
-      }
-    }
-    // each warp drains what is left in its queue
-    __syncwarp();
-    drain_paths<NDIM, TX, TY, TZ>(J, A, Qw, qn);
-    fence_proxy_async_smem();
-    __syncthreads();
-    if (tid == 0) {
-      const int nst = misc[1];
-      A.out.stay[t] = nst < room ? nst : room;
-      if (NDIM == 3)
-        tma_reduce_add_4d(&jmap, J, tix * TX, tiy * TY, tiz * TZ, 0);
-      else
-        tma_reduce_add_3d(&jmap, J, tix * TX, tiy * TY, 0);
-      tma_commit();
-      tma_wait_read0();
-    }
-  }
-}
-
 // ------------------------------------------------------------ support kernels
 __device__ inline void tile_origin(const Tiles& tg, int t, int o[3]) {
   o[0] = (t % tg.nt[0]) * tg.T[0];
@@ -1703,15 +1419,16 @@ __global__ void k_tiled_kinetic(PushConst C, Tiles tg, TileSide in, double* ke, 
   }
 }
 
-template <int NDIM, int TX, int TY, int TZ, int MINB>
+template <int NDIM, int TX, int TY, int TZ, int MINB, bool SORT = true>
 int occupancy() {
   using G = Geo<NDIM, TX, TY, TZ>;
   static int occ = -1;
   if (occ < 0) {
-    cudaFuncSetAttribute(k_tile_push<NDIM, TX, TY, TZ, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM);
+    cudaFuncSetAttribute(k_tile_push<NDIM, TX, TY, TZ, MINB, SORT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         G::SMEM);
     int o = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_tile_push<NDIM, TX, TY, TZ, MINB>, kThreads, G::SMEM) !=
-            cudaSuccess ||
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_tile_push<NDIM, TX, TY, TZ, MINB, SORT>, kThreads,
+                                                      G::SMEM) != cudaSuccess ||
         o < 1)
       o = 1;
     occ = o;
@@ -1735,34 +1452,11 @@ int occupancy_s() {
   return occ;
 }
 
-template <int NDIM, int TX, int TY, int TZ>
-int occupancy_t() {
-  using S = GeoT<NDIM, TX, TY, TZ>;
-  static int occ = -1;
-  if (occ < 0) {
-    cudaFuncSetAttribute(k_tile_stream<NDIM, TX, TY, TZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM);
-    int o = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_tile_stream<NDIM, TX, TY, TZ>, kThreads, S::SMEM) !=
-            cudaSuccess ||
-        o < 1)
-      o = 1;
-    occ = o;
-  }
-  return occ;
-}
-
-template <int NDIM, int TX, int TY, int TZ>
-void launch_stream(const CUtensorMap* fmap, const CUtensorMap* jmap, const TileArgs& A, int grid, cudaStream_t s) {
-  using S = GeoT<NDIM, TX, TY, TZ>;
-  occupancy_t<NDIM, TX, TY, TZ>();
-  k_tile_stream<NDIM, TX, TY, TZ><<<grid, kThreads, S::SMEM, s>>>(*fmap, *jmap, A);
-}
-
-template <int NDIM, int TX, int TY, int TZ, int MINB>
+template <int NDIM, int TX, int TY, int TZ, int MINB, bool SORT>
 void launch_push(const CUtensorMap* fmap, const CUtensorMap* jmap, const TileArgs& A, int grid, cudaStream_t s) {
   using G = Geo<NDIM, TX, TY, TZ>;
-  occupancy<NDIM, TX, TY, TZ, MINB>();
-  k_tile_push<NDIM, TX, TY, TZ, MINB><<<grid, kThreads, G::SMEM, s>>>(*fmap, *jmap, A);
+  occupancy<NDIM, TX, TY, TZ, MINB, SORT>();
+  k_tile_push<NDIM, TX, TY, TZ, MINB, SORT><<<grid, kThreads, G::SMEM, s>>>(*fmap, *jmap, A);
 }
 
 template <int NDIM, int TX, int TY, int TZ>
@@ -1828,18 +1522,6 @@ int tiled_small_capacity() { return kCapS - 9; }
 
 
 
-int tiled_stream_grid(int ndim, const int T[3], int ntiles) {
-  int dev = 0, sms = 1;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  int occ = 1;
-#define X(N, A_, B_, C_) \
-  if (shape_is(ndim, T, N, A_, B_, C_)) occ = occupancy_t<N, A_, B_, C_>();
-  PICGB_TILE_SHAPES(X)
-#undef X
-  const int g = sms * occ;
-  return g < ntiles ? g : ntiles;
-}
 
 int tiled_push_grid(int ndim, const int T[3], int ntiles, bool small, int minb) {
   int dev = 0, sms = 1;
@@ -1965,15 +1647,6 @@ void tiled_push(const Layout& L, const PushConst& C, const Tiles& tg, const Tile
   cudaMemsetAsync(work, 0, sizeof(int), s);
   cudaMemsetAsync(out.inc, 0, sizeof(int) * (size_t)tg.ntiles, s);
   const int* T = tg.T;
-  if (stream && !tg.small) {
-#define X(N, A_, B_, C_)                                 \
-  if (shape_is(tg.ndim, T, N, A_, B_, C_)) {             \
-    launch_stream<N, A_, B_, C_>(fmap, jmap, A, grid, s); \
-    return;                                              \
-  }
-    PICGB_TILE_SHAPES(X)
-#undef X
-  }
   if (tg.small) {
 #define X(N, A_, B_, C_)                                \
   if (shape_is(tg.ndim, T, N, A_, B_, C_)) {            \
@@ -1983,13 +1656,17 @@ void tiled_push(const Layout& L, const PushConst& C, const Tiles& tg, const Tile
     PICGB_SMALL_SHAPES(X)
 #undef X
   }
-#define X(N, A_, B_, C_)                                   \
-  if (shape_is(tg.ndim, T, N, A_, B_, C_)) {               \
-    if (minb == 2)                                         \
-      launch_push<N, A_, B_, C_, 2>(fmap, jmap, A, grid, s); \
-    else                                                   \
-      launch_push<N, A_, B_, C_, 3>(fmap, jmap, A, grid, s); \
-    return;                                                \
+  // the general kernel: counting sort by cell, or (between re-sorts) the
+  // order-keeping compaction
+#define X(N, A_, B_, C_)                                                    \
+  if (shape_is(tg.ndim, T, N, A_, B_, C_)) {                                \
+    if (minb == 2)                                                          \
+      stream ? launch_push<N, A_, B_, C_, 2, false>(fmap, jmap, A, grid, s) \
+             : launch_push<N, A_, B_, C_, 2, true>(fmap, jmap, A, grid, s); \
+    else                                                                    \
+      stream ? launch_push<N, A_, B_, C_, 3, false>(fmap, jmap, A, grid, s) \
+             : launch_push<N, A_, B_, C_, 3, true>(fmap, jmap, A, grid, s); \
+    return;                                                                 \
   }
   PICGB_TILE_SHAPES(X)
 #undef X

@@ -90,12 +90,11 @@ struct TileSide {
   int* inc;
 };
 
-// stream = true: the in-place step that keeps the last sort's order (empty
-// slots where particles left); false: the step that re-sorts every tile
+// stream = true: the step between re-sorts (stayers keep the order they were
+// read in, compacted); false: the step that counting-sorts every tile by cell
 void tiled_push(const Layout& L, const PushConst& C, const Tiles& tg, const TileSide& in, const TileSide& out,
                 Flat32 spill, int* spill_count, long long spill_cap, int grid, int* work, const CUtensorMap* fmap,
                 const CUtensorMap* jmap, int* status, bool stream, int minb, cudaStream_t s);
-int tiled_stream_grid(int ndim, const int T[3], int ntiles);
 // Batched form: many simulations (one table entry per simulation and species)
 // in one launch of the sorting kernel.  tiled_fill_args writes one entry
 // (tiled_args_bytes bytes) on the host; tile0[n] is the exclusive prefix of

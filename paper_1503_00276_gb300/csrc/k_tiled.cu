@@ -503,6 +503,9 @@ __device__ inline void sort_and_store(const TileArgs& A, int t, int tix, int tiy
     if (hk >= 0) atomicAdd(&hist[hk], hc);
   }
   __syncthreads();
+  // every push of the chunk is done: snapshot of the crossing-queue count, read
+  // by every thread after the caller's next barrier
+  if (tid == 0) misc[5] = misc[1];
   // exclusive scan of hist in place
   {
     constexpr int PER = (G::NK + kThreads - 1) / kThreads;
@@ -595,6 +598,9 @@ __device__ inline void compact_and_store(const TileArgs& A, int t, int tix, int 
   }
   if (lane == 31) misc[8 + warp] = x;
   __syncthreads();
+  // every push of the chunk is done: snapshot of the crossing-queue count,
+  // read by every thread after the caller's next barrier
+  if (tid == 0) misc[5] = misc[1];
   int pre = 0, total = 0;
 #pragma unroll
   for (int w = 0; w < kThreads / 32; ++w) {
@@ -718,7 +724,7 @@ __device__ inline bool sort_tile(const TileArgs& A, const CUtensorMap* fmap, con
     else
       compact_and_store<NDIM, TX, TY, TZ>(A, t, tix, tiy, tiz, base, room, pp, key, nvalid, ws, misc);
     __syncthreads();
-    const int nq = misc[1];
+    const int nq = misc[5];  // the same value in every thread
     if (nq > kQCap / 2) {
       drain_queue<NDIM, TX, TY, TZ>(J, A, Q, nq < kQCap ? nq : kQCap);
       __syncthreads();

@@ -77,7 +77,8 @@ struct Geo {
   static constexpr int HOFF = JOFF + ((JBYTES + 127) / 128) * 128;   // hist[NK]
   static constexpr int QOFF = HOFF + ((NK * 4 + 15) / 16) * 16;      // queue
   static constexpr int MOFF = QOFF + ((kQCap * QW * 4 + 15) / 16) * 16;
-  static constexpr int SMEM = MOFF + 256;
+  static constexpr int NOFF = MOFF + 256;  // the 27 neighbour tiles' regions (Nbr)
+  static constexpr int SMEM = NOFF + 27 * 24;
 };
 
 struct P {
@@ -457,18 +458,51 @@ __device__ inline void store_particle(const Part32& o, long long s, const P& q) 
   if (o.id) o.id[s] = q.id;
 }
 
+// Region of one of the 27 tiles around (and including) the current one, by
+// direction code (dx+1) + 3(dy+1) + 9(dz+1).
+struct Nbr {
+  long long base;
+  int cap, res, tile, pad;
+};
+
+// Thread d < 27 of the block: the region of neighbour d of tile (tix, tiy, tiz).
+__device__ inline void load_neighbour(const TileArgs& A, int tix, int tiy, int tiz, Nbr* nb) {
+  const int d = threadIdx.x;
+  if (d < 27) {
+    const int ix = (tix + d % 3 - 1 + A.nt[0]) % A.nt[0];
+    const int iy = (tiy + (d / 3) % 3 - 1 + A.nt[1]) % A.nt[1];
+    const int iz = (tiz + d / 9 - 1 + A.nt[2]) % A.nt[2];
+    const int dt_ = (iz * A.nt[1] + iy) * A.nt[0] + ix;
+    nb[d].tile = dt_;
+    nb[d].base = A.base[dt_];
+    nb[d].cap = A.cap[dt_];
+    nb[d].res = A.res[dt_];
+  }
+}
+
 // A particle that left tile (tix, tiy, tiz): appended, with one global atomic,
 // to the arrival slots at the back of its new tile's output region (spill
-// list when they are full).
+// list when they are full).  nb: the neighbour regions in shared memory, or
+// nullptr to look them up in global memory.
 template <int NDIM>
-__device__ inline void store_leaver(const TileArgs& A, int tix, int tiy, int tiz, const P& q) {
+__device__ inline void store_leaver(const TileArgs& A, int tix, int tiy, int tiz, const P& q,
+                                    const Nbr* nb = nullptr) {
   const int dir = (int)(q.cell >> 24);
+  P q2 = q;
+  q2.cell = (q.cell & 0x00FFFFFFu) | ((uint32_t)DIR_STAY << 24);
+  if (nb) {
+    const Nbr& n = nb[dir];
+    const int slot = atomicAdd(&A.out.inc[n.tile], 1);
+    if (slot < n.res)
+      store_particle<NDIM>(A.out.p, n.base + n.cap - 1 - slot, q2);
+    else
+      spill_put(A, n.tile, q2);
+    return;
+  }
   const int ix = (tix + dir % 3 - 1 + A.nt[0]) % A.nt[0];
   const int iy = (tiy + (dir / 3) % 3 - 1 + A.nt[1]) % A.nt[1];
   const int iz = (tiz + dir / 9 - 1 + A.nt[2]) % A.nt[2];
   const int dt_ = (iz * A.nt[1] + iy) * A.nt[0] + ix;
-  P q2 = q;
-  q2.cell = (q.cell & 0x00FFFFFFu) | ((uint32_t)DIR_STAY << 24);
   const int slot = atomicAdd(&A.out.inc[dt_], 1);
   if (slot < A.res[dt_])
     store_particle<NDIM>(A.out.p, A.base[dt_] + A.cap[dt_] - 1 - slot, q2);
@@ -481,7 +515,8 @@ __device__ inline void store_leaver(const TileArgs& A, int tix, int tiy, int tiz
 // order, leavers to the back of their new tile's output region.
 template <int NDIM, int TX, int TY, int TZ, int PPT = kPPT>
 __device__ inline void sort_and_store(const TileArgs& A, int t, int tix, int tiy, int tiz, long long base, int room,
-                                      P (&pp)[PPT], int (&key)[PPT], int nvalid, int& ws, int* hist, int* misc) {
+                                      P (&pp)[PPT], int (&key)[PPT], int nvalid, int& ws, int* hist, int* misc,
+                                      const Nbr* nb = nullptr) {
   using G = Geo<NDIM, TX, TY, TZ>;
   const int tid = threadIdx.x;
   __syncthreads();  // previous chunk's ranks read
@@ -571,7 +606,7 @@ __device__ inline void sort_and_store(const TileArgs& A, int t, int tix, int tiy
           else
             spill_put(A, t, pp[r]);
         } else if (k < G::NK) {
-          store_leaver<NDIM>(A, tix, tiy, tiz, pp[r]);
+          store_leaver<NDIM>(A, tix, tiy, tiz, pp[r], nb);
         }
       }
     }
@@ -584,7 +619,8 @@ __device__ inline void sort_and_store(const TileArgs& A, int t, int tix, int tiy
 // the counting sort), leavers to their new tile as in sort_and_store.
 template <int NDIM, int TX, int TY, int TZ>
 __device__ inline void compact_and_store(const TileArgs& A, int t, int tix, int tiy, int tiz, long long base, int room,
-                                         P (&pp)[kPPT], int (&key)[kPPT], int nvalid, int& ws, int* misc) {
+                                         P (&pp)[kPPT], int (&key)[kPPT], int nvalid, int& ws, int* misc,
+                                         const Nbr* nb) {
   using G = Geo<NDIM, TX, TY, TZ>;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   int cnt = 0;
@@ -620,7 +656,7 @@ __device__ inline void compact_and_store(const TileArgs& A, int t, int tix, int 
         spill_put(A, t, q);
       ++pos;
     } else {
-      store_leaver<NDIM>(A, tix, tiy, tiz, q);
+      store_leaver<NDIM>(A, tix, tiy, tiz, q, nb);
     }
   }
   ws += total;
@@ -639,7 +675,10 @@ __device__ inline bool sort_tile(const TileArgs& A, const CUtensorMap* fmap, con
   int* hist = reinterpret_cast<int*>(smem + G::HOFF);
   float* Q = reinterpret_cast<float*>(smem + G::QOFF);
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + G::MOFF);
-  int* misc = reinterpret_cast<int*>(smem + G::MOFF + 16);  // [0] tile [1] queue [6] stayers [7] total [8..15] scan
+  // misc: [0] tile [1] queue count [2] table entry [5] queue-count snapshot
+  // [6] stayers of the chunk [7] chunk total [8..15] scan
+  int* misc = reinterpret_cast<int*>(smem + G::MOFF + 16);
+  Nbr* nb = reinterpret_cast<Nbr*>(smem + G::NOFF);
   const int tid = threadIdx.x;
   const int tix = t % A.nt[0], tiy = (t / A.nt[0]) % A.nt[1], tiz = t / (A.nt[0] * A.nt[1]);
   const int x0 = tix * TX, y0 = tiy * TY, z0 = tiz * TZ;
@@ -651,6 +690,7 @@ __device__ inline bool sort_tile(const TileArgs& A, const CUtensorMap* fmap, con
       tma_load_3d(F, fmap, bar, x0, y0, 0);
   }
   for (int k = tid; k < 3 * G::JPL; k += kThreads) J[k] = 0.f;
+  load_neighbour(A, tix, tiy, tiz, nb);
   const long long base = A.base[t];
   const int cap = A.cap[t];
   const int res = A.res[t];
@@ -720,9 +760,9 @@ __device__ inline bool sort_tile(const TileArgs& A, const CUtensorMap* fmap, con
       acc_flush<NDIM, TX, TY, TZ>(J, acc);
     }
     if constexpr (SORT)
-      sort_and_store<NDIM, TX, TY, TZ>(A, t, tix, tiy, tiz, base, room, pp, key, nvalid, ws, hist, misc);
+      sort_and_store<NDIM, TX, TY, TZ>(A, t, tix, tiy, tiz, base, room, pp, key, nvalid, ws, hist, misc, nb);
     else
-      compact_and_store<NDIM, TX, TY, TZ>(A, t, tix, tiy, tiz, base, room, pp, key, nvalid, ws, misc);
+      compact_and_store<NDIM, TX, TY, TZ>(A, t, tix, tiy, tiz, base, room, pp, key, nvalid, ws, misc, nb);
     __syncthreads();
     const int nq = misc[5];  // the same value in every thread
     if (nq > kQCap / 2) {

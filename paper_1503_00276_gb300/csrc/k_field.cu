@@ -186,6 +186,64 @@ __global__ void k_yee_e(Layout L, Ptr3<T> E, Ptr3<T> B, Ptr3<T> J, T dt, T dx1, 
   E.c[2][c] = E.c[2][c] + dt * (dB2d1 - dB1d2) - dt * J.c[2][c];
 }
 
+// FP32 forms of the two sweeps (the FP32 cell-offset path): multiplication by
+// 1/dx and explicit fused multiply-adds.  The FP64 sweeps above keep the
+// oracle's operation order (divisions, no contraction) for the FP64 parity.
+__global__ void k_yee_b_half_f32(Layout L, Ptr3<float> E, Ptr3<float> B, float h, float i1, float i2, float i3) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int k = blockIdx.z;
+  if (i >= L.nx || j >= L.ny) return;
+  const long long c = L.idx(i, j, k);
+  const long long cx = c + (i + 1 == L.nx ? 1 - L.nx : 1);
+  const long long cy = c + (j + 1 == L.ny ? (long long)(1 - L.ny) * L.NX : L.NX);
+  const float* __restrict__ E1 = E.c[0];
+  const float* __restrict__ E2 = E.c[1];
+  const float* __restrict__ E3 = E.c[2];
+  const float e1 = __ldg(E1 + c), e2 = __ldg(E2 + c), e3 = __ldg(E3 + c);
+  const float dE3d2 = (__ldg(E3 + cy) - e3) * i2;
+  const float dE3d1 = (__ldg(E3 + cx) - e3) * i1;
+  const float dE2d1 = (__ldg(E2 + cx) - e2) * i1;
+  const float dE1d2 = (__ldg(E1 + cy) - e1) * i2;
+  float dE2d3 = 0.f, dE1d3 = 0.f;
+  if (L.ndim == 3) {
+    const long long cz = c + (k + 1 == L.nz ? (long long)(1 - L.nz) * L.NX * L.NY : (long long)L.NX * L.NY);
+    dE2d3 = (__ldg(E2 + cz) - e2) * i3;
+    dE1d3 = (__ldg(E1 + cz) - e1) * i3;
+  }
+  B.c[0][c] = fmaf(-h, dE3d2 - dE2d3, B.c[0][c]);
+  B.c[1][c] = fmaf(-h, dE1d3 - dE3d1, B.c[1][c]);
+  B.c[2][c] = fmaf(-h, dE2d1 - dE1d2, B.c[2][c]);
+}
+
+__global__ void k_yee_e_f32(Layout L, Ptr3<float> E, Ptr3<float> B, Ptr3<float> J, float dt, float i1, float i2,
+                            float i3) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int k = blockIdx.z;
+  if (i >= L.nx || j >= L.ny) return;
+  const long long c = L.idx(i, j, k);
+  const long long cx = c - (i == 0 ? 1 - L.nx : 1);
+  const long long cy = c - (j == 0 ? (long long)(1 - L.ny) * L.NX : L.NX);
+  const float* __restrict__ B1 = B.c[0];
+  const float* __restrict__ B2 = B.c[1];
+  const float* __restrict__ B3 = B.c[2];
+  const float b1 = __ldg(B1 + c), b2 = __ldg(B2 + c), b3 = __ldg(B3 + c);
+  const float dB3d2 = (b3 - __ldg(B3 + cy)) * i2;
+  const float dB3d1 = (b3 - __ldg(B3 + cx)) * i1;
+  const float dB2d1 = (b2 - __ldg(B2 + cx)) * i1;
+  const float dB1d2 = (b1 - __ldg(B1 + cy)) * i2;
+  float dB2d3 = 0.f, dB1d3 = 0.f;
+  if (L.ndim == 3) {
+    const long long cz = c - (k == 0 ? (long long)(1 - L.nz) * L.NX * L.NY : (long long)L.NX * L.NY);
+    dB2d3 = (b2 - __ldg(B2 + cz)) * i3;
+    dB1d3 = (b1 - __ldg(B1 + cz)) * i3;
+  }
+  E.c[0][c] = fmaf(dt, dB3d2 - dB2d3 - __ldg(J.c[0] + c), E.c[0][c]);
+  E.c[1][c] = fmaf(dt, dB1d3 - dB3d1 - __ldg(J.c[1] + c), E.c[1][c]);
+  E.c[2][c] = fmaf(dt, dB2d1 - dB1d2 - __ldg(J.c[2] + c), E.c[2][c]);
+}
+
 // ---------------------------------------------------------------- diagnostics
 __device__ inline double block_sum(double v, double* red) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
@@ -340,13 +398,21 @@ void smooth_pass(const Layout& L, T* comp, T* tmp, int dim, double w0, double w1
 template <typename T>
 void yee_b_half(const Layout& L, T* const* e, T* const* b, double dt, const double dx[3], cudaStream_t s) {
   Ptr3<T> E{{e[0], e[1], e[2]}}, B{{b[0], b[1], b[2]}};
-  k_yee_b_half<T><<<interior_grid(L), kBlock, 0, s>>>(L, E, B, (T)(dt / 2.0), (T)dx[0], (T)dx[1], (T)dx[2]);
+  if constexpr (sizeof(T) == 4)
+    k_yee_b_half_f32<<<interior_grid(L), kBlock, 0, s>>>(L, E, B, (float)(dt / 2.0), (float)(1.0 / dx[0]),
+                                                         (float)(1.0 / dx[1]), (float)(1.0 / dx[2]));
+  else
+    k_yee_b_half<T><<<interior_grid(L), kBlock, 0, s>>>(L, E, B, (T)(dt / 2.0), (T)dx[0], (T)dx[1], (T)dx[2]);
 }
 
 template <typename T>
 void yee_e(const Layout& L, T* const* e, T* const* b, T* const* j, double dt, const double dx[3], cudaStream_t s) {
   Ptr3<T> E{{e[0], e[1], e[2]}}, B{{b[0], b[1], b[2]}}, J{{j[0], j[1], j[2]}};
-  k_yee_e<T><<<interior_grid(L), kBlock, 0, s>>>(L, E, B, J, (T)dt, (T)dx[0], (T)dx[1], (T)dx[2]);
+  if constexpr (sizeof(T) == 4)
+    k_yee_e_f32<<<interior_grid(L), kBlock, 0, s>>>(L, E, B, J, (float)dt, (float)(1.0 / dx[0]),
+                                                    (float)(1.0 / dx[1]), (float)(1.0 / dx[2]));
+  else
+    k_yee_e<T><<<interior_grid(L), kBlock, 0, s>>>(L, E, B, J, (T)dt, (T)dx[0], (T)dx[1], (T)dx[2]);
 }
 
 template <typename T>

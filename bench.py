@@ -384,9 +384,14 @@ def run_e2e(args, g, sps, n_p, tile, barrier, max_over_ranks, sum_over_ranks):
     t0 = time.perf_counter()
     sim = pg.Simulation(g, sps, precision=args.precision, explicit=[(xn, un, q)],
                         tile=tile if args.precision == "fp32" else None, sort_period=args.sort_period)
+    ta = time.perf_counter()
+    t_diag = 0.0
     for _ in range(steps):
         sim.step(1)
+        td = time.perf_counter()
         sim.diag()
+        t_diag += time.perf_counter() - td
+    tb = time.perf_counter()
     got = sim.particles_into(xn, un)
     sim.close()
     torch.cuda.synchronize()
@@ -399,7 +404,9 @@ def run_e2e(args, g, sps, n_p, tile, barrier, max_over_ranks, sum_over_ranks):
     d2h = 2 * n_p * 3 * 8 + steps * 80
     return {"value": value, "unit": UNIT, "h2d_bytes_per_step": h2d / steps, "d2h_bytes_per_step": d2h / steps,
             "job": f"pic_init from pinned host FP64 arrays + {steps} x (pic_step + pic_diag) + pic_particles to "
-                   f"pinned host", "seconds": sec}
+                   f"pinned host", "seconds": sec,
+            "phases_s": {"init_upload": round(ta - t0, 3), "steps": round(tb - ta - t_diag, 3),
+                         "diag": round(t_diag, 3), "readback_free": round(t1 - tb, 3)}}
 
 
 # ---------------------------------------------------------------- oracle arms

@@ -1408,26 +1408,65 @@ __global__ void k_global_to_flat(int ndim, Layout L, Tiles tg, PushConst C, cons
 }
 
 // charge density with linear weights (FP64 atomics) of every particle in the store
+// Charge density (FP64, linear weights) of every particle of tile t.  A thread
+// takes kRhoRun consecutive slots -- cell-sorted runs after the last sort --
+// and sums the weights of consecutive same-cell particles in registers before
+// its FP64 atomics, one set per cell change.
+constexpr int kRhoRun = 8;
+
+__device__ inline void rho_flush(const Layout& L, double* rho, int ndim, int i, int j, int k, const double (&w)[8]) {
+  for (int c3 = 0; c3 < (ndim == 3 ? 2 : 1); ++c3)
+    for (int c2 = 0; c2 < 2; ++c2)
+      for (int c1 = 0; c1 < 2; ++c1) atomicAdd(&rho[L.idx(i + c1, j + c2, k + c3)], w[c3 * 4 + c2 * 2 + c1]);
+}
+
 __global__ void k_tiled_rho(Layout L, PushConst C, Tiles tg, TileSide in, double* rho) {
   const int t = blockIdx.x;
   int n;
   tile_slot(tg, in, t, 0, n);
-  for (int k = threadIdx.x; k < n; k += blockDim.x) {
-    const long long s = tile_slot(tg, in, t, k, n);
-    const uint32_t c = in.p.cell[s];
-    if (c == kHoleCell) continue;
-    int o[3];
-    tile_origin(tg, dest_tile(tg, t, c), o);
-    const int i = o[0] + (int)(c & 255), j = o[1] + (int)((c >> 8) & 255), kk = o[2] + (int)((c >> 16) & 255);
-    const double e0 = in.p.o[0][s], e1 = in.p.o[1][s], e2 = tg.ndim == 3 ? (double)in.p.o[2][s] : 0.0;
-    const double qv = C.q / C.dvol;
-    for (int c3 = 0; c3 < (tg.ndim == 3 ? 2 : 1); ++c3)
-      for (int c2 = 0; c2 < 2; ++c2)
-        for (int c1 = 0; c1 < 2; ++c1) {
-          double w = (c1 ? e0 : 1.0 - e0) * (c2 ? e1 : 1.0 - e1);
-          if (tg.ndim == 3) w *= (c3 ? e2 : 1.0 - e2);
-          atomicAdd(&rho[L.idx(i + c1, j + c2, kk + c3)], qv * w);
-        }
+  const double qv = C.q / C.dvol;
+  int o[3];
+  tile_origin(tg, t, o);
+  for (int k0 = threadIdx.x * kRhoRun; k0 < n; k0 += blockDim.x * kRhoRun) {
+    double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    int cur = -1;
+    for (int m = 0; m < kRhoRun && k0 + m < n; ++m) {
+      const long long s = tile_slot(tg, in, t, k0 + m, n);
+      const uint32_t c = in.p.cell[s];
+      if (c == kHoleCell) continue;
+      // a stored cell is relative to this tile (direction code "stay"); any
+      // other code is deposited on its own at its tile's origin
+      const bool other = (int)(c >> 24) != DIR_STAY;
+      const int cell = other ? -2 : (int)(c & 0x00FFFFFFu);
+      if (cell != cur) {
+        if (cur >= 0)
+          rho_flush(L, rho, tg.ndim, o[0] + (cur & 255), o[1] + ((cur >> 8) & 255), o[2] + ((cur >> 16) & 255),
+                    acc);
+        cur = other ? -1 : cell;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) acc[q] = 0.0;
+      }
+      const double e0 = in.p.o[0][s], e1 = in.p.o[1][s], e2 = tg.ndim == 3 ? (double)in.p.o[2][s] : 0.0;
+#pragma unroll
+      for (int c3 = 0; c3 < 2; ++c3)
+#pragma unroll
+        for (int c2 = 0; c2 < 2; ++c2)
+#pragma unroll
+          for (int c1 = 0; c1 < 2; ++c1) {
+            double w = (c1 ? e0 : 1.0 - e0) * (c2 ? e1 : 1.0 - e1);
+            if (tg.ndim == 3) w *= (c3 ? e2 : 1.0 - e2);
+            acc[c3 * 4 + c2 * 2 + c1] += qv * w;
+          }
+      if (other) {
+        int od[3];
+        tile_origin(tg, dest_tile(tg, t, c), od);
+        rho_flush(L, rho, tg.ndim, od[0] + (int)(c & 255), od[1] + (int)((c >> 8) & 255),
+                  od[2] + (int)((c >> 16) & 255), acc);
+        cur = -1;
+      }
+    }
+    if (cur >= 0)
+      rho_flush(L, rho, tg.ndim, o[0] + (cur & 255), o[1] + ((cur >> 8) & 255), o[2] + ((cur >> 16) & 255), acc);
   }
 }
 

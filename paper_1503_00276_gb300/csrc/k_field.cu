@@ -296,6 +296,7 @@ __global__ void k_field_energy(Layout L, Ptr6<T> F, double* acc) {
 }
 
 template <typename T>
+// dx1..dx3: the reciprocal cell sizes
 __global__ void k_gauss(Layout L, Ptr3<T> E, const double* __restrict__ rho, double rho_bg, double dx1, double dx2,
                         double dx3, double* gmax, double* rmax, double* pmax) {
   __shared__ double red[32];
@@ -306,8 +307,10 @@ __global__ void k_gauss(Layout L, Ptr3<T> E, const double* __restrict__ rho, dou
   if (i < L.nx && j < L.ny) {
     const long long sx = 1, sy = L.NX, sz = (long long)L.NX * L.NY;
     long long c = L.idx(i, j, k);
-    double div = ((double)E.c[0][c] - (double)E.c[0][c - sx]) / dx1 + ((double)E.c[1][c] - (double)E.c[1][c - sy]) / dx2;
-    if (L.ndim == 3) div = div + ((double)E.c[2][c] - (double)E.c[2][c - sz]) / dx3;
+    // FP64 differences (exact for FP32 E) times 1/dx: the residual is itself
+    // ~1e-7 of rho, so the divergence stays in FP64
+    double div = ((double)E.c[0][c] - (double)E.c[0][c - sx]) * dx1 + ((double)E.c[1][c] - (double)E.c[1][c - sy]) * dx2;
+    if (L.ndim == 3) div = div + ((double)E.c[2][c] - (double)E.c[2][c - sz]) * dx3;
     double rt = rho[c] + rho_bg;
     g = fabs(div - rt);
     r = fabs(rt);
@@ -425,7 +428,8 @@ template <typename T>
 void gauss_residual(const Layout& L, T* const* e, const double* rho, double rho_bg, const double dx[3], Diag64* acc,
                     cudaStream_t s) {
   Ptr3<T> E{{e[0], e[1], e[2]}};
-  k_gauss<T><<<interior_grid(L), kBlock, 0, s>>>(L, E, rho, rho_bg, dx[0], dx[1], dx[2], &acc->gauss_max,
+  k_gauss<T><<<interior_grid(L), kBlock, 0, s>>>(L, E, rho, rho_bg, 1.0 / dx[0], 1.0 / dx[1], 1.0 / dx[2],
+                                                 &acc->gauss_max,
                                                  &acc->rho_max, &acc->rho_part_max);
 }
 

@@ -1408,16 +1408,20 @@ __global__ void k_global_to_flat(int ndim, Layout L, Tiles tg, PushConst C, cons
 }
 
 // charge density with linear weights (FP64 atomics) of every particle in the store
-// Charge density (FP64, linear weights) of every particle of tile t.  A thread
-// takes kRhoRun consecutive slots -- cell-sorted runs after the last sort --
-// and sums the weights of consecutive same-cell particles in registers before
-// its FP64 atomics, one set per cell change.
+// Charge density (linear weights, FP64 grid sums) of every particle of tile
+// t.  A thread takes kRhoRun consecutive slots -- cell-sorted runs after the
+// last sort -- and sums the weights of consecutive same-cell particles in
+// registers before its FP64 atomics, one set per cell change.  The weights of
+// FP32 offsets are formed in FP32 (GB300's FP64 pipe is the bottleneck
+// otherwise); every sum into the grid is FP64.
 constexpr int kRhoRun = 8;
 
-__device__ inline void rho_flush(const Layout& L, double* rho, int ndim, int i, int j, int k, const double (&w)[8]) {
+__device__ inline void rho_flush(const Layout& L, double* rho, int ndim, int i, int j, int k, const float (&w)[8],
+                                 double qv) {
   for (int c3 = 0; c3 < (ndim == 3 ? 2 : 1); ++c3)
     for (int c2 = 0; c2 < 2; ++c2)
-      for (int c1 = 0; c1 < 2; ++c1) atomicAdd(&rho[L.idx(i + c1, j + c2, k + c3)], w[c3 * 4 + c2 * 2 + c1]);
+      for (int c1 = 0; c1 < 2; ++c1)
+        atomicAdd(&rho[L.idx(i + c1, j + c2, k + c3)], qv * (double)w[c3 * 4 + c2 * 2 + c1]);
 }
 
 __global__ void k_tiled_rho(Layout L, PushConst C, Tiles tg, TileSide in, double* rho) {
@@ -1428,7 +1432,7 @@ __global__ void k_tiled_rho(Layout L, PushConst C, Tiles tg, TileSide in, double
   int o[3];
   tile_origin(tg, t, o);
   for (int k0 = threadIdx.x * kRhoRun; k0 < n; k0 += blockDim.x * kRhoRun) {
-    double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     int cur = -1;
     for (int m = 0; m < kRhoRun && k0 + m < n; ++m) {
       const long long s = tile_slot(tg, in, t, k0 + m, n);
@@ -1441,32 +1445,32 @@ __global__ void k_tiled_rho(Layout L, PushConst C, Tiles tg, TileSide in, double
       if (cell != cur) {
         if (cur >= 0)
           rho_flush(L, rho, tg.ndim, o[0] + (cur & 255), o[1] + ((cur >> 8) & 255), o[2] + ((cur >> 16) & 255),
-                    acc);
+                    acc, qv);
         cur = other ? -1 : cell;
 #pragma unroll
-        for (int q = 0; q < 8; ++q) acc[q] = 0.0;
+        for (int q = 0; q < 8; ++q) acc[q] = 0.f;
       }
-      const double e0 = in.p.o[0][s], e1 = in.p.o[1][s], e2 = tg.ndim == 3 ? (double)in.p.o[2][s] : 0.0;
+      const float e0 = in.p.o[0][s], e1 = in.p.o[1][s], e2 = tg.ndim == 3 ? in.p.o[2][s] : 0.f;
 #pragma unroll
       for (int c3 = 0; c3 < 2; ++c3)
 #pragma unroll
         for (int c2 = 0; c2 < 2; ++c2)
 #pragma unroll
           for (int c1 = 0; c1 < 2; ++c1) {
-            double w = (c1 ? e0 : 1.0 - e0) * (c2 ? e1 : 1.0 - e1);
-            if (tg.ndim == 3) w *= (c3 ? e2 : 1.0 - e2);
-            acc[c3 * 4 + c2 * 2 + c1] += qv * w;
+            float w = (c1 ? e0 : 1.f - e0) * (c2 ? e1 : 1.f - e1);
+            if (tg.ndim == 3) w *= (c3 ? e2 : 1.f - e2);
+            acc[c3 * 4 + c2 * 2 + c1] += w;
           }
       if (other) {
         int od[3];
         tile_origin(tg, dest_tile(tg, t, c), od);
         rho_flush(L, rho, tg.ndim, od[0] + (int)(c & 255), od[1] + (int)((c >> 8) & 255),
-                  od[2] + (int)((c >> 16) & 255), acc);
+                  od[2] + (int)((c >> 16) & 255), acc, qv);
         cur = -1;
       }
     }
     if (cur >= 0)
-      rho_flush(L, rho, tg.ndim, o[0] + (cur & 255), o[1] + ((cur >> 8) & 255), o[2] + ((cur >> 16) & 255), acc);
+      rho_flush(L, rho, tg.ndim, o[0] + (cur & 255), o[1] + ((cur >> 8) & 255), o[2] + ((cur >> 16) & 255), acc, qv);
   }
 }
 
@@ -1481,9 +1485,13 @@ __global__ void k_tiled_kinetic(PushConst C, Tiles tg, TileSide in, double* ke, 
     const long long s = tile_slot(tg, in, t, k, n);
     if (in.p.cell[s] == kHoleCell) continue;
     ++live;
-    const double a = in.p.u[0][s], b = in.p.u[1][s], c = in.p.u[2][s];
-    v += C.q * C.rqm * (sqrt(1.0 + a * a + b * b + c * c) - 1.0);
+    // gamma - 1 = u^2 / (1 + gamma) in FP32 from the FP32 momenta (no
+    // cancellation at small u), summed in FP64
+    const float a = in.p.u[0][s], b = in.p.u[1][s], c = in.p.u[2][s];
+    const float u2 = fmaf(a, a, fmaf(b, b, c * c));
+    v += (double)(u2 / (1.f + sqrtf(1.f + u2)));
   }
+  v *= C.q * C.rqm;
   for (int o = 16; o > 0; o >>= 1) live += __shfl_down_sync(0xffffffffu, live, o);
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
   __shared__ int cnt[32];

@@ -336,6 +336,32 @@ pic_status pic_batch_autotune(int nsims, const pic_grid* grids, const pic_specie
                               const pic_allocator* alloc, void* stream, int warmup, int steps, pic_tune_choice* best,
                               pic_tune_choice* tried, int max_tried, int* n_tried);
 
+
+/* ---- Checkpoint / restart ---------------------------------------------------
+ * The restart files of the thesis' code (its restart section: dump the full
+ * state every n steps, resume from it) for this library's state.
+ * pic_checkpoint_save writes one self-describing binary file: magic
+ * "PICGBCK1", version, sizeof(pic_grid), the effective grid (tile shape, sort
+ * period, blocks per SM and slack as in use), the step count, then per species
+ * its macro-charge, rqm, count and id flag followed by its particles in the
+ * stored precision (FP32 form: tile index, packed cell, 3 offsets, 3 momenta,
+ * ids; FP64 form: positions, momenta, ids), then the six E/B planes as stored
+ * (guard cells included).  The current and charge are not stored: the next
+ * step recomputes them.  It synchronises S's stream and streams through a
+ * 64 MiB host buffer.  Errors: PIC_EINVAL (bad arguments, file cannot be
+ * written), PIC_ENOMEM, PIC_ECUDA.
+ * pic_checkpoint_load creates a new simulation from such a file (on `stream`,
+ * memory from `alloc`): the restored particles, fields and step count are the
+ * saved ones bit for bit (the order of particles within a tile may differ).
+ * Errors: PIC_EINVAL for a missing, truncated or foreign file (nothing is
+ * allocated), plus those of pic_init. */
+pic_status pic_checkpoint_save(pic_sim* S, const char* path);
+pic_status pic_checkpoint_load(const char* path, const pic_allocator* alloc, void* cuda_stream, pic_sim** out);
+
+/* The effective grid of S (tile shape etc. as in use), its species count and
+ * step count; any output pointer may be NULL. */
+pic_status pic_info(const pic_sim* S, pic_grid* grid, int* nspecies, long long* step);
+
 #ifdef __cplusplus
 }
 #endif

@@ -147,6 +147,50 @@ class Simulation:
         check(code, "pic_init")
         self._h = h
 
+    # -- checkpoint / restart ---------------------------------------------------
+    def save(self, path: str):
+        """pic_checkpoint_save: the full state (particles, E/B, step) to a file."""
+        check(self._lib.pic_checkpoint_save(self._h, str(path).encode()), "pic_checkpoint_save")
+
+    @classmethod
+    def load(cls, path: str, stream=None, use_torch_allocator=True) -> "Simulation":
+        """pic_checkpoint_load: a new simulation from a checkpoint file."""
+        self = cls.__new__(cls)
+        self._lib = load()
+        torch = _torch()
+        self._torch = torch
+        self._alloc = None
+        stream_ptr = None
+        self.stream = None
+        if torch is not None and torch.cuda.is_available():
+            st = stream if stream is not None else torch.cuda.current_stream()
+            self.stream = st
+            stream_ptr = C.c_void_p(st.cuda_stream)
+            if use_torch_allocator:
+                self._alloc = _TorchAllocator(torch, torch.cuda.current_device(), st)
+        h = C.c_void_p()
+        check(self._lib.pic_checkpoint_load(str(path).encode(), C.byref(self._alloc.struct) if self._alloc else None,
+                                            stream_ptr, C.byref(h)), "pic_checkpoint_load")
+        self._h = h
+        g = _capi.PicGrid()
+        nsp = C.c_int()
+        check(self._lib.pic_info(h, C.byref(g), C.byref(nsp), None), "pic_info")
+        self._g = g
+        self.precision = int(g.precision)
+        self.ndim = int(g.ndim)
+        self.shape = (int(g.nx[2]) if g.ndim == 3 else 1, int(g.nx[1]), int(g.nx[0]))
+        self.nspecies = int(nsp.value)
+        self._keep = None
+        return self
+
+    def info(self) -> dict:
+        g = _capi.PicGrid()
+        nsp = C.c_int()
+        step = C.c_longlong()
+        check(self._lib.pic_info(self._h, C.byref(g), C.byref(nsp), C.byref(step)), "pic_info")
+        return {"tile": tuple(g.tile), "sort_period": int(g.sort_period), "ctas_per_sm": int(g.ctas_per_sm),
+                "nspecies": int(nsp.value), "step": int(step.value), "precision": int(g.precision)}
+
     # -- lifecycle ----------------------------------------------------------
     def close(self):
         if getattr(self, "_h", None):

@@ -77,6 +77,9 @@ PROTOTYPES = {
     "pic_batch_sim": (C.c_int, [_P, C.c_int, C.POINTER(_P)]),
     "pic_batch_info": (C.c_int, [_P, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong), C.POINTER(C.c_int)]),
     "pic_batch_destroy": (C.c_int, [_P]),
+    "pic_checkpoint_save": (C.c_int, [_P, C.c_char_p]),
+    "pic_checkpoint_load": (C.c_int, [C.c_char_p, C.POINTER(PicAllocator), _P, C.POINTER(_P)]),
+    "pic_info": (C.c_int, [_P, C.POINTER(PicGrid), C.POINTER(C.c_int), C.POINTER(C.c_longlong)]),
     "pic_autotune": (C.c_int, [C.POINTER(PicGrid), C.POINTER(PicSpecies), C.c_int, C.POINTER(PicAllocator), _P, C.c_int,
                                C.c_int, C.POINTER(PicTuneChoice), C.POINTER(PicTuneChoice), C.c_int,
                                C.POINTER(C.c_int)]),

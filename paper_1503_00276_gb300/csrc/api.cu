@@ -874,8 +874,12 @@ pic_status pic_destroy(pic_sim* S) {
 }
 
 namespace {
+// Loads species k of a simulation being set up from a checkpoint instead of
+// the pic_species description.
+using RestoreFn = std::function<pic_status(pic_sim*, int, SpeciesState&)>;
+
 pic_status init_sim(const pic_grid* grid, const pic_species* species, int nspecies, const pic_allocator* alloc,
-                    void* stream, bool no_small, pic_sim** out);
+                    void* stream, bool no_small, pic_sim** out, const RestoreFn* restore = nullptr);
 }
 
 pic_status pic_init(const pic_grid* grid, const pic_species* species, int nspecies, const pic_allocator* alloc,
@@ -885,7 +889,7 @@ pic_status pic_init(const pic_grid* grid, const pic_species* species, int nspeci
 
 namespace {
 pic_status init_sim(const pic_grid* grid, const pic_species* species, int nspecies, const pic_allocator* alloc,
-                    void* stream, bool no_small, pic_sim** out) {
+                    void* stream, bool no_small, pic_sim** out, const RestoreFn* restore) {
   if (!out) {
     set_error("out is NULL");
     return PIC_EINVAL;
@@ -893,7 +897,7 @@ pic_status init_sim(const pic_grid* grid, const pic_species* species, int nspeci
   *out = nullptr;
   pic_status st = validate_grid(grid);
   if (st != PIC_OK) return st;
-  if (nspecies < 0 || (nspecies > 0 && !species)) {
+  if (nspecies < 0 || (nspecies > 0 && !species && !restore)) {
     set_error("bad species list");
     return PIC_EINVAL;
   }
@@ -989,7 +993,11 @@ pic_status init_sim(const pic_grid* grid, const pic_species* species, int nspeci
     if (S->prec == PIC_FP32_CELLOFF) {
       if ((st = setup_tiles(S, S->sp[k])) != PIC_OK) return bail(st);
     }
-    if ((st = load_species(S, species[k], S->sp[k])) != PIC_OK) return bail(st);
+    if (restore)
+      st = (*restore)(S, k, S->sp[k]);
+    else
+      st = load_species(S, species[k], S->sp[k]);
+    if (st != PIC_OK) return bail(st);
     if (S->prec == PIC_FP32_CELLOFF) {
       if ((st = alloc_spill(S, S->sp[k])) != PIC_OK) return bail(st);
     }
@@ -1005,7 +1013,7 @@ pic_status init_sim(const pic_grid* grid, const pic_species* species, int nspeci
   if (S->prec == PIC_FP32_CELLOFF) {
     if ((st = make_maps(S)) != PIC_OK) return bail(st);
   }
-  if (grid->init_e_gauss_x1) {
+  if (grid->init_e_gauss_x1 && !restore) {
     compute_rho(S);
     if (S->prec == PIC_FP64_PLAIN)
       init_e_gauss_x1<double>(S->L, S->rho, grid->rho_bg, grid->dx[0], fld_ptr<double>(S, 0), S->s);
@@ -1807,6 +1815,223 @@ pic_status pic_batch_autotune(int nsims, const pic_grid* grids, const pic_specie
                               pic_tune_choice* tried, int max_tried, int* n_tried) {
   return tune_run(nsims, grids, species, nspecies, alloc, stream, warmup, steps, true, best, tried, max_tried,
                   n_tried);
+}
+
+
+// ------------------------------------------------------------- checkpoint
+
+namespace {
+
+const char kCkptMagic[8] = {'P', 'I', 'C', 'G', 'B', 'C', 'K', '1'};
+constexpr uint32_t kCkptVersion = 1;
+constexpr size_t kIoChunk = size_t(64) << 20;  // host staging per copy
+
+struct CkptSpecies {
+  double rqm, q;
+  long long n, np_max;
+  int ids, pad;
+};
+
+bool write_dev(FILE* f, const void* dev, size_t bytes, cudaStream_t s, std::vector<unsigned char>& buf) {
+  for (size_t o = 0; o < bytes; o += kIoChunk) {
+    const size_t m = std::min(kIoChunk, bytes - o);
+    if (cudaMemcpyAsync(buf.data(), static_cast<const char*>(dev) + o, m, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess || fwrite(buf.data(), 1, m, f) != m)
+      return false;
+  }
+  return true;
+}
+
+bool read_dev(FILE* f, void* dev, size_t bytes, cudaStream_t s, std::vector<unsigned char>& buf) {
+  for (size_t o = 0; o < bytes; o += kIoChunk) {
+    const size_t m = std::min(kIoChunk, bytes - o);
+    if (fread(buf.data(), 1, m, f) != m ||
+        cudaMemcpyAsync(static_cast<char*>(dev) + o, buf.data(), m, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+      return false;
+  }
+  return true;
+}
+
+pic_grid effective_grid(const pic_sim* S) {
+  pic_grid g = S->g;
+  for (int d = 0; d < 3; ++d) g.tile[d] = S->prec == PIC_FP32_CELLOFF ? S->T[d] : 0;
+  g.sort_period = S->sort_period;
+  g.ctas_per_sm = S->minb;
+  g.slack = S->slack;
+  g.init_e_gauss_x1 = 0;
+  return g;
+}
+
+// the arrays of one species' records, in file order
+std::vector<std::pair<void*, size_t>> species_arrays(const pic_sim* S, const SpeciesState& sp, const Flat32& fl,
+                                                     long long n) {
+  std::vector<std::pair<void*, size_t>> a;
+  const size_t m = (size_t)n;
+  if (S->prec == PIC_FP32_CELLOFF) {
+    a.push_back({fl.tile, 4 * m});
+    a.push_back({fl.cell, 4 * m});
+    for (int d = 0; d < 3; ++d) a.push_back({fl.o[d], 4 * m});
+    for (int d = 0; d < 3; ++d) a.push_back({fl.u[d], 4 * m});
+    if (sp.ids) a.push_back({fl.id, 4 * m});
+  } else {
+    for (int d = 0; d < S->ndim; ++d) a.push_back({sp.plain.x[d], 8 * m});
+    for (int d = 0; d < 3; ++d) a.push_back({sp.plain.u[d], 8 * m});
+    if (sp.ids) a.push_back({sp.plain.id, 4 * m});
+  }
+  return a;
+}
+
+}  // namespace
+
+pic_status pic_checkpoint_save(pic_sim* S, const char* path) {
+  if (!S || !path) {
+    set_error("pic_checkpoint_save: bad arguments");
+    return PIC_EINVAL;
+  }
+  if (cudaStreamSynchronize(S->s) != cudaSuccess) return cuda_check("pic_checkpoint_save");
+  FILE* f = fopen(path, "wb");
+  if (!f) {
+    set_error(std::string("pic_checkpoint_save: cannot open ") + path);
+    return PIC_EINVAL;
+  }
+  std::vector<unsigned char> buf(kIoChunk);
+  bool ok = true;
+  auto put = [&](const void* p, size_t n) { ok = ok && fwrite(p, 1, n, f) == n; };
+  const uint32_t hdr[4] = {kCkptVersion, (uint32_t)sizeof(pic_grid), (uint32_t)sizeof(CkptSpecies), 0};
+  put(kCkptMagic, 8);
+  put(hdr, sizeof(hdr));
+  const pic_grid g = effective_grid(S);
+  put(&g, sizeof(g));
+  const long long step = S->step;
+  const int nsp = (int)S->sp.size(), pad = 0;
+  put(&step, 8);
+  put(&nsp, 4);
+  put(&pad, 4);
+  pic_status st = PIC_OK;
+  for (auto& sp : S->sp) {
+    Flat32 fl{};
+    long long n = sp.n;
+    bool alloc = false;
+    if (S->prec == PIC_FP32_CELLOFF && (st = flatten(S, sp, fl, n, false, 0, alloc)) != PIC_OK) break;
+    const CkptSpecies h{sp.rqm, sp.q, n, sp.np_max, sp.ids ? 1 : 0, 0};
+    put(&h, sizeof(h));
+    for (auto& a : species_arrays(S, sp, fl, n)) ok = ok && write_dev(f, a.first, a.second, S->s, buf);
+    if (alloc) free_flat(S, fl);
+    if (!ok) break;
+  }
+  const size_t eb = elem_bytes(S);
+  for (int c = 0; c < 6 && ok && st == PIC_OK; ++c)
+    ok = write_dev(f, static_cast<char*>(S->fld) + (size_t)c * eb * (size_t)S->L.plane, eb * (size_t)S->L.plane,
+                   S->s, buf);
+  ok = (fclose(f) == 0) && ok;
+  if (st != PIC_OK) return st;
+  if (!ok) {
+    set_error(std::string("pic_checkpoint_save: write failed: ") + path);
+    return PIC_EINVAL;
+  }
+  return cuda_check("pic_checkpoint_save");
+}
+
+pic_status pic_checkpoint_load(const char* path, const pic_allocator* alloc, void* stream, pic_sim** out) {
+  if (!path || !out) {
+    set_error("pic_checkpoint_load: bad arguments");
+    return PIC_EINVAL;
+  }
+  *out = nullptr;
+  FILE* f = fopen(path, "rb");
+  if (!f) {
+    set_error(std::string("pic_checkpoint_load: cannot open ") + path);
+    return PIC_EINVAL;
+  }
+  struct Closer {
+    FILE* f;
+    ~Closer() { fclose(f); }
+  } closer{f};
+  char magic[8];
+  uint32_t hdr[4];
+  pic_grid g{};
+  long long step = 0;
+  int nsp = 0, pad = 0;
+  if (fread(magic, 1, 8, f) != 8 || memcmp(magic, kCkptMagic, 8) != 0 || fread(hdr, 1, sizeof(hdr), f) != sizeof(hdr) ||
+      hdr[0] != kCkptVersion || hdr[1] != sizeof(pic_grid) || hdr[2] != sizeof(CkptSpecies) ||
+      fread(&g, 1, sizeof(g), f) != sizeof(g) || fread(&step, 1, 8, f) != 8 || fread(&nsp, 1, 4, f) != 4 ||
+      fread(&pad, 1, 4, f) != 4 || nsp < 0 || nsp > 64) {
+    set_error(std::string("pic_checkpoint_load: not a checkpoint of this library version: ") + path);
+    return PIC_EINVAL;
+  }
+  std::vector<unsigned char> buf(kIoChunk);
+  RestoreFn restore = [&](pic_sim* S, int, SpeciesState& sp) -> pic_status {
+    CkptSpecies h{};
+    if (fread(&h, 1, sizeof(h), f) != sizeof(h) || h.n < 0) {
+      set_error("pic_checkpoint_load: truncated species record");
+      return PIC_EINVAL;
+    }
+    sp.rqm = h.rqm;
+    sp.q = h.q;
+    sp.n = h.n;
+    sp.np_max = h.np_max;
+    sp.ids = h.ids != 0;
+    const size_t m = (size_t)std::max<long long>(h.n, 1);
+    Flat32 fl{};
+    if (S->prec == PIC_FP32_CELLOFF) {
+      bool okf = true;
+      fl = alloc_flat(S, h.n, sp.ids, okf);
+      if (!okf) {
+        free_flat(S, fl);
+        set_error("out of device memory (checkpoint particles)");
+        return PIC_ENOMEM;
+      }
+    } else {
+      for (int d = 0; d < 3; ++d) {
+        sp.plain.x[d] = d < S->ndim ? (double*)S->al.get(8 * m) : nullptr;
+        sp.plain.u[d] = (double*)S->al.get(8 * m);
+        if ((d < S->ndim && !sp.plain.x[d]) || !sp.plain.u[d]) {
+          set_error("out of device memory (checkpoint particles)");
+          return PIC_ENOMEM;
+        }
+      }
+      sp.plain.id = sp.ids ? (int*)S->al.get(4 * m) : nullptr;
+      sp.plain.n = h.n;
+    }
+    for (auto& a : species_arrays(S, sp, fl, h.n))
+      if (!read_dev(f, a.first, a.second, S->s, buf)) {
+        if (S->prec == PIC_FP32_CELLOFF) free_flat(S, fl);
+        set_error("pic_checkpoint_load: truncated particle data");
+        return PIC_EINVAL;
+      }
+    if (S->prec == PIC_FP32_CELLOFF) {
+      const pic_status st = bin_flat(S, sp, fl, h.n);
+      free_flat(S, fl);
+      return st;
+    }
+    return PIC_OK;
+  };
+  pic_sim* S = nullptr;
+  pic_status st = init_sim(&g, nullptr, nsp, alloc, stream, false, &S, &restore);
+  if (st != PIC_OK) return st;
+  const size_t eb = elem_bytes(S);
+  for (int c = 0; c < 6; ++c)
+    if (!read_dev(f, static_cast<char*>(S->fld) + (size_t)c * eb * (size_t)S->L.plane, eb * (size_t)S->L.plane, S->s,
+                  buf)) {
+      pic_destroy(S);
+      set_error("pic_checkpoint_load: truncated field data");
+      return PIC_EINVAL;
+    }
+  S->step = step;
+  *out = S;
+  return cuda_check("pic_checkpoint_load");
+}
+
+pic_status pic_info(const pic_sim* S, pic_grid* grid, int* nspecies, long long* step) {
+  if (!S) {
+    set_error("pic_info: bad arguments");
+    return PIC_EINVAL;
+  }
+  if (grid) *grid = effective_grid(S);
+  if (nspecies) *nspecies = (int)S->sp.size();
+  if (step) *step = S->step;
+  return PIC_OK;
 }
 
 }  // extern "C"

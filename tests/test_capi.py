@@ -138,3 +138,18 @@ def test_autotune_arguments_are_checked_before_any_device_work(capi):
     assert lib.pic_autotune(C.byref(gs), C.byref(sp), 1, None, None, 1, 0, C.byref(best), None, 0, None) == -1
     g64 = _grid_struct(workload.Grid(ndim=2, nx=(64, 32, 1), dx=dx, dt=workload.courant_dt(dx, 2)), 0)
     assert lib.pic_autotune(C.byref(g64), C.byref(sp), 1, None, None, 1, 2, C.byref(best), None, 0, None) == -1
+
+
+def test_checkpoint_load_rejects_missing_and_foreign_files(capi, tmp_path):
+    lib = capi.load()
+    h = C.c_void_p()
+    assert lib.pic_checkpoint_load(str(tmp_path / "none.ckpt").encode(), None, None, C.byref(h)) == -1
+    bad = tmp_path / "bad.ckpt"
+    bad.write_bytes(b"NOTACKPT" + bytes(200))
+    assert lib.pic_checkpoint_load(str(bad).encode(), None, None, C.byref(h)) == -1
+    assert b"not a checkpoint" in lib.pic_last_error()
+    trunc = tmp_path / "trunc.ckpt"
+    trunc.write_bytes(b"PICGBCK1" + bytes(6))
+    assert lib.pic_checkpoint_load(str(trunc).encode(), None, None, C.byref(h)) == -1
+    assert not h.value
+    assert lib.pic_checkpoint_save(None, b"x") == -1

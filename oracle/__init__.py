@@ -15,6 +15,8 @@ the readings of garbled passages and the list of pins.
 from __future__ import annotations
 
 import ctypes as C
+import dataclasses
+import math
 import os
 import platform
 import subprocess
@@ -55,7 +57,7 @@ class OraGrid(C.Structure):
     _fields_ = [("ndim", C.c_int), ("nx", C.c_int * 3), ("dx", C.c_double * 3), ("xmin", C.c_double * 3),
                 ("dt", C.c_double), ("e0", C.c_double * 3), ("b0", C.c_double * 3),
                 ("smooth_level", C.c_int * 3), ("smooth_w", ((C.c_double * 3) * MAX_PASS) * 3),
-                ("rho_bg", C.c_double)]
+                ("rho_bg", C.c_double), ("open_x1", C.c_int)]
 
 
 class OraSpecies(C.Structure):
@@ -124,6 +126,7 @@ def make_grid(g) -> OraGrid:
                 og.smooth_w[d][p][m] = float(w[m])
     og.dt = float(g.dt)
     og.rho_bg = float(g.rho_bg)
+    og.open_x1 = int(bool(getattr(g, "move_window", False)))
     return og
 
 
@@ -132,7 +135,13 @@ class State:
 
     def __init__(self, grid, species_list, xs, us, charges, fields=None):
         self.grid = grid
+        self.species = list(species_list)
         self.og = make_grid(grid)
+        self.nstep = 0
+        self.shifts = 0
+        # particle ids (initial generator index; injected particles continue it)
+        self.ids = [np.arange(np.asarray(x).shape[0], dtype=np.int64) for x in xs]
+        self.created = [np.asarray(x).shape[0] for x in xs]
         shape = (int(grid.nx[2]), int(grid.nx[1]), int(grid.nx[0]))
         self.fld = [np.zeros(shape) if fields is None else np.ascontiguousarray(fields[c], dtype=np.float64).copy()
                     for c in range(6)]
@@ -160,9 +169,57 @@ class State:
         return len(self.x)
 
     def step(self, nsteps: int = 1):
+        if getattr(self.grid, "move_window", False):
+            for _ in range(int(nsteps)):
+                self.window_step()
+            return
         lib().ora_step(C.byref(self.og), self._fp, self._cp, self._sp, self.nsp, int(nsteps))
+        self.nstep += int(nsteps)
+
+    # -- moving window (thesis: dynamic simulation spaces) --------------------
+    def window_step(self):
+        """One step of a window moving at c in +x1.  The front boundary moves
+        outward and the back boundary inward at c; the window is shifted by one
+        cell when it lags c t by a cell (the step that reaches t = (n+1) dt):
+        then every field value moves one cell back, the back column of cells and
+        its plasma are discarded, and the new front column gets zero fields and
+        fresh plasma.  x1 is open (no wrap); particles outside the window after
+        the step are removed.  Order: particle phase, removal, smoothing and
+        field solve, then the shift of the fields and the injection."""
+        g = self.grid
+        dx1 = float(g.dx[0])
+        shift = int(math.floor(float(self.nstep + 1) * float(g.dt) / dx1)) > self.shifts
+        self.particle_phase()
+        lo = self.og.xmin[0] + (dx1 if shift else 0.0)
+        hi = lo + int(g.nx[0]) * dx1
+        for s in range(self.nsp):
+            keep = (self.x[s][:, 0] >= lo) & (self.x[s][:, 0] < hi)
+            if not keep.all():
+                self.x[s] = np.ascontiguousarray(self.x[s][keep])
+                self.u[s] = np.ascontiguousarray(self.u[s][keep])
+                self.ids[s] = self.ids[s][keep]
+        self._refresh()
+        self.smooth_current()
+        self.field_solve()
+        if shift:
+            for f in self.fld:
+                f[..., :-1] = f[..., 1:].copy()
+                f[..., -1] = 0.0
+            self.og.xmin[0] = lo
+            self.shifts += 1
+            import workload
+            for s in range(self.nsp):
+                gx = dataclasses.replace(g, xmin=(lo, g.xmin[1], g.xmin[2]))
+                xn, un = workload.inject_column(gx, self.species[s], lo, self.created[s])
+                self.x[s] = np.ascontiguousarray(np.concatenate([self.x[s], xn]))
+                self.u[s] = np.ascontiguousarray(np.concatenate([self.u[s], un]))
+                self.ids[s] = np.concatenate([self.ids[s], self.created[s] + np.arange(xn.shape[0])])
+                self.created[s] += xn.shape[0]
+            self._refresh()
+        self.nstep += 1
 
     def particle_phase(self):
+        self._refresh()
         lib().ora_particle_phase(C.byref(self.og), self._fp, self._cp, self._sp, self.nsp)
 
     def smooth_current(self):
@@ -284,3 +341,60 @@ def tile_bin(grid, tile, x):
     lib().ora_tile_bin(C.byref(og), t, n, _dp(xx), tid.ctypes.data_as(LLP), counts.ctypes.data_as(LLP),
                        order.ctypes.data_as(LLP))
     return tid, counts, order
+
+
+# --- laser pulse initialisation ----------------------------------------------
+
+def laser_envelope(xi, rise, length, fall):
+    """Longitudinal envelope behind the pulse front (xi >= 0 behind it): the
+    thesis calls rise and fall "approximately Gaussian" without a formula;
+    read as sin^2 over the rise, 1 over the length, cos^2 over the fall, 0
+    elsewhere (reading R21)."""
+    xi = np.asarray(xi, dtype=np.float64)
+    f = np.zeros_like(xi)
+    a = (xi >= 0) & (xi < rise)
+    f[a] = np.sin(0.5 * math.pi * xi[a] / rise) ** 2
+    b = (xi >= rise) & (xi < rise + length)
+    f[b] = 1.0
+    c = (xi >= rise + length) & (xi < rise + length + fall)
+    f[c] = np.cos(0.5 * math.pi * (xi[c] - rise - length) / fall) ** 2
+    return f
+
+
+def laser_fields(grid, laser, xmin1=None):
+    """E and B of a pulse moving in +x1 at t = 0, each component at its own
+    staggered positions (E2 at (i, j+1/2, k), E3 at (i, j, k+1/2), B2 at
+    (i+1/2, j, k+1/2), B3 at (i+1/2, j+1/2, k)): the vector potential
+    A = vosc f(xi) T(r) cos(k (x1 - x_front) + phase) along p = (0, cos pol,
+    sin pol), T(r) = exp(-r^2 / w0^2) about the box axis plus offset, gives in
+    the slowly varying envelope approximation E = -dA/dt = -vosc k f T
+    sin(k (x1 - x_front) + phase) p and B = x1-hat x E (B3 = E2, B2 = -E3).
+    Returns the six arrays [nz][ny][nx] (E1 = B1 = 0)."""
+    nx, ny = int(grid.nx[0]), int(grid.nx[1])
+    nz = int(grid.nx[2]) if grid.ndim == 3 else 1
+    dx = grid.dx
+    x0 = float(grid.xmin[0] if xmin1 is None else xmin1)
+    xfront = x0 + nx * dx[0] - laser.start
+    c2 = grid.xmin[1] + 0.5 * ny * dx[1] + laser.offset[0]
+    c3 = (grid.xmin[2] + 0.5 * nz * dx[2] + laser.offset[1]) if grid.ndim == 3 else 0.0
+    th = math.radians(laser.pol)
+    k_, j_, i_ = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+
+    def amp(s1, s2, s3):
+        x1 = x0 + (i_ + s1) * dx[0]
+        x2 = grid.xmin[1] + (j_ + s2) * dx[1]
+        r2 = (x2 - c2) ** 2
+        if grid.ndim == 3:
+            x3 = grid.xmin[2] + (k_ + s3) * dx[2]
+            r2 = r2 + (x3 - c3) ** 2
+        f = laser_envelope(xfront - x1, laser.rise, laser.length, laser.fall)
+        return -laser.vosc * laser.rkkp * f * np.exp(-r2 / laser.w0 ** 2) * \
+            np.sin(laser.rkkp * (x1 - xfront) + laser.phase)
+
+    zero = np.zeros((nz, ny, nx))
+    s3 = 0.5 if grid.ndim == 3 else 0.0
+    e2 = amp(0.0, 0.5, 0.0) * math.cos(th)
+    e3 = amp(0.0, 0.0, s3) * math.sin(th)
+    b2 = -amp(0.5, 0.0, s3) * math.sin(th)
+    b3 = amp(0.5, 0.5, 0.0) * math.cos(th)
+    return [zero, e2, e3, zero.copy(), b2, b3]

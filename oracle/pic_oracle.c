@@ -55,6 +55,20 @@ static long wrapi(long i, long n) {
   return r < 0 ? r + n : r;
 }
 
+/* open x1 (moving window): a grid value beyond x1 reads as 0 and a deposit
+   there is dropped; every other index wraps periodically */
+static int outside(const ora_grid* g, long i) { return g->open_x1 && (i < 0 || i >= g->nx[0]); }
+
+static long at(const ora_grid* g, long i, long j, long k);
+
+static double rd(const ora_grid* g, const double* F, long i, long j, long k) {
+  return outside(g, i) ? 0.0 : F[at(g, i, j, k)];
+}
+
+static void add_to(const ora_grid* g, double* F, long i, long j, long k, double v) {
+  if (!outside(g, i)) F[at(g, i, j, k)] += v;
+}
+
 static long at(const ora_grid* g, long i, long j, long k) {
   long nx = g->nx[0], ny = g->nx[1], nz = g->nx[2];
   return (wrapi(k, nz) * ny + wrapi(j, ny)) * nx + wrapi(i, nx);
@@ -89,8 +103,8 @@ static double interp_component(const ora_grid* g, const double* F, int comp, con
   }
   if (g->ndim == 2) {
     /* (1-e1)[(1-e2) F(i1,i2) + e2 F(i1,i2+1)] + e1[(1-e2) F(i1+1,i2) + e2 F(i1+1,i2+1)] */
-    double lo = (1.0 - eps[1]) * F[at(g, i[0], i[1], 0)] + eps[1] * F[at(g, i[0], i[1] + 1, 0)];
-    double hi = (1.0 - eps[1]) * F[at(g, i[0] + 1, i[1], 0)] + eps[1] * F[at(g, i[0] + 1, i[1] + 1, 0)];
+    double lo = (1.0 - eps[1]) * rd(g, F, i[0], i[1], 0) + eps[1] * rd(g, F, i[0], i[1] + 1, 0);
+    double hi = (1.0 - eps[1]) * rd(g, F, i[0] + 1, i[1], 0) + eps[1] * rd(g, F, i[0] + 1, i[1] + 1, 0);
     return (1.0 - eps[0]) * lo + eps[0] * hi;
   }
   double acc = 0.0;
@@ -98,7 +112,7 @@ static double interp_component(const ora_grid* g, const double* F, int comp, con
     for (int c2 = 0; c2 < 2; ++c2)
       for (int c1 = 0; c1 < 2; ++c1) {
         double w = (c1 ? eps[0] : 1.0 - eps[0]) * (c2 ? eps[1] : 1.0 - eps[1]) * (c3 ? eps[2] : 1.0 - eps[2]);
-        acc = acc + w * F[at(g, i[0] + c1, i[1] + c2, i[2] + c3)];
+        acc = acc + w * rd(g, F, i[0] + c1, i[1] + c2, i[2] + c3);
       }
   return acc;
 }
@@ -153,6 +167,7 @@ void ora_move(const ora_grid* g, double x[3], const double u[3]) {
 /* periodic boundary (node configuration "communicates with its own opposite boundary") */
 void ora_wrap(const ora_grid* g, double x[3]) {
   for (int d = 0; d < g->ndim; ++d) {
+    if (d == 0 && g->open_x1) continue; /* open x1: removed by the caller instead */
     double L = g->nx[d] * g->dx[d];
     double xmax = g->xmin[d] + L;
     while (x[d] >= xmax) x[d] = x[d] - L;
@@ -192,7 +207,7 @@ static void deposit_segment(const ora_grid* g, double* cur[3], const long cell[3
         for (int c2 = 0; c2 < 2; ++c2)
           for (int c1 = 0; c1 < 2; ++c1) {
             double w = (c1 ? p[0] : 1.0 - p[0]) * (c2 ? p[1] : 1.0 - p[1]);
-            cur[2][at(g, cell[0] + c1, cell[1] + c2, 0)] += amp * w;
+            add_to(g, cur[2], cell[0] + c1, cell[1] + c2, 0, amp * w);
           }
         continue;
       }
@@ -204,7 +219,7 @@ static void deposit_segment(const ora_grid* g, double* cur[3], const long cell[3
           double w = ct ? p[t] : 1.0 - p[t];
           long idx[3] = {cell[0], cell[1], 0};
           idx[t] += ct;
-          cur[d][at(g, idx[0], idx[1], 0)] += amp * w;
+          add_to(g, cur[d], idx[0], idx[1], 0, amp * w);
         }
       } else {
         int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
@@ -214,7 +229,7 @@ static void deposit_segment(const ora_grid* g, double* cur[3], const long cell[3
             long idx[3] = {cell[0], cell[1], cell[2]};
             idx[t1] += c1;
             idx[t2] += c2;
-            cur[d][at(g, idx[0], idx[1], idx[2])] += amp * w;
+            add_to(g, cur[d], idx[0], idx[1], idx[2], amp * w);
           }
       }
       p[d] = b[d];
@@ -304,7 +319,7 @@ void ora_deposit_rho(const ora_grid* g, double* rho, const double* x, long long 
         for (int c1 = 0; c1 < 2; ++c1) {
           double w = (c1 ? e[0] : 1.0 - e[0]) * (c2 ? e[1] : 1.0 - e[1]);
           if (g->ndim == 3) w = w * (c3 ? e[2] : 1.0 - e[2]);
-          rho[at(g, i[0] + c1, i[1] + c2, i[2] + c3)] += q * w / dvol;
+          add_to(g, rho, i[0] + c1, i[1] + c2, i[2] + c3, q * w / dvol);
         }
   }
 }
@@ -325,7 +340,7 @@ static void smooth_pass(const ora_grid* g, double* f, int d, const double w[3], 
         lo[d] -= 1;
         hi[d] += 1;
         tmp[at(g, s[0], s[1], s[2])] =
-            (w[0] * f[at(g, lo[0], lo[1], lo[2])] + w[1] * f[at(g, i, j, k)] + w[2] * f[at(g, hi[0], hi[1], hi[2])]) / ws;
+            (w[0] * rd(g, f, lo[0], lo[1], lo[2]) + w[1] * f[at(g, i, j, k)] + w[2] * rd(g, f, hi[0], hi[1], hi[2])) / ws;
       }
   memcpy(f, tmp, sizeof(double) * (size_t)(nx * ny * nz));
 }
@@ -354,8 +369,8 @@ static void advance_b_half(const ora_grid* g, double* const fld[6]) {
       for (long i = 0; i < nx; ++i) {
         long c = at(g, i, j, k);
         double dE3d2 = (E3[at(g, i, j + 1, k)] - E3[c]) / g->dx[1];
-        double dE3d1 = (E3[at(g, i + 1, j, k)] - E3[c]) / g->dx[0];
-        double dE2d1 = (E2[at(g, i + 1, j, k)] - E2[c]) / g->dx[0];
+        double dE3d1 = (rd(g, E3, i + 1, j, k) - E3[c]) / g->dx[0];
+        double dE2d1 = (rd(g, E2, i + 1, j, k) - E2[c]) / g->dx[0];
         double dE1d2 = (E1[at(g, i, j + 1, k)] - E1[c]) / g->dx[1];
         double dE2d3 = d3 ? (E2[at(g, i, j, k + 1)] - E2[c]) / g->dx[2] : 0.0;
         double dE1d3 = d3 ? (E1[at(g, i, j, k + 1)] - E1[c]) / g->dx[2] : 0.0;
@@ -376,8 +391,8 @@ static void advance_e(const ora_grid* g, double* const fld[6], double* const cur
       for (long i = 0; i < nx; ++i) {
         long c = at(g, i, j, k);
         double dB3d2 = (B3[c] - B3[at(g, i, j - 1, k)]) / g->dx[1];
-        double dB3d1 = (B3[c] - B3[at(g, i - 1, j, k)]) / g->dx[0];
-        double dB2d1 = (B2[c] - B2[at(g, i - 1, j, k)]) / g->dx[0];
+        double dB3d1 = (B3[c] - rd(g, B3, i - 1, j, k)) / g->dx[0];
+        double dB2d1 = (B2[c] - rd(g, B2, i - 1, j, k)) / g->dx[0];
         double dB1d2 = (B1[c] - B1[at(g, i, j - 1, k)]) / g->dx[1];
         double dB2d3 = d3 ? (B2[c] - B2[at(g, i, j, k - 1)]) / g->dx[2] : 0.0;
         double dB1d3 = d3 ? (B1[c] - B1[at(g, i, j, k - 1)]) / g->dx[2] : 0.0;
@@ -460,7 +475,7 @@ double ora_gauss_residual(const ora_grid* g, double* const fld[6], const double*
     for (long j = 0; j < ny; ++j)
       for (long i = 0; i < nx; ++i) {
         long c = at(g, i, j, k);
-        double div = (fld[0][c] - fld[0][at(g, i - 1, j, k)]) / g->dx[0] +
+        double div = (fld[0][c] - rd(g, fld[0], i - 1, j, k)) / g->dx[0] +
                      (fld[1][c] - fld[1][at(g, i, j - 1, k)]) / g->dx[1];
         if (d3) div = div + (fld[2][c] - fld[2][at(g, i, j, k - 1)]) / g->dx[2];
         double e = fabs(div - rho[c]);

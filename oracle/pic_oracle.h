@@ -19,6 +19,9 @@ typedef struct {
   int smooth_level[3];                   /* passes per direction */
   double smooth_w[3][ORA_MAX_PASS][3];   /* weights per direction and pass */
   double rho_bg;                         /* fixed background charge density */
+  int open_x1;                           /* 1: x1 is open (moving window): values beyond
+                                            x1 read as 0, deposits there are dropped,
+                                            particles are not wrapped in x1 */
 } ora_grid;
 
 typedef struct {

@@ -79,6 +79,7 @@ class Grid:
     smooth_w: tuple = ((1.0, 2.0, 1.0),) * 3
     rho_bg: float = 1.0            # fixed neutralising ion background density
     init_e_gauss_x1: bool = False  # initial E1 from the discrete Gauss law along x1
+    move_window: bool = False      # window moving at c in x1 (x1 open; periodic in x2, x3)
 
     @property
     def ncells(self) -> int:
@@ -106,6 +107,26 @@ class Species:
     @property
     def ppc_total(self) -> int:
         return int(self.ppc[0]) * int(self.ppc[1]) * int(self.ppc[2])
+
+
+@dataclass
+class Laser:
+    """A pulse propagating in +x1 (the thesis' pulse section, wavetype 1):
+    vosc = peak normalised vector potential a0, rkkp = wavenumber k (= omega0
+    / omega_p), w0 = spot size, rise / length / fall = envelope distances,
+    start = distance of the pulse front from the +x1 side of the box,
+    pol = polarisation angle in degrees from x2 towards x3, phase, offset =
+    transverse offset of the axis from the box centre."""
+    vosc: float = 1.0
+    rkkp: float = 10.0
+    w0: float = 4.0
+    rise: float = 1.0
+    fall: float = 1.0
+    length: float = 0.0
+    start: float = 1.0
+    pol: float = 0.0
+    phase: float = 0.0
+    offset: tuple = (0.0, 0.0)
 
 
 def courant_dt(dx, ndim: int, frac: float = 0.99) -> float:
@@ -229,3 +250,31 @@ def config4(seed: int = 20005, nsims: int = 64):
                     seed=seed + 1000 * (i + 1))
         out.append((g, [s]))
     return out, 500
+
+
+def inject_column(grid: Grid, sp: Species, xmin1: float, first_index: int):
+    """Fresh plasma for the front column (cell index nx1 - 1) of a window whose
+    x1 edge is now ``xmin1``: the particles of the column's cells in cell order
+    (x3 slowest), each cell's sub-lattice as the loader's, momenta from draws
+    of global particle indices first_index, first_index + 1, ... (the loader's
+    stream continued).  Returns (x[n,3], u[n,3])."""
+    nx, ny = int(grid.nx[0]), int(grid.nx[1])
+    nz = int(grid.nx[2]) if grid.ndim == 3 else 1
+    ppc = sp.ppc_total
+    k = np.arange(ny * nz * ppc, dtype=np.int64)
+    col = k // ppc
+    sub = k % ppc
+    cj, ck = col % ny, col // ny
+    npx, npy = int(sp.ppc[0]), int(sp.ppc[1])
+    si, sj, sk = sub % npx, (sub // npx) % npy, sub // (npx * npy)
+    x = np.zeros((k.size, 3))
+    x[:, 0] = xmin1 + ((nx - 1) + (si + 0.5) / float(sp.ppc[0])) * grid.dx[0]
+    x[:, 1] = grid.xmin[1] + (cj + (sj + 0.5) / float(sp.ppc[1])) * grid.dx[1]
+    if grid.ndim == 3:
+        x[:, 2] = grid.xmin[2] + (ck + (sk + 0.5) / float(sp.ppc[2])) * grid.dx[2]
+    gidx = np.uint64(first_index) + k.astype(np.uint64)
+    u = np.zeros((k.size, 3))
+    for d in range(3):
+        u[:, d] = sp.ufl[d] + sp.uth[d] * normal(sp.seed, np.uint64(3) * gidx + np.uint64(d)) if sp.uth[d] != 0.0 \
+            else np.full(k.size, float(sp.ufl[d]))
+    return x, u

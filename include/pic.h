@@ -117,6 +117,14 @@ typedef struct {
   int ctas_per_sm;          /* PIC_FP32_CELLOFF: thread blocks per SM the general tile
                                kernel is built for: 3 (80 registers per thread) or 2
                                (128); 0 = default 3 */
+  int move_window;          /* 1: the window moves at c in +x1 (thesis: dynamic simulation
+                               space, if_move): x1 is open -- fields beyond it are 0, particles
+                               leaving through it are dropped -- and whenever c t runs a full
+                               cell ahead of the window, every field value and particle moves
+                               one cell back, the back column is discarded and the front column
+                               gets zero fields and fresh plasma of every species (its lattice,
+                               u_th, u_fl and draw stream continued; explicit species need
+                               ppc set).  PIC_FP32_CELLOFF only (else PIC_EUNSUPPORTED). */
 } pic_grid;
 
 /* One particle species (appendix nl_species / nl_profile).  Either loaded on the
@@ -361,6 +369,27 @@ pic_status pic_checkpoint_load(const char* path, const pic_allocator* alloc, voi
 /* The effective grid of S (tile shape etc. as in use), its species count and
  * step count; any output pointer may be NULL. */
 pic_status pic_info(const pic_sim* S, pic_grid* grid, int* nspecies, long long* step);
+
+
+/* ---- Laser pulses ------------------------------------------------------------
+ * A pulse moving in +x1 (the thesis' pulse input, wavetype 1), added to the
+ * current fields: vosc = peak normalised vector potential a0; rkkp = its
+ * wavenumber k (= omega0 / omega_p); w0 = spot size (field 1/e radius of the
+ * Gaussian transverse profile); rise / length / fall = envelope distances
+ * behind the front (sin^2 rise, flat, cos^2 fall -- the thesis says
+ * "approximately Gaussian"); start = distance of the front from the +x1 side
+ * of the box; pol = polarisation angle from x2 towards x3 in degrees; phase;
+ * offset = transverse offset of the axis from the box centre (x2, x3).  With
+ * A = vosc f(xi) T(r) cos(k (x1 - x_front) + phase) along the polarisation,
+ * E = -dA/dt and B = x1-hat x E in the slowly varying envelope form, each
+ * component at its own staggered position.  The thesis' focus is not modelled
+ * (the pulse is set up with its waist profile).  Synchronises S's stream. */
+typedef struct {
+  double vosc, rkkp, w0, rise, fall, length, start, pol, phase;
+  double offset[2];
+} pic_laser;
+
+pic_status pic_laser_add(pic_sim* S, const pic_laser* laser);
 
 #ifdef __cplusplus
 }

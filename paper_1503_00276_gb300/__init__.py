@@ -74,6 +74,7 @@ def _grid_struct(grid, precision, tile=None, slack=0.0, sort_period=0, ctas_per_
     g.slack = float(slack)
     g.sort_period = int(sort_period)
     g.ctas_per_sm = int(ctas_per_sm)
+    g.move_window = int(bool(getattr(grid, "move_window", False)))
     return g
 
 
@@ -146,6 +147,16 @@ class Simulation:
         self._keep = None
         check(code, "pic_init")
         self._h = h
+
+    # -- laser ----------------------------------------------------------------
+    def add_laser(self, laser):
+        """pic_laser_add: a pulse moving in +x1 (attributes of workload.Laser)."""
+        L = _capi.PicLaser()
+        for f in ("vosc", "rkkp", "w0", "rise", "fall", "length", "start", "pol", "phase"):
+            setattr(L, f, float(getattr(laser, f)))
+        off = tuple(getattr(laser, "offset", (0.0, 0.0)))
+        L.offset[0], L.offset[1] = float(off[0]), float(off[1] if len(off) > 1 else 0.0)
+        check(self._lib.pic_laser_add(self._h, C.byref(L)), "pic_laser_add")
 
     # -- checkpoint / restart ---------------------------------------------------
     def save(self, path: str):

@@ -30,7 +30,7 @@ class PicGrid(C.Structure):
                 ("smooth_level", C.c_int * 3), ("smooth_w", ((C.c_double * 3) * MAX_SMOOTH) * 3),
                 ("rho_bg", C.c_double), ("init_e_gauss_x1", C.c_int), ("precision", C.c_int),
                 ("tile", C.c_int * 3), ("slack", C.c_double), ("sort_period", C.c_int),
-                ("ctas_per_sm", C.c_int)]
+                ("ctas_per_sm", C.c_int), ("move_window", C.c_int)]
 
 
 class PicSpecies(C.Structure):
@@ -38,6 +38,12 @@ class PicSpecies(C.Structure):
                 ("density", C.c_double), ("seed", C.c_ulonglong), ("n_explicit", C.c_longlong),
                 ("x0", C.POINTER(C.c_double)), ("u0", C.POINTER(C.c_double)), ("q_explicit", C.c_double),
                 ("np_max", C.c_longlong), ("track_ids", C.c_int)]
+
+
+class PicLaser(C.Structure):
+    _fields_ = [("vosc", C.c_double), ("rkkp", C.c_double), ("w0", C.c_double), ("rise", C.c_double),
+                ("fall", C.c_double), ("length", C.c_double), ("start", C.c_double), ("pol", C.c_double),
+                ("phase", C.c_double), ("offset", C.c_double * 2)]
 
 
 class PicTuneChoice(C.Structure):
@@ -79,6 +85,7 @@ PROTOTYPES = {
     "pic_batch_destroy": (C.c_int, [_P]),
     "pic_checkpoint_save": (C.c_int, [_P, C.c_char_p]),
     "pic_checkpoint_load": (C.c_int, [C.c_char_p, C.POINTER(PicAllocator), _P, C.POINTER(_P)]),
+    "pic_laser_add": (C.c_int, [_P, C.POINTER(PicLaser)]),
     "pic_info": (C.c_int, [_P, C.POINTER(PicGrid), C.POINTER(C.c_int), C.POINTER(C.c_longlong)]),
     "pic_autotune": (C.c_int, [C.POINTER(PicGrid), C.POINTER(PicSpecies), C.c_int, C.POINTER(PicAllocator), _P, C.c_int,
                                C.c_int, C.POINTER(PicTuneChoice), C.POINTER(PicTuneChoice), C.c_int,

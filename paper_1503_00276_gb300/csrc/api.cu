@@ -115,6 +115,12 @@ struct SpeciesState {
   long long spill_cap = 0;
   int grid = 0;             // persistent CTAs of the tile kernel
   int* work = nullptr;      // its dynamic tile counter
+  // lattice description (moving-window injection continues the loader)
+  int ppc[3] = {0, 0, 0};
+  double uth[3] = {0, 0, 0}, ufl[3] = {0, 0, 0};
+  unsigned long long seed = 0;
+  long long created = 0;    // particles ever created (ids and draw indices continue from here)
+  int* d_lost = nullptr;    // particles dropped through an open x1 boundary in the last step
 };
 
 constexpr int kTimingSlots = 5;
@@ -154,7 +160,9 @@ struct pic_sim {
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_pending;
   int sticky_flags = 0;
   long long nlaunch = 0;  // kernels launched by pic_step since the last reset
-  bool no_small = false;  // member of a batch: the general tile kernel only
+  bool no_small = false;  // member of a batch or moving window: the general tile kernel only
+  bool moving = false;    // window moving at c in +x1
+  long long shifts = 0;   // one-cell shifts of the window so far
   bool in_batch = false;  // stepped by its batch; pic_step refuses it
 };
 
@@ -513,6 +521,12 @@ pic_status load_species(pic_sim* S, const pic_species& in, SpeciesState& sp) {
   sp.rqm = in.rqm;
   sp.ids = in.track_ids != 0;
   sp.np_max = in.np_max;
+  for (int d = 0; d < 3; ++d) {
+    sp.ppc[d] = d < S->ndim ? in.ppc[d] : 1;
+    sp.uth[d] = in.uth[d];
+    sp.ufl[d] = in.ufl[d];
+  }
+  sp.seed = in.seed;
   if (in.rqm == 0.0 || !std::isfinite(in.rqm)) {
     set_error("species rqm must be finite and non-zero");
     return PIC_EINVAL;
@@ -700,10 +714,13 @@ pic_status alloc_spill(pic_sim* S, SpeciesState& sp) {
   sp.spill_cap = std::max<long long>(1 << 16, sp.n / 64);
   bool ok = true;
   sp.spill = alloc_flat(S, sp.spill_cap, sp.ids, ok);
-  if (!ok) {
+  sp.d_lost = (int*)S->al.get(sizeof(int));
+  if (!ok || !sp.d_lost) {
     set_error("out of device memory (spill list)");
     return PIC_ENOMEM;
   }
+  cudaMemsetAsync(sp.d_lost, 0, sizeof(int), S->s);
+  if (sp.created < sp.n) sp.created = sp.n;
   return PIC_OK;
 }
 
@@ -754,6 +771,9 @@ void field_step(pic_sim* S) {
 
 pic_status one_step(pic_sim* S, bool check_now) {
   Span whole(S, 4);
+  // moving window: shift by one cell at the end of the step that brings c t a
+  // full cell past the last shift
+  const bool shift = S->moving && (long long)std::floor((double)(S->step + 1) * S->g.dt / S->g.dx[0]) > S->shifts;
   cudaMemsetAsync(S->cur, 0, 3 * elem_bytes(S) * (size_t)S->L.plane, S->s);
   {
     Span sp(S, 0);
@@ -771,9 +791,18 @@ pic_status one_step(pic_sim* S, bool check_now) {
         // the steps before it keep the order they find (blocks compacted)
         const bool stream = S->sort_period > 1 && !s.tg.small && (S->step + 1) % S->sort_period != 0;
         tiled_push(S->L, C, s.tg, s.side[in], s.side[out], s.spill, &S->dstat->spill_count, s.spill_cap,
-                   s.grid, s.work, &S->fmap, &S->jmap, &S->dstat->status, stream, S->minb,
+                   s.grid, s.work, &S->fmap, &S->jmap, &S->dstat->status, stream, S->minb, shift ? 1 : 0, s.d_lost,
                    S->s);
         s.cur = out;
+        if (shift) {  // fresh plasma for the new front column
+          const long long cnt = (long long)S->L.ny * S->L.nz * s.ppc[0] * s.ppc[1] * s.ppc[2];
+          const int nxs[3] = {S->L.nx, S->L.ny, S->L.nz};
+          tiled_inject(C, s.tg, s.side[out], s.spill, &S->dstat->spill_count, s.spill_cap, &S->dstat->status, nxs,
+                       s.ppc, s.uth, s.ufl, s.seed, s.created, cnt, S->s);
+          s.created += cnt;
+          s.n += cnt;
+          S->nlaunch += cnt > 0 ? 1 : 0;
+        }
       }
       S->nlaunch += s.n > 0 || S->prec == PIC_FP32_CELLOFF ? 1 : 0;
     }
@@ -782,6 +811,15 @@ pic_status one_step(pic_sim* S, bool check_now) {
     field_step<double>(S);
   else
     field_step<float>(S);
+  if (shift) {  // every field value one cell back; zero front column
+    float* eb[6];
+    for (int c = 0; c < 6; ++c) eb[c] = fld_ptr<float>(S, c);
+    shift_x<float>(S->L, eb, 6, S->s);
+    fill_guards<float>(S->L, eb, 6, S->s);
+    S->g.xmin[0] += S->g.dx[0];
+    ++S->shifts;
+    S->nlaunch += 2;
+  }
   ++S->step;
   pic_status st = cuda_check("step launch");
   if (st != PIC_OK) return st;
@@ -790,6 +828,13 @@ pic_status one_step(pic_sim* S, bool check_now) {
   if (cudaStreamSynchronize(S->s) != cudaSuccess) return cuda_check("step");
   const int flags = S->hstat->status;
   S->sticky_flags |= flags;
+  if (S->moving)
+    for (auto& s : S->sp) {
+      int lost = 0;
+      cudaMemcpy(&lost, s.d_lost, sizeof(int), cudaMemcpyDeviceToHost);
+      cudaMemsetAsync(s.d_lost, 0, sizeof(int), S->s);
+      s.n -= lost;
+    }
   if (flags & ST_SPILL) {
     if (flags & ST_SPILL_LOST) {
       set_error("particle spill list overflowed: particles were lost");
@@ -907,8 +952,13 @@ pic_status init_sim(const pic_grid* grid, const pic_species* species, int nspeci
     set_error("no CUDA device");
     return PIC_ECUDA;
   }
+  if (grid->move_window && grid->precision != PIC_FP32_CELLOFF) {
+    set_error("move_window needs the FP32 cell-offset form");
+    return PIC_EUNSUPPORTED;
+  }
   pic_sim* S = new pic_sim();
-  S->no_small = no_small;
+  S->moving = grid->move_window != 0;
+  S->no_small = no_small || S->moving;
   S->g = *grid;
   S->ndim = grid->ndim;
   S->prec = grid->precision;
@@ -921,6 +971,7 @@ pic_status init_sim(const pic_grid* grid, const pic_species* species, int nspeci
   S->sort_period = grid->sort_period > 0 ? grid->sort_period : 1;
   int nxv[3] = {grid->nx[0], grid->nx[1], grid->ndim == 3 ? grid->nx[2] : 1};
   S->L = make_layout(S->ndim, nxv);
+  S->L.open_x = S->moving ? 1 : 0;
   if (S->prec == PIC_FP32_CELLOFF) {
     for (int d = 0; d < 3; ++d) S->T[d] = d < S->ndim ? grid->tile[d] : 1;
     if (S->T[0] <= 0 || S->T[1] <= 0 || (S->ndim == 3 && S->T[2] <= 0)) {
@@ -1829,7 +1880,10 @@ constexpr size_t kIoChunk = size_t(64) << 20;  // host staging per copy
 struct CkptSpecies {
   double rqm, q;
   long long n, np_max;
-  int ids, pad;
+  int ids, ppc[3];
+  double uth[3], ufl[3];
+  unsigned long long seed;
+  long long created;
 };
 
 bool write_dev(FILE* f, const void* dev, size_t bytes, cudaStream_t s, std::vector<unsigned char>& buf) {
@@ -1903,9 +1957,10 @@ pic_status pic_checkpoint_save(pic_sim* S, const char* path) {
   put(hdr, sizeof(hdr));
   const pic_grid g = effective_grid(S);
   put(&g, sizeof(g));
-  const long long step = S->step;
+  const long long step = S->step, shifts = S->shifts;
   const int nsp = (int)S->sp.size(), pad = 0;
   put(&step, 8);
+  put(&shifts, 8);
   put(&nsp, 4);
   put(&pad, 4);
   pic_status st = PIC_OK;
@@ -1914,7 +1969,19 @@ pic_status pic_checkpoint_save(pic_sim* S, const char* path) {
     long long n = sp.n;
     bool alloc = false;
     if (S->prec == PIC_FP32_CELLOFF && (st = flatten(S, sp, fl, n, false, 0, alloc)) != PIC_OK) break;
-    const CkptSpecies h{sp.rqm, sp.q, n, sp.np_max, sp.ids ? 1 : 0, 0};
+    CkptSpecies h{};
+    h.rqm = sp.rqm;
+    h.q = sp.q;
+    h.n = n;
+    h.np_max = sp.np_max;
+    h.ids = sp.ids ? 1 : 0;
+    for (int d = 0; d < 3; ++d) {
+      h.ppc[d] = sp.ppc[d];
+      h.uth[d] = sp.uth[d];
+      h.ufl[d] = sp.ufl[d];
+    }
+    h.seed = sp.seed;
+    h.created = sp.created;
     put(&h, sizeof(h));
     for (auto& a : species_arrays(S, sp, fl, n)) ok = ok && write_dev(f, a.first, a.second, S->s, buf);
     if (alloc) free_flat(S, fl);
@@ -1951,11 +2018,12 @@ pic_status pic_checkpoint_load(const char* path, const pic_allocator* alloc, voi
   char magic[8];
   uint32_t hdr[4];
   pic_grid g{};
-  long long step = 0;
+  long long step = 0, shifts = 0;
   int nsp = 0, pad = 0;
   if (fread(magic, 1, 8, f) != 8 || memcmp(magic, kCkptMagic, 8) != 0 || fread(hdr, 1, sizeof(hdr), f) != sizeof(hdr) ||
       hdr[0] != kCkptVersion || hdr[1] != sizeof(pic_grid) || hdr[2] != sizeof(CkptSpecies) ||
-      fread(&g, 1, sizeof(g), f) != sizeof(g) || fread(&step, 1, 8, f) != 8 || fread(&nsp, 1, 4, f) != 4 ||
+      fread(&g, 1, sizeof(g), f) != sizeof(g) || fread(&step, 1, 8, f) != 8 || fread(&shifts, 1, 8, f) != 8 ||
+      fread(&nsp, 1, 4, f) != 4 ||
       fread(&pad, 1, 4, f) != 4 || nsp < 0 || nsp > 64) {
     set_error(std::string("pic_checkpoint_load: not a checkpoint of this library version: ") + path);
     return PIC_EINVAL;
@@ -1972,6 +2040,13 @@ pic_status pic_checkpoint_load(const char* path, const pic_allocator* alloc, voi
     sp.n = h.n;
     sp.np_max = h.np_max;
     sp.ids = h.ids != 0;
+    for (int d = 0; d < 3; ++d) {
+      sp.ppc[d] = h.ppc[d];
+      sp.uth[d] = h.uth[d];
+      sp.ufl[d] = h.ufl[d];
+    }
+    sp.seed = h.seed;
+    sp.created = h.created;
     const size_t m = (size_t)std::max<long long>(h.n, 1);
     Flat32 fl{};
     if (S->prec == PIC_FP32_CELLOFF) {
@@ -2019,8 +2094,49 @@ pic_status pic_checkpoint_load(const char* path, const pic_allocator* alloc, voi
       return PIC_EINVAL;
     }
   S->step = step;
+  S->shifts = shifts;
   *out = S;
   return cuda_check("pic_checkpoint_load");
+}
+
+pic_status pic_laser_add(pic_sim* S, const pic_laser* L) {
+  if (!S || !L || !(L->rkkp > 0.0) || !(L->w0 > 0.0) || L->rise < 0.0 || L->fall < 0.0 || L->length < 0.0) {
+    set_error("pic_laser_add: bad arguments");
+    return PIC_EINVAL;
+  }
+  const pic_grid& g = S->g;
+  const double nxr[3] = {(double)S->L.nx, (double)S->L.ny, (double)S->L.nz};
+  const double pol = L->pol * 3.141592653589793 / 180.0;
+  double p[18];
+  p[0] = L->vosc;
+  p[1] = L->rkkp;
+  p[2] = L->w0;
+  p[3] = L->rise;
+  p[4] = L->length;
+  p[5] = L->fall;
+  p[6] = g.xmin[0] + nxr[0] * g.dx[0] - L->start;  // pulse front
+  p[7] = g.xmin[1] + 0.5 * nxr[1] * g.dx[1] + L->offset[0];
+  p[8] = S->ndim == 3 ? g.xmin[2] + 0.5 * nxr[2] * g.dx[2] + L->offset[1] : 0.0;
+  p[9] = cos(pol);
+  p[10] = sin(pol);
+  p[11] = L->phase;
+  for (int d = 0; d < 3; ++d) {
+    p[12 + d] = g.xmin[d];
+    p[15 + d] = d < S->ndim ? g.dx[d] : 1.0;
+  }
+  if (S->prec == PIC_FP64_PLAIN) {
+    double* f[6];
+    for (int c = 0; c < 6; ++c) f[c] = fld_ptr<double>(S, c);
+    laser_add<double>(S->L, f, p, S->s);
+    fill_guards<double>(S->L, f, 6, S->s);
+  } else {
+    float* f[6];
+    for (int c = 0; c < 6; ++c) f[c] = fld_ptr<float>(S, c);
+    laser_add<float>(S->L, f, p, S->s);
+    fill_guards<float>(S->L, f, 6, S->s);
+  }
+  if (cudaStreamSynchronize(S->s) != cudaSuccess) return cuda_check("pic_laser_add");
+  return cuda_check("pic_laser_add");
 }
 
 pic_status pic_info(const pic_sim* S, pic_grid* grid, int* nspecies, long long* step) {

@@ -26,6 +26,7 @@ struct Layout {
   int gx, gy, gz;         // guard widths below
   int NX, NY, NZ;         // padded extents
   long long plane;        // elements per component
+  int open_x;             // 1: x1 is open (moving window): guards beyond x1 hold 0, no wrap
 
   __host__ __device__ inline long long idx(int i, int j, int k) const {
     return ((long long)(k + gz) * NY + (j + gy)) * NX + (i + gx);
@@ -45,6 +46,7 @@ inline Layout make_layout(int ndim, const int nx[3]) {
   L.NY = L.ny + GY_LO + GY_HI;
   L.NZ = ndim == 3 ? L.nz + GY_LO + GY_HI : 1;
   L.plane = (long long)L.NX * L.NY * L.NZ;
+  L.open_x = 0;
   return L;
 }
 

@@ -86,6 +86,10 @@ __global__ void k_fill_guards(Layout L, PtrN<T, 6> P, int ncomp) {
   if (!guard_xyz(L, g, X, Y, Z)) return;
   const int i = X - L.gx, j = Y - L.gy, k = Z - L.gz;
   const long long dst = ((long long)Z * L.NY + Y) * L.NX + X;
+  if (L.open_x && (i < 0 || i >= L.nx)) {  // beyond an open x1 boundary: no field
+    for (int c = 0; c < ncomp; ++c) P.c[c][dst] = T(0);
+    return;
+  }
   const long long src = L.idx(wrapi(i, L.nx), wrapi(j, L.ny), wrapi(k, L.nz));
   for (int c = 0; c < ncomp; ++c) P.c[c][dst] = P.c[c][src];
 }
@@ -101,10 +105,11 @@ __global__ void k_fold_guards(Layout L, PtrN<T, 6> P, int ncomp) {
   if (!guard_xyz(L, g, X, Y, Z)) return;
   const int i = X - L.gx, j = Y - L.gy, k = Z - L.gz;
   const long long src = ((long long)Z * L.NY + Y) * L.NX + X;
+  const bool drop = L.open_x && (i < 0 || i >= L.nx);  // deposited beyond an open x1 boundary
   const long long dst = L.idx(wrapi(i, L.nx), wrapi(j, L.ny), wrapi(k, L.nz));
   for (int c = 0; c < ncomp; ++c) {
     const T v = P.c[c][src];
-    if (v != T(0)) atomicAdd(&P.c[c][dst], v);
+    if (v != T(0) && !drop) atomicAdd(&P.c[c][dst], v);
     P.c[c][src] = T(0);
   }
 }
@@ -119,10 +124,13 @@ __global__ void k_smooth(Layout L, const T* __restrict__ f, T* __restrict__ out,
   if (i >= L.nx || j >= L.ny) return;
   int lo[3] = {i, j, k}, hi[3] = {i, j, k};
   int n[3] = {L.nx, L.ny, L.nz};
+  const bool lo_out = L.open_x && dim == 0 && lo[0] == 0, hi_out = L.open_x && dim == 0 && hi[0] == n[0] - 1;
   lo[dim] = lo[dim] == 0 ? n[dim] - 1 : lo[dim] - 1;
   hi[dim] = hi[dim] == n[dim] - 1 ? 0 : hi[dim] + 1;
   long long c = L.idx(i, j, k);
-  out[c] = (w0 * f[L.idx(lo[0], lo[1], lo[2])] + w1 * f[c] + w2 * f[L.idx(hi[0], hi[1], hi[2])]) / ws;
+  const T fl = lo_out ? T(0) : f[L.idx(lo[0], lo[1], lo[2])];  // beyond an open x1 boundary: 0
+  const T fh = hi_out ? T(0) : f[L.idx(hi[0], hi[1], hi[2])];
+  out[c] = (w0 * fl + w1 * f[c] + w2 * fh) / ws;
 }
 
 // ---------------------------------------------------------------- Yee solve
@@ -201,9 +209,10 @@ __global__ void k_yee_b_half_f32(Layout L, Ptr3<float> E, Ptr3<float> B, float h
   const float* __restrict__ E2 = E.c[1];
   const float* __restrict__ E3 = E.c[2];
   const float e1 = __ldg(E1 + c), e2 = __ldg(E2 + c), e3 = __ldg(E3 + c);
+  const bool front = L.open_x && i + 1 == L.nx;  // beyond an open x1 boundary: E = 0
   const float dE3d2 = (__ldg(E3 + cy) - e3) * i2;
-  const float dE3d1 = (__ldg(E3 + cx) - e3) * i1;
-  const float dE2d1 = (__ldg(E2 + cx) - e2) * i1;
+  const float dE3d1 = ((front ? 0.f : __ldg(E3 + cx)) - e3) * i1;
+  const float dE2d1 = ((front ? 0.f : __ldg(E2 + cx)) - e2) * i1;
   const float dE1d2 = (__ldg(E1 + cy) - e1) * i2;
   float dE2d3 = 0.f, dE1d3 = 0.f;
   if (L.ndim == 3) {
@@ -229,9 +238,10 @@ __global__ void k_yee_e_f32(Layout L, Ptr3<float> E, Ptr3<float> B, Ptr3<float> 
   const float* __restrict__ B2 = B.c[1];
   const float* __restrict__ B3 = B.c[2];
   const float b1 = __ldg(B1 + c), b2 = __ldg(B2 + c), b3 = __ldg(B3 + c);
+  const bool back = L.open_x && i == 0;  // beyond an open x1 boundary: B = 0
   const float dB3d2 = (b3 - __ldg(B3 + cy)) * i2;
-  const float dB3d1 = (b3 - __ldg(B3 + cx)) * i1;
-  const float dB2d1 = (b2 - __ldg(B2 + cx)) * i1;
+  const float dB3d1 = (b3 - (back ? 0.f : __ldg(B3 + cx))) * i1;
+  const float dB2d1 = (b2 - (back ? 0.f : __ldg(B2 + cx))) * i1;
   const float dB1d2 = (b1 - __ldg(B1 + cy)) * i2;
   float dB2d3 = 0.f, dB1d3 = 0.f;
   if (L.ndim == 3) {
@@ -242,6 +252,75 @@ __global__ void k_yee_e_f32(Layout L, Ptr3<float> E, Ptr3<float> B, Ptr3<float> 
   E.c[0][c] = fmaf(dt, dB3d2 - dB2d3 - __ldg(J.c[0] + c), E.c[0][c]);
   E.c[1][c] = fmaf(dt, dB1d3 - dB3d1 - __ldg(J.c[1] + c), E.c[1][c]);
   E.c[2][c] = fmaf(dt, dB2d1 - dB1d2 - __ldg(J.c[2] + c), E.c[2][c]);
+}
+
+// Moving window: every field value one cell back in x1 (value at i <- value
+// at i + 1), zero in the new front column.  One warp per row; a row is read
+// ahead of where it is written.
+template <typename T>
+__global__ void k_shift_x(Layout L, PtrN<T, 6> P, int ncomp) {
+  const int lane = threadIdx.x & 31;
+  const long long row = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const long long rows = (long long)ncomp * L.ny * L.nz;
+  if (row >= rows) return;
+  const int c = (int)(row / ((long long)L.ny * L.nz));
+  const long long r = row - (long long)c * L.ny * L.nz;
+  const int j = (int)(r % L.ny), k = (int)(r / L.ny);
+  T* f = P.c[c] + L.idx(0, j, k);
+  for (int b = 0; b < L.nx; b += 32) {
+    const int i = b + lane;
+    const T v = i + 1 < L.nx ? f[i + 1] : T(0);
+    __syncwarp();
+    if (i < L.nx) f[i] = v;
+    __syncwarp();
+  }
+}
+
+// Laser pulse moving in +x1 added to E2, E3, B2, B3, each at its staggered
+// position: E_p = -vosc k f(xi) exp(-r^2 / w0^2) sin(k (x1 - x_front) +
+// phase) along p = (0, cos pol, sin pol), B3 = E2, B2 = -E3 (slowly varying
+// envelope of the vector potential A = vosc f T cos(...)); f is sin^2 over
+// the rise, 1 over the length, cos^2 over the fall behind the front.
+struct LaserDev {
+  double vosc, k, w0, rise, length, fall, xfront, c2, c3, cpol, spol, phase;
+  double xmin[3], dx[3];
+};
+
+__device__ inline double laser_amp(const LaserDev& P, int ndim, double x1, double x2, double x3) {
+  const double xi = P.xfront - x1;
+  double f = 0.0;
+  if (xi >= 0.0 && xi < P.rise) {
+    const double s = sin(0.5 * 3.141592653589793 * xi / P.rise);
+    f = s * s;
+  } else if (xi >= P.rise && xi < P.rise + P.length) {
+    f = 1.0;
+  } else if (xi >= P.rise + P.length && xi < P.rise + P.length + P.fall) {
+    const double s = cos(0.5 * 3.141592653589793 * (xi - P.rise - P.length) / P.fall);
+    f = s * s;
+  }
+  if (f == 0.0) return 0.0;
+  double r2 = (x2 - P.c2) * (x2 - P.c2);
+  if (ndim == 3) r2 += (x3 - P.c3) * (x3 - P.c3);
+  return -P.vosc * P.k * f * exp(-r2 / (P.w0 * P.w0)) * sin(P.k * (x1 - P.xfront) + P.phase);
+}
+
+template <typename T>
+__global__ void k_laser_add(Layout L, Ptr6<T> F, LaserDev P) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int k = blockIdx.z;
+  if (i >= L.nx || j >= L.ny) return;
+  const long long c = L.idx(i, j, k);
+  const double h3 = L.ndim == 3 ? 0.5 : 0.0;
+  auto X = [&](int d, int n, double s) { return P.xmin[d] + (n + s) * P.dx[d]; };
+  const double e2 = laser_amp(P, L.ndim, X(0, i, 0.0), X(1, j, 0.5), X(2, k, 0.0)) * P.cpol;
+  const double e3 = laser_amp(P, L.ndim, X(0, i, 0.0), X(1, j, 0.0), X(2, k, h3)) * P.spol;
+  const double b2 = -laser_amp(P, L.ndim, X(0, i, 0.5), X(1, j, 0.0), X(2, k, h3)) * P.spol;
+  const double b3 = laser_amp(P, L.ndim, X(0, i, 0.5), X(1, j, 0.5), X(2, k, 0.0)) * P.cpol;
+  F.c[1][c] = (T)((double)F.c[1][c] + e2);
+  F.c[2][c] = (T)((double)F.c[2][c] + e3);
+  F.c[4][c] = (T)((double)F.c[4][c] + b2);
+  F.c[5][c] = (T)((double)F.c[5][c] + b3);
 }
 
 // ---------------------------------------------------------------- diagnostics
@@ -419,6 +498,37 @@ void yee_e(const Layout& L, T* const* e, T* const* b, T* const* j, double dt, co
 }
 
 template <typename T>
+void shift_x(const Layout& L, T* const* comps, int ncomp, cudaStream_t s) {
+  PtrN<T, 6> P{};
+  for (int c = 0; c < ncomp; ++c) P.c[c] = comps[c];
+  const long long rows = (long long)ncomp * L.ny * L.nz;
+  k_shift_x<T><<<(unsigned)((rows + 7) / 8), 256, 0, s>>>(L, P, ncomp);
+}
+
+template <typename T>
+void laser_add(const Layout& L, T* const* f, const double* p, cudaStream_t s) {
+  Ptr6<T> F{{f[0], f[1], f[2], f[3], f[4], f[5]}};
+  LaserDev P;
+  P.vosc = p[0];
+  P.k = p[1];
+  P.w0 = p[2];
+  P.rise = p[3];
+  P.length = p[4];
+  P.fall = p[5];
+  P.xfront = p[6];
+  P.c2 = p[7];
+  P.c3 = p[8];
+  P.cpol = p[9];
+  P.spol = p[10];
+  P.phase = p[11];
+  for (int d = 0; d < 3; ++d) {
+    P.xmin[d] = p[12 + d];
+    P.dx[d] = p[15 + d];
+  }
+  k_laser_add<T><<<interior_grid(L), kBlock, 0, s>>>(L, F, P);
+}
+
+template <typename T>
 void field_energy(const Layout& L, T* const* f, Diag64* acc, cudaStream_t s) {
   Ptr6<T> F{{f[0], f[1], f[2], f[3], f[4], f[5]}};
   k_field_energy<T><<<interior_grid(L), kBlock, 0, s>>>(L, F, &acc->field_energy);
@@ -455,6 +565,8 @@ void init_e_gauss_x1(const Layout& L, const double* rho, double rho_bg, double d
   template void yee_b_half<T>(const Layout&, T* const*, T* const*, double, const double[3], cudaStream_t);     \
   template void yee_e<T>(const Layout&, T* const*, T* const*, T* const*, double, const double[3], cudaStream_t); \
   template void field_energy<T>(const Layout&, T* const*, Diag64*, cudaStream_t);                             \
+  template void shift_x<T>(const Layout&, T* const*, int, cudaStream_t);                                      \
+  template void laser_add<T>(const Layout&, T* const*, const double*, cudaStream_t);                          \
   template void gauss_residual<T>(const Layout&, T* const*, const double*, double, const double[3], Diag64*,   \
                                   cudaStream_t);                                                              \
   template void pack_interior<T>(const Layout&, const T*, double*, cudaStream_t);                             \

@@ -56,6 +56,9 @@ struct TileArgs {
   float j3f;            // q / dV (2D3V out-of-plane current per unit v3 and time share)
   float e0[3], b0[3];
   int* status;
+  int shift_x;          // moving window: this step ends with a one-cell shift back in x1
+  int open_x;           // x1 open: a particle leaving the box in x1 is dropped
+  int* lost;            // count of dropped particles
 };
 
 // Shared-memory tiles: fields and current cover local cells [-1, T+3) in x
@@ -387,6 +390,7 @@ __device__ inline int push_one(const float* F, float* J, const TileArgs& A, P& p
     if (nz < 0.f) { nz += 1.f; cz = -1; } else if (nz >= 1.f) { nz -= 1.f; cz = 1; }
     if (nz >= 1.f) { nz = 0.f; cz += 1; }
   }
+  cx -= A.shift_x;  // moving window: the cell grid moves one cell forward under the particle
   int gx = lx + cx, gy = ly + cy, gz = lz + cz;
   const int dx_ = gx < 0 ? -1 : (gx >= TX ? 1 : 0);
   const int dy_ = gy < 0 ? -1 : (gy >= TY ? 1 : 0);
@@ -469,6 +473,10 @@ struct Nbr {
 __device__ inline void load_neighbour(const TileArgs& A, int tix, int tiy, int tiz, Nbr* nb) {
   const int d = threadIdx.x;
   if (d < 27) {
+    if (A.open_x && (tix + d % 3 - 1 < 0 || tix + d % 3 - 1 >= A.nt[0])) {
+      nb[d].tile = -1;  // beyond an open x1 boundary
+      return;
+    }
     const int ix = (tix + d % 3 - 1 + A.nt[0]) % A.nt[0];
     const int iy = (tiy + (d / 3) % 3 - 1 + A.nt[1]) % A.nt[1];
     const int iz = (tiz + d / 9 - 1 + A.nt[2]) % A.nt[2];
@@ -492,11 +500,19 @@ __device__ inline void store_leaver(const TileArgs& A, int tix, int tiy, int tiz
   q2.cell = (q.cell & 0x00FFFFFFu) | ((uint32_t)DIR_STAY << 24);
   if (nb) {
     const Nbr& n = nb[dir];
+    if (n.tile < 0) {  // left through an open x1 boundary
+      atomicAdd(A.lost, 1);
+      return;
+    }
     const int slot = atomicAdd(&A.out.inc[n.tile], 1);
     if (slot < n.res)
       store_particle<NDIM>(A.out.p, n.base + n.cap - 1 - slot, q2);
     else
       spill_put(A, n.tile, q2);
+    return;
+  }
+  if (A.open_x && (tix + dir % 3 - 1 < 0 || tix + dir % 3 - 1 >= A.nt[0])) {
+    atomicAdd(A.lost, 1);
     return;
   }
   const int ix = (tix + dir % 3 - 1 + A.nt[0]) % A.nt[0];
@@ -1512,6 +1528,55 @@ __global__ void k_tiled_kinetic(PushConst C, Tiles tg, TileSide in, double* ke, 
   }
 }
 
+// Moving window: fresh plasma for the new front column (cell index nx1 - 1)
+// -- the column's cells in cell order (x3 slowest), the loader's sub-lattice
+// in each cell, momenta from the loader's draws for global particle indices
+// first, first + 1, ... -- appended to the arrival slots of the last tile
+// column on the output side (spill list when full).
+struct InjectSpec {
+  int ndim;
+  int nx[3], ppc[3];
+  double uth[3], ufl[3];
+  unsigned long long seed;
+  long long first;
+};
+
+__global__ void k_inject(TileArgs A, Tiles tg, InjectSpec J, long long count) {
+  const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= count) return;
+  const int ppc = J.ppc[0] * J.ppc[1] * J.ppc[2];
+  const long long col = k / ppc;
+  const int sub = (int)(k - col * ppc);
+  const int cj = (int)(col % J.nx[1]), ck = (int)(col / J.nx[1]);
+  const int si = sub % J.ppc[0], sj = (sub / J.ppc[0]) % J.ppc[1], sk = sub / (J.ppc[0] * J.ppc[1]);
+  const int ix = tg.nt[0] - 1, iy = cj / tg.T[1], iz = J.ndim == 3 ? ck / tg.T[2] : 0;
+  const int t = (iz * tg.nt[1] + iy) * tg.nt[0] + ix;
+  const int lx = J.nx[0] - 1 - ix * tg.T[0], ly = cj - iy * tg.T[1], lz = J.ndim == 3 ? ck - iz * tg.T[2] : 0;
+  P q;
+  q.cell = (uint32_t)lx | ((uint32_t)ly << 8) | ((uint32_t)lz << 16) | ((uint32_t)DIR_STAY << 24);
+  q.o0 = (float)((si + 0.5) / J.ppc[0]);
+  q.o1 = (float)((sj + 0.5) / J.ppc[1]);
+  q.o2 = J.ndim == 3 ? (float)((sk + 0.5) / J.ppc[2]) : 0.f;
+  const unsigned long long g = (unsigned long long)(J.first + k);
+  float uu[3];
+  for (int d = 0; d < 3; ++d)
+    uu[d] = (float)(J.uth[d] != 0.0 ? J.ufl[d] + J.uth[d] * normal_dev(J.seed, 3ull * g + d) : J.ufl[d]);
+  q.u0 = uu[0];
+  q.u1 = uu[1];
+  q.u2 = uu[2];
+  q.id = (int)g;
+  const int slot = atomicAdd(&A.out.inc[t], 1);
+  if (slot < A.res[t]) {
+    const long long s = A.base[t] + A.cap[t] - 1 - slot;
+    if (J.ndim == 3)
+      store_particle<3>(A.out.p, s, q);
+    else
+      store_particle<2>(A.out.p, s, q);  // 2D stores have no third offset array
+  } else {
+    spill_put(A, t, q);
+  }
+}
+
 template <int NDIM, int TX, int TY, int TZ, int MINB, bool SORT = true>
 int occupancy() {
   using G = Geo<NDIM, TX, TY, TZ>;
@@ -1661,6 +1726,9 @@ TileArgs make_args(const PushConst& C, const Tiles& tg, const TileSide& in, cons
   }
   A.j3f = (float)(C.q / C.dvol);
   A.status = status;
+  A.shift_x = 0;
+  A.open_x = 0;
+  A.lost = nullptr;
   return A;
 }
 
@@ -1734,9 +1802,11 @@ bool tiled_push_batch(int ndim, const int T[3], const void* args, const CUtensor
 
 void tiled_push(const Layout& L, const PushConst& C, const Tiles& tg, const TileSide& in, const TileSide& out,
                 Flat32 spill, int* spill_count, long long spill_cap, int grid, int* work, const CUtensorMap* fmap,
-                const CUtensorMap* jmap, int* status, bool stream, int minb, cudaStream_t s) {
-  (void)L;
-  const TileArgs A = make_args(C, tg, in, out, spill, spill_count, spill_cap, work, status);
+                const CUtensorMap* jmap, int* status, bool stream, int minb, int shift_x, int* lost, cudaStream_t s) {
+  TileArgs A = make_args(C, tg, in, out, spill, spill_count, spill_cap, work, status);
+  A.shift_x = shift_x;
+  A.open_x = L.open_x;
+  A.lost = lost;
   cudaMemsetAsync(work, 0, sizeof(int), s);
   cudaMemsetAsync(out.inc, 0, sizeof(int) * (size_t)tg.ntiles, s);
   const int* T = tg.T;
@@ -1763,6 +1833,24 @@ void tiled_push(const Layout& L, const PushConst& C, const Tiles& tg, const Tile
   }
   PICGB_TILE_SHAPES(X)
 #undef X
+}
+
+void tiled_inject(const PushConst& C, const Tiles& tg, const TileSide& out, Flat32 spill, int* spill_count,
+                  long long spill_cap, int* status, const int nx[3], const int ppc[3], const double uth[3],
+                  const double ufl[3], unsigned long long seed, long long first, long long count, cudaStream_t s) {
+  if (count <= 0) return;
+  const TileArgs A = make_args(C, tg, out, out, spill, spill_count, spill_cap, nullptr, status);
+  InjectSpec J;
+  J.ndim = tg.ndim;
+  for (int d = 0; d < 3; ++d) {
+    J.nx[d] = nx[d];
+    J.ppc[d] = ppc[d];
+    J.uth[d] = uth[d];
+    J.ufl[d] = ufl[d];
+  }
+  J.seed = seed;
+  J.first = first;
+  k_inject<<<(unsigned)((count + 255) / 256), 256, 0, s>>>(A, tg, J, count);
 }
 
 void tiled_flatten(const Tiles& tg, const TileSide& in, const long long* out_off, Flat32 out, cudaStream_t s) {

@@ -24,6 +24,11 @@ void yee_b_half(const Layout& L, T* const* e, T* const* b, double dt, const doub
 template <typename T>
 void yee_e(const Layout& L, T* const* e, T* const* b, T* const* j, double dt, const double dx[3], cudaStream_t s);
 template <typename T> void field_energy(const Layout& L, T* const* f, Diag64* acc, cudaStream_t s);
+// moving window: every E/B value one cell back in x1, zero front column
+template <typename T> void shift_x(const Layout& L, T* const* comps, int ncomp, cudaStream_t s);
+// laser pulse added to E2, E3, B2, B3; p: vosc, k, w0, rise, length, fall,
+// x_front, axis x2, axis x3, cos pol, sin pol, phase, xmin[3], dx[3]
+template <typename T> void laser_add(const Layout& L, T* const* f, const double* p, cudaStream_t s);
 template <typename T>
 void gauss_residual(const Layout& L, T* const* e, const double* rho, double rho_bg, const double dx[3], Diag64* acc,
                     cudaStream_t s);
@@ -94,7 +99,13 @@ struct TileSide {
 // read in, compacted); false: the step that counting-sorts every tile by cell
 void tiled_push(const Layout& L, const PushConst& C, const Tiles& tg, const TileSide& in, const TileSide& out,
                 Flat32 spill, int* spill_count, long long spill_cap, int grid, int* work, const CUtensorMap* fmap,
-                const CUtensorMap* jmap, int* status, bool stream, int minb, cudaStream_t s);
+                const CUtensorMap* jmap, int* status, bool stream, int minb, int shift_x, int* lost,
+                cudaStream_t s);
+// moving window: `count` fresh particles of the front column appended to the
+// last tile column of side `out` (global particle indices first, ...)
+void tiled_inject(const PushConst& C, const Tiles& tg, const TileSide& out, Flat32 spill, int* spill_count,
+                  long long spill_cap, int* status, const int nx[3], const int ppc[3], const double uth[3],
+                  const double ufl[3], unsigned long long seed, long long first, long long count, cudaStream_t s);
 // Batched form: many simulations (one table entry per simulation and species)
 // in one launch of the sorting kernel.  tiled_fill_args writes one entry
 // (tiled_args_bytes bytes) on the host; tile0[n] is the exclusive prefix of

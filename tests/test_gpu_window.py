@@ -1,0 +1,70 @@
+"""GPU parity of the moving window and the laser set-up against the oracle.
+
+* pic_laser_add: E2, E3, B2, B3 of the pulse equal the oracle's laser_fields
+  (FP64 form to 1e-12, FP32 form to 1e-6 of the peak: one rounding).
+* A 2D run with the window moving at c, a laser pulse and a warm plasma: after
+  20 steps (about 14 one-cell shifts) the shift count, the set of surviving
+  particles (ids: the back columns dropped, the injected ones continuing the
+  loader's sequence), their positions and momenta (1e-4 of a cell / of u: FP32
+  against FP64 over 20 steps, as the many-step parity test) and the fields
+  (1e-4 of their maxima) match the oracle.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workload
+
+pytestmark = pytest.mark.gpu
+
+NAMES = ["E1", "E2", "E3", "B1", "B2", "B3"]
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32", 1e-6)])
+def test_laser_setup_matches_oracle(prec, tol):
+    import paper_1503_00276_gb300 as pg
+    dx = (0.1, 0.2, 1.0)
+    g = workload.Grid(ndim=2, nx=(128, 32, 1), dx=dx, dt=workload.courant_dt(dx, 2))
+    las = workload.Laser(vosc=2.0, rkkp=10.0, w0=1.5, rise=1.5, length=0.5, fall=1.5, start=2.0, pol=30.0,
+                         phase=0.3, offset=(0.4, 0.0))
+    sim = pg.Simulation(g, [], precision=prec, tile=(32, 16) if prec == "fp32" else None)
+    sim.add_laser(las)
+    ref = oracle.laser_fields(g, las)
+    for c, name in enumerate(NAMES):
+        m = max(np.max(np.abs(ref[c])), 1e-300)
+        assert np.max(np.abs(sim.fields(name) - ref[c])) <= tol * max(m, 1.0), name
+    sim.close()
+
+
+def test_moving_window_with_laser_matches_oracle():
+    import paper_1503_00276_gb300 as pg
+    dx = (0.1, 0.2, 1.0)
+    g = workload.Grid(ndim=2, nx=(64, 32, 1), dx=dx, dt=workload.courant_dt(dx, 2), move_window=True)
+    sp = workload.Species(ppc=(2, 2, 1), uth=(0.1, 0.1, 0.1), ufl=(0.3, 0.0, 0.0), seed=17)
+    las = workload.Laser(vosc=0.5, rkkp=8.0, w0=2.0, rise=1.0, fall=1.0, start=1.0)
+    ref = oracle.from_workload(g, [sp])
+    for c, f in enumerate(oracle.laser_fields(g, las)):
+        ref.fld[c] += f
+    sim = pg.Simulation(g, [sp], precision="fp32", tile=(32, 16), track_ids=True)
+    sim.add_laser(las)
+    n = 20
+    ref.step(n)
+    sim.step(n)
+    assert ref.shifts >= 10
+    ids = sim.ids()
+    x, u = sim.particles()
+    assert np.array_equal(np.sort(ids), np.sort(ref.ids[0]))
+    pos = {int(i): k for k, i in enumerate(ref.ids[0])}
+    order = np.array([pos[int(i)] for i in ids])
+    L2 = g.nx[1] * dx[1]
+    d = x - ref.x[0][order]
+    d[:, 1] -= L2 * np.round(d[:, 1] / L2)
+    assert np.max(np.abs(d[:, 0] / dx[0])) < 1e-4 and np.max(np.abs(d[:, 1] / dx[1])) < 1e-4
+    assert np.max(np.abs(u - ref.u[0][order])) < 1e-4
+    for c, name in enumerate(NAMES):
+        m = np.max(np.abs(ref.fld[c]))
+        if m == 0:
+            continue
+        assert np.max(np.abs(sim.fields(name) - ref.fld[c])) < 1e-4 * m, name
+    assert sim.diag()["n_particles"] == ref.x[0].shape[0]
+    sim.close()

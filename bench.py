@@ -65,6 +65,9 @@ def parse():
     p.add_argument("--scan-steps", type=int, default=20,
                    help="timed steps of the batched-scan comparison (64 runs, batched vs one by one)")
     p.add_argument("--no-scan", action="store_true")
+    p.add_argument("--wake-steps", type=int, default=200,
+                   help="timed steps of the 2D laser-wakefield workload (moving window)")
+    p.add_argument("--no-wake", action="store_true")
     return p.parse_args()
 
 
@@ -295,6 +298,8 @@ def run_ours(args):
 
     if not args.no_scan:
         out["batch_scan"] = run_batch_scan(args, max_over_ranks)
+    if not args.no_wake:
+        out["wakefield_2d"] = run_wakefield(args, max_over_ranks)
 
     if rank == 0 and ws == 1 and not args.no_cpu:
         out["cpu_baseline"] = run_cpu_baseline(args, budget_s=15.0)
@@ -303,6 +308,38 @@ def run_ours(args):
     if dist is not None:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def run_wakefield(args, max_over_ranks):
+    """The 2D laser-wakefield workload in the FP32 form: 2048 x 256 cells,
+    4.2M electrons, laser a0 = 2, window moving at c (a one-cell shift with
+    a fresh front column about every 1.5 steps)."""
+    import torch
+
+    import paper_1503_00276_gb300 as pg
+    import workload
+
+    g, sps, las, _ = workload.config1()
+    sim = pg.Simulation(g, sps, precision="fp32")
+    sim.add_laser(las)
+    K, W = args.wake_steps, 5
+    stream = torch.cuda.current_stream()
+    sim.step(W)
+    torch.cuda.synchronize()
+    n0 = sim.n_particles()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    sim.step(K)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = max_over_ranks(e0.elapsed_time(e1))
+    d = sim.diag()
+    info = sim.info()
+    sim.close()
+    return {"workload": "2D3V laser wakefield 2048x256 cells, dx 0.05 x 0.2, 8 ppc cold electrons "
+                        f"({n0:,}), a0=2, omega0=10, spot 4, window moving at c", "steps": K, "warmup": W,
+            "value": n0 * K / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / K, "tile": list(info["tile"]),
+            "field_energy_after": d["field_energy"], "n_particles_after": d["n_particles"]}
 
 
 def run_batch_scan(args, max_over_ranks):

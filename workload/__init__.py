@@ -210,6 +210,20 @@ def config0(seed: int = 20001):
     return g, [s], 100
 
 
+def config1(seed: int = 20002):
+    """2D3V laser wakefield: 2048 x 256 cells, dx1 = 0.05, dx2 = 0.2, 8 ppc (4 x 2)
+    cold uniform electrons, window moving at c in x1, a pulse a0 = 2,
+    omega0/omega_p = 10, spot 4, polarised in x2, sin^2 rise and fall of 1.5
+    (the intensity FWHM duration 1.5 read as the envelope distances), front
+    1.0 behind the +x1 edge; 2000 steps.  The plasma fills the window from the
+    start (no vacuum gap: density profiles are not part of this hot path)."""
+    dx = (0.05, 0.2, 1.0)
+    g = Grid(ndim=2, nx=(2048, 256, 1), dx=dx, dt=courant_dt(dx, 2), move_window=True)
+    s = Species(rqm=-1.0, ppc=(4, 2, 1), uth=(0.0, 0.0, 0.0), seed=seed)
+    las = Laser(vosc=2.0, rkkp=10.0, w0=4.0, rise=1.5, length=0.0, fall=1.5, start=1.0)
+    return g, [s], las, 2000
+
+
 def config3(ppc_total: int = 8, seed: int = 20004, nx=(512, 256, 256)):
     """3D3V periodic thermal plasma, 512x256x256 cells, u_th = 0.05, 200 steps."""
     lattice = {1: (1, 1, 1), 2: (2, 1, 1), 4: (2, 2, 1), 8: (2, 2, 2), 16: (4, 2, 2)}[ppc_total]

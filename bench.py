@@ -300,6 +300,7 @@ def run_ours(args):
         out["batch_scan"] = run_batch_scan(args, max_over_ranks)
     if not args.no_wake:
         out["wakefield_2d"] = run_wakefield(args, max_over_ranks)
+        out["beam_wake_3d"] = run_beam_wake(args, max_over_ranks)
 
     if rank == 0 and ws == 1 and not args.no_cpu:
         out["cpu_baseline"] = run_cpu_baseline(args, budget_s=15.0)
@@ -340,6 +341,36 @@ def run_wakefield(args, max_over_ranks):
                         f"({n0:,}), a0=2, omega0=10, spot 4, window moving at c", "steps": K, "warmup": W,
             "value": n0 * K / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / K, "tile": list(info["tile"]),
             "field_energy_after": d["field_energy"], "n_particles_after": d["n_particles"]}
+
+
+def run_beam_wake(args, max_over_ranks):
+    """The 3D beam-driven wake in the FP32 form: 256 x 128 x 128 cells, 33.5M
+    plasma electrons plus a 4.2M-macroparticle bi-Gaussian driver at
+    gamma = 60000, window moving at c."""
+    import torch
+
+    import paper_1503_00276_gb300 as pg
+    import workload
+
+    g, sps, (bx, bu, bq), _ = workload.config2()
+    sim = pg.Simulation(g, sps, precision="fp32", explicit=[None, (bx, bu, bq)])
+    K, W = max(args.wake_steps // 4, 10), 5
+    stream = torch.cuda.current_stream()
+    sim.step(W)
+    torch.cuda.synchronize()
+    n0 = sim.n_particles(0) + sim.n_particles(1)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    sim.step(K)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = max_over_ranks(e0.elapsed_time(e1))
+    info = sim.info()
+    sim.close()
+    return {"workload": "3D3V beam-driven wake 256x128x128 cells, dx 0.05 x 0.1 x 0.1, 8 ppc cold plasma + "
+                        f"bi-Gaussian driver gamma=60000, sigma 1 x 0.3, n_b/n_0=5 ({n0:,} particles), window "
+                        "moving at c", "steps": K, "warmup": W, "value": n0 * K / (ms / 1e3), "unit": UNIT,
+            "ms_per_step": ms / K, "tile": list(info["tile"])}
 
 
 def run_batch_scan(args, max_over_ranks):

@@ -56,9 +56,9 @@ __global__ void k_tile_totals(const int* stay, const int* inc, const int* res, i
   if (k < n) tot[k] = stay[k] + (inc[k] < res[k] ? inc[k] : res[k]);
 }
 
-struct StatusWord {
+struct StatusWord {  // status bits of every kernel of one simulation (ST_*); spill counts are per species
   int status;
-  int spill_count;
+  int pad;
 };
 
 // ------------------------------------------------------------- allocation
@@ -121,6 +121,7 @@ struct SpeciesState {
   unsigned long long seed = 0;
   long long created = 0;    // particles ever created (ids and draw indices continue from here)
   int* d_lost = nullptr;    // particles dropped through an open x1 boundary in the last step
+  int* d_spill = nullptr;   // records in this species' spill list
 };
 
 constexpr int kTimingSlots = 5;
@@ -508,6 +509,23 @@ pic_status rebuild(pic_sim* S, SpeciesState& sp, int spill_n) {
   return st;
 }
 
+// Every species whose spill list holds records is re-binned (its records
+// merged back into the store); the counters restart from zero.
+pic_status rebuild_spilled(pic_sim* S) {
+  for (auto& s : S->sp) {
+    if (!s.d_spill) continue;
+    int n = 0;
+    if (cudaMemcpyAsync(&n, s.d_spill, sizeof(int), cudaMemcpyDeviceToHost, S->s) != cudaSuccess ||
+        cudaStreamSynchronize(S->s) != cudaSuccess)
+      return cuda_check("spill count");
+    if (n <= 0) continue;
+    const pic_status st = rebuild(S, s, (int)std::min<long long>(n, s.spill_cap));
+    if (st != PIC_OK) return st;
+    cudaMemsetAsync(s.d_spill, 0, sizeof(int), S->s);
+  }
+  return PIC_OK;
+}
+
 // ------------------------------------------------------------- loading
 pic_status load_species(pic_sim* S, const pic_species& in, SpeciesState& sp) {
   const pic_grid& g = S->g;
@@ -715,11 +733,13 @@ pic_status alloc_spill(pic_sim* S, SpeciesState& sp) {
   bool ok = true;
   sp.spill = alloc_flat(S, sp.spill_cap, sp.ids, ok);
   sp.d_lost = (int*)S->al.get(sizeof(int));
-  if (!ok || !sp.d_lost) {
+  sp.d_spill = (int*)S->al.get(sizeof(int));
+  if (!ok || !sp.d_lost || !sp.d_spill) {
     set_error("out of device memory (spill list)");
     return PIC_ENOMEM;
   }
   cudaMemsetAsync(sp.d_lost, 0, sizeof(int), S->s);
+  cudaMemsetAsync(sp.d_spill, 0, sizeof(int), S->s);
   if (sp.created < sp.n) sp.created = sp.n;
   return PIC_OK;
 }
@@ -790,14 +810,14 @@ pic_status one_step(pic_sim* S, bool check_now) {
         // the last step of every sort_period steps re-sorts each tile by cell;
         // the steps before it keep the order they find (blocks compacted)
         const bool stream = S->sort_period > 1 && !s.tg.small && (S->step + 1) % S->sort_period != 0;
-        tiled_push(S->L, C, s.tg, s.side[in], s.side[out], s.spill, &S->dstat->spill_count, s.spill_cap,
+        tiled_push(S->L, C, s.tg, s.side[in], s.side[out], s.spill, s.d_spill, s.spill_cap,
                    s.grid, s.work, &S->fmap, &S->jmap, &S->dstat->status, stream, S->minb, shift ? 1 : 0, s.d_lost,
                    S->s);
         s.cur = out;
         if (shift) {  // fresh plasma for the new front column
           const long long cnt = (long long)S->L.ny * S->L.nz * s.ppc[0] * s.ppc[1] * s.ppc[2];
           const int nxs[3] = {S->L.nx, S->L.ny, S->L.nz};
-          tiled_inject(C, s.tg, s.side[out], s.spill, &S->dstat->spill_count, s.spill_cap, &S->dstat->status, nxs,
+          tiled_inject(C, s.tg, s.side[out], s.spill, s.d_spill, s.spill_cap, &S->dstat->status, nxs,
                        s.ppc, s.uth, s.ufl, s.seed, s.created, cnt, S->s);
           s.created += cnt;
           s.n += cnt;
@@ -842,10 +862,7 @@ pic_status one_step(pic_sim* S, bool check_now) {
     }
     // the spilled particles were fully advanced; re-bin before the next step
     Span rb(S, 3);
-    for (auto& s : S->sp) {
-      st = rebuild(S, s, S->hstat->spill_count);
-      if (st != PIC_OK) return st;
-    }
+    if ((st = rebuild_spilled(S)) != PIC_OK) return st;
     cudaMemsetAsync(S->dstat, 0, sizeof(StatusWord), S->s);
   }
   if (flags & ST_TIMEOUT) {
@@ -1485,7 +1502,7 @@ pic_status batch_build(pic_batch* B) {
       }
       PushConst C = make_const(S, sp);
       StatusWord* st = S->dstat;
-      tiled_fill_args(args.data() + ab * k, C, sp.tg, sp.side[p], sp.side[1 - p], sp.spill, &st->spill_count,
+      tiled_fill_args(args.data() + ab * k, C, sp.tg, sp.side[p], sp.side[1 - p], sp.spill, sp.d_spill,
                       sp.spill_cap, &st->status);
       if (p == 0) {
         fme[k] = S->fmap;
@@ -1680,10 +1697,8 @@ pic_status pic_batch_step(pic_batch* B, int nsteps) {
           set_error("pic_batch_step: simulation " + std::to_string(i) + ": spill list overflowed");
           return PIC_EOVERFLOW;
         }
-        for (auto& sp : S->sp) {
-          const pic_status st = rebuild(S, sp, B->h_stat[i].spill_count);
-          if (st != PIC_OK) return st;
-        }
+        const pic_status st = rebuild_spilled(S);
+        if (st != PIC_OK) return st;
         cudaMemsetAsync(S->dstat, 0, sizeof(StatusWord), B->s);
         B->dirty = true;
       }

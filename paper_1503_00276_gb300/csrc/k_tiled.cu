@@ -1401,7 +1401,14 @@ __global__ void k_global_to_flat(int ndim, Layout L, Tiles tg, PushConst C, cons
       o = 0.f;
       c += 1;
     }
-    if (c >= nn[d]) c -= nn[d];
+    if (c >= nn[d]) {
+      if (d == 0 && L.open_x) {  // open x1: stay in the last cell, just below its far face
+        c = nn[d] - 1;
+        o = 0.99999994f;
+      } else {
+        c -= nn[d];
+      }
+    }
     cell[d] = (int)c;
     off[d] = o;
   }

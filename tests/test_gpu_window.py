@@ -68,3 +68,38 @@ def test_moving_window_with_laser_matches_oracle():
         assert np.max(np.abs(sim.fields(name) - ref.fld[c])) < 1e-4 * m, name
     assert sim.diag()["n_particles"] == ref.x[0].shape[0]
     sim.close()
+
+
+def test_beam_driver_in_moving_window_matches_oracle():
+    """A plasma plus a bi-Gaussian relativistic driver (explicit species, no
+    injection) in a 3D moving window: both species against the oracle after
+    10 steps."""
+    import paper_1503_00276_gb300 as pg
+    dx = (0.05, 0.1, 0.1)
+    g = workload.Grid(ndim=3, nx=(64, 16, 16), dx=dx, dt=workload.courant_dt(dx, 3), move_window=True)
+    plasma = workload.Species(ppc=(1, 1, 2), uth=(0.02, 0.02, 0.02), seed=41)
+    beam = workload.Species(rqm=-1.0, ppc=(0, 0, 0), seed=42)
+    bx, bu, bq = workload.beam_particles(g, 3000, (2.2, 0.8, 0.8), 0.3, 0.15, 100.0, 2.0, 42)
+    px, pu = workload.load_particles(g, plasma)
+    ref = oracle.State(g, [plasma, beam], [px, bx], [pu, bu], [workload.macro_charge(g, plasma), bq])
+    sim = pg.Simulation(g, [plasma, beam], precision="fp32", explicit=[None, (bx, bu, bq)], tile=(16, 8, 4),
+                        track_ids=True)
+    ref.step(10)
+    sim.step(10)
+    assert ref.shifts >= 5
+    for s in range(2):
+        ids = sim.ids(s)
+        x, u = sim.particles(s)
+        assert np.array_equal(np.sort(ids), np.sort(ref.ids[s]))
+        pos = {int(i): k for k, i in enumerate(ref.ids[s])}
+        order = np.array([pos[int(i)] for i in ids])
+        L = np.array([1e300, g.nx[1] * dx[1], g.nx[2] * dx[2]])
+        d = x - ref.x[s][order]
+        d[:, 1:] -= L[1:] * np.round(d[:, 1:] / L[1:])
+        assert np.max(np.abs(d / np.array(dx))) < 1e-4, s
+        assert np.max(np.abs(u - ref.u[s][order]) / (1 + np.abs(ref.u[s][order]))) < 1e-4, s
+    for c, name in enumerate(NAMES):
+        m = np.max(np.abs(ref.fld[c]))
+        if m > 0:
+            assert np.max(np.abs(sim.fields(name) - ref.fld[c])) < 1e-4 * m, name
+    sim.close()

@@ -224,6 +224,48 @@ def config1(seed: int = 20002):
     return g, [s], las, 2000
 
 
+def beam_particles(grid: Grid, n: int, center, sigma1: float, sigma_r: float, gamma: float, peak_density: float,
+                   seed: int):
+    """A bi-Gaussian electron driver of n macroparticles: x1 ~ N(center1,
+    sigma1), x2, x3 ~ N(center, sigma_r) (draw 3p + d of the SplitMix64 /
+    Box-Muller stream ``seed`` for particle p), longitudinal x1 clipped to the
+    box, transverse wrapped (periodic); every u = (sqrt(gamma^2 - 1), 0, 0).
+    The macro-charge makes the peak density ``peak_density``: total charge
+    -peak (2 pi)^(d/2) sigma1 sigma_r^(d-1).  Returns (x, u, q)."""
+    p = np.arange(n, dtype=np.uint64)
+    x = np.zeros((n, 3))
+    for d in range(grid.ndim):
+        z = normal(seed, np.uint64(3) * p + np.uint64(d))
+        sig = sigma1 if d == 0 else sigma_r
+        x[:, d] = center[d] + sig * z
+        lo, L = grid.xmin[d], grid.nx[d] * grid.dx[d]
+        if d == 0:
+            x[:, 0] = np.clip(x[:, 0], lo, np.nextafter(lo + L, lo))
+        else:
+            x[:, d] = lo + np.mod(x[:, d] - lo, L)
+    u = np.zeros((n, 3))
+    u[:, 0] = math.sqrt(gamma * gamma - 1.0)
+    vol = (2.0 * math.pi) ** (grid.ndim / 2.0) * sigma1 * sigma_r ** (grid.ndim - 1)
+    q = -peak_density * vol / n
+    return x, u, q
+
+
+def config2(seed: int = 20003, nx=(256, 128, 128), nbeam: int = 4194304):
+    """3D3V beam-driven wake: 256 x 128 x 128 cells, dx1 = 0.05, dx2 = dx3 = 0.1,
+    8 ppc (2 x 2 x 2) cold electrons plus a bi-Gaussian driver (gamma = 60000,
+    sigma_z = 1, sigma_r = 0.3, peak n_b/n_0 = 5, ``nbeam`` macroparticles)
+    centred 3 behind the +x1 edge on the axis, window moving at c; 500 steps.
+    Returns (grid, [plasma, beam species], (x, u, q) of the beam, steps)."""
+    dx = (0.05, 0.1, 0.1)
+    g = Grid(ndim=3, nx=tuple(nx), dx=dx, dt=courant_dt(dx, 3), move_window=True)
+    plasma = Species(rqm=-1.0, ppc=(2, 2, 2), uth=(0.0, 0.0, 0.0), seed=seed)
+    beam = Species(rqm=-1.0, ppc=(0, 0, 0), seed=seed + 1)
+    L = [g.nx[d] * g.dx[d] for d in range(3)]
+    centre = (L[0] - 3.0, 0.5 * L[1], 0.5 * L[2])
+    bx, bu, bq = beam_particles(g, nbeam, centre, 1.0, 0.3, 60000.0, 5.0, seed + 1)
+    return g, [plasma, beam], (bx, bu, bq), 500
+
+
 def config3(ppc_total: int = 8, seed: int = 20004, nx=(512, 256, 256)):
     """3D3V periodic thermal plasma, 512x256x256 cells, u_th = 0.05, 200 steps."""
     lattice = {1: (1, 1, 1), 2: (2, 1, 1), 4: (2, 2, 1), 8: (2, 2, 2), 16: (4, 2, 2)}[ppc_total]
@@ -275,6 +317,8 @@ def inject_column(grid: Grid, sp: Species, xmin1: float, first_index: int):
     nx, ny = int(grid.nx[0]), int(grid.nx[1])
     nz = int(grid.nx[2]) if grid.ndim == 3 else 1
     ppc = sp.ppc_total
+    if ppc == 0:  # a species without a lattice (a beam) gets no fresh plasma
+        return np.zeros((0, 3)), np.zeros((0, 3))
     k = np.arange(ny * nz * ppc, dtype=np.int64)
     col = k // ppc
     sub = k % ppc

@@ -325,8 +325,10 @@ def run_wakefield(args, max_over_ranks):
     sim.add_laser(las)
     K, W = args.wake_steps, 5
     stream = torch.cuda.current_stream()
+    sim.timing_enable(True)
     sim.step(W)
     torch.cuda.synchronize()
+    sim.timing_read(reset=True)
     n0 = sim.n_particles()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
@@ -334,12 +336,15 @@ def run_wakefield(args, max_over_ranks):
     e1.record(stream)
     torch.cuda.synchronize()
     ms = max_over_ranks(e0.elapsed_time(e1))
+    tim = sim.timing_read()
     d = sim.diag()
     info = sim.info()
     sim.close()
     return {"workload": "2D3V laser wakefield 2048x256 cells, dx 0.05 x 0.2, 8 ppc cold electrons "
                         f"({n0:,}), a0=2, omega0=10, spot 4, window moving at c", "steps": K, "warmup": W,
             "value": n0 * K / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / K, "tile": list(info["tile"]),
+            "stages_ms_per_step": {k: round(v[0] / K, 4) for k, v in tim.items() if k != "launches"},
+            "rebuilds": int(tim["rebuild"][1]),
             "field_energy_after": d["field_energy"], "n_particles_after": d["n_particles"]}
 
 
@@ -356,8 +361,10 @@ def run_beam_wake(args, max_over_ranks):
     sim = pg.Simulation(g, sps, precision="fp32", explicit=[None, (bx, bu, bq)])
     K, W = max(args.wake_steps // 4, 10), 5
     stream = torch.cuda.current_stream()
+    sim.timing_enable(True)
     sim.step(W)
     torch.cuda.synchronize()
+    sim.timing_read(reset=True)
     n0 = sim.n_particles(0) + sim.n_particles(1)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
@@ -365,12 +372,15 @@ def run_beam_wake(args, max_over_ranks):
     e1.record(stream)
     torch.cuda.synchronize()
     ms = max_over_ranks(e0.elapsed_time(e1))
+    tim = sim.timing_read()
     info = sim.info()
     sim.close()
     return {"workload": "3D3V beam-driven wake 256x128x128 cells, dx 0.05 x 0.1 x 0.1, 8 ppc cold plasma + "
                         f"bi-Gaussian driver gamma=60000, sigma 1 x 0.3, n_b/n_0=5 ({n0:,} particles), window "
                         "moving at c", "steps": K, "warmup": W, "value": n0 * K / (ms / 1e3), "unit": UNIT,
-            "ms_per_step": ms / K, "tile": list(info["tile"])}
+            "ms_per_step": ms / K, "tile": list(info["tile"]),
+            "stages_ms_per_step": {k: round(v[0] / K, 4) for k, v in tim.items() if k != "launches"},
+            "rebuilds": int(tim["rebuild"][1])}
 
 
 def run_batch_scan(args, max_over_ranks):

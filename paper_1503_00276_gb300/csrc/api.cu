@@ -50,12 +50,6 @@ __global__ void k_check_box(int ndim, PushConst C, const double* x0, const doubl
   }
 }
 
-// particles held by each tile: its stayers plus its arrivals (at most res)
-__global__ void k_tile_totals(const int* stay, const int* inc, const int* res, int* tot, int n) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k < n) tot[k] = stay[k] + (inc[k] < res[k] ? inc[k] : res[k]);
-}
-
 struct StatusWord {  // status bits of every kernel of one simulation (ST_*); spill counts are per species
   int status;
   int pad;
@@ -122,6 +116,8 @@ struct SpeciesState {
   long long created = 0;    // particles ever created (ids and draw indices continue from here)
   int* d_lost = nullptr;    // particles dropped through an open x1 boundary in the last step
   int* d_spill = nullptr;   // records in this species' spill list
+  SliceScratch slices{};    // work items of the tile kernel (heavy tiles split)
+  double slack = 0.25;      // region growth room; raised after each spill
 };
 
 constexpr int kTimingSlots = 5;
@@ -384,19 +380,43 @@ pic_status bin_flat(pic_sim* S, SpeciesState& sp, Flat32& flat, long long n) {
     set_error("binning: " + std::to_string(n - total) + " particles outside the grid");
     return PIC_EINVAL;
   }
-  // region of tile t: its count plus slack for growth, of which the back
-  // part `res` receives the particles entering the tile during a step
+  // Region of tile t: its count plus slack for growth, of which the back
+  // part `res` receives the particles entering the tile during a step.  The
+  // arrivals come from the neighbours, so `res` follows the fullest of the 27
+  // tiles around (a tile ahead of a dense beam is empty until the beam enters
+  // it); with a moving window a shift step also brings the whole first cell
+  // column of the tile ahead in x1.
   std::vector<int> hcap(nt), hres(nt);
   std::vector<long long> hbase(nt);
+  const int* ntd = sp.tg.nt;
+  std::vector<long long> nbmax(nt, 0);
+  for (int t = 0; t < nt; ++t) {
+    const int ix = t % ntd[0], iy = (t / ntd[0]) % ntd[1], iz = t / (ntd[0] * ntd[1]);
+    long long m = 0;
+    for (int dz = (ntd[2] > 1 ? -1 : 0); dz <= (ntd[2] > 1 ? 1 : 0); ++dz)
+      for (int dy = (ntd[1] > 1 ? -1 : 0); dy <= (ntd[1] > 1 ? 1 : 0); ++dy)
+        for (int dx = (ntd[0] > 1 ? -1 : 0); dx <= (ntd[0] > 1 ? 1 : 0); ++dx) {
+          const int jx = (ix + dx + ntd[0]) % ntd[0], jy = (iy + dy + ntd[1]) % ntd[1];
+          const int jz = (iz + dz + ntd[2]) % ntd[2];
+          m = std::max<long long>(m, hc[(jz * ntd[1] + jy) * ntd[0] + jx]);
+        }
+    nbmax[t] = m;
+  }
   long long slots = 0;
   for (int t = 0; t < nt; ++t) {
     const long long c = hc[t];
-    const long long extra = std::max<long long>(64, (long long)std::ceil(c * S->slack));
+    long long res = std::max<long long>(32, (long long)std::ceil(0.5 * sp.slack * nbmax[t]));
+    if (S->moving) {
+      const int ix = t % ntd[0];
+      const long long ahead = ix + 1 < ntd[0] ? hc[t + 1] : 0;
+      res = std::max<long long>(res, (long long)std::ceil(1.25 * ahead / S->T[0]) + 32);
+    }
+    res = (res + 3) / 4 * 4;  // a multiple of 4, so that the stayer part ends 16-byte aligned
+    const long long extra = std::max<long long>({64, (long long)std::ceil(c * sp.slack), 2 * res});
     long long cap = (c + extra + 3) / 4 * 4;
     if (cap > (1ll << 30)) cap = 1ll << 30;
     hcap[t] = (int)cap;
-    // a multiple of 4, so that the stayer part of a region ends 16-byte aligned
-    hres[t] = (int)(std::min<long long>(cap - c, std::max<long long>(32, extra / 2)) & ~3ll);
+    hres[t] = (int)(std::min<long long>(cap - c, res) & ~3ll);
     hbase[t] = slots;
     slots += cap;
   }
@@ -416,6 +436,15 @@ pic_status bin_flat(pic_sim* S, SpeciesState& sp, Flat32& flat, long long n) {
       return PIC_ENOMEM;
     }
     sp.slots = slots;
+    S->al.put(sp.slices.extra);
+    const long long ecap = slice_list_capacity(slots, nt);
+    sp.slices.extra = (int2*)S->al.get(sizeof(int2) * (size_t)ecap);
+    sp.slices.cap = (int)std::min<long long>(ecap, 1ll << 30);
+    if (!sp.slices.extra) {
+      S->al.put(counts);
+      set_error("out of device memory (slice list)");
+      return PIC_ENOMEM;
+    }
   }
   long long max_cap = 0;
   for (int t = 0; t < nt; ++t) max_cap = std::max<long long>(max_cap, hcap[t]);
@@ -519,6 +548,9 @@ pic_status rebuild_spilled(pic_sim* S) {
         cudaStreamSynchronize(S->s) != cudaSuccess)
       return cuda_check("spill count");
     if (n <= 0) continue;
+    // regions sized afresh from the new counts, with more growth room than
+    // the last time (a beam keeps filling the tiles ahead of it)
+    s.slack = std::min(1.0, std::max(s.slack, 0.25) * 1.5);
     const pic_status st = rebuild(S, s, (int)std::min<long long>(n, s.spill_cap));
     if (st != PIC_OK) return st;
     cudaMemsetAsync(s.d_spill, 0, sizeof(int), S->s);
@@ -717,7 +749,9 @@ pic_status setup_tiles(pic_sim* S, SpeciesState& sp) {
     ok = ok && sd.stay && sd.inc;
   }
   sp.work = (int*)S->al.get(sizeof(int));
-  if (!ok || !sp.work) {
+  sp.slices.nslice = (int*)S->al.get(4 * (size_t)tg.ntiles);
+  sp.slices.nextra = (int*)S->al.get(sizeof(int));
+  if (!ok || !sp.work || !sp.slices.nslice || !sp.slices.nextra) {
     set_error("out of device memory (tile tables)");
     return PIC_ENOMEM;
   }
@@ -810,9 +844,10 @@ pic_status one_step(pic_sim* S, bool check_now) {
         // the last step of every sort_period steps re-sorts each tile by cell;
         // the steps before it keep the order they find (blocks compacted)
         const bool stream = S->sort_period > 1 && !s.tg.small && (S->step + 1) % S->sort_period != 0;
-        tiled_push(S->L, C, s.tg, s.side[in], s.side[out], s.spill, s.d_spill, s.spill_cap,
-                   s.grid, s.work, &S->fmap, &S->jmap, &S->dstat->status, stream, S->minb, shift ? 1 : 0, s.d_lost,
-                   S->s);
+        const int nk = tiled_push(S->L, C, s.tg, s.side[in], s.side[out], s.spill, s.d_spill, s.spill_cap, s.grid,
+                                  s.work, &S->fmap, &S->jmap, &S->dstat->status, stream, S->minb, shift ? 1 : 0,
+                                  s.d_lost, &s.slices, S->s);
+        S->nlaunch += nk - 1;  // the tile kernel itself is counted below
         s.cur = out;
         if (shift) {  // fresh plasma for the new front column
           const long long cnt = (long long)S->L.ny * S->L.nz * s.ppc[0] * s.ppc[1] * s.ppc[2];
@@ -1057,6 +1092,7 @@ pic_status init_sim(const pic_grid* grid, const pic_species* species, int nspeci
   cudaMemsetAsync(S->dstat, 0, sizeof(StatusWord), S->s);
   if ((st = cuda_check("pic_init")) != PIC_OK) return bail(st);
   S->sp.resize((size_t)nspecies);
+  for (auto& s : S->sp) s.slack = S->slack;
   for (int k = 0; k < nspecies; ++k) {
     if (S->prec == PIC_FP32_CELLOFF) {
       if ((st = setup_tiles(S, S->sp[k])) != PIC_OK) return bail(st);

@@ -37,6 +37,8 @@ constexpr int kChunk = kThreads * kPPT;      // 1024
 constexpr int kQCap = 320;                   // crossing queue entries
 constexpr uint32_t kHoleCell = 0xFFFFFFFFu;  // cell word of an empty slot
 constexpr long long kWaitLimit = 2000000000ll;  // mbarrier waits give up after 2 s
+constexpr int kSliceChunks = 8;                // chunks per work item of a heavy tile
+constexpr int kDensePerCell = 32;              // particles per cell above which a tile counts as dense
 
 struct TileArgs {
   int nt[3];
@@ -56,6 +58,10 @@ struct TileArgs {
   float j3f;            // q / dV (2D3V out-of-plane current per unit v3 and time share)
   float e0[3], b0[3];
   int* status;
+  const int* nslice;    // [ntiles] slices of each tile (nullptr: one work item per tile)
+  const int2* extra;    // (tile, slice) of the work items after the first ntiles
+  const int* nextra;    // entries of `extra`
+  int extra_cap;
   int shift_x;          // moving window: this step ends with a one-cell shift back in x1
   int open_x;           // x1 open: a particle leaving the box in x1 is dropped
   int* lost;            // count of dropped particles
@@ -260,6 +266,53 @@ __device__ inline void acc_flush(float* J, Acc& a) {
   a.cell = -1;
 }
 
+// Adds each active lane's 12 values at its cell, given as the code
+// (x + 1) | (y + 1) << 8 | (z + 1) << 16 of tile-local cell coordinates (a
+// piece may lie in the halo cells -1 and T).  Called by all 32 lanes of the
+// warp.  A shared-memory FP32 add is a compare-and-swap loop that
+// retries once per lane on the same word, so where several lanes hold the same
+// cell (a dense beam puts a whole warp on one cell) their values are first
+// summed across the warp and one lane adds them; lanes alone or in pairs on a
+// cell add directly.
+constexpr int kAggMin = 3;  // lanes on one cell from which the warp sums first
+
+template <int NDIM, int TX, int TY, int TZ>
+__device__ inline void flush_warp(float* J, bool act, int cell, const float (&w)[12]) {
+  using G = Geo<NDIM, TX, TY, TZ>;
+  constexpr unsigned kFull = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const unsigned peers = __match_any_sync(kFull, act ? cell : -1);
+  const bool big = act && __popc(peers) >= kAggMin;
+  if (act && !big)
+    flush_cell<NDIM, G::JX, G::JY, G::JPL>(J, (cell & 255) - 1, ((cell >> 8) & 255) - 1, ((cell >> 16) & 255) - 1, w);
+  unsigned lead = __ballot_sync(kFull, big && (__ffs(peers) - 1) == lane);
+  while (lead) {  // one round per crowded cell
+    const int L = __ffs(lead) - 1;
+    lead &= lead - 1;
+    const int c = __shfl_sync(kFull, cell, L);
+    const bool mine = big && cell == c;
+    float v[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) v[k] = mine ? w[k] : 0.f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+      for (int k = 0; k < (NDIM == 3 ? 12 : 8); ++k) v[k] += __shfl_xor_sync(kFull, v[k], o);
+    }
+    if (lane == L)
+      flush_cell<NDIM, G::JX, G::JY, G::JPL>(J, (c & 255) - 1, ((c >> 8) & 255) - 1, ((c >> 16) & 255) - 1, v);
+  }
+}
+
+// acc_flush for a whole warp (all lanes call it)
+template <int NDIM, int TX, int TY, int TZ>
+__device__ inline void acc_flush_warp(float* J, Acc& a) {
+  flush_warp<NDIM, TX, TY, TZ>(J, a.cell >= 0, a.cell + 0x010101, a.w);
+#pragma unroll
+  for (int k = 0; k < 12; ++k) a.w[k] = 0.f;
+  a.cell = -1;
+}
+
 // Gather + push + move of one particle, deposit of its first in-cell piece into
 // the accumulator, crossing pieces queued.  Rewrites p in the coordinates of
 // the tile it ends in; returns its key: new cell (stayers) or NC + direction.
@@ -409,28 +462,44 @@ __device__ inline int push_one(const float* F, float* J, const TileArgs& A, P& p
   return dir == DIR_STAY ? gx + TX * (gy + TY * gz) : G::NC;
 }
 
-// Deposit the queued crossing pieces (all but the first of each path).
-template <int NDIM, int TX, int TY, int TZ>
+// Deposit the queued crossing pieces (all but the first of each path).  All
+// threads of the block call it, one entry per thread and round.  AGG (dense
+// tiles, where the paths queued together share their cells): the second piece
+// of each path goes through flush_warp; otherwise every piece is added
+// directly.
+template <int NDIM, int TX, int TY, int TZ, bool AGG = false>
 __device__ inline void drain_queue(float* J, const TileArgs& A, const float* Q, int n) {
   using G = Geo<NDIM, TX, TY, TZ>;
-  for (int q = threadIdx.x; q < n; q += kThreads) {
-    const float* e = Q + q * G::QW;
-    const int c = __float_as_int(e[0]);
-    const int lx = c & 255, ly = (c >> 8) & 255, lz = (c >> 16) & 255;
-    const float ax = e[1], ay = e[2], bx = e[3], by = e[4];
-    const float az = NDIM == 3 ? e[5] : 0.f, bz = NDIM == 3 ? e[6] : 0.f;
-    const float v3 = NDIM == 3 ? 0.f : e[5];
-    walk<NDIM>(ax, ay, az, bx, by, bz,
-               [&](int k, int ox, int oy, int oz, float sx0, float sy0, float sz0, float sx1, float sy1, float sz1,
-                   float frac) {
-                 if (k == 0) return;
-                 float w[12];
-                 seg_weights<NDIM>(A, sx0, sy0, sz0, sx1, sy1, sz1, v3 * frac, w);
-                 flush_cell<NDIM, G::JX, G::JY, G::JPL>(J, lx + ox, ly + oy, lz + oz, w);
-               });
+  for (int q0 = 0; q0 < n; q0 += kThreads) {
+    const int q = q0 + threadIdx.x;
+    float w1[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) w1[k] = 0.f;
+    int c1 = -1;
+    if (q < n) {
+      const float* e = Q + q * G::QW;
+      const int c = __float_as_int(e[0]);
+      const int lx = c & 255, ly = (c >> 8) & 255, lz = (c >> 16) & 255;
+      const float ax = e[1], ay = e[2], bx = e[3], by = e[4];
+      const float az = NDIM == 3 ? e[5] : 0.f, bz = NDIM == 3 ? e[6] : 0.f;
+      const float v3 = NDIM == 3 ? 0.f : e[5];
+      walk<NDIM>(ax, ay, az, bx, by, bz,
+                 [&](int k, int ox, int oy, int oz, float sx0, float sy0, float sz0, float sx1, float sy1, float sz1,
+                     float frac) {
+                   if (k == 0) return;
+                   if (AGG && k == 1) {
+                     seg_weights<NDIM>(A, sx0, sy0, sz0, sx1, sy1, sz1, v3 * frac, w1);
+                     c1 = (lx + ox + 1) | ((ly + oy + 1) << 8) | ((lz + oz + 1) << 16);
+                     return;
+                   }
+                   float w[12];
+                   seg_weights<NDIM>(A, sx0, sy0, sz0, sx1, sy1, sz1, v3 * frac, w);
+                   flush_cell<NDIM, G::JX, G::JY, G::JPL>(J, lx + ox, ly + oy, lz + oz, w);
+                 });
+    }
+    if (AGG) flush_warp<NDIM, TX, TY, TZ>(J, c1 >= 0, c1, w1);
   }
 }
-
 
 __device__ inline void spill_put(const TileArgs& A, int tile, const P& q) {
   atomicOr(A.status, ST_SPILL);
@@ -532,7 +601,7 @@ __device__ inline void store_leaver(const TileArgs& A, int tix, int tiy, int tiz
 template <int NDIM, int TX, int TY, int TZ, int PPT = kPPT>
 __device__ inline void sort_and_store(const TileArgs& A, int t, int tix, int tiy, int tiz, long long base, int room,
                                       P (&pp)[PPT], int (&key)[PPT], int nvalid, int& ws, int* hist, int* misc,
-                                      const Nbr* nb = nullptr) {
+                                      const Nbr* nb = nullptr, int* stay_ctr = nullptr) {
   using G = Geo<NDIM, TX, TY, TZ>;
   const int tid = threadIdx.x;
   __syncthreads();  // previous chunk's ranks read
@@ -592,12 +661,17 @@ __device__ inline void sort_and_store(const TileArgs& A, int t, int tix, int tiy
     for (int r = 0; r < PER; ++r) {
       const int k = tid * PER + r;
       if (k < G::NK) hist[k] = pre;
-      if (k == G::NC) misc[6] = pre;  // stayers in this chunk (hist[NC] moves during ranking)
+      if (k == G::NC) {
+        misc[6] = pre;  // stayers in this chunk (hist[NC] moves during ranking)
+        // a tile split over several blocks reserves its chunk's output slots
+        if (stay_ctr) misc[4] = atomicAdd(stay_ctr, pre);
+      }
       pre += v[r];
     }
   }
   __syncthreads();
   const int nst = misc[6];
+  const int wsb = stay_ctr ? misc[4] : ws;
   // rank within key (a run of equal keys takes one atomic) and write; every
   // index into pp/key is a compile-time constant, so the chunk stays in
   // registers
@@ -616,7 +690,7 @@ __device__ inline void sort_and_store(const TileArgs& A, int t, int tix, int tiy
           rs = r;
         }
         if (k < G::NC) {
-          const int pos = ws + p0 + (r - rs);
+          const int pos = wsb + p0 + (r - rs);
           if (pos < room)
             store_particle<NDIM>(A.out.p, base + pos, pp[r]);
           else
@@ -684,15 +758,16 @@ __device__ inline void compact_and_store(const TileArgs& A, int t, int tix, int 
 // up (the block then stops).
 template <int NDIM, int TX, int TY, int TZ, bool SORT>
 __device__ inline bool sort_tile(const TileArgs& A, const CUtensorMap* fmap, const CUtensorMap* jmap, int t,
-                                 unsigned char* smem, uint32_t& phase) {
+                                 int slice, unsigned char* smem, uint32_t& phase) {
   using G = Geo<NDIM, TX, TY, TZ>;
   float* F = reinterpret_cast<float*>(smem + G::FOFF);
   float* J = reinterpret_cast<float*>(smem + G::JOFF);
   int* hist = reinterpret_cast<int*>(smem + G::HOFF);
   float* Q = reinterpret_cast<float*>(smem + G::QOFF);
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + G::MOFF);
-  // misc: [0] tile [1] queue count [2] table entry [5] queue-count snapshot
-  // [6] stayers of the chunk [7] chunk total [8..15] scan
+  // misc: [0] tile [1] queue count [2] table entry or slice [4] stayer base of
+  // the chunk (sliced tile) [5] queue-count snapshot [6] stayers of the chunk
+  // [7] chunk total [8..15] scan
   int* misc = reinterpret_cast<int*>(smem + G::MOFF + 16);
   Nbr* nb = reinterpret_cast<Nbr*>(smem + G::NOFF);
   const int tid = threadIdx.x;
@@ -710,10 +785,22 @@ __device__ inline bool sort_tile(const TileArgs& A, const CUtensorMap* fmap, con
   const long long base = A.base[t];
   const int cap = A.cap[t];
   const int res = A.res[t];
-  const int nstay = A.in.stay[t];
+  const int room = cap - res;  // stayer slots of the output region
+  int nstay = A.in.stay[t];
+  nstay = nstay < room ? nstay : room;  // a sliced tile's count includes what it spilled
   int ninc = A.in.inc[t];
   ninc = ninc < res ? ninc : res;
-  const int room = cap - res;  // stayer slots of the output region
+  // a heavy tile is split into slices of kSliceChunks chunks (separate work
+  // items); their stayers reserve output slots with an atomic per chunk
+  const int nslices = A.nslice ? A.nslice[t] : 1;
+  int* stay_ctr = (SORT && nslices > 1) ? A.out.stay + t : nullptr;
+  // A dense tile (a beam: many lanes of a warp on one cell) takes one particle
+  // per thread and pass, so that a pass queues at most kThreads crossing paths
+  // and the queue never overflows; its current is summed across each warp
+  // before the shared-memory adds.
+  const bool dense = nstay + ninc > kDensePerCell * G::NC;
+  const int per = dense ? 1 : kPPT;  // particles per thread and chunk
+  const int csz = kThreads * per;
   const bool ok = mbar_wait_bounded(bar, phase, kWaitLimit);
   if (__syncthreads_or(!ok)) {  // every thread takes the same decision
     if (tid == 0) atomicOr(A.status, ST_TIMEOUT);
@@ -724,13 +811,23 @@ __device__ inline bool sort_tile(const TileArgs& A, const CUtensorMap* fmap, con
 
   int ws = 0;
   // chunks over the stayers (front, 16-byte aligned) then the arrivals (back)
-  const int nchunk_s = (nstay + kChunk - 1) / kChunk;
-  const int nchunk_i = (ninc + kChunk - 1) / kChunk;
-  for (int ch = 0; ch < nchunk_s + nchunk_i; ++ch) {
+  const int nchunk_s = (nstay + csz - 1) / csz;
+  const int nchunk_i = (ninc + csz - 1) / csz;
+  const int spc = kSliceChunks * (kPPT / per);  // chunks per slice (a slice is kSliceChunks * kChunk particles)
+  const int ch_end = nslices > 1 ? min(nchunk_s + nchunk_i, (slice + 1) * spc) : nchunk_s + nchunk_i;
+  for (int ch = nslices > 1 ? slice * spc : 0; ch < ch_end; ++ch) {
     P pp[kPPT];
     int key[kPPT];
     int nvalid;
-    if (ch < nchunk_s) {
+    if (ch < nchunk_s && dense) {
+      const int first = ch * csz + tid;
+      nvalid = first < nstay ? 1 : 0;
+      if (nvalid) {
+        const long long s = base + first;
+        pp[0] = P{A.in.p.cell[s], A.in.p.o[0][s], A.in.p.o[1][s], NDIM == 3 ? A.in.p.o[2][s] : 0.f,
+                  A.in.p.u[0][s], A.in.p.u[1][s], A.in.p.u[2][s], A.in.p.id ? A.in.p.id[s] : 0};
+      }
+    } else if (ch < nchunk_s) {
       const int first = ch * kChunk + tid * kPPT;
       nvalid = nstay - first;
       nvalid = nvalid < 0 ? 0 : (nvalid > kPPT ? kPPT : nvalid);
@@ -752,9 +849,9 @@ __device__ inline bool sort_tile(const TileArgs& A, const CUtensorMap* fmap, con
         pp[3] = P{cl.w, q0.w, q1.w, q2.w, v0.w, v1.w, v2.w, idv.w};
       }
     } else {
-      const int first = (ch - nchunk_s) * kChunk + tid * kPPT;
+      const int first = (ch - nchunk_s) * csz + tid * per;
       nvalid = ninc - first;
-      nvalid = nvalid < 0 ? 0 : (nvalid > kPPT ? kPPT : nvalid);
+      nvalid = nvalid < 0 ? 0 : (nvalid > per ? per : nvalid);
 #pragma unroll
       for (int r = 0; r < kPPT; ++r) {
         if (r < nvalid) {
@@ -772,17 +869,24 @@ __device__ inline bool sort_tile(const TileArgs& A, const CUtensorMap* fmap, con
 #pragma unroll
       for (int r = 0; r < kPPT; ++r)
         key[r] = r < nvalid ? push_one<NDIM, TX, TY, TZ>(F, J, A, pp[r], acc, Q, misc + 1)
-                                                    : Geo<NDIM, TX, TY, TZ>::NK;
-      acc_flush<NDIM, TX, TY, TZ>(J, acc);
+                            : Geo<NDIM, TX, TY, TZ>::NK;
+      if (dense)
+        acc_flush_warp<NDIM, TX, TY, TZ>(J, acc);
+      else
+        acc_flush<NDIM, TX, TY, TZ>(J, acc);
     }
     if constexpr (SORT)
-      sort_and_store<NDIM, TX, TY, TZ>(A, t, tix, tiy, tiz, base, room, pp, key, nvalid, ws, hist, misc, nb);
+      sort_and_store<NDIM, TX, TY, TZ>(A, t, tix, tiy, tiz, base, room, pp, key, nvalid, ws, hist, misc, nb,
+                                       stay_ctr);
     else
       compact_and_store<NDIM, TX, TY, TZ>(A, t, tix, tiy, tiz, base, room, pp, key, nvalid, ws, misc, nb);
     __syncthreads();
     const int nq = misc[5];  // the same value in every thread
-    if (nq > kQCap / 2) {
-      drain_queue<NDIM, TX, TY, TZ>(J, A, Q, nq < kQCap ? nq : kQCap);
+    if (nq > (dense ? kQCap - kThreads : kQCap / 2)) {
+      if (dense)
+        drain_queue<NDIM, TX, TY, TZ, true>(J, A, Q, nq < kQCap ? nq : kQCap);
+      else
+        drain_queue<NDIM, TX, TY, TZ>(J, A, Q, nq < kQCap ? nq : kQCap);
       __syncthreads();
       if (tid == 0) misc[1] = 0;
       __syncthreads();  // the reset lands before the next chunk queues anything
@@ -791,9 +895,12 @@ __device__ inline bool sort_tile(const TileArgs& A, const CUtensorMap* fmap, con
   __syncthreads();
   {
     const int nq = misc[1];
-    if (nq > 0) drain_queue<NDIM, TX, TY, TZ>(J, A, Q, nq < kQCap ? nq : kQCap);
+    if (nq > 0 && dense)
+      drain_queue<NDIM, TX, TY, TZ, true>(J, A, Q, nq < kQCap ? nq : kQCap);
+    else if (nq > 0)
+      drain_queue<NDIM, TX, TY, TZ>(J, A, Q, nq < kQCap ? nq : kQCap);
   }
-  if (tid == 0) A.out.stay[t] = ws < room ? ws : room;
+  if (tid == 0 && !stay_ctr) A.out.stay[t] = ws < room ? ws : room;
   // flush the current tile: every thread orders its shared atomics before the
   // async proxy reads them; one thread issues the TMA reduce-add and waits
   // until the TMA has read the tile before the next tile reuses it
@@ -823,16 +930,36 @@ __global__ void __launch_bounds__(kThreads, MINB)
     fence_barrier_init();
   }
   uint32_t phase = 0;
+  // work items: slice 0 of every tile, then the further slices of heavy tiles
+  int nextra = 0;
+  if (A.nslice) {
+    nextra = *A.nextra;
+    nextra = nextra < A.extra_cap ? nextra : A.extra_cap;
+  }
   for (;;) {
     __syncthreads();
     if (tid == 0) {
-      misc[0] = atomicAdd(A.work, 1);
+      const int w = atomicAdd(A.work, 1);
+      int t = w, slice = 0;
+      if (w >= A.ntiles) {
+        t = A.ntiles;  // no work left
+        for (int e = w - A.ntiles; e < nextra; e = atomicAdd(A.work, 1) - A.ntiles) {
+          const int2 x = A.extra[e];
+          if (x.x >= 0) {  // entries of a tile whose reservation did not fit are -1
+            t = x.x;
+            slice = x.y;
+            break;
+          }
+        }
+      }
+      misc[0] = t;
+      misc[2] = slice;
       misc[1] = 0;
     }
     __syncthreads();
     const int t = misc[0];
     if (t >= A.ntiles) break;
-    if (!sort_tile<NDIM, TX, TY, TZ, SORT>(A, &fmap, &jmap, t, smem, phase)) return;
+    if (!sort_tile<NDIM, TX, TY, TZ, SORT>(A, &fmap, &jmap, t, misc[2], smem, phase)) return;
   }
 }
 
@@ -885,7 +1012,8 @@ __global__ void __launch_bounds__(kThreads, MINB) k_tile_push_batch(const BatchT
     const int w = misc[0];
     if (w >= total) break;
     const int s = misc[2];
-    if (!sort_tile<NDIM, TX, TY, TZ, true>(B.args[s], B.fmaps + s, B.jmaps + s, w - B.tile0[s], smem, phase)) return;
+    if (!sort_tile<NDIM, TX, TY, TZ, true>(B.args[s], B.fmaps + s, B.jmaps + s, w - B.tile0[s], 0, smem, phase))
+      return;
   }
 }
 
@@ -1265,7 +1393,8 @@ __device__ inline int dest_tile(const Tiles& tg, int t, uint32_t cell) {
 
 // slot of the k-th particle of tile t: stayers from the front, arrivals at the back
 __device__ inline long long tile_slot(const Tiles& tg, const TileSide& in, int t, int k, int& n) {
-  const int ns = in.stay[t];
+  int ns = in.stay[t];
+  ns = ns < tg.cap[t] - tg.res[t] ? ns : tg.cap[t] - tg.res[t];  // a sliced tile counts its overflow too
   int ni = in.inc[t];
   ni = ni < tg.res[t] ? ni : tg.res[t];
   n = ns + ni;
@@ -1733,6 +1862,10 @@ TileArgs make_args(const PushConst& C, const Tiles& tg, const TileSide& in, cons
   }
   A.j3f = (float)(C.q / C.dvol);
   A.status = status;
+  A.nslice = nullptr;
+  A.extra = nullptr;
+  A.nextra = nullptr;
+  A.extra_cap = 0;
   A.shift_x = 0;
   A.open_x = 0;
   A.lost = nullptr;
@@ -1807,13 +1940,57 @@ bool tiled_push_batch(int ndim, const int T[3], const void* args, const CUtensor
   return false;
 }
 
-void tiled_push(const Layout& L, const PushConst& C, const Tiles& tg, const TileSide& in, const TileSide& out,
+// Slices of every tile (one per kSliceChunks chunks of its particles); the
+// slices after the first are appended to the extra list.  The list is sized
+// so that every tile fits (see slice_list_capacity); a tile whose reservation
+// would not fit all the same stays whole and marks its entries -1.
+__global__ void k_slices(Tiles tg, TileSide in, int* nslice, int2* extra, int* nextra, int cap) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= tg.ntiles) return;
+  int n;
+  tile_slot(tg, in, t, 0, n);
+  int ns = in.stay[t];
+  const int room = tg.cap[t] - tg.res[t];
+  ns = ns < room ? ns : room;
+  const int chunks = (ns + kChunk - 1) / kChunk + (n - ns + kChunk - 1) / kChunk;
+  int s = (chunks + kSliceChunks - 1) / kSliceChunks;
+  s = s > 1 ? s : 1;
+  if (s > 1) {
+    const int e0 = atomicAdd(nextra, s - 1);
+    const bool fits = e0 + (s - 1) <= cap;
+    for (int k = 1; k < s && e0 + k - 1 < cap; ++k) extra[e0 + k - 1] = fits ? make_int2(t, k) : make_int2(-1, 0);
+    if (!fits) s = 1;
+  }
+  nslice[t] = s;
+}
+
+// A tile region of c slots holds at most c / kChunk + 2 chunks (stayers and
+// arrivals are chunked apart), so it adds at most c / (kChunk kSliceChunks) +
+// 1/8 slices to the list.
+long long slice_list_capacity(long long slots, int ntiles) {
+  return slots / (kChunk * kSliceChunks) + ntiles / 4 + 64;
+}
+
+int tiled_push(const Layout& L, const PushConst& C, const Tiles& tg, const TileSide& in, const TileSide& out,
                 Flat32 spill, int* spill_count, long long spill_cap, int grid, int* work, const CUtensorMap* fmap,
-                const CUtensorMap* jmap, int* status, bool stream, int minb, int shift_x, int* lost, cudaStream_t s) {
+                const CUtensorMap* jmap, int* status, bool stream, int minb, int shift_x, int* lost,
+                const SliceScratch* slices, cudaStream_t s) {
   TileArgs A = make_args(C, tg, in, out, spill, spill_count, spill_cap, work, status);
   A.shift_x = shift_x;
   A.open_x = L.open_x;
   A.lost = lost;
+  int launches = 1;
+  if (slices && slices->extra && !stream && !tg.small) {  // heavy tiles are split over several blocks
+    cudaMemsetAsync(slices->nextra, 0, sizeof(int), s);
+    cudaMemsetAsync(out.stay, 0, sizeof(int) * (size_t)tg.ntiles, s);
+    k_slices<<<(tg.ntiles + 255) / 256, 256, 0, s>>>(tg, in, slices->nslice, slices->extra, slices->nextra,
+                                                     slices->cap);
+    A.nslice = slices->nslice;
+    A.extra = slices->extra;
+    A.nextra = slices->nextra;
+    A.extra_cap = slices->cap;
+    launches += 1;
+  }
   cudaMemsetAsync(work, 0, sizeof(int), s);
   cudaMemsetAsync(out.inc, 0, sizeof(int) * (size_t)tg.ntiles, s);
   const int* T = tg.T;
@@ -1821,7 +1998,7 @@ void tiled_push(const Layout& L, const PushConst& C, const Tiles& tg, const Tile
 #define X(N, A_, B_, C_)                                \
   if (shape_is(tg.ndim, T, N, A_, B_, C_)) {            \
     launch_push_s<N, A_, B_, C_>(fmap, jmap, A, grid, s); \
-    return;                                             \
+    return launches;                                    \
   }
     PICGB_SMALL_SHAPES(X)
 #undef X
@@ -1836,10 +2013,11 @@ void tiled_push(const Layout& L, const PushConst& C, const Tiles& tg, const Tile
     else                                                                    \
       stream ? launch_push<N, A_, B_, C_, 3, false>(fmap, jmap, A, grid, s) \
              : launch_push<N, A_, B_, C_, 3, true>(fmap, jmap, A, grid, s); \
-    return;                                                                 \
+    return launches;                                                        \
   }
   PICGB_TILE_SHAPES(X)
 #undef X
+  return 0;
 }
 
 void tiled_inject(const PushConst& C, const Tiles& tg, const TileSide& out, Flat32 spill, int* spill_count,

@@ -95,12 +95,26 @@ struct TileSide {
   int* inc;
 };
 
+// Work items of the tile kernel beyond one per tile: a tile with more than
+// kSliceChunks chunks of particles is split into slices that separate blocks
+// take.  nslice[ntiles] counts each tile's slices; extra[cap] lists the
+// (tile, slice >= 1) items, nextra[0] of them.
+struct SliceScratch {
+  int* nslice;
+  int2* extra;
+  int* nextra;
+  int cap;
+};
+// capacity of the extra list for a particle store of `slots` slots in ntiles regions
+long long slice_list_capacity(long long slots, int ntiles);
+
 // stream = true: the step between re-sorts (stayers keep the order they were
-// read in, compacted); false: the step that counting-sorts every tile by cell
-void tiled_push(const Layout& L, const PushConst& C, const Tiles& tg, const TileSide& in, const TileSide& out,
+// read in, compacted); false: the step that counting-sorts every tile by cell.
+// Returns the number of kernels it launched.
+int tiled_push(const Layout& L, const PushConst& C, const Tiles& tg, const TileSide& in, const TileSide& out,
                 Flat32 spill, int* spill_count, long long spill_cap, int grid, int* work, const CUtensorMap* fmap,
                 const CUtensorMap* jmap, int* status, bool stream, int minb, int shift_x, int* lost,
-                cudaStream_t s);
+                const SliceScratch* slices, cudaStream_t s);
 // moving window: `count` fresh particles of the front column appended to the
 // last tile column of side `out` (global particle indices first, ...)
 void tiled_inject(const PushConst& C, const Tiles& tg, const TileSide& out, Flat32 spill, int* spill_count,

@@ -115,8 +115,8 @@ typedef struct {
                                tile by cell; the steps between update particles in
                                place (0 = default 1: sort every step) */
   int ctas_per_sm;          /* PIC_FP32_CELLOFF: thread blocks per SM the general tile
-                               kernel is built for: 3 (80 registers per thread) or 2
-                               (128); 0 = default 3 */
+                               kernel is built for: 4 (64 registers per thread) or 2
+                               (128); 0 = default 4 */
   int move_window;          /* 1: the window moves at c in +x1 (thesis: dynamic simulation
                                space, if_move): x1 is open -- fields beyond it are 0, particles
                                leaving through it are dropped -- and whenever c t runs a full
@@ -317,7 +317,7 @@ pic_status pic_batch_destroy(pic_batch* B);
  * Chooses the launch parameters of the FP32 particle step by running them: the
  * tile shape (3D 8x8x8, 16x8x4, 8x4x4, 4x4x4, 4x4x2; 2D 32x16, 16x16, 8x8,
  * 16x8, 8x4 -- those dividing every grid), the thread blocks per SM of the
- * general tile kernel (3 or 2: its particles per block per SM), and the sort
+ * general tile kernel (4 or 2: its particles in flight per SM), and the sort
  * period (1 or 4).  Each candidate is set up from the same grid/species,
  * stepped `warmup` steps, then `steps` steps are timed with CUDA events on
  * `stream`; the candidate is freed before the next.  The thesis tunes nothing
@@ -338,7 +338,7 @@ pic_status pic_autotune(const pic_grid* grid, const pic_species* species, int ns
                         int max_tried, int* n_tried);
 
 /* The same for a batch (pic_batch_init arguments): general tile shapes that
- * divide every member's grid, 3 or 2 blocks per SM, sort period 1; each
+ * divide every member's grid, 4 or 2 blocks per SM, sort period 1; each
  * candidate is a whole batch. */
 pic_status pic_batch_autotune(int nsims, const pic_grid* grids, const pic_species* species, int nspecies,
                               const pic_allocator* alloc, void* stream, int warmup, int steps, pic_tune_choice* best,

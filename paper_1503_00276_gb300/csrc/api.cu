@@ -149,7 +149,7 @@ struct pic_sim {
   int T[3] = {1, 1, 1};
   double slack = 0.25;
   int sort_period = 1;
-  int minb = 3;  // CTAs per SM the general tile kernel is built for (2 or 3)
+  int minb = 4;  // CTAs per SM the general tile kernel is built for (2 or 4)
   bool timing = false;
   double t_ms[kTimingSlots] = {0, 0, 0, 0, 0};
   long long t_n[kTimingSlots] = {0, 0, 0, 0, 0};
@@ -1047,12 +1047,12 @@ pic_status init_sim(const pic_grid* grid, const pic_species* species, int nspeci
     int ctas = grid->ctas_per_sm;
     if (ctas == 0)
       if (const char* e = getenv("PICGB_TILE_CTAS")) ctas = atoi(e);
-    if (ctas != 0 && ctas != 2 && ctas != 3) {
-      set_error("ctas_per_sm must be 0 (default), 2 or 3");
+    if (ctas != 0 && ctas != 2 && ctas != 4) {
+      set_error("ctas_per_sm must be 0 (default), 2 or 4");
       delete S;
       return PIC_EINVAL;
     }
-    S->minb = ctas == 2 ? 2 : 3;
+    S->minb = ctas == 2 ? 2 : 4;
     if (tiled_push_smem_bytes(S->ndim, S->T) < 0) {
       set_error("unsupported tile shape (3D: 4x4x4, 4x4x2, 8x4x4, 8x8x8, 16x8x4; 2D: 8x4, 8x8, 16x8, 16x16, 32x16)");
       delete S;
@@ -1481,7 +1481,7 @@ struct pic_batch {
   StatusWord* d_stat = nullptr;  // one per simulation
   StatusWord* h_stat = nullptr;  // pinned mirror
   int grid = 0;
-  int minb = 3;
+  int minb = 4;
   bool use_graph = true;
   bool dirty = true;  // tables / graphs must be rebuilt before the next step
   cudaGraphExec_t exec[2] = {nullptr, nullptr};
@@ -1629,7 +1629,7 @@ pic_status pic_batch_init(int nsims, const pic_grid* grids, const pic_species* s
     return PIC_ECUDA;
   }
   B->ndim = ndim;
-  B->minb = grids[0].ctas_per_sm == 2 ? 2 : 3;
+  B->minb = grids[0].ctas_per_sm == 2 ? 2 : 4;
   for (int d = 0; d < 3; ++d) B->T[d] = T[d];
   if (alloc && alloc->alloc) {
     B->al.user = *alloc;
@@ -1817,7 +1817,7 @@ std::vector<TuneCand> tune_candidates(int nsims, const pic_grid* grids, bool bat
     if (!fits) continue;
     const bool general = k < ngen;
     if (batch && !general) continue;
-    for (int ctas : {3, 2}) {
+    for (int ctas : {4, 2}) {
       if (!general && ctas == 2) continue;  // the small-tile kernel has one build
       for (int sort : {1, 4}) {
         if ((batch || !general) && sort != 1) continue;

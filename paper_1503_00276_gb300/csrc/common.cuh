@@ -169,6 +169,10 @@ __device__ inline void bulk_s2g(void* dst, const void* src, uint32_t bytes) {
                : "memory");
 }
 
+// L2 prefetch of `bytes` bytes at `src` (both multiples of 16)
+__device__ inline void bulk_prefetch_l2(const void* src, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
 __device__ inline void tma_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
 __device__ inline void tma_wait_read1() { asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory"); }
 __device__ inline void tma_wait_read0() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }

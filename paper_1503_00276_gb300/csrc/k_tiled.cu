@@ -15,7 +15,7 @@
 //     in-cell piece of consecutive same-cell particles in registers and flushes
 //     once per cell; pieces after a face crossing (a few % of particles) are
 //     queued in shared memory and deposited by full warps;
-//   * each chunk of 1024 advanced particles is counting-sorted by new cell in
+//   * each chunk of 512 advanced particles is counting-sorted by new cell in
 //     shared memory (keys only -- the particles stay in registers) and written
 //     to the front of the tile's region on the other store side; particles that
 //     left the tile are appended, with one global atomic each, to the back of
@@ -32,9 +32,9 @@ namespace picgb {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kPPT = 4;                      // consecutive particles per thread per chunk
-constexpr int kChunk = kThreads * kPPT;      // 1024
-constexpr int kQCap = 320;                   // crossing queue entries
+constexpr int kPPT = 2;                      // consecutive particles per thread per chunk
+constexpr int kChunk = kThreads * kPPT;      // 512
+constexpr int kQCap = 192;                   // crossing queue entries
 constexpr uint32_t kHoleCell = 0xFFFFFFFFu;  // cell word of an empty slot
 constexpr long long kWaitLimit = 2000000000ll;  // mbarrier waits give up after 2 s
 constexpr int kSliceChunks = 8;                // chunks per work item of a heavy tile
@@ -98,6 +98,25 @@ struct P {
 };
 
 __device__ inline float lerp(float a, float b, float w) { return fmaf(w, b - a, a); }
+
+// N consecutive 32-bit words from a 4N-byte aligned address, one vector load
+template <typename T, int N>
+__device__ inline void load_vec(const T* p, T (&v)[N]) {
+  static_assert(sizeof(T) == 4 && (N == 1 || N == 2 || N == 4), "32-bit words, 1, 2 or 4 of them");
+  if constexpr (N == 4) {
+    const uint4 w = *reinterpret_cast<const uint4*>(p);
+    v[0] = __builtin_bit_cast(T, w.x);
+    v[1] = __builtin_bit_cast(T, w.y);
+    v[2] = __builtin_bit_cast(T, w.z);
+    v[3] = __builtin_bit_cast(T, w.w);
+  } else if constexpr (N == 2) {
+    const uint2 w = *reinterpret_cast<const uint2*>(p);
+    v[0] = __builtin_bit_cast(T, w.x);
+    v[1] = __builtin_bit_cast(T, w.y);
+  } else {
+    v[0] = *p;
+  }
+}
 
 // Trilinear (bilinear in 2D) weighting of one staged component.
 template <int NDIM, int FX, int FY>
@@ -704,6 +723,116 @@ __device__ inline void sort_and_store(const TileArgs& A, int t, int tix, int tiy
   ws += nst;
 }
 
+// The counting sort of the general kernel with three block barriers per chunk
+// (sort_and_store takes six).  Only stayers are ranked (leavers go to their new
+// tile through store_leaver), so the histogram has NC bins.  It is kept in two
+// buffers used by alternate chunks, so one is cleared while the other is in
+// use, and packed two 16-bit counts per word (a chunk holds at most kChunk <
+// 65536 particles).  Every thread adds up the earlier warps' totals itself
+// instead of one thread scanning them.  Returns the crossing-queue count
+// snapshot taken when every push of the chunk was done (misc[5]).
+template <int NDIM, int TX, int TY, int TZ>
+__device__ inline int sort_and_store_lean(const TileArgs& A, int t, int tix, int tiy, int tiz, long long base,
+                                          int room, P (&pp)[kPPT], int (&key)[kPPT], int nvalid, int& ws,
+                                          uint32_t* h2, uint32_t* h2next, int* misc, const Nbr* nb,
+                                          int* stay_ctr) {
+  using G = Geo<NDIM, TX, TY, TZ>;
+  static_assert(kChunk < 65536, "16-bit histogram counts");
+  constexpr int PER = ((G::NC + kThreads - 1) / kThreads + 1) & ~1;  // bins per thread, even
+  static_assert(PER * kThreads >= G::NC, "every bin owned by a thread");
+  constexpr int NW = G::NC / 2;  // words per histogram buffer
+  static_assert(G::NC % 2 == 0 && G::NC * 4 <= G::QOFF - G::HOFF, "two packed buffers in the histogram space");
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  {
+    int hk = -1, hc = 0;
+#pragma unroll
+    for (int r = 0; r < kPPT; ++r) {
+      if (r < nvalid && key[r] < G::NC) {
+        if (key[r] != hk) {
+          if (hk >= 0) atomicAdd(&h2[hk >> 1], (uint32_t)hc << (16 * (hk & 1)));
+          hk = key[r];
+          hc = 0;
+        }
+        ++hc;
+      }
+    }
+    if (hk >= 0) atomicAdd(&h2[hk >> 1], (uint32_t)hc << (16 * (hk & 1)));
+  }
+  __syncthreads();  // every push and count of the chunk is done
+  if (tid == 0) misc[5] = misc[1];
+  uint32_t v[PER];
+  int run = 0;
+#pragma unroll
+  for (int r = 0; r < PER; r += 2) {
+    const int k = tid * PER + r;
+    const uint32_t w = k < G::NC ? h2[k >> 1] : 0u;
+    v[r] = w & 0xFFFFu;
+    v[r + 1] = w >> 16;
+    run += (int)(v[r] + v[r + 1]);
+  }
+  int x = run;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) misc[8 + warp] = x;
+  // the other buffer's last use (the previous chunk's ranking) ended before the barrier above
+  for (int k = tid; k < NW; k += kThreads) h2next[k] = 0u;
+  __syncthreads();
+  int pre = x - run, nst = 0;
+#pragma unroll
+  for (int w = 0; w < kThreads / 32; ++w) {
+    const int c = misc[8 + w];
+    pre += w < warp ? c : 0;
+    nst += c;  // stayers of the chunk
+  }
+#pragma unroll
+  for (int r = 0; r < PER; r += 2) {
+    const int k = tid * PER + r;
+    if (k < G::NC) {
+      const uint32_t lo = (uint32_t)pre;
+      pre += (int)v[r];
+      h2[k >> 1] = lo | ((uint32_t)pre << 16);
+      pre += (int)v[r + 1];
+    }
+  }
+  // a tile split over several blocks reserves its chunk's output slots
+  if (stay_ctr && tid == 0) misc[4] = atomicAdd(stay_ctr, nst);
+  const int nq = misc[5];
+  __syncthreads();
+  const int wsb = stay_ctr ? misc[4] : ws;
+  {
+    int p0 = 0, rs = 0;
+#pragma unroll
+    for (int r = 0; r < kPPT; ++r) {
+      if (r < nvalid) {
+        const int k = key[r];
+        if (k < G::NC && (r == 0 || key[r > 0 ? r - 1 : 0] != k)) {  // first of a run of equal keys
+          int n = 1;
+#pragma unroll
+          for (int m = r + 1; m < kPPT; ++m)
+            if (m < nvalid && n == m - r && key[m] == k) ++n;
+          const int sh = 16 * (k & 1);
+          p0 = (int)((atomicAdd(&h2[k >> 1], (uint32_t)n << sh) >> sh) & 0xFFFFu);
+          rs = r;
+        }
+        if (k < G::NC) {
+          const int pos = wsb + p0 + (r - rs);
+          if (pos < room)
+            store_particle<NDIM>(A.out.p, base + pos, pp[r]);
+          else
+            spill_put(A, t, pp[r]);
+        } else if (k < G::NK) {
+          store_leaver<NDIM>(A, tix, tiy, tiz, pp[r], nb);
+        }
+      }
+    }
+  }
+  ws += nst;
+  return nq;
+}
+
 // The step between two re-sorts: the chunk's stayers go to the front of the
 // tile's output region in the order they were read (one block scan instead of
 // the counting sort), leavers to their new tile as in sort_and_store.
@@ -781,6 +910,8 @@ __device__ inline bool sort_tile(const TileArgs& A, const CUtensorMap* fmap, con
       tma_load_3d(F, fmap, bar, x0, y0, 0);
   }
   for (int k = tid; k < 3 * G::JPL; k += kThreads) J[k] = 0.f;
+  if (SORT)  // both buffers of sort_and_store_lean's packed histogram
+    for (int k = tid; k < G::NC; k += kThreads) hist[k] = 0;
   load_neighbour(A, tix, tiy, tiz, nb);
   const long long base = A.base[t];
   const int cap = A.cap[t];
@@ -810,6 +941,7 @@ __device__ inline bool sort_tile(const TileArgs& A, const CUtensorMap* fmap, con
   phase ^= 1u;
 
   int ws = 0;
+  int nch = 0;  // chunks done: picks the histogram buffer
   // chunks over the stayers (front, 16-byte aligned) then the arrivals (back)
   const int nchunk_s = (nstay + csz - 1) / csz;
   const int nchunk_i = (ninc + csz - 1) / csz;
@@ -833,20 +965,19 @@ __device__ inline bool sort_tile(const TileArgs& A, const CUtensorMap* fmap, con
       nvalid = nvalid < 0 ? 0 : (nvalid > kPPT ? kPPT : nvalid);
       if (nvalid > 0) {
         const long long s = base + first;
-        const uint4 cl = *reinterpret_cast<const uint4*>(A.in.p.cell + s);
-        const float4 q0 = *reinterpret_cast<const float4*>(A.in.p.o[0] + s);
-        const float4 q1 = *reinterpret_cast<const float4*>(A.in.p.o[1] + s);
-        float4 q2 = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (NDIM == 3) q2 = *reinterpret_cast<const float4*>(A.in.p.o[2] + s);
-        const float4 v0 = *reinterpret_cast<const float4*>(A.in.p.u[0] + s);
-        const float4 v1 = *reinterpret_cast<const float4*>(A.in.p.u[1] + s);
-        const float4 v2 = *reinterpret_cast<const float4*>(A.in.p.u[2] + s);
-        int4 idv = make_int4(0, 0, 0, 0);
-        if (A.in.p.id) idv = *reinterpret_cast<const int4*>(A.in.p.id + s);
-        pp[0] = P{cl.x, q0.x, q1.x, q2.x, v0.x, v1.x, v2.x, idv.x};
-        pp[1] = P{cl.y, q0.y, q1.y, q2.y, v0.y, v1.y, v2.y, idv.y};
-        pp[2] = P{cl.z, q0.z, q1.z, q2.z, v0.z, v1.z, v2.z, idv.z};
-        pp[3] = P{cl.w, q0.w, q1.w, q2.w, v0.w, v1.w, v2.w, idv.w};
+        uint32_t cl[kPPT];
+        float q0[kPPT], q1[kPPT], q2[kPPT] = {}, v0[kPPT], v1[kPPT], v2[kPPT];
+        int idv[kPPT] = {};
+        load_vec(A.in.p.cell + s, cl);
+        load_vec(A.in.p.o[0] + s, q0);
+        load_vec(A.in.p.o[1] + s, q1);
+        if (NDIM == 3) load_vec(A.in.p.o[2] + s, q2);
+        load_vec(A.in.p.u[0] + s, v0);
+        load_vec(A.in.p.u[1] + s, v1);
+        load_vec(A.in.p.u[2] + s, v2);
+        if (A.in.p.id) load_vec(A.in.p.id + s, idv);
+#pragma unroll
+        for (int r = 0; r < kPPT; ++r) pp[r] = P{cl[r], q0[r], q1[r], q2[r], v0[r], v1[r], v2[r], idv[r]};
       }
     } else {
       const int first = (ch - nchunk_s) * csz + tid * per;
@@ -875,14 +1006,19 @@ __device__ inline bool sort_tile(const TileArgs& A, const CUtensorMap* fmap, con
       else
         acc_flush<NDIM, TX, TY, TZ>(J, acc);
     }
-    if constexpr (SORT)
-      sort_and_store<NDIM, TX, TY, TZ>(A, t, tix, tiy, tiz, base, room, pp, key, nvalid, ws, hist, misc, nb,
-                                       stay_ctr);
-    else
+    int nq;  // the same value in every thread
+    if constexpr (SORT) {
+      uint32_t* h2 = reinterpret_cast<uint32_t*>(hist) + (nch & 1) * (G::NC / 2);
+      uint32_t* h2next = reinterpret_cast<uint32_t*>(hist) + ((nch + 1) & 1) * (G::NC / 2);
+      nq = sort_and_store_lean<NDIM, TX, TY, TZ>(A, t, tix, tiy, tiz, base, room, pp, key, nvalid, ws, h2, h2next,
+                                                 misc, nb, stay_ctr);
+    } else {
       compact_and_store<NDIM, TX, TY, TZ>(A, t, tix, tiy, tiz, base, room, pp, key, nvalid, ws, misc, nb);
-    __syncthreads();
-    const int nq = misc[5];  // the same value in every thread
-    if (nq > (dense ? kQCap - kThreads : kQCap / 2)) {
+      __syncthreads();
+      nq = misc[5];
+    }
+    ++nch;
+    if (nq > (dense ? kQCap - kThreads : kQCap / 2)) {  // entries [0, nq) are complete since the snapshot
       if (dense)
         drain_queue<NDIM, TX, TY, TZ, true>(J, A, Q, nq < kQCap ? nq : kQCap);
       else
@@ -1830,7 +1966,7 @@ int tiled_push_grid(int ndim, const int T[3], int ntiles, bool small, int minb) 
   } else {
 #define X(N, A_, B_, C_)                  \
   if (shape_is(ndim, T, N, A_, B_, C_)) \
-    occ = minb == 2 ? occupancy<N, A_, B_, C_, 2>() : occupancy<N, A_, B_, C_, 3>();
+    occ = minb == 2 ? occupancy<N, A_, B_, C_, 2>() : occupancy<N, A_, B_, C_, 4>();
     PICGB_TILE_SHAPES(X)
 #undef X
   }
@@ -1905,7 +2041,7 @@ int tiled_batch_grid(int ndim, const int T[3], int total_tiles, int minb) {
   int occ = 0;
 #define X(N, A_, B_, C_) \
   if (shape_is(ndim, T, N, A_, B_, C_)) \
-    occ = minb == 2 ? occupancy_b<N, A_, B_, C_, 2>() : occupancy_b<N, A_, B_, C_, 3>();
+    occ = minb == 2 ? occupancy_b<N, A_, B_, C_, 2>() : occupancy_b<N, A_, B_, C_, 4>();
   PICGB_TILE_SHAPES(X)
 #undef X
   if (occ < 1) return 0;
@@ -1930,8 +2066,8 @@ bool tiled_push_batch(int ndim, const int T[3], const void* args, const CUtensor
       occupancy_b<N, A_, B_, C_, 2>();                                        \
       k_tile_push_batch<N, A_, B_, C_, 2><<<grid, kThreads, G::SMEM, s>>>(B); \
     } else {                                                                  \
-      occupancy_b<N, A_, B_, C_, 3>();                                        \
-      k_tile_push_batch<N, A_, B_, C_, 3><<<grid, kThreads, G::SMEM, s>>>(B); \
+      occupancy_b<N, A_, B_, C_, 4>();                                        \
+      k_tile_push_batch<N, A_, B_, C_, 4><<<grid, kThreads, G::SMEM, s>>>(B); \
     }                                                                         \
     return true;                                                              \
   }
@@ -2011,8 +2147,8 @@ int tiled_push(const Layout& L, const PushConst& C, const Tiles& tg, const TileS
       stream ? launch_push<N, A_, B_, C_, 2, false>(fmap, jmap, A, grid, s) \
              : launch_push<N, A_, B_, C_, 2, true>(fmap, jmap, A, grid, s); \
     else                                                                    \
-      stream ? launch_push<N, A_, B_, C_, 3, false>(fmap, jmap, A, grid, s) \
-             : launch_push<N, A_, B_, C_, 3, true>(fmap, jmap, A, grid, s); \
+      stream ? launch_push<N, A_, B_, C_, 4, false>(fmap, jmap, A, grid, s) \
+             : launch_push<N, A_, B_, C_, 4, true>(fmap, jmap, A, grid, s); \
     return launches;                                                        \
   }
   PICGB_TILE_SHAPES(X)

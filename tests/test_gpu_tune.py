@@ -49,7 +49,7 @@ def test_batch_autotune_over_members():
         mem.append((g, [workload.Species(ppc=(2, 2, 1), uth=(0.2,) * 3, seed=90 + i)]))
     best, tried = pg.batch_autotune(mem, warmup=1, steps=2)
     assert {t["tile"] for t in tried} == {(32, 16, 1), (16, 16, 1), (8, 8, 1)}
-    assert {t["ctas_per_sm"] for t in tried} == {2, 3}
+    assert {t["ctas_per_sm"] for t in tried} == {2, 4}
     ran = [t for t in tried if t["ms_per_step"] > 0]
     assert len(ran) == len(tried) and best["ms_per_step"] == min(t["ms_per_step"] for t in ran)
     b = pg.Batch(mem, tile=best["tile"], ctas_per_sm=best["ctas_per_sm"])

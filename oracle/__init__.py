@@ -57,7 +57,7 @@ class OraGrid(C.Structure):
     _fields_ = [("ndim", C.c_int), ("nx", C.c_int * 3), ("dx", C.c_double * 3), ("xmin", C.c_double * 3),
                 ("dt", C.c_double), ("e0", C.c_double * 3), ("b0", C.c_double * 3),
                 ("smooth_level", C.c_int * 3), ("smooth_w", ((C.c_double * 3) * MAX_PASS) * 3),
-                ("rho_bg", C.c_double), ("open_x1", C.c_int)]
+                ("rho_bg", C.c_double), ("open_x1", C.c_int), ("isis", C.c_int)]
 
 
 class OraSpecies(C.Structure):
@@ -84,6 +84,7 @@ def lib():
             L.ora_move.argtypes = [gp, _DP, _DP]
             L.ora_wrap.argtypes = [gp, _DP]
             L.ora_deposit_vb.argtypes = [gp, C.POINTER(_DP), _DP, _DP, C.c_double, C.c_double]
+            L.ora_deposit_isis.argtypes = [gp, C.POINTER(_DP), _DP, _DP, C.c_double, C.c_double]
             L.ora_deposit_rho.argtypes = [gp, _DP, _DP, C.c_longlong, C.c_double]
             L.ora_smooth.argtypes = [gp, _DP]
             L.ora_field_solve.argtypes = [gp, C.POINTER(_DP), C.POINTER(_DP)]
@@ -127,6 +128,7 @@ def make_grid(g) -> OraGrid:
     og.dt = float(g.dt)
     og.rho_bg = float(g.rho_bg)
     og.open_x1 = int(bool(getattr(g, "move_window", False)))
+    og.isis = int(getattr(g, "deposit", "vb") == "isis")
     return og
 
 
@@ -136,6 +138,8 @@ class State:
     def __init__(self, grid, species_list, xs, us, charges, fields=None):
         self.grid = grid
         self.species = list(species_list)
+        if getattr(grid, "deposit", "vb") == "isis" and grid.ndim != 2:
+            raise ValueError("the ISIS deposit is defined for 2D3V only")
         self.og = make_grid(grid)
         self.nstep = 0
         self.shifts = 0
@@ -290,6 +294,18 @@ def deposit_vb(grid, xold, xnew, v3, q):
     cp = (_DP * 3)(*[_dp(c) for c in cur])
     lib().ora_deposit_vb(C.byref(og), cp, _dp(np.ascontiguousarray(xold, dtype=np.float64)),
                          _dp(np.ascontiguousarray(xnew, dtype=np.float64)), float(v3), float(q))
+    return cur
+
+
+def deposit_isis(grid, xold, xnew, v3, q):
+    """ISIS deposit of one path (2D3V only)."""
+    assert grid.ndim == 2, "the thesis defines the ISIS deposit for 2D"
+    og = make_grid(grid)
+    shape = (int(grid.nx[2]), int(grid.nx[1]), int(grid.nx[0]))
+    cur = [np.zeros(shape) for _ in range(3)]
+    cp = (_DP * 3)(*[_dp(c) for c in cur])
+    lib().ora_deposit_isis(C.byref(og), cp, _dp(np.ascontiguousarray(xold, dtype=np.float64)),
+                           _dp(np.ascontiguousarray(xnew, dtype=np.float64)), float(v3), float(q))
     return cur
 
 

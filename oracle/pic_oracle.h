@@ -22,6 +22,8 @@ typedef struct {
   int open_x1;                           /* 1: x1 is open (moving window): values beyond
                                             x1 read as 0, deposits there are dropped,
                                             particles are not wrapped in x1 */
+  int isis;                              /* 1: ISIS current deposit (2D3V) instead of
+                                            TRISTAN / Villasenor-Buneman */
 } ora_grid;
 
 typedef struct {
@@ -39,6 +41,8 @@ void ora_move(const ora_grid* g, double x[3], const double u[3]);
 void ora_wrap(const ora_grid* g, double x[3]);
 void ora_deposit_vb(const ora_grid* g, double* cur[3], const double xold[3], const double xnew[3], double v3,
                     double q);
+void ora_deposit_isis(const ora_grid* g, double* cur[3], const double xold[3], const double xnew[3], double v3,
+                      double q);
 void ora_deposit_rho(const ora_grid* g, double* rho, const double* x, long long n, double q);
 void ora_smooth(const ora_grid* g, double* f);
 void ora_field_solve(const ora_grid* g, double* const fld[6], double* const cur[3]);

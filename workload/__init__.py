@@ -80,6 +80,7 @@ class Grid:
     rho_bg: float = 1.0            # fixed neutralising ion background density
     init_e_gauss_x1: bool = False  # initial E1 from the discrete Gauss law along x1
     move_window: bool = False      # window moving at c in x1 (x1 open; periodic in x2, x3)
+    deposit: str = "vb"            # current deposit: "vb" (TRISTAN / Villasenor-Buneman) or "isis" (2D)
 
     @property
     def ncells(self) -> int:

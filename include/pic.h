@@ -125,7 +125,16 @@ typedef struct {
                                gets zero fields and fresh plasma of every species (its lattice,
                                u_th, u_fl and draw stream continued; explicit species need
                                ppc set).  PIC_FP32_CELLOFF only (else PIC_EUNSUPPORTED). */
+  int deposit;              /* current deposit (thesis ch. 3, "ISIS or TRISTAN methods"):
+                               PIC_DEPOSIT_TRISTAN (0, default; Villasenor-Buneman: the path
+                               is split at cell faces and each piece is the average of its
+                               orthogonal-move orders) or PIC_DEPOSIT_ISIS (1; the average of
+                               the two orders of orthogonal moves of the whole path, not
+                               split; 2D3V only, else PIC_EUNSUPPORTED).  Both conserve
+                               charge exactly; they differ by a divergence-free current. */
 } pic_grid;
+
+enum { PIC_DEPOSIT_TRISTAN = 0, PIC_DEPOSIT_ISIS = 1 };
 
 /* One particle species (appendix nl_species / nl_profile).  Either loaded on the
  * device from the num_par_x lattice and a seed, or given explicitly. */

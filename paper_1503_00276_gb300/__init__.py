@@ -75,6 +75,10 @@ def _grid_struct(grid, precision, tile=None, slack=0.0, sort_period=0, ctas_per_
     g.sort_period = int(sort_period)
     g.ctas_per_sm = int(ctas_per_sm)
     g.move_window = int(bool(getattr(grid, "move_window", False)))
+    dep = getattr(grid, "deposit", "vb")
+    if dep not in ("vb", "isis"):
+        raise ValueError(f"unknown deposit {dep!r} (vb or isis)")
+    g.deposit = 1 if dep == "isis" else 0
     return g
 
 

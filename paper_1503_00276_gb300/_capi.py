@@ -30,7 +30,7 @@ class PicGrid(C.Structure):
                 ("smooth_level", C.c_int * 3), ("smooth_w", ((C.c_double * 3) * MAX_SMOOTH) * 3),
                 ("rho_bg", C.c_double), ("init_e_gauss_x1", C.c_int), ("precision", C.c_int),
                 ("tile", C.c_int * 3), ("slack", C.c_double), ("sort_period", C.c_int),
-                ("ctas_per_sm", C.c_int), ("move_window", C.c_int)]
+                ("ctas_per_sm", C.c_int), ("move_window", C.c_int), ("deposit", C.c_int)]
 
 
 class PicSpecies(C.Structure):

@@ -202,6 +202,7 @@ PushConst make_const(const pic_sim* S, const SpeciesState& sp) {
   C.rqm = sp.rqm;
   C.q = sp.q;
   C.dvol = dvol;
+  C.isis = g.deposit == PIC_DEPOSIT_ISIS ? 1 : 0;
   return C;
 }
 
@@ -940,6 +941,14 @@ pic_status validate_grid(const pic_grid* g) {
   if (!(g->dt > 0.0) || !std::isfinite(g->dt)) {
     set_error("dt must be positive");
     return PIC_EINVAL;
+  }
+  if (g->deposit != PIC_DEPOSIT_TRISTAN && g->deposit != PIC_DEPOSIT_ISIS) {
+    set_error("deposit must be PIC_DEPOSIT_TRISTAN or PIC_DEPOSIT_ISIS");
+    return PIC_EINVAL;
+  }
+  if (g->deposit == PIC_DEPOSIT_ISIS && g->ndim != 2) {
+    set_error("the ISIS deposit is defined for 2D3V only");
+    return PIC_EUNSUPPORTED;
   }
   if (g->dt >= 1.0 / std::sqrt(s)) {
     set_error("Courant condition violated: dt >= 1/sqrt(sum dx^-2)");

@@ -81,7 +81,7 @@ __device__ inline void boris(double u[3], const double e[3], const double b[3], 
 // i.e. the midpoint weights plus the covariance term D_t1 D_t2 / 12.
 template <int NDIM>
 __device__ inline void deposit_segment(const Layout& L, const PushConst& C, J3 J, const int cell[3],
-                                       const double a[3], const double b[3], double v3frac) {
+                                       const double a[3], const double b[3], double v3frac, bool only_j3 = false) {
   double dl[3], m[3];
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
@@ -89,12 +89,14 @@ __device__ inline void deposit_segment(const Layout& L, const PushConst& C, J3 J
     m[d] = 0.5 * (a[d] + b[d]);
   }
   if (NDIM == 2) {
+    if (!only_j3) {
     double a1 = C.q * dl[0] * C.dx[0] / (C.dt * C.dvol);
     double a2 = C.q * dl[1] * C.dx[1] / (C.dt * C.dvol);
     atomicAdd(&J.c[0][L.idx(cell[0], cell[1], 0)], a1 * (1.0 - m[1]));
     atomicAdd(&J.c[0][L.idx(cell[0], cell[1] + 1, 0)], a1 * m[1]);
     atomicAdd(&J.c[1][L.idx(cell[0], cell[1], 0)], a2 * (1.0 - m[0]));
     atomicAdd(&J.c[1][L.idx(cell[0] + 1, cell[1], 0)], a2 * m[0]);
+    }
     double a3 = C.q * v3frac / C.dvol;
     double cv = dl[0] * dl[1] / 12.0;
     atomicAdd(&J.c[2][L.idx(cell[0], cell[1], 0)], a3 * ((1.0 - m[0]) * (1.0 - m[1]) + cv));
@@ -123,7 +125,7 @@ __device__ inline void deposit_segment(const Layout& L, const PushConst& C, J3 J
 // per direction) and deposit each in-cell piece.
 template <int NDIM>
 __device__ inline void deposit_path(const Layout& L, const PushConst& C, J3 J, const double xo[3],
-                                    const double xn[3], double v3) {
+                                    const double xn[3], double v3, bool only_j3 = false) {
   int i0[3] = {0, 0, 0};
   double a[3] = {0, 0, 0}, b[3] = {0, 0, 0};
   const int nn[3] = {L.nx, L.ny, L.nz};
@@ -181,11 +183,53 @@ __device__ inline void deposit_path(const Layout& L, const PushConst& C, J3 J, c
       la[d] = p0[d] - (double)off[d];
       lb[d] = p1[d] - (double)off[d];
     }
-    deposit_segment<NDIM>(L, C, J, cell, la, lb, v3 * (t1 - t0));
+    deposit_segment<NDIM>(L, C, J, cell, la, lb, v3 * (t1 - t0), only_j3);
     if (m < nc) off[dc[m]] += sc[m];
     for (int d = 0; d < 3; ++d) p0[d] = p1[d];
     t0 = t1;
   }
+}
+
+// ISIS deposit (2D3V): the in-plane current of the whole straight path is the
+// average of the two orders of orthogonal moves, not split at cell faces.  A
+// move along x puts, through the J1 face of column i0 + d (d = -1, 0, 1), the
+// part of the move inside that column -- the change of the linear charge
+// weights it causes -- with the transverse weights of its fixed coordinate
+// (y_a in one order, y_b in the other, averaged).  J3 is TRISTAN's: the time
+// integral along the straight path.
+__device__ inline double lin_w(double s) { return fmax(0.0, 1.0 - fabs(s)); }
+
+__device__ inline void deposit_isis(const Layout& L, const PushConst& C, J3 J, const double xo[3],
+                                    const double xn[3], double v3) {
+  int i0[2];
+  double a[2], b[2];
+  const int nn[2] = {L.nx, L.ny};
+  for (int d = 0; d < 2; ++d) {
+    double go = (xo[d] - C.xmin[d]) / C.dx[d];
+    double gn = (xn[d] - C.xmin[d]) / C.dx[d];
+    double fl = floor(go);
+    int ic = (int)fl;
+    a[d] = go - fl;
+    b[d] = gn - fl;
+    if (ic >= nn[d]) ic -= nn[d];
+    i0[d] = ic;
+  }
+  double f[2][3], w[2][4];
+  for (int d = 0; d < 2; ++d) {
+    f[d][0] = fmin(b[d], 0.0);
+    f[d][1] = fmin(fmax(b[d], 0.0), 1.0) - a[d];
+    f[d][2] = fmax(b[d] - 1.0, 0.0);
+    for (int m = 0; m < 4; ++m) w[d][m] = 0.5 * (lin_w(a[d] - (double)(m - 1)) + lin_w(b[d] - (double)(m - 1)));
+  }
+  const double c1 = C.q * C.dx[0] / (C.dt * C.dvol), c2 = C.q * C.dx[1] / (C.dt * C.dvol);
+  for (int d = 0; d < 3; ++d)
+    for (int m = 0; m < 4; ++m) {
+      if (f[0][d] != 0.0 && w[1][m] != 0.0)
+        atomicAdd(&J.c[0][L.idx(i0[0] + d - 1, i0[1] + m - 1, 0)], c1 * f[0][d] * w[1][m]);
+      if (f[1][d] != 0.0 && w[0][m] != 0.0)
+        atomicAdd(&J.c[1][L.idx(i0[0] + m - 1, i0[1] + d - 1, 0)], c2 * f[1][d] * w[0][m]);
+    }
+  deposit_path<2>(L, C, J, xo, xn, v3, true);
 }
 
 template <int NDIM>
@@ -208,7 +252,10 @@ __global__ void __launch_bounds__(256) k_plain_push(Layout L, PushConst C, Plain
     atomicOr(status, ST_NONFINITE);
     return;
   }
-  deposit_path<NDIM>(L, C, J, xo, x, u[2] / gam);
+  if (NDIM == 2 && C.isis)
+    deposit_isis(L, C, J, xo, x, u[2] / gam);
+  else
+    deposit_path<NDIM>(L, C, J, xo, x, u[2] / gam);
   // periodic wrap
 #pragma unroll
   for (int d = 0; d < NDIM; ++d) {

@@ -56,6 +56,8 @@ struct TileArgs {
   float dt_dx[3];       // dt / dx_d
   float cf[3];          // q dx_d / (dt dV): current density per cell-unit of displacement
   float j3f;            // q / dV (2D3V out-of-plane current per unit v3 and time share)
+  int isis;             // 1: ISIS deposit (2D3V): a crossing path's in-plane current is
+                        // that of its whole straight path, not split at faces
   float e0[3], b0[3];
   int* status;
   const int* nslice;    // [ntiles] slices of each tile (nullptr: one work item per tile)
@@ -268,6 +270,51 @@ __device__ inline void walk(float ax, float ay, float az, float bx, float by, fl
   }
 }
 
+// ISIS deposit (2D3V) of a whole straight path a -> b that starts in tile cell
+// (lx, ly) (a, b in cell units relative to that cell): the in-plane current is
+// the average of the two orders of orthogonal moves.  A move along x from a_x to
+// b_x puts, through the J1 face of column lx + d (d = -1, 0, 1), the part of
+// the move inside that column (the change of the linear charge weights it
+// causes); the transverse weights are those of the fixed coordinate of the
+// move, a_y in one order and b_y in the other, averaged.  Likewise for y.  J3 is
+// the time integral along the straight path, the same as TRISTAN's (its pieces).
+__device__ inline float lin_w(float s) { return fmaxf(0.f, 1.f - fabsf(s)); }
+
+template <int TX, int TY>
+__device__ inline void isis_path(float* J, const TileArgs& A, int lx, int ly, float ax, float ay, float bx,
+                                 float by, float v3) {
+  using G = Geo<2, TX, TY, 1>;
+  const float fx[3] = {fminf(bx, 0.f), fminf(fmaxf(bx, 0.f), 1.f) - ax, fmaxf(bx - 1.f, 0.f)};
+  const float fy[3] = {fminf(by, 0.f), fminf(fmaxf(by, 0.f), 1.f) - ay, fmaxf(by - 1.f, 0.f)};
+  float wx[4], wy[4];  // nodes -1 .. 2 relative to the start cell
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    wx[m] = 0.5f * (lin_w(ax - (float)(m - 1)) + lin_w(bx - (float)(m - 1)));
+    wy[m] = 0.5f * (lin_w(ay - (float)(m - 1)) + lin_w(by - (float)(m - 1)));
+  }
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      if (fx[d] != 0.f && wy[m] != 0.f)  // J1 at (lx + d - 1, ly + m - 1)
+        atomicAdd(&J[(ly + m) * G::JX + (lx + d)], A.cf[0] * fx[d] * wy[m]);
+      if (fy[d] != 0.f && wx[m] != 0.f)  // J2 at (lx + m - 1, ly + d - 1)
+        atomicAdd(&J[G::JPL + (ly + d) * G::JX + (lx + m)], A.cf[1] * fy[d] * wx[m]);
+    }
+  }
+  walk<2>(ax, ay, 0.f, bx, by, 0.f,
+          [&](int k, int ox, int oy, int oz, float sx0, float sy0, float sz0, float sx1, float sy1, float sz1,
+              float frac) {
+            float w[12];
+            seg_weights<2>(A, sx0, sy0, 0.f, sx1, sy1, 0.f, v3 * frac, w);
+            const int c = 2 * G::JPL + (ly + oy + 1) * G::JX + (lx + ox + 1);
+            atomicAdd(&J[c], w[4]);
+            atomicAdd(&J[c + 1], w[5]);
+            atomicAdd(&J[c + G::JX], w[6]);
+            atomicAdd(&J[c + G::JX + 1], w[7]);
+          });
+}
+
 // Per-thread accumulator of first pieces that start in the same cell.
 struct Acc {
   float w[12];
@@ -415,14 +462,16 @@ __device__ inline int push_one(const float* F, float* J, const TileArgs& A, P& p
       if (w == 1) p1y = (float)(scy > 0);
       if (w == 2) p1z = (float)(scz > 0);
     }
-    if (acc.cell != cellp) {
-      acc_flush<NDIM, TX, TY, TZ>(J, acc);
-      acc.cell = cellp;
-    }
-    float w[12];
-    seg_weights<NDIM>(A, ax, ay, az, p1x, p1y, p1z, v3 * t1, w);
+    if (!(NDIM == 2 && A.isis && tm < 1.f)) {  // an ISIS crossing path is deposited whole below
+      if (acc.cell != cellp) {
+        acc_flush<NDIM, TX, TY, TZ>(J, acc);
+        acc.cell = cellp;
+      }
+      float w[12];
+      seg_weights<NDIM>(A, ax, ay, az, p1x, p1y, p1z, v3 * t1, w);
 #pragma unroll
-    for (int k = 0; k < (NDIM == 3 ? 12 : 8); ++k) acc.w[k] += w[k];
+      for (int k = 0; k < (NDIM == 3 ? 12 : 8); ++k) acc.w[k] += w[k];
+    }
   }
   if (tm < 1.f) {
     const int q = atomicAdd(qn, 1);
@@ -441,6 +490,9 @@ __device__ inline int push_one(const float* F, float* J, const TileArgs& A, P& p
       }
     } else {
       // queue full: deposit the remaining pieces here
+      if (NDIM == 2 && A.isis)
+        isis_path<TX, TY>(J, A, lx, ly, ax, ay, bx, by, v3);
+      else
       walk<NDIM>(ax, ay, az, bx, by, bz,
                  [&](int k, int ox, int oy, int oz, float sx0, float sy0, float sz0, float sx1, float sy1, float sz1,
                      float frac) {
@@ -502,6 +554,9 @@ __device__ inline void drain_queue(float* J, const TileArgs& A, const float* Q, 
       const float ax = e[1], ay = e[2], bx = e[3], by = e[4];
       const float az = NDIM == 3 ? e[5] : 0.f, bz = NDIM == 3 ? e[6] : 0.f;
       const float v3 = NDIM == 3 ? 0.f : e[5];
+      if (NDIM == 2 && A.isis)
+        isis_path<TX, TY>(J, A, lx, ly, ax, ay, bx, by, v3);
+      else
       walk<NDIM>(ax, ay, az, bx, by, bz,
                  [&](int k, int ox, int oy, int oz, float sx0, float sy0, float sz0, float sx1, float sy1, float sz1,
                      float frac) {
@@ -1997,6 +2052,7 @@ TileArgs make_args(const PushConst& C, const Tiles& tg, const TileSide& in, cons
     A.b0[d] = (float)C.b0[d];
   }
   A.j3f = (float)(C.q / C.dvol);
+  A.isis = C.isis;
   A.status = status;
   A.nslice = nullptr;
   A.extra = nullptr;

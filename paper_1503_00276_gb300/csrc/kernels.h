@@ -44,6 +44,7 @@ struct PushConst {        // per-species constants of one step
   double e0[3], b0[3];
   double rqm, q, dvol;
   double L[3];            // box length per direction
+  int isis;               // 1: ISIS deposit (2D3V), 0: TRISTAN / Villasenor-Buneman
 };
 
 // FP64 plain form

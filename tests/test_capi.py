@@ -97,6 +97,16 @@ def test_bad_arguments_are_rejected(capi):
     assert lib.pic_bin_tiles(nx, bad_tile, 0, None, C.c_void_p(8), C.c_void_p(8), None, None, None) == -1
 
 
+def test_deposit_choice_is_checked(capi):
+    g = _grid(ndim=3)
+    g.deposit = 1  # ISIS: defined for 2D3V only
+    assert _init(capi, g)[0] == -8
+    assert b"ISIS" in capi.load().pic_last_error()
+    g = _grid()
+    g.deposit = 7
+    assert _init(capi, g)[0] == -1
+
+
 def test_valid_grid_without_device_reports_cuda_error(capi):
     import torch
     if torch.cuda.is_available():

@@ -381,21 +381,30 @@ pic_status pic_info(const pic_sim* S, pic_grid* grid, int* nspecies, long long* 
 
 
 /* ---- Laser pulses ------------------------------------------------------------
- * A pulse moving in +x1 (the thesis' pulse input, wavetype 1), added to the
- * current fields: vosc = peak normalised vector potential a0; rkkp = its
- * wavenumber k (= omega0 / omega_p); w0 = spot size (field 1/e radius of the
- * Gaussian transverse profile); rise / length / fall = envelope distances
- * behind the front (sin^2 rise, flat, cos^2 fall -- the thesis says
- * "approximately Gaussian"); start = distance of the front from the +x1 side
- * of the box; pol = polarisation angle from x2 towards x3 in degrees; phase;
- * offset = transverse offset of the axis from the box centre (x2, x3).  With
- * A = vosc f(xi) T(r) cos(k (x1 - x_front) + phase) along the polarisation,
- * E = -dA/dt and B = x1-hat x E in the slowly varying envelope form, each
- * component at its own staggered position.  The thesis' focus is not modelled
- * (the pulse is set up with its waist profile).  Synchronises S's stream. */
+ * A pulse added to the current fields (the thesis' pulse input): wavetype 1
+ * (or 0) moves in +x1, wavetype 2 in +x2.  vosc = peak normalised vector
+ * potential a0; rkkp = its wavenumber k (= omega0 / omega_p); w0 = spot size
+ * (field 1/e radius in the focal plane); rise / length / fall = envelope
+ * distances behind the front (rise 10 s^3 - 15 s^4 + 6 s^5 with s the
+ * fraction of the rise, flat, then the mirror image -- the thesis' temporal
+ * profile); start = distance of the front from the side of the box the pulse
+ * moves towards; pol = polarisation angle in degrees from the in-plane
+ * transverse axis (x2 for wavetype 1, x1 for wavetype 2) towards x3; phase;
+ * offset = transverse offset of the axis from the box centre (in-plane axis,
+ * x3).  focus_on: 1 = the lowest Hermite-Gaussian beam of the thesis' laser-beam
+ * section with its focal plane at distance `focus` from that same side (spot
+ * size w0 sqrt(1 + (z/z_R)^2), curvature and Gouy phase; 2D: slab beam with
+ * amplitude sqrt(w0 / w) and half the Gouy phase); 0 = waist profile w0
+ * everywhere.  A along the polarisation gives E = -dA/dt and B = e_k x E in
+ * the slowly varying envelope form, each component at its own staggered
+ * position.  The thesis' `time` is the step at which the caller adds the
+ * pulse.  Synchronises S's stream. */
 typedef struct {
   double vosc, rkkp, w0, rise, fall, length, start, pol, phase;
   double offset[2];
+  int wavetype;             /* 1 (or 0): along x1; 2: along x2 */
+  int focus_on;
+  double focus;
 } pic_laser;
 
 pic_status pic_laser_add(pic_sim* S, const pic_laser* laser);

@@ -362,55 +362,87 @@ def tile_bin(grid, tile, x):
 # --- laser pulse initialisation ----------------------------------------------
 
 def laser_envelope(xi, rise, length, fall):
-    """Longitudinal envelope behind the pulse front (xi >= 0 behind it): the
-    thesis calls rise and fall "approximately Gaussian" without a formula;
-    read as sin^2 over the rise, 1 over the length, cos^2 over the fall, 0
-    elsewhere (reading R21)."""
+    """Longitudinal envelope behind the pulse front (xi >= 0 behind it), the
+    thesis' temporal profile: it rises as 10 s^3 - 15 s^4 + 6 s^5 with s =
+    xi / rise (ch. on injection simulations; the appendix calls the rise and
+    fall "approximately Gaussian"), stays 1 over `length` and falls as the
+    mirror image over `fall`; 0 elsewhere (reading R21)."""
     xi = np.asarray(xi, dtype=np.float64)
+
+    def poly(s):
+        return 10.0 * s ** 3 - 15.0 * s ** 4 + 6.0 * s ** 5
+
     f = np.zeros_like(xi)
     a = (xi >= 0) & (xi < rise)
-    f[a] = np.sin(0.5 * math.pi * xi[a] / rise) ** 2
+    f[a] = poly(xi[a] / rise)
     b = (xi >= rise) & (xi < rise + length)
     f[b] = 1.0
     c = (xi >= rise + length) & (xi < rise + length + fall)
-    f[c] = np.cos(0.5 * math.pi * (xi[c] - rise - length) / fall) ** 2
+    f[c] = poly(1.0 - (xi[c] - rise - length) / fall)
     return f
 
 
 def laser_fields(grid, laser, xmin1=None):
-    """E and B of a pulse moving in +x1 at t = 0, each component at its own
-    staggered positions (E2 at (i, j+1/2, k), E3 at (i, j, k+1/2), B2 at
-    (i+1/2, j, k+1/2), B3 at (i+1/2, j+1/2, k)): the vector potential
-    A = vosc f(xi) T(r) cos(k (x1 - x_front) + phase) along p = (0, cos pol,
-    sin pol), T(r) = exp(-r^2 / w0^2) about the box axis plus offset, gives in
-    the slowly varying envelope approximation E = -dA/dt = -vosc k f T
-    sin(k (x1 - x_front) + phase) p and B = x1-hat x E (B3 = E2, B2 = -E3).
-    Returns the six arrays [nz][ny][nx] (E1 = B1 = 0)."""
+    """E and B of a pulse at t = 0, each component at its own staggered
+    position.  The pulse moves in +x_a (wavetype 1: a = x1, 2: a = x2); with
+    the vector potential A = vosc f(xi) g T cos(psi) along p = cos(pol) e_t +
+    sin(pol) e_3 (e_t the in-plane transverse axis), the slowly varying
+    envelope approximation gives E = -dA/dt = -vosc k f g T sin(psi) p and
+    B = e_a x E.  Without a focal plane g = 1, T = exp(-r^2 / w0^2) and
+    psi = k (x_a - x_front) + phase.  With one (the thesis' Hermite-Gaussian
+    beam, its laser-beam section): z = x_a - x_focus, z_R = k w0^2 / 2, w = w0
+    sqrt(1 + (z/z_R)^2), T = exp(-r^2 / w^2), g = w0 / w in 3D and sqrt(w0 / w)
+    for the 2D slab beam, psi += k r^2 / (2 R) - Gouy with R = z + z_R^2 / z and
+    Gouy = atan(z / z_R) (half in 2D).  Returns the six arrays [nz][ny][nx]."""
     nx, ny = int(grid.nx[0]), int(grid.nx[1])
     nz = int(grid.nx[2]) if grid.ndim == 3 else 1
     dx = grid.dx
-    x0 = float(grid.xmin[0] if xmin1 is None else xmin1)
-    xfront = x0 + nx * dx[0] - laser.start
-    c2 = grid.xmin[1] + 0.5 * ny * dx[1] + laser.offset[0]
-    c3 = (grid.xmin[2] + 0.5 * nz * dx[2] + laser.offset[1]) if grid.ndim == 3 else 0.0
+    a = 1 if int(getattr(laser, "wavetype", 1)) == 2 else 0
+    t = 1 - a
+    xmin = [float(grid.xmin[0] if xmin1 is None else xmin1), float(grid.xmin[1]), float(grid.xmin[2])]
+    nn = [nx, ny, nz]
+    upper = xmin[a] + nn[a] * dx[a]
+    xfront = upper - laser.start
+    ct = xmin[t] + 0.5 * nn[t] * dx[t] + laser.offset[0]
+    c3 = (xmin[2] + 0.5 * nz * dx[2] + laser.offset[1]) if grid.ndim == 3 else 0.0
+    focus = getattr(laser, "focus", None)
     th = math.radians(laser.pol)
     k_, j_, i_ = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    k = laser.rkkp
 
     def amp(s1, s2, s3):
-        x1 = x0 + (i_ + s1) * dx[0]
-        x2 = grid.xmin[1] + (j_ + s2) * dx[1]
-        r2 = (x2 - c2) ** 2
+        x = [xmin[0] + (i_ + s1) * dx[0], xmin[1] + (j_ + s2) * dx[1],
+             xmin[2] + (k_ + s3) * dx[2] if grid.ndim == 3 else np.zeros(i_.shape)]
+        r2 = (x[t] - ct) ** 2
         if grid.ndim == 3:
-            x3 = grid.xmin[2] + (k_ + s3) * dx[2]
-            r2 = r2 + (x3 - c3) ** 2
-        f = laser_envelope(xfront - x1, laser.rise, laser.length, laser.fall)
-        return -laser.vosc * laser.rkkp * f * np.exp(-r2 / laser.w0 ** 2) * \
-            np.sin(laser.rkkp * (x1 - xfront) + laser.phase)
+            r2 = r2 + (x[2] - c3) ** 2
+        f = laser_envelope(xfront - x[a], laser.rise, laser.length, laser.fall)
+        w2 = laser.w0 ** 2 * np.ones(r2.shape)
+        g = np.ones(r2.shape)
+        psi = k * (x[a] - xfront) + laser.phase
+        if focus is not None:
+            zr = 0.5 * k * laser.w0 ** 2
+            z = x[a] - (upper - focus)
+            q = 1.0 + (z / zr) ** 2
+            w2 = laser.w0 ** 2 * q
+            g = q ** -0.5 if grid.ndim == 3 else q ** -0.25
+            with np.errstate(divide="ignore", invalid="ignore"):
+                curv = np.where(z != 0.0, k * r2 / (2.0 * (z + zr * zr / z)), 0.0)
+            gouy = np.arctan(z / zr)
+            psi = psi + curv - (gouy if grid.ndim == 3 else 0.5 * gouy)
+        return -laser.vosc * k * f * g * np.exp(-r2 / w2) * np.sin(psi)
 
     zero = np.zeros((nz, ny, nx))
     s3 = 0.5 if grid.ndim == 3 else 0.0
-    e2 = amp(0.0, 0.5, 0.0) * math.cos(th)
-    e3 = amp(0.0, 0.0, s3) * math.sin(th)
-    b2 = -amp(0.5, 0.0, s3) * math.sin(th)
-    b3 = amp(0.5, 0.5, 0.0) * math.cos(th)
-    return [zero, e2, e3, zero.copy(), b2, b3]
+    out = [zero.copy() for _ in range(6)]
+    if a == 0:  # E2, E3; B3 = E2, B2 = -E3
+        out[1] = amp(0.0, 0.5, 0.0) * math.cos(th)
+        out[2] = amp(0.0, 0.0, s3) * math.sin(th)
+        out[4] = -amp(0.5, 0.0, s3) * math.sin(th)
+        out[5] = amp(0.5, 0.5, 0.0) * math.cos(th)
+    else:  # E1, E3; B1 = E3, B3 = -E1
+        out[0] = amp(0.5, 0.0, 0.0) * math.cos(th)
+        out[2] = amp(0.0, 0.0, s3) * math.sin(th)
+        out[3] = amp(0.0, 0.5, s3) * math.sin(th)
+        out[5] = -amp(0.5, 0.5, 0.0) * math.cos(th)
+    return out

@@ -154,12 +154,16 @@ class Simulation:
 
     # -- laser ----------------------------------------------------------------
     def add_laser(self, laser):
-        """pic_laser_add: a pulse moving in +x1 (attributes of workload.Laser)."""
+        """pic_laser_add: a pulse moving in +x1 or +x2 (attributes of workload.Laser)."""
         L = _capi.PicLaser()
         for f in ("vosc", "rkkp", "w0", "rise", "fall", "length", "start", "pol", "phase"):
             setattr(L, f, float(getattr(laser, f)))
         off = tuple(getattr(laser, "offset", (0.0, 0.0)))
         L.offset[0], L.offset[1] = float(off[0]), float(off[1] if len(off) > 1 else 0.0)
+        L.wavetype = int(getattr(laser, "wavetype", 1))
+        focus = getattr(laser, "focus", None)
+        L.focus_on = int(focus is not None)
+        L.focus = float(focus) if focus is not None else 0.0
         check(self._lib.pic_laser_add(self._h, C.byref(L)), "pic_laser_add")
 
     # -- checkpoint / restart ---------------------------------------------------

@@ -43,7 +43,8 @@ class PicSpecies(C.Structure):
 class PicLaser(C.Structure):
     _fields_ = [("vosc", C.c_double), ("rkkp", C.c_double), ("w0", C.c_double), ("rise", C.c_double),
                 ("fall", C.c_double), ("length", C.c_double), ("start", C.c_double), ("pol", C.c_double),
-                ("phase", C.c_double), ("offset", C.c_double * 2)]
+                ("phase", C.c_double), ("offset", C.c_double * 2), ("wavetype", C.c_int), ("focus_on", C.c_int),
+                ("focus", C.c_double)]
 
 
 class PicTuneChoice(C.Structure):

@@ -2160,22 +2160,25 @@ pic_status pic_checkpoint_load(const char* path, const pic_allocator* alloc, voi
 }
 
 pic_status pic_laser_add(pic_sim* S, const pic_laser* L) {
-  if (!S || !L || !(L->rkkp > 0.0) || !(L->w0 > 0.0) || L->rise < 0.0 || L->fall < 0.0 || L->length < 0.0) {
+  if (!S || !L || !(L->rkkp > 0.0) || !(L->w0 > 0.0) || L->rise < 0.0 || L->fall < 0.0 || L->length < 0.0 ||
+      (L->wavetype != 0 && L->wavetype != 1 && L->wavetype != 2)) {
     set_error("pic_laser_add: bad arguments");
     return PIC_EINVAL;
   }
   const pic_grid& g = S->g;
   const double nxr[3] = {(double)S->L.nx, (double)S->L.ny, (double)S->L.nz};
+  const int a = L->wavetype == 2 ? 1 : 0, tr = 1 - a;  // propagation and in-plane transverse axes
   const double pol = L->pol * 3.141592653589793 / 180.0;
-  double p[18];
+  const double upper = g.xmin[a] + nxr[a] * g.dx[a];  // the side the pulse moves towards
+  double p[21];
   p[0] = L->vosc;
   p[1] = L->rkkp;
   p[2] = L->w0;
   p[3] = L->rise;
   p[4] = L->length;
   p[5] = L->fall;
-  p[6] = g.xmin[0] + nxr[0] * g.dx[0] - L->start;  // pulse front
-  p[7] = g.xmin[1] + 0.5 * nxr[1] * g.dx[1] + L->offset[0];
+  p[6] = upper - L->start;  // pulse front
+  p[7] = g.xmin[tr] + 0.5 * nxr[tr] * g.dx[tr] + L->offset[0];
   p[8] = S->ndim == 3 ? g.xmin[2] + 0.5 * nxr[2] * g.dx[2] + L->offset[1] : 0.0;
   p[9] = cos(pol);
   p[10] = sin(pol);
@@ -2184,6 +2187,9 @@ pic_status pic_laser_add(pic_sim* S, const pic_laser* L) {
     p[12 + d] = g.xmin[d];
     p[15 + d] = d < S->ndim ? g.dx[d] : 1.0;
   }
+  p[18] = a;
+  p[19] = L->focus_on ? 1.0 : 0.0;
+  p[20] = upper - L->focus;  // focal plane
   if (S->prec == PIC_FP64_PLAIN) {
     double* f[6];
     for (int c = 0; c < 6; ++c) f[c] = fld_ptr<double>(S, c);

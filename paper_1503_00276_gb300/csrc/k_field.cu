@@ -276,32 +276,51 @@ __global__ void k_shift_x(Layout L, PtrN<T, 6> P, int ncomp) {
   }
 }
 
-// Laser pulse moving in +x1 added to E2, E3, B2, B3, each at its staggered
-// position: E_p = -vosc k f(xi) exp(-r^2 / w0^2) sin(k (x1 - x_front) +
-// phase) along p = (0, cos pol, sin pol), B3 = E2, B2 = -E3 (slowly varying
-// envelope of the vector potential A = vosc f T cos(...)); f is sin^2 over
-// the rise, 1 over the length, cos^2 over the fall behind the front.
+// Laser pulse added to the fields, each component at its staggered position.
+// The pulse moves in +x_a (a = 0: wavetype 1, along x1; a = 1: wavetype 2,
+// along x2) with the vector potential A = vosc f(xi) g T cos(psi) along
+// p = cos(pol) e_t + sin(pol) e_3 (e_t the in-plane transverse axis); in the
+// slowly varying envelope form E = -dA/dt = -vosc k f g T sin(psi) p and
+// B = e_a x E.  xi = x_front - x_a; f rises as 10 s^3 - 15 s^4 + 6 s^5
+// (s = xi / rise), stays 1 over `length` and falls as the mirror image over
+// `fall` (the thesis' temporal profile).  With a focal plane (focus_on) the
+// transverse profile is the lowest Hermite-Gaussian beam of the thesis'
+// laser-beam section: z = x_a - x_focus, z_R = k w0^2 / 2, w = w0 sqrt(1 +
+// (z/z_R)^2), T = exp(-r^2 / w^2), g = w0 / w (3D; sqrt(w0 / w) for the 2D
+// slab beam), psi = k (x_a - x_front) + k r^2 / (2 R) - G + phase with
+// R = z + z_R^2 / z and the Gouy phase G = atan(z / z_R) (half of it in 2D).
+// Without a focal plane g = 1, w = w0, psi = k (x_a - x_front) + phase.
 struct LaserDev {
-  double vosc, k, w0, rise, length, fall, xfront, c2, c3, cpol, spol, phase;
+  double vosc, k, w0, rise, length, fall, xfront, ct, c3, cpol, spol, phase;
   double xmin[3], dx[3];
+  int axis, focus_on;
+  double xfocus;
 };
 
-__device__ inline double laser_amp(const LaserDev& P, int ndim, double x1, double x2, double x3) {
-  const double xi = P.xfront - x1;
+__device__ inline double laser_profile(double s) { return s * s * s * (10.0 + s * (-15.0 + 6.0 * s)); }
+
+__device__ inline double laser_amp(const LaserDev& P, int ndim, const double x[3]) {
+  const int a = P.axis, t = 1 - P.axis;
+  const double xi = P.xfront - x[a];
   double f = 0.0;
-  if (xi >= 0.0 && xi < P.rise) {
-    const double s = sin(0.5 * 3.141592653589793 * xi / P.rise);
-    f = s * s;
-  } else if (xi >= P.rise && xi < P.rise + P.length) {
+  if (xi >= 0.0 && xi < P.rise)
+    f = laser_profile(xi / P.rise);
+  else if (xi >= P.rise && xi < P.rise + P.length)
     f = 1.0;
-  } else if (xi >= P.rise + P.length && xi < P.rise + P.length + P.fall) {
-    const double s = cos(0.5 * 3.141592653589793 * (xi - P.rise - P.length) / P.fall);
-    f = s * s;
-  }
+  else if (xi >= P.rise + P.length && xi < P.rise + P.length + P.fall)
+    f = laser_profile(1.0 - (xi - P.rise - P.length) / P.fall);
   if (f == 0.0) return 0.0;
-  double r2 = (x2 - P.c2) * (x2 - P.c2);
-  if (ndim == 3) r2 += (x3 - P.c3) * (x3 - P.c3);
-  return -P.vosc * P.k * f * exp(-r2 / (P.w0 * P.w0)) * sin(P.k * (x1 - P.xfront) + P.phase);
+  double r2 = (x[t] - P.ct) * (x[t] - P.ct);
+  if (ndim == 3) r2 += (x[2] - P.c3) * (x[2] - P.c3);
+  double w2 = P.w0 * P.w0, g = 1.0, psi = P.k * (x[a] - P.xfront) + P.phase;
+  if (P.focus_on) {
+    const double zr = 0.5 * P.k * P.w0 * P.w0, z = x[a] - P.xfocus, q = 1.0 + (z / zr) * (z / zr);
+    w2 *= q;
+    g = ndim == 3 ? 1.0 / sqrt(q) : 1.0 / sqrt(sqrt(q));
+    const double gouy = atan(z / zr);
+    psi += (z != 0.0 ? P.k * r2 / (2.0 * (z + zr * zr / z)) : 0.0) - (ndim == 3 ? gouy : 0.5 * gouy);
+  }
+  return -P.vosc * P.k * f * g * exp(-r2 / w2) * sin(psi);
 }
 
 template <typename T>
@@ -312,15 +331,23 @@ __global__ void k_laser_add(Layout L, Ptr6<T> F, LaserDev P) {
   if (i >= L.nx || j >= L.ny) return;
   const long long c = L.idx(i, j, k);
   const double h3 = L.ndim == 3 ? 0.5 : 0.0;
-  auto X = [&](int d, int n, double s) { return P.xmin[d] + (n + s) * P.dx[d]; };
-  const double e2 = laser_amp(P, L.ndim, X(0, i, 0.0), X(1, j, 0.5), X(2, k, 0.0)) * P.cpol;
-  const double e3 = laser_amp(P, L.ndim, X(0, i, 0.0), X(1, j, 0.0), X(2, k, h3)) * P.spol;
-  const double b2 = -laser_amp(P, L.ndim, X(0, i, 0.5), X(1, j, 0.0), X(2, k, h3)) * P.spol;
-  const double b3 = laser_amp(P, L.ndim, X(0, i, 0.5), X(1, j, 0.5), X(2, k, 0.0)) * P.cpol;
-  F.c[1][c] = (T)((double)F.c[1][c] + e2);
-  F.c[2][c] = (T)((double)F.c[2][c] + e3);
-  F.c[4][c] = (T)((double)F.c[4][c] + b2);
-  F.c[5][c] = (T)((double)F.c[5][c] + b3);
+  // position of a component with stagger (s1, s2, s3)
+  auto A = [&](double s1, double s2, double s3) {
+    const double x[3] = {P.xmin[0] + (i + s1) * P.dx[0], P.xmin[1] + (j + s2) * P.dx[1],
+                         P.xmin[2] + (k + s3) * P.dx[2]};
+    return laser_amp(P, L.ndim, x);
+  };
+  if (P.axis == 0) {  // along x1: E2, E3; B3 = E2, B2 = -E3
+    F.c[1][c] = (T)((double)F.c[1][c] + A(0.0, 0.5, 0.0) * P.cpol);
+    F.c[2][c] = (T)((double)F.c[2][c] + A(0.0, 0.0, h3) * P.spol);
+    F.c[4][c] = (T)((double)F.c[4][c] - A(0.5, 0.0, h3) * P.spol);
+    F.c[5][c] = (T)((double)F.c[5][c] + A(0.5, 0.5, 0.0) * P.cpol);
+  } else {  // along x2: E1, E3; B1 = E3, B3 = -E1
+    F.c[0][c] = (T)((double)F.c[0][c] + A(0.5, 0.0, 0.0) * P.cpol);
+    F.c[2][c] = (T)((double)F.c[2][c] + A(0.0, 0.0, h3) * P.spol);
+    F.c[3][c] = (T)((double)F.c[3][c] + A(0.0, 0.5, h3) * P.spol);
+    F.c[5][c] = (T)((double)F.c[5][c] - A(0.5, 0.5, 0.0) * P.cpol);
+  }
 }
 
 // ---------------------------------------------------------------- diagnostics
@@ -516,7 +543,7 @@ void laser_add(const Layout& L, T* const* f, const double* p, cudaStream_t s) {
   P.length = p[4];
   P.fall = p[5];
   P.xfront = p[6];
-  P.c2 = p[7];
+  P.ct = p[7];
   P.c3 = p[8];
   P.cpol = p[9];
   P.spol = p[10];
@@ -525,6 +552,9 @@ void laser_add(const Layout& L, T* const* f, const double* p, cudaStream_t s) {
     P.xmin[d] = p[12 + d];
     P.dx[d] = p[15 + d];
   }
+  P.axis = (int)p[18];
+  P.focus_on = p[19] != 0.0;
+  P.xfocus = p[20];
   k_laser_add<T><<<interior_grid(L), kBlock, 0, s>>>(L, F, P);
 }
 

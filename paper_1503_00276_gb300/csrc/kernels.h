@@ -26,8 +26,9 @@ void yee_e(const Layout& L, T* const* e, T* const* b, T* const* j, double dt, co
 template <typename T> void field_energy(const Layout& L, T* const* f, Diag64* acc, cudaStream_t s);
 // moving window: every E/B value one cell back in x1, zero front column
 template <typename T> void shift_x(const Layout& L, T* const* comps, int ncomp, cudaStream_t s);
-// laser pulse added to E2, E3, B2, B3; p: vosc, k, w0, rise, length, fall,
-// x_front, axis x2, axis x3, cos pol, sin pol, phase, xmin[3], dx[3]
+// laser pulse added to the fields; p: vosc, k, w0, rise, length, fall,
+// x_front, transverse axis position (in-plane), axis x3, cos pol, sin pol,
+// phase, xmin[3], dx[3], propagation axis (0: x1, 1: x2), focus on, x_focus
 template <typename T> void laser_add(const Layout& L, T* const* f, const double* p, cudaStream_t s);
 template <typename T>
 void gauss_residual(const Layout& L, T* const* e, const double* rho, double rho_bg, const double dx[3], Diag64* acc,

@@ -40,7 +40,7 @@ def test_struct_layouts_match_header(capi, tmp_path):
     import subprocess
     prog = tmp_path / "layout.c"
     fields = {"pic_grid": capi.PicGrid, "pic_species": capi.PicSpecies, "pic_diag_t": capi.PicDiag,
-              "pic_allocator": capi.PicAllocator, "pic_tune_choice": capi.PicTuneChoice}
+              "pic_allocator": capi.PicAllocator, "pic_tune_choice": capi.PicTuneChoice, "pic_laser": capi.PicLaser}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "pic.h"', "int main(void) {"]
     for cname, cls in fields.items():
         lines.append(f'  printf("{cname} %zu\\n", sizeof({cname}));')

@@ -1,7 +1,8 @@
 """GPU parity of the moving window and the laser set-up against the oracle.
 
-* pic_laser_add: E2, E3, B2, B3 of the pulse equal the oracle's laser_fields
-  (FP64 form to 1e-12, FP32 form to 1e-6 of the peak: one rounding).
+* pic_laser_add: the fields of pulses moving in x1 and x2, with and without a
+  focal plane, in 2D and 3D, equal the oracle's laser_fields (FP64 form to
+  1e-12, FP32 form to 1e-6 of the peak: one rounding).
 * A 2D run with the window moving at c, a laser pulse and a warm plasma: after
   20 steps (about 14 one-cell shifts) the shift count, the set of surviving
   particles (ids: the back columns dropped, the injected ones continuing the
@@ -20,16 +21,25 @@ pytestmark = pytest.mark.gpu
 NAMES = ["E1", "E2", "E3", "B1", "B2", "B3"]
 
 
+@pytest.mark.parametrize("ndim", [2, 3])
+@pytest.mark.parametrize("wavetype,focus", [(1, None), (2, None), (1, 3.0), (2, -4.0)])
 @pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32", 1e-6)])
-def test_laser_setup_matches_oracle(prec, tol):
+def test_laser_setup_matches_oracle(prec, tol, wavetype, focus, ndim):
     import paper_1503_00276_gb300 as pg
-    dx = (0.1, 0.2, 1.0)
-    g = workload.Grid(ndim=2, nx=(128, 32, 1), dx=dx, dt=workload.courant_dt(dx, 2))
+    if ndim == 2:
+        dx = (0.1, 0.2, 1.0)
+        g = workload.Grid(ndim=2, nx=(128, 32, 1), dx=dx, dt=workload.courant_dt(dx, 2))
+        tile = (32, 16)
+    else:
+        dx = (0.1, 0.2, 0.2)
+        g = workload.Grid(ndim=3, nx=(64, 32, 16), dx=dx, dt=workload.courant_dt(dx, 3))
+        tile = (8, 8, 8)
     las = workload.Laser(vosc=2.0, rkkp=10.0, w0=1.5, rise=1.5, length=0.5, fall=1.5, start=2.0, pol=30.0,
-                         phase=0.3, offset=(0.4, 0.0))
-    sim = pg.Simulation(g, [], precision=prec, tile=(32, 16) if prec == "fp32" else None)
+                         phase=0.3, offset=(0.4, -0.2), wavetype=wavetype, focus=focus)
+    sim = pg.Simulation(g, [], precision=prec, tile=tile if prec == "fp32" else None)
     sim.add_laser(las)
     ref = oracle.laser_fields(g, las)
+    assert max(np.max(np.abs(r)) for r in ref) > 1.0  # the pulse lies in the box
     for c, name in enumerate(NAMES):
         m = max(np.max(np.abs(ref[c])), 1e-300)
         assert np.max(np.abs(sim.fields(name) - ref[c])) <= tol * max(m, 1.0), name

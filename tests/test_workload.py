@@ -72,3 +72,14 @@ def test_config4_scan_draws():
     # uneven sizes: several distinct grids and particle counts
     assert len({g.nx for g, _ in sims}) > 8
     assert len({workload.n_particles(g, s[0]) for g, s in sims}) > 8
+
+
+def test_config1_pulse_intensity_fwhm_is_the_stated_duration():
+    """The 2D wakefield stand-in's pulse: intensity (envelope squared) full width
+    at half maximum 1.5 with the thesis' polynomial rise and fall."""
+    import oracle
+    _, _, las, _ = workload.config1()
+    xi = np.linspace(0.0, las.rise + las.length + las.fall, 200001)
+    inten = oracle.laser_envelope(xi, las.rise, las.length, las.fall) ** 2
+    above = xi[inten >= 0.5]
+    assert abs((above[-1] - above[0]) - 1.5) < 2e-3

@@ -112,12 +112,14 @@ class Species:
 
 @dataclass
 class Laser:
-    """A pulse propagating in +x1 (the thesis' pulse section, wavetype 1):
+    """A pulse (the thesis' pulse section): wavetype 1 moves in +x1, 2 in +x2;
     vosc = peak normalised vector potential a0, rkkp = wavenumber k (= omega0
     / omega_p), w0 = spot size, rise / length / fall = envelope distances,
-    start = distance of the pulse front from the +x1 side of the box,
-    pol = polarisation angle in degrees from x2 towards x3, phase, offset =
-    transverse offset of the axis from the box centre."""
+    start = distance of the pulse front from the side of the box it moves
+    towards, pol = polarisation angle in degrees from the in-plane transverse
+    axis towards x3, phase, offset = transverse offset of the axis from the box
+    centre, focus = distance of the focal plane from that side (None: the
+    waist profile everywhere)."""
     vosc: float = 1.0
     rkkp: float = 10.0
     w0: float = 4.0
@@ -128,6 +130,8 @@ class Laser:
     pol: float = 0.0
     phase: float = 0.0
     offset: tuple = (0.0, 0.0)
+    wavetype: int = 1
+    focus: object = None
 
 
 def courant_dt(dx, ndim: int, frac: float = 0.99) -> float:
@@ -214,14 +218,15 @@ def config0(seed: int = 20001):
 def config1(seed: int = 20002):
     """2D3V laser wakefield: 2048 x 256 cells, dx1 = 0.05, dx2 = 0.2, 8 ppc (4 x 2)
     cold uniform electrons, window moving at c in x1, a pulse a0 = 2,
-    omega0/omega_p = 10, spot 4, polarised in x2, sin^2 rise and fall of 1.5
-    (the intensity FWHM duration 1.5 read as the envelope distances), front
-    1.0 behind the +x1 edge; 2000 steps.  The plasma fills the window from the
-    start (no vacuum gap: density profiles are not part of this hot path)."""
+    omega0/omega_p = 10, spot 4, polarised in x2, with the thesis' polynomial
+    rise and fall of 1.945 each: the intensity f^2 of the envelope then has a
+    full width at half maximum of 1.5 (the duration given); front 1.0 behind
+    the +x1 edge; 2000 steps.  The plasma fills the window from the start (no
+    vacuum gap: density profiles are not part of this hot path)."""
     dx = (0.05, 0.2, 1.0)
     g = Grid(ndim=2, nx=(2048, 256, 1), dx=dx, dt=courant_dt(dx, 2), move_window=True)
     s = Species(rqm=-1.0, ppc=(4, 2, 1), uth=(0.0, 0.0, 0.0), seed=seed)
-    las = Laser(vosc=2.0, rkkp=10.0, w0=4.0, rise=1.5, length=0.0, fall=1.5, start=1.0)
+    las = Laser(vosc=2.0, rkkp=10.0, w0=4.0, rise=1.945, length=0.0, fall=1.945, start=1.0)
     return g, [s], las, 2000
 
 

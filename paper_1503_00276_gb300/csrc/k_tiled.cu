@@ -370,6 +370,31 @@ __device__ inline void flush_warp(float* J, bool act, int cell, const float (&w)
   }
 }
 
+// Before the end-of-chunk flush (all lanes of the warp call it): the lanes hold
+// runs in cell order, so neighbouring lanes often end on the same cell (at 8
+// particles per cell and 2 per thread, about four lanes per cell), and their
+// shared-memory adds would all hit the same 12 words.  Aligned pairs, then
+// aligned quads, of lanes on one cell are summed into the lower lane; the
+// upper one is emptied.
+template <int NDIM>
+__device__ inline void acc_merge_pairs(Acc& a) {
+  constexpr unsigned kFull = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int s = 1; s <= 2; s <<= 1) {
+    const int up = __shfl_down_sync(kFull, a.cell, s);    // cell of lane + s
+    const int down = __shfl_up_sync(kFull, a.cell, s);    // cell of lane - s
+    const bool take = (lane & (2 * s - 1)) == 0 && a.cell >= 0 && up == a.cell;
+    const bool give = (lane & (2 * s - 1)) == s && a.cell >= 0 && down == a.cell;
+#pragma unroll
+    for (int k = 0; k < (NDIM == 3 ? 12 : 8); ++k) {
+      const float v = __shfl_down_sync(kFull, a.w[k], s);
+      if (take) a.w[k] += v;
+    }
+    if (give) a.cell = -1;
+  }
+}
+
 // acc_flush for a whole warp (all lanes call it)
 template <int NDIM, int TX, int TY, int TZ>
 __device__ inline void acc_flush_warp(float* J, Acc& a) {
@@ -1056,10 +1081,12 @@ __device__ inline bool sort_tile(const TileArgs& A, const CUtensorMap* fmap, con
       for (int r = 0; r < kPPT; ++r)
         key[r] = r < nvalid ? push_one<NDIM, TX, TY, TZ>(F, J, A, pp[r], acc, Q, misc + 1)
                             : Geo<NDIM, TX, TY, TZ>::NK;
-      if (dense)
+      if (dense) {
         acc_flush_warp<NDIM, TX, TY, TZ>(J, acc);
-      else
+      } else {
+        acc_merge_pairs<NDIM>(acc);
         acc_flush<NDIM, TX, TY, TZ>(J, acc);
+      }
     }
     int nq;  // the same value in every thread
     if constexpr (SORT) {

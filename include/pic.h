@@ -110,7 +110,8 @@ typedef struct {
   pic_precision precision;
   int tile[3];              /* PIC_FP32_CELLOFF tile size in cells (0 = default:
                                2D 32x16, 3D 8x8x8); nx must be a multiple */
-  double slack;             /* per-tile storage slack fraction (0 = default 0.25) */
+  double slack;             /* per-tile storage slack fraction (0 = default: 0.25, or
+                               0.75 with a moving window) */
   int sort_period;          /* PIC_FP32_CELLOFF: every sort_period-th step re-sorts each
                                tile by cell; the steps between update particles in
                                place (0 = default 1: sort every step) */

@@ -408,8 +408,12 @@ pic_status bin_flat(pic_sim* S, SpeciesState& sp, Flat32& flat, long long n) {
     const long long c = hc[t];
     long long res = std::max<long long>(32, (long long)std::ceil(0.5 * sp.slack * nbmax[t]));
     if (S->moving) {
+      // a shift step brings the first cell column of the tile ahead; the
+      // front tile column gets the fresh plasma of the new front cells instead
       const int ix = t % ntd[0];
-      const long long ahead = ix + 1 < ntd[0] ? hc[t + 1] : 0;
+      const long long lattice = (long long)sp.ppc[0] * sp.ppc[1] * sp.ppc[2] * S->T[0] * S->T[1] *
+                                (S->ndim == 3 ? S->T[2] : 1);
+      const long long ahead = ix + 1 < ntd[0] ? hc[t + 1] : lattice;
       res = std::max<long long>(res, (long long)std::ceil(1.25 * ahead / S->T[0]) + 32);
     }
     res = (res + 3) / 4 * 4;  // a multiple of 4, so that the stayer part ends 16-byte aligned
@@ -1028,7 +1032,8 @@ pic_status init_sim(const pic_grid* grid, const pic_species* species, int nspeci
     S->al.user = *alloc;
     S->al.has_user = true;
   }
-  S->slack = grid->slack > 0.0 ? grid->slack : 0.25;
+  // a moving window compresses and drags plasma through the tiles: more growth room
+  S->slack = grid->slack > 0.0 ? grid->slack : (grid->move_window ? 0.75 : 0.25);
   S->sort_period = grid->sort_period > 0 ? grid->sort_period : 1;
   int nxv[3] = {grid->nx[0], grid->nx[1], grid->ndim == 3 ? grid->nx[2] : 1};
   S->L = make_layout(S->ndim, nxv);

@@ -62,7 +62,7 @@ class OraGrid(C.Structure):
 
 class OraSpecies(C.Structure):
     _fields_ = [("rqm", C.c_double), ("q", C.c_double), ("n", C.c_longlong),
-                ("x", C.POINTER(C.c_double)), ("u", C.POINTER(C.c_double))]
+                ("x", C.POINTER(C.c_double)), ("u", C.POINTER(C.c_double)), ("w", C.POINTER(C.c_double))]
 
 
 _DP = C.POINTER(C.c_double)
@@ -135,7 +135,7 @@ def make_grid(g) -> OraGrid:
 class State:
     """Oracle simulation state: six field arrays, three current arrays, species."""
 
-    def __init__(self, grid, species_list, xs, us, charges, fields=None):
+    def __init__(self, grid, species_list, xs, us, charges, fields=None, weights=None, ids=None, created=None):
         self.grid = grid
         self.species = list(species_list)
         if getattr(grid, "deposit", "vb") == "isis" and grid.ndim != 2:
@@ -144,8 +144,16 @@ class State:
         self.nstep = 0
         self.shifts = 0
         # particle ids (initial generator index; injected particles continue it)
-        self.ids = [np.arange(np.asarray(x).shape[0], dtype=np.int64) for x in xs]
-        self.created = [np.asarray(x).shape[0] for x in xs]
+        self.ids = [np.arange(np.asarray(x).shape[0], dtype=np.int64) if ids is None or ids[s] is None
+                    else np.asarray(ids[s], dtype=np.int64).copy() for s, x in enumerate(xs)]
+        # particles ever created, counting the lattice places a profile skipped:
+        # the id and draw index of the next injected particle
+        self.created = [int(created[s]) if created is not None else
+                        (np.asarray(xs[s]).shape[0] if ids is None or ids[s] is None
+                         else (int(self.ids[s][-1]) + 1 if self.ids[s].size else 0)) for s in range(len(xs))]
+        # per-particle charge weights (density profile); None: all 1
+        self.w = [None if weights is None or weights[s] is None
+                  else np.ascontiguousarray(weights[s], dtype=np.float64).copy() for s in range(len(xs))]
         shape = (int(grid.nx[2]), int(grid.nx[1]), int(grid.nx[0]))
         self.fld = [np.zeros(shape) if fields is None else np.ascontiguousarray(fields[c], dtype=np.float64).copy()
                     for c in range(6)]
@@ -167,6 +175,7 @@ class State:
             self._sp[i].n = self.x[i].shape[0]
             self._sp[i].x = _dp(self.x[i])
             self._sp[i].u = _dp(self.u[i])
+            self._sp[i].w = _dp(self.w[i]) if self.w[i] is not None else None
 
     @property
     def nsp(self):
@@ -202,6 +211,8 @@ class State:
                 self.x[s] = np.ascontiguousarray(self.x[s][keep])
                 self.u[s] = np.ascontiguousarray(self.u[s][keep])
                 self.ids[s] = self.ids[s][keep]
+                if self.w[s] is not None:
+                    self.w[s] = np.ascontiguousarray(self.w[s][keep])
         self._refresh()
         self.smooth_current()
         self.field_solve()
@@ -214,11 +225,18 @@ class State:
             import workload
             for s in range(self.nsp):
                 gx = dataclasses.replace(g, xmin=(lo, g.xmin[1], g.xmin[2]))
-                xn, un = workload.inject_column(gx, self.species[s], lo, self.created[s])
+                sp = self.species[s]
+                xn, un = workload.inject_column(gx, sp, lo, self.created[s])
+                idn = self.created[s] + np.arange(xn.shape[0])
+                self.created[s] += xn.shape[0]
+                wn = workload.profile_weight(sp, xn)  # the profile at the lab-frame positions
+                if wn is not None:
+                    keep = sp.density * wn > sp.den_min
+                    xn, un, wn, idn = xn[keep], un[keep], wn[keep], idn[keep]
+                    self.w[s] = np.ascontiguousarray(np.concatenate([self.w[s], wn]))
                 self.x[s] = np.ascontiguousarray(np.concatenate([self.x[s], xn]))
                 self.u[s] = np.ascontiguousarray(np.concatenate([self.u[s], un]))
-                self.ids[s] = np.concatenate([self.ids[s], self.created[s] + np.arange(xn.shape[0])])
-                self.created[s] += xn.shape[0]
+                self.ids[s] = np.concatenate([self.ids[s], idn])
             self._refresh()
         self.nstep += 1
 
@@ -255,13 +273,21 @@ class State:
 def from_workload(grid, species_list, fields=None, index=None):
     """Oracle state loaded from the seeded generator (all particles, or ``index``)."""
     import workload
-    xs, us, qs = [], [], []
+    xs, us, qs, ws, ids, created = [], [], [], [], [], []
     for s in species_list:
-        x, u = workload.load_particles(grid, s, index)
+        if s.profile is not None:
+            assert index is None, "a density profile needs the whole lattice"
+            x, u, w, idx = workload.load_weighted(grid, s)
+        else:
+            x, u = workload.load_particles(grid, s, index)
+            w, idx = None, None
         xs.append(x)
         us.append(u)
+        ws.append(w)
+        ids.append(idx)
+        created.append(workload.n_particles(grid, s) if index is None else x.shape[0])
         qs.append(workload.macro_charge(grid, s))
-    st = State(grid, species_list, xs, us, qs, fields)
+    st = State(grid, species_list, xs, us, qs, fields, weights=ws, ids=ids, created=created)
     if grid.init_e_gauss_x1:
         st.init_e_gauss_x1()
     return st

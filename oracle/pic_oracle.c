@@ -368,8 +368,14 @@ void ora_deposit_isis(const ora_grid* g, double* cur[3], const double xold[3], c
 /* ------------------------------------------------------------------------ */
 
 void ora_deposit_rho(const ora_grid* g, double* rho, const double* x, long long n, double q) {
+  ora_deposit_rho_w(g, rho, x, NULL, n, q);
+}
+
+/* the same with per-particle charge weights w[p] (NULL: all 1) */
+void ora_deposit_rho_w(const ora_grid* g, double* rho, const double* x, const double* wt, long long n, double q0) {
   double dvol = cell_volume(g);
   for (long long p = 0; p < n; ++p) {
+    const double q = wt ? q0 * wt[p] : q0;
     long i[3] = {0, 0, 0};
     double e[3] = {0, 0, 0};
     for (int d = 0; d < g->ndim; ++d) {
@@ -506,9 +512,9 @@ void ora_particle_phase(const ora_grid* g, double* const fld[6], double* cur[3],
       double xold[3] = {x[0], x[1], x[2]};
       ora_advance_particle(g, fld, sp[s].rqm, x, u);
       if (g->isis)
-        ora_deposit_isis(g, cur, xold, x, u[2] / ora_gamma(u), sp[s].q);
+        ora_deposit_isis(g, cur, xold, x, u[2] / ora_gamma(u), sp[s].w ? sp[s].q * sp[s].w[p] : sp[s].q);
       else
-        ora_deposit_vb(g, cur, xold, x, u[2] / ora_gamma(u), sp[s].q);
+        ora_deposit_vb(g, cur, xold, x, u[2] / ora_gamma(u), sp[s].w ? sp[s].q * sp[s].w[p] : sp[s].q);
       ora_wrap(g, x);
     }
   }
@@ -531,7 +537,7 @@ void ora_step(const ora_grid* g, double* const fld[6], double* cur[3], const ora
 void ora_rho(const ora_grid* g, const ora_species* sp, int nsp, double* rho) {
   long n = (long)g->nx[0] * g->nx[1] * g->nx[2];
   for (long c = 0; c < n; ++c) rho[c] = g->rho_bg;
-  for (int s = 0; s < nsp; ++s) ora_deposit_rho(g, rho, sp[s].x, sp[s].n, sp[s].q);
+  for (int s = 0; s < nsp; ++s) ora_deposit_rho_w(g, rho, sp[s].x, sp[s].w, sp[s].n, sp[s].q);
 }
 
 /* max over nodes of |div E - rho|, div E by backward differences of the staggered E */
@@ -565,7 +571,8 @@ double ora_field_energy(const ora_grid* g, double* const fld[6]) {
 double ora_kinetic_energy(const ora_species* sp, int nsp) {
   double s = 0.0;
   for (int k = 0; k < nsp; ++k)
-    for (long long p = 0; p < sp[k].n; ++p) s = s + sp[k].q * sp[k].rqm * (ora_gamma(sp[k].u + 3 * p) - 1.0);
+    for (long long p = 0; p < sp[k].n; ++p)
+      s = s + (sp[k].w ? sp[k].q * sp[k].w[p] : sp[k].q) * sp[k].rqm * (ora_gamma(sp[k].u + 3 * p) - 1.0);
   return s;
 }
 

@@ -32,6 +32,8 @@ typedef struct {
   long long n;
   double* x;         /* [n][3] global positions */
   double* u;         /* [n][3] momenta p/(m c) */
+  const double* w;   /* [n] charge weights (density profile), NULL: all 1;
+                        particle p carries charge q w[p] */
 } ora_species;
 
 void ora_gather(const ora_grid* g, double* const fld[6], const double x[3], double eb[6]);
@@ -44,6 +46,7 @@ void ora_deposit_vb(const ora_grid* g, double* cur[3], const double xold[3], con
 void ora_deposit_isis(const ora_grid* g, double* cur[3], const double xold[3], const double xnew[3], double v3,
                       double q);
 void ora_deposit_rho(const ora_grid* g, double* rho, const double* x, long long n, double q);
+void ora_deposit_rho_w(const ora_grid* g, double* rho, const double* x, const double* w, long long n, double q);
 void ora_smooth(const ora_grid* g, double* f);
 void ora_field_solve(const ora_grid* g, double* const fld[6], double* const cur[3]);
 void ora_advance_particle(const ora_grid* g, double* const fld[6], double rqm, double x[3], double u[3]);

@@ -104,6 +104,13 @@ class Species:
     # giving density ~ 1 + delta sin(k x1) to first order
     perturb_delta: float = 0.0
     perturb_k: float = 0.0
+    # density profile (nl_num_x / nl_profile): per direction None or (x points,
+    # f values) of a piecewise-linear function, constant beyond its ends; the
+    # density is density * prod_d f_d(x_d).  A particle's charge is scaled by
+    # the profile at its initial position; no particle is created where the
+    # density is not above den_min.
+    profile: tuple = None
+    den_min: float = 0.0
 
     @property
     def ppc_total(self) -> int:
@@ -147,6 +154,34 @@ def macro_charge(grid: Grid, sp: Species) -> float:
 
 def n_particles(grid: Grid, sp: Species) -> int:
     return grid.ncells * sp.ppc_total
+
+
+def profile_weight(sp: Species, x):
+    """Product of the piecewise-linear profile functions at positions x[n,3]
+    (1 where a direction has none); None for a species without a profile."""
+    if sp.profile is None:
+        return None
+    x = np.asarray(x, dtype=np.float64)
+    w = np.ones(x.shape[0])
+    for d, prof in enumerate(sp.profile):
+        if prof is None:
+            continue
+        xs, fs = (np.asarray(v, dtype=np.float64) for v in prof)
+        w = w * np.interp(x[:, d], xs, fs)
+    return w
+
+
+def load_weighted(grid: Grid, sp: Species):
+    """The loader with the density profile applied: (x, u, w, ids) of the
+    particles that are created (density * w > den_min), ids = their lattice
+    indices.  w is None for a species without a profile (all of them kept)."""
+    x, u = load_particles(grid, sp)
+    w = profile_weight(sp, x)
+    ids = np.arange(x.shape[0], dtype=np.int64)
+    if w is None:
+        return x, u, None, ids
+    keep = sp.density * w > sp.den_min
+    return np.ascontiguousarray(x[keep]), np.ascontiguousarray(u[keep]), np.ascontiguousarray(w[keep]), ids[keep]
 
 
 def load_particles(grid: Grid, sp: Species, index=None):

@@ -159,6 +159,20 @@ typedef struct {
   long long np_max;         /* storage limit in particles (0 = no limit) */
   int track_ids;            /* 1: keep an int32 particle id (lattice index or explicit
                                row) alongside each particle, for pic_particle_ids */
+  /* Density profile (nl_num_x / nl_profile), lattice species only: per
+   * direction prof_n[d] points (0 = flat) at prof_x[d][0..n-1] (ascending) with
+   * values prof_f[d][...]; the density is `density` times the product of the
+   * piecewise-linear functions (constant beyond the end points).  Each
+   * particle's charge is q times the profile at its initial position (for a
+   * moving window, at the lab-frame position where it is injected); no
+   * particle is created where density times the profile is not above den_min.
+   * Host arrays, copied during pic_init. */
+  int prof_n[3];
+  const double* prof_x[3];
+  const double* prof_f[3];
+  double den_min;
+  const double* w0;         /* explicit species: per-particle charge weights (n_explicit
+                               values; NULL = all 1) */
 } pic_species;
 
 typedef struct pic_sim pic_sim;   /* opaque; owns all device state */
@@ -210,6 +224,12 @@ pic_status pic_particles(pic_sim* sim, int species, double* x, double* u, long l
 /* Particle ids (species with track_ids) in the same order as pic_particles. */
 pic_status pic_particle_ids(pic_sim* sim, int species, int* ids, long long cap, long long* n_out,
                             int dst_on_device);
+
+/* Charge weights of a species' particles (1 without a profile or explicit
+ * weights), in the order of pic_particles / pic_particle_ids; same arguments
+ * and errors as pic_particle_ids. */
+pic_status pic_particle_weights(pic_sim* S, int species, double* w, long long cap, long long* n_out,
+                                int dst_on_device);
 
 /* Number of tiles of the PIC_FP32_CELLOFF store and the particle count of each
  * (tiles in x1-fastest order), host array of ntiles entries. */

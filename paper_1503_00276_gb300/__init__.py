@@ -93,9 +93,21 @@ def _species_struct(sp, explicit=None, track_ids=False, np_max=0):
     s.seed = int(getattr(sp, "seed", 0)) & 0xFFFFFFFFFFFFFFFF
     s.track_ids = int(bool(track_ids))
     s.np_max = int(np_max)
-    keep = None
+    keep = []
+    prof = getattr(sp, "profile", None)
+    if explicit is None and prof is not None:
+        for d, pd in enumerate(prof):
+            if pd is None:
+                continue
+            xs, fs = (np.ascontiguousarray(v, dtype=np.float64) for v in pd)
+            assert xs.shape == fs.shape and xs.ndim == 1 and xs.size > 0
+            s.prof_n[d] = xs.size
+            s.prof_x[d] = xs.ctypes.data_as(C.POINTER(C.c_double))
+            s.prof_f[d] = fs.ctypes.data_as(C.POINTER(C.c_double))
+            keep += [xs, fs]
+        s.den_min = float(getattr(sp, "den_min", 0.0))
     if explicit is not None:
-        x, u, q = explicit
+        x, u, q = explicit[:3]
         x = np.ascontiguousarray(x, dtype=np.float64)
         u = np.ascontiguousarray(u, dtype=np.float64)
         assert x.shape == u.shape and x.ndim == 2 and x.shape[1] == 3
@@ -103,7 +115,12 @@ def _species_struct(sp, explicit=None, track_ids=False, np_max=0):
         s.x0 = x.ctypes.data_as(C.POINTER(C.c_double))
         s.u0 = u.ctypes.data_as(C.POINTER(C.c_double))
         s.q_explicit = float(q)
-        keep = (x, u)
+        keep += [x, u]
+        if len(explicit) > 3 and explicit[3] is not None:  # per-particle charge weights
+            w = np.ascontiguousarray(explicit[3], dtype=np.float64)
+            assert w.shape == (x.shape[0],)
+            s.w0 = w.ctypes.data_as(C.POINTER(C.c_double))
+            keep.append(w)
     return s, keep
 
 
@@ -113,8 +130,9 @@ class Simulation:
     grid / species: objects with the attributes of ``pic_grid`` / ``pic_species``
     (ndim, nx, dx, xmin, dt, e0, b0, smooth_level, smooth_w, rho_bg,
     init_e_gauss_x1 / rqm, ppc, uth, ufl, density, seed).  ``explicit``: optional
-    list, per species, of (x[n,3], u[n,3], q) host arrays that replace the lattice
-    loader.  ``precision``: "fp64" (plain form) or "fp32" (cell-offset tiled form).
+    list, per species, of (x[n,3], u[n,3], q[, w[n]]) host arrays that replace the
+    lattice loader (w: per-particle charge weights).  A species' ``profile`` /
+    ``den_min`` (see ``workload.Species``) give its density profile.  ``precision``: "fp64" (plain form) or "fp32" (cell-offset tiled form).
     """
 
     def __init__(self, grid, species, precision="fp64", explicit=None, tile=None, track_ids=False, slack=0.0,
@@ -285,6 +303,15 @@ class Simulation:
         got = C.c_longlong()
         check(self._lib.pic_particle_ids(self._h, species, out.ctypes.data_as(C.c_void_p), n, C.byref(got), 0),
               "pic_particle_ids")
+        return out
+
+    def weights(self, species: int = 0) -> np.ndarray:
+        """pic_particle_weights: charge weight of each particle (1 without a profile)."""
+        n = self.n_particles(species)
+        out = np.empty(n, dtype=np.float64)
+        got = C.c_longlong()
+        check(self._lib.pic_particle_weights(self._h, species, out.ctypes.data_as(C.c_void_p), n, C.byref(got), 0),
+              "pic_particle_weights")
         return out
 
     def tile_counts(self, species: int = 0) -> np.ndarray:

@@ -37,7 +37,9 @@ class PicSpecies(C.Structure):
     _fields_ = [("rqm", C.c_double), ("ppc", C.c_int * 3), ("uth", C.c_double * 3), ("ufl", C.c_double * 3),
                 ("density", C.c_double), ("seed", C.c_ulonglong), ("n_explicit", C.c_longlong),
                 ("x0", C.POINTER(C.c_double)), ("u0", C.POINTER(C.c_double)), ("q_explicit", C.c_double),
-                ("np_max", C.c_longlong), ("track_ids", C.c_int)]
+                ("np_max", C.c_longlong), ("track_ids", C.c_int), ("prof_n", C.c_int * 3),
+                ("prof_x", C.POINTER(C.c_double) * 3), ("prof_f", C.POINTER(C.c_double) * 3), ("den_min", C.c_double),
+                ("w0", C.POINTER(C.c_double))]
 
 
 class PicLaser(C.Structure):
@@ -69,6 +71,7 @@ PROTOTYPES = {
     "pic_set_field": (C.c_int, [_P, C.c_int, _P, C.c_size_t, C.c_int]),
     "pic_particles": (C.c_int, [_P, C.c_int, _P, _P, C.c_longlong, C.POINTER(C.c_longlong), C.c_int]),
     "pic_particle_ids": (C.c_int, [_P, C.c_int, _P, C.c_longlong, C.POINTER(C.c_longlong), C.c_int]),
+    "pic_particle_weights": (C.c_int, [_P, C.c_int, _P, C.c_longlong, C.POINTER(C.c_longlong), C.c_int]),
     "pic_tile_counts": (C.c_int, [_P, C.c_int, C.POINTER(C.c_longlong), C.c_longlong, C.POINTER(C.c_longlong)]),
     "pic_diag": (C.c_int, [_P, C.POINTER(PicDiag)]),
     "pic_timing_enable": (C.c_int, [_P, C.c_int]),

@@ -50,6 +50,12 @@ __global__ void k_check_box(int ndim, PushConst C, const double* x0, const doubl
   }
 }
 
+// FP32 weights to FP64 (null: all 1)
+__global__ void k_widen(const float* w, double* out, long long n) {
+  const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < n) out[k] = w ? (double)w[k] : 1.0;
+}
+
 struct StatusWord {  // status bits of every kernel of one simulation (ST_*); spill counts are per species
   int status;
   int pad;
@@ -118,6 +124,12 @@ struct SpeciesState {
   int* d_spill = nullptr;   // records in this species' spill list
   SliceScratch slices{};    // work items of the tile kernel (heavy tiles split)
   double slack = 0.25;      // region growth room; raised after each spill
+  // density profile / explicit weights: per-particle charge weights
+  bool weighted = false;
+  bool has_prof = false;
+  ProfileDev prof{};        // device copy of the profile tables (lattice species)
+  double* prof_mem = nullptr;
+  int* d_kept = nullptr;    // particles the last injection created
 };
 
 constexpr int kTimingSlots = 5;
@@ -309,7 +321,7 @@ pic_status make_maps(pic_sim* S) {
 }
 
 // ------------------------------------------------------------- tiled store
-Part32 alloc_part(pic_sim* S, long long slots, bool ids, bool& ok) {
+Part32 alloc_part(pic_sim* S, long long slots, bool ids, bool& ok, bool weights = false) {
   Part32 p{};
   p.cell = (uint32_t*)S->al.get(4 * (size_t)slots);
   for (int d = 0; d < 3; ++d) {
@@ -318,7 +330,9 @@ Part32 alloc_part(pic_sim* S, long long slots, bool ids, bool& ok) {
   }
   if (S->ndim == 2) p.o[2] = nullptr;
   p.id = ids ? (int*)S->al.get(4 * (size_t)slots) : nullptr;
-  ok = p.cell && p.o[0] && p.o[1] && (S->ndim == 2 || p.o[2]) && p.u[0] && p.u[1] && p.u[2] && (!ids || p.id);
+  p.w = weights ? (float*)S->al.get(4 * (size_t)slots) : nullptr;
+  ok = p.cell && p.o[0] && p.o[1] && (S->ndim == 2 || p.o[2]) && p.u[0] && p.u[1] && p.u[2] && (!ids || p.id) &&
+       (!weights || p.w);
   return p;
 }
 
@@ -329,10 +343,11 @@ void free_part(pic_sim* S, Part32& p) {
     S->al.put(p.u[d]);
   }
   S->al.put(p.id);
+  S->al.put(p.w);
   p = Part32{};
 }
 
-Flat32 alloc_flat(pic_sim* S, long long n, bool ids, bool& ok) {
+Flat32 alloc_flat(pic_sim* S, long long n, bool ids, bool& ok, bool weights = false) {
   Flat32 f{};
   size_t m = (size_t)std::max<long long>(n, 1);
   f.tile = (int*)S->al.get(4 * m);
@@ -342,7 +357,9 @@ Flat32 alloc_flat(pic_sim* S, long long n, bool ids, bool& ok) {
     f.u[d] = (float*)S->al.get(4 * m);
   }
   f.id = ids ? (int*)S->al.get(4 * m) : nullptr;
-  ok = f.tile && f.cell && f.o[0] && f.o[1] && f.o[2] && f.u[0] && f.u[1] && f.u[2] && (!ids || f.id);
+  f.w = weights ? (float*)S->al.get(4 * m) : nullptr;
+  ok = f.tile && f.cell && f.o[0] && f.o[1] && f.o[2] && f.u[0] && f.u[1] && f.u[2] && (!ids || f.id) &&
+       (!weights || f.w);
   return f;
 }
 
@@ -354,6 +371,7 @@ void free_flat(pic_sim* S, Flat32& f) {
     S->al.put(f.u[d]);
   }
   S->al.put(f.id);
+  S->al.put(f.w);
   f = Flat32{};
 }
 
@@ -433,8 +451,8 @@ pic_status bin_flat(pic_sim* S, SpeciesState& sp, Flat32& flat, long long n) {
   if (slots > sp.slots) {
     for (int b = 0; b < 2; ++b) free_part(S, sp.side[b].p);
     bool ok0, ok1;
-    sp.side[0].p = alloc_part(S, slots, sp.ids, ok0);
-    sp.side[1].p = alloc_part(S, slots, sp.ids, ok1);
+    sp.side[0].p = alloc_part(S, slots, sp.ids, ok0, sp.weighted);
+    sp.side[1].p = alloc_part(S, slots, sp.ids, ok1, sp.weighted);
     if (!ok0 || !ok1) {
       S->al.put(counts);
       set_error("out of device memory (particle store of " + std::to_string(slots) + " slots)");
@@ -453,8 +471,14 @@ pic_status bin_flat(pic_sim* S, SpeciesState& sp, Flat32& flat, long long n) {
   }
   long long max_cap = 0;
   for (int t = 0; t < nt; ++t) max_cap = std::max<long long>(max_cap, hcap[t]);
-  sp.tg.small = !S->no_small && tiled_has_small(S->ndim, S->T) &&
+  sp.tg.small = !S->no_small && !sp.weighted && tiled_has_small(S->ndim, S->T) &&
                 (max_cap <= tiled_small_capacity() || !tiled_has_general(S->ndim, S->T));
+  if (!sp.tg.small && !tiled_has_general(S->ndim, S->T)) {
+    S->al.put(counts);
+    set_error("this tile shape has only the small-tile kernel, which a moving window, a batch member or a "
+              "species with charge weights does not use (or a tile holds too many particles for it)");
+    return PIC_EUNSUPPORTED;
+  }
   sp.grid = tiled_push_grid(S->ndim, S->T, nt, sp.tg.small != 0, S->minb);
   cudaMemcpyAsync(sp.tg.cap, hcap.data(), 4 * (size_t)nt, cudaMemcpyHostToDevice, S->s);
   cudaMemcpyAsync(sp.tg.res, hres.data(), 4 * (size_t)nt, cudaMemcpyHostToDevice, S->s);
@@ -501,7 +525,7 @@ pic_status flatten(pic_sim* S, SpeciesState& sp, Flat32& flat, long long& n, boo
   const long long nstore = last_off + last_cnt;
   n = nstore + (include_spill ? spill_n : 0);
   bool ok = true;
-  flat = alloc_flat(S, n, sp.ids, ok);
+  flat = alloc_flat(S, n, sp.ids, ok, sp.weighted);
   allocated = true;
   if (!ok) {
     S->al.put(tot);
@@ -524,6 +548,7 @@ pic_status flatten(pic_sim* S, SpeciesState& sp, Flat32& flat, long long& n, boo
       cp(flat.u[d], sp.spill.u[d]);
     }
     if (flat.id && sp.spill.id) cp(flat.id, sp.spill.id);
+    if (flat.w && sp.spill.w) cp(flat.w, sp.spill.w);
   }
   cudaError_t e = cudaStreamSynchronize(S->s);
   S->al.put(tot);
@@ -622,11 +647,69 @@ pic_status load_species(pic_sim* S, const pic_species& in, SpeciesState& sp) {
     sp.q = sign * in.density * dvol / (double)ppc;
   sp.n = n;
 
-  // FP64 SoA of the initial state, in chunks (device)
-  const long long chunk = S->prec == PIC_FP64_PLAIN ? std::max<long long>(n, 1) : std::min<long long>(n, 1ll << 25);
+  // density profile (lattice species) or explicit weights: per-particle charge weights
+  sp.has_prof = false;
+  sp.prof = ProfileDev{};
+  if (in.n_explicit <= 0) {
+    size_t tot = 0;
+    for (int d = 0; d < nd; ++d) {
+      const int np = in.prof_n[d];
+      if (np <= 0) continue;
+      if (!in.prof_x[d] || !in.prof_f[d]) {
+        set_error("density profile: prof_x / prof_f missing");
+        return PIC_EINVAL;
+      }
+      for (int k = 0; k < np; ++k)
+        if (!std::isfinite(in.prof_x[d][k]) || !std::isfinite(in.prof_f[d][k]) || in.prof_f[d][k] < 0.0 ||
+            (k > 0 && !(in.prof_x[d][k] >= in.prof_x[d][k - 1]))) {
+          set_error("density profile: points must be finite and ascending, values >= 0");
+          return PIC_EINVAL;
+        }
+      tot += 2 * (size_t)np;
+    }
+    if (tot > 0) {
+      std::vector<double> h;
+      h.reserve(tot);
+      for (int d = 0; d < nd; ++d)
+        for (int a = 0; a < 2 && in.prof_n[d] > 0; ++a)
+          for (int k = 0; k < in.prof_n[d]; ++k) h.push_back(a == 0 ? in.prof_x[d][k] : in.prof_f[d][k]);
+      sp.prof_mem = (double*)S->al.get(8 * tot);
+      if (!sp.prof_mem) {
+        set_error("out of device memory (density profile)");
+        return PIC_ENOMEM;
+      }
+      cudaMemcpyAsync(sp.prof_mem, h.data(), 8 * tot, cudaMemcpyHostToDevice, S->s);
+      size_t o = 0;
+      for (int d = 0; d < nd; ++d) {
+        const int np = in.prof_n[d];
+        if (np <= 0) continue;
+        sp.prof.n[d] = np;
+        sp.prof.x[d] = sp.prof_mem + o;
+        sp.prof.f[d] = sp.prof_mem + o + np;
+        o += 2 * (size_t)np;
+      }
+      sp.prof.density = in.density;
+      sp.prof.den_min = in.den_min;
+      sp.has_prof = true;
+      cudaStreamSynchronize(S->s);
+    }
+  }
+  sp.weighted = sp.has_prof || (in.n_explicit > 0 && in.w0 != nullptr);
+  sp.created = n;  // lattice places (ids and draw indices), kept or not
+
+  // FP64 SoA of the initial state, in chunks (device); with a profile the
+  // loader's output is staged and only the kept particles are moved on
+  const long long chunk = S->prec == PIC_FP64_PLAIN && !sp.has_prof ? std::max<long long>(n, 1)
+                                                                    : std::min<long long>(std::max<long long>(n, 1),
+                                                                                          1ll << 25);
   double* xs[3] = {nullptr, nullptr, nullptr};
   double* us[3] = {nullptr, nullptr, nullptr};
   int* ids = nullptr;
+  double* ws = nullptr;      // weights of the staged chunk
+  double* cx[3] = {nullptr, nullptr, nullptr};  // FP32 form with a profile: the kept particles
+  double* cu[3] = {nullptr, nullptr, nullptr};
+  int* cid = nullptr;
+  void* pscr = nullptr;      // profile_compact scratch
   double* aos = nullptr;
   auto fail = [&](const char* what) {
     set_error(std::string("out of device memory (") + what + ")");
@@ -640,21 +723,51 @@ pic_status load_species(pic_sim* S, const pic_species& in, SpeciesState& sp) {
     }
     sp.plain.id = sp.ids ? (int*)S->al.get(4 * (size_t)std::max<long long>(n, 1)) : nullptr;
     if (sp.ids && !sp.plain.id) return fail("ids");
+    sp.plain.w = sp.weighted ? (double*)S->al.get(8 * (size_t)std::max<long long>(n, 1)) : nullptr;
+    if (sp.weighted && !sp.plain.w) return fail("weights");
     sp.plain.n = n;
   }
   Flat32 flat{};
   bool flat_ok = true;
   if (S->prec == PIC_FP32_CELLOFF) {
-    flat = alloc_flat(S, n, sp.ids, flat_ok);
+    flat = alloc_flat(S, n, sp.ids, flat_ok, sp.weighted);
     if (!flat_ok) {
       free_flat(S, flat);
       return fail("flat staging");
     }
   }
+  const bool staged = S->prec == PIC_FP32_CELLOFF || sp.has_prof;
+  if (staged) {
+    for (int d = 0; d < 3; ++d) {
+      xs[d] = (double*)S->al.get(8 * (size_t)chunk);
+      us[d] = (double*)S->al.get(8 * (size_t)chunk);
+      if (!xs[d] || !us[d]) return fail("staging");
+    }
+    ids = sp.ids ? (int*)S->al.get(4 * (size_t)chunk) : nullptr;
+    if (sp.ids && !ids) return fail("staging");
+  }
+  if (sp.weighted && S->prec == PIC_FP32_CELLOFF) {
+    ws = (double*)S->al.get(8 * (size_t)chunk);
+    if (!ws) return fail("staging");
+  }
+  if (sp.has_prof) {
+    pscr = S->al.get(profile_scratch_bytes(chunk));
+    if (!pscr) return fail("profile scratch");
+    if (S->prec == PIC_FP32_CELLOFF) {
+      for (int d = 0; d < 3; ++d) {
+        cx[d] = (double*)S->al.get(8 * (size_t)chunk);
+        cu[d] = (double*)S->al.get(8 * (size_t)chunk);
+        if (!cx[d] || !cu[d]) return fail("staging");
+      }
+      cid = sp.ids ? (int*)S->al.get(4 * (size_t)chunk) : nullptr;
+      if (sp.ids && !cid) return fail("staging");
+    }
+  }
   double* scratch_x2 = nullptr;
+  long long kept = 0;  // particles created so far: where the next ones go
   for (long long first = 0; first < n; first += chunk) {
     const long long cnt = std::min(chunk, n - first);
-    if (S->prec == PIC_FP64_PLAIN) {
+    if (!staged) {  // FP64 plain, no profile: straight into the particle arrays
       for (int d = 0; d < 3; ++d) {
         xs[d] = sp.plain.x[d] ? sp.plain.x[d] + first : nullptr;
         us[d] = sp.plain.u[d] + first;
@@ -664,15 +777,6 @@ pic_status load_species(pic_sim* S, const pic_species& in, SpeciesState& sp) {
         if (!scratch_x2) scratch_x2 = (double*)S->al.get(8 * (size_t)chunk);
         if (!scratch_x2) return fail("staging");
         xs[2] = scratch_x2;
-      }
-    } else {
-      if (!xs[0]) {
-        for (int d = 0; d < 3; ++d) {
-          xs[d] = (double*)S->al.get(8 * (size_t)chunk);
-          us[d] = (double*)S->al.get(8 * (size_t)chunk);
-          if (!xs[d] || !us[d]) return fail("staging");
-        }
-        ids = sp.ids ? (int*)S->al.get(4 * (size_t)chunk) : nullptr;
       }
     }
     if (in.n_explicit > 0) {
@@ -690,6 +794,9 @@ pic_status load_species(pic_sim* S, const pic_species& in, SpeciesState& sp) {
         cudaMemcpyAsync(ids, h.data(), 4 * (size_t)cnt, cudaMemcpyHostToDevice, S->s);
         cudaStreamSynchronize(S->s);
       }
+      if (in.w0)  // explicit weights
+        cudaMemcpyAsync(S->prec == PIC_FP64_PLAIN ? sp.plain.w + first : ws, in.w0 + first, 8 * (size_t)cnt,
+                        cudaMemcpyHostToDevice, S->s);
     } else {
       LatticeSpec L{};
       L.ndim = nd;
@@ -704,29 +811,60 @@ pic_status load_species(pic_sim* S, const pic_species& in, SpeciesState& sp) {
       L.seed = in.seed;
       lattice_load(L, first, cnt, xs, us, ids, S->s);
     }
+    long long got = cnt;  // particles of this chunk that are created
+    double* const* gx = xs;
+    double* const* gu = us;
+    const int* gid = ids;
+    if (sp.has_prof) {
+      if (S->prec == PIC_FP64_PLAIN) {
+        double* dxp[3] = {sp.plain.x[0] + kept, sp.plain.x[1] + kept, nd == 3 ? sp.plain.x[2] + kept : nullptr};
+        double* dup[3] = {sp.plain.u[0] + kept, sp.plain.u[1] + kept, sp.plain.u[2] + kept};
+        got = profile_compact(nd, sp.prof, cnt, xs, us, ids, dxp, dup, sp.plain.id ? sp.plain.id + kept : nullptr,
+                              sp.plain.w + kept, pscr, S->s);
+      } else {
+        got = profile_compact(nd, sp.prof, cnt, xs, us, ids, cx, cu, cid, ws, pscr, S->s);
+        gx = cx;
+        gu = cu;
+        gid = cid;
+      }
+      if (got < 0) return cuda_check("density profile");
+    }
     if (S->prec == PIC_FP32_CELLOFF) {
       Flat32 part = flat;
-      part.tile += first;
-      part.cell += first;
+      part.tile += kept;
+      part.cell += kept;
       for (int d = 0; d < 3; ++d) {
-        part.o[d] += first;
-        part.u[d] += first;
+        part.o[d] += kept;
+        part.u[d] += kept;
       }
-      if (part.id) part.id += first;
+      if (part.id) part.id += kept;
+      if (part.w) part.w += kept;
       PushConst C = make_const(S, sp);
-      global_to_flat(nd, S->L, sp.tg, C, xs, us, ids, cnt, part, &S->dstat->status, S->s);
+      global_to_flat(nd, S->L, sp.tg, C, gx, gu, gid, sp.weighted ? ws : nullptr, got, part, &S->dstat->status,
+                     S->s);
     }
+    kept += got;
     cudaError_t e = cudaStreamSynchronize(S->s);
     if (e != cudaSuccess) return cuda_check("loading particles");
   }
+  n = kept;
+  sp.n = n;
+  if (S->prec == PIC_FP64_PLAIN) sp.plain.n = n;
   if (aos) S->al.put(aos);
   if (scratch_x2) S->al.put(scratch_x2);
-  if (S->prec == PIC_FP32_CELLOFF) {
+  if (staged) {
     for (int d = 0; d < 3; ++d) {
       S->al.put(xs[d]);
       S->al.put(us[d]);
+      S->al.put(cx[d]);
+      S->al.put(cu[d]);
     }
     S->al.put(ids);
+    S->al.put(cid);
+  }
+  S->al.put(ws);
+  S->al.put(pscr);
+  if (S->prec == PIC_FP32_CELLOFF) {
     pic_status st = bin_flat(S, sp, flat, n);
     free_flat(S, flat);
     if (st != PIC_OK) return st;
@@ -770,15 +908,17 @@ pic_status setup_tiles(pic_sim* S, SpeciesState& sp) {
 pic_status alloc_spill(pic_sim* S, SpeciesState& sp) {
   sp.spill_cap = std::max<long long>(1 << 16, sp.n / 64);
   bool ok = true;
-  sp.spill = alloc_flat(S, sp.spill_cap, sp.ids, ok);
+  sp.spill = alloc_flat(S, sp.spill_cap, sp.ids, ok, sp.weighted);
   sp.d_lost = (int*)S->al.get(sizeof(int));
   sp.d_spill = (int*)S->al.get(sizeof(int));
-  if (!ok || !sp.d_lost || !sp.d_spill) {
+  sp.d_kept = (int*)S->al.get(sizeof(int));
+  if (!ok || !sp.d_lost || !sp.d_spill || !sp.d_kept) {
     set_error("out of device memory (spill list)");
     return PIC_ENOMEM;
   }
   cudaMemsetAsync(sp.d_lost, 0, sizeof(int), S->s);
   cudaMemsetAsync(sp.d_spill, 0, sizeof(int), S->s);
+  cudaMemsetAsync(sp.d_kept, 0, sizeof(int), S->s);
   if (sp.created < sp.n) sp.created = sp.n;
   return PIC_OK;
 }
@@ -852,15 +992,19 @@ pic_status one_step(pic_sim* S, bool check_now) {
         const int nk = tiled_push(S->L, C, s.tg, s.side[in], s.side[out], s.spill, s.d_spill, s.spill_cap, s.grid,
                                   s.work, &S->fmap, &S->jmap, &S->dstat->status, stream, S->minb, shift ? 1 : 0,
                                   s.d_lost, &s.slices, S->s);
+        if (nk == 0) {
+          set_error("no tile kernel for this tile shape");
+          return PIC_EUNSUPPORTED;
+        }
         S->nlaunch += nk - 1;  // the tile kernel itself is counted below
         s.cur = out;
         if (shift) {  // fresh plasma for the new front column
           const long long cnt = (long long)S->L.ny * S->L.nz * s.ppc[0] * s.ppc[1] * s.ppc[2];
           const int nxs[3] = {S->L.nx, S->L.ny, S->L.nz};
           tiled_inject(C, s.tg, s.side[out], s.spill, s.d_spill, s.spill_cap, &S->dstat->status, nxs,
-                       s.ppc, s.uth, s.ufl, s.seed, s.created, cnt, S->s);
-          s.created += cnt;
-          s.n += cnt;
+                       s.ppc, s.uth, s.ufl, s.seed, s.created, cnt, s.has_prof ? &s.prof : nullptr, s.d_kept,
+                       S->s);
+          s.created += cnt;  // lattice places; the particles created are counted on the device
           S->nlaunch += cnt > 0 ? 1 : 0;
         }
       }
@@ -890,10 +1034,12 @@ pic_status one_step(pic_sim* S, bool check_now) {
   S->sticky_flags |= flags;
   if (S->moving)
     for (auto& s : S->sp) {
-      int lost = 0;
+      int lost = 0, kept = 0;
       cudaMemcpy(&lost, s.d_lost, sizeof(int), cudaMemcpyDeviceToHost);
+      cudaMemcpy(&kept, s.d_kept, sizeof(int), cudaMemcpyDeviceToHost);
       cudaMemsetAsync(s.d_lost, 0, sizeof(int), S->s);
-      s.n -= lost;
+      cudaMemsetAsync(s.d_kept, 0, sizeof(int), S->s);
+      s.n += kept - lost;
     }
   if (flags & ST_SPILL) {
     if (flags & ST_SPILL_LOST) {
@@ -1351,6 +1497,50 @@ pic_status pic_particle_ids(pic_sim* S, int species, int* ids, long long cap, lo
   cudaStreamSynchronize(S->s);
   free_flat(S, flat);
   return cuda_check("pic_particle_ids");
+}
+
+pic_status pic_particle_weights(pic_sim* S, int species, double* w, long long cap, long long* n_out,
+                                int dst_on_device) {
+  if (!S || species < 0 || species >= (int)S->sp.size() || !n_out || !w) {
+    set_error("pic_particle_weights: bad arguments");
+    return PIC_EINVAL;
+  }
+  SpeciesState& sp = S->sp[(size_t)species];
+  Flat32 flat{};
+  long long n = sp.n;
+  bool allocated = false;
+  if (S->prec == PIC_FP32_CELLOFF) {
+    const pic_status st = flatten(S, sp, flat, n, false, 0, allocated);
+    if (st != PIC_OK) {
+      if (allocated) free_flat(S, flat);
+      return st;
+    }
+  } else {
+    n = sp.plain.n;
+  }
+  *n_out = n;
+  if (n > cap) {
+    if (allocated) free_flat(S, flat);
+    set_error("pic_particle_weights: capacity too small");
+    return PIC_EOVERFLOW;
+  }
+  double* d = (double*)S->al.get(8 * (size_t)std::max<long long>(n, 1));
+  if (!d) {
+    if (allocated) free_flat(S, flat);
+    set_error("out of device memory (weights)");
+    return PIC_ENOMEM;
+  }
+  if (n > 0) {
+    if (S->prec == PIC_FP64_PLAIN && sp.plain.w)
+      cudaMemcpyAsync(d, sp.plain.w, 8 * (size_t)n, cudaMemcpyDeviceToDevice, S->s);
+    else
+      k_widen<<<(unsigned)((n + 255) / 256), 256, 0, S->s>>>(S->prec == PIC_FP32_CELLOFF ? flat.w : nullptr, d, n);
+    cudaMemcpyAsync(w, d, 8 * (size_t)n, dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, S->s);
+  }
+  cudaStreamSynchronize(S->s);
+  S->al.put(d);
+  if (allocated) free_flat(S, flat);
+  return cuda_check("pic_particle_weights");
 }
 
 pic_status pic_tile_counts(pic_sim* S, int species, long long* counts, long long cap, long long* ntiles_out) {
@@ -1939,7 +2129,7 @@ pic_status pic_batch_autotune(int nsims, const pic_grid* grids, const pic_specie
 namespace {
 
 const char kCkptMagic[8] = {'P', 'I', 'C', 'G', 'B', 'C', 'K', '1'};
-constexpr uint32_t kCkptVersion = 1;
+constexpr uint32_t kCkptVersion = 2;
 constexpr size_t kIoChunk = size_t(64) << 20;  // host staging per copy
 
 struct CkptSpecies {
@@ -1949,6 +2139,8 @@ struct CkptSpecies {
   double uth[3], ufl[3];
   unsigned long long seed;
   long long created;
+  int weighted, prof_n[3];  // charge weights stored; profile tables that follow the particles
+  double density, den_min;
 };
 
 bool write_dev(FILE* f, const void* dev, size_t bytes, cudaStream_t s, std::vector<unsigned char>& buf) {
@@ -1993,11 +2185,16 @@ std::vector<std::pair<void*, size_t>> species_arrays(const pic_sim* S, const Spe
     for (int d = 0; d < 3; ++d) a.push_back({fl.o[d], 4 * m});
     for (int d = 0; d < 3; ++d) a.push_back({fl.u[d], 4 * m});
     if (sp.ids) a.push_back({fl.id, 4 * m});
+    if (sp.weighted) a.push_back({fl.w, 4 * m});
   } else {
     for (int d = 0; d < S->ndim; ++d) a.push_back({sp.plain.x[d], 8 * m});
     for (int d = 0; d < 3; ++d) a.push_back({sp.plain.u[d], 8 * m});
     if (sp.ids) a.push_back({sp.plain.id, 4 * m});
+    if (sp.weighted) a.push_back({sp.plain.w, 8 * m});
   }
+  size_t tab = 0;  // the profile tables (x then f per direction)
+  for (int d = 0; d < 3; ++d) tab += 2 * (size_t)sp.prof.n[d];
+  if (sp.has_prof && tab) a.push_back({sp.prof_mem, 8 * tab});
   return a;
 }
 
@@ -2047,6 +2244,10 @@ pic_status pic_checkpoint_save(pic_sim* S, const char* path) {
     }
     h.seed = sp.seed;
     h.created = sp.created;
+    h.weighted = sp.weighted ? 1 : 0;
+    for (int d = 0; d < 3; ++d) h.prof_n[d] = sp.has_prof ? sp.prof.n[d] : 0;
+    h.density = sp.prof.density;
+    h.den_min = sp.prof.den_min;
     put(&h, sizeof(h));
     for (auto& a : species_arrays(S, sp, fl, n)) ok = ok && write_dev(f, a.first, a.second, S->s, buf);
     if (alloc) free_flat(S, fl);
@@ -2112,11 +2313,33 @@ pic_status pic_checkpoint_load(const char* path, const pic_allocator* alloc, voi
     }
     sp.seed = h.seed;
     sp.created = h.created;
+    sp.weighted = h.weighted != 0;
+    size_t tab = 0;
+    for (int d = 0; d < 3; ++d) tab += 2 * (size_t)std::max(h.prof_n[d], 0);
+    sp.has_prof = tab > 0;
+    sp.prof = ProfileDev{};
+    if (sp.has_prof) {
+      sp.prof_mem = (double*)S->al.get(8 * tab);
+      if (!sp.prof_mem) {
+        set_error("out of device memory (density profile)");
+        return PIC_ENOMEM;
+      }
+      size_t o = 0;
+      for (int d = 0; d < 3; ++d) {
+        sp.prof.n[d] = h.prof_n[d];
+        if (h.prof_n[d] <= 0) continue;
+        sp.prof.x[d] = sp.prof_mem + o;
+        sp.prof.f[d] = sp.prof_mem + o + h.prof_n[d];
+        o += 2 * (size_t)h.prof_n[d];
+      }
+      sp.prof.density = h.density;
+      sp.prof.den_min = h.den_min;
+    }
     const size_t m = (size_t)std::max<long long>(h.n, 1);
     Flat32 fl{};
     if (S->prec == PIC_FP32_CELLOFF) {
       bool okf = true;
-      fl = alloc_flat(S, h.n, sp.ids, okf);
+      fl = alloc_flat(S, h.n, sp.ids, okf, sp.weighted);
       if (!okf) {
         free_flat(S, fl);
         set_error("out of device memory (checkpoint particles)");
@@ -2132,6 +2355,11 @@ pic_status pic_checkpoint_load(const char* path, const pic_allocator* alloc, voi
         }
       }
       sp.plain.id = sp.ids ? (int*)S->al.get(4 * m) : nullptr;
+      sp.plain.w = sp.weighted ? (double*)S->al.get(8 * m) : nullptr;
+      if (sp.weighted && !sp.plain.w) {
+        set_error("out of device memory (checkpoint particles)");
+        return PIC_ENOMEM;
+      }
       sp.plain.n = h.n;
     }
     for (auto& a : species_arrays(S, sp, fl, h.n))

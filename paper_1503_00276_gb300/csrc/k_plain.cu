@@ -81,7 +81,8 @@ __device__ inline void boris(double u[3], const double e[3], const double b[3], 
 // i.e. the midpoint weights plus the covariance term D_t1 D_t2 / 12.
 template <int NDIM>
 __device__ inline void deposit_segment(const Layout& L, const PushConst& C, J3 J, const int cell[3],
-                                       const double a[3], const double b[3], double v3frac, bool only_j3 = false) {
+                                       const double a[3], const double b[3], double v3frac, double q,
+                                       bool only_j3 = false) {
   double dl[3], m[3];
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
@@ -90,14 +91,14 @@ __device__ inline void deposit_segment(const Layout& L, const PushConst& C, J3 J
   }
   if (NDIM == 2) {
     if (!only_j3) {
-    double a1 = C.q * dl[0] * C.dx[0] / (C.dt * C.dvol);
-    double a2 = C.q * dl[1] * C.dx[1] / (C.dt * C.dvol);
+    double a1 = q * dl[0] * C.dx[0] / (C.dt * C.dvol);
+    double a2 = q * dl[1] * C.dx[1] / (C.dt * C.dvol);
     atomicAdd(&J.c[0][L.idx(cell[0], cell[1], 0)], a1 * (1.0 - m[1]));
     atomicAdd(&J.c[0][L.idx(cell[0], cell[1] + 1, 0)], a1 * m[1]);
     atomicAdd(&J.c[1][L.idx(cell[0], cell[1], 0)], a2 * (1.0 - m[0]));
     atomicAdd(&J.c[1][L.idx(cell[0] + 1, cell[1], 0)], a2 * m[0]);
     }
-    double a3 = C.q * v3frac / C.dvol;
+    double a3 = q * v3frac / C.dvol;
     double cv = dl[0] * dl[1] / 12.0;
     atomicAdd(&J.c[2][L.idx(cell[0], cell[1], 0)], a3 * ((1.0 - m[0]) * (1.0 - m[1]) + cv));
     atomicAdd(&J.c[2][L.idx(cell[0] + 1, cell[1], 0)], a3 * (m[0] * (1.0 - m[1]) - cv));
@@ -108,7 +109,7 @@ __device__ inline void deposit_segment(const Layout& L, const PushConst& C, J3 J
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
     int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
-    double amp = C.q * dl[d] * C.dx[d] / (C.dt * C.dvol);
+    double amp = q * dl[d] * C.dx[d] / (C.dt * C.dvol);
     double cv = dl[t1] * dl[t2] / 12.0;
     int id[3] = {cell[0], cell[1], cell[2]};
     atomicAdd(&J.c[d][L.idx(id[0], id[1], id[2])], amp * ((1.0 - m[t1]) * (1.0 - m[t2]) + cv));
@@ -125,7 +126,7 @@ __device__ inline void deposit_segment(const Layout& L, const PushConst& C, J3 J
 // per direction) and deposit each in-cell piece.
 template <int NDIM>
 __device__ inline void deposit_path(const Layout& L, const PushConst& C, J3 J, const double xo[3],
-                                    const double xn[3], double v3, bool only_j3 = false) {
+                                    const double xn[3], double v3, double q, bool only_j3 = false) {
   int i0[3] = {0, 0, 0};
   double a[3] = {0, 0, 0}, b[3] = {0, 0, 0};
   const int nn[3] = {L.nx, L.ny, L.nz};
@@ -183,7 +184,7 @@ __device__ inline void deposit_path(const Layout& L, const PushConst& C, J3 J, c
       la[d] = p0[d] - (double)off[d];
       lb[d] = p1[d] - (double)off[d];
     }
-    deposit_segment<NDIM>(L, C, J, cell, la, lb, v3 * (t1 - t0), only_j3);
+    deposit_segment<NDIM>(L, C, J, cell, la, lb, v3 * (t1 - t0), q, only_j3);
     if (m < nc) off[dc[m]] += sc[m];
     for (int d = 0; d < 3; ++d) p0[d] = p1[d];
     t0 = t1;
@@ -200,7 +201,7 @@ __device__ inline void deposit_path(const Layout& L, const PushConst& C, J3 J, c
 __device__ inline double lin_w(double s) { return fmax(0.0, 1.0 - fabs(s)); }
 
 __device__ inline void deposit_isis(const Layout& L, const PushConst& C, J3 J, const double xo[3],
-                                    const double xn[3], double v3) {
+                                    const double xn[3], double v3, double q) {
   int i0[2];
   double a[2], b[2];
   const int nn[2] = {L.nx, L.ny};
@@ -221,7 +222,7 @@ __device__ inline void deposit_isis(const Layout& L, const PushConst& C, J3 J, c
     f[d][2] = fmax(b[d] - 1.0, 0.0);
     for (int m = 0; m < 4; ++m) w[d][m] = 0.5 * (lin_w(a[d] - (double)(m - 1)) + lin_w(b[d] - (double)(m - 1)));
   }
-  const double c1 = C.q * C.dx[0] / (C.dt * C.dvol), c2 = C.q * C.dx[1] / (C.dt * C.dvol);
+  const double c1 = q * C.dx[0] / (C.dt * C.dvol), c2 = q * C.dx[1] / (C.dt * C.dvol);
   for (int d = 0; d < 3; ++d)
     for (int m = 0; m < 4; ++m) {
       if (f[0][d] != 0.0 && w[1][m] != 0.0)
@@ -229,7 +230,7 @@ __device__ inline void deposit_isis(const Layout& L, const PushConst& C, J3 J, c
       if (f[1][d] != 0.0 && w[0][m] != 0.0)
         atomicAdd(&J.c[1][L.idx(i0[0] + m - 1, i0[1] + d - 1, 0)], c2 * f[1][d] * w[0][m]);
     }
-  deposit_path<2>(L, C, J, xo, xn, v3, true);
+  deposit_path<2>(L, C, J, xo, xn, v3, q, true);
 }
 
 template <int NDIM>
@@ -252,10 +253,11 @@ __global__ void __launch_bounds__(256) k_plain_push(Layout L, PushConst C, Plain
     atomicOr(status, ST_NONFINITE);
     return;
   }
+  const double qp = p.w ? C.q * p.w[n] : C.q;  // charge of this particle (density profile)
   if (NDIM == 2 && C.isis)
-    deposit_isis(L, C, J, xo, x, u[2] / gam);
+    deposit_isis(L, C, J, xo, x, u[2] / gam, qp);
   else
-    deposit_path<NDIM>(L, C, J, xo, x, u[2] / gam);
+    deposit_path<NDIM>(L, C, J, xo, x, u[2] / gam, qp);
   // periodic wrap
 #pragma unroll
   for (int d = 0; d < NDIM; ++d) {
@@ -295,28 +297,37 @@ __global__ void k_plain_rho(Layout L, PushConst C, Plain p, double* rho) {
       for (int c1 = 0; c1 < 2; ++c1) {
         double w = (c1 ? e[0] : 1.0 - e[0]) * (c2 ? e[1] : 1.0 - e[1]);
         if (NDIM == 3) w = w * (c3 ? e[2] : 1.0 - e[2]);
-        atomicAdd(&rho[L.idx(i[0] + c1, i[1] + c2, i[2] + c3)], C.q * w / C.dvol);
+        atomicAdd(&rho[L.idx(i[0] + c1, i[1] + c2, i[2] + c3)], (p.w ? C.q * p.w[n] : C.q) * w / C.dvol);
       }
 }
 
 __global__ void k_plain_kinetic(PushConst C, Plain p, double* ke, double* qsum) {
   __shared__ double red[8];
   long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  double v = 0.0;
+  double v = 0.0, qn = 0.0;
   if (n < p.n) {
     double u0 = p.u[0][n], u1 = p.u[1][n], u2 = p.u[2][n];
-    v = C.q * C.rqm * (sqrt(1.0 + u0 * u0 + u1 * u1 + u2 * u2) - 1.0);
+    qn = p.w ? C.q * p.w[n] : C.q;
+    v = qn * C.rqm * (sqrt(1.0 + u0 * u0 + u1 * u1 + u2 * u2) - 1.0);
   }
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __shared__ double redq[8];
+  for (int o = 16; o > 0; o >>= 1) {
+    v += __shfl_down_sync(0xffffffffu, v, o);
+    qn += __shfl_down_sync(0xffffffffu, qn, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red[threadIdx.x >> 5] = v;
+    redq[threadIdx.x >> 5] = qn;
+  }
   __syncthreads();
   if (threadIdx.x == 0) {
-    double s = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+    double s = 0.0, sq = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      s += red[w];
+      sq += redq[w];
+    }
     atomicAdd(ke, s);
-    long long cnt = p.n - (long long)blockIdx.x * blockDim.x;
-    if (cnt > blockDim.x) cnt = blockDim.x;
-    atomicAdd(qsum, C.q * (double)cnt);
+    atomicAdd(qsum, sq);
   }
 }
 
@@ -383,6 +394,67 @@ void plain_kinetic(const PushConst& C, Plain p, Diag64* acc, cudaStream_t s) {
   if (p.n == 0) return;
   unsigned blocks = (unsigned)((p.n + 255) / 256);
   k_plain_kinetic<<<blocks, 256, 0, s>>>(C, p, &acc->kinetic_energy, &acc->total_charge);
+}
+
+namespace {
+// weight and keep flag of every loaded particle
+__global__ void k_profile_keep(int ndim, ProfileDev P, long long n, const double* x0, const double* x1,
+                               const double* x2, double* w, int* keep) {
+  const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  const double x[3] = {x0[k], x1[k], ndim == 3 ? x2[k] : 0.0};
+  const double v = profile_weight(P, x);
+  w[k] = v;
+  keep[k] = P.density * v > P.den_min ? 1 : 0;
+}
+
+// the kept particles, in order, to their compacted places
+__global__ void k_profile_scatter(long long n, const int* keep, const long long* pos, const double* x0,
+                                  const double* x1, const double* x2, const double* u0, const double* u1,
+                                  const double* u2, const int* id, const double* w, double* dx0, double* dx1,
+                                  double* dx2, double* du0, double* du1, double* du2, int* did, double* dw) {
+  const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n || !keep[k]) return;
+  const long long j = pos[k];
+  dx0[j] = x0[k];
+  dx1[j] = x1[k];
+  if (dx2) dx2[j] = x2[k];
+  du0[j] = u0[k];
+  du1[j] = u1[k];
+  du2[j] = u2[k];
+  if (did) did[j] = id[k];
+  dw[j] = w[k];
+}
+}  // namespace
+
+size_t profile_scratch_bytes(long long count) {
+  auto al = [](size_t b) { return (b + 255) / 256 * 256; };
+  return al(8 * (size_t)count) + al(4 * (size_t)count) + al(8 * (size_t)count) + al(scan_scratch_bytes(count));
+}
+
+long long profile_compact(int ndim, const ProfileDev& P, long long count, double* const x[3], double* const u[3],
+                          const int* id, double* const dx[3], double* const du[3], int* did, double* dw,
+                          void* scratch, cudaStream_t s) {
+  if (count <= 0) return 0;
+  auto al = [](size_t b) { return (b + 255) / 256 * 256; };
+  char* c = reinterpret_cast<char*>(scratch);
+  double* w = reinterpret_cast<double*>(c);
+  c += al(8 * (size_t)count);
+  int* keep = reinterpret_cast<int*>(c);
+  c += al(4 * (size_t)count);
+  long long* pos = reinterpret_cast<long long*>(c);
+  c += al(8 * (size_t)count);
+  const unsigned blocks = (unsigned)((count + 255) / 256);
+  k_profile_keep<<<blocks, 256, 0, s>>>(ndim, P, count, x[0], x[1], x[2], w, keep);
+  exclusive_scan_i32(keep, pos, count, c, s);
+  k_profile_scatter<<<blocks, 256, 0, s>>>(count, keep, pos, x[0], x[1], x[2], u[0], u[1], u[2], id, w, dx[0],
+                                           dx[1], dx[2], du[0], du[1], du[2], did, dw);
+  long long last_pos = 0;
+  int last_keep = 0;
+  cudaMemcpyAsync(&last_pos, pos + count - 1, 8, cudaMemcpyDeviceToHost, s);
+  cudaMemcpyAsync(&last_keep, keep + count - 1, 4, cudaMemcpyDeviceToHost, s);
+  if (cudaStreamSynchronize(s) != cudaSuccess) return -1;
+  return last_pos + last_keep;
 }
 
 void lattice_load(const LatticeSpec& S, long long first, long long count, double* const x[3], double* const u[3],

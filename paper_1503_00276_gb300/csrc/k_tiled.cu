@@ -82,7 +82,7 @@ struct Geo {
   static constexpr int JPL = JX * JY * JZ;
   static constexpr int FBYTES = 6 * FPL * 4;
   static constexpr int JBYTES = 3 * JPL * 4;
-  static constexpr int QW = NDIM == 3 ? 7 : 6;  // words per queue entry
+  static constexpr int QW = NDIM == 3 ? 8 : 7;  // words per queue entry (last: charge weight)
   static constexpr int FOFF = 0;
   static constexpr int JOFF = ((FBYTES + 127) / 128) * 128;
   static constexpr int HOFF = JOFF + ((JBYTES + 127) / 128) * 128;   // hist[NK]
@@ -97,6 +97,7 @@ struct P {
   float o0, o1, o2;
   float u0, u1, u2;
   int id;
+  float w;  // charge weight (density profile; 1 without one)
 };
 
 __device__ inline float lerp(float a, float b, float w) { return fmaf(w, b - a, a); }
@@ -145,16 +146,16 @@ __device__ inline float interp(const float* F, int ix, int iy, int iz, float wx,
 // J3 (n,n+x,n+y,n+x+y) in 3D; J1 (n,n+y) J2 (n,n+x) J3 (n,n+x,n+y,n+x+y) in 2D.
 template <int NDIM>
 __device__ inline void seg_weights(const TileArgs& A, float ax, float ay, float az, float bx, float by, float bz,
-                                   float v3frac, float w[12]) {
+                                   float v3frac, float w[12], float q = 1.f) {
   const float dx = bx - ax, dy = by - ay;
   const float mx = 0.5f * (ax + bx), my = 0.5f * (ay + by);
   if (NDIM == 2) {
-    const float a1 = A.cf[0] * dx, a2 = A.cf[1] * dy;
+    const float a1 = A.cf[0] * q * dx, a2 = A.cf[1] * q * dy;
     w[0] = a1 * (1.f - my);
     w[1] = a1 * my;
     w[2] = a2 * (1.f - mx);
     w[3] = a2 * mx;
-    const float a3 = A.j3f * v3frac;
+    const float a3 = A.j3f * q * v3frac;
     const float cv = dx * dy * (1.f / 12.f);
     w[4] = a3 * ((1.f - mx) * (1.f - my) + cv);
     w[5] = a3 * (mx * (1.f - my) - cv);
@@ -162,18 +163,18 @@ __device__ inline void seg_weights(const TileArgs& A, float ax, float ay, float 
     w[7] = a3 * (mx * my + cv);
   } else {
     const float dz = bz - az, mz = 0.5f * (az + bz);
-    float a = A.cf[0] * dx, cv = dy * dz * (1.f / 12.f);
+    float a = A.cf[0] * q * dx, cv = dy * dz * (1.f / 12.f);
     w[0] = a * ((1.f - my) * (1.f - mz) + cv);
     w[1] = a * (my * (1.f - mz) - cv);
     w[2] = a * ((1.f - my) * mz - cv);
     w[3] = a * (my * mz + cv);
-    a = A.cf[1] * dy;
+    a = A.cf[1] * q * dy;
     cv = dz * dx * (1.f / 12.f);
     w[4] = a * ((1.f - mz) * (1.f - mx) + cv);
     w[5] = a * (mz * (1.f - mx) - cv);
     w[6] = a * ((1.f - mz) * mx - cv);
     w[7] = a * (mz * mx + cv);
-    a = A.cf[2] * dz;
+    a = A.cf[2] * q * dz;
     cv = dx * dy * (1.f / 12.f);
     w[8] = a * ((1.f - mx) * (1.f - my) + cv);
     w[9] = a * (mx * (1.f - my) - cv);
@@ -282,7 +283,7 @@ __device__ inline float lin_w(float s) { return fmaxf(0.f, 1.f - fabsf(s)); }
 
 template <int TX, int TY>
 __device__ inline void isis_path(float* J, const TileArgs& A, int lx, int ly, float ax, float ay, float bx,
-                                 float by, float v3) {
+                                 float by, float v3, float q) {
   using G = Geo<2, TX, TY, 1>;
   const float fx[3] = {fminf(bx, 0.f), fminf(fmaxf(bx, 0.f), 1.f) - ax, fmaxf(bx - 1.f, 0.f)};
   const float fy[3] = {fminf(by, 0.f), fminf(fmaxf(by, 0.f), 1.f) - ay, fmaxf(by - 1.f, 0.f)};
@@ -297,16 +298,16 @@ __device__ inline void isis_path(float* J, const TileArgs& A, int lx, int ly, fl
 #pragma unroll
     for (int m = 0; m < 4; ++m) {
       if (fx[d] != 0.f && wy[m] != 0.f)  // J1 at (lx + d - 1, ly + m - 1)
-        atomicAdd(&J[(ly + m) * G::JX + (lx + d)], A.cf[0] * fx[d] * wy[m]);
+        atomicAdd(&J[(ly + m) * G::JX + (lx + d)], A.cf[0] * q * fx[d] * wy[m]);
       if (fy[d] != 0.f && wx[m] != 0.f)  // J2 at (lx + m - 1, ly + d - 1)
-        atomicAdd(&J[G::JPL + (ly + d) * G::JX + (lx + m)], A.cf[1] * fy[d] * wx[m]);
+        atomicAdd(&J[G::JPL + (ly + d) * G::JX + (lx + m)], A.cf[1] * q * fy[d] * wx[m]);
     }
   }
   walk<2>(ax, ay, 0.f, bx, by, 0.f,
           [&](int k, int ox, int oy, int oz, float sx0, float sy0, float sz0, float sx1, float sy1, float sz1,
               float frac) {
             float w[12];
-            seg_weights<2>(A, sx0, sy0, 0.f, sx1, sy1, 0.f, v3 * frac, w);
+            seg_weights<2>(A, sx0, sy0, 0.f, sx1, sy1, 0.f, v3 * frac, w, q);
             const int c = 2 * G::JPL + (ly + oy + 1) * G::JX + (lx + ox + 1);
             atomicAdd(&J[c], w[4]);
             atomicAdd(&J[c + 1], w[5]);
@@ -493,7 +494,7 @@ __device__ inline int push_one(const float* F, float* J, const TileArgs& A, P& p
         acc.cell = cellp;
       }
       float w[12];
-      seg_weights<NDIM>(A, ax, ay, az, p1x, p1y, p1z, v3 * t1, w);
+      seg_weights<NDIM>(A, ax, ay, az, p1x, p1y, p1z, v3 * t1, w, p.w);
 #pragma unroll
       for (int k = 0; k < (NDIM == 3 ? 12 : 8); ++k) acc.w[k] += w[k];
     }
@@ -513,17 +514,19 @@ __device__ inline int push_one(const float* F, float* J, const TileArgs& A, P& p
       } else {
         e[5] = v3;
       }
+      e[G::QW - 1] = p.w;
     } else {
       // queue full: deposit the remaining pieces here
+      const float pw = p.w;
       if (NDIM == 2 && A.isis)
-        isis_path<TX, TY>(J, A, lx, ly, ax, ay, bx, by, v3);
+        isis_path<TX, TY>(J, A, lx, ly, ax, ay, bx, by, v3, pw);
       else
       walk<NDIM>(ax, ay, az, bx, by, bz,
                  [&](int k, int ox, int oy, int oz, float sx0, float sy0, float sz0, float sx1, float sy1, float sz1,
                      float frac) {
                    if (k == 0) return;
                    float w[12];
-                   seg_weights<NDIM>(A, sx0, sy0, sz0, sx1, sy1, sz1, v3 * frac, w);
+                   seg_weights<NDIM>(A, sx0, sy0, sz0, sx1, sy1, sz1, v3 * frac, w, pw);
                    flush_cell<NDIM, G::JX, G::JY, G::JPL>(J, lx + ox, ly + oy, lz + oz, w);
                  });
     }
@@ -579,20 +582,21 @@ __device__ inline void drain_queue(float* J, const TileArgs& A, const float* Q, 
       const float ax = e[1], ay = e[2], bx = e[3], by = e[4];
       const float az = NDIM == 3 ? e[5] : 0.f, bz = NDIM == 3 ? e[6] : 0.f;
       const float v3 = NDIM == 3 ? 0.f : e[5];
+      const float pw = e[G::QW - 1];
       if (NDIM == 2 && A.isis)
-        isis_path<TX, TY>(J, A, lx, ly, ax, ay, bx, by, v3);
+        isis_path<TX, TY>(J, A, lx, ly, ax, ay, bx, by, v3, pw);
       else
       walk<NDIM>(ax, ay, az, bx, by, bz,
                  [&](int k, int ox, int oy, int oz, float sx0, float sy0, float sz0, float sx1, float sy1, float sz1,
                      float frac) {
                    if (k == 0) return;
                    if (AGG && k == 1) {
-                     seg_weights<NDIM>(A, sx0, sy0, sz0, sx1, sy1, sz1, v3 * frac, w1);
+                     seg_weights<NDIM>(A, sx0, sy0, sz0, sx1, sy1, sz1, v3 * frac, w1, pw);
                      c1 = (lx + ox + 1) | ((ly + oy + 1) << 8) | ((lz + oz + 1) << 16);
                      return;
                    }
                    float w[12];
-                   seg_weights<NDIM>(A, sx0, sy0, sz0, sx1, sy1, sz1, v3 * frac, w);
+                   seg_weights<NDIM>(A, sx0, sy0, sz0, sx1, sy1, sz1, v3 * frac, w, pw);
                    flush_cell<NDIM, G::JX, G::JY, G::JPL>(J, lx + ox, ly + oy, lz + oz, w);
                  });
     }
@@ -616,6 +620,7 @@ __device__ inline void spill_put(const TileArgs& A, int tile, const P& q) {
   A.spill.u[1][k] = q.u1;
   A.spill.u[2][k] = q.u2;
   if (A.spill.id) A.spill.id[k] = q.id;
+  if (A.spill.w) A.spill.w[k] = q.w;
 }
 
 template <int NDIM>
@@ -628,6 +633,7 @@ __device__ inline void store_particle(const Part32& o, long long s, const P& q) 
   o.u[1][s] = q.u1;
   o.u[2][s] = q.u2;
   if (o.id) o.id[s] = q.id;
+  if (o.w) o.w[s] = q.w;
 }
 
 // Region of one of the 27 tiles around (and including) the current one, by
@@ -1037,7 +1043,8 @@ __device__ inline bool sort_tile(const TileArgs& A, const CUtensorMap* fmap, con
       if (nvalid) {
         const long long s = base + first;
         pp[0] = P{A.in.p.cell[s], A.in.p.o[0][s], A.in.p.o[1][s], NDIM == 3 ? A.in.p.o[2][s] : 0.f,
-                  A.in.p.u[0][s], A.in.p.u[1][s], A.in.p.u[2][s], A.in.p.id ? A.in.p.id[s] : 0};
+                  A.in.p.u[0][s], A.in.p.u[1][s], A.in.p.u[2][s], A.in.p.id ? A.in.p.id[s] : 0,
+                  A.in.p.w ? A.in.p.w[s] : 1.f};
       }
     } else if (ch < nchunk_s) {
       const int first = ch * kChunk + tid * kPPT;
@@ -1048,6 +1055,9 @@ __device__ inline bool sort_tile(const TileArgs& A, const CUtensorMap* fmap, con
         uint32_t cl[kPPT];
         float q0[kPPT], q1[kPPT], q2[kPPT] = {}, v0[kPPT], v1[kPPT], v2[kPPT];
         int idv[kPPT] = {};
+        float wv[kPPT];
+#pragma unroll
+        for (int r = 0; r < kPPT; ++r) wv[r] = 1.f;
         load_vec(A.in.p.cell + s, cl);
         load_vec(A.in.p.o[0] + s, q0);
         load_vec(A.in.p.o[1] + s, q1);
@@ -1056,8 +1066,9 @@ __device__ inline bool sort_tile(const TileArgs& A, const CUtensorMap* fmap, con
         load_vec(A.in.p.u[1] + s, v1);
         load_vec(A.in.p.u[2] + s, v2);
         if (A.in.p.id) load_vec(A.in.p.id + s, idv);
+        if (A.in.p.w) load_vec(A.in.p.w + s, wv);
 #pragma unroll
-        for (int r = 0; r < kPPT; ++r) pp[r] = P{cl[r], q0[r], q1[r], q2[r], v0[r], v1[r], v2[r], idv[r]};
+        for (int r = 0; r < kPPT; ++r) pp[r] = P{cl[r], q0[r], q1[r], q2[r], v0[r], v1[r], v2[r], idv[r], wv[r]};
       }
     } else {
       const int first = (ch - nchunk_s) * csz + tid * per;
@@ -1068,7 +1079,8 @@ __device__ inline bool sort_tile(const TileArgs& A, const CUtensorMap* fmap, con
         if (r < nvalid) {
           const long long s = base + cap - ninc + first + r;
           pp[r] = P{A.in.p.cell[s], A.in.p.o[0][s], A.in.p.o[1][s], NDIM == 3 ? A.in.p.o[2][s] : 0.f,
-                    A.in.p.u[0][s], A.in.p.u[1][s], A.in.p.u[2][s], A.in.p.id ? A.in.p.id[s] : 0};
+                    A.in.p.u[0][s], A.in.p.u[1][s], A.in.p.u[2][s], A.in.p.id ? A.in.p.id[s] : 0,
+                    A.in.p.w ? A.in.p.w[s] : 1.f};
         }
       }
     }
@@ -1336,6 +1348,7 @@ __device__ inline P stage_get(const float* IN, int i) {
   p.u1 = IN[5 * kCapS + i];
   p.u2 = IN[6 * kCapS + i];
   p.id = __float_as_int(IN[7 * kCapS + i]);
+  p.w = 1.f;  // weighted species do not use the small-tile kernel
   return p;
 }
 
@@ -1538,7 +1551,7 @@ __global__ void __launch_bounds__(kThreads, 3)
             const int i = first + r;
             const long long s = i < ns ? base + i : base + cap - ni + (i - ns);
             qq[r] = P{A.in.p.cell[s], A.in.p.o[0][s], A.in.p.o[1][s], NDIM == 3 ? A.in.p.o[2][s] : 0.f,
-                      A.in.p.u[0][s], A.in.p.u[1][s], A.in.p.u[2][s], has_id ? A.in.p.id[s] : 0};
+                      A.in.p.u[0][s], A.in.p.u[1][s], A.in.p.u[2][s], has_id ? A.in.p.id[s] : 0, 1.f};
           }
         }
         Acc acc;
@@ -1676,6 +1689,7 @@ __global__ void k_flatten(Tiles tg, TileSide in, const long long* out_off, Flat3
       out.u[1][w] = in.p.u[1][s];
       out.u[2][w] = in.p.u[2][s];
       if (out.id) out.id[w] = in.p.id ? in.p.id[s] : 0;
+      if (out.w) out.w[w] = in.p.w ? in.p.w[s] : 1.f;
     }
     __syncthreads();
     if (threadIdx.x == 0) done += tot;
@@ -1706,6 +1720,7 @@ __global__ void k_flat_scatter(Flat32 f, long long n, Tiles tg, int* cursor, Par
   out.u[1][s] = f.u[1][k];
   out.u[2][s] = f.u[2][k];
   if (out.id) out.id[s] = f.id ? f.id[k] : 0;
+  if (out.w) out.w[s] = f.w ? f.w[k] : 1.f;
 }
 
 __global__ void k_flat_to_global(int ndim, Tiles tg, PushConst C, Flat32 f, long long n, double* x, double* u) {
@@ -1726,7 +1741,7 @@ __global__ void k_flat_to_global(int ndim, Tiles tg, PushConst C, Flat32 f, long
 // global FP64 position -> tile, packed local cell, FP32 offset
 __global__ void k_global_to_flat(int ndim, Layout L, Tiles tg, PushConst C, const double* x0, const double* x1,
                                  const double* x2, const double* u0, const double* u1, const double* u2,
-                                 const int* id, long long n, Flat32 out, int* status) {
+                                 const int* id, const double* w, long long n, Flat32 out, int* status) {
   const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= n) return;
   const double* xs[3] = {x0, x1, x2};
@@ -1775,6 +1790,7 @@ __global__ void k_global_to_flat(int ndim, Layout L, Tiles tg, PushConst C, cons
   out.u[1][k] = (float)u1[k];
   out.u[2][k] = (float)u2[k];
   if (out.id) out.id[k] = id ? id[k] : (int)k;
+  if (out.w) out.w[k] = w ? (float)w[k] : 1.f;
 }
 
 // charge density with linear weights (FP64 atomics) of every particle in the store
@@ -1821,6 +1837,7 @@ __global__ void k_tiled_rho(Layout L, PushConst C, Tiles tg, TileSide in, double
         for (int q = 0; q < 8; ++q) acc[q] = 0.f;
       }
       const float e0 = in.p.o[0][s], e1 = in.p.o[1][s], e2 = tg.ndim == 3 ? in.p.o[2][s] : 0.f;
+      const float pw = in.p.w ? in.p.w[s] : 1.f;
 #pragma unroll
       for (int c3 = 0; c3 < 2; ++c3)
 #pragma unroll
@@ -1829,7 +1846,7 @@ __global__ void k_tiled_rho(Layout L, PushConst C, Tiles tg, TileSide in, double
           for (int c1 = 0; c1 < 2; ++c1) {
             float w = (c1 ? e0 : 1.f - e0) * (c2 ? e1 : 1.f - e1);
             if (tg.ndim == 3) w *= (c3 ? e2 : 1.f - e2);
-            acc[c3 * 4 + c2 * 2 + c1] += w;
+            acc[c3 * 4 + c2 * 2 + c1] += w * pw;
           }
       if (other) {
         int od[3];
@@ -1849,36 +1866,35 @@ __global__ void k_tiled_kinetic(PushConst C, Tiles tg, TileSide in, double* ke, 
   const int t = blockIdx.x;
   int n;
   tile_slot(tg, in, t, 0, n);
-  double v = 0.0;
-  int live = 0;
+  double v = 0.0, live = 0.0;  // live: charge weight of the tile's particles
   for (int k = threadIdx.x; k < n; k += blockDim.x) {
     const long long s = tile_slot(tg, in, t, k, n);
     if (in.p.cell[s] == kHoleCell) continue;
-    ++live;
+    const float pw = in.p.w ? in.p.w[s] : 1.f;
+    live += pw;
     // gamma - 1 = u^2 / (1 + gamma) in FP32 from the FP32 momenta (no
     // cancellation at small u), summed in FP64
     const float a = in.p.u[0][s], b = in.p.u[1][s], c = in.p.u[2][s];
     const float u2 = fmaf(a, a, fmaf(b, b, c * c));
-    v += (double)(u2 / (1.f + sqrtf(1.f + u2)));
+    v += (double)(pw * (u2 / (1.f + sqrtf(1.f + u2))));
   }
   v *= C.q * C.rqm;
   for (int o = 16; o > 0; o >>= 1) live += __shfl_down_sync(0xffffffffu, live, o);
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-  __shared__ int cnt[32];
+  __shared__ double cnt[32];
   if ((threadIdx.x & 31) == 0) {
     red[threadIdx.x >> 5] = v;
     cnt[threadIdx.x >> 5] = live;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    double s = 0.0;
-    long long c = 0;
+    double s = 0.0, c = 0.0;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
       s += red[w];
       c += cnt[w];
     }
     atomicAdd(ke, s);
-    atomicAdd(qsum, C.q * (double)c);
+    atomicAdd(qsum, C.q * c);
   }
 }
 
@@ -1893,6 +1909,10 @@ struct InjectSpec {
   double uth[3], ufl[3];
   unsigned long long seed;
   long long first;
+  double xlo[3], dx[3];  // lower corner of the window after the shift (lab frame), cell size
+  ProfileDev prof;
+  int has_prof;
+  int* kept;             // particles created
 };
 
 __global__ void k_inject(TileArgs A, Tiles tg, InjectSpec J, long long count) {
@@ -1919,6 +1939,16 @@ __global__ void k_inject(TileArgs A, Tiles tg, InjectSpec J, long long count) {
   q.u1 = uu[1];
   q.u2 = uu[2];
   q.id = (int)g;
+  q.w = 1.f;
+  if (J.has_prof) {  // the profile at the particle's lab-frame position
+    const double x[3] = {J.xlo[0] + (J.nx[0] - 1 + (si + 0.5) / J.ppc[0]) * J.dx[0],
+                         J.xlo[1] + (cj + (sj + 0.5) / J.ppc[1]) * J.dx[1],
+                         J.ndim == 3 ? J.xlo[2] + (ck + (sk + 0.5) / J.ppc[2]) * J.dx[2] : 0.0};
+    const double w = profile_weight(J.prof, x);
+    if (!(J.prof.density * w > J.prof.den_min)) return;  // no particle where the density is this low
+    q.w = (float)w;
+  }
+  atomicAdd(J.kept, 1);
   const int slot = atomicAdd(&A.out.inc[t], 1);
   if (slot < A.res[t]) {
     const long long s = A.base[t] + A.cap[t] - 1 - slot;
@@ -2241,7 +2271,8 @@ int tiled_push(const Layout& L, const PushConst& C, const Tiles& tg, const TileS
 
 void tiled_inject(const PushConst& C, const Tiles& tg, const TileSide& out, Flat32 spill, int* spill_count,
                   long long spill_cap, int* status, const int nx[3], const int ppc[3], const double uth[3],
-                  const double ufl[3], unsigned long long seed, long long first, long long count, cudaStream_t s) {
+                  const double ufl[3], unsigned long long seed, long long first, long long count,
+                  const ProfileDev* prof, int* kept, cudaStream_t s) {
   if (count <= 0) return;
   const TileArgs A = make_args(C, tg, out, out, spill, spill_count, spill_cap, nullptr, status);
   InjectSpec J;
@@ -2254,6 +2285,13 @@ void tiled_inject(const PushConst& C, const Tiles& tg, const TileSide& out, Flat
   }
   J.seed = seed;
   J.first = first;
+  for (int d = 0; d < 3; ++d) {
+    J.xlo[d] = C.xmin[d] + (d == 0 ? C.dx[0] : 0.0);  // the window after its one-cell shift
+    J.dx[d] = C.dx[d];
+  }
+  J.has_prof = prof != nullptr;
+  if (prof) J.prof = *prof;
+  J.kept = kept;
   k_inject<<<(unsigned)((count + 255) / 256), 256, 0, s>>>(A, tg, J, count);
 }
 
@@ -2282,10 +2320,11 @@ void flat_to_global(int ndim, const Tiles& tg, const PushConst& C, const Flat32&
 }
 
 void global_to_flat(int ndim, const Layout& L, const Tiles& tg, const PushConst& C, double* const x[3],
-                    double* const u[3], const int* id, long long n, Flat32 out, int* status, cudaStream_t s) {
+                    double* const u[3], const int* id, const double* w, long long n, Flat32 out, int* status,
+                    cudaStream_t s) {
   if (n == 0) return;
   k_global_to_flat<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(ndim, L, tg, C, x[0], x[1], x[2], u[0], u[1], u[2],
-                                                                id, n, out, status);
+                                                                id, w, n, out, status);
 }
 
 void tiled_rho(const Layout& L, const PushConst& C, const Tiles& tg, const TileSide& in, double* rho, cudaStream_t s) {

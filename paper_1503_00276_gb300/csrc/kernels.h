@@ -53,6 +53,7 @@ struct Plain {
   double* x[3];
   double* u[3];
   int* id;
+  double* w;              // charge weights (density profile); null: all 1
   long long n;
 };
 void plain_push(int ndim, const Layout& L, const PushConst& C, Plain p, double* const* f, double* const* j,
@@ -66,6 +67,7 @@ struct Part32 {           // one particle buffer (structure of arrays)
   float* o[3];            // in-cell offsets in [0,1)
   float* u[3];
   int* id;                // may be null
+  float* w;               // charge weights (density profile); null: all 1
 };
 struct Flat32 {           // unsorted staging form (load, rebuild, copy-out)
   int* tile;
@@ -73,6 +75,7 @@ struct Flat32 {           // unsorted staging form (load, rebuild, copy-out)
   float* o[3];
   float* u[3];
   int* id;
+  float* w;
 };
 struct Tiles {
   int ndim;
@@ -119,9 +122,52 @@ int tiled_push(const Layout& L, const PushConst& C, const Tiles& tg, const TileS
                 const SliceScratch* slices, cudaStream_t s);
 // moving window: `count` fresh particles of the front column appended to the
 // last tile column of side `out` (global particle indices first, ...)
+// A density profile on the device: per direction n[d] points (0: flat), at
+// x[d][0..n-1] with values f[d][...]; the weight is the product of the
+// piecewise-linear functions (constant beyond the ends), and no particle is
+// created where density * weight is not above den_min.
+struct ProfileDev {
+  int n[3];
+  const double* x[3];
+  const double* f[3];
+  double density, den_min;
+};
+// weight of the profile at position x (piecewise linear per direction,
+// constant beyond the ends; product over the directions)
+__device__ inline double profile_weight(const ProfileDev& P, const double x[3]) {
+  double w = 1.0;
+  for (int d = 0; d < 3; ++d) {
+    const int n = P.n[d];
+    if (n <= 0) continue;
+    const double* xs = P.x[d];
+    const double* fs = P.f[d];
+    double f;
+    if (x[d] <= xs[0]) {
+      f = fs[0];
+    } else if (x[d] >= xs[n - 1]) {
+      f = fs[n - 1];
+    } else {
+      int lo = 0, hi = n - 1;
+      while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (xs[mid] <= x[d])
+          lo = mid;
+        else
+          hi = mid;
+      }
+      const double slope = (fs[hi] - fs[lo]) / (xs[hi] - xs[lo]);
+      f = slope * (x[d] - xs[lo]) + fs[lo];
+    }
+    w *= f;
+  }
+  return w;
+}
+
+// `kept`: count of the particles created (those the profile keeps)
 void tiled_inject(const PushConst& C, const Tiles& tg, const TileSide& out, Flat32 spill, int* spill_count,
                   long long spill_cap, int* status, const int nx[3], const int ppc[3], const double uth[3],
-                  const double ufl[3], unsigned long long seed, long long first, long long count, cudaStream_t s);
+                  const double ufl[3], unsigned long long seed, long long first, long long count,
+                  const ProfileDev* prof, int* kept, cudaStream_t s);
 // Batched form: many simulations (one table entry per simulation and species)
 // in one launch of the sorting kernel.  tiled_fill_args writes one entry
 // (tiled_args_bytes bytes) on the host; tile0[n] is the exclusive prefix of
@@ -145,7 +191,8 @@ void flat_scatter(const Flat32& f, long long n, const Tiles& tg, int* cursor, Pa
 void flat_to_global(int ndim, const Tiles& tg, const PushConst& C, const Flat32& f, long long n, double* x, double* u,
                     cudaStream_t s);
 void global_to_flat(int ndim, const Layout& L, const Tiles& tg, const PushConst& C, double* const x[3],
-                    double* const u[3], const int* id, long long n, Flat32 out, int* status, cudaStream_t s);
+                    double* const u[3], const int* id, const double* w, long long n, Flat32 out, int* status,
+                    cudaStream_t s);
 void tiled_rho(const Layout& L, const PushConst& C, const Tiles& tg, const TileSide& in, double* rho, cudaStream_t s);
 void tiled_kinetic(const PushConst& C, const Tiles& tg, const TileSide& in, Diag64* acc, cudaStream_t s);
 
@@ -161,6 +208,13 @@ struct LatticeSpec {
 };
 void lattice_load(const LatticeSpec& S, long long first, long long count, double* const x[3], double* const u[3],
                   int* id, cudaStream_t s);
+// Weights of `count` FP64 particles from the profile and the keep flags
+// (density * weight > den_min); then the kept ones moved, in order, to
+// dst (x, u, id, w) from index dst_first on.  Returns the number kept (syncs).
+long long profile_compact(int ndim, const ProfileDev& P, long long count, double* const x[3], double* const u[3],
+                          const int* id, double* const dx[3], double* const du[3], int* did, double* dw,
+                          void* scratch, cudaStream_t s);
+size_t profile_scratch_bytes(long long count);
 
 // ----------------------------------------------------------------- sorting
 // Exclusive prefix sum of n int32 counts into int64 starts; `scratch` holds at

@@ -83,3 +83,12 @@ def test_config1_pulse_intensity_fwhm_is_the_stated_duration():
     inten = oracle.laser_envelope(xi, las.rise, las.length, las.fall) ** 2
     above = xi[inten >= 0.5]
     assert abs((above[-1] - above[0]) - 1.5) < 2e-3
+
+
+def test_config1_vacuum_gap_puts_the_plasma_edge_ahead_of_the_pulse():
+    g, sps, las, _ = workload.config1(vacuum_gap=2.0)
+    edge = g.nx[0] * g.dx[0] - las.start + 2.0
+    x = np.array([[edge - 1e-3, 1.0, 0.0], [edge + 1e-3, 1.0, 0.0]])
+    w = workload.profile_weight(sps[0], x)
+    assert w[0] == 0.0 and w[1] == 1.0
+    assert workload.load_weighted(g, sps[0])[0].shape[0] == 0  # the window starts in vacuum

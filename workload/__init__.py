@@ -26,6 +26,7 @@ x1-fastest order.
 """
 from __future__ import annotations
 
+import dataclasses
 import math
 from dataclasses import dataclass, field
 
@@ -250,18 +251,24 @@ def config0(seed: int = 20001):
     return g, [s], 100
 
 
-def config1(seed: int = 20002):
+def config1(seed: int = 20002, vacuum_gap: float = None):
     """2D3V laser wakefield: 2048 x 256 cells, dx1 = 0.05, dx2 = 0.2, 8 ppc (4 x 2)
     cold uniform electrons, window moving at c in x1, a pulse a0 = 2,
     omega0/omega_p = 10, spot 4, polarised in x2, with the thesis' polynomial
     rise and fall of 1.945 each: the intensity f^2 of the envelope then has a
     full width at half maximum of 1.5 (the duration given); front 1.0 behind
-    the +x1 edge; 2000 steps.  The plasma fills the window from the start (no
-    vacuum gap: density profiles are not part of this hot path)."""
+    the +x1 edge; 2000 steps.  The plasma fills the window from the start; with
+    ``vacuum_gap`` it begins that far ahead of the pulse front instead (a
+    density profile: vacuum, then density 1), so the window meets it as it
+    moves."""
     dx = (0.05, 0.2, 1.0)
     g = Grid(ndim=2, nx=(2048, 256, 1), dx=dx, dt=courant_dt(dx, 2), move_window=True)
     s = Species(rqm=-1.0, ppc=(4, 2, 1), uth=(0.0, 0.0, 0.0), seed=seed)
     las = Laser(vosc=2.0, rkkp=10.0, w0=4.0, rise=1.945, length=0.0, fall=1.945, start=1.0)
+    if vacuum_gap is not None:
+        edge = g.nx[0] * dx[0] - las.start + vacuum_gap  # lab x1 where the plasma begins
+        s = dataclasses.replace(s, profile=(((0.0, edge, edge + 1e-9, 1e9), (0.0, 0.0, 1.0, 1.0)), None),
+                                den_min=1e-6)
     return g, [s], las, 2000
 
 

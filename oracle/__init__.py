@@ -57,7 +57,8 @@ class OraGrid(C.Structure):
     _fields_ = [("ndim", C.c_int), ("nx", C.c_int * 3), ("dx", C.c_double * 3), ("xmin", C.c_double * 3),
                 ("dt", C.c_double), ("e0", C.c_double * 3), ("b0", C.c_double * 3),
                 ("smooth_level", C.c_int * 3), ("smooth_w", ((C.c_double * 3) * MAX_PASS) * 3),
-                ("rho_bg", C.c_double), ("open_x1", C.c_int), ("isis", C.c_int)]
+                ("rho_bg", C.c_double), ("open_x1", C.c_int), ("isis", C.c_int),
+                ("inc_b2", C.POINTER(C.c_double)), ("inc_b3", C.POINTER(C.c_double))]
 
 
 class OraSpecies(C.Structure):
@@ -201,7 +202,9 @@ class State:
         field solve, then the shift of the fields and the injection."""
         g = self.grid
         dx1 = float(g.dx[0])
-        shift = int(math.floor(float(self.nstep + 1) * float(g.dt) / dx1)) > self.shifts
+        # the window moves at c from time window_start on
+        lag = float(self.nstep + 1) * float(g.dt) - float(getattr(g, "window_start", 0.0))
+        shift = lag > 0.0 and int(math.floor(lag / dx1)) > self.shifts
         self.particle_phase()
         lo = self.og.xmin[0] + (dx1 if shift else 0.0)
         hi = lo + int(g.nx[0]) * dx1
@@ -248,8 +251,28 @@ class State:
         for c in self.cur:
             lib().ora_smooth(C.byref(self.og), _dp(c))
 
+    def add_antenna(self, laser):
+        """A pulse entering through the lower x1 boundary (open x1 only)."""
+        assert getattr(self.grid, "move_window", False), "an antenna needs the open x1 boundary"
+        if not hasattr(self, "antennas"):
+            self.antennas = []
+            self.xmin1_initial = float(self.og.xmin[0])
+        self.antennas.append(laser)
+
     def field_solve(self):
+        ants = getattr(self, "antennas", [])
+        if ants:  # B just below the lower x1 boundary at t = (n + 1/2) dt
+            tt = (self.nstep + 0.5) * float(self.grid.dt)
+            b2 = b3 = 0.0
+            for las in ants:
+                p2, p3 = antenna_planes(self.grid, las, tt, float(self.og.xmin[0]), self.xmin1_initial)
+                b2, b3 = b2 + p2, b3 + p3
+            self._inc = (np.ascontiguousarray(b2, dtype=np.float64), np.ascontiguousarray(b3, dtype=np.float64))
+            self.og.inc_b2 = _dp(self._inc[0])
+            self.og.inc_b3 = _dp(self._inc[1])
         lib().ora_field_solve(C.byref(self.og), self._fp, self._cp)
+        self.og.inc_b2 = None
+        self.og.inc_b3 = None
 
     def rho(self) -> np.ndarray:
         r = np.zeros_like(self.cur[0])
@@ -408,6 +431,33 @@ def laser_envelope(xi, rise, length, fall):
     return f
 
 
+def _pulse_amp(laser, ndim, x, a, xfront, ct, c3, xfocus):
+    """-vosc k f g T sin(psi) of a pulse moving in +x_a at positions x (three
+    arrays), for the front at xfront, the transverse axis at (ct, c3) and the
+    focal plane at xfocus (None: the waist profile everywhere); see
+    laser_fields."""
+    t = 1 - a
+    k = laser.rkkp
+    r2 = (x[t] - ct) ** 2
+    if ndim == 3:
+        r2 = r2 + (x[2] - c3) ** 2
+    f = laser_envelope(xfront - x[a], laser.rise, laser.length, laser.fall)
+    w2 = laser.w0 ** 2 * np.ones(np.shape(r2))
+    g = np.ones(np.shape(r2))
+    psi = k * (x[a] - xfront) + laser.phase
+    if xfocus is not None:
+        zr = 0.5 * k * laser.w0 ** 2
+        z = x[a] - xfocus
+        q = 1.0 + (z / zr) ** 2
+        w2 = laser.w0 ** 2 * q
+        g = q ** -0.5 if ndim == 3 else q ** -0.25
+        with np.errstate(divide="ignore", invalid="ignore"):
+            curv = np.where(z != 0.0, k * r2 / (2.0 * (z + zr * zr / z)), 0.0)
+        gouy = np.arctan(z / zr)
+        psi = psi + curv - (gouy if ndim == 3 else 0.5 * gouy)
+    return -laser.vosc * k * f * g * np.exp(-r2 / w2) * np.sin(psi)
+
+
 def laser_fields(grid, laser, xmin1=None):
     """E and B of a pulse at t = 0, each component at its own staggered
     position.  The pulse moves in +x_a (wavetype 1: a = x1, 2: a = x2); with
@@ -432,31 +482,14 @@ def laser_fields(grid, laser, xmin1=None):
     ct = xmin[t] + 0.5 * nn[t] * dx[t] + laser.offset[0]
     c3 = (xmin[2] + 0.5 * nz * dx[2] + laser.offset[1]) if grid.ndim == 3 else 0.0
     focus = getattr(laser, "focus", None)
+    xfocus = None if focus is None else upper - focus
     th = math.radians(laser.pol)
     k_, j_, i_ = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
-    k = laser.rkkp
 
     def amp(s1, s2, s3):
         x = [xmin[0] + (i_ + s1) * dx[0], xmin[1] + (j_ + s2) * dx[1],
              xmin[2] + (k_ + s3) * dx[2] if grid.ndim == 3 else np.zeros(i_.shape)]
-        r2 = (x[t] - ct) ** 2
-        if grid.ndim == 3:
-            r2 = r2 + (x[2] - c3) ** 2
-        f = laser_envelope(xfront - x[a], laser.rise, laser.length, laser.fall)
-        w2 = laser.w0 ** 2 * np.ones(r2.shape)
-        g = np.ones(r2.shape)
-        psi = k * (x[a] - xfront) + laser.phase
-        if focus is not None:
-            zr = 0.5 * k * laser.w0 ** 2
-            z = x[a] - (upper - focus)
-            q = 1.0 + (z / zr) ** 2
-            w2 = laser.w0 ** 2 * q
-            g = q ** -0.5 if grid.ndim == 3 else q ** -0.25
-            with np.errstate(divide="ignore", invalid="ignore"):
-                curv = np.where(z != 0.0, k * r2 / (2.0 * (z + zr * zr / z)), 0.0)
-            gouy = np.arctan(z / zr)
-            psi = psi + curv - (gouy if grid.ndim == 3 else 0.5 * gouy)
-        return -laser.vosc * k * f * g * np.exp(-r2 / w2) * np.sin(psi)
+        return _pulse_amp(laser, grid.ndim, x, a, xfront, ct, c3, xfocus)
 
     zero = np.zeros((nz, ny, nx))
     s3 = 0.5 if grid.ndim == 3 else 0.0
@@ -472,3 +505,33 @@ def laser_fields(grid, laser, xmin1=None):
         out[3] = amp(0.0, 0.5, s3) * math.sin(th)
         out[5] = -amp(0.5, 0.5, 0.0) * math.cos(th)
     return out
+
+
+def antenna_planes(grid, laser, time, xlo1, xmin1_initial):
+    """B2 and B3 ([nz][ny]) just below the lower x1 boundary (x1 = xlo1 -
+    dx1/2) at `time`, of a pulse that enters the box through that boundary
+    moving in +x1 (the antenna form of the pulse input): its front crosses the
+    boundary at time `start`, so x_front = xlo1 + (time - start); the focal
+    plane (if any) lies `focus` into the box from the initial boundary
+    xmin1_initial; otherwise as laser_fields (B3 = E2, B2 = -E3)."""
+    ny = int(grid.nx[1])
+    nz = int(grid.nx[2]) if grid.ndim == 3 else 1
+    dx = grid.dx
+    ct = grid.xmin[1] + 0.5 * ny * dx[1] + laser.offset[0]
+    c3 = (grid.xmin[2] + 0.5 * nz * dx[2] + laser.offset[1]) if grid.ndim == 3 else 0.0
+    focus = getattr(laser, "focus", None)
+    xfocus = None if focus is None else xmin1_initial + focus
+    xfront = xlo1 + (time - laser.start)
+    th = math.radians(laser.pol)
+    k_, j_ = np.meshgrid(np.arange(nz), np.arange(ny), indexing="ij")
+    x1 = np.full(j_.shape, xlo1 - 0.5 * dx[0])
+    s3 = 0.5 if grid.ndim == 3 else 0.0
+
+    def amp(s2, s3_):
+        x = [x1, grid.xmin[1] + (j_ + s2) * dx[1],
+             grid.xmin[2] + (k_ + s3_) * dx[2] if grid.ndim == 3 else np.zeros(j_.shape)]
+        return _pulse_amp(laser, grid.ndim, x, 0, xfront, ct, c3, xfocus)
+
+    b2 = -amp(0.0, s3) * math.sin(th)
+    b3 = amp(0.5, 0.0) * math.cos(th)
+    return np.ascontiguousarray(b2), np.ascontiguousarray(b3)

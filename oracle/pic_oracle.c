@@ -462,8 +462,12 @@ static void advance_e(const ora_grid* g, double* const fld[6], double* const cur
       for (long i = 0; i < nx; ++i) {
         long c = at(g, i, j, k);
         double dB3d2 = (B3[c] - B3[at(g, i, j - 1, k)]) / g->dx[1];
-        double dB3d1 = (B3[c] - rd(g, B3, i - 1, j, k)) / g->dx[0];
-        double dB2d1 = (B2[c] - rd(g, B2, i - 1, j, k)) / g->dx[0];
+        /* below an open lower x1 boundary: the entering pulse's B (or 0) */
+        const int lower = g->open_x1 && i == 0;
+        double b3m = lower ? (g->inc_b3 ? g->inc_b3[k * ny + j] : 0.0) : rd(g, B3, i - 1, j, k);
+        double b2m = lower ? (g->inc_b2 ? g->inc_b2[k * ny + j] : 0.0) : rd(g, B2, i - 1, j, k);
+        double dB3d1 = (B3[c] - b3m) / g->dx[0];
+        double dB2d1 = (B2[c] - b2m) / g->dx[0];
         double dB1d2 = (B1[c] - B1[at(g, i, j - 1, k)]) / g->dx[1];
         double dB2d3 = d3 ? (B2[c] - B2[at(g, i, j, k - 1)]) / g->dx[2] : 0.0;
         double dB1d3 = d3 ? (B1[c] - B1[at(g, i, j, k - 1)]) / g->dx[2] : 0.0;

@@ -24,6 +24,11 @@ typedef struct {
                                             particles are not wrapped in x1 */
   int isis;                              /* 1: ISIS current deposit (2D3V) instead of
                                             TRISTAN / Villasenor-Buneman */
+  /* open x1: B2 and B3 just below the lower x1 boundary ([nz][ny], at
+     x1 = xmin - dx1/2 and time n + 1/2), read by the E update there instead
+     of 0 -- a pulse entering through that boundary; NULL: 0 */
+  const double* inc_b2;
+  const double* inc_b3;
 } ora_grid;
 
 typedef struct {

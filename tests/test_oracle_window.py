@@ -184,3 +184,49 @@ def test_focused_pulse_narrows_to_the_waist_at_the_focal_plane():
         st2.fld[c][...] = f
     st2.step(n)
     assert _width_x2(st2, g) > 1.8 * w0
+
+
+def test_window_starts_moving_at_window_start():
+    dx = (0.1, 0.4, 1.0)
+    g = workload.Grid(ndim=2, nx=(40, 4, 1), dx=dx, dt=workload.courant_dt(dx, 2), move_window=True,
+                      window_start=1.0)
+    st = _vacuum(g)
+    n0 = int(1.0 / g.dt)
+    st.step(n0)
+    assert st.shifts == 0
+    st.step(30)
+    assert st.shifts == int(math.floor(((n0 + 30) * g.dt - 1.0) / dx[0]))
+
+
+def test_antenna_pulse_enters_through_the_lower_boundary():
+    """A pulse driven through the lower x1 boundary (the window held still)
+    enters the vacuum box whole: once it is in, it carries the field energy of
+    the same pulse set up inside the box, its centroid is where the front
+    travelling at the discrete group velocity puts it, and nothing is left
+    behind at the boundary."""
+    dx = (0.05, 0.4, 1.0)
+    g = workload.Grid(ndim=2, nx=(400, 16, 1), dx=dx, dt=workload.courant_dt(dx, 2), move_window=True,
+                      window_start=1e9)
+    las = workload.Laser(vosc=0.1, rkkp=6.0, w0=1e3, rise=2.0, length=0.0, fall=2.0, start=0.5, antenna=True)
+    st = _vacuum(g)
+    st.add_antenna(las)
+    n = int(round(7.0 / g.dt))
+    st.step(n)
+    t = n * g.dt
+    vg = _group_velocity(las.rkkp, dx[0], g.dt)
+    # the same pulse set up in the box with its centre where the injected one should be
+    ref = _vacuum(g)
+    centre = (t - las.start) * vg - 2.0
+    box = dataclasses.replace(las, antenna=False, start=g.nx[0] * dx[0] - (centre + 2.0))
+    for c, f in enumerate(oracle.laser_fields(g, box)):
+        ref.fld[c][...] = f
+    e_inj, e_box = st.field_energy(), ref.field_energy()
+    assert abs(e_inj - e_box) < 0.02 * e_box, (e_inj, e_box)
+    xc = _centroid(st, dx[0], 0.0)
+    assert abs(xc - centre) < 0.1, (xc, centre)
+    tail = np.abs(st.fld[1][0][:, : int(1.0 / dx[0])]).max()
+    assert tail < 0.01 * 0.1 * 6.0
+    # the same field, not just the same energy: sign and phase of E2 and B3
+    for c in (1, 5):
+        a, b = st.fld[c].ravel(), ref.fld[c].ravel()
+        assert np.dot(a, b) / math.sqrt(np.dot(a, a) * np.dot(b, b)) > 0.98, c

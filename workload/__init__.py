@@ -81,6 +81,7 @@ class Grid:
     rho_bg: float = 1.0            # fixed neutralising ion background density
     init_e_gauss_x1: bool = False  # initial E1 from the discrete Gauss law along x1
     move_window: bool = False      # window moving at c in x1 (x1 open; periodic in x2, x3)
+    window_start: float = 0.0      # time from which the window moves (before it: x1 open, static)
     deposit: str = "vb"            # current deposit: "vb" (TRISTAN / Villasenor-Buneman) or "isis" (2D)
 
     @property
@@ -140,6 +141,7 @@ class Laser:
     offset: tuple = (0.0, 0.0)
     wavetype: int = 1
     focus: object = None
+    antenna: bool = False          # enters through the lower x1 boundary; its front crosses it at time `start`
 
 
 def courant_dt(dx, ndim: int, frac: float = 0.99) -> float:

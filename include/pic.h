@@ -133,6 +133,8 @@ typedef struct {
                                the two orders of orthogonal moves of the whole path, not
                                split; 2D3V only, else PIC_EUNSUPPORTED).  Both conserve
                                charge exactly; they differ by a divergence-free current. */
+  double window_start;      /* move_window: time from which the window moves (before it
+                               the box is still, x1 open); 0 = from the start */
 } pic_grid;
 
 enum { PIC_DEPOSIT_TRISTAN = 0, PIC_DEPOSIT_ISIS = 1 };
@@ -426,6 +428,13 @@ typedef struct {
   int wavetype;             /* 1 (or 0): along x1; 2: along x2 */
   int focus_on;
   double focus;
+  int antenna;              /* 1: the pulse enters through the lower x1 boundary instead
+                               of being set up in the box (move_window simulations, whose
+                               x1 is open; wavetype 1): below that boundary the E update
+                               reads the pulse's B, its front crossing the boundary at time
+                               `start`; `focus` is then measured into the box from that
+                               boundary.  Every later pic_step drives it (not stored in
+                               checkpoints). */
 } pic_laser;
 
 pic_status pic_laser_add(pic_sim* S, const pic_laser* laser);

@@ -79,6 +79,7 @@ def _grid_struct(grid, precision, tile=None, slack=0.0, sort_period=0, ctas_per_
     if dep not in ("vb", "isis"):
         raise ValueError(f"unknown deposit {dep!r} (vb or isis)")
     g.deposit = 1 if dep == "isis" else 0
+    g.window_start = float(getattr(grid, "window_start", 0.0))
     return g
 
 
@@ -182,6 +183,7 @@ class Simulation:
         focus = getattr(laser, "focus", None)
         L.focus_on = int(focus is not None)
         L.focus = float(focus) if focus is not None else 0.0
+        L.antenna = int(bool(getattr(laser, "antenna", False)))
         check(self._lib.pic_laser_add(self._h, C.byref(L)), "pic_laser_add")
 
     # -- checkpoint / restart ---------------------------------------------------

@@ -30,7 +30,8 @@ class PicGrid(C.Structure):
                 ("smooth_level", C.c_int * 3), ("smooth_w", ((C.c_double * 3) * MAX_SMOOTH) * 3),
                 ("rho_bg", C.c_double), ("init_e_gauss_x1", C.c_int), ("precision", C.c_int),
                 ("tile", C.c_int * 3), ("slack", C.c_double), ("sort_period", C.c_int),
-                ("ctas_per_sm", C.c_int), ("move_window", C.c_int), ("deposit", C.c_int)]
+                ("ctas_per_sm", C.c_int), ("move_window", C.c_int), ("deposit", C.c_int),
+                ("window_start", C.c_double)]
 
 
 class PicSpecies(C.Structure):
@@ -46,7 +47,7 @@ class PicLaser(C.Structure):
     _fields_ = [("vosc", C.c_double), ("rkkp", C.c_double), ("w0", C.c_double), ("rise", C.c_double),
                 ("fall", C.c_double), ("length", C.c_double), ("start", C.c_double), ("pol", C.c_double),
                 ("phase", C.c_double), ("offset", C.c_double * 2), ("wavetype", C.c_int), ("focus_on", C.c_int),
-                ("focus", C.c_double)]
+                ("focus", C.c_double), ("antenna", C.c_int)]
 
 
 class PicTuneChoice(C.Structure):

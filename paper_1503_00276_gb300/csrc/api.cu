@@ -170,6 +170,11 @@ struct pic_sim {
   int sticky_flags = 0;
   long long nlaunch = 0;  // kernels launched by pic_step since the last reset
   bool no_small = false;  // member of a batch or moving window: the general tile kernel only
+  // laser antennas (pulses entering through the lower x1 boundary)
+  std::vector<unsigned char> h_ants;  // antenna_bytes() per pulse
+  void* d_ants = nullptr;
+  int n_ants = 0;
+  float* d_inc = nullptr;             // [2][ny nz] incident B2, B3 below the boundary
   bool moving = false;    // window moving at c in +x1
   long long shifts = 0;   // one-cell shifts of the window so far
   bool in_batch = false;  // stepped by its batch; pic_step refuses it
@@ -960,7 +965,13 @@ void field_step(pic_sim* S) {
     // the sweeps wrap their neighbours periodically; the guard cells (read by
     // the particle kernels) are refreshed once at the end
     yee_b_half<T>(L, e, b, S->g.dt, dx, S->s);
-    yee_e<T>(L, e, b, j, S->g.dt, dx, S->s);
+    const float* inc = nullptr;
+    if (S->n_ants > 0) {  // the entering pulses' B below the lower x1 boundary at t = (n + 1/2) dt
+      antenna_plane(L, S->d_ants, S->n_ants, ((double)S->step + 0.5) * S->g.dt, S->g.xmin[0], S->d_inc, S->s);
+      inc = S->d_inc;
+      S->nlaunch += 1;
+    }
+    yee_e<T>(L, e, b, j, S->g.dt, dx, S->s, inc);
     yee_b_half<T>(L, e, b, S->g.dt, dx, S->s);
     T* eb[6] = {e[0], e[1], e[2], b[0], b[1], b[2]};
     fill_guards<T>(L, eb, 6, S->s);
@@ -972,7 +983,9 @@ pic_status one_step(pic_sim* S, bool check_now) {
   Span whole(S, 4);
   // moving window: shift by one cell at the end of the step that brings c t a
   // full cell past the last shift
-  const bool shift = S->moving && (long long)std::floor((double)(S->step + 1) * S->g.dt / S->g.dx[0]) > S->shifts;
+  // the window moves at c from window_start on
+  const double lag = (double)(S->step + 1) * S->g.dt - S->g.window_start;
+  const bool shift = S->moving && lag > 0.0 && (long long)std::floor(lag / S->g.dx[0]) > S->shifts;
   cudaMemsetAsync(S->cur, 0, 3 * elem_bytes(S) * (size_t)S->L.plane, S->s);
   {
     Span sp(S, 0);
@@ -2398,6 +2411,11 @@ pic_status pic_laser_add(pic_sim* S, const pic_laser* L) {
     set_error("pic_laser_add: bad arguments");
     return PIC_EINVAL;
   }
+  if (L->antenna && (!S->moving || S->prec != PIC_FP32_CELLOFF || L->wavetype == 2)) {
+    set_error("pic_laser_add: an antenna needs the open x1 boundary of a move_window simulation (FP32) and "
+              "wavetype 1");
+    return PIC_EUNSUPPORTED;
+  }
   const pic_grid& g = S->g;
   const double nxr[3] = {(double)S->L.nx, (double)S->L.ny, (double)S->L.nz};
   const int a = L->wavetype == 2 ? 1 : 0, tr = 1 - a;  // propagation and in-plane transverse axes
@@ -2423,6 +2441,26 @@ pic_status pic_laser_add(pic_sim* S, const pic_laser* L) {
   p[18] = a;
   p[19] = L->focus_on ? 1.0 : 0.0;
   p[20] = upper - L->focus;  // focal plane
+  if (L->antenna) {  // driven at the lower x1 boundary from the next step on
+    p[6] = L->start;                   // time at which the front crosses the boundary
+    p[20] = g.xmin[0] + L->focus;      // focal plane, into the box from that boundary
+    const size_t rb = antenna_bytes();
+    S->h_ants.resize(rb * (size_t)(S->n_ants + 1));
+    antenna_store(p, S->h_ants.data() + rb * (size_t)S->n_ants);
+    void* d = S->al.get(S->h_ants.size());
+    if (!S->d_inc) S->d_inc = (float*)S->al.get(2 * sizeof(float) * (size_t)S->L.ny * (size_t)S->L.nz);
+    if (!d || !S->d_inc) {
+      S->al.put(d);
+      set_error("out of device memory (antenna)");
+      return PIC_ENOMEM;
+    }
+    cudaMemcpyAsync(d, S->h_ants.data(), S->h_ants.size(), cudaMemcpyHostToDevice, S->s);
+    if (cudaStreamSynchronize(S->s) != cudaSuccess) return cuda_check("pic_laser_add");
+    S->al.put(S->d_ants);
+    S->d_ants = d;
+    S->n_ants += 1;
+    return PIC_OK;
+  }
   if (S->prec == PIC_FP64_PLAIN) {
     double* f[6];
     for (int c = 0; c < 6; ++c) f[c] = fld_ptr<double>(S, c);

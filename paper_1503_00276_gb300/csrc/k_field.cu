@@ -5,6 +5,7 @@
 // rounds every operation exactly as written; the FP32 instantiation is
 // bandwidth-bound, so the contraction would buy nothing there.
 #include <cstdio>
+#include <cstring>
 
 #include "kernels.h"
 
@@ -226,7 +227,7 @@ __global__ void k_yee_b_half_f32(Layout L, Ptr3<float> E, Ptr3<float> B, float h
 }
 
 __global__ void k_yee_e_f32(Layout L, Ptr3<float> E, Ptr3<float> B, Ptr3<float> J, float dt, float i1, float i2,
-                            float i3) {
+                            float i3, const float* inc) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   const int k = blockIdx.z;
@@ -238,10 +239,14 @@ __global__ void k_yee_e_f32(Layout L, Ptr3<float> E, Ptr3<float> B, Ptr3<float> 
   const float* __restrict__ B2 = B.c[1];
   const float* __restrict__ B3 = B.c[2];
   const float b1 = __ldg(B1 + c), b2 = __ldg(B2 + c), b3 = __ldg(B3 + c);
-  const bool back = L.open_x && i == 0;  // beyond an open x1 boundary: B = 0
+  // beyond an open x1 boundary: B = 0, or that of a pulse entering there
+  const bool back = L.open_x && i == 0;
+  const long long p = (long long)k * L.ny + j;  // this row in the incident planes
+  const float b3m = back ? (inc ? inc[(long long)L.ny * L.nz + p] : 0.f) : __ldg(B3 + cx);
+  const float b2m = back ? (inc ? inc[p] : 0.f) : __ldg(B2 + cx);
   const float dB3d2 = (b3 - __ldg(B3 + cy)) * i2;
-  const float dB3d1 = (b3 - (back ? 0.f : __ldg(B3 + cx))) * i1;
-  const float dB2d1 = (b2 - (back ? 0.f : __ldg(B2 + cx))) * i1;
+  const float dB3d1 = (b3 - b3m) * i1;
+  const float dB2d1 = (b2 - b2m) * i1;
   const float dB1d2 = (b1 - __ldg(B1 + cy)) * i2;
   float dB2d3 = 0.f, dB1d3 = 0.f;
   if (L.ndim == 3) {
@@ -515,11 +520,12 @@ void yee_b_half(const Layout& L, T* const* e, T* const* b, double dt, const doub
 }
 
 template <typename T>
-void yee_e(const Layout& L, T* const* e, T* const* b, T* const* j, double dt, const double dx[3], cudaStream_t s) {
+void yee_e(const Layout& L, T* const* e, T* const* b, T* const* j, double dt, const double dx[3], cudaStream_t s,
+           const float* inc) {
   Ptr3<T> E{{e[0], e[1], e[2]}}, B{{b[0], b[1], b[2]}}, J{{j[0], j[1], j[2]}};
   if constexpr (sizeof(T) == 4)
     k_yee_e_f32<<<interior_grid(L), kBlock, 0, s>>>(L, E, B, J, (float)dt, (float)(1.0 / dx[0]),
-                                                    (float)(1.0 / dx[1]), (float)(1.0 / dx[2]));
+                                                    (float)(1.0 / dx[1]), (float)(1.0 / dx[2]), inc);
   else
     k_yee_e<T><<<interior_grid(L), kBlock, 0, s>>>(L, E, B, J, (T)dt, (T)dx[0], (T)dx[1], (T)dx[2]);
 }
@@ -530,6 +536,65 @@ void shift_x(const Layout& L, T* const* comps, int ncomp, cudaStream_t s) {
   for (int c = 0; c < ncomp; ++c) P.c[c] = comps[c];
   const long long rows = (long long)ncomp * L.ny * L.nz;
   k_shift_x<T><<<(unsigned)((rows + 7) / 8), 256, 0, s>>>(L, P, ncomp);
+}
+
+// B2 and B3 of the antenna pulses just below the lower x1 boundary (x1 =
+// xlo1 - dx1/2) at time t, summed into inc[2][ny nz]: each pulse's front is
+// at xlo1 + (t - start); B3 = E2, B2 = -E3 of laser_amp at the B positions.
+__global__ void k_antenna_plane(Layout L, const LaserDev* P, int n, double t, double xlo1, float* inc) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int k = blockIdx.y;
+  if (j >= L.ny) return;
+  const double h3 = L.ndim == 3 ? 0.5 : 0.0;
+  double b2 = 0.0, b3 = 0.0;
+  for (int a = 0; a < n; ++a) {
+    LaserDev Q = P[a];
+    Q.xfront = xlo1 + (t - Q.xfront);  // xfront holds `start` for an antenna
+    const double x1 = xlo1 - 0.5 * Q.dx[0];
+    const double xb2[3] = {x1, Q.xmin[1] + j * Q.dx[1], Q.xmin[2] + (k + h3) * Q.dx[2]};
+    const double xb3[3] = {x1, Q.xmin[1] + (j + 0.5) * Q.dx[1], Q.xmin[2] + k * Q.dx[2]};
+    b2 -= laser_amp(Q, L.ndim, xb2) * Q.spol;
+    b3 += laser_amp(Q, L.ndim, xb3) * Q.cpol;
+  }
+  const long long p = (long long)k * L.ny + j;
+  inc[p] = (float)b2;
+  inc[(long long)L.ny * L.nz + p] = (float)b3;
+}
+
+LaserDev laser_dev(const double* p) {
+  LaserDev P;
+  P.vosc = p[0];
+  P.k = p[1];
+  P.w0 = p[2];
+  P.rise = p[3];
+  P.length = p[4];
+  P.fall = p[5];
+  P.xfront = p[6];
+  P.ct = p[7];
+  P.c3 = p[8];
+  P.cpol = p[9];
+  P.spol = p[10];
+  P.phase = p[11];
+  for (int d = 0; d < 3; ++d) {
+    P.xmin[d] = p[12 + d];
+    P.dx[d] = p[15 + d];
+  }
+  P.axis = (int)p[18];
+  P.focus_on = p[19] != 0.0;
+  P.xfocus = p[20];
+  return P;
+}
+
+size_t antenna_bytes() { return sizeof(LaserDev); }
+
+void antenna_store(const double* p, void* dst) {
+  const LaserDev P = laser_dev(p);
+  std::memcpy(dst, &P, sizeof(P));
+}
+
+void antenna_plane(const Layout& L, const void* ants, int n, double t, double xlo1, float* inc, cudaStream_t s) {
+  k_antenna_plane<<<dim3((L.ny + 127) / 128, L.nz), 128, 0, s>>>(L, static_cast<const LaserDev*>(ants), n, t, xlo1,
+                                                                 inc);
 }
 
 template <typename T>
@@ -593,7 +658,8 @@ void init_e_gauss_x1(const Layout& L, const double* rho, double rho_bg, double d
   template void fold_guards<T>(const Layout&, T* const*, int, cudaStream_t);                                  \
   template void smooth_pass<T>(const Layout&, T*, T*, int, double, double, double, cudaStream_t);             \
   template void yee_b_half<T>(const Layout&, T* const*, T* const*, double, const double[3], cudaStream_t);     \
-  template void yee_e<T>(const Layout&, T* const*, T* const*, T* const*, double, const double[3], cudaStream_t); \
+  template void yee_e<T>(const Layout&, T* const*, T* const*, T* const*, double, const double[3], cudaStream_t,   \
+                         const float*);                                                                       \
   template void field_energy<T>(const Layout&, T* const*, Diag64*, cudaStream_t);                             \
   template void shift_x<T>(const Layout&, T* const*, int, cudaStream_t);                                      \
   template void laser_add<T>(const Layout&, T* const*, const double*, cudaStream_t);                          \

@@ -21,8 +21,11 @@ template <typename T>
 void smooth_pass(const Layout& L, T* comp, T* tmp, int dim, double w0, double w1, double w2, cudaStream_t s);
 template <typename T>
 void yee_b_half(const Layout& L, T* const* e, T* const* b, double dt, const double dx[3], cudaStream_t s);
+// inc (FP32 form, open x1): B2 and B3 just below the lower x1 boundary,
+// [2][ny nz], read there instead of 0 (antenna pulses); null: 0
 template <typename T>
-void yee_e(const Layout& L, T* const* e, T* const* b, T* const* j, double dt, const double dx[3], cudaStream_t s);
+void yee_e(const Layout& L, T* const* e, T* const* b, T* const* j, double dt, const double dx[3], cudaStream_t s,
+           const float* inc = nullptr);
 template <typename T> void field_energy(const Layout& L, T* const* f, Diag64* acc, cudaStream_t s);
 // moving window: every E/B value one cell back in x1, zero front column
 template <typename T> void shift_x(const Layout& L, T* const* comps, int ncomp, cudaStream_t s);
@@ -30,6 +33,13 @@ template <typename T> void shift_x(const Layout& L, T* const* comps, int ncomp, 
 // x_front, transverse axis position (in-plane), axis x3, cos pol, sin pol,
 // phase, xmin[3], dx[3], propagation axis (0: x1, 1: x2), focus on, x_focus
 template <typename T> void laser_add(const Layout& L, T* const* f, const double* p, cudaStream_t s);
+// antenna pulses: a record of antenna_bytes() bytes per pulse, written by
+// antenna_store from the same parameters as laser_add (with `start` in
+// place of x_front and the lab focal plane); antenna_plane sums their B2, B3
+// just below the lower x1 boundary at lab position xlo1 and time t into inc
+size_t antenna_bytes();
+void antenna_store(const double* p, void* dst);
+void antenna_plane(const Layout& L, const void* ants, int n, double t, double xlo1, float* inc, cudaStream_t s);
 template <typename T>
 void gauss_residual(const Layout& L, T* const* e, const double* rho, double rho_bg, const double dx[3], Diag64* acc,
                     cudaStream_t s);

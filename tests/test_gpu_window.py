@@ -113,3 +113,33 @@ def test_beam_driver_in_moving_window_matches_oracle():
         if m > 0:
             assert np.max(np.abs(sim.fields(name) - ref.fld[c])) < 1e-4 * m, name
     sim.close()
+
+
+def test_antenna_and_window_start_match_oracle():
+    """A pulse driven through the lower x1 boundary into a warm plasma while
+    the window is still; the window starts moving at window_start: fields,
+    shift count and particles against the oracle after 40 steps."""
+    import paper_1503_00276_gb300 as pg
+    dx = (0.05, 0.2, 1.0)
+    g = workload.Grid(ndim=2, nx=(128, 16, 1), dx=dx, dt=workload.courant_dt(dx, 2), move_window=True,
+                      window_start=1.0)
+    sp = workload.Species(ppc=(2, 1, 1), uth=(0.02, 0.02, 0.02), seed=61)
+    las = workload.Laser(vosc=0.5, rkkp=8.0, w0=1.2, rise=0.6, length=0.0, fall=0.6, start=0.1, antenna=True,
+                         focus=2.0)
+    x, u = workload.load_particles(g, sp)
+    ref = oracle.State(g, [sp], [x], [u], [workload.macro_charge(g, sp)])
+    ref.add_antenna(las)
+    sim = pg.Simulation(g, [sp], precision="fp32", tile=(32, 16), track_ids=True)
+    sim.add_laser(las)
+    n = 40
+    ref.step(n)
+    sim.step(n)
+    assert ref.shifts == int(np.floor((n * g.dt - 1.0) / dx[0])) and ref.shifts > 0
+    for c, name in enumerate(NAMES):
+        m = np.max(np.abs(ref.fld[c]))
+        if m > 0:
+            assert np.max(np.abs(sim.fields(name) - ref.fld[c])) < 1e-4 * m, name
+    assert np.max(np.abs(ref.fld[1])) > 0.5  # the pulse is in
+    ids = sim.ids()
+    assert np.array_equal(np.sort(ids), np.sort(ref.ids[0]))
+    sim.close()

@@ -928,15 +928,16 @@ pic_status alloc_spill(pic_sim* S, SpeciesState& sp) {
   return PIC_OK;
 }
 
-// rho of every species into S->rho (padded FP64), guards folded
-void compute_rho(pic_sim* S) {
+// rho of every species into S->rho (padded FP64), guards folded; acc
+// non-null (FP32 form): the kinetic energy and charge summed in the same pass
+void compute_rho(pic_sim* S, Diag64* acc = nullptr) {
   cudaMemsetAsync(S->rho, 0, 8 * (size_t)S->L.plane, S->s);
   for (auto& sp : S->sp) {
     PushConst C = make_const(S, sp);
     if (S->prec == PIC_FP64_PLAIN)
       plain_rho(S->ndim, S->L, C, sp.plain, S->rho, S->s);
     else
-      tiled_rho(S->L, C, sp.tg, sp.side[sp.cur], S->rho, S->s);
+      tiled_rho(S->L, C, sp.tg, sp.side[sp.cur], S->rho, acc, S->s);
   }
   double* r[1] = {S->rho};
   fold_guards<double>(S->L, r, 1, S->s);
@@ -1603,7 +1604,7 @@ pic_status pic_diag(pic_sim* S, pic_diag_t* out) {
     return PIC_EINVAL;
   }
   cudaMemsetAsync(S->dacc, 0, sizeof(Diag64), S->s);
-  compute_rho(S);
+  compute_rho(S, S->prec == PIC_FP64_PLAIN ? nullptr : S->dacc);
   double dx[3] = {S->g.dx[0], S->g.dx[1], S->ndim == 3 ? S->g.dx[2] : 1.0};
   long long n = 0;
   if (S->prec == PIC_FP64_PLAIN) {
@@ -1614,15 +1615,11 @@ pic_status pic_diag(pic_sim* S, pic_diag_t* out) {
   } else {
     float* f[6];
     for (int c = 0; c < 6; ++c) f[c] = fld_ptr<float>(S, c);
-    gauss_residual<float>(S->L, f, S->rho, S->g.rho_bg, dx, S->dacc, S->s);
-    field_energy<float>(S->L, f, S->dacc, S->s);
+    diag_fields<float>(S->L, f, S->rho, S->g.rho_bg, dx, S->dacc, S->s);
   }
   for (auto& sp : S->sp) {
     PushConst C = make_const(S, sp);
-    if (S->prec == PIC_FP64_PLAIN)
-      plain_kinetic(C, sp.plain, S->dacc, S->s);
-    else
-      tiled_kinetic(C, sp.tg, sp.side[sp.cur], S->dacc, S->s);
+    if (S->prec == PIC_FP64_PLAIN) plain_kinetic(C, sp.plain, S->dacc, S->s);
     n += sp.n;
   }
   Diag64 h{};

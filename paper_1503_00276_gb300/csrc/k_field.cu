@@ -4,6 +4,7 @@
 // Compiled without multiply-add contraction so that the FP64 instantiation
 // rounds every operation exactly as written; the FP32 instantiation is
 // bandwidth-bound, so the contraction would buy nothing there.
+#include <algorithm>
 #include <cstdio>
 #include <cstring>
 
@@ -406,6 +407,51 @@ __global__ void k_field_energy(Layout L, Ptr6<T> F, double* acc) {
   if (threadIdx.x == 0 && threadIdx.y == 0) atomicAdd(acc, s);
 }
 
+// Field energy and Gauss-law diagnostics in one pass over the cells, a fixed
+// number of blocks striding over them (one atomic per block and quantity):
+// sum of E^2 + B^2 (FP32 squares for FP32 fields, summed in FP64), and the
+// maxima of |div E - rho_total|, |rho_total| and |rho_particles| as k_gauss.
+template <typename T>
+__global__ void __launch_bounds__(256) k_diag_fields(Layout L, Ptr6<T> F, const double* __restrict__ rho,
+                                                     double rho_bg, double i1, double i2, double i3, Diag64* acc) {
+  __shared__ double red[32];
+  const long long ncell = (long long)L.nx * L.ny * L.nz;
+  const long long sx = 1, sy = L.NX, sz = (long long)L.NX * L.NY;
+  double s = 0.0, g = 0.0, r = 0.0, p = 0.0;
+  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < ncell;
+       q += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(q % L.nx);
+    const long long rest = q / L.nx;
+    const int j = (int)(rest % L.ny), k = (int)(rest / L.ny);
+    const long long c = L.idx(i, j, k);
+    if constexpr (sizeof(T) == 4) {
+      float e = 0.f;
+#pragma unroll
+      for (int m = 0; m < 6; ++m) e = fmaf(F.c[m][c], F.c[m][c], e);
+      s += (double)e;
+    } else {
+#pragma unroll
+      for (int m = 0; m < 6; ++m) s = s + (double)F.c[m][c] * (double)F.c[m][c];
+    }
+    double div = ((double)F.c[0][c] - (double)F.c[0][c - sx]) * i1 + ((double)F.c[1][c] - (double)F.c[1][c - sy]) * i2;
+    if (L.ndim == 3) div = div + ((double)F.c[2][c] - (double)F.c[2][c - sz]) * i3;
+    const double rt = rho[c] + rho_bg;
+    g = fmax(g, fabs(div - rt));
+    r = fmax(r, fabs(rt));
+    p = fmax(p, fabs(rho[c]));
+  }
+  s = block_sum(s, red);
+  g = block_max(g, red);
+  r = block_max(r, red);
+  p = block_max(p, red);
+  if (threadIdx.x == 0) {
+    atomicAdd(&acc->field_energy, s);
+    atomic_max_nonneg(&acc->gauss_max, g);
+    atomic_max_nonneg(&acc->rho_max, r);
+    atomic_max_nonneg(&acc->rho_part_max, p);
+  }
+}
+
 template <typename T>
 // dx1..dx3: the reciprocal cell sizes
 __global__ void k_gauss(Layout L, Ptr3<T> E, const double* __restrict__ rho, double rho_bg, double dx1, double dx2,
@@ -630,6 +676,19 @@ void field_energy(const Layout& L, T* const* f, Diag64* acc, cudaStream_t s) {
 }
 
 template <typename T>
+void diag_fields(const Layout& L, T* const* f, const double* rho, double rho_bg, const double dx[3], Diag64* acc,
+                 cudaStream_t s) {
+  Ptr6<T> F{{f[0], f[1], f[2], f[3], f[4], f[5]}};
+  int dev = 0, sms = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const long long ncell = (long long)L.nx * L.ny * L.nz;
+  const long long want = (ncell + 255) / 256;
+  const int blocks = (int)std::min<long long>(want, 8ll * sms);
+  k_diag_fields<T><<<blocks, 256, 0, s>>>(L, F, rho, rho_bg, 1.0 / dx[0], 1.0 / dx[1], 1.0 / dx[2], acc);
+}
+
+template <typename T>
 void gauss_residual(const Layout& L, T* const* e, const double* rho, double rho_bg, const double dx[3], Diag64* acc,
                     cudaStream_t s) {
   Ptr3<T> E{{e[0], e[1], e[2]}};
@@ -661,6 +720,8 @@ void init_e_gauss_x1(const Layout& L, const double* rho, double rho_bg, double d
   template void yee_e<T>(const Layout&, T* const*, T* const*, T* const*, double, const double[3], cudaStream_t,   \
                          const float*);                                                                       \
   template void field_energy<T>(const Layout&, T* const*, Diag64*, cudaStream_t);                             \
+  template void diag_fields<T>(const Layout&, T* const*, const double*, double, const double[3], Diag64*,      \
+                               cudaStream_t);                                                                  \
   template void shift_x<T>(const Layout&, T* const*, int, cudaStream_t);                                      \
   template void laser_add<T>(const Layout&, T* const*, const double*, cudaStream_t);                          \
   template void gauss_residual<T>(const Layout&, T* const*, const double*, double, const double[3], Diag64*,   \

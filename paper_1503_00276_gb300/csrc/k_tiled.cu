@@ -1793,30 +1793,42 @@ __global__ void k_global_to_flat(int ndim, Layout L, Tiles tg, PushConst C, cons
   if (out.w) out.w[k] = w ? (float)w[k] : 1.f;
 }
 
-// charge density with linear weights (FP64 atomics) of every particle in the store
-// Charge density (linear weights, FP64 grid sums) of every particle of tile
-// t.  A thread takes kRhoRun consecutive slots -- cell-sorted runs after the
-// last sort -- and sums the weights of consecutive same-cell particles in
-// registers before its FP64 atomics, one set per cell change.  The weights of
-// FP32 offsets are formed in FP32 (GB300's FP64 pipe is the bottleneck
-// otherwise); every sum into the grid is FP64.
+// Charge density of one tile's particles (one block per tile).  A thread
+// takes kRhoRun consecutive slots -- cell-sorted runs after the last sort --
+// and sums the weights of consecutive same-cell particles in registers (FP32,
+// the weights of FP32 offsets).
 constexpr int kRhoRun = 8;
 
-__device__ inline void rho_flush(const Layout& L, double* rho, int ndim, int i, int j, int k, const float (&w)[8],
-                                 double qv) {
-  for (int c3 = 0; c3 < (ndim == 3 ? 2 : 1); ++c3)
-    for (int c2 = 0; c2 < 2; ++c2)
-      for (int c1 = 0; c1 < 2; ++c1)
-        atomicAdd(&rho[L.idx(i + c1, j + c2, k + c3)], qv * (double)w[c3 * 4 + c2 * 2 + c1]);
-}
-
-__global__ void k_tiled_rho(Layout L, PushConst C, Tiles tg, TileSide in, double* rho) {
+// Every stored
+// particle's cell is local to its tile, so its weights land on the tile's
+// (T+1)^d nodes: runs of consecutive particles on one cell are summed in
+// registers (FP32), the runs in a shared-memory FP64 node tile, and the node tile is
+// added to the FP64 grid once -- plain adds for the nodes no other tile
+// touches, atomics on the tile's faces.  KIN: the same pass also sums the
+// kinetic energy m c^2 (gamma - 1) and the charge of the tile's particles
+// into acc, gamma - 1 = u^2 / (1 + gamma) in FP32 from the FP32 momenta (no
+// cancellation at small u), summed in FP64.
+template <bool KIN>
+__global__ void k_tiled_rho(Layout L, PushConst C, Tiles tg, TileSide in, double* rho, Diag64* acc) {
+  extern __shared__ double R[];
+  double kin = 0.0, live = 0.0;
   const int t = blockIdx.x;
+  const int R0 = tg.T[0] + 1, R1 = tg.T[1] + 1, R2 = tg.ndim == 3 ? tg.T[2] + 1 : 1;
+  const int nr = R0 * R1 * R2;
+  for (int q = threadIdx.x; q < nr; q += blockDim.x) R[q] = 0.0;
+  __syncthreads();
   int n;
   tile_slot(tg, in, t, 0, n);
   const double qv = C.q / C.dvol;
   int o[3];
   tile_origin(tg, t, o);
+  auto flush = [&](int cell, const float (&w)[8]) {
+    const int a = cell & 255, b = (cell >> 8) & 255, c = (cell >> 16) & 255;
+    for (int c3 = 0; c3 < (tg.ndim == 3 ? 2 : 1); ++c3)
+      for (int c2 = 0; c2 < 2; ++c2)
+        for (int c1 = 0; c1 < 2; ++c1)
+          atomicAdd(&R[((c + c3) * R1 + (b + c2)) * R0 + (a + c1)], (double)w[c3 * 4 + c2 * 2 + c1]);
+  };
   for (int k0 = threadIdx.x * kRhoRun; k0 < n; k0 += blockDim.x * kRhoRun) {
     float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     int cur = -1;
@@ -1824,20 +1836,21 @@ __global__ void k_tiled_rho(Layout L, PushConst C, Tiles tg, TileSide in, double
       const long long s = tile_slot(tg, in, t, k0 + m, n);
       const uint32_t c = in.p.cell[s];
       if (c == kHoleCell) continue;
-      // a stored cell is relative to this tile (direction code "stay"); any
-      // other code is deposited on its own at its tile's origin
-      const bool other = (int)(c >> 24) != DIR_STAY;
-      const int cell = other ? -2 : (int)(c & 0x00FFFFFFu);
+      const int cell = (int)(c & 0x00FFFFFFu);
       if (cell != cur) {
-        if (cur >= 0)
-          rho_flush(L, rho, tg.ndim, o[0] + (cur & 255), o[1] + ((cur >> 8) & 255), o[2] + ((cur >> 16) & 255),
-                    acc, qv);
-        cur = other ? -1 : cell;
+        if (cur >= 0) flush(cur, acc);
+        cur = cell;
 #pragma unroll
         for (int q = 0; q < 8; ++q) acc[q] = 0.f;
       }
       const float e0 = in.p.o[0][s], e1 = in.p.o[1][s], e2 = tg.ndim == 3 ? in.p.o[2][s] : 0.f;
       const float pw = in.p.w ? in.p.w[s] : 1.f;
+      if constexpr (KIN) {
+        const float ua = in.p.u[0][s], ub = in.p.u[1][s], uc = in.p.u[2][s];
+        const float u2 = fmaf(ua, ua, fmaf(ub, ub, uc * uc));
+        kin += (double)(pw * (u2 / (1.f + sqrtf(1.f + u2))));
+        live += pw;
+      }
 #pragma unroll
       for (int c3 = 0; c3 < 2; ++c3)
 #pragma unroll
@@ -1848,53 +1861,41 @@ __global__ void k_tiled_rho(Layout L, PushConst C, Tiles tg, TileSide in, double
             if (tg.ndim == 3) w *= (c3 ? e2 : 1.f - e2);
             acc[c3 * 4 + c2 * 2 + c1] += w * pw;
           }
-      if (other) {
-        int od[3];
-        tile_origin(tg, dest_tile(tg, t, c), od);
-        rho_flush(L, rho, tg.ndim, od[0] + (int)(c & 255), od[1] + (int)((c >> 8) & 255),
-                  od[2] + (int)((c >> 16) & 255), acc, qv);
-        cur = -1;
-      }
     }
-    if (cur >= 0)
-      rho_flush(L, rho, tg.ndim, o[0] + (cur & 255), o[1] + ((cur >> 8) & 255), o[2] + ((cur >> 16) & 255), acc, qv);
+    if (cur >= 0) flush(cur, acc);
   }
-}
-
-__global__ void k_tiled_kinetic(PushConst C, Tiles tg, TileSide in, double* ke, double* qsum) {
-  __shared__ double red[32];
-  const int t = blockIdx.x;
-  int n;
-  tile_slot(tg, in, t, 0, n);
-  double v = 0.0, live = 0.0;  // live: charge weight of the tile's particles
-  for (int k = threadIdx.x; k < n; k += blockDim.x) {
-    const long long s = tile_slot(tg, in, t, k, n);
-    if (in.p.cell[s] == kHoleCell) continue;
-    const float pw = in.p.w ? in.p.w[s] : 1.f;
-    live += pw;
-    // gamma - 1 = u^2 / (1 + gamma) in FP32 from the FP32 momenta (no
-    // cancellation at small u), summed in FP64
-    const float a = in.p.u[0][s], b = in.p.u[1][s], c = in.p.u[2][s];
-    const float u2 = fmaf(a, a, fmaf(b, b, c * c));
-    v += (double)(pw * (u2 / (1.f + sqrtf(1.f + u2))));
-  }
-  v *= C.q * C.rqm;
-  for (int o = 16; o > 0; o >>= 1) live += __shfl_down_sync(0xffffffffu, live, o);
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-  __shared__ double cnt[32];
-  if ((threadIdx.x & 31) == 0) {
-    red[threadIdx.x >> 5] = v;
-    cnt[threadIdx.x >> 5] = live;
+  if constexpr (KIN) {
+    __shared__ double red[2][32];
+    for (int m = 16; m > 0; m >>= 1) {
+      kin += __shfl_down_sync(0xffffffffu, kin, m);
+      live += __shfl_down_sync(0xffffffffu, live, m);
+    }
+    if ((threadIdx.x & 31) == 0) {
+      red[0][threadIdx.x >> 5] = kin;
+      red[1][threadIdx.x >> 5] = live;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double a = 0.0, b = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+        a += red[0][w];
+        b += red[1][w];
+      }
+      atomicAdd(&acc->kinetic_energy, C.q * C.rqm * a);
+      atomicAdd(&acc->total_charge, C.q * b);
+    }
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    double s = 0.0, c = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-      s += red[w];
-      c += cnt[w];
-    }
-    atomicAdd(ke, s);
-    atomicAdd(qsum, C.q * c);
+  for (int q = threadIdx.x; q < nr; q += blockDim.x) {
+    const double v = R[q];
+    if (v == 0.0) continue;
+    const int a = q % R0, b = (q / R0) % R1, c = q / (R0 * R1);
+    const long long g = L.idx(o[0] + a, o[1] + b, o[2] + c);
+    const bool face = a == 0 || a == R0 - 1 || b == 0 || b == R1 - 1 || (tg.ndim == 3 && (c == 0 || c == R2 - 1));
+    if (face)
+      atomicAdd(&rho[g], qv * v);
+    else
+      rho[g] += qv * v;  // no other tile of this launch reaches this node
   }
 }
 
@@ -2327,12 +2328,13 @@ void global_to_flat(int ndim, const Layout& L, const Tiles& tg, const PushConst&
                                                                 id, w, n, out, status);
 }
 
-void tiled_rho(const Layout& L, const PushConst& C, const Tiles& tg, const TileSide& in, double* rho, cudaStream_t s) {
-  k_tiled_rho<<<tg.ntiles, 256, 0, s>>>(L, C, tg, in, rho);
-}
-
-void tiled_kinetic(const PushConst& C, const Tiles& tg, const TileSide& in, Diag64* acc, cudaStream_t s) {
-  k_tiled_kinetic<<<tg.ntiles, 256, 0, s>>>(C, tg, in, &acc->kinetic_energy, &acc->total_charge);
+void tiled_rho(const Layout& L, const PushConst& C, const Tiles& tg, const TileSide& in, double* rho, Diag64* acc,
+               cudaStream_t s) {
+  const size_t nodes = (size_t)(tg.T[0] + 1) * (tg.T[1] + 1) * (tg.ndim == 3 ? tg.T[2] + 1 : 1);
+  if (acc)
+    k_tiled_rho<true><<<tg.ntiles, 256, 8 * nodes, s>>>(L, C, tg, in, rho, acc);
+  else
+    k_tiled_rho<false><<<tg.ntiles, 256, 8 * nodes, s>>>(L, C, tg, in, rho, nullptr);
 }
 
 }  // namespace picgb

@@ -27,6 +27,10 @@ template <typename T>
 void yee_e(const Layout& L, T* const* e, T* const* b, T* const* j, double dt, const double dx[3], cudaStream_t s,
            const float* inc = nullptr);
 template <typename T> void field_energy(const Layout& L, T* const* f, Diag64* acc, cudaStream_t s);
+// field energy and the Gauss-law maxima in one pass (f: E1..E3, B1..B3)
+template <typename T>
+void diag_fields(const Layout& L, T* const* f, const double* rho, double rho_bg, const double dx[3], Diag64* acc,
+                 cudaStream_t s);
 // moving window: every E/B value one cell back in x1, zero front column
 template <typename T> void shift_x(const Layout& L, T* const* comps, int ncomp, cudaStream_t s);
 // laser pulse added to the fields; p: vosc, k, w0, rise, length, fall,
@@ -203,8 +207,10 @@ void flat_to_global(int ndim, const Tiles& tg, const PushConst& C, const Flat32&
 void global_to_flat(int ndim, const Layout& L, const Tiles& tg, const PushConst& C, double* const x[3],
                     double* const u[3], const int* id, const double* w, long long n, Flat32 out, int* status,
                     cudaStream_t s);
-void tiled_rho(const Layout& L, const PushConst& C, const Tiles& tg, const TileSide& in, double* rho, cudaStream_t s);
-void tiled_kinetic(const PushConst& C, const Tiles& tg, const TileSide& in, Diag64* acc, cudaStream_t s);
+// acc non-null: the kinetic energy and charge of the particles summed into it
+// in the same pass
+void tiled_rho(const Layout& L, const PushConst& C, const Tiles& tg, const TileSide& in, double* rho, Diag64* acc,
+               cudaStream_t s);
 
 // ----------------------------------------------------------------- loading
 // Lattice loader (nl_species num_par_x, vth, vfl) on the device, FP64 output.

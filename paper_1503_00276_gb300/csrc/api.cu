@@ -1615,7 +1615,7 @@ pic_status pic_diag(pic_sim* S, pic_diag_t* out) {
   } else {
     float* f[6];
     for (int c = 0; c < 6; ++c) f[c] = fld_ptr<float>(S, c);
-    diag_fields<float>(S->L, f, S->rho, S->g.rho_bg, dx, S->dacc, S->s);
+    diag_fields(S->L, f, S->rho, S->g.rho_bg, dx, S->dacc, S->s);
   }
   for (auto& sp : S->sp) {
     PushConst C = make_const(S, sp);

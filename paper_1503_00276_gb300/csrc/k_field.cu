@@ -407,48 +407,58 @@ __global__ void k_field_energy(Layout L, Ptr6<T> F, double* acc) {
   if (threadIdx.x == 0 && threadIdx.y == 0) atomicAdd(acc, s);
 }
 
-// Field energy and Gauss-law diagnostics in one pass over the cells, a fixed
-// number of blocks striding over them (one atomic per block and quantity):
-// sum of E^2 + B^2 (FP32 squares for FP32 fields, summed in FP64), and the
-// maxima of |div E - rho_total|, |rho_total| and |rho_particles| as k_gauss.
-template <typename T>
-__global__ void __launch_bounds__(256) k_diag_fields(Layout L, Ptr6<T> F, const double* __restrict__ rho,
-                                                     double rho_bg, double i1, double i2, double i3, Diag64* acc) {
+// Field energy and Gauss-law diagnostics of the FP32 fields in one pass over
+// the cells, a fixed number of blocks striding over them (one atomic per block
+// and quantity): the sum of E^2 + B^2 (FP32 squares of four cells, summed in
+// FP64), and the maxima of |div E - rho_total|, |rho_total| and
+// |rho_particles| as k_gauss.  The divergence terms are differences of FP32
+// values taken in FP32 (their rounding is of the order of the fields' own);
+// rho_total and the residual are FP64.  The maxima are kept as the bit
+// patterns of non-negative doubles, whose integer order is their order.
+constexpr int kDiagThreads = 256;
+constexpr int kDiagUnroll = 4;
+
+__global__ void __launch_bounds__(kDiagThreads) k_diag_fields(Layout L, Ptr6<float> F, const double* __restrict__ rho,
+                                                              double rho_bg, float i1, float i2, float i3,
+                                                              Diag64* acc) {
   __shared__ double red[32];
-  const long long ncell = (long long)L.nx * L.ny * L.nz;
-  const long long sx = 1, sy = L.NX, sz = (long long)L.NX * L.NY;
-  double s = 0.0, g = 0.0, r = 0.0, p = 0.0;
-  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < ncell;
-       q += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(q % L.nx);
-    const long long rest = q / L.nx;
-    const int j = (int)(rest % L.ny), k = (int)(rest / L.ny);
-    const long long c = L.idx(i, j, k);
-    if constexpr (sizeof(T) == 4) {
-      float e = 0.f;
+  const int ncell = L.nx * L.ny * L.nz;  // < 2^31 (checked by the launcher)
+  const int stride = gridDim.x * blockDim.x;
+  const int sy = L.NX, sz = L.NX * L.NY;
+  double s = 0.0;
+  long long g = 0, r = 0, p = 0;
+  for (int q0 = blockIdx.x * blockDim.x + threadIdx.x; q0 < ncell; q0 += kDiagUnroll * stride) {
+    float es = 0.f;
 #pragma unroll
-      for (int m = 0; m < 6; ++m) e = fmaf(F.c[m][c], F.c[m][c], e);
-      s += (double)e;
-    } else {
+    for (int u = 0; u < kDiagUnroll; ++u) {
+      const int q = q0 + u * stride;
+      if (q >= ncell) break;
+      const int i = q % L.nx, rest = q / L.nx;
+      const int j = rest % L.ny, k = rest / L.ny;
+      const long long c = L.idx(i, j, k);
 #pragma unroll
-      for (int m = 0; m < 6; ++m) s = s + (double)F.c[m][c] * (double)F.c[m][c];
+      for (int m = 0; m < 6; ++m) {
+        const float v = F.c[m][c];
+        es = fmaf(v, v, es);
+      }
+      float div = (F.c[0][c] - F.c[0][c - 1]) * i1 + (F.c[1][c] - F.c[1][c - sy]) * i2;
+      if (L.ndim == 3) div += (F.c[2][c] - F.c[2][c - sz]) * i3;
+      const double rp = rho[c], rt = rp + rho_bg;
+      g = max(g, __double_as_longlong(fabs((double)div - rt)));
+      r = max(r, __double_as_longlong(fabs(rt)));
+      p = max(p, __double_as_longlong(fabs(rp)));
     }
-    double div = ((double)F.c[0][c] - (double)F.c[0][c - sx]) * i1 + ((double)F.c[1][c] - (double)F.c[1][c - sy]) * i2;
-    if (L.ndim == 3) div = div + ((double)F.c[2][c] - (double)F.c[2][c - sz]) * i3;
-    const double rt = rho[c] + rho_bg;
-    g = fmax(g, fabs(div - rt));
-    r = fmax(r, fabs(rt));
-    p = fmax(p, fabs(rho[c]));
+    s += (double)es;
   }
   s = block_sum(s, red);
-  g = block_max(g, red);
-  r = block_max(r, red);
-  p = block_max(p, red);
+  const double gm = block_max(__longlong_as_double(g), red);
+  const double rm = block_max(__longlong_as_double(r), red);
+  const double pm = block_max(__longlong_as_double(p), red);
   if (threadIdx.x == 0) {
     atomicAdd(&acc->field_energy, s);
-    atomic_max_nonneg(&acc->gauss_max, g);
-    atomic_max_nonneg(&acc->rho_max, r);
-    atomic_max_nonneg(&acc->rho_part_max, p);
+    atomic_max_nonneg(&acc->gauss_max, gm);
+    atomic_max_nonneg(&acc->rho_max, rm);
+    atomic_max_nonneg(&acc->rho_part_max, pm);
   }
 }
 
@@ -675,17 +685,22 @@ void field_energy(const Layout& L, T* const* f, Diag64* acc, cudaStream_t s) {
   k_field_energy<T><<<interior_grid(L), kBlock, 0, s>>>(L, F, &acc->field_energy);
 }
 
-template <typename T>
-void diag_fields(const Layout& L, T* const* f, const double* rho, double rho_bg, const double dx[3], Diag64* acc,
+void diag_fields(const Layout& L, float* const* f, const double* rho, double rho_bg, const double dx[3], Diag64* acc,
                  cudaStream_t s) {
-  Ptr6<T> F{{f[0], f[1], f[2], f[3], f[4], f[5]}};
+  Ptr6<float> F{{f[0], f[1], f[2], f[3], f[4], f[5]}};
   int dev = 0, sms = 1;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const long long ncell = (long long)L.nx * L.ny * L.nz;
-  const long long want = (ncell + 255) / 256;
+  if (ncell <= 0 || ncell >= (1ll << 31)) {  // int32 cell index in the kernel
+    gauss_residual<float>(L, f, rho, rho_bg, dx, acc, s);
+    field_energy<float>(L, f, acc, s);
+    return;
+  }
+  const long long want = (ncell + kDiagThreads * kDiagUnroll - 1) / (kDiagThreads * kDiagUnroll);
   const int blocks = (int)std::min<long long>(want, 8ll * sms);
-  k_diag_fields<T><<<blocks, 256, 0, s>>>(L, F, rho, rho_bg, 1.0 / dx[0], 1.0 / dx[1], 1.0 / dx[2], acc);
+  k_diag_fields<<<blocks, kDiagThreads, 0, s>>>(L, F, rho, rho_bg, (float)(1.0 / dx[0]), (float)(1.0 / dx[1]),
+                                               (float)(1.0 / dx[2]), acc);
 }
 
 template <typename T>
@@ -720,8 +735,6 @@ void init_e_gauss_x1(const Layout& L, const double* rho, double rho_bg, double d
   template void yee_e<T>(const Layout&, T* const*, T* const*, T* const*, double, const double[3], cudaStream_t,   \
                          const float*);                                                                       \
   template void field_energy<T>(const Layout&, T* const*, Diag64*, cudaStream_t);                             \
-  template void diag_fields<T>(const Layout&, T* const*, const double*, double, const double[3], Diag64*,      \
-                               cudaStream_t);                                                                  \
   template void shift_x<T>(const Layout&, T* const*, int, cudaStream_t);                                      \
   template void laser_add<T>(const Layout&, T* const*, const double*, cudaStream_t);                          \
   template void gauss_residual<T>(const Layout&, T* const*, const double*, double, const double[3], Diag64*,   \

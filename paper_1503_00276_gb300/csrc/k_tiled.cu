@@ -1793,91 +1793,150 @@ __global__ void k_global_to_flat(int ndim, Layout L, Tiles tg, PushConst C, cons
   if (out.w) out.w[k] = w ? (float)w[k] : 1.f;
 }
 
-// Charge density of one tile's particles (one block per tile).  A thread
-// takes kRhoRun consecutive slots -- cell-sorted runs after the last sort --
-// and sums the weights of consecutive same-cell particles in registers (FP32,
-// the weights of FP32 offsets).
-constexpr int kRhoRun = 8;
-
-// Every stored
+// Charge density of one tile's particles (one block per tile).  Every stored
 // particle's cell is local to its tile, so its weights land on the tile's
-// (T+1)^d nodes: runs of consecutive particles on one cell are summed in
-// registers (FP32), the runs in a shared-memory FP64 node tile, and the node tile is
-// added to the FP64 grid once -- plain adds for the nodes no other tile
-// touches, atomics on the tile's faces.  KIN: the same pass also sums the
-// kinetic energy m c^2 (gamma - 1) and the charge of the tile's particles
-// into acc, gamma - 1 = u^2 / (1 + gamma) in FP32 from the FP32 momenta (no
-// cancellation at small u), summed in FP64.
+// (T+1)^d nodes.  A warp takes kRhoWarp consecutive slots: it copies them
+// coalesced into shared memory (cp.async), and each lane then takes kRhoRun consecutive
+// ones -- cell-sorted runs after the last sort -- summing the weights of
+// consecutive same-cell particles in registers (FP32).  Each run goes into a
+// shared node tile of 64-bit fixed-point sums (units of 2^-32, so the node
+// sums do not depend on the order of the adds; node sums must stay below 2^31
+// particle weights), kept as two 32-bit words added by 32-bit atomics (the
+// low word's carry goes into the high word with the high part of the add);
+// the node tile is then added to the FP64 grid once: plain
+// adds for the nodes no other tile touches, atomics on the tile's faces.
+// KIN: the same pass also sums the kinetic energy m c^2 (gamma - 1) and the
+// charge of the tile's particles into acc, gamma - 1 = u^2 / (1 + gamma) in
+// FP32 from the FP32 momenta (no cancellation at small u), per run in FP32,
+// across runs in FP64.
+constexpr int kRhoRun = 8;
+constexpr int kRhoWarp = 32 * kRhoRun;
+constexpr int kRhoThreads = 128;
+constexpr int kRhoPad = kRhoWarp + kRhoWarp / 32;  // one padding word per 32: conflict-free strided reads
+
 template <bool KIN>
-__global__ void k_tiled_rho(Layout L, PushConst C, Tiles tg, TileSide in, double* rho, Diag64* acc) {
-  extern __shared__ double R[];
-  double kin = 0.0, live = 0.0;
+__global__ void __launch_bounds__(kRhoThreads) k_tiled_rho(Layout L, PushConst C, Tiles tg, TileSide in, double* rho,
+                                                           Diag64* acc) {
+  constexpr int NA = KIN ? 8 : 5;  // staged arrays: cell, o1..o3, w[, u1..u3]
+  __shared__ float stg[kRhoThreads / 32][NA][kRhoPad];
+  // node sums, fixed point in units of 2^-32: low words Rlo[nr], high words Rhi[nr]
+  extern __shared__ unsigned int Rlo[];
   const int t = blockIdx.x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int R0 = tg.T[0] + 1, R1 = tg.T[1] + 1, R2 = tg.ndim == 3 ? tg.T[2] + 1 : 1;
   const int nr = R0 * R1 * R2;
-  for (int q = threadIdx.x; q < nr; q += blockDim.x) R[q] = 0.0;
-  __syncthreads();
-  int n;
-  tile_slot(tg, in, t, 0, n);
-  const double qv = C.q / C.dvol;
+  int* Rhi = reinterpret_cast<int*>(Rlo + nr);
+  for (int q = threadIdx.x; q < nr; q += blockDim.x) {
+    Rlo[q] = 0u;
+    Rhi[q] = 0;
+  }
+  int ns = in.stay[t];
+  ns = ns < tg.cap[t] - tg.res[t] ? ns : tg.cap[t] - tg.res[t];  // a sliced tile counts its overflow too
+  int ni = in.inc[t];
+  ni = ni < tg.res[t] ? ni : tg.res[t];
+  const int n = ns + ni;
+  const long long base = tg.base[t], back = tg.base[t] + tg.cap[t] - ni - ns;
+  const bool d3 = tg.ndim == 3, has_w = in.p.w != nullptr;
   int o[3];
   tile_origin(tg, t, o);
-  auto flush = [&](int cell, const float (&w)[8]) {
-    const int a = cell & 255, b = (cell >> 8) & 255, c = (cell >> 16) & 255;
-    for (int c3 = 0; c3 < (tg.ndim == 3 ? 2 : 1); ++c3)
-      for (int c2 = 0; c2 < 2; ++c2)
-        for (int c1 = 0; c1 < 2; ++c1)
-          atomicAdd(&R[((c + c3) * R1 + (b + c2)) * R0 + (a + c1)], (double)w[c3 * 4 + c2 * 2 + c1]);
-  };
-  for (int k0 = threadIdx.x * kRhoRun; k0 < n; k0 += blockDim.x * kRhoRun) {
-    float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  __syncthreads();
+  double kin = 0.0, live = 0.0;
+  float(*S)[kRhoPad] = stg[warp];
+  for (int k0 = warp * kRhoWarp; k0 < n; k0 += (kRhoThreads / 32) * kRhoWarp) {
+    // coalesced: slot k0 + 32 m + lane into word p + p / 32 of each array,
+    // copied straight to shared memory so that all of them are in flight
+#pragma unroll
+    for (int m = 0; m < kRhoRun; ++m) {
+      const int p = 32 * m + lane, k = k0 + p, w = p + m;
+      if (k < n) {
+        const long long s = k < ns ? base + k : back + k;
+        cp_async4(&S[0][w], &in.p.cell[s]);
+        cp_async4(&S[1][w], &in.p.o[0][s]);
+        cp_async4(&S[2][w], &in.p.o[1][s]);
+        if (d3) cp_async4(&S[3][w], &in.p.o[2][s]);
+        if (has_w) cp_async4(&S[4][w], &in.p.w[s]);
+        if constexpr (KIN) {
+          cp_async4(&S[5][w], &in.p.u[0][s]);
+          cp_async4(&S[6][w], &in.p.u[1][s]);
+          cp_async4(&S[7][w], &in.p.u[2][s]);
+        }
+      } else {
+        S[0][w] = __uint_as_float(kHoleCell);
+      }
+    }
+    cp_async_commit();
+    cp_async_wait0();
+    __syncwarp();
+    float accw[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    float kp = 0.f, lp = 0.f;  // this run's kinetic energy and charge
     int cur = -1;
-    for (int m = 0; m < kRhoRun && k0 + m < n; ++m) {
-      const long long s = tile_slot(tg, in, t, k0 + m, n);
-      const uint32_t c = in.p.cell[s];
-      if (c == kHoleCell) continue;
-      const int cell = (int)(c & 0x00FFFFFFu);
+    auto flush = [&]() {
+      const int a = cur & 255, b = (cur >> 8) & 255, c = (cur >> 16) & 255;
+      for (int c3 = 0; c3 < (d3 ? 2 : 1); ++c3)
+        for (int c2 = 0; c2 < 2; ++c2)
+          for (int c1 = 0; c1 < 2; ++c1) {
+            // x = hi + lo 2^-32 exactly: floor and fraction of an FP32 value are
+            // exact, and the fraction's 2^32 multiple rounds to the nearest unit
+            const float x = accw[c3 * 4 + c2 * 2 + c1], fl = floorf(x);
+            const int hi = (int)fl;
+            const unsigned lo = __float2uint_rn((x - fl) * 4294967296.f);
+            const int q = ((c + c3) * R1 + (b + c2)) * R0 + (a + c1);
+            const unsigned old = atomicAdd(&Rlo[q], lo);
+            const int carry = old + lo < old ? 1 : 0;
+            if (hi + carry != 0) atomicAdd(&Rhi[q], hi + carry);
+          }
+    };
+#pragma unroll
+    for (int j = 0; j < kRhoRun; ++j) {
+      const int p = kRhoRun * lane + j, w = p + p / 32;
+      const uint32_t cw = __float_as_uint(S[0][w]);
+      if (cw == kHoleCell) continue;
+      const int cell = (int)(cw & 0x00FFFFFFu);
       if (cell != cur) {
-        if (cur >= 0) flush(cur, acc);
+        if (cur >= 0) flush();
         cur = cell;
 #pragma unroll
-        for (int q = 0; q < 8; ++q) acc[q] = 0.f;
+        for (int q = 0; q < 8; ++q) accw[q] = 0.f;
       }
-      const float e0 = in.p.o[0][s], e1 = in.p.o[1][s], e2 = tg.ndim == 3 ? in.p.o[2][s] : 0.f;
-      const float pw = in.p.w ? in.p.w[s] : 1.f;
+      const float e0 = S[1][w], e1 = S[2][w], e2 = d3 ? S[3][w] : 0.f, pw = has_w ? S[4][w] : 1.f;
       if constexpr (KIN) {
-        const float ua = in.p.u[0][s], ub = in.p.u[1][s], uc = in.p.u[2][s];
+        const float ua = S[5][w], ub = S[6][w], uc = S[7][w];
         const float u2 = fmaf(ua, ua, fmaf(ub, ub, uc * uc));
-        kin += (double)(pw * (u2 / (1.f + sqrtf(1.f + u2))));
-        live += pw;
+        kp = fmaf(pw, u2 / (1.f + sqrtf(1.f + u2)), kp);
+        lp += pw;
       }
+      const float f1[2] = {1.f - e0, e0}, f2[2] = {1.f - e1, e1}, f3[2] = {1.f - e2, e2};
 #pragma unroll
       for (int c3 = 0; c3 < 2; ++c3)
 #pragma unroll
-        for (int c2 = 0; c2 < 2; ++c2)
+        for (int c2 = 0; c2 < 2; ++c2) {
+          const float w23 = f2[c2] * (d3 ? f3[c3] : 1.f) * pw;
 #pragma unroll
-          for (int c1 = 0; c1 < 2; ++c1) {
-            float w = (c1 ? e0 : 1.f - e0) * (c2 ? e1 : 1.f - e1);
-            if (tg.ndim == 3) w *= (c3 ? e2 : 1.f - e2);
-            acc[c3 * 4 + c2 * 2 + c1] += w * pw;
-          }
+          for (int c1 = 0; c1 < 2; ++c1) accw[c3 * 4 + c2 * 2 + c1] = fmaf(f1[c1], w23, accw[c3 * 4 + c2 * 2 + c1]);
+        }
     }
-    if (cur >= 0) flush(cur, acc);
+    if (cur >= 0) flush();
+    if constexpr (KIN) {
+      kin += (double)kp;
+      live += (double)lp;
+    }
+    __syncwarp();
   }
   if constexpr (KIN) {
-    __shared__ double red[2][32];
+    __shared__ double red[2][kRhoThreads / 32];
+    double dk = kin, dl = live;
     for (int m = 16; m > 0; m >>= 1) {
-      kin += __shfl_down_sync(0xffffffffu, kin, m);
-      live += __shfl_down_sync(0xffffffffu, live, m);
+      dk += __shfl_down_sync(0xffffffffu, dk, m);
+      dl += __shfl_down_sync(0xffffffffu, dl, m);
     }
-    if ((threadIdx.x & 31) == 0) {
-      red[0][threadIdx.x >> 5] = kin;
-      red[1][threadIdx.x >> 5] = live;
+    if (lane == 0) {
+      red[0][warp] = dk;
+      red[1][warp] = dl;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
       double a = 0.0, b = 0.0;
-      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      for (int w = 0; w < kRhoThreads / 32; ++w) {
         a += red[0][w];
         b += red[1][w];
       }
@@ -1886,12 +1945,14 @@ __global__ void k_tiled_rho(Layout L, PushConst C, Tiles tg, TileSide in, double
     }
   }
   __syncthreads();
+  const double qv = C.q / C.dvol;
   for (int q = threadIdx.x; q < nr; q += blockDim.x) {
-    const double v = R[q];
-    if (v == 0.0) continue;
+    const unsigned long long fx = ((unsigned long long)(unsigned)Rhi[q] << 32) + Rlo[q];
+    if (fx == 0ull) continue;
+    const double v = (double)(long long)fx * (1.0 / 4294967296.0);
     const int a = q % R0, b = (q / R0) % R1, c = q / (R0 * R1);
     const long long g = L.idx(o[0] + a, o[1] + b, o[2] + c);
-    const bool face = a == 0 || a == R0 - 1 || b == 0 || b == R1 - 1 || (tg.ndim == 3 && (c == 0 || c == R2 - 1));
+    const bool face = a == 0 || a == R0 - 1 || b == 0 || b == R1 - 1 || (d3 && (c == 0 || c == R2 - 1));
     if (face)
       atomicAdd(&rho[g], qv * v);
     else
@@ -2332,9 +2393,9 @@ void tiled_rho(const Layout& L, const PushConst& C, const Tiles& tg, const TileS
                cudaStream_t s) {
   const size_t nodes = (size_t)(tg.T[0] + 1) * (tg.T[1] + 1) * (tg.ndim == 3 ? tg.T[2] + 1 : 1);
   if (acc)
-    k_tiled_rho<true><<<tg.ntiles, 256, 8 * nodes, s>>>(L, C, tg, in, rho, acc);
+    k_tiled_rho<true><<<tg.ntiles, kRhoThreads, 8 * nodes, s>>>(L, C, tg, in, rho, acc);
   else
-    k_tiled_rho<false><<<tg.ntiles, 256, 8 * nodes, s>>>(L, C, tg, in, rho, nullptr);
+    k_tiled_rho<false><<<tg.ntiles, kRhoThreads, 8 * nodes, s>>>(L, C, tg, in, rho, nullptr);
 }
 
 }  // namespace picgb

@@ -27,9 +27,9 @@ template <typename T>
 void yee_e(const Layout& L, T* const* e, T* const* b, T* const* j, double dt, const double dx[3], cudaStream_t s,
            const float* inc = nullptr);
 template <typename T> void field_energy(const Layout& L, T* const* f, Diag64* acc, cudaStream_t s);
-// field energy and the Gauss-law maxima in one pass (f: E1..E3, B1..B3)
-template <typename T>
-void diag_fields(const Layout& L, T* const* f, const double* rho, double rho_bg, const double dx[3], Diag64* acc,
+// field energy and the Gauss-law maxima of the FP32 fields in one pass (f:
+// E1..E3, B1..B3)
+void diag_fields(const Layout& L, float* const* f, const double* rho, double rho_bg, const double dx[3], Diag64* acc,
                  cudaStream_t s);
 // moving window: every E/B value one cell back in x1, zero front column
 template <typename T> void shift_x(const Layout& L, T* const* comps, int ncomp, cudaStream_t s);

@@ -83,6 +83,7 @@ class Grid:
     move_window: bool = False      # window moving at c in x1 (x1 open; periodic in x2, x3)
     window_start: float = 0.0      # time from which the window moves (before it: x1 open, static)
     deposit: str = "vb"            # current deposit: "vb" (TRISTAN / Villasenor-Buneman) or "isis" (2D)
+    coords: str = "cartesian"      # "cylindrical": 2D r-z (x1 = z, x2 = r), xmin[1] = -dx[1]/2
 
     @property
     def ncells(self) -> int:
@@ -386,3 +387,45 @@ def inject_column(grid: Grid, sp: Species, xmin1: float, first_index: int):
         u[:, d] = sp.ufl[d] + sp.uth[d] * normal(sp.seed, np.uint64(3) * gidx + np.uint64(d)) if sp.uth[d] != 0.0 \
             else np.full(k.size, float(sp.ufl[d]))
     return x, u
+
+
+# ---------------------------------------------------------------- r-z geometry
+def cyl_grid(nz: int, nr: int, dz: float, dr: float, zmin: float = 0.0, frac: float = 0.99,
+             b0=(0.0, 0.0, 0.0), e0=(0.0, 0.0, 0.0), rho_bg: float = 0.0) -> Grid:
+    """2D cylindrically symmetric box: x1 = z (periodic), x2 = r with the axis
+    through the middle of the first cell (xmin[1] = -dr/2) and a wall at
+    r = (nr - 1/2) dr."""
+    return Grid(ndim=2, nx=(int(nz), int(nr), 1), dx=(float(dz), float(dr), 1.0), xmin=(float(zmin), -0.5 * dr, 0.0),
+                dt=cyl_courant_dt(dz, dr, frac), e0=tuple(e0), b0=tuple(b0), rho_bg=rho_bg,
+                coords="cylindrical")
+
+
+# Largest eigenvalue of the radial part of the r-z field solve (the Etheta, Bz,
+# Br family with the axis rule), in units of 4/dr^2: a mode bound to the axis,
+# the same for every nr >= 10 (smaller grids have a smaller one).  The leapfrog
+# is stable for dt < 1 / sqrt(1/dz^2 + CYL_RADIAL_EIG / dr^2).
+CYL_RADIAL_EIG = 1.2105
+
+
+def cyl_courant_dt(dz: float, dr: float, frac: float = 0.99) -> float:
+    return frac / math.sqrt(1.0 / dz ** 2 + CYL_RADIAL_EIG / dr ** 2)
+
+
+def load_cylindrical(grid: Grid, sp: Species, index=None):
+    """Lattice particles of an r-z box: the Cartesian lattice of the (z, r)
+    cells with r measured from the lower edge -dr/2 of the first cell, and the
+    points of that cell below the axis reflected to -r.  Returns (x[n,3] with
+    columns z, r, 0; u[n,3] = (pz, pr, ptheta))."""
+    assert grid.coords == "cylindrical"
+    x, u = load_particles(grid, sp, index)
+    x[:, 1] = np.abs(x[:, 1])
+    return x, u
+
+
+def config_cyl(seed: int = 20006, nz: int = 2048, nr: int = 512, ppc=(2, 2, 1), uth: float = 0.05):
+    """r-z thermal plasma column (uniform density 1 out to the wall, fixed ion
+    background): nz x nr cells of 0.1 c/w_p, electrons."""
+    g = cyl_grid(nz, nr, 0.1, 0.1, rho_bg=1.0)
+    sp = Species(rqm=-1.0, ppc=tuple(ppc), uth=(uth, uth, uth), density=1.0, seed=seed)
+    return g, [sp], 200
+

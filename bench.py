@@ -68,6 +68,9 @@ def parse():
     p.add_argument("--wake-steps", type=int, default=200,
                    help="timed steps of the 2D laser-wakefield workload (moving window)")
     p.add_argument("--no-wake", action="store_true")
+    p.add_argument("--cyl-steps", type=int, default=20,
+                   help="timed steps of the r-z (2D cylindrically symmetric) plasma column, FP64")
+    p.add_argument("--no-cyl", action="store_true")
     return p.parse_args()
 
 
@@ -301,6 +304,8 @@ def run_ours(args):
     if not args.no_wake:
         out["wakefield_2d"] = run_wakefield(args, max_over_ranks)
         out["beam_wake_3d"] = run_beam_wake(args, max_over_ranks)
+    if not args.no_cyl:
+        out["cylindrical_2d"] = run_cylindrical(args, max_over_ranks)
 
     if rank == 0 and ws == 1 and not args.no_cpu:
         out["cpu_baseline"] = run_cpu_baseline(args, budget_s=15.0)
@@ -309,6 +314,40 @@ def run_ours(args):
     if dist is not None:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def run_cylindrical(args, max_over_ranks):
+    """The r-z (2D cylindrically symmetric) mode, FP64 plain form: a thermal
+    plasma column of 2048 x 512 cells of 0.1 c/w_p out to a conducting wall,
+    4 rings per cell (4.2M), u_th = 0.05, fixed ion background."""
+    import torch
+
+    import paper_1503_00276_gb300 as pg
+    import workload
+
+    g, sps, _ = workload.config_cyl()
+    sim = pg.Simulation(g, sps, precision="fp64")
+    K, W = args.cyl_steps, 3
+    stream = torch.cuda.current_stream()
+    sim.timing_enable(True)
+    sim.step(W)
+    torch.cuda.synchronize()
+    sim.timing_read(reset=True)
+    n0 = sim.n_particles()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    sim.step(K)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = max_over_ranks(e0.elapsed_time(e1))
+    tim = sim.timing_read()
+    d = sim.diag()
+    sim.close()
+    return {"workload": f"r-z plasma column 2048x512 cells, dz = dr = 0.1, 2x2 rings per cell ({n0:,}), "
+                        "u_th=0.05, conducting wall, FP64 plain", "steps": K, "warmup": W,
+            "value": n0 * K / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / K,
+            "stages_ms_per_step": {k: round(v[0] / K, 4) for k, v in tim.items() if k != "launches"},
+            "gauss_resid_max_after": d["gauss_resid_max"], "rho_abs_max_after": d["rho_abs_max"]}
 
 
 def run_wakefield(args, max_over_ranks):

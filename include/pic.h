@@ -135,9 +135,30 @@ typedef struct {
                                charge exactly; they differ by a divergence-free current. */
   double window_start;      /* move_window: time from which the window moves (before it
                                the box is still, x1 open); 0 = from the start */
+  int coords;               /* PIC_COORDS_CARTESIAN (0, default) or PIC_COORDS_CYLINDRICAL (1):
+                               the 2D cylindrically symmetric mode (thesis ch. 3).  x1 = z
+                               (periodic), x2 = r with the axis through the middle of the first
+                               cell (xmin[1] must be -dx[1]/2) and a perfectly conducting wall at
+                               r = (nx[1] - 1/2) dx[1]; E1,E2,E3 are Ez,Er,Etheta (B, J likewise).
+                               The field solve weights the r-derivatives of the z components by
+                               the radius and advances Bz on the axis from Faraday's law on the
+                               disc of radius dx[1]/2; field rows at the axis follow the axial
+                               parity.  Particles are rings: x2 = r >= 0, u = (pz, pr, ptheta),
+                               charge q * w * r per radian (w the own weight, 1 without one),
+                               moved in 3D and rotated back into the r-z plane; lattice points
+                               below the axis are reflected; a particle reaching the wall is
+                               absorbed (its slot stays, with r = -1 and u = 0).  J and RHO are
+                               densities (current or charge per r dr dz); pic_diag totals are
+                               over the full 2 pi.  Needs ndim 2, PIC_FP64_PLAIN, the TRISTAN
+                               deposit, no smoothing, move_window, init_e_gauss_x1 or density
+                               profile, no laser (else PIC_EUNSUPPORTED); bc[1] is not read.
+                               Time step: dt < 1/sqrt(1/dx1^2 + 1.2105/dx2^2) (PIC_ECOURANT), the
+                               radial factor being the largest eigenvalue of the discrete radial
+                               operator with the axis rule, in units of 4/dx2^2. */
 } pic_grid;
 
 enum { PIC_DEPOSIT_TRISTAN = 0, PIC_DEPOSIT_ISIS = 1 };
+enum { PIC_COORDS_CARTESIAN = 0, PIC_COORDS_CYLINDRICAL = 1 };
 
 /* One particle species (appendix nl_species / nl_profile).  Either loaded on the
  * device from the num_par_x lattice and a seed, or given explicitly. */

@@ -80,6 +80,7 @@ def _grid_struct(grid, precision, tile=None, slack=0.0, sort_period=0, ctas_per_
         raise ValueError(f"unknown deposit {dep!r} (vb or isis)")
     g.deposit = 1 if dep == "isis" else 0
     g.window_start = float(getattr(grid, "window_start", 0.0))
+    g.coords = 1 if getattr(grid, "coords", "cartesian") == "cylindrical" else 0
     return g
 
 

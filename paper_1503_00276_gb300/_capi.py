@@ -31,7 +31,7 @@ class PicGrid(C.Structure):
                 ("rho_bg", C.c_double), ("init_e_gauss_x1", C.c_int), ("precision", C.c_int),
                 ("tile", C.c_int * 3), ("slack", C.c_double), ("sort_period", C.c_int),
                 ("ctas_per_sm", C.c_int), ("move_window", C.c_int), ("deposit", C.c_int),
-                ("window_start", C.c_double)]
+                ("window_start", C.c_double), ("coords", C.c_int)]
 
 
 class PicSpecies(C.Structure):

@@ -27,6 +27,7 @@ UNITS = {
     "api.cu": [],
     "k_field.cu": ["--fmad=false"],
     "k_plain.cu": ["--fmad=false"],
+    "k_cyl.cu": ["--fmad=false"],
     "k_sort.cu": [],
     "k_tiled.cu": [],
 }

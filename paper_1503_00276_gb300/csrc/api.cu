@@ -178,6 +178,8 @@ struct pic_sim {
   bool moving = false;    // window moving at c in +x1
   long long shifts = 0;   // one-cell shifts of the window so far
   bool in_batch = false;  // stepped by its batch; pic_step refuses it
+  bool cyl = false;       // 2D cylindrically symmetric (r-z) mode
+  CylConst K{};
 };
 
 namespace {
@@ -699,7 +701,11 @@ pic_status load_species(pic_sim* S, const pic_species& in, SpeciesState& sp) {
       cudaStreamSynchronize(S->s);
     }
   }
-  sp.weighted = sp.has_prof || (in.n_explicit > 0 && in.w0 != nullptr);
+  if (S->cyl && sp.has_prof) {
+    set_error("the r-z mode takes no density profile");
+    return PIC_EUNSUPPORTED;
+  }
+  sp.weighted = sp.has_prof || (in.n_explicit > 0 && in.w0 != nullptr) || S->cyl;  // r-z: ring weights
   sp.created = n;  // lattice places (ids and draw indices), kept or not
 
   // FP64 SoA of the initial state, in chunks (device); with a profile the
@@ -855,6 +861,9 @@ pic_status load_species(pic_sim* S, const pic_species& in, SpeciesState& sp) {
   n = kept;
   sp.n = n;
   if (S->prec == PIC_FP64_PLAIN) sp.plain.n = n;
+  if (S->cyl)  // rings: lattice points below the axis reflected, w = own weight * r
+    cyl_load_fix(n, sp.plain.x[1], sp.plain.w, in.n_explicit <= 0, in.n_explicit > 0 && in.w0 != nullptr,
+                 &S->dstat->status, S->s);
   if (aos) S->al.put(aos);
   if (scratch_x2) S->al.put(scratch_x2);
   if (staged) {
@@ -932,6 +941,11 @@ pic_status alloc_spill(pic_sim* S, SpeciesState& sp) {
 // non-null (FP32 form): the kinetic energy and charge summed in the same pass
 void compute_rho(pic_sim* S, Diag64* acc = nullptr) {
   cudaMemsetAsync(S->rho, 0, 8 * (size_t)S->L.plane, S->s);
+  if (S->cyl) {
+    for (auto& sp : S->sp) cyl_rho(S->L, make_const(S, sp), S->K, sp.plain, S->rho, S->s);
+    cyl_rho_finish(S->L, S->K, S->rho, S->s);
+    return;
+  }
   for (auto& sp : S->sp) {
     PushConst C = make_const(S, sp);
     if (S->prec == PIC_FP64_PLAIN)
@@ -997,7 +1011,10 @@ pic_status one_step(pic_sim* S, bool check_now) {
         double* j[3];
         for (int c = 0; c < 6; ++c) f[c] = fld_ptr<double>(S, c);
         for (int c = 0; c < 3; ++c) j[c] = cur_ptr<double>(S, c);
-        plain_push(S->ndim, S->L, C, s.plain, f, j, &S->dstat->status, S->s);
+        if (S->cyl)
+          cyl_push(S->L, C, S->K, s.plain, f, j, &S->dstat->status, S->s);
+        else
+          plain_push(S->ndim, S->L, C, s.plain, f, j, &S->dstat->status, S->s);
       } else {
         const int in = s.cur, out = 1 - s.cur;
         // the last step of every sort_period steps re-sorts each tile by cell;
@@ -1025,10 +1042,22 @@ pic_status one_step(pic_sim* S, bool check_now) {
       S->nlaunch += s.n > 0 || S->prec == PIC_FP32_CELLOFF ? 1 : 0;
     }
   }
-  if (S->prec == PIC_FP64_PLAIN)
+  if (S->cyl) {
+    double* f[6];
+    double* j[3];
+    for (int c = 0; c < 6; ++c) f[c] = fld_ptr<double>(S, c);
+    for (int c = 0; c < 3; ++c) j[c] = cur_ptr<double>(S, c);
+    {
+      Span sp(S, 1);
+      cyl_current(S->L, S->K, j, S->s);
+    }
+    Span sp(S, 2);
+    S->nlaunch += 1 + cyl_field_step(S->L, S->K, f, j, S->s);
+  } else if (S->prec == PIC_FP64_PLAIN) {
     field_step<double>(S);
-  else
+  } else {
     field_step<float>(S);
+  }
   if (shift) {  // every field value one cell back; zero front column
     float* eb[6];
     for (int c = 0; c < 6; ++c) eb[c] = fld_ptr<float>(S, c);
@@ -1093,7 +1122,7 @@ pic_status validate_grid(const pic_grid* g) {
     }
     s += 1.0 / (g->dx[d] * g->dx[d]);
     for (int side = 0; side < 2; ++side)
-      if (g->bc[d][side] != PIC_BC_PERIODIC) {
+      if (g->bc[d][side] != PIC_BC_PERIODIC && !(g->coords == PIC_COORDS_CYLINDRICAL && d == 1)) {
         set_error("only periodic boundaries are implemented");
         return PIC_EUNSUPPORTED;
       }
@@ -1113,6 +1142,27 @@ pic_status validate_grid(const pic_grid* g) {
   if (g->deposit == PIC_DEPOSIT_ISIS && g->ndim != 2) {
     set_error("the ISIS deposit is defined for 2D3V only");
     return PIC_EUNSUPPORTED;
+  }
+  if (g->coords != PIC_COORDS_CARTESIAN && g->coords != PIC_COORDS_CYLINDRICAL) {
+    set_error("coords must be PIC_COORDS_CARTESIAN or PIC_COORDS_CYLINDRICAL");
+    return PIC_EINVAL;
+  }
+  if (g->coords == PIC_COORDS_CYLINDRICAL) {
+    if (g->ndim != 2 || g->precision != PIC_FP64_PLAIN || g->deposit != PIC_DEPOSIT_TRISTAN || g->move_window ||
+        g->init_e_gauss_x1 || g->smooth_level[0] || g->smooth_level[1]) {
+      set_error("the r-z mode needs ndim 2, PIC_FP64_PLAIN and the TRISTAN deposit, without smoothing, "
+                "move_window or init_e_gauss_x1");
+      return PIC_EUNSUPPORTED;
+    }
+    if (std::fabs(g->xmin[1] + 0.5 * g->dx[1]) > 1e-12 * g->dx[1]) {
+      set_error("the r-z mode puts the axis through the middle of the first cell: xmin[1] must be -dx[1]/2");
+      return PIC_EINVAL;
+    }
+    // the radial operator's largest eigenvalue with the axis rule is 1.2105 x 4/dr^2
+    if (g->dt >= 1.0 / std::sqrt(1.0 / (g->dx[0] * g->dx[0]) + 1.2105 / (g->dx[1] * g->dx[1]))) {
+      set_error("Courant condition of the r-z mode violated: dt >= 1/sqrt(1/dz^2 + 1.2105/dr^2)");
+      return PIC_ECOURANT;
+    }
   }
   if (g->dt >= 1.0 / std::sqrt(s)) {
     set_error("Courant condition violated: dt >= 1/sqrt(sum dx^-2)");
@@ -1198,6 +1248,8 @@ pic_status init_sim(const pic_grid* grid, const pic_species* species, int nspeci
   int nxv[3] = {grid->nx[0], grid->nx[1], grid->ndim == 3 ? grid->nx[2] : 1};
   S->L = make_layout(S->ndim, nxv);
   S->L.open_x = S->moving ? 1 : 0;
+  S->cyl = grid->coords == PIC_COORDS_CYLINDRICAL;
+  S->K = CylConst{grid->nx[0], grid->nx[1], grid->dx[0], grid->dx[1], grid->dt, ((double)grid->nx[1] - 0.5) * grid->dx[1]};
   if (S->prec == PIC_FP32_CELLOFF) {
     for (int d = 0; d < 3; ++d) S->T[d] = d < S->ndim ? grid->tile[d] : 1;
     if (S->T[0] <= 0 || S->T[1] <= 0 || (S->ndim == 3 && S->T[2] <= 0)) {
@@ -1301,7 +1353,10 @@ pic_status init_sim(const pic_grid* grid, const pic_species* species, int nspeci
   if (S->prec == PIC_FP64_PLAIN) {
     double* f[6];
     for (int c = 0; c < 6; ++c) f[c] = fld_ptr<double>(S, c);
-    fill_guards<double>(S->L, f, 6, S->s);
+    if (S->cyl)
+      cyl_bound(S->L, S->K, f, true, S->s);
+    else
+      fill_guards<double>(S->L, f, 6, S->s);
   } else {
     float* f[6];
     for (int c = 0; c < 6; ++c) f[c] = fld_ptr<float>(S, c);
@@ -1390,7 +1445,10 @@ pic_status pic_set_field(pic_sim* S, int which, const void* src, size_t src_byte
     unpack_interior<double>(S->L, from, f, S->s);
     double* all[6];
     for (int c = 0; c < 6; ++c) all[c] = fld_ptr<double>(S, c);
-    fill_guards<double>(S->L, all, 6, S->s);
+    if (S->cyl)
+      cyl_bound(S->L, S->K, all, true, S->s);
+    else
+      fill_guards<double>(S->L, all, 6, S->s);
   } else {
     float* f = fld_ptr<float>(S, which);
     unpack_interior<float>(S->L, from, f, S->s);
@@ -1607,7 +1665,11 @@ pic_status pic_diag(pic_sim* S, pic_diag_t* out) {
   compute_rho(S, S->prec == PIC_FP64_PLAIN ? nullptr : S->dacc);
   double dx[3] = {S->g.dx[0], S->g.dx[1], S->ndim == 3 ? S->g.dx[2] : 1.0};
   long long n = 0;
-  if (S->prec == PIC_FP64_PLAIN) {
+  if (S->cyl) {
+    double* f[6];
+    for (int c = 0; c < 6; ++c) f[c] = fld_ptr<double>(S, c);
+    cyl_diag(S->L, S->K, f, S->rho, S->g.rho_bg, S->dacc, S->s);
+  } else if (S->prec == PIC_FP64_PLAIN) {
     double* f[6];
     for (int c = 0; c < 6; ++c) f[c] = fld_ptr<double>(S, c);
     gauss_residual<double>(S->L, f, S->rho, S->g.rho_bg, dx, S->dacc, S->s);
@@ -1619,7 +1681,10 @@ pic_status pic_diag(pic_sim* S, pic_diag_t* out) {
   }
   for (auto& sp : S->sp) {
     PushConst C = make_const(S, sp);
-    if (S->prec == PIC_FP64_PLAIN) plain_kinetic(C, sp.plain, S->dacc, S->s);
+    if (S->cyl)
+      cyl_kinetic(C, sp.plain, S->dacc, S->s);
+    else if (S->prec == PIC_FP64_PLAIN)
+      plain_kinetic(C, sp.plain, S->dacc, S->s);
     n += sp.n;
   }
   Diag64 h{};
@@ -1633,6 +1698,12 @@ pic_status pic_diag(pic_sim* S, pic_diag_t* out) {
   out->field_energy = 0.5 * h.field_energy * dvol;
   out->kinetic_energy = h.kinetic_energy;
   out->total_charge = h.total_charge;
+  if (S->cyl) {  // per-radian sums (field energy already volume-weighted) over the full 2 pi
+    const double two_pi = 2.0 * 3.141592653589793;
+    out->field_energy = 0.5 * h.field_energy * two_pi;
+    out->kinetic_energy = h.kinetic_energy * two_pi;
+    out->total_charge = h.total_charge * two_pi;
+  }
   out->gauss_resid_max = h.gauss_max;
   out->rho_abs_max = h.rho_max;
   out->rho_particles_abs_max = h.rho_part_max;
@@ -2407,6 +2478,10 @@ pic_status pic_laser_add(pic_sim* S, const pic_laser* L) {
       (L->wavetype != 0 && L->wavetype != 1 && L->wavetype != 2)) {
     set_error("pic_laser_add: bad arguments");
     return PIC_EINVAL;
+  }
+  if (S->cyl) {
+    set_error("pic_laser_add: no laser in the r-z mode");
+    return PIC_EUNSUPPORTED;
   }
   if (L->antenna && (!S->moving || S->prec != PIC_FP32_CELLOFF || L->wavetype == 2)) {
     set_error("pic_laser_add: an antenna needs the open x1 boundary of a move_window simulation (FP32) and "

@@ -212,6 +212,36 @@ void global_to_flat(int ndim, const Layout& L, const Tiles& tg, const PushConst&
 void tiled_rho(const Layout& L, const PushConst& C, const Tiles& tg, const TileSide& in, double* rho, Diag64* acc,
                cudaStream_t s);
 
+// ----------------------------------------------------------------- r-z mode
+// 2D cylindrically symmetric form (FP64 plain particles as rings: x[1] = r,
+// r = -1 once absorbed at the wall; w = own weight * r at loading).  Field
+// rows: node row j at r = (j - 1/2) dr, half rows at r = j dr, row 0 the
+// mirror / axis row, row nr the conducting wall.
+struct CylConst {
+  int nz, nr;
+  double dz, dr, dt;
+  double rmax;  // (nr - 1/2) dr
+};
+// lattice: reflect r < 0 (first cell below the axis); explicit: r < 0 flags
+// ST_BADCELL.  Then w = (has_w0 ? w : 1) * r.
+void cyl_load_fix(long long n, double* r, double* w, bool lattice, bool has_w0, int* status, cudaStream_t s);
+void cyl_push(const Layout& L, const PushConst& C, const CylConst& K, Plain p, double* const* f, double* const* j,
+              int* status, cudaStream_t s);
+// deposited current -> densities (guards and the mirror row folded, / V(r))
+void cyl_current(const Layout& L, const CylConst& K, double* const* j, cudaStream_t s);
+// axis / wall rows (and, with zguards, the periodic z guard columns)
+void cyl_bound(const Layout& L, const CylConst& K, double* const* f, bool zguards, cudaStream_t s);
+// B half step, E step, B half step with the boundary rows; returns launches
+int cyl_field_step(const Layout& L, const CylConst& K, double* const* f, double* const* j, cudaStream_t s);
+// ring charges on the node rows (rho zeroed by the caller), then to density
+void cyl_rho(const Layout& L, const PushConst& C, const CylConst& K, Plain p, double* rho, cudaStream_t s);
+void cyl_rho_finish(const Layout& L, const CylConst& K, double* rho, cudaStream_t s);
+// field energy sum (per radian, not halved) and the Gauss maxima
+void cyl_diag(const Layout& L, const CylConst& K, double* const* f, const double* rho, double rho_bg, Diag64* acc,
+              cudaStream_t s);
+// kinetic energy and charge of the live rings (per radian)
+void cyl_kinetic(const PushConst& C, Plain p, Diag64* acc, cudaStream_t s);
+
 // ----------------------------------------------------------------- loading
 // Lattice loader (nl_species num_par_x, vth, vfl) on the device, FP64 output.
 struct LatticeSpec {

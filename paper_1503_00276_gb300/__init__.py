@@ -229,7 +229,8 @@ class Simulation:
         step = C.c_longlong()
         check(self._lib.pic_info(self._h, C.byref(g), C.byref(nsp), C.byref(step)), "pic_info")
         return {"tile": tuple(g.tile), "sort_period": int(g.sort_period), "ctas_per_sm": int(g.ctas_per_sm),
-                "nspecies": int(nsp.value), "step": int(step.value), "precision": int(g.precision)}
+                "nspecies": int(nsp.value), "step": int(step.value), "precision": int(g.precision),
+                "coords": int(g.coords)}
 
     # -- lifecycle ----------------------------------------------------------
     def close(self):

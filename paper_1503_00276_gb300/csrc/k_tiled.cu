@@ -1795,20 +1795,20 @@ __global__ void k_global_to_flat(int ndim, Layout L, Tiles tg, PushConst C, cons
 
 // Charge density of one tile's particles (one block per tile).  Every stored
 // particle's cell is local to its tile, so its weights land on the tile's
-// (T+1)^d nodes.  A warp takes kRhoWarp consecutive slots: it copies them
-// coalesced into shared memory (cp.async), and each lane then takes kRhoRun consecutive
-// ones -- cell-sorted runs after the last sort -- summing the weights of
-// consecutive same-cell particles in registers (FP32).  Each run goes into a
-// shared node tile of 64-bit fixed-point sums (units of 2^-32, so the node
-// sums do not depend on the order of the adds; node sums must stay below 2^31
-// particle weights), kept as two 32-bit words added by 32-bit atomics (the
-// low word's carry goes into the high word with the high part of the add);
-// the node tile is then added to the FP64 grid once: plain
-// adds for the nodes no other tile touches, atomics on the tile's faces.
+// (T+1)^d nodes.  A warp takes kRhoWarp consecutive slots, copied coalesced
+// into shared memory by cp.async; each lane then takes kRhoRun consecutive ones
+// (cell-sorted runs after the last sort) and sums the weights of consecutive
+// same-cell particles in registers (FP32).  Each run goes into a shared node
+// tile of 64-bit fixed-point sums in units of 2^-32, so the node sums do not
+// depend on the order of the adds (a node's sum must stay below 2^31 particle
+// weights).  The sums are kept as two 32-bit words added by 32-bit atomics: the
+// low word's carry goes into the high word with the high part of the add.  The
+// node tile is then added to the FP64 grid once: plain adds for the nodes no
+// other tile touches, atomics on the tile's faces.
 // KIN: the same pass also sums the kinetic energy m c^2 (gamma - 1) and the
-// charge of the tile's particles into acc, gamma - 1 = u^2 / (1 + gamma) in
-// FP32 from the FP32 momenta (no cancellation at small u), per run in FP32,
-// across runs in FP64.
+// charge of the tile's particles into acc; gamma - 1 = u^2 / (1 + gamma) in
+// FP32 from the FP32 momenta (no cancellation at small u), summed per run in
+// FP32 and across runs in FP64.
 constexpr int kRhoRun = 8;
 constexpr int kRhoWarp = 32 * kRhoRun;
 constexpr int kRhoThreads = 128;

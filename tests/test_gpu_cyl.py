@@ -207,3 +207,32 @@ def test_unsupported_r_z_options_are_refused(case):
         pg.Simulation(g, [workload.Species(rqm=-1.0, ppc=(1, 1, 1))], precision=prec)
     want = {"fp32": "EUNSUPPORTED", "xmin": "EINVAL", "courant": "ECOURANT", "smooth": "EUNSUPPORTED"}[case]
     assert want in str(e.value) or {"EUNSUPPORTED": "-8", "EINVAL": "-1", "ECOURANT": "-4"}[want] in str(e.value)
+
+
+def test_checkpoint_roundtrip_in_the_r_z_mode(tmp_path):
+    """Save / load keeps the mode, the ring weights and the absorbed slots bit
+    for bit, and the restored run continues like the uninterrupted one."""
+    import paper_1503_00276_gb300 as pg
+    g = _grid(16, 12, rho_bg=0.0)
+    rng = np.random.default_rng(8)
+    n = 96
+    x = np.c_[rng.uniform(0, 1.6, n), rng.uniform(0.0, 1.1, n), np.zeros(n)]
+    u = np.c_[rng.normal(0, 0.3, n), rng.normal(0.5, 1.5, n), rng.normal(0, 1.0, n)]
+    a = _sim(g, [workload.Species(rqm=-1.0)], [(x, u, -0.01, -1.0, None)])
+    a.step(6)
+    path = tmp_path / "rz.ckpt"
+    a.save(path)
+    b = pg.Simulation.load(path)
+    assert b.info()["coords"] == 1
+    for s in (a, b):
+        assert (s.particles(0)[0][:, 1] < 0).any()  # some rings were absorbed
+    np.testing.assert_array_equal(a.particles(0)[0], b.particles(0)[0])
+    np.testing.assert_array_equal(a.weights(0), b.weights(0))
+    for name in NAMES:
+        np.testing.assert_array_equal(a.fields(name), b.fields(name))
+    a.step(4)
+    b.step(4)
+    np.testing.assert_allclose(b.particles(0)[0], a.particles(0)[0], rtol=0, atol=1e-12)
+    assert abs(a.diag()["field_energy"] - b.diag()["field_energy"]) <= 1e-12 * a.diag()["field_energy"]
+    a.close()
+    b.close()

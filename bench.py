@@ -187,6 +187,26 @@ def describe(args, n_p: int):
     }
 
 
+# ---------------------------------------------------------------- replicas
+def rank_reducers(dist, device):
+    """(max over ranks, sum over ranks) of a host float, through an all-reduce
+    of a one-element FP64 tensor on ``device``; identities without a process
+    group.  Each rank runs its own replica (no data-path collective): the job's
+    time is the slowest rank's and its units are the sum over the ranks."""
+    import torch
+
+    def reduce(v: float, op) -> float:
+        if dist is None:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=op)
+        return float(t.item())
+
+    if dist is None:
+        return (lambda v: v), (lambda v: v)
+    return (lambda v: reduce(v, dist.ReduceOp.MAX)), (lambda v: reduce(v, dist.ReduceOp.SUM))
+
+
 # ---------------------------------------------------------------- our arm
 def run_ours(args):
     import torch
@@ -209,19 +229,7 @@ def run_ours(args):
             dist.barrier()
         torch.cuda.synchronize()
 
-    def max_over_ranks(v: float) -> float:
-        if dist is None:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
-
-    def sum_over_ranks(v: float) -> float:
-        if dist is None:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        return float(t.item())
+    max_over_ranks, sum_over_ranks = rank_reducers(dist, "cuda")
 
     def timed(sim, steps, warmup, clocks=None):
         for _ in range(warmup):

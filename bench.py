@@ -325,37 +325,44 @@ def run_ours(args):
 
 
 def run_cylindrical(args, max_over_ranks):
-    """The r-z (2D cylindrically symmetric) mode, FP64 plain form: a thermal
-    plasma column of 2048 x 512 cells of 0.1 c/w_p out to a conducting wall,
-    4 rings per cell (4.2M), u_th = 0.05, fixed ion background."""
+    """The r-z (2D cylindrically symmetric) mode: a thermal plasma column of
+    2048 x 512 cells of 0.1 c/w_p out to a conducting wall, 4 rings per cell
+    (4.2M), u_th = 0.05, fixed ion background; the FP32 tiled form (the
+    line's value) and the FP64 plain form."""
     import torch
 
     import paper_1503_00276_gb300 as pg
     import workload
 
     g, sps, _ = workload.config_cyl()
-    sim = pg.Simulation(g, sps, precision="fp64")
     K, W = args.cyl_steps, 3
     stream = torch.cuda.current_stream()
-    sim.timing_enable(True)
-    sim.step(W)
-    torch.cuda.synchronize()
-    sim.timing_read(reset=True)
-    n0 = sim.n_particles()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    sim.step(K)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms = max_over_ranks(e0.elapsed_time(e1))
-    tim = sim.timing_read()
-    d = sim.diag()
-    sim.close()
-    return {"workload": f"r-z plasma column 2048x512 cells, dz = dr = 0.1, 2x2 rings per cell ({n0:,}), "
-                        "u_th=0.05, conducting wall, FP64 plain", "steps": K, "warmup": W,
-            "value": n0 * K / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / K,
-            "stages_ms_per_step": {k: round(v[0] / K, 4) for k, v in tim.items() if k != "launches"},
-            "gauss_resid_max_after": d["gauss_resid_max"], "rho_abs_max_after": d["rho_abs_max"]}
+    res = {}
+    for prec in ("fp32", "fp64"):
+        sim = pg.Simulation(g, sps, precision=prec)
+        sim.timing_enable(True)
+        sim.step(W)
+        torch.cuda.synchronize()
+        sim.timing_read(reset=True)
+        n0 = sim.n_particles()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sim.step(K)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = max_over_ranks(e0.elapsed_time(e1))
+        tim = sim.timing_read()
+        d = sim.diag()
+        info = sim.info()
+        sim.close()
+        res[prec] = {"value": n0 * K / (ms / 1e3), "ms_per_step": ms / K, "tile": list(info["tile"]),
+                     "stages_ms_per_step": {k: round(v[0] / K, 4) for k, v in tim.items() if k != "launches"},
+                     "gauss_resid_max_after": d["gauss_resid_max"], "rho_abs_max_after": d["rho_abs_max"]}
+    out = {"workload": f"r-z plasma column 2048x512 cells, dz = dr = 0.1, 2x2 rings per cell ({n0:,}), "
+                       "u_th=0.05, conducting wall", "steps": K, "warmup": W, "unit": UNIT,
+           "value": res["fp32"]["value"], "precision": "fp32 tiled (value); fp64 plain beside it"}
+    out.update({"fp32": res["fp32"], "fp64": res["fp64"], "fp32_speedup": res["fp32"]["value"] / res["fp64"]["value"]})
+    return out
 
 
 def run_wakefield(args, max_over_ranks):

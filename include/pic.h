@@ -147,11 +147,12 @@ typedef struct {
                                charge q * w * r per radian (w the own weight, 1 without one),
                                moved in 3D and rotated back into the r-z plane; lattice points
                                below the axis are reflected; a particle reaching the wall is
-                               absorbed (its slot stays, with r = -1 and u = 0).  J and RHO are
-                               densities (current or charge per r dr dz); pic_diag totals are
-                               over the full 2 pi.  Needs ndim 2, PIC_FP64_PLAIN, the TRISTAN
-                               deposit, no smoothing, move_window, init_e_gauss_x1 or density
-                               profile, no laser (else PIC_EUNSUPPORTED); bc[1] is not read.
+                               absorbed (PIC_FP64_PLAIN: its slot stays, with r = -1 and u = 0;
+                               PIC_FP32_CELLOFF: it is removed).  J and RHO are densities
+                               (current or charge per r dr dz); pic_diag totals are over the full
+                               2 pi.  Needs ndim 2 and the TRISTAN deposit, no smoothing,
+                               move_window, init_e_gauss_x1 or density profile, no laser, not in a
+                               batch (else PIC_EUNSUPPORTED); bc[1] is not read.
                                Time step: dt < 1/sqrt(1/dx1^2 + 1.2105/dx2^2) (PIC_ECOURANT), the
                                radial factor being the largest eigenvalue of the discrete radial
                                operator with the axis rule, in units of 4/dx2^2. */

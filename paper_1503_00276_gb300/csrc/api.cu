@@ -222,6 +222,7 @@ PushConst make_const(const pic_sim* S, const SpeciesState& sp) {
   C.q = sp.q;
   C.dvol = dvol;
   C.isis = g.deposit == PIC_DEPOSIT_ISIS ? 1 : 0;
+  C.cyl = S->cyl ? 1 : 0;
   return C;
 }
 
@@ -851,6 +852,9 @@ pic_status load_species(pic_sim* S, const pic_species& in, SpeciesState& sp) {
       if (part.id) part.id += kept;
       if (part.w) part.w += kept;
       PushConst C = make_const(S, sp);
+      if (S->cyl)  // rings: lattice points below the axis reflected, w = own weight * r
+        cyl_load_fix(got, gx[1], ws, in.n_explicit <= 0, in.n_explicit > 0 && in.w0 != nullptr, &S->dstat->status,
+                     S->s);
       global_to_flat(nd, S->L, sp.tg, C, gx, gu, gid, sp.weighted ? ws : nullptr, got, part, &S->dstat->status,
                      S->s);
     }
@@ -861,7 +865,7 @@ pic_status load_species(pic_sim* S, const pic_species& in, SpeciesState& sp) {
   n = kept;
   sp.n = n;
   if (S->prec == PIC_FP64_PLAIN) sp.plain.n = n;
-  if (S->cyl)  // rings: lattice points below the axis reflected, w = own weight * r
+  if (S->cyl && S->prec == PIC_FP64_PLAIN)  // rings: lattice points below the axis reflected, w = own weight * r
     cyl_load_fix(n, sp.plain.x[1], sp.plain.w, in.n_explicit <= 0, in.n_explicit > 0 && in.w0 != nullptr,
                  &S->dstat->status, S->s);
   if (aos) S->al.put(aos);
@@ -941,9 +945,15 @@ pic_status alloc_spill(pic_sim* S, SpeciesState& sp) {
 // non-null (FP32 form): the kinetic energy and charge summed in the same pass
 void compute_rho(pic_sim* S, Diag64* acc = nullptr) {
   cudaMemsetAsync(S->rho, 0, 8 * (size_t)S->L.plane, S->s);
-  if (S->cyl) {
-    for (auto& sp : S->sp) cyl_rho(S->L, make_const(S, sp), S->K, sp.plain, S->rho, S->s);
-    cyl_rho_finish(S->L, S->K, S->rho, S->s);
+  if (S->cyl) {  // ring charges (FP64: charges; FP32 tiles: per dz dr), then / V(r)
+    for (auto& sp : S->sp) {
+      PushConst C = make_const(S, sp);
+      if (S->prec == PIC_FP64_PLAIN)
+        cyl_rho(S->L, C, S->K, sp.plain, S->rho, S->s);
+      else
+        tiled_rho(S->L, C, sp.tg, sp.side[sp.cur], S->rho, acc, S->s);
+    }
+    cyl_rho_finish(S->L, S->K, S->rho, S->prec == PIC_FP64_PLAIN ? S->g.dx[0] * S->g.dx[1] : 1.0, S->s);
     return;
   }
   for (auto& sp : S->sp) {
@@ -955,6 +965,21 @@ void compute_rho(pic_sim* S, Diag64* acc = nullptr) {
   }
   double* r[1] = {S->rho};
   fold_guards<double>(S->L, r, 1, S->s);
+}
+
+// r-z: current to densities, then the r-z field solve
+template <typename T>
+void cyl_fields(pic_sim* S) {
+  T* f[6];
+  T* j[3];
+  for (int c = 0; c < 6; ++c) f[c] = fld_ptr<T>(S, c);
+  for (int c = 0; c < 3; ++c) j[c] = cur_ptr<T>(S, c);
+  {
+    Span sp(S, 1);
+    cyl_current<T>(S->L, S->K, j, S->s);
+  }
+  Span sp(S, 2);
+  S->nlaunch += 1 + cyl_field_step<T>(S->L, S->K, f, j, S->s);
 }
 
 template <typename T>
@@ -1042,17 +1067,10 @@ pic_status one_step(pic_sim* S, bool check_now) {
       S->nlaunch += s.n > 0 || S->prec == PIC_FP32_CELLOFF ? 1 : 0;
     }
   }
-  if (S->cyl) {
-    double* f[6];
-    double* j[3];
-    for (int c = 0; c < 6; ++c) f[c] = fld_ptr<double>(S, c);
-    for (int c = 0; c < 3; ++c) j[c] = cur_ptr<double>(S, c);
-    {
-      Span sp(S, 1);
-      cyl_current(S->L, S->K, j, S->s);
-    }
-    Span sp(S, 2);
-    S->nlaunch += 1 + cyl_field_step(S->L, S->K, f, j, S->s);
+  if (S->cyl && S->prec == PIC_FP64_PLAIN) {
+    cyl_fields<double>(S);
+  } else if (S->cyl) {
+    cyl_fields<float>(S);
   } else if (S->prec == PIC_FP64_PLAIN) {
     field_step<double>(S);
   } else {
@@ -1075,7 +1093,7 @@ pic_status one_step(pic_sim* S, bool check_now) {
   if (cudaStreamSynchronize(S->s) != cudaSuccess) return cuda_check("step");
   const int flags = S->hstat->status;
   S->sticky_flags |= flags;
-  if (S->moving)
+  if (S->moving || (S->cyl && S->prec == PIC_FP32_CELLOFF))  // dropped (and injected) particles
     for (auto& s : S->sp) {
       int lost = 0, kept = 0;
       cudaMemcpy(&lost, s.d_lost, sizeof(int), cudaMemcpyDeviceToHost);
@@ -1148,10 +1166,10 @@ pic_status validate_grid(const pic_grid* g) {
     return PIC_EINVAL;
   }
   if (g->coords == PIC_COORDS_CYLINDRICAL) {
-    if (g->ndim != 2 || g->precision != PIC_FP64_PLAIN || g->deposit != PIC_DEPOSIT_TRISTAN || g->move_window ||
-        g->init_e_gauss_x1 || g->smooth_level[0] || g->smooth_level[1]) {
-      set_error("the r-z mode needs ndim 2, PIC_FP64_PLAIN and the TRISTAN deposit, without smoothing, "
-                "move_window or init_e_gauss_x1");
+    if (g->ndim != 2 || g->deposit != PIC_DEPOSIT_TRISTAN || g->move_window || g->init_e_gauss_x1 ||
+        g->smooth_level[0] || g->smooth_level[1]) {
+      set_error("the r-z mode needs ndim 2 and the TRISTAN deposit, without smoothing, move_window or "
+                "init_e_gauss_x1");
       return PIC_EUNSUPPORTED;
     }
     if (std::fabs(g->xmin[1] + 0.5 * g->dx[1]) > 1e-12 * g->dx[1]) {
@@ -1233,7 +1251,8 @@ pic_status init_sim(const pic_grid* grid, const pic_species* species, int nspeci
   }
   pic_sim* S = new pic_sim();
   S->moving = grid->move_window != 0;
-  S->no_small = no_small || S->moving;
+  // r-z rings are weighted: the general tile kernel (the small one has no weights)
+  S->no_small = no_small || S->moving || grid->coords == PIC_COORDS_CYLINDRICAL;
   S->g = *grid;
   S->ndim = grid->ndim;
   S->prec = grid->precision;
@@ -1354,13 +1373,16 @@ pic_status init_sim(const pic_grid* grid, const pic_species* species, int nspeci
     double* f[6];
     for (int c = 0; c < 6; ++c) f[c] = fld_ptr<double>(S, c);
     if (S->cyl)
-      cyl_bound(S->L, S->K, f, true, S->s);
+      cyl_bound<double>(S->L, S->K, f, true, S->s);
     else
       fill_guards<double>(S->L, f, 6, S->s);
   } else {
     float* f[6];
     for (int c = 0; c < 6; ++c) f[c] = fld_ptr<float>(S, c);
-    fill_guards<float>(S->L, f, 6, S->s);
+    if (S->cyl)
+      cyl_bound<float>(S->L, S->K, f, true, S->s);
+    else
+      fill_guards<float>(S->L, f, 6, S->s);
   }
   if (cudaStreamSynchronize(S->s) != cudaSuccess) return bail(cuda_check("pic_init"));
   if ((st = cuda_check("pic_init")) != PIC_OK) return bail(st);
@@ -1446,7 +1468,7 @@ pic_status pic_set_field(pic_sim* S, int which, const void* src, size_t src_byte
     double* all[6];
     for (int c = 0; c < 6; ++c) all[c] = fld_ptr<double>(S, c);
     if (S->cyl)
-      cyl_bound(S->L, S->K, all, true, S->s);
+      cyl_bound<double>(S->L, S->K, all, true, S->s);
     else
       fill_guards<double>(S->L, all, 6, S->s);
   } else {
@@ -1454,7 +1476,10 @@ pic_status pic_set_field(pic_sim* S, int which, const void* src, size_t src_byte
     unpack_interior<float>(S->L, from, f, S->s);
     float* all[6];
     for (int c = 0; c < 6; ++c) all[c] = fld_ptr<float>(S, c);
-    fill_guards<float>(S->L, all, 6, S->s);
+    if (S->cyl)
+      cyl_bound<float>(S->L, S->K, all, true, S->s);
+    else
+      fill_guards<float>(S->L, all, 6, S->s);
   }
   if (cudaStreamSynchronize(S->s) != cudaSuccess) return cuda_check("pic_set_field");
   return cuda_check("pic_set_field");
@@ -1665,10 +1690,14 @@ pic_status pic_diag(pic_sim* S, pic_diag_t* out) {
   compute_rho(S, S->prec == PIC_FP64_PLAIN ? nullptr : S->dacc);
   double dx[3] = {S->g.dx[0], S->g.dx[1], S->ndim == 3 ? S->g.dx[2] : 1.0};
   long long n = 0;
-  if (S->cyl) {
+  if (S->cyl && S->prec == PIC_FP64_PLAIN) {
     double* f[6];
     for (int c = 0; c < 6; ++c) f[c] = fld_ptr<double>(S, c);
-    cyl_diag(S->L, S->K, f, S->rho, S->g.rho_bg, S->dacc, S->s);
+    cyl_diag<double>(S->L, S->K, f, S->rho, S->g.rho_bg, S->dacc, S->s);
+  } else if (S->cyl) {
+    float* f[6];
+    for (int c = 0; c < 6; ++c) f[c] = fld_ptr<float>(S, c);
+    cyl_diag<float>(S->L, S->K, f, S->rho, S->g.rho_bg, S->dacc, S->s);
   } else if (S->prec == PIC_FP64_PLAIN) {
     double* f[6];
     for (int c = 0; c < 6; ++c) f[c] = fld_ptr<double>(S, c);
@@ -1681,9 +1710,9 @@ pic_status pic_diag(pic_sim* S, pic_diag_t* out) {
   }
   for (auto& sp : S->sp) {
     PushConst C = make_const(S, sp);
-    if (S->cyl)
+    if (S->cyl && S->prec == PIC_FP64_PLAIN)
       cyl_kinetic(C, sp.plain, S->dacc, S->s);
-    else if (S->prec == PIC_FP64_PLAIN)
+    else if (S->prec == PIC_FP64_PLAIN && !S->cyl)
       plain_kinetic(C, sp.plain, S->dacc, S->s);
     n += sp.n;
   }
@@ -1869,8 +1898,8 @@ pic_status pic_batch_init(int nsims, const pic_grid* grids, const pic_species* s
   *out = nullptr;
   const int ndim = grids[0].ndim;
   for (int i = 0; i < nsims; ++i) {
-    if (grids[i].precision != PIC_FP32_CELLOFF || grids[i].ndim != ndim) {
-      set_error("pic_batch_init: every simulation must be FP32 cell-offset with the same ndim");
+    if (grids[i].precision != PIC_FP32_CELLOFF || grids[i].ndim != ndim || grids[i].coords != PIC_COORDS_CARTESIAN) {
+      set_error("pic_batch_init: every simulation must be Cartesian, FP32 cell-offset, with the same ndim");
       return PIC_EINVAL;
     }
     for (int d = 0; d < 3; ++d)

@@ -30,6 +30,16 @@ namespace {
 __device__ inline double r_node(const CylConst& K, int j) { return ((double)j - 0.5) * K.dr; }
 __device__ inline double r_half(const CylConst& K, int j) { return (double)j * K.dr; }
 
+// the six field planes / three current planes in the stored precision
+template <typename T>
+struct FT6 {
+  T* c[6];
+};
+template <typename T>
+struct JT3 {
+  T* c[3];
+};
+
 // Lattice points of the first cell below the axis reflected to -r; ring
 // weight w = (own weight, 1 without one) * r.  An explicit position below the
 // axis is an error.
@@ -114,27 +124,29 @@ __global__ void __launch_bounds__(256) k_cyl_push(Layout L, PushConst C, CylCons
 // for jz, jtheta, half rows for jr).  The row-1 thread of a column is the only
 // reader of its mirror row and clears it afterwards; the row nr-1 thread
 // clears the wall row.
-__device__ inline double fold_z(const Layout& L, const CylConst& K, const double* A, int i, int j) {
-  double v = A[L.idx(i, j, 0)];
+template <typename T>
+__device__ inline T fold_z(const Layout& L, const CylConst& K, const T* A, int i, int j) {
+  T v = A[L.idx(i, j, 0)];
   if (i == K.nz - 1) v = v + A[L.idx(-1, j, 0)];
   if (i < 3) v = v + A[L.idx(K.nz + i, j, 0)];
   return v;
 }
 
-__global__ void k_cyl_current(Layout L, CylConst K, J3 J) {
+template <typename T>
+__global__ void k_cyl_current(Layout L, CylConst K, JT3<T> J) {
   const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= (long long)K.nz * (K.nr - 1)) return;
   const int i = (int)(q % K.nz), j = 1 + (int)(q / K.nz);
   for (int c = 0; c < 3; ++c) {
-    double* A = J.c[c];
-    double v = fold_z(L, K, A, i, j);
+    T* A = J.c[c];
+    T v = fold_z(L, K, A, i, j);
     if (j == 1) {
-      const double v0 = fold_z(L, K, A, i, 0);
+      const T v0 = fold_z(L, K, A, i, 0);
       v = c == 0 ? v + v0 : (c == 2 ? v - v0 : v);
-      A[L.idx(i, 0, 0)] = 0.0;
+      A[L.idx(i, 0, 0)] = T(0);
     }
-    A[L.idx(i, j, 0)] = v / (c == 1 ? r_half(K, j) : r_node(K, j));
-    if (j == K.nr - 1) A[L.idx(i, K.nr, 0)] = 0.0;
+    A[L.idx(i, j, 0)] = v / (T)(c == 1 ? r_half(K, j) : r_node(K, j));
+    if (j == K.nr - 1) A[L.idx(i, K.nr, 0)] = T(0);
   }
 }
 
@@ -142,70 +154,76 @@ __global__ void k_cyl_current(Layout L, CylConst K, J3 J) {
 // 2d-field-solve-b-part1/-part2 with 2d-field-solve-cyl for Bz and the axis
 // rule for Bz at j = 0: the loop of radius dr/2 about the axis encloses the
 // disc pi (dr/2)^2 and runs along Etheta at r = dr/2, hence the factor 4).
-__global__ void k_cyl_b_half(Layout L, CylConst K, F6 F, double h) {
+// Arithmetic in the stored precision T.
+template <typename T>
+__global__ void k_cyl_b_half(Layout L, CylConst K, FT6<T> F, T h) {
   const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= (long long)K.nz * K.nr) return;
   const int i = (int)(q % K.nz), j = (int)(q / K.nz);
   const int ip = i + 1 == K.nz ? 0 : i + 1;
-  const double* Ez = F.c[0];
-  const double* Er = F.c[1];
-  const double* Et = F.c[2];
-  double* Bz = const_cast<double*>(F.c[3]);
-  double* Br = const_cast<double*>(F.c[4]);
-  double* Bt = const_cast<double*>(F.c[5]);
+  const T* Ez = F.c[0];
+  const T* Er = F.c[1];
+  const T* Et = F.c[2];
+  T* Bz = F.c[3];
+  T* Br = F.c[4];
+  T* Bt = F.c[5];
+  const T dz = (T)K.dz, dr = (T)K.dr;
   const long long c = L.idx(i, j, 0);
   if (j == 0) {
-    Bz[c] = Bz[c] - h * 4.0 * Et[L.idx(i, 1, 0)] / K.dr;
+    Bz[c] = Bz[c] - h * T(4) * Et[L.idx(i, 1, 0)] / dr;
     return;  // Br_0 mirrors row 1, Btheta_0 = 0 on the axis
   }
-  Bz[c] = Bz[c] - h * (r_node(K, j + 1) * Et[L.idx(i, j + 1, 0)] - r_node(K, j) * Et[c]) / (r_half(K, j) * K.dr);
-  Br[c] = Br[c] + h * ((Et[L.idx(ip, j, 0)] - Et[c]) / K.dz);
-  Bt[c] = Bt[c] - h * ((Er[L.idx(ip, j, 0)] - Er[c]) / K.dz - (Ez[L.idx(i, j + 1, 0)] - Ez[c]) / K.dr);
+  Bz[c] = Bz[c] - h * ((T)r_node(K, j + 1) * Et[L.idx(i, j + 1, 0)] - (T)r_node(K, j) * Et[c]) / ((T)r_half(K, j) * dr);
+  Br[c] = Br[c] + h * ((Et[L.idx(ip, j, 0)] - Et[c]) / dz);
+  Bt[c] = Bt[c] - h * ((Er[L.idx(ip, j, 0)] - Er[c]) / dz - (Ez[L.idx(i, j + 1, 0)] - Ez[c]) / dr);
 }
 
 // E advanced by dt from B and j, rows 1 .. nr-1 (eq. 2d-field-solve-e with
 // 2d-field-solve-cyl for Ez).
-__global__ void k_cyl_e(Layout L, CylConst K, F6 F, J3 J, double dt) {
+template <typename T>
+__global__ void k_cyl_e(Layout L, CylConst K, FT6<T> F, JT3<T> J, T dt) {
   const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= (long long)K.nz * (K.nr - 1)) return;
   const int i = (int)(q % K.nz), j = 1 + (int)(q / K.nz);
   const int im = i == 0 ? K.nz - 1 : i - 1;
-  double* Ez = const_cast<double*>(F.c[0]);
-  double* Er = const_cast<double*>(F.c[1]);
-  double* Et = const_cast<double*>(F.c[2]);
-  const double* Bz = F.c[3];
-  const double* Br = F.c[4];
-  const double* Bt = F.c[5];
+  T* Ez = F.c[0];
+  T* Er = F.c[1];
+  T* Et = F.c[2];
+  const T* Bz = F.c[3];
+  const T* Br = F.c[4];
+  const T* Bt = F.c[5];
+  const T dz = (T)K.dz, dr = (T)K.dr;
   const long long c = L.idx(i, j, 0), cd = L.idx(i, j - 1, 0), cm = L.idx(im, j, 0);
-  Ez[c] = Ez[c] + dt * ((r_half(K, j) * Bt[c] - r_half(K, j - 1) * Bt[cd]) / (r_node(K, j) * K.dr) - J.c[0][c]);
-  Er[c] = Er[c] + dt * (-((Bt[c] - Bt[cm]) / K.dz) - J.c[1][c]);
-  Et[c] = Et[c] + dt * ((Br[c] - Br[cm]) / K.dz - (Bz[c] - Bz[cd]) / K.dr - J.c[2][c]);
+  Ez[c] = Ez[c] + dt * (((T)r_half(K, j) * Bt[c] - (T)r_half(K, j - 1) * Bt[cd]) / ((T)r_node(K, j) * dr) - J.c[0][c]);
+  Er[c] = Er[c] + dt * (-((Bt[c] - Bt[cm]) / dz) - J.c[1][c]);
+  Et[c] = Et[c] + dt * ((Br[c] - Br[cm]) / dz - (Bz[c] - Bz[cd]) / dr - J.c[2][c]);
 }
 
 // Axis and wall rows, one thread per z column: Ez_0 = Ez_1, Etheta_0 =
 // -Etheta_1, Br_0 = -Br_1 (the mirror row at r = -dr/2), Er_0 = Btheta_0 = 0
 // (odd, on the axis); at the wall (row nr) and beyond every field is 0.
-__global__ void k_cyl_rows(Layout L, CylConst K, F6 F) {
+template <typename T>
+__global__ void k_cyl_rows(Layout L, CylConst K, FT6<T> F) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= K.nz) return;
-  double* f[6];
-  for (int c = 0; c < 6; ++c) f[c] = const_cast<double*>(F.c[c]);
+  T* const* f = F.c;
   const long long r0 = L.idx(i, 0, 0), r1 = L.idx(i, 1, 0);
   f[0][r0] = f[0][r1];
   f[2][r0] = -f[2][r1];
   f[4][r0] = -f[4][r1];
-  f[1][r0] = 0.0;
-  f[5][r0] = 0.0;
+  f[1][r0] = T(0);
+  f[5][r0] = T(0);
   for (int j = K.nr; j <= K.nr + 1; ++j)
-    for (int c = 0; c < 6; ++c) f[c][L.idx(i, j, 0)] = 0.0;
+    for (int c = 0; c < 6; ++c) f[c][L.idx(i, j, 0)] = T(0);
 }
 
 // Periodic z guard columns (-1, nz .. nz+2) of rows 0 .. nr+1, for the gather.
-__global__ void k_cyl_zguards(Layout L, CylConst K, F6 F) {
+template <typename T>
+__global__ void k_cyl_zguards(Layout L, CylConst K, FT6<T> F) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j > K.nr + 1) return;
   for (int c = 0; c < 6; ++c) {
-    double* f = const_cast<double*>(F.c[c]);
+    T* f = F.c[c];
     f[L.idx(-1, j, 0)] = f[L.idx(K.nz - 1, j, 0)];
     for (int g = 0; g < 3; ++g) f[L.idx(K.nz + g, j, 0)] = f[L.idx(g, j, 0)];
   }
@@ -229,9 +247,10 @@ __global__ void k_cyl_rho(Layout L, PushConst C, Plain p, double* rho) {
 }
 
 // charge to density, one thread per (z column, node row 1 .. nr-1): guards
-// folded, row 0 folded onto row 1 (even), divided by V = r_j dz dr; the mirror
-// and wall rows cleared by the row-1 and row nr-1 threads (their only readers)
-__global__ void k_cyl_rho_finish(Layout L, CylConst K, double* rho) {
+// folded, row 0 folded onto row 1 (even), divided by V = r_j * area (area =
+// dz dr for charges, 1 for a sum already per dz dr); the mirror and wall rows
+// cleared by the row-1 and row nr-1 threads (their only readers)
+__global__ void k_cyl_rho_finish(Layout L, CylConst K, double* rho, double area) {
   const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= (long long)K.nz * (K.nr - 1)) return;
   const int i = (int)(q % K.nz), j = 1 + (int)(q / K.nz);
@@ -240,7 +259,7 @@ __global__ void k_cyl_rho_finish(Layout L, CylConst K, double* rho) {
     v = v + fold_z(L, K, rho, i, 0);
     rho[L.idx(i, 0, 0)] = 0.0;
   }
-  rho[L.idx(i, j, 0)] = v / (r_node(K, j) * K.dz * K.dr);
+  rho[L.idx(i, j, 0)] = v / (r_node(K, j) * area);
   if (j == K.nr - 1) rho[L.idx(i, K.nr, 0)] = 0.0;
 }
 
@@ -271,7 +290,8 @@ __device__ inline double cyl_block_max(double v, double* red) {
 // divergence (z difference plus (1/r_j) d(r Er)/dr).  Volumes: r dr dz at
 // each component's radius, the axis disc (dr/2)^2/2 dz for the half row on
 // the axis; the mirror row and the wall row are left out.
-__global__ void __launch_bounds__(256) k_cyl_diag_fields(Layout L, CylConst K, F6 F, const double* rho,
+template <typename T>
+__global__ void __launch_bounds__(256) k_cyl_diag_fields(Layout L, CylConst K, FT6<T> F, const double* rho,
                                                          double rho_bg, Diag64* acc) {
   __shared__ double red[32];
   const long long ncell = (long long)K.nz * K.nr;
@@ -281,13 +301,15 @@ __global__ void __launch_bounds__(256) k_cyl_diag_fields(Layout L, CylConst K, F
     const int i = (int)(q % K.nz), j = (int)(q / K.nz);
     const long long c = L.idx(i, j, 0);
     const double vh = j == 0 ? 0.125 * K.dr * K.dr * K.dz : r_half(K, j) * K.dr * K.dz;
-    s = s + (F.c[1][c] * F.c[1][c] + F.c[3][c] * F.c[3][c] + F.c[5][c] * F.c[5][c]) * vh;
+    const double f1 = F.c[1][c], f3 = F.c[3][c], f5 = F.c[5][c];
+    s = s + (f1 * f1 + f3 * f3 + f5 * f5) * vh;
     if (j == 0) continue;
     const double vn = r_node(K, j) * K.dr * K.dz;
-    s = s + (F.c[0][c] * F.c[0][c] + F.c[2][c] * F.c[2][c] + F.c[4][c] * F.c[4][c]) * vn;
+    const double f0 = F.c[0][c], f2 = F.c[2][c], f4 = F.c[4][c];
+    s = s + (f0 * f0 + f2 * f2 + f4 * f4) * vn;
     const int im = i == 0 ? K.nz - 1 : i - 1;
-    const double div = (F.c[0][c] - F.c[0][L.idx(im, j, 0)]) / K.dz +
-                       (r_half(K, j) * F.c[1][c] - r_half(K, j - 1) * F.c[1][L.idx(i, j - 1, 0)]) /
+    const double div = (f0 - (double)F.c[0][L.idx(im, j, 0)]) / K.dz +
+                       (r_half(K, j) * f1 - r_half(K, j - 1) * (double)F.c[1][L.idx(i, j - 1, 0)]) /
                            (r_node(K, j) * K.dr);
     const double rt = rho[c] + rho_bg;
     gm = fmax(gm, fabs(div - rt));
@@ -342,27 +364,32 @@ void cyl_push(const Layout& L, const PushConst& C, const CylConst& K, Plain p, d
   k_cyl_push<<<blocks_for(p.n), 256, 0, s>>>(L, C, K, p, f6(f), J, status);
 }
 
-void cyl_current(const Layout& L, const CylConst& K, double* const* j, cudaStream_t s) {
-  J3 J{{j[0], j[1], j[2]}};
-  k_cyl_current<<<blocks_for((long long)K.nz * (K.nr - 1)), 256, 0, s>>>(L, K, J);
+template <typename T>
+void cyl_current(const Layout& L, const CylConst& K, T* const* j, cudaStream_t s) {
+  JT3<T> J{{j[0], j[1], j[2]}};
+  k_cyl_current<T><<<blocks_for((long long)K.nz * (K.nr - 1)), 256, 0, s>>>(L, K, J);
 }
 
-void cyl_bound(const Layout& L, const CylConst& K, double* const* f, bool zguards, cudaStream_t s) {
-  k_cyl_rows<<<blocks_for(K.nz), 256, 0, s>>>(L, K, f6(f));
-  if (zguards) k_cyl_zguards<<<blocks_for(K.nr + 2), 256, 0, s>>>(L, K, f6(f));
+template <typename T>
+void cyl_bound(const Layout& L, const CylConst& K, T* const* f, bool zguards, cudaStream_t s) {
+  FT6<T> F{{f[0], f[1], f[2], f[3], f[4], f[5]}};
+  k_cyl_rows<T><<<blocks_for(K.nz), 256, 0, s>>>(L, K, F);
+  if (zguards) k_cyl_zguards<T><<<blocks_for(K.nr + 2), 256, 0, s>>>(L, K, F);
 }
 
-int cyl_field_step(const Layout& L, const CylConst& K, double* const* f, double* const* j, cudaStream_t s) {
-  J3 J{{j[0], j[1], j[2]}};
-  const F6 F = f6(f);
+template <typename T>
+int cyl_field_step(const Layout& L, const CylConst& K, T* const* f, T* const* j, cudaStream_t s) {
+  JT3<T> J{{j[0], j[1], j[2]}};
+  FT6<T> F{{f[0], f[1], f[2], f[3], f[4], f[5]}};
   const long long nb = (long long)K.nz * K.nr, ne = (long long)K.nz * (K.nr - 1);
-  k_cyl_b_half<<<blocks_for(nb), 256, 0, s>>>(L, K, F, 0.5 * K.dt);
-  k_cyl_rows<<<blocks_for(K.nz), 256, 0, s>>>(L, K, F);
-  k_cyl_e<<<blocks_for(ne), 256, 0, s>>>(L, K, F, J, K.dt);
-  k_cyl_rows<<<blocks_for(K.nz), 256, 0, s>>>(L, K, F);
-  k_cyl_b_half<<<blocks_for(nb), 256, 0, s>>>(L, K, F, 0.5 * K.dt);
-  k_cyl_rows<<<blocks_for(K.nz), 256, 0, s>>>(L, K, F);
-  k_cyl_zguards<<<blocks_for(K.nr + 2), 256, 0, s>>>(L, K, F);
+  const T h = (T)(0.5 * K.dt), dt = (T)K.dt;
+  k_cyl_b_half<T><<<blocks_for(nb), 256, 0, s>>>(L, K, F, h);
+  k_cyl_rows<T><<<blocks_for(K.nz), 256, 0, s>>>(L, K, F);
+  k_cyl_e<T><<<blocks_for(ne), 256, 0, s>>>(L, K, F, J, dt);
+  k_cyl_rows<T><<<blocks_for(K.nz), 256, 0, s>>>(L, K, F);
+  k_cyl_b_half<T><<<blocks_for(nb), 256, 0, s>>>(L, K, F, h);
+  k_cyl_rows<T><<<blocks_for(K.nz), 256, 0, s>>>(L, K, F);
+  k_cyl_zguards<T><<<blocks_for(K.nr + 2), 256, 0, s>>>(L, K, F);
   return 7;
 }
 
@@ -370,19 +397,31 @@ void cyl_rho(const Layout& L, const PushConst& C, const CylConst& K, Plain p, do
   if (p.n > 0) k_cyl_rho<<<blocks_for(p.n), 256, 0, s>>>(L, C, p, rho);
 }
 
-void cyl_rho_finish(const Layout& L, const CylConst& K, double* rho, cudaStream_t s) {
-  k_cyl_rho_finish<<<blocks_for((long long)K.nz * (K.nr - 1)), 256, 0, s>>>(L, K, rho);
+void cyl_rho_finish(const Layout& L, const CylConst& K, double* rho, double area, cudaStream_t s) {
+  k_cyl_rho_finish<<<blocks_for((long long)K.nz * (K.nr - 1)), 256, 0, s>>>(L, K, rho, area);
 }
 
-void cyl_diag(const Layout& L, const CylConst& K, double* const* f, const double* rho, double rho_bg, Diag64* acc,
+template <typename T>
+void cyl_diag(const Layout& L, const CylConst& K, T* const* f, const double* rho, double rho_bg, Diag64* acc,
               cudaStream_t s) {
   int dev = 0, sms = 1;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const long long want = ((long long)K.nz * K.nr + 255) / 256;
   const int blocks = (int)std::min<long long>(want, 8ll * sms);
-  k_cyl_diag_fields<<<blocks, 256, 0, s>>>(L, K, f6(f), rho, rho_bg, acc);
+  FT6<T> F{{f[0], f[1], f[2], f[3], f[4], f[5]}};
+  k_cyl_diag_fields<T><<<blocks, 256, 0, s>>>(L, K, F, rho, rho_bg, acc);
 }
+
+#define PICGB_CYL_INST(T)                                                                                \
+  template void cyl_current<T>(const Layout&, const CylConst&, T* const*, cudaStream_t);                 \
+  template void cyl_bound<T>(const Layout&, const CylConst&, T* const*, bool, cudaStream_t);             \
+  template int cyl_field_step<T>(const Layout&, const CylConst&, T* const*, T* const*, cudaStream_t);    \
+  template void cyl_diag<T>(const Layout&, const CylConst&, T* const*, const double*, double, Diag64*,   \
+                            cudaStream_t);
+PICGB_CYL_INST(float)
+PICGB_CYL_INST(double)
+#undef PICGB_CYL_INST
 
 void cyl_kinetic(const PushConst& C, Plain p, Diag64* acc, cudaStream_t s) {
   if (p.n > 0) k_cyl_kinetic<<<blocks_for(p.n), 256, 0, s>>>(C, p, acc);

@@ -67,6 +67,9 @@ struct TileArgs {
   int shift_x;          // moving window: this step ends with a one-cell shift back in x1
   int open_x;           // x1 open: a particle leaving the box in x1 is dropped
   int* lost;            // count of dropped particles
+  int cyl;              // 2D r-z mode: x2 = r, rings rotated back into the r-z plane
+  int nrow;             // r-z: cell rows; the conducting wall is the upper face of row nrow-1
+  float dr, dt;         // r-z: dx2 and dt
 };
 
 // Shared-memory tiles: fields and current cover local cells [-1, T+3) in x
@@ -408,8 +411,9 @@ __device__ inline void acc_flush_warp(float* J, Acc& a) {
 // Gather + push + move of one particle, deposit of its first in-cell piece into
 // the accumulator, crossing pieces queued.  Rewrites p in the coordinates of
 // the tile it ends in; returns its key: new cell (stayers) or NC + direction.
-template <int NDIM, int TX, int TY, int TZ, int QCAP = kQCap>
-__device__ inline int push_one(const float* F, float* J, const TileArgs& A, P& p, Acc& acc, float* Q, int* qn) {
+template <int NDIM, int TX, int TY, int TZ, int QCAP = kQCap, bool CYL = false>
+__device__ inline int push_one(const float* F, float* J, const TileArgs& A, P& p, Acc& acc, float* Q, int* qn,
+                               int row0 = 0) {
   using G = Geo<NDIM, TX, TY, TZ>;
   const int lx = p.cell & 255, ly = (p.cell >> 8) & 255, lz = NDIM == 3 ? (p.cell >> 16) & 255 : 0;
   if (lx >= TX || ly >= TY || lz >= TZ) {
@@ -462,15 +466,44 @@ __device__ inline int push_one(const float* F, float* J, const TileArgs& A, P& p
   // position update in cell units
   const float ig2 = rsqrtf(1.f + ux * ux + uy * uy + uz * uz);
   const float ax = p.o0, ay = p.o1, az = NDIM == 3 ? p.o2 : 0.f;
-  const float bx = ax + ux * ig2 * A.dt_dx[0];
-  const float by = ay + uy * ig2 * A.dt_dx[1];
+  float bx = ax + ux * ig2 * A.dt_dx[0];
+  float by = ay + uy * ig2 * A.dt_dx[1];
   const float bz = NDIM == 3 ? az + uz * ig2 * A.dt_dx[2] : 0.f;
+  // r-z (thesis ch. 3, 2D cylindrically symmetric position update): the ring
+  // moves in 3D from (r, 0) by (dt v_r, dt v_theta) and is rotated back into
+  // the r-z plane; p_r is the momentum along the new radius and r p_theta is
+  // conserved.  The radial step r' - r is formed without cancellation.  A
+  // ring reaching the wall (upper face of the last row) is absorbed: its path
+  // is cut there.
+  float un1 = uy, un2 = uz, tclip = 1.f;
+  bool absorbed = false;
+  if constexpr (CYL) {
+    const float r = ((float)(row0 + ly) + ay - 0.5f) * A.dr;
+    const float d2 = uy * ig2 * A.dt, d3 = uz * ig2 * A.dt;
+    const float x2 = r + d2, rn = sqrtf(x2 * x2 + d3 * d3);
+    if (rn > 0.f) {
+      by = ay + (d2 * (r + x2) + d3 * d3) / ((r + rn) * A.dr);
+      un1 = (uy * x2 + uz * d3) / rn;
+      un2 = uz * r / rn;
+    } else {
+      by = ay - r / A.dr;
+      un1 = sqrtf(uy * uy + uz * uz);
+      un2 = 0.f;
+    }
+    const float top = (float)(A.nrow - row0 - ly);  // the wall, in this cell's units
+    if (by >= top) {
+      tclip = (top - ay) / (by - ay);
+      bx = fmaf(tclip, bx - ax, ax);
+      by = top;
+      absorbed = true;
+    }
+  }
   if (!(isfinite(bx) && isfinite(by) && isfinite(bz) && isfinite(ux) && isfinite(uy) && isfinite(uz))) {
     atomicOr(A.status, ST_NONFINITE);
     p.cell = cellp | ((uint32_t)DIR_STAY << 24);
     return lx + TX * (ly + TY * lz);  // kept in place, not advanced
   }
-  const float v3 = uz * ig2;
+  const float v3 = uz * ig2 * tclip;  // r-z: v_theta before the rotation, for the time up to the wall
   // first in-cell piece into the accumulator; later pieces to the queue
   float tcx, tcy, tcz;
   int scx, scy, scz;
@@ -531,6 +564,13 @@ __device__ inline int push_one(const float* F, float* J, const TileArgs& A, P& p
                  });
     }
   }
+  if constexpr (CYL) {
+    if (absorbed) {
+      atomicAdd(A.lost, 1);
+      p.cell = kHoleCell;
+      return G::NK;  // absorbed at the wall
+    }
+  }
   // new cell and offset
   int cx = 0, cy = 0, cz = 0;
   float nx = bx, ny = by, nz = bz;
@@ -556,8 +596,8 @@ __device__ inline int push_one(const float* F, float* J, const TileArgs& A, P& p
   p.o1 = ny;
   p.o2 = NDIM == 3 ? nz : 0.f;
   p.u0 = ux;
-  p.u1 = uy;
-  p.u2 = uz;
+  p.u1 = CYL ? un1 : uy;
+  p.u2 = CYL ? un2 : uz;
   return dir == DIR_STAY ? gx + TX * (gy + TY * gz) : G::NC;
 }
 
@@ -971,7 +1011,7 @@ __device__ inline void compact_and_store(const TileArgs& A, int t, int tix, int 
 // the fields, advance, sort and store every particle of the tile, flush the
 // current.  Called by all threads of the block; false if a bounded wait gave
 // up (the block then stops).
-template <int NDIM, int TX, int TY, int TZ, bool SORT>
+template <int NDIM, int TX, int TY, int TZ, bool SORT, bool CYL = false>
 __device__ inline bool sort_tile(const TileArgs& A, const CUtensorMap* fmap, const CUtensorMap* jmap, int t,
                                  int slice, unsigned char* smem, uint32_t& phase) {
   using G = Geo<NDIM, TX, TY, TZ>;
@@ -1091,7 +1131,7 @@ __device__ inline bool sort_tile(const TileArgs& A, const CUtensorMap* fmap, con
       acc.cell = -1;
 #pragma unroll
       for (int r = 0; r < kPPT; ++r)
-        key[r] = r < nvalid ? push_one<NDIM, TX, TY, TZ>(F, J, A, pp[r], acc, Q, misc + 1)
+        key[r] = r < nvalid ? push_one<NDIM, TX, TY, TZ, kQCap, CYL>(F, J, A, pp[r], acc, Q, misc + 1, tiy * TY)
                             : Geo<NDIM, TX, TY, TZ>::NK;
       if (dense) {
         acc_flush_warp<NDIM, TX, TY, TZ>(J, acc);
@@ -1147,7 +1187,7 @@ __device__ inline bool sort_tile(const TileArgs& A, const CUtensorMap* fmap, con
   return true;
 }
 
-template <int NDIM, int TX, int TY, int TZ, int MINB, bool SORT = true>
+template <int NDIM, int TX, int TY, int TZ, int MINB, bool SORT = true, bool CYL = false>
 __global__ void __launch_bounds__(kThreads, MINB)
     k_tile_push(const __grid_constant__ CUtensorMap fmap, const __grid_constant__ CUtensorMap jmap, TileArgs A) {
   using G = Geo<NDIM, TX, TY, TZ>;
@@ -1189,7 +1229,7 @@ __global__ void __launch_bounds__(kThreads, MINB)
     __syncthreads();
     const int t = misc[0];
     if (t >= A.ntiles) break;
-    if (!sort_tile<NDIM, TX, TY, TZ, SORT>(A, &fmap, &jmap, t, misc[2], smem, phase)) return;
+    if (!sort_tile<NDIM, TX, TY, TZ, SORT, CYL>(A, &fmap, &jmap, t, misc[2], smem, phase)) return;
   }
 }
 
@@ -2023,15 +2063,15 @@ __global__ void k_inject(TileArgs A, Tiles tg, InjectSpec J, long long count) {
   }
 }
 
-template <int NDIM, int TX, int TY, int TZ, int MINB, bool SORT = true>
+template <int NDIM, int TX, int TY, int TZ, int MINB, bool SORT = true, bool CYL = false>
 int occupancy() {
   using G = Geo<NDIM, TX, TY, TZ>;
   static int occ = -1;
   if (occ < 0) {
-    cudaFuncSetAttribute(k_tile_push<NDIM, TX, TY, TZ, MINB, SORT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(k_tile_push<NDIM, TX, TY, TZ, MINB, SORT, CYL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          G::SMEM);
     int o = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_tile_push<NDIM, TX, TY, TZ, MINB, SORT>, kThreads,
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_tile_push<NDIM, TX, TY, TZ, MINB, SORT, CYL>, kThreads,
                                                       G::SMEM) != cudaSuccess ||
         o < 1)
       o = 1;
@@ -2056,11 +2096,26 @@ int occupancy_s() {
   return occ;
 }
 
-template <int NDIM, int TX, int TY, int TZ, int MINB, bool SORT>
+template <int NDIM, int TX, int TY, int TZ, int MINB, bool SORT, bool CYL = false>
 void launch_push(const CUtensorMap* fmap, const CUtensorMap* jmap, const TileArgs& A, int grid, cudaStream_t s) {
   using G = Geo<NDIM, TX, TY, TZ>;
-  occupancy<NDIM, TX, TY, TZ, MINB, SORT>();
-  k_tile_push<NDIM, TX, TY, TZ, MINB, SORT><<<grid, kThreads, G::SMEM, s>>>(*fmap, *jmap, A);
+  occupancy<NDIM, TX, TY, TZ, MINB, SORT, CYL>();
+  k_tile_push<NDIM, TX, TY, TZ, MINB, SORT, CYL><<<grid, kThreads, G::SMEM, s>>>(*fmap, *jmap, A);
+}
+
+// r-z rings (2D shapes only, 4 blocks per SM): the general kernel with the
+// ring move; false for a shape it is not built for
+template <int NDIM, int TX, int TY, int TZ>
+bool launch_push_cyl(const CUtensorMap* fmap, const CUtensorMap* jmap, const TileArgs& A, int grid, bool stream,
+                     cudaStream_t s) {
+  if constexpr (NDIM == 2) {
+    if (stream)
+      launch_push<NDIM, TX, TY, TZ, 4, false, true>(fmap, jmap, A, grid, s);
+    else
+      launch_push<NDIM, TX, TY, TZ, 4, true, true>(fmap, jmap, A, grid, s);
+    return true;
+  }
+  return false;
 }
 
 template <int NDIM, int TX, int TY, int TZ>
@@ -2180,6 +2235,10 @@ TileArgs make_args(const PushConst& C, const Tiles& tg, const TileSide& in, cons
   A.shift_x = 0;
   A.open_x = 0;
   A.lost = nullptr;
+  A.cyl = 0;
+  A.nrow = 0;
+  A.dr = 0.f;
+  A.dt = 0.f;
   return A;
 }
 
@@ -2290,6 +2349,10 @@ int tiled_push(const Layout& L, const PushConst& C, const Tiles& tg, const TileS
   A.shift_x = shift_x;
   A.open_x = L.open_x;
   A.lost = lost;
+  A.cyl = C.cyl;
+  A.nrow = L.ny;
+  A.dr = (float)C.dx[1];
+  A.dt = (float)C.dt;
   int launches = 1;
   if (slices && slices->extra && !stream && !tg.small) {  // heavy tiles are split over several blocks
     cudaMemsetAsync(slices->nextra, 0, sizeof(int), s);
@@ -2318,6 +2381,8 @@ int tiled_push(const Layout& L, const PushConst& C, const Tiles& tg, const TileS
   // order-keeping compaction
 #define X(N, A_, B_, C_)                                                    \
   if (shape_is(tg.ndim, T, N, A_, B_, C_)) {                                \
+    if (A.cyl)                                                              \
+      return launch_push_cyl<N, A_, B_, C_>(fmap, jmap, A, grid, stream, s) ? launches : 0; \
     if (minb == 2)                                                          \
       stream ? launch_push<N, A_, B_, C_, 2, false>(fmap, jmap, A, grid, s) \
              : launch_push<N, A_, B_, C_, 2, true>(fmap, jmap, A, grid, s); \

@@ -60,6 +60,7 @@ struct PushConst {        // per-species constants of one step
   double rqm, q, dvol;
   double L[3];            // box length per direction
   int isis;               // 1: ISIS deposit (2D3V), 0: TRISTAN / Villasenor-Buneman
+  int cyl;                // 1: r-z mode (x2 = r, rings), 0: Cartesian
 };
 
 // FP64 plain form
@@ -228,16 +229,19 @@ void cyl_load_fix(long long n, double* r, double* w, bool lattice, bool has_w0, 
 void cyl_push(const Layout& L, const PushConst& C, const CylConst& K, Plain p, double* const* f, double* const* j,
               int* status, cudaStream_t s);
 // deposited current -> densities (guards and the mirror row folded, / V(r))
-void cyl_current(const Layout& L, const CylConst& K, double* const* j, cudaStream_t s);
+template <typename T> void cyl_current(const Layout& L, const CylConst& K, T* const* j, cudaStream_t s);
 // axis / wall rows (and, with zguards, the periodic z guard columns)
-void cyl_bound(const Layout& L, const CylConst& K, double* const* f, bool zguards, cudaStream_t s);
+template <typename T> void cyl_bound(const Layout& L, const CylConst& K, T* const* f, bool zguards, cudaStream_t s);
 // B half step, E step, B half step with the boundary rows; returns launches
-int cyl_field_step(const Layout& L, const CylConst& K, double* const* f, double* const* j, cudaStream_t s);
+template <typename T>
+int cyl_field_step(const Layout& L, const CylConst& K, T* const* f, T* const* j, cudaStream_t s);
 // ring charges on the node rows (rho zeroed by the caller), then to density
 void cyl_rho(const Layout& L, const PushConst& C, const CylConst& K, Plain p, double* rho, cudaStream_t s);
-void cyl_rho_finish(const Layout& L, const CylConst& K, double* rho, cudaStream_t s);
+// (area: dz dr when rho holds charges, 1 when it holds charge per dz dr)
+void cyl_rho_finish(const Layout& L, const CylConst& K, double* rho, double area, cudaStream_t s);
 // field energy sum (per radian, not halved) and the Gauss maxima
-void cyl_diag(const Layout& L, const CylConst& K, double* const* f, const double* rho, double rho_bg, Diag64* acc,
+template <typename T>
+void cyl_diag(const Layout& L, const CylConst& K, T* const* f, const double* rho, double rho_bg, Diag64* acc,
               cudaStream_t s);
 // kinetic energy and charge of the live rings (per radian)
 void cyl_kinetic(const PushConst& C, Plain p, Diag64* acc, cudaStream_t s);

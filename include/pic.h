@@ -74,7 +74,10 @@ typedef enum {
 
 /* Boundary types (appendix nl_emf_bound / nl_spe_bound).  This build
  * implements periodic boundaries (nl_node_conf if_periodic) only. */
-enum { PIC_BC_PERIODIC = 0 };
+/* boundary types (appendix nl_emf_bound): periodic; 5 = conducting boundary
+ * with particle absorption and 20 = axial boundary, the two r boundaries of
+ * the 2D cylindrically symmetric mode (lower r: 20, upper r: 5) */
+enum { PIC_BC_PERIODIC = 0, PIC_BC_CONDUCT_ABSORB = 5, PIC_BC_AXIAL = 20 };
 
 /* Field selectors for pic_fields / pic_set_field. */
 enum { PIC_E1 = 0, PIC_E2, PIC_E3, PIC_B1, PIC_B2, PIC_B3, PIC_J1, PIC_J2, PIC_J3, PIC_RHO };
@@ -98,7 +101,8 @@ typedef struct {
   double xmin[3];           /* lower corner of the box (nl_space xmin) */
   double dx[3];             /* cell size */
   double dt;                /* time step; must satisfy dt < 1/sqrt(sum_d dx_d^-2) */
-  int bc[3][2];             /* boundary type per direction and side: PIC_BC_PERIODIC */
+  int bc[3][2];             /* boundary type per direction and side: PIC_BC_PERIODIC; in the
+                               r-z mode bc[1] = {PIC_BC_AXIAL, PIC_BC_CONDUCT_ABSORB} */
   double e0[3], b0[3];      /* constant external fields added at the gather (nl_el_mag_fld) */
   int smooth_level[3];      /* smoothing passes of J per direction (0 = off) */
   double smooth_w[3][PIC_MAX_SMOOTH][3];  /* weights (swfj) per direction and pass;
@@ -152,7 +156,8 @@ typedef struct {
                                (current or charge per r dr dz); pic_diag totals are over the full
                                2 pi.  Needs ndim 2 and the TRISTAN deposit, no smoothing,
                                move_window, init_e_gauss_x1 or density profile, no laser, not in a
-                               batch (else PIC_EUNSUPPORTED); bc[1] is not read.
+                               batch (else PIC_EUNSUPPORTED); bc[1] must be {PIC_BC_AXIAL,
+                               PIC_BC_CONDUCT_ABSORB} (else PIC_EINVAL).
                                Time step: dt < 1/sqrt(1/dx1^2 + 1.2105/dx2^2) (PIC_ECOURANT), the
                                radial factor being the largest eigenvalue of the discrete radial
                                operator with the axis rule, in units of 4/dx2^2. */

@@ -41,9 +41,11 @@ C4  Row 0 (r = -dr/2) mirrors row 1: what the deposit puts on row 0 is folded
 C5  Field rows at the axis: Ez_0 = Ez_1, Etheta_0 = -Etheta_1, Br_0 = -Br_1
     (mirror row), Er_0 = Btheta_0 = 0 (odd, on the axis), Bz_0 from the axis
     formula.
-C6  The upper r boundary (not described for this mode) is a perfectly
-    conducting wall at node row nr, r_max = (nr - 1/2) dr: Ez = Etheta = Br = 0
-    there and every field beyond it 0.  A particle whose move reaches r_max is
+C6  The upper r boundary is the appendix's boundary type 5, "conducting
+    boundary with particle absorption" (the lower one is type 20, the axial
+    boundary of this mode): a perfectly conducting wall at node row nr,
+    r_max = (nr - 1/2) dr, with Ez = Etheta = Br = 0 there and every field
+    beyond it 0.  A particle whose move reaches r_max is
     absorbed: its path is deposited up to the wall (out-of-plane current for
     that fraction of the step) and its slot is kept with r = -1, u = 0.
 C7  The out-of-plane current of a move uses ptheta before the rotation (the

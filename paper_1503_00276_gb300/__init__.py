@@ -81,6 +81,8 @@ def _grid_struct(grid, precision, tile=None, slack=0.0, sort_period=0, ctas_per_
     g.deposit = 1 if dep == "isis" else 0
     g.window_start = float(getattr(grid, "window_start", 0.0))
     g.coords = 1 if getattr(grid, "coords", "cartesian") == "cylindrical" else 0
+    if g.coords:  # r-z: the axial boundary below, the conducting, absorbing wall above
+        g.bc[1][0], g.bc[1][1] = _capi.PIC_BC_AXIAL, _capi.PIC_BC_CONDUCT_ABSORB
     return g
 
 

@@ -12,6 +12,8 @@ STATUS_NAMES = {0: "PIC_OK", -1: "PIC_EINVAL", -2: "PIC_ENOMEM", -3: "PIC_ECUDA"
                 -5: "PIC_EOVERFLOW", -6: "PIC_ENONFINITE", -7: "PIC_ETIMEOUT", -8: "PIC_EUNSUPPORTED",
                 -9: "PIC_ENOTBUILT"}
 PIC_FP64_PLAIN, PIC_FP32_CELLOFF = 0, 1
+PIC_BC_PERIODIC, PIC_BC_CONDUCT_ABSORB, PIC_BC_AXIAL = 0, 5, 20
+PIC_COORDS_CARTESIAN, PIC_COORDS_CYLINDRICAL = 0, 1
 PIC_E1, PIC_E2, PIC_E3, PIC_B1, PIC_B2, PIC_B3, PIC_J1, PIC_J2, PIC_J3, PIC_RHO = range(10)
 FIELD_NAMES = {"E1": 0, "E2": 1, "E3": 2, "B1": 3, "B2": 4, "B3": 5, "J1": 6, "J2": 7, "J3": 8, "RHO": 9}
 MAX_SMOOTH = 8

@@ -1172,6 +1172,10 @@ pic_status validate_grid(const pic_grid* g) {
                 "init_e_gauss_x1");
       return PIC_EUNSUPPORTED;
     }
+    if (g->bc[1][0] != PIC_BC_AXIAL || g->bc[1][1] != PIC_BC_CONDUCT_ABSORB) {
+      set_error("the r-z mode's r boundaries are bc[1] = {PIC_BC_AXIAL, PIC_BC_CONDUCT_ABSORB}");
+      return PIC_EINVAL;
+    }
     if (std::fabs(g->xmin[1] + 0.5 * g->dx[1]) > 1e-12 * g->dx[1]) {
       set_error("the r-z mode puts the axis through the middle of the first cell: xmin[1] must be -dx[1]/2");
       return PIC_EINVAL;

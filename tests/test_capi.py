@@ -163,3 +163,36 @@ def test_checkpoint_load_rejects_missing_and_foreign_files(capi, tmp_path):
     assert lib.pic_checkpoint_load(str(trunc).encode(), None, None, C.byref(h)) == -1
     assert not h.value
     assert lib.pic_checkpoint_save(None, b"x") == -1
+
+
+def _cyl_grid(frac=0.99):
+    g = workload.cyl_grid(16, 8, 0.1, 0.1, frac=frac)
+    from paper_1503_00276_gb300 import _grid_struct
+    return _grid_struct(g, 0)
+
+
+def test_r_z_arguments_are_checked_before_any_device_work(capi):
+    """The r-z mode's grid rules (axial and conducting-absorbing r boundaries,
+    the axis through the first cell, its own time-step bound, the options it
+    does not combine with) are checked before any device work."""
+    import torch
+    lib = capi.load()
+    g = _cyl_grid()
+    assert g.bc[1][0] == capi.PIC_BC_AXIAL and g.bc[1][1] == capi.PIC_BC_CONDUCT_ABSORB
+    g.bc[1][0] = capi.PIC_BC_PERIODIC
+    assert _init(capi, g)[0] == -1 and b"PIC_BC_AXIAL" in lib.pic_last_error()
+    g = _cyl_grid()
+    g.xmin[1] = 0.0
+    assert _init(capi, g)[0] == -1 and b"axis" in lib.pic_last_error()
+    # inside the Cartesian bound, outside the r-z one
+    g = _cyl_grid(frac=1.001)
+    assert _init(capi, g)[0] == -4 and b"r-z" in lib.pic_last_error()
+    g = _cyl_grid()
+    g.smooth_level[0] = 1
+    assert _init(capi, g)[0] == -8
+    g = _cyl_grid()
+    g.coords = 2
+    g.bc[1][0] = g.bc[1][1] = capi.PIC_BC_PERIODIC
+    assert _init(capi, g)[0] == -1 and b"coords" in lib.pic_last_error()
+    if not torch.cuda.is_available():
+        assert _init(capi, _cyl_grid())[0] == -3

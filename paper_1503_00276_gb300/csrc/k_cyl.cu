@@ -1,4 +1,7 @@
-// k_cyl.cu -- the 2D cylindrically symmetric (r-z) mode, FP64 plain form.
+// k_cyl.cu -- the 2D cylindrically symmetric (r-z) mode: the FP64 plain
+// particle kernels, and the field, current and diagnostic kernels of both
+// forms (templated on the stored precision; the FP32 form's particles move in
+// the tile kernel's r-z instantiation).
 //
 // Thesis ch. 3, the 2D cylindrically symmetric algorithms: the Cartesian 2D
 // grid with x1 -> z and x2 -> r (E1,E2,E3 -> Ez,Er,Etheta; B and j likewise),
@@ -16,9 +19,9 @@
 //     B_Theta of the printed Ez update is read as B_Theta,i1,i2-1), Bz on the
 //     axis from the integral form of Faraday's law (eq.
 //     2d-field-solve-cyl-b1-axis), parity rows at the axis.
-// Particles are rings: x[1] = r >= 0 (r = -1: absorbed at the wall), charge
-// q * w per radian with w = (own weight) * r at loading.  Compiled without
-// multiply-add contraction, like the Cartesian plain form.
+// Particles are rings: x[1] = r >= 0 (FP64 form: r = -1 once absorbed at the
+// wall), charge q * w per radian with w = (own weight) * r at loading.
+// Compiled without multiply-add contraction, like the Cartesian plain form.
 #include <algorithm>
 
 #include "plain_dev.cuh"

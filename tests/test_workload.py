@@ -92,3 +92,25 @@ def test_config1_vacuum_gap_puts_the_plasma_edge_ahead_of_the_pulse():
     w = workload.profile_weight(sps[0], x)
     assert w[0] == 0.0 and w[1] == 1.0
     assert workload.load_weighted(g, sps[0])[0].shape[0] == 0  # the window starts in vacuum
+
+
+def test_cylindrical_recipe():
+    """r-z input recipe: the Cartesian lattice of the (z, r) cells from r =
+    -dr/2, the first cell's points below the axis reflected; positions in
+    [0, r_max); dt at 0.99 of the r-z bound, below the Cartesian one."""
+    import math
+    import numpy as np
+    g = workload.cyl_grid(8, 6, 0.1, 0.2)
+    assert g.coords == "cylindrical" and g.xmin[1] == -0.1
+    assert abs(g.dt - 0.99 / math.sqrt(1 / 0.1 ** 2 + workload.CYL_RADIAL_EIG / 0.2 ** 2)) < 1e-15
+    assert g.dt < workload.courant_dt((0.1, 0.2, 1.0), 2)
+    sp = workload.Species(rqm=-1.0, ppc=(2, 2, 1), uth=(0.1,) * 3, seed=3)
+    x, u = workload.load_cylindrical(g, sp)
+    xc, uc = workload.load_particles(g, sp)
+    rmax = (6 - 0.5) * 0.2
+    assert np.all(x[:, 1] >= 0.0) and np.all(x[:, 1] < rmax)
+    np.testing.assert_array_equal(x[:, 1], np.abs(xc[:, 1]))
+    np.testing.assert_array_equal(x[:, 0], xc[:, 0])
+    np.testing.assert_array_equal(u, uc)
+    below = xc[:, 1] < 0.0
+    assert below.sum() == 8 * 2  # one of the two r points of each first-row cell, per z point

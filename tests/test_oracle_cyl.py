@@ -163,3 +163,42 @@ def test_field_energy_of_a_uniform_axial_field():
     s.boundary_fields()
     L = 12 * 0.1
     assert abs(s.field_energy() - 0.5 * 1.7 ** 2 * math.pi * s.rmax ** 2 * L) <= 1e-12 * s.field_energy()
+
+
+def _radial_te_eig(n, dr=1.0):
+    """Largest eigenvalue of the radial part of the r-z solve for the Etheta,
+    Bz family (Etheta on node rows 1..n-1 with Etheta_n = 0 at the wall, Bz on
+    half rows 0..n-1 with the axis rule), from the discrete stencils."""
+    rn = lambda j: (j - 0.5) * dr
+    rh = lambda j: j * dr
+    D = np.zeros((n - 1, n))  # d Etheta_j / dt = -(Bz_j - Bz_{j-1}) / dr
+    G = np.zeros((n, n - 1))  # d Bz_j / dt from Etheta
+    for j in range(1, n):
+        D[j - 1, j] = -1.0 / dr
+        D[j - 1, j - 1] = 1.0 / dr
+    G[0, 0] = -4.0 / dr
+    for j in range(1, n):
+        if j + 1 <= n - 1:
+            G[j, j] -= rn(j + 1) / (rh(j) * dr)
+        G[j, j - 1] += rn(j) / (rh(j) * dr)
+    return float(np.max(np.real(np.linalg.eigvals(-G @ D))))
+
+
+def test_time_step_bound_of_the_r_z_solve():
+    """The leapfrog is stable while dt^2 (4/dz^2 + lambda_r) / 4 < 1, lambda_r
+    the largest radial eigenvalue: 1.2105 x 4/dr^2 with the axis rule (a mode
+    bound to the axis, the same for every nr >= 10).  Vacuum fields stay
+    bounded over 4000 steps at 0.99 of that bound and blow up at 0.99 of the
+    Cartesian one, which lies above it."""
+    lam = [_radial_te_eig(n) / 4.0 for n in (12, 40, 160)]
+    assert max(lam) - min(lam) < 1e-8 and abs(lam[0] - workload.CYL_RADIAL_EIG) < 1e-4
+    for dt, grows in ((workload.cyl_courant_dt(0.1, 0.1), False), (workload.courant_dt((0.1, 0.1, 1.0), 2), True)):
+        s = CylState(16, 12, 0.1, 0.1, dt)
+        rng = np.random.default_rng(0)
+        for c in range(6):
+            s.F[c][:] = rng.normal(0, 1, s.F[c].shape)
+        s.boundary_fields()
+        e0 = s.field_energy()
+        s.step(4000 if not grows else 600)
+        ratio = s.field_energy() / e0
+        assert (not np.isfinite(ratio) or ratio > 1e3) == grows, (dt, ratio)

@@ -196,3 +196,22 @@ def test_r_z_arguments_are_checked_before_any_device_work(capi):
     assert _init(capi, g)[0] == -1 and b"coords" in lib.pic_last_error()
     if not torch.cuda.is_available():
         assert _init(capi, _cyl_grid())[0] == -3
+
+
+def test_enum_values_match_header(capi, tmp_path):
+    """The binding's constants equal the header's enums as the C compiler sees them."""
+    import subprocess
+    names = ["PIC_OK", "PIC_FP64_PLAIN", "PIC_FP32_CELLOFF", "PIC_BC_PERIODIC", "PIC_BC_CONDUCT_ABSORB",
+             "PIC_BC_AXIAL", "PIC_COORDS_CARTESIAN", "PIC_COORDS_CYLINDRICAL", "PIC_E1", "PIC_B3", "PIC_J1",
+             "PIC_RHO"]
+    prog = tmp_path / "enums.c"
+    lines = ['#include <stdio.h>', '#include "pic.h"', "int main(void) {"]
+    lines += [f'  printf("{n} %d\\n", (int){n});' for n in names]
+    lines.append("  return 0; }")
+    prog.write_text("\n".join(lines))
+    exe = tmp_path / "enums"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)], check=True)
+    out = dict(l.split() for l in subprocess.run([str(exe)], capture_output=True, text=True, check=True)
+               .stdout.splitlines())
+    for n in names:
+        assert int(out[n]) == getattr(capi, n), n

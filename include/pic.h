@@ -284,16 +284,21 @@ pic_status pic_destroy(pic_sim* sim);
 /* Message of the last failure on this thread (never NULL). */
 const char* pic_last_error(void);
 
-/* Stateless tile binning (not in the thesis: the supporting per-tile sort).
+/* Stateless tile binning (not in the thesis: the supporting per-tile sort;
+ * the thesis keeps each node's particles in one unsorted array, appendix
+ * nl_species num_par_max).
  * For n particles with integer cell coordinates cell[n][3] (device, int32,
  * each in [0, nx_d)), computes the tile of each particle
  * t = ((c3/T3)*nt2 + c2/T2)*nt1 + c1/T1 (nt_d = nx_d/T_d), the count of every
  * tile (tile_count[ntiles], device int32), the exclusive prefix sum of the counts
  * (tile_start[ntiles], device int64) and a permutation perm[n] (device int64)
  * that lists particles tile by tile, in increasing particle index within each
- * tile.  Scratch memory comes from `alloc` (NULL = cudaMalloc) and is
- * released before returning.  `stream` is a cudaStream_t.  In 2D pass
- * nx[2] = tile[2] = 1 and cell[.][2] = 0. */
+ * tile (a stable sort by tile: the result is unique and does not depend on
+ * scheduling).  n must be below 2^31.  Scratch memory (about 5 bytes per
+ * particle, 9 with more than 255 tiles, 13 with more than 65535) comes from
+ * `alloc` (NULL = cudaMalloc) and is released before returning.  `stream` is a
+ * cudaStream_t.  In 2D pass nx[2] = tile[2] = 1 and cell[.][2] = 0.  A cell
+ * outside [0, nx) returns PIC_EINVAL (the outputs are then unspecified). */
 pic_status pic_bin_tiles(const int nx[3], const int tile[3], long long n, const int* cell,
                          int* tile_count, long long* tile_start, long long* perm,
                          const pic_allocator* alloc, void* stream);
@@ -308,21 +313,23 @@ pic_status pic_bin_tiles(const int nx[3], const int tile[3], long long n, const 
  * its own pool and accounting, in latency-critical paths where a cudaMalloc or
  * cudaFree (which may synchronise the device) is not allowed, or where an
  * allocation failure mid-run cannot be handled.  They get the same result as
- * pic_bin_tiles (same arguments, same output, order within a tile again
- * unspecified) with the scratch taken from a fixed array compiled into the
- * library:
+ * pic_bin_tiles (same arguments, same output: particles tile by tile, in
+ * increasing particle index within each tile) with the scratch taken from a
+ * fixed array compiled into the library:
  *  - its size is PIC_BIN_NOALLOC_SCRATCH_BYTES (16 MiB), reserved on every GPU
  *    that loads the library until the process exits;
- *  - the scratch a call needs is about 4 bytes per particle plus 4 bytes per
- *    tile (e.g. 3 million particles on 512 thousand tiles take 14 MiB);
- *    requests needing more than the array return PIC_EINVAL with a message,
- *    and nothing runs;
- *  - the first call on a device (with that device current) looks the array's
- *    device address up once with cudaGetSymbolAddress; make that first call
- *    before any stream capture;
- *  - every call on a device shares the one array and the function clears what
- *    must start at zero, so calls whose GPU work overlaps (different streams,
- *    threads or processes sharing the library on one device) race and must be
+ *  - the scratch a call needs is about 5 bytes per particle with up to 255
+ *    tiles, 9 with up to 65535 and 13 beyond (e.g. 1.8 million particles on
+ *    32 thousand tiles take 15 MiB); requests needing more than the array
+ *    return PIC_EINVAL with a message, and nothing runs;
+ *  - the first call in a CUDA context (the device current) looks the array's
+ *    device address up with cudaGetSymbolAddress and keeps it for that
+ *    context (a device reset makes a new context, which looks it up again);
+ *    make that first call before any stream capture;
+ *  - every call in one process shares the array on a device (each process has
+ *    its own copy of the library's device memory) and the function clears
+ *    what must start at zero, so calls whose GPU work overlaps (different
+ *    streams or threads of one process on one device) race and must be
  *    serialised by the caller;
  *  - like pic_bin_tiles it synchronises `stream` before returning.
  * It calls no cudaMalloc, cudaFree or other allocating routine. */

@@ -268,13 +268,17 @@ def test_bin_tiles_matches_oracle_binning():
     _, counts, order = oracle.tile_bin(g, tile, cells.astype(np.float64) + 0.5)
     np.testing.assert_array_equal(cnt.cpu().numpy(), counts)
     np.testing.assert_array_equal(start.cpu().numpy(), np.concatenate([[0], np.cumsum(counts)[:-1]]))
-    p = perm.cpu().numpy()
-    st = start.cpu().numpy()
-    for t in rng.integers(0, counts.size, 50):
-        seg = np.sort(p[st[t]:st[t] + counts[t]])
-        np.testing.assert_array_equal(seg, order[st[t]:st[t] + counts[t]])
-    # every particle appears exactly once
-    np.testing.assert_array_equal(np.sort(p), np.arange(n))
+    # the permutation is the oracle's stable order: tile by tile, increasing
+    # particle index within each tile (bit-exact index work)
+    np.testing.assert_array_equal(perm.cpu().numpy(), order)
+    # more than 2^16 tiles (three 8-bit passes over the tile key), and one tile
+    for nx2, tile2, n2 in (((512, 256, 8), (2, 2, 2), 300007), ((16, 8, 8), (16, 8, 8), 5003)):
+        c2 = np.stack([rng.integers(0, nx2[d], n2) for d in range(3)], axis=1).astype(np.int32)
+        cn, sn, pn = pg.bin_tiles(nx2, tile2, torch.from_numpy(c2).cuda())
+        g2 = workload.Grid(ndim=3, nx=nx2, dx=(1.0, 1.0, 1.0), dt=0.1)
+        _, counts2, order2 = oracle.tile_bin(g2, tile2, c2.astype(np.float64) + 0.5)
+        np.testing.assert_array_equal(cn.cpu().numpy(), counts2)
+        np.testing.assert_array_equal(pn.cpu().numpy(), order2)
     # empty input
     c0, s0, p0 = pg.bin_tiles(nx, tile, torch.zeros((0, 3), dtype=torch.int32, device="cuda"))
     assert int(c0.sum()) == 0 and int(s0.max()) == 0 and p0.numel() == 0

@@ -302,7 +302,9 @@ __device__ inline void compact_and_store(const TileArgs& A, int t, int tix, int 
 // the fields, advance, sort and store every particle of the tile, flush the
 // current.  Called by all threads of the block; false if a bounded wait gave
 // up (the block then stops).
-template <int NDIM, int TX, int TY, int TZ, bool SORT, bool CYL = false>
+// IDW = false: the store carries neither ids nor charge weights (every
+// particle's id is 0 and weight 1 at compile time, which frees registers)
+template <int NDIM, int TX, int TY, int TZ, bool SORT, bool CYL = false, bool IDW = true>
 __device__ inline bool sort_tile(const TileArgs& A, const CUtensorMap* fmap, const CUtensorMap* jmap, int t,
                                  int slice, unsigned char* smem, uint32_t& phase) {
   using G = Geo<NDIM, TX, TY, TZ>;
@@ -374,8 +376,8 @@ __device__ inline bool sort_tile(const TileArgs& A, const CUtensorMap* fmap, con
       if (nvalid) {
         const long long s = base + first;
         pp[0] = P{A.in.p.cell[s], A.in.p.o[0][s], A.in.p.o[1][s], NDIM == 3 ? A.in.p.o[2][s] : 0.f,
-                  A.in.p.u[0][s], A.in.p.u[1][s], A.in.p.u[2][s], A.in.p.id ? A.in.p.id[s] : 0,
-                  A.in.p.w ? A.in.p.w[s] : 1.f};
+                  A.in.p.u[0][s], A.in.p.u[1][s], A.in.p.u[2][s], IDW && A.in.p.id ? A.in.p.id[s] : 0,
+                  IDW && A.in.p.w ? A.in.p.w[s] : 1.f};
       }
     } else if (ch < nchunk_s) {
       const int first = ch * kChunk + tid * kPPT;
@@ -396,8 +398,8 @@ __device__ inline bool sort_tile(const TileArgs& A, const CUtensorMap* fmap, con
         load_vec(A.in.p.u[0] + s, v0);
         load_vec(A.in.p.u[1] + s, v1);
         load_vec(A.in.p.u[2] + s, v2);
-        if (A.in.p.id) load_vec(A.in.p.id + s, idv);
-        if (A.in.p.w) load_vec(A.in.p.w + s, wv);
+        if (IDW && A.in.p.id) load_vec(A.in.p.id + s, idv);
+        if (IDW && A.in.p.w) load_vec(A.in.p.w + s, wv);
 #pragma unroll
         for (int r = 0; r < kPPT; ++r) pp[r] = P{cl[r], q0[r], q1[r], q2[r], v0[r], v1[r], v2[r], idv[r], wv[r]};
       }
@@ -410,8 +412,8 @@ __device__ inline bool sort_tile(const TileArgs& A, const CUtensorMap* fmap, con
         if (r < nvalid) {
           const long long s = base + cap - ninc + first + r;
           pp[r] = P{A.in.p.cell[s], A.in.p.o[0][s], A.in.p.o[1][s], NDIM == 3 ? A.in.p.o[2][s] : 0.f,
-                    A.in.p.u[0][s], A.in.p.u[1][s], A.in.p.u[2][s], A.in.p.id ? A.in.p.id[s] : 0,
-                    A.in.p.w ? A.in.p.w[s] : 1.f};
+                    A.in.p.u[0][s], A.in.p.u[1][s], A.in.p.u[2][s], IDW && A.in.p.id ? A.in.p.id[s] : 0,
+                    IDW && A.in.p.w ? A.in.p.w[s] : 1.f};
         }
       }
     }
@@ -478,7 +480,7 @@ __device__ inline bool sort_tile(const TileArgs& A, const CUtensorMap* fmap, con
   return true;
 }
 
-template <int NDIM, int TX, int TY, int TZ, int MINB, bool SORT = true, bool CYL = false>
+template <int NDIM, int TX, int TY, int TZ, int MINB, bool SORT = true, bool CYL = false, bool IDW = true>
 __global__ void __launch_bounds__(kThreads, MINB)
     k_tile_push(const __grid_constant__ CUtensorMap fmap, const __grid_constant__ CUtensorMap jmap, TileArgs A) {
   using G = Geo<NDIM, TX, TY, TZ>;
@@ -520,7 +522,7 @@ __global__ void __launch_bounds__(kThreads, MINB)
     __syncthreads();
     const int t = misc[0];
     if (t >= A.ntiles) break;
-    if (!sort_tile<NDIM, TX, TY, TZ, SORT, CYL>(A, &fmap, &jmap, t, misc[2], smem, phase)) return;
+    if (!sort_tile<NDIM, TX, TY, TZ, SORT, CYL, IDW>(A, &fmap, &jmap, t, misc[2], smem, phase)) return;
   }
 }
 
@@ -1342,16 +1344,16 @@ __global__ void k_inject(TileArgs A, Tiles tg, InjectSpec J, long long count) {
   }
 }
 
-template <int NDIM, int TX, int TY, int TZ, int MINB, bool SORT = true, bool CYL = false>
+template <int NDIM, int TX, int TY, int TZ, int MINB, bool SORT = true, bool CYL = false, bool IDW = true>
 int occupancy() {
   using G = Geo<NDIM, TX, TY, TZ>;
   static int occ = -1;
   if (occ < 0) {
-    cudaFuncSetAttribute(k_tile_push<NDIM, TX, TY, TZ, MINB, SORT, CYL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         G::SMEM);
+    cudaFuncSetAttribute(k_tile_push<NDIM, TX, TY, TZ, MINB, SORT, CYL, IDW>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM);
     int o = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_tile_push<NDIM, TX, TY, TZ, MINB, SORT, CYL>, kThreads,
-                                                      G::SMEM) != cudaSuccess ||
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_tile_push<NDIM, TX, TY, TZ, MINB, SORT, CYL, IDW>,
+                                                      kThreads, G::SMEM) != cudaSuccess ||
         o < 1)
       o = 1;
     occ = o;
@@ -1375,9 +1377,18 @@ int occupancy_s() {
   return occ;
 }
 
+// The sorting step of a store without ids and weights (the common case) runs
+// the IDW = false instantiation; every other case the general one.
 template <int NDIM, int TX, int TY, int TZ, int MINB, bool SORT, bool CYL = false>
 void launch_push(const CUtensorMap* fmap, const CUtensorMap* jmap, const TileArgs& A, int grid, cudaStream_t s) {
   using G = Geo<NDIM, TX, TY, TZ>;
+  if constexpr (SORT && !CYL) {
+    if (!A.in.p.id && !A.in.p.w) {
+      occupancy<NDIM, TX, TY, TZ, MINB, SORT, CYL, false>();
+      k_tile_push<NDIM, TX, TY, TZ, MINB, SORT, CYL, false><<<grid, kThreads, G::SMEM, s>>>(*fmap, *jmap, A);
+      return;
+    }
+  }
   occupancy<NDIM, TX, TY, TZ, MINB, SORT, CYL>();
   k_tile_push<NDIM, TX, TY, TZ, MINB, SORT, CYL><<<grid, kThreads, G::SMEM, s>>>(*fmap, *jmap, A);
 }
@@ -1496,6 +1507,7 @@ TileArgs make_args(const PushConst& C, const Tiles& tg, const TileSide& in, cons
     A.e0[d] = (float)C.e0[d];
     A.b0[d] = (float)C.b0[d];
   }
+  A.ext = C.e0[0] != 0.0 || C.e0[1] != 0.0 || C.e0[2] != 0.0 || C.b0[0] != 0.0 || C.b0[1] != 0.0 || C.b0[2] != 0.0;
   A.j3f = (float)(C.q / C.dvol);
   A.isis = C.isis;
   A.status = status;

@@ -26,6 +26,7 @@ struct TileArgs {
   int isis;             // 1: ISIS deposit (2D3V): a crossing path's in-plane current is
                         // that of its whole straight path, not split at faces
   float e0[3], b0[3];
+  int ext;              // 1: some e0 / b0 component is non-zero
   int* status;
   const int* nslice;    // [ntiles] slices of each tile (nullptr: one work item per tile)
   const int2* extra;    // (tile, slice) of the work items after the first ntiles
@@ -153,24 +154,32 @@ __device__ inline void seg_weights(const TileArgs& A, float ax, float ay, float 
     w[6] = a3 * ((1.f - mx) * my - cv);
     w[7] = a3 * (mx * my + cv);
   } else {
+    // a ((1 - m1)(1 - m2) + c) etc. as fused products: a (1 - m1), a m1 and
+    // a c once per component, then one FMA per weight
     const float dz = bz - az, mz = 0.5f * (az + bz);
-    float a = A.cf[0] * q * dx, cv = dy * dz * (1.f / 12.f);
-    w[0] = a * ((1.f - my) * (1.f - mz) + cv);
-    w[1] = a * (my * (1.f - mz) - cv);
-    w[2] = a * ((1.f - my) * mz - cv);
-    w[3] = a * (my * mz + cv);
+    const float nx = 1.f - mx, ny = 1.f - my, nz = 1.f - mz;
+    const float c12 = 1.f / 12.f;
+    float a = A.cf[0] * q * dx, an = a * ny, am = a * my, ac = a * (dy * dz * c12);
+    w[0] = fmaf(an, nz, ac);
+    w[1] = fmaf(am, nz, -ac);
+    w[2] = fmaf(an, mz, -ac);
+    w[3] = fmaf(am, mz, ac);
     a = A.cf[1] * q * dy;
-    cv = dz * dx * (1.f / 12.f);
-    w[4] = a * ((1.f - mz) * (1.f - mx) + cv);
-    w[5] = a * (mz * (1.f - mx) - cv);
-    w[6] = a * ((1.f - mz) * mx - cv);
-    w[7] = a * (mz * mx + cv);
+    an = a * nz;
+    am = a * mz;
+    ac = a * (dz * dx * c12);
+    w[4] = fmaf(an, nx, ac);
+    w[5] = fmaf(am, nx, -ac);
+    w[6] = fmaf(an, mx, -ac);
+    w[7] = fmaf(am, mx, ac);
     a = A.cf[2] * q * dz;
-    cv = dx * dy * (1.f / 12.f);
-    w[8] = a * ((1.f - mx) * (1.f - my) + cv);
-    w[9] = a * (mx * (1.f - my) - cv);
-    w[10] = a * ((1.f - mx) * my - cv);
-    w[11] = a * (mx * my + cv);
+    an = a * nx;
+    am = a * mx;
+    ac = a * (dx * dy * c12);
+    w[8] = fmaf(an, ny, ac);
+    w[9] = fmaf(am, ny, -ac);
+    w[10] = fmaf(an, my, -ac);
+    w[11] = fmaf(am, my, ac);
   }
 }
 
@@ -432,12 +441,14 @@ __device__ inline int push_one(const float* F, float* J, const TileArgs& A, P& p
     b2 = interp<2, FX, FY>(F + 4 * FP, x1, ly, 0, wx1, p.o1, 0.f);
     b3 = interp<2, FX, FY>(F + 5 * FP, x1, y1, 0, wx1, wy1, 0.f);
   }
-  e1 += A.e0[0];
-  e2 += A.e0[1];
-  e3 += A.e0[2];
-  b1 += A.b0[0];
-  b2 += A.b0[1];
-  b3 += A.b0[2];
+  if (A.ext) {  // constant external fields (uniform branch)
+    e1 += A.e0[0];
+    e2 += A.e0[1];
+    e3 += A.e0[2];
+    b1 += A.b0[0];
+    b2 += A.b0[1];
+    b3 += A.b0[2];
+  }
   // Boris push
   const float al = A.qmdt2;
   const float p1x = fmaf(al, e1, p.u0), p1y = fmaf(al, e2, p.u1), p1z = fmaf(al, e3, p.u2);
@@ -486,7 +497,8 @@ __device__ inline int push_one(const float* F, float* J, const TileArgs& A, P& p
       absorbed = true;
     }
   }
-  if (!(isfinite(bx) && isfinite(by) && isfinite(bz) && isfinite(ux) && isfinite(uy) && isfinite(uz))) {
+  // one test for all six: a NaN or an infinity in any of them makes the sum non-finite
+  if (!isfinite(((bx + by) + bz) + ((ux + uy) + uz))) {
     atomicOr(A.status, ST_NONFINITE);
     p.cell = cellp | ((uint32_t)DIR_STAY << 24);
     return lx + TX * (ly + TY * lz);  // kept in place, not advanced

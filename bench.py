@@ -172,16 +172,24 @@ def make_workload(args, rank: int):
     return g, sps, steps
 
 
-def describe(args, n_p: int):
+def describe(args, n_p: int, info=None, arm: str = "ours"):
+    """The workload of the line.  info: the simulation's pic_info (tile shape
+    and sort period as in use); arm "reference": the FP64 CPU oracle."""
     nx = [int(v) for v in args.nx.split(",")]
+    if arm == "reference":
+        form, prec = "FP64 CPU oracle (reference arm)", "fp64 (oracle)"
+    else:
+        form, prec = ("FP32 cell-offset tiled" if args.precision == "fp32" else "FP64 plain"), args.precision
+    tile = None
+    if arm != "reference" and args.precision == "fp32":
+        tile = list(info["tile"]) if info else args.tile
     return {
         "workload": (f"3D3V periodic thermal plasma {nx[0]}x{nx[1]}x{nx[2]} cells, {args.ppc} ppc "
-                     f"({n_p:,} electrons), u_th=0.05c, dx=0.1 c/w_p, dt=0.99 Courant, "
-                     f"{'FP32 cell-offset tiled' if args.precision == 'fp32' else 'FP64 plain'}"),
-        "grid": nx, "ppc": args.ppc, "precision": args.precision,
-        "tile": args.tile if args.precision == "fp32" else None,
+                     f"({n_p:,} electrons), u_th=0.05c, dx=0.1 c/w_p, dt=0.99 Courant, {form}"),
+        "grid": nx, "ppc": args.ppc, "precision": prec,
+        "tile": tile,
         "smoothing_passes": args.smooth,
-        "sort_period": args.sort_period or None,
+        "sort_period": (int(info["sort_period"]) if info else (args.sort_period or 1)) if arm != "reference" else None,
         "l2": "inputs larger than L2 (particle store >= 7.5 GB vs 129 MB L2)",
         "steps_in_config": 200,
     }
@@ -259,6 +267,7 @@ def run_ours(args):
     clocks = ClockSampler(local)
     ms, tim, clk = timed(sim, args.steps, args.warmup, clocks)
     diag = sim.diag()
+    info = sim.info()
     sim.close()
     del sim
     ms_max = max_over_ranks(ms)
@@ -279,7 +288,7 @@ def run_ours(args):
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec == "fp32" else "f64",
-           "data": "synthetic (seeded lattice + Maxwellian loader, no dataset)", "config": describe(args, n_p),
+           "data": "synthetic (seeded lattice + Maxwellian loader, no dataset)", "config": describe(args, n_p, info),
            "roofline": roof, "clocks": clk, "gpu_launches": launches,
            "stages_ms_per_step": {k: round(v[0] / max(args.steps, 1), 4) for k, v in tim.items()
                                   if k not in ("launches",)},
@@ -317,6 +326,23 @@ def run_ours(args):
 
     if rank == 0 and ws == 1 and not args.no_cpu:
         out["cpu_baseline"] = run_cpu_baseline(args, budget_s=15.0)
+    # the side measurements in one flat object at the end of the line
+    summ = {"kernel_ms": roof["k1_ms_per_launch"], "hbm_frac": roof["frac"]}
+    if "fp64_plain" in out:
+        summ["fp64_plain_pushes_per_s"] = out["fp64_plain"]["value"]
+        summ["fp32_over_fp64_plain"] = round(out["fp64_plain"]["fp32_speedup"], 2)
+    if "batch_scan" in out:
+        summ["batch_pushes_per_s"] = out["batch_scan"]["batched"]["value"]
+        summ["batch_over_one_by_one"] = round(out["batch_scan"]["speedup"], 3)
+    for k in ("wakefield_2d", "beam_wake_3d", "cylindrical_2d"):
+        if k in out:
+            summ[k + "_pushes_per_s"] = out[k]["value"]
+    if "cylindrical_2d" in out:
+        summ["rz_fp32_over_fp64"] = round(out["cylindrical_2d"]["fp32_speedup"], 2)
+    if "cpu_baseline" in out:
+        summ["oracle_pushes_per_s"] = out["cpu_baseline"]["value"]
+        summ["oracle_cores"] = out["cpu_baseline"]["cores"]
+    out["summary"] = summ
     if rank == 0:
         print(json.dumps(out), flush=True)
     if dist is not None:
@@ -542,7 +568,7 @@ def run_e2e(args, g, sps, n_p, tile, barrier, max_over_ranks, sum_over_ranks):
 
 
 # ---------------------------------------------------------------- oracle arms
-def oracle_sample(cells_target: int, ppc: int):
+def oracle_sample(cells_target: int, ppc: int, seed: int = 20004):
     """A periodic sub-box of the workload (same dx, u_th, ppc) with about
     cells_target cells."""
     import workload
@@ -552,11 +578,61 @@ def oracle_sample(cells_target: int, ppc: int):
         dims[k % 3] *= 2
         k += 1
     dims.sort(reverse=True)
-    g, sps, _ = workload.config3(ppc, seed=20004, nx=tuple(dims))
+    g, sps, _ = workload.config3(ppc, seed=seed, nx=tuple(dims))
     return g, sps, dims
 
 
+def _oracle_process(cells, ppc, seed, warmup, steps, barrier, queue):
+    """One host process of the all-core oracle run: its own periodic sub-box
+    (own seed), warm-up steps, then (after every process is ready) timed
+    steps; reports (particles, steps, start, end) in wall-clock time."""
+    sys.path.insert(0, ROOT)
+    import oracle
+    import workload
+    g, sps, dims = oracle_sample(cells, ppc, seed)
+    st = oracle.from_workload(g, sps)
+    n = workload.n_particles(g, sps[0])
+    st.step(max(warmup, 1))
+    barrier.wait()
+    t0 = time.time()
+    st.step(steps)
+    queue.put((n, steps, t0, time.time(), dims))
+
+
+def oracle_all_cores(cells, ppc, warmup, steps, nproc):
+    """The unchanged oracle on nproc host cores at once: independent processes
+    (started with spawn; no state shared with this GPU process) on disjoint
+    periodic sub-boxes.  Returns (pushes/s over the common timed span,
+    particles per process, box dims)."""
+    import multiprocessing as mp
+    import oracle
+    oracle.build()  # the processes load the built library
+    ctx = mp.get_context("spawn")
+    barrier = ctx.Barrier(nproc)
+    queue = ctx.Queue()
+    procs = [ctx.Process(target=_oracle_process, args=(cells, ppc, 20004 + 17 * k, warmup, steps, barrier, queue))
+             for k in range(nproc)]
+    for p in procs:
+        p.start()
+    res = [queue.get() for _ in procs]
+    for p in procs:
+        p.join()
+    total = sum(n * k for n, k, _, _, _ in res)
+    span = max(e for _, _, _, e, _ in res) - min(b for _, _, b, _, _ in res)
+    return total / span, res[0][0], res[0][4], span
+
+
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
 def run_cpu_baseline(args, budget_s: float):
+    """The FP64 oracle on the host: one thread on a 64x64x32 sub-box (about
+    budget_s), then every host core at once (the core count read here), each
+    on its own 32x32x32 sub-box for about budget_s."""
     import oracle
     import workload
     g, sps, dims = oracle_sample(1 << 17, args.ppc)
@@ -571,39 +647,43 @@ def run_cpu_baseline(args, budget_s: float):
         st.step(more)
     total = (time.perf_counter() - t1) + one
     steps = more + 1
-    return {"value": n * steps / total, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{dims[0]}x{dims[1]}x{dims[2]} periodic sub-box of the workload, {args.ppc} ppc "
-                      f"({n:,} electrons), {steps} full FP64 steps, single thread, {total:.1f} s"}
+    single = {"value": n * steps / total, "cores": 1,
+              "sample": f"{dims[0]}x{dims[1]}x{dims[2]} periodic sub-box, {n:,} electrons, {steps} steps, "
+                        f"{total:.1f} s"}
+    cores = host_cores()
+    # each process: a quarter of the single-thread box, steps for ~budget_s
+    per_step = one / 4.0
+    msteps = max(2, int(budget_s / max(per_step, 1e-3)))
+    val, np_, mdims, span = oracle_all_cores(1 << 15, args.ppc, 1, msteps, cores)
+    return {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{cores} host processes at once, each a {mdims[0]}x{mdims[1]}x{mdims[2]} periodic sub-box of "
+                      f"the workload at {args.ppc} ppc ({np_:,} electrons), {msteps} full FP64 steps, {span:.1f} s",
+            "single_thread": single}
 
 
 def run_reference(args):
+    """The reference arm: the FP64 oracle on every host core (independent
+    processes on disjoint periodic sub-boxes of the workload); each of the
+    K + W steps advances every sub-box one step, sized so that the run takes
+    about 150 s."""
     ws, rank, _ = dist_env()
     if rank != 0:
         return
-    import oracle
     import workload
     k, w = args.steps, args.warmup
-    # each step a bounded sample: about 150 s over the whole run at ~1.2 us per
-    # particle-step of the oracle
+    cores = host_cores()
+    # ~1.2 us per particle-step of the oracle on one core
     cells = int(150.0 / max(k + w, 1) / (args.ppc * 1.2e-6))
     cells = max(512, min(cells, 1 << 21))
-    g, sps, dims = oracle_sample(cells, args.ppc)
     g_full, sp_full, _ = make_workload(args, 0)
-    st = oracle.from_workload(g, sps)
-    n = workload.n_particles(g, sps[0])
-    if w:
-        st.step(w)
-    t0 = time.perf_counter()
-    st.step(k)
-    sec = time.perf_counter() - t0
-    value = n * k / sec
-    sample = (f"{dims[0]}x{dims[1]}x{dims[2]} periodic sub-box of the workload, {args.ppc} ppc ({n:,} electrons) "
-              f"per step, FP64 oracle, single thread")
+    value, n, dims, span = oracle_all_cores(cells, args.ppc, w, k, cores)
+    sample = (f"{cores} host processes at once, each a {dims[0]}x{dims[1]}x{dims[2]} periodic sub-box of the workload, "
+              f"{args.ppc} ppc ({n:,} electrons) per process, FP64 oracle, {w} warm-up + {k} timed steps")
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": k,
-           "warmup": w, "ms_per_step": sec / max(k, 1) * 1e3, "higher_is_better": True, "scaling": "weak",
+           "warmup": w, "ms_per_step": span / max(k, 1) * 1e3, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded lattice + Maxwellian loader)",
-           "config": describe(args, workload.n_particles(g_full, sp_full[0])),
-           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+           "config": describe(args, workload.n_particles(g_full, sp_full[0]), arm="reference"),
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 

@@ -233,20 +233,32 @@ pic_status pic_init(const pic_grid* grid, const pic_species* species, int nspeci
  * PIC_ENONFINITE if a NaN/Inf was flagged. */
 pic_status pic_step(pic_sim* sim, int nsteps);
 
-/* Copy one grid quantity (PIC_E1 .. PIC_RHO) as a dense FP64 [nz][ny][nx] array
- * into dst (dst_bytes >= 8 * cells; device pointer if dst_on_device).  J is the
+/* The grid data dumps of the thesis' diagnostics (appendix, input blocks
+ * nl_diag_emf for the full E and B data and nl_diag_phy_field for the current
+ * and the charge density), returned to the caller instead of written to files.
+ * Copy one grid quantity (PIC_E1 .. PIC_RHO) as a dense FP64 [nz][ny][nx] array
+ * into dst (dst_bytes >= 8 * cells; device pointer if dst_on_device), each
+ * component at its own staggered position (ch. 3, Yee grid).  J is the
  * (folded, smoothed) current of the last step; RHO is computed on demand from the
- * current particle positions with the linear weights, background excluded. */
+ * current particle positions with the linear weights, background excluded.
+ * Errors: PIC_EINVAL (null sim or dst, which out of range, dst_bytes too
+ * small); PIC_ECUDA.  Synchronises the stream. */
 pic_status pic_fields(pic_sim* sim, int which, void* dst, size_t dst_bytes, int dst_on_device);
 
 /* Overwrite one field component (PIC_E1 .. PIC_B3) from a dense FP64
  * [nz][ny][nx] array (device pointer if src_on_device). */
 pic_status pic_set_field(pic_sim* sim, int which, const void* src, size_t src_bytes, int src_on_device);
 
-/* Copy the particles of one species as global FP64 positions x[n][3] and
- * momenta u[n][3] (either pointer may be NULL).  cap is the row capacity of
- * the destination; *n_out receives the particle count (PIC_EOVERFLOW when it
- * exceeds cap, nothing copied).  Rows come in the library's storage order. */
+/* The particle data dumps of the thesis' diagnostics (appendix, input block
+ * nl_diag_particles: each particle's position and momentum), without the
+ * gamma filter, returned to the caller.  Copy the particles of one species as
+ * global FP64 positions x[n][3] (x in c/w_p; 2D: x[.][2] = 0; r-z: (z, r, 0))
+ * and momenta u[n][3] = p/(m_e c) (either pointer may be NULL).  cap is the
+ * row capacity of the destination; *n_out receives the particle count
+ * (PIC_EOVERFLOW when it exceeds cap, nothing copied).  Rows come in the
+ * library's storage order (pic_particle_ids gives the matching ids).
+ * Errors: PIC_EINVAL (null sim or n_out, species out of range); PIC_ECUDA.
+ * Synchronises the stream. */
 pic_status pic_particles(pic_sim* sim, int species, double* x, double* u, long long cap,
                          long long* n_out, int dst_on_device);
 
@@ -265,8 +277,16 @@ pic_status pic_particle_weights(pic_sim* S, int species, double* w, long long ca
 pic_status pic_tile_counts(pic_sim* sim, int species, long long* counts, long long cap,
                            long long* ntiles_out);
 
-/* FP64 device reductions of the Gauss-law residual, energies and charge
- * (synchronises the stream). */
+/* Global numbers of the state, reduced in FP64 on the device: the residual
+ * of Gauss's law (ch. 3, Maxwell's equations, eq. maxwell-1: div E = 4 pi rho,
+ * div E = rho in normalised units) as max |div E - rho - rho_bg| over nodes
+ * with div E from the backward differences of the staggered E; the field
+ * energy (1/2) sum (E^2 + B^2) dV; the particles' kinetic energy
+ * sum |q| |rqm| (gamma - 1); their total charge and count; the largest |rho|
+ * (net, and of the particles alone).  These condense what the thesis'
+ * diagnostics dump (appendix, nl_diag_* blocks) into the checks that the
+ * scheme conserves charge and energy.  Synchronises the stream.  Errors:
+ * PIC_EINVAL (null arguments); PIC_ECUDA. */
 pic_status pic_diag(pic_sim* sim, pic_diag_t* out);
 
 /* Per-stage device time accumulated with CUDA events on the simulation's stream
@@ -278,10 +298,17 @@ pic_status pic_diag(pic_sim* sim, pic_diag_t* out);
 pic_status pic_timing_enable(pic_sim* sim, int enable);
 pic_status pic_timing_read(pic_sim* sim, double* ms, long long* launches, int nslots, int reset);
 
-/* Release every device buffer.  NULL is accepted. */
+/* End of a run (the end of the thesis' main loop, ch. 4, high level
+ * description and flow chart): release every device buffer, stream event and
+ * table the simulation owns (through the allocator it was created with).
+ * NULL is accepted.  sim must not be used afterwards; a borrowed batch member
+ * (pic_batch_sim) must not be passed. */
 pic_status pic_destroy(pic_sim* sim);
 
-/* Message of the last failure on this thread (never NULL). */
+/* Message of the last failure on this thread (never NULL; "no error" before
+ * the first one).  The thesis' code reports failures of its input and run
+ * phases by messages; here every call returns a pic_status and leaves the
+ * message here, valid until the next failing call on the same thread. */
 const char* pic_last_error(void);
 
 /* Stateless tile binning (not in the thesis: the supporting per-tile sort;
@@ -356,7 +383,9 @@ typedef struct pic_batch pic_batch;
  * 16x8x4; 2D 32x16, 16x16, 8x8).  sort_period is forced to 1.  Device memory
  * comes from `alloc` (NULL: cudaMalloc); all work is enqueued on `stream`.
  * Errors: PIC_EINVAL for mismatched grids (message names the member),
- * PIC_ENOMEM, PIC_ECUDA, plus every error pic_init reports for a member. */
+ * PIC_EUNSUPPORTED for a member with move_window or the r-z mode (the batched
+ * step has no window shift, injection or r-z solve), PIC_ENOMEM, PIC_ECUDA,
+ * plus every error pic_init reports for a member. */
 pic_status pic_batch_init(int nsims, const pic_grid* grids, const pic_species* species, int nspecies,
                           const pic_allocator* alloc, void* stream, pic_batch** out);
 
@@ -420,7 +449,12 @@ pic_status pic_batch_autotune(int nsims, const pic_grid* grids, const pic_specie
  * its macro-charge, rqm, count and id flag followed by its particles in the
  * stored precision (FP32 form: tile index, packed cell, 3 offsets, 3 momenta,
  * ids; FP64 form: positions, momenta, ids), then the six E/B planes as stored
- * (guard cells included).  The current and charge are not stored: the next
+ * (guard cells included), then the table of pulses driven through the lower
+ * x1 boundary (pic_laser.antenna; lab-frame records).  A moving window's
+ * state travels in the effective grid (x1 origin after its shifts), the step
+ * and shift counts and each species' count of injected lattice places, so a
+ * restored window keeps shifting, injecting and driving its pulses as the
+ * uninterrupted run would.  The current and charge are not stored: the next
  * step recomputes them.  It synchronises S's stream and streams through a
  * 64 MiB host buffer.  Errors: PIC_EINVAL (bad arguments, file cannot be
  * written), PIC_ENOMEM, PIC_ECUDA.

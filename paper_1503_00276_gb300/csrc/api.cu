@@ -1902,8 +1902,15 @@ pic_status pic_batch_init(int nsims, const pic_grid* grids, const pic_species* s
   *out = nullptr;
   const int ndim = grids[0].ndim;
   for (int i = 0; i < nsims; ++i) {
-    if (grids[i].precision != PIC_FP32_CELLOFF || grids[i].ndim != ndim || grids[i].coords != PIC_COORDS_CARTESIAN) {
-      set_error("pic_batch_init: every simulation must be Cartesian, FP32 cell-offset, with the same ndim");
+    if (grids[i].coords != PIC_COORDS_CARTESIAN || grids[i].move_window) {
+      // the batched step has no window shift, injection or open x1 boundary,
+      // and no r-z field solve: such a member is refused, not mis-stepped
+      set_error("pic_batch_init: simulation " + std::to_string(i) +
+                " asks for a moving window or the r-z mode, which the batched step does not do");
+      return PIC_EUNSUPPORTED;
+    }
+    if (grids[i].precision != PIC_FP32_CELLOFF || grids[i].ndim != ndim) {
+      set_error("pic_batch_init: every simulation must be FP32 cell-offset, with the same ndim");
       return PIC_EINVAL;
     }
     for (int d = 0; d < 3; ++d)
@@ -2243,7 +2250,7 @@ pic_status pic_batch_autotune(int nsims, const pic_grid* grids, const pic_specie
 namespace {
 
 const char kCkptMagic[8] = {'P', 'I', 'C', 'G', 'B', 'C', 'K', '1'};
-constexpr uint32_t kCkptVersion = 2;
+constexpr uint32_t kCkptVersion = 3;  // 3: the antenna pulse table follows the fields
 constexpr size_t kIoChunk = size_t(64) << 20;  // host staging per copy
 
 struct CkptSpecies {
@@ -2371,6 +2378,14 @@ pic_status pic_checkpoint_save(pic_sim* S, const char* path) {
   for (int c = 0; c < 6 && ok && st == PIC_OK; ++c)
     ok = write_dev(f, static_cast<char*>(S->fld) + (size_t)c * eb * (size_t)S->L.plane, eb * (size_t)S->L.plane,
                    S->s, buf);
+  // pulses entering through the lower x1 boundary (their records are in the
+  // lab frame: start time, focal plane), so a restored moving-window run
+  // keeps driving them
+  const int nants = S->n_ants;
+  const uint32_t rb = (uint32_t)antenna_bytes();
+  put(&nants, 4);
+  put(&rb, 4);
+  if (nants > 0) put(S->h_ants.data(), (size_t)rb * (size_t)nants);
   ok = (fclose(f) == 0) && ok;
   if (st != PIC_OK) return st;
   if (!ok) {
@@ -2502,6 +2517,30 @@ pic_status pic_checkpoint_load(const char* path, const pic_allocator* alloc, voi
     }
   S->step = step;
   S->shifts = shifts;
+  int nants = 0;
+  uint32_t rb = 0;
+  if (fread(&nants, 1, 4, f) != 4 || fread(&rb, 1, 4, f) != 4 || nants < 0 || nants > (1 << 20) ||
+      (nants > 0 && rb != (uint32_t)antenna_bytes())) {
+    pic_destroy(S);
+    set_error("pic_checkpoint_load: truncated or foreign antenna table");
+    return PIC_EINVAL;
+  }
+  if (nants > 0) {
+    S->h_ants.resize((size_t)rb * (size_t)nants);
+    S->d_ants = S->al.get(S->h_ants.size());
+    S->d_inc = (float*)S->al.get(2 * sizeof(float) * (size_t)S->L.ny * (size_t)S->L.nz);
+    if (fread(S->h_ants.data(), 1, S->h_ants.size(), f) != S->h_ants.size() || !S->d_ants || !S->d_inc) {
+      pic_destroy(S);
+      set_error("pic_checkpoint_load: antenna table truncated or out of device memory");
+      return PIC_EINVAL;
+    }
+    cudaMemcpyAsync(S->d_ants, S->h_ants.data(), S->h_ants.size(), cudaMemcpyHostToDevice, S->s);
+    if (cudaStreamSynchronize(S->s) != cudaSuccess) {
+      pic_destroy(S);
+      return cuda_check("pic_checkpoint_load");
+    }
+    S->n_ants = nants;
+  }
   *out = S;
   return cuda_check("pic_checkpoint_load");
 }

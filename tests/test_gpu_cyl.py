@@ -198,7 +198,7 @@ def test_unsupported_r_z_options_are_refused(case):
     if case == "batch":
         with pytest.raises(pg.PicError) as e:
             pg.Batch([(g, sps), (g, sps)], tile=(16, 8))
-        assert e.value.code == -1
+        assert e.value.code == -8  # PIC_EUNSUPPORTED: the batched step has no r-z solve
         return
     if case == "xmin":
         g = dataclasses.replace(g, xmin=(0.0, 0.0, 0.0))

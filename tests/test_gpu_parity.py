@@ -160,6 +160,52 @@ def test_fp32_tiled_one_step_matches_oracle(case, sort_period):
     sim.close()
 
 
+# Current smoothing in the FP32 form (appendix nl_smooth: smooth_level passes
+# of (w0, w1, w2) / sum per direction): J after the smoothing of one step,
+# and the fields it drives, against the oracle's ora_smooth.  The weights are
+# the default (1, 2, 1) or, per pass, a binomial pass followed by the
+# compensator (-1, 6, -1) (a per-pass weight table).
+SMOOTH_CASES = {
+    "3d_8x8x8": ((2, 2, 2), None),
+    "3d_8x8x8_compensated": ((2, 2, 2), [(1.0, 2.0, 1.0), (-1.0, 6.0, -1.0)]),
+    "2d_32x16": ((2, 2, 0), None),
+    "3d_4x4x4_small": ((1, 2, 1), None),
+}
+
+
+@pytest.mark.parametrize("sort_period", [1, 2])
+@pytest.mark.parametrize("case", sorted(SMOOTH_CASES))
+def test_fp32_tiled_smoothing_matches_oracle(case, sort_period):
+    level, per_pass = SMOOTH_CASES[case]
+    base = case.replace("_compensated", "")
+    ndim, nx, tile, ppc, uth = CASES_32[base]
+    dx = (0.1, 0.1, 0.1)
+    sw = tuple(per_pass if per_pass else (1.0, 2.0, 1.0) for _ in range(3))
+    g = workload.Grid(ndim=ndim, nx=nx, dx=dx, dt=workload.courant_dt(dx, ndim), smooth_level=level,
+                      smooth_w=sw)
+    sp = workload.Species(ppc=ppc, uth=(uth,) * 3, seed=4242)
+    f = workload.random_fields(g, seed=19, amp=0.2)
+    ref = oracle.from_workload(g, [sp], fields=f)
+    sim = _sim(g, [sp], "fp32", fields=f, tile=tile, sort_period=sort_period)
+    ref.particle_phase()
+    raw = [c.copy() for c in ref.cur]
+    ref.smooth_current()
+    jref = [c.copy() for c in ref.cur]
+    ref.field_solve()
+    sim.step(1)
+    for c, name in enumerate(["J1", "J2", "J3"]):
+        jm = np.max(np.abs(jref[c]))
+        assert jm > 0, name
+        assert np.max(np.abs(raw[c] - jref[c])) > 0.05 * jm, name  # the smoothing is not a no-op here
+        assert np.max(np.abs(sim.fields(name) - jref[c])) < 2e-5 * jm, name
+    for c, name in enumerate(["E1", "E2", "E3", "B1", "B2", "B3"]):
+        assert np.max(np.abs(sim.fields(name) - ref.fld[c])) < 2e-5 * np.max(np.abs(ref.fld[c])), name
+    x, u = sim.particles()
+    ids = sim.ids()
+    assert _pos_err_cells(g, x, ref.x[0][ids]) < 2e-5
+    sim.close()
+
+
 @pytest.mark.parametrize("sort_period", [1, 3, 8])
 def test_fp32_tiled_many_steps_close_to_oracle(sort_period):
     ndim, nx, tile, ppc, uth = CASES_32["3d_8x8x8"]

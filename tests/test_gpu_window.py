@@ -46,10 +46,15 @@ def test_laser_setup_matches_oracle(prec, tol, wavetype, focus, ndim):
     sim.close()
 
 
-def test_moving_window_with_laser_matches_oracle():
+@pytest.mark.parametrize("smooth", [0, 2])
+def test_moving_window_with_laser_matches_oracle(smooth):
+    """20 steps of a window moving at c with a laser, FP32, against the oracle;
+    with smooth = 2 the current is smoothed by two (1, 2, 1) passes per
+    direction, which reach across the open x1 side (values beyond it read 0)."""
     import paper_1503_00276_gb300 as pg
     dx = (0.1, 0.2, 1.0)
-    g = workload.Grid(ndim=2, nx=(64, 32, 1), dx=dx, dt=workload.courant_dt(dx, 2), move_window=True)
+    g = workload.Grid(ndim=2, nx=(64, 32, 1), dx=dx, dt=workload.courant_dt(dx, 2), move_window=True,
+                      smooth_level=(smooth, smooth, 0))
     sp = workload.Species(ppc=(2, 2, 1), uth=(0.1, 0.1, 0.1), ufl=(0.3, 0.0, 0.0), seed=17)
     las = workload.Laser(vosc=0.5, rkkp=8.0, w0=2.0, rise=1.0, fall=1.0, start=1.0)
     ref = oracle.from_workload(g, [sp])

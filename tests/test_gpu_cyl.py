@@ -319,3 +319,29 @@ def test_fp32_absorption_removes_the_same_rings():
     o = np.argsort(sim.ids(0))
     assert np.max(np.abs(xs[o, 1] - ref.species[0]["x"][live_ref, 1])) <= 1e-4
     sim.close()
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_uniform_column_residual_sits_on_the_first_row_and_stays(prec):
+    """The r-z benchmark column (uniform lattice-loaded electrons, fixed ion
+    background 1, no initial E): the particles' density is -1 exactly on node
+    rows 2 .. nr-1, but -1.375 on row 1 (the fold of the mirror row below the
+    axis, whose rings all land on the first node row), so div E - rho - rho_bg
+    starts at +0.375 there and nowhere else.  The scheme conserves charge, so
+    that residual stays as it is: pic_diag's maximum after 20 steps equals the
+    initial one to 1e-5 of the particles' largest |rho| (FP32; 1e-10 FP64)."""
+    import paper_1503_00276_gb300 as pg
+    g, sps, _ = workload.config_cyl(nz=64, nr=32)
+    sim = pg.Simulation(g, sps, precision=prec)
+    r0 = _div_e_minus_rho(sim, g)
+    np.testing.assert_allclose(r0[0], 0.375, atol=1e-6)
+    assert np.max(np.abs(r0[1:])) < 1e-6
+    d0 = sim.diag()
+    assert abs(d0["gauss_resid_max"] - 0.375) < 1e-6
+    sim.step(20)
+    d1 = sim.diag()
+    tol = 1e-5 if prec == "fp32" else 1e-10
+    assert abs(d1["gauss_resid_max"] - d0["gauss_resid_max"]) <= tol * d1["rho_particles_abs_max"]
+    r1 = _div_e_minus_rho(sim, g)
+    assert np.max(np.abs(r1 - r0)) <= tol * d1["rho_particles_abs_max"]
+    sim.close()

@@ -382,10 +382,14 @@ typedef struct pic_batch pic_batch;
  * field; tile {0,0,0} picks the first shape that divides every grid (3D 8x8x8,
  * 16x8x4; 2D 32x16, 16x16, 8x8).  sort_period is forced to 1.  Device memory
  * comes from `alloc` (NULL: cudaMalloc); all work is enqueued on `stream`.
+ * Members may have a moving window (move_window, open x1, front injection,
+ * lasers and antennas added through their pic_batch_sim handles): each
+ * shifts on its own steps, exactly as pic_step would move it; such a batch is
+ * enqueued step by step instead of as a graph, because the members shift on
+ * different steps.
  * Errors: PIC_EINVAL for mismatched grids (message names the member),
- * PIC_EUNSUPPORTED for a member with move_window or the r-z mode (the batched
- * step has no window shift, injection or r-z solve), PIC_ENOMEM, PIC_ECUDA,
- * plus every error pic_init reports for a member. */
+ * PIC_EUNSUPPORTED for an r-z member (the batched step has no r-z solve),
+ * PIC_ENOMEM, PIC_ECUDA, plus every error pic_init reports for a member. */
 pic_status pic_batch_init(int nsims, const pic_grid* grids, const pic_species* species, int nspecies,
                           const pic_allocator* alloc, void* stream, pic_batch** out);
 

@@ -419,7 +419,9 @@ class Batch:
     for the particles of all members and one CUDA graph launch per step.
 
     ``members``: list of (grid, [species, ...]) with the same number of
-    species each.  ``tile``: common tile shape (None: the library's choice).
+    species each, or of (grid, [species, ...], laser) where laser is None, one
+    pulse or a list of pulses given to that member's pic_laser_add after
+    pic_batch_init.  ``tile``: common tile shape (None: the library's choice).
     """
 
     def __init__(self, members, tile=None, track_ids=False, slack=0.0, stream=None, use_torch_allocator=True,
@@ -432,7 +434,8 @@ class Batch:
         assert n >= 1 and nsp >= 1 and all(len(m[1]) == nsp for m in members)
         grids = (_capi.PicGrid * n)()
         specs = (_capi.PicSpecies * (n * nsp))()
-        for i, (g, sps) in enumerate(members):
+        for i, m in enumerate(members):
+            g, sps = m[0], m[1]
             grids[i] = _grid_struct(g, PIC_FP32_CELLOFF, tile, slack, 1, ctas_per_sm)
             for k, sp in enumerate(sps):
                 specs[i * nsp + k] = _species_struct(sp, None, track_ids)[0]
@@ -453,6 +456,12 @@ class Batch:
                                         stream_ptr, C.byref(h))
         check(code, "pic_batch_init")
         self._h = h
+        for i, m in enumerate(members):
+            lasers = m[2] if len(m) > 2 else None
+            if lasers is None:
+                continue
+            for las in (lasers if isinstance(lasers, (list, tuple)) else [lasers]):
+                self.sim(i).add_laser(las)
 
     def __len__(self):
         return len(self._members)
@@ -527,7 +536,8 @@ def batch_autotune(members, warmup=2, steps=3, slack=0.0, stream=None, use_torch
     nsp = len(members[0][1])
     grids = (_capi.PicGrid * n)()
     specs = (_capi.PicSpecies * (n * nsp))()
-    for i, (g, sps) in enumerate(members):
+    for i, m in enumerate(members):  # (grid, species[, lasers]): the candidates run without the pulses
+        g, sps = m[0], m[1]
         grids[i] = _grid_struct(g, PIC_FP32_CELLOFF, None, slack, 1)
         for k, sp in enumerate(sps):
             specs[i * nsp + k] = _species_struct(sp)[0]

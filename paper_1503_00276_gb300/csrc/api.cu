@@ -19,6 +19,16 @@ namespace picgb {
 static thread_local std::string g_err = "no error";
 void set_error(const std::string& msg) { g_err = msg; }
 
+// the counters of every (member, species) of a batch into one array, and
+// reset them (batched moving windows)
+__global__ void k_batch_gather_counts(int* const* src, int* dst, int n) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < n) {
+    dst[k] = *src[k];
+    *src[k] = 0;
+  }
+}
+
 namespace {
 
 // ------------------------------------------------------------- small kernels
@@ -1805,9 +1815,27 @@ struct pic_batch {
   cudaGraphExec_t exec[2] = {nullptr, nullptr};
   long long step = 0;
   long long nlaunch = 0;
+  // moving windows (members with move_window): the per-step shift flag of
+  // every member (host mirror pinned), and the dropped / created particle
+  // counters of every (member, species) gathered into one array per step
+  bool moving = false;
+  int* d_shift = nullptr;
+  int* h_shift = nullptr;
+  int** d_cnt_src = nullptr;  // [2 nent]: each entry's d_lost, d_kept
+  int* d_cnt = nullptr;       // [2 nent]
+  int* h_cnt = nullptr;       // pinned mirror
 };
 
 namespace {
+
+// the moving-window decision of one member for the step it is about to take
+// (the same rule as one_step: the step whose end brings c t a full cell past
+// the last shift ends with a shift; the window moves from window_start on)
+bool window_shift_due(const pic_sim* S) {
+  if (!S->moving) return false;
+  const double lag = (double)(S->step + 1) * S->g.dt - S->g.window_start;
+  return lag > 0.0 && (long long)std::floor(lag / S->g.dx[0]) > S->shifts;
+}
 
 void batch_drop_graphs(pic_batch* B) {
   for (int p = 0; p < 2; ++p)
@@ -1818,7 +1846,18 @@ void batch_drop_graphs(pic_batch* B) {
 }
 
 // Everything one step enqueues for all simulations, store side p as input.
+// One step of every member on the batch's stream.  A batch with moving
+// windows is never captured (its members shift on different steps): the shift
+// flags of the step go to the device first, then after the batched particle
+// kernel every shifting member gets its fresh front column, field solve and
+// field shift as in one_step.
 void batch_enqueue(pic_batch* B, int p) {
+  const int nsims = (int)B->sims.size();
+  std::vector<char> shift(nsims, 0);
+  if (B->moving) {
+    for (int i = 0; i < nsims; ++i) B->h_shift[i] = shift[i] = window_shift_due(B->sims[i]) ? 1 : 0;
+    cudaMemcpyAsync(B->d_shift, B->h_shift, sizeof(int) * nsims, cudaMemcpyHostToDevice, B->s);
+  }
   for (pic_sim* S : B->sims) cudaMemsetAsync(S->cur, 0, 3 * 4 * (size_t)S->L.plane, B->s);
   for (auto& e : B->ent) {
     SpeciesState& sp = B->sims[e.first]->sp[e.second];
@@ -1826,7 +1865,33 @@ void batch_enqueue(pic_batch* B, int p) {
   }
   tiled_push_batch(B->ndim, B->T, B->d_args[p], B->d_fmaps, B->d_jmaps, B->d_tile0, (int)B->ent.size(), B->d_work,
                    B->grid, B->minb, B->s);
-  for (pic_sim* S : B->sims) field_step<float>(S);
+  for (int i = 0; i < nsims; ++i) {
+    pic_sim* S = B->sims[i];
+    if (shift[i]) {  // fresh plasma for the new front column, into the output side of this step
+      B->nlaunch += (long long)S->sp.size() + 2;  // injection per species, field shift and guards below
+      for (auto& sp : S->sp) {
+        const int out = 1 - sp.cur;
+        PushConst C = make_const(S, sp);
+        const long long cnt = (long long)S->L.ny * S->L.nz * sp.ppc[0] * sp.ppc[1] * sp.ppc[2];
+        const int nxs[3] = {S->L.nx, S->L.ny, S->L.nz};
+        tiled_inject(C, sp.tg, sp.side[out], sp.spill, sp.d_spill, sp.spill_cap, &S->dstat->status, nxs, sp.ppc,
+                     sp.uth, sp.ufl, sp.seed, sp.created, cnt, sp.has_prof ? &sp.prof : nullptr, sp.d_kept, B->s);
+        sp.created += cnt;
+      }
+    }
+    field_step<float>(S);
+    if (shift[i]) {  // every field value one cell back; zero front column
+      float* eb[6];
+      for (int c = 0; c < 6; ++c) eb[c] = fld_ptr<float>(S, c);
+      shift_x<float>(S->L, eb, 6, B->s);
+      fill_guards<float>(S->L, eb, 6, B->s);
+      S->g.xmin[0] += S->g.dx[0];
+      ++S->shifts;
+    }
+  }
+  if (B->moving)
+    k_batch_gather_counts<<<(unsigned)((2 * B->ent.size() + 127) / 128), 128, 0, B->s>>>(B->d_cnt_src, B->d_cnt,
+                                                                                      (int)(2 * B->ent.size()));
 }
 
 long long batch_launches_per_step(const pic_batch* B) {
@@ -1834,8 +1899,9 @@ long long batch_launches_per_step(const pic_batch* B) {
   for (const pic_sim* S : B->sims) {
     n += 5;  // fold, B half, E, B half, fill
     for (int d = 0; d < S->ndim; ++d) n += 3 * (long long)S->g.smooth_level[d];
+    if (S->n_ants > 0) n += 1;  // the antenna plane
   }
-  return n;
+  return n + (B->moving ? 1 : 0);  // the counter gather
 }
 
 pic_status batch_build(pic_batch* B) {
@@ -1857,7 +1923,8 @@ pic_status batch_build(pic_batch* B) {
       PushConst C = make_const(S, sp);
       StatusWord* st = S->dstat;
       tiled_fill_args(args.data() + ab * k, C, sp.tg, sp.side[p], sp.side[1 - p], sp.spill, sp.d_spill,
-                      sp.spill_cap, &st->status);
+                      sp.spill_cap, &st->status, S->L.open_x, S->moving ? sp.d_lost : nullptr,
+                      S->moving ? B->d_shift + B->ent[k].first : nullptr);
       if (p == 0) {
         fme[k] = S->fmap;
         jme[k] = S->jmap;
@@ -1902,11 +1969,10 @@ pic_status pic_batch_init(int nsims, const pic_grid* grids, const pic_species* s
   *out = nullptr;
   const int ndim = grids[0].ndim;
   for (int i = 0; i < nsims; ++i) {
-    if (grids[i].coords != PIC_COORDS_CARTESIAN || grids[i].move_window) {
-      // the batched step has no window shift, injection or open x1 boundary,
-      // and no r-z field solve: such a member is refused, not mis-stepped
+    if (grids[i].coords != PIC_COORDS_CARTESIAN) {
+      // the batched step has no r-z field solve: such a member is refused, not mis-stepped
       set_error("pic_batch_init: simulation " + std::to_string(i) +
-                " asks for a moving window or the r-z mode, which the batched step does not do");
+                " asks for the r-z mode, which the batched step does not do");
       return PIC_EUNSUPPORTED;
     }
     if (grids[i].precision != PIC_FP32_CELLOFF || grids[i].ndim != ndim) {
@@ -1996,6 +2062,32 @@ pic_status pic_batch_init(int nsims, const pic_grid* grids, const pic_species* s
     set_error("pic_batch_init: pinned host allocation failed");
     return bail(PIC_ENOMEM);
   }
+  for (pic_sim* S : B->sims) B->moving = B->moving || S->moving;
+  if (B->moving) {
+    // members shift on different steps, so the step is not a fixed graph
+    B->use_graph = false;
+    B->d_shift = (int*)B->al.get(sizeof(int) * nsims);
+    B->d_cnt_src = (int**)B->al.get(sizeof(int*) * 2 * n);
+    B->d_cnt = (int*)B->al.get(sizeof(int) * 2 * n);
+    if (!B->d_shift || !B->d_cnt_src || !B->d_cnt) {
+      set_error("pic_batch_init: out of device memory (window tables)");
+      return bail(PIC_ENOMEM);
+    }
+    if (cudaMallocHost(&B->h_shift, sizeof(int) * nsims) != cudaSuccess ||
+        cudaMallocHost(&B->h_cnt, sizeof(int) * 2 * n) != cudaSuccess) {
+      set_error("pic_batch_init: pinned host allocation failed");
+      return bail(PIC_ENOMEM);
+    }
+    std::vector<int*> src(2 * (size_t)n);
+    for (int k = 0; k < n; ++k) {
+      SpeciesState& sp = B->sims[B->ent[k].first]->sp[B->ent[k].second];
+      src[2 * k] = sp.d_lost;
+      src[2 * k + 1] = sp.d_kept;
+    }
+    cudaMemcpyAsync(B->d_cnt_src, src.data(), sizeof(int*) * 2 * n, cudaMemcpyHostToDevice, B->s);
+    cudaMemsetAsync(B->d_shift, 0, sizeof(int) * nsims, B->s);
+    if (cudaStreamSynchronize(B->s) != cudaSuccess) return bail(cuda_check("pic_batch_init"));
+  }
   cudaMemsetAsync(B->d_stat, 0, sizeof(StatusWord) * nsims, B->s);
   // every member reports into the batch's status array and runs on the
   // batch's stream from now on (the members were set up on the caller's
@@ -2048,7 +2140,12 @@ pic_status pic_batch_step(pic_batch* B, int nsteps) {
     }
     ++B->step;
     cudaMemcpyAsync(B->h_stat, B->d_stat, sizeof(StatusWord) * nsims, cudaMemcpyDeviceToHost, B->s);
+    if (B->moving)
+      cudaMemcpyAsync(B->h_cnt, B->d_cnt, sizeof(int) * 2 * B->ent.size(), cudaMemcpyDeviceToHost, B->s);
     if (cudaStreamSynchronize(B->s) != cudaSuccess) return cuda_check("pic_batch_step");
+    if (B->moving)  // particles dropped through the open x1 side and created at the front
+      for (size_t k = 0; k < B->ent.size(); ++k)
+        B->sims[B->ent[k].first]->sp[B->ent[k].second].n += B->h_cnt[2 * k + 1] - B->h_cnt[2 * k];
     for (int i = 0; i < nsims; ++i) {
       pic_sim* S = B->sims[i];
       const int flags = B->h_stat[i].status;
@@ -2108,6 +2205,8 @@ pic_status pic_batch_destroy(pic_batch* B) {
   }
   B->al.release_all();
   if (B->h_stat) cudaFreeHost(B->h_stat);
+  if (B->h_shift) cudaFreeHost(B->h_shift);
+  if (B->h_cnt) cudaFreeHost(B->h_cnt);
   if (B->ev_in) cudaEventDestroy(B->ev_in);
   if (B->ev_out) cudaEventDestroy(B->ev_out);
   if (B->s) cudaStreamDestroy(B->s);

@@ -445,7 +445,10 @@ __device__ inline bool sort_tile(const TileArgs& A, const CUtensorMap* fmap, con
       nq = misc[5];
     }
     ++nch;
-    if (nq > (dense ? kQCap - kThreads : kQCap / 2)) {  // entries [0, nq) are complete since the snapshot
+    // drain when another chunk's typical crossings might not fit (fuller
+    // drains keep more of the block busy; an overflow falls back to direct
+    // deposits, so this is a cost question only)
+    if (nq > (dense ? kQCap - kThreads : kQCap - 64)) {  // entries [0, nq) are complete since the snapshot
       if (dense)
         drain_queue<NDIM, TX, TY, TZ, true>(J, A, Q, nq < kQCap ? nq : kQCap);
       else
@@ -1516,6 +1519,7 @@ TileArgs make_args(const PushConst& C, const Tiles& tg, const TileSide& in, cons
   A.nextra = nullptr;
   A.extra_cap = 0;
   A.shift_x = 0;
+  A.shift_ptr = nullptr;
   A.open_x = 0;
   A.lost = nullptr;
   A.cyl = 0;
@@ -1546,8 +1550,12 @@ int occupancy_b() {
 size_t tiled_args_bytes() { return sizeof(TileArgs); }
 
 void tiled_fill_args(void* dst, const PushConst& C, const Tiles& tg, const TileSide& in, const TileSide& out,
-                     Flat32 spill, int* spill_count, long long spill_cap, int* status) {
-  const TileArgs A = make_args(C, tg, in, out, spill, spill_count, spill_cap, nullptr, status);
+                     Flat32 spill, int* spill_count, long long spill_cap, int* status, int open_x, int* lost,
+                     const int* shift_ptr) {
+  TileArgs A = make_args(C, tg, in, out, spill, spill_count, spill_cap, nullptr, status);
+  A.open_x = open_x;
+  A.lost = lost;
+  A.shift_ptr = shift_ptr;
   memcpy(dst, &A, sizeof(A));
 }
 

@@ -189,8 +189,12 @@ void tiled_inject(const PushConst& C, const Tiles& tg, const TileSide& out, Flat
 // the entries' tile counts.  tiled_push_batch returns false for a tile shape
 // the kernel is not built for.
 size_t tiled_args_bytes();
+// open_x, lost, shift_ptr: a member with a moving window (open x1, its count
+// of dropped particles, its per-step shift flag in device memory); 0 / null
+// otherwise
 void tiled_fill_args(void* dst, const PushConst& C, const Tiles& tg, const TileSide& in, const TileSide& out,
-                     Flat32 spill, int* spill_count, long long spill_cap, int* status);
+                     Flat32 spill, int* spill_count, long long spill_cap, int* status, int open_x, int* lost,
+                     const int* shift_ptr);
 int tiled_batch_grid(int ndim, const int T[3], int total_tiles, int minb);
 bool tiled_push_batch(int ndim, const int T[3], const void* args, const CUtensorMap* fmaps, const CUtensorMap* jmaps,
                       const int* tile0, int n, int* work, int grid, int minb, cudaStream_t s);

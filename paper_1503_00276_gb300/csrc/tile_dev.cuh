@@ -33,6 +33,7 @@ struct TileArgs {
   const int* nextra;    // entries of `extra`
   int extra_cap;
   int shift_x;          // moving window: this step ends with a one-cell shift back in x1
+  const int* shift_ptr; // batched runs: the member's shift flag of this step in device memory (else null)
   int open_x;           // x1 open: a particle leaving the box in x1 is dropped
   int* lost;            // count of dropped particles
   int cyl;              // 2D r-z mode: x2 = r, rings rotated back into the r-z plane
@@ -408,17 +409,35 @@ __device__ inline void acc_flush_warp(float* J, Acc& a) {
 // Gather + push + move of one particle, deposit of its first in-cell piece into
 // the accumulator, crossing pieces queued.  Rewrites p in the coordinates of
 // the tile it ends in; returns its key: new cell (stayers) or NC + direction.
-template <int NDIM, int TX, int TY, int TZ, int QCAP = kQCap, bool CYL = false>
-__device__ inline int push_one(const float* F, float* J, const TileArgs& A, P& p, Acc& acc, float* Q, int* qn,
-                               int row0 = 0) {
+// The first half of a particle's step: gather (eq. 2d-field-weighting-e3 and
+// its 3D extension), relativistic Boris push (eq. momentum-update) and
+// position update (eq. 2d-position-update; r-z: the ring move of ch. 3), in
+// straight-line code without memory writes, so that a thread's particles can
+// be advanced side by side before any of them deposits.  A particle whose cell
+// word is corrupt is gathered at a clamped cell and flagged; the flags are
+// reported by deposit_one.
+struct Adv {
+  float ax, ay, az, bx, by, bz;  // path in cell units relative to the start cell
+  float ux, uy, uz;              // u^{n+1/2} (r-z: Cartesian at the start, before the rotation)
+  float un1, un2;                // r-z: momenta after the rotation into the new r-z plane
+  float v3;                      // out-of-plane velocity times the time share up to the wall (r-z)
+  int lx, ly, lz;
+  int bad;                       // 1: corrupt cell word, 2: non-finite result
+  bool absorbed;                 // r-z: the ring reached the wall
+};
+
+template <int NDIM, int TX, int TY, int TZ, bool CYL = false>
+__device__ inline Adv advance_one(const float* F, const TileArgs& A, const P& p, int row0 = 0) {
   using G = Geo<NDIM, TX, TY, TZ>;
-  const int lx = p.cell & 255, ly = (p.cell >> 8) & 255, lz = NDIM == 3 ? (p.cell >> 16) & 255 : 0;
-  if (lx >= TX || ly >= TY || lz >= TZ) {
-    atomicOr(A.status, ST_BADCELL);
-    p.cell = kHoleCell;
-    return G::NK;  // dropped
-  }
-  const int cellp = lx | (ly << 8) | (lz << 16);
+  Adv a;
+  int lx = p.cell & 255, ly = (p.cell >> 8) & 255, lz = NDIM == 3 ? (p.cell >> 16) & 255 : 0;
+  a.bad = (lx >= TX || ly >= TY || lz >= TZ) ? 1 : 0;
+  lx = min(lx, TX - 1);  // keeps the stencil reads inside the staged tile
+  ly = min(ly, TY - 1);
+  lz = min(lz, TZ - 1);
+  a.lx = lx;
+  a.ly = ly;
+  a.lz = lz;
   const bool hx = p.o0 < 0.5f, hy = p.o1 < 0.5f, hz = p.o2 < 0.5f;
   const int x1 = lx - hx, y1 = ly - hy, z1 = lz - hz;
   const float wx1 = hx ? p.o0 + 0.5f : p.o0 - 0.5f;
@@ -498,12 +517,46 @@ __device__ inline int push_one(const float* F, float* J, const TileArgs& A, P& p
     }
   }
   // one test for all six: a NaN or an infinity in any of them makes the sum non-finite
-  if (!isfinite(((bx + by) + bz) + ((ux + uy) + uz))) {
+  if (!isfinite(((bx + by) + bz) + ((ux + uy) + uz)) && !a.bad) a.bad = 2;
+  a.ax = ax;
+  a.ay = ay;
+  a.az = az;
+  a.bx = bx;
+  a.by = by;
+  a.bz = bz;
+  a.ux = ux;
+  a.uy = uy;
+  a.uz = uz;
+  a.un1 = un1;
+  a.un2 = un2;
+  a.v3 = uz * ig2 * tclip;  // r-z: v_theta before the rotation, for the time up to the wall
+  a.absorbed = absorbed;
+  return a;
+}
+
+// The second half: report flags, deposit the first in-cell piece of the path
+// into the accumulator and queue the rest, new cell and offset; rewrites p in
+// the coordinates of the tile it ends in and returns its key (new cell for
+// stayers, NC for leavers, NK when dropped).
+template <int NDIM, int TX, int TY, int TZ, int QCAP = kQCap, bool CYL = false>
+__device__ inline int deposit_one(float* J, const TileArgs& A, P& p, const Adv& ad, Acc& acc, float* Q, int* qn) {
+  using G = Geo<NDIM, TX, TY, TZ>;
+  const int lx = ad.lx, ly = ad.ly, lz = ad.lz;
+  const int cellp = lx | (ly << 8) | (lz << 16);
+  if (ad.bad == 1) {
+    atomicOr(A.status, ST_BADCELL);
+    p.cell = kHoleCell;
+    return G::NK;  // dropped
+  }
+  if (ad.bad == 2) {
     atomicOr(A.status, ST_NONFINITE);
     p.cell = cellp | ((uint32_t)DIR_STAY << 24);
     return lx + TX * (ly + TY * lz);  // kept in place, not advanced
   }
-  const float v3 = uz * ig2 * tclip;  // r-z: v_theta before the rotation, for the time up to the wall
+  const float ax = ad.ax, ay = ad.ay, az = ad.az, bx = ad.bx, by = ad.by, bz = ad.bz;
+  const float ux = ad.ux, uy = ad.uy, uz = ad.uz, un1 = ad.un1, un2 = ad.un2;
+  const bool absorbed = ad.absorbed;
+  const float v3 = ad.v3;
   // first in-cell piece into the accumulator; later pieces to the queue
   float tcx, tcy, tcz;
   int scx, scy, scz;
@@ -582,7 +635,7 @@ __device__ inline int push_one(const float* F, float* J, const TileArgs& A, P& p
     if (nz < 0.f) { nz += 1.f; cz = -1; } else if (nz >= 1.f) { nz -= 1.f; cz = 1; }
     if (nz >= 1.f) { nz = 0.f; cz += 1; }
   }
-  cx -= A.shift_x;  // moving window: the cell grid moves one cell forward under the particle
+  cx -= A.shift_ptr ? *A.shift_ptr : A.shift_x;  // moving window: the cell grid moves one cell forward
   int gx = lx + cx, gy = ly + cy, gz = lz + cz;
   const int dx_ = gx < 0 ? -1 : (gx >= TX ? 1 : 0);
   const int dy_ = gy < 0 ? -1 : (gy >= TY ? 1 : 0);
@@ -599,6 +652,15 @@ __device__ inline int push_one(const float* F, float* J, const TileArgs& A, P& p
   p.u1 = CYL ? un1 : uy;
   p.u2 = CYL ? un2 : uz;
   return dir == DIR_STAY ? gx + TX * (gy + TY * gz) : G::NC;
+}
+
+// Gather + push + move of one particle, deposit of its first in-cell piece into
+// the accumulator, crossing pieces queued (advance_one then deposit_one).
+template <int NDIM, int TX, int TY, int TZ, int QCAP = kQCap, bool CYL = false>
+__device__ inline int push_one(const float* F, float* J, const TileArgs& A, P& p, Acc& acc, float* Q, int* qn,
+                               int row0 = 0) {
+  const Adv a = advance_one<NDIM, TX, TY, TZ, CYL>(F, A, p, row0);
+  return deposit_one<NDIM, TX, TY, TZ, QCAP, CYL>(J, A, p, a, acc, Q, qn);
 }
 
 // Deposit the queued crossing pieces (all but the first of each path).  All

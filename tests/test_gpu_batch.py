@@ -9,7 +9,10 @@ CUDA graph launch per step.
   tolerances (2e-5 of a cell, 2e-5 (1 + |u|), grid values 2e-5 of their max);
 * re-binning: a member whose tile storage overflows is re-binned between steps
   and keeps every particle;
-* graph replay and direct launches give the same run (same tolerance as above).
+* graph replay and direct launches give the same run (same tolerance as above);
+* wakefield members (windows moving at c that shift on different steps, open
+  x1, front injection, in-box pulses and one antenna) against the same members
+  run alone and, for one member, the FP64 oracle, after 30 steps at 1e-4.
 """
 import os
 
@@ -140,3 +143,100 @@ def test_batch_graph_and_direct_launches_agree():
         _compare(a.sim(i), b.sim(i), 1e-4)
     a.close()
     b.close()
+
+
+def _wake_members():
+    """Four small wakefield members: windows moving at c from different times
+    and with different cell sizes (so they shift on different steps), warm
+    plasmas of different densities, in-box pulses of different a0 and one
+    pulse driven in through the lower x1 boundary."""
+    spec = (  # nx, dx, ppc, density, window_start, laser
+        ((128, 16, 1), (0.05, 0.2, 1.0), (2, 2, 1), 1.0, 0.0,
+         workload.Laser(vosc=1.0, rkkp=10.0, w0=1.2, rise=0.6, fall=0.6, start=1.0)),
+        ((64, 32, 1), (0.1, 0.2, 1.0), (2, 1, 1), 0.7, 0.5,
+         workload.Laser(vosc=2.0, rkkp=8.0, w0=2.0, rise=1.0, fall=1.0, start=1.0)),
+        ((96, 16, 1), (0.05, 0.2, 1.0), (1, 2, 1), 1.5, 0.3,
+         workload.Laser(vosc=0.5, rkkp=8.0, w0=1.2, rise=0.6, fall=0.6, start=0.1, antenna=True, focus=2.0)),
+        ((128, 32, 1), (0.05, 0.2, 1.0), (2, 2, 1), 0.5, 0.0,
+         workload.Laser(vosc=3.0, rkkp=10.0, w0=2.0, rise=0.8, fall=0.8, start=1.0)),
+    )
+    out = []
+    for i, (nx, dx, ppc, dens, t0, las) in enumerate(spec):
+        g = workload.Grid(ndim=2, nx=nx, dx=dx, dt=workload.courant_dt(dx, 2), rho_bg=dens, move_window=True,
+                          window_start=t0)
+        s = workload.Species(ppc=ppc, uth=(0.02, 0.02, 0.02), density=dens, seed=800 + i)
+        out.append((g, [s], las))
+    return out
+
+
+def _compare_window(a, b, dx, tol):
+    """Same surviving particles (ids), positions in cells and momenta within
+    tol; every field within tol of its maximum."""
+    ia, ib = a.ids(), b.ids()
+    assert np.array_equal(np.sort(ia), np.sort(ib))
+    (xa, ua), (xb, ub) = a.particles(), b.particles()
+    pa, pb = np.argsort(ia), np.argsort(ib)
+    L2 = a.shape[1] * dx[1]
+    d = xa[pa] - xb[pb]
+    d[:, 1] -= L2 * np.round(d[:, 1] / L2)
+    assert np.max(np.abs(d[:, 0] / dx[0])) < tol and np.max(np.abs(d[:, 1] / dx[1])) < tol
+    assert np.max(np.abs(ua[pa] - ub[pb]) / (1 + np.abs(ub[pb]))) < tol
+    for name in ("E1", "E2", "E3", "B1", "B2", "B3"):
+        fb = b.fields(name)
+        m = np.max(np.abs(fb))
+        if m > 0:
+            assert np.max(np.abs(a.fields(name) - fb)) < tol * m, name
+
+
+def test_batch_of_wakefield_members_with_windows_matches_members_alone_and_oracle():
+    """Four members with moving windows and lasers, 30 steps as one batch: each
+    member equals the same member run alone through pic_step (ids, positions,
+    momenta, fields at 1e-4; shift counts and particle counts exactly), and
+    member 0 equals the FP64 oracle at 1e-4 (FP32 against FP64 over 30 steps,
+    the tolerance of the single moving-window parity test)."""
+    import paper_1503_00276_gb300 as pg
+    mem = _wake_members()
+    n = 30
+    batch = pg.Batch(mem, track_ids=True)
+    assert batch.info()["tile"] == (32, 16, 1)
+    g0, sps0, las0 = mem[0]
+    ref = oracle.from_workload(g0, sps0)
+    for c, f in enumerate(oracle.laser_fields(g0, las0)):
+        ref.fld[c] += f
+    batch.step(n)
+    assert batch.info()["steps"] == n
+    shifts = []
+    for i, (g, sps, las) in enumerate(mem):
+        solo = pg.Simulation(g, sps, precision="fp32", tile=(32, 16), track_ids=True)
+        solo.add_laser(las)
+        solo.step(n)
+        m = batch.sim(i)
+        dm, ds = m.diag(), solo.diag()
+        assert dm["step"] == n and dm["error_flags"] & ~2 == 0
+        assert dm["n_particles"] == ds["n_particles"] == m.n_particles()
+        # one-cell shifts so far: the window moves at c from window_start on
+        shifts.append(max(0, int(np.floor((n * g.dt - g.window_start) / g.dx[0]))))
+        # fields are stored window-relative: a member shifted a different
+        # number of times would differ from its solo run by whole cells
+        _compare_window(m, solo, g.dx, 1e-4)
+        solo.close()
+    # the members shift on different steps and by different counts
+    assert len(set(shifts)) >= 3 and min(shifts) >= 10, shifts
+    ref.step(n)
+    assert ref.shifts == shifts[0]
+    m0 = batch.sim(0)
+    ids = m0.ids()
+    x, u = m0.particles()
+    assert np.array_equal(np.sort(ids), np.sort(ref.ids[0]))
+    pos = {int(i): k for k, i in enumerate(ref.ids[0])}
+    order = np.array([pos[int(i)] for i in ids])
+    d = x - ref.x[0][order]
+    L2 = g0.nx[1] * g0.dx[1]
+    d[:, 1] -= L2 * np.round(d[:, 1] / L2)
+    assert np.max(np.abs(d[:, 0] / g0.dx[0])) < 1e-4 and np.max(np.abs(d[:, 1] / g0.dx[1])) < 1e-4
+    assert np.max(np.abs(u - ref.u[0][order]) / (1 + np.abs(ref.u[0][order]))) < 1e-4
+    for c, name in enumerate(("E1", "E2", "E3", "B1", "B2", "B3")):
+        mref = np.max(np.abs(ref.fld[c]))
+        if mref > 0:
+            assert np.max(np.abs(m0.fields(name) - ref.fld[c])) < 1e-4 * mref, name
+    batch.close()

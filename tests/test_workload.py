@@ -61,17 +61,24 @@ def test_config4_scan_draws():
     sims, steps = workload.config4()
     assert len(sims) == 64 and steps == 500
     again, _ = workload.config4()
-    assert [(g.nx, s[0].ppc, s[0].density, s[0].ufl) for g, s in sims] == \
-        [(g.nx, s[0].ppc, s[0].density, s[0].ufl) for g, s in again]
-    for g, (sp,) in sims:
+    assert [(g.nx, s[0].ppc, s[0].density, las.vosc) for g, s, las in sims] == \
+        [(g.nx, s[0].ppc, s[0].density, las.vosc) for g, s, las in again]
+    for g, (sp,), las in sims:
         assert g.nx[0] in (128, 256, 512, 1024) and g.nx[1] in (64, 128, 256, 512) and g.nx[2] == 1
         assert sp.ppc_total in (4, 8, 16, 32)
-        assert 0.5 <= sp.density < 2.0 and 0.5 <= sp.ufl[1] < 3.0
-        assert g.rho_bg == sp.density  # neutral
+        assert 0.5 <= sp.density < 2.0 and 0.5 <= las.vosc < 3.0
+        assert g.rho_bg == sp.density and g.move_window  # neutral, window at c
+        assert sp.uth == (0.0, 0.0, 0.0) and sp.ufl == (0.0, 0.0, 0.0)  # cold
         assert abs(g.dt - 0.99 / math.sqrt(1 / 0.05 ** 2 + 1 / 0.2 ** 2)) < 1e-15
+        # omega0 = 10 w_p: 10 n^-1/2 of the member's own plasma frequency
+        assert las.rkkp == 10.0 and las.wavetype == 1 and not las.antenna
+        assert las.w0 <= 0.25 * g.nx[1] * g.dx[1] + 1e-12
+        # the whole pulse (front 1.0 behind the edge, rise + fall behind it) is in the box
+        assert g.nx[0] * g.dx[0] - las.start - las.rise - las.fall > 0.0
     # uneven sizes: several distinct grids and particle counts
-    assert len({g.nx for g, _ in sims}) > 8
-    assert len({workload.n_particles(g, s[0]) for g, s in sims}) > 8
+    assert len({g.nx for g, _, _ in sims}) > 8
+    assert len({workload.n_particles(g, s[0]) for g, s, _ in sims}) > 8
+    assert len({round(las.vosc, 6) for _, _, las in sims}) == 64
 
 
 def test_config1_pulse_intensity_fwhm_is_the_stated_duration():

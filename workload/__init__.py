@@ -327,19 +327,22 @@ def config3(ppc_total: int = 8, seed: int = 20004, nx=(512, 256, 256)):
 
 
 def config4(seed: int = 20005, nsims: int = 64):
-    """Batched parameter scan: ``nsims`` independent 2D3V runs of uneven size
-    drawn from the seed (500 steps each).
+    """Batched parameter scan of 2D3V laser-wakefield runs: ``nsims``
+    independent members of uneven size drawn from the seed, 500 steps each.
 
     Draw i uses counters 8i .. 8i+4 of the SplitMix64 stream ``seed``: grid
     nx1 in {128, 256, 512, 1024} x nx2 in {64, 128, 256, 512}, ppc in
-    {4, 8, 16, 32} (lattices 2x2, 4x2, 4x4, 8x4), plasma density scale
-    U[0.5, 2) and laser strength a0 U[0.5, 3); dx1 = 0.05, dx2 = 0.2,
-    dt = 0.99 of the Courant limit.  The boundary-injected laser and the moving
-    window of a wakefield run are not part of this hot path, so each run is a
-    uniform, neutralised (ion background = density scale) cold plasma whose
-    electrons start with the transverse momentum a0 in x2 -- the quiver
-    momentum the drawn laser would give them -- plus u_th = 0.01.
-    Returns a list of (Grid, [Species]) and the step count.
+    {4, 8, 16, 32} (lattices 2x2, 4x2, 4x4, 8x4), plasma density scale n
+    U[0.5, 2) in units of the density n0 that sets w_p, and laser strength a0
+    U[0.5, 3); dx1 = 0.05, dx2 = 0.2, dt = 0.99 of the Courant limit.  Each
+    member is a wakefield run like the single 2D one: cold electrons of density
+    n over a fixed ion background of the same density, filling a window that
+    moves at c in x1 (open x1, fresh plasma injected at the front), and a pulse
+    placed in the box, polarised in x2, with omega0 = 10 w_p (omega0 over the
+    member's own plasma frequency: 10 n^-1/2), the polynomial rise and fall of
+    1.945 each, front 1.0 behind the +x1 edge and spot min(4, a quarter of the
+    transverse box).
+    Returns a list of (Grid, [Species], Laser) and the step count.
     """
     lattices = {4: (2, 2, 1), 8: (4, 2, 1), 16: (4, 4, 1), 32: (8, 4, 1)}
     dx = (0.05, 0.2, 1.0)
@@ -352,10 +355,11 @@ def config4(seed: int = 20005, nsims: int = 64):
         ppc = (4, 8, 16, 32)[int(r[2] * 4)]
         dens = 0.5 + 1.5 * float(r[3])
         a0 = 0.5 + 2.5 * float(r[4])
-        g = Grid(ndim=2, nx=(nx1, nx2, 1), dx=dx, dt=dt, rho_bg=dens)
-        s = Species(rqm=-1.0, ppc=lattices[ppc], uth=(0.01, 0.01, 0.01), ufl=(0.0, a0, 0.0), density=dens,
-                    seed=seed + 1000 * (i + 1))
-        out.append((g, [s]))
+        g = Grid(ndim=2, nx=(nx1, nx2, 1), dx=dx, dt=dt, rho_bg=dens, move_window=True)
+        s = Species(rqm=-1.0, ppc=lattices[ppc], density=dens, seed=seed + 1000 * (i + 1))
+        las = Laser(vosc=a0, rkkp=10.0, w0=min(4.0, 0.25 * nx2 * dx[1]), rise=1.945, length=0.0, fall=1.945,
+                    start=1.0)
+        out.append((g, [s], las))
     return out, 500
 
 

@@ -143,7 +143,7 @@ class ClockSampler:
 
 def source_hash() -> str:
     h = hashlib.sha256()
-    for f in ("k_tiled.cu", "common.cuh", "kernels.h"):
+    for f in ("k_tiled.cu", "tile_dev.cuh", "common.cuh", "kernels.h"):
         with open(os.path.join(ROOT, "paper_1503_00276_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

@@ -361,56 +361,44 @@ __device__ inline bool sort_tile(const TileArgs& A, const CUtensorMap* fmap, con
 
   int ws = 0;
   int nch = 0;  // chunks done: picks the histogram buffer
-  // chunks over the stayers (front, 16-byte aligned) then the arrivals (back)
-  const int nchunk_s = (nstay + csz - 1) / csz;
-  const int nchunk_i = (ninc + csz - 1) / csz;
+  // chunks over the tile's particles read as one sequence, the stayers (front,
+  // 16-byte aligned) followed by the arrivals (back), so that the arrivals
+  // fill the last stayer chunk instead of taking a pass of their own
+  const int ntot = nstay + ninc;
+  const int nchunk = (ntot + csz - 1) / csz;
   const int spc = kSliceChunks * (kPPT / per);  // chunks per slice (a slice is kSliceChunks * kChunk particles)
-  const int ch_end = nslices > 1 ? min(nchunk_s + nchunk_i, (slice + 1) * spc) : nchunk_s + nchunk_i;
+  const int ch_end = nslices > 1 ? min(nchunk, (slice + 1) * spc) : nchunk;
   for (int ch = nslices > 1 ? slice * spc : 0; ch < ch_end; ++ch) {
     P pp[kPPT];
     int key[kPPT];
-    int nvalid;
-    if (ch < nchunk_s && dense) {
-      const int first = ch * csz + tid;
-      nvalid = first < nstay ? 1 : 0;
-      if (nvalid) {
-        const long long s = base + first;
-        pp[0] = P{A.in.p.cell[s], A.in.p.o[0][s], A.in.p.o[1][s], NDIM == 3 ? A.in.p.o[2][s] : 0.f,
-                  A.in.p.u[0][s], A.in.p.u[1][s], A.in.p.u[2][s], IDW && A.in.p.id ? A.in.p.id[s] : 0,
-                  IDW && A.in.p.w ? A.in.p.w[s] : 1.f};
-      }
-    } else if (ch < nchunk_s) {
-      const int first = ch * kChunk + tid * kPPT;
-      nvalid = nstay - first;
-      nvalid = nvalid < 0 ? 0 : (nvalid > kPPT ? kPPT : nvalid);
-      if (nvalid > 0) {
-        const long long s = base + first;
-        uint32_t cl[kPPT];
-        float q0[kPPT], q1[kPPT], q2[kPPT] = {}, v0[kPPT], v1[kPPT], v2[kPPT];
-        int idv[kPPT] = {};
-        float wv[kPPT];
+    const int first = ch * csz + tid * per;
+    int nvalid = ntot - first;
+    nvalid = nvalid < 0 ? 0 : (nvalid > per ? per : nvalid);
+    if (!dense && first + kPPT <= nstay) {  // a whole pair of stayers: vector loads
+      const long long s = base + first;
+      uint32_t cl[kPPT];
+      float q0[kPPT], q1[kPPT], q2[kPPT] = {}, v0[kPPT], v1[kPPT], v2[kPPT];
+      int idv[kPPT] = {};
+      float wv[kPPT];
 #pragma unroll
-        for (int r = 0; r < kPPT; ++r) wv[r] = 1.f;
-        load_vec(A.in.p.cell + s, cl);
-        load_vec(A.in.p.o[0] + s, q0);
-        load_vec(A.in.p.o[1] + s, q1);
-        if (NDIM == 3) load_vec(A.in.p.o[2] + s, q2);
-        load_vec(A.in.p.u[0] + s, v0);
-        load_vec(A.in.p.u[1] + s, v1);
-        load_vec(A.in.p.u[2] + s, v2);
-        if (IDW && A.in.p.id) load_vec(A.in.p.id + s, idv);
-        if (IDW && A.in.p.w) load_vec(A.in.p.w + s, wv);
+      for (int r = 0; r < kPPT; ++r) wv[r] = 1.f;
+      load_vec(A.in.p.cell + s, cl);
+      load_vec(A.in.p.o[0] + s, q0);
+      load_vec(A.in.p.o[1] + s, q1);
+      if (NDIM == 3) load_vec(A.in.p.o[2] + s, q2);
+      load_vec(A.in.p.u[0] + s, v0);
+      load_vec(A.in.p.u[1] + s, v1);
+      load_vec(A.in.p.u[2] + s, v2);
+      if (IDW && A.in.p.id) load_vec(A.in.p.id + s, idv);
+      if (IDW && A.in.p.w) load_vec(A.in.p.w + s, wv);
 #pragma unroll
-        for (int r = 0; r < kPPT; ++r) pp[r] = P{cl[r], q0[r], q1[r], q2[r], v0[r], v1[r], v2[r], idv[r], wv[r]};
-      }
-    } else {
-      const int first = (ch - nchunk_s) * csz + tid * per;
-      nvalid = ninc - first;
-      nvalid = nvalid < 0 ? 0 : (nvalid > per ? per : nvalid);
+      for (int r = 0; r < kPPT; ++r) pp[r] = P{cl[r], q0[r], q1[r], q2[r], v0[r], v1[r], v2[r], idv[r], wv[r]};
+    } else {  // one at a time: the last stayers, the arrivals, a dense tile
 #pragma unroll
       for (int r = 0; r < kPPT; ++r) {
         if (r < nvalid) {
-          const long long s = base + cap - ninc + first + r;
+          const int v = first + r;
+          const long long s = v < nstay ? base + v : base + cap - ninc + (v - nstay);
           pp[r] = P{A.in.p.cell[s], A.in.p.o[0][s], A.in.p.o[1][s], NDIM == 3 ? A.in.p.o[2][s] : 0.f,
                     A.in.p.u[0][s], A.in.p.u[1][s], A.in.p.u[2][s], IDW && A.in.p.id ? A.in.p.id[s] : 0,
                     IDW && A.in.p.w ? A.in.p.w[s] : 1.f};
@@ -429,7 +417,7 @@ __device__ inline bool sort_tile(const TileArgs& A, const CUtensorMap* fmap, con
       if (dense) {
         acc_flush_warp<NDIM, TX, TY, TZ>(J, acc);
       } else {
-        acc_merge_pairs<NDIM>(acc);
+        acc_merge_runs<NDIM>(acc);
         acc_flush<NDIM, TX, TY, TZ>(J, acc);
       }
     }
@@ -1613,7 +1601,7 @@ __global__ void k_slices(Tiles tg, TileSide in, int* nslice, int2* extra, int* n
   int ns = in.stay[t];
   const int room = tg.cap[t] - tg.res[t];
   ns = ns < room ? ns : room;
-  const int chunks = (ns + kChunk - 1) / kChunk + (n - ns + kChunk - 1) / kChunk;
+  const int chunks = (ns + (n - ns) + kChunk - 1) / kChunk;  // stayers and arrivals read as one sequence
   int s = (chunks + kSliceChunks - 1) / kSliceChunks;
   s = s > 1 ? s : 1;
   if (s > 1) {
@@ -1625,9 +1613,8 @@ __global__ void k_slices(Tiles tg, TileSide in, int* nslice, int2* extra, int* n
   nslice[t] = s;
 }
 
-// A tile region of c slots holds at most c / kChunk + 2 chunks (stayers and
-// arrivals are chunked apart), so it adds at most c / (kChunk kSliceChunks) +
-// 1/8 slices to the list.
+// A tile region of c slots holds at most c / kChunk + 1 chunks, so it adds at
+// most c / (kChunk kSliceChunks) + 1/8 slices to the list.
 long long slice_list_capacity(long long slots, int ntiles) {
   return slots / (kChunk * kSliceChunks) + ntiles / 4 + 64;
 }

@@ -372,29 +372,27 @@ __device__ inline void flush_warp(float* J, bool act, int cell, const float (&w)
   }
 }
 
-// Before the end-of-chunk flush (all lanes of the warp call it): the lanes hold
-// runs in cell order, so neighbouring lanes often end on the same cell (at 8
-// particles per cell and 2 per thread, about four lanes per cell), and their
-// shared-memory adds would all hit the same 12 words.  Aligned pairs, then
-// aligned quads, of lanes on one cell are summed into the lower lane; the
-// upper one is emptied.
+// Lanes hold runs of equal cells (stayers arrive sorted by cell): each lane's
+// accumulator is summed into the first lane of its run (segmented suffix sums
+// in log steps, as many as the longest run needs); the other lanes are emptied.
 template <int NDIM>
-__device__ inline void acc_merge_pairs(Acc& a) {
+__device__ inline void acc_merge_runs(Acc& a) {
   constexpr unsigned kFull = 0xffffffffu;
   const int lane = threadIdx.x & 31;
-#pragma unroll
-  for (int s = 1; s <= 2; s <<= 1) {
-    const int up = __shfl_down_sync(kFull, a.cell, s);    // cell of lane + s
-    const int down = __shfl_up_sync(kFull, a.cell, s);    // cell of lane - s
-    const bool take = (lane & (2 * s - 1)) == 0 && a.cell >= 0 && up == a.cell;
-    const bool give = (lane & (2 * s - 1)) == s && a.cell >= 0 && down == a.cell;
+  const int up1 = __shfl_down_sync(kFull, a.cell, 1);
+  const int dn1 = __shfl_up_sync(kFull, a.cell, 1);
+  const unsigned ends = __ballot_sync(kFull, lane == 31 || a.cell < 0 || up1 != a.cell);
+  const int e = __ffs(ends & (kFull << lane)) - 1;  // last lane of my run
+  const bool head = lane == 0 || a.cell < 0 || dn1 != a.cell;
+  const int maxlen = (int)__reduce_max_sync(kFull, head ? (unsigned)(e - lane + 1) : 1u);
+  for (int s = 1; s < maxlen; s <<= 1) {
 #pragma unroll
     for (int k = 0; k < (NDIM == 3 ? 12 : 8); ++k) {
       const float v = __shfl_down_sync(kFull, a.w[k], s);
-      if (take) a.w[k] += v;
+      if (lane + s <= e) a.w[k] += v;
     }
-    if (give) a.cell = -1;
   }
+  if (!head) a.cell = -1;
 }
 
 // acc_flush for a whole warp (all lanes call it)

@@ -472,10 +472,11 @@ def run_beam_wake(args, max_over_ranks):
 def run_batch_scan(args, max_over_ranks):
     """The batched parameter scan: 64 independent 2D3V wakefield runs of uneven
     size (81.7M electrons in all; windows moving at c, in-box pulses of a0 0.5-3
-    at omega0 = 10 w_p), advanced as one batch (one tile-kernel launch per step
-    for every member's particles) versus one by one through pic_step.  Both read
-    the device status back after every step.  Each arm takes 3 untimed steps,
-    then --scan-steps timed ones."""
+    at omega0 = 10 w_p), advanced as one batch (one CUDA graph per step: one
+    tile-kernel launch for every member's particles and one launch per field
+    stage for all members) versus one by one through pic_step.  Both read the
+    device status back after every step.  Each arm takes 3 untimed steps, then
+    --scan-steps timed ones."""
     import torch
 
     import paper_1503_00276_gb300 as pg

@@ -372,8 +372,11 @@ pic_status pic_bin_tiles_noalloc(const int nx[3], const int tile[3], long long n
  * Boris push, move and Villasenor-Buneman deposit of section 2.2, current fold,
  * smoothing and Yee solve of section 2.1), but the particle step of all members
  * is ONE launch of the persistent sorting tile kernel, whose work items are the
- * tiles of all members, and the whole step of the batch is one CUDA graph
- * launch (captured once per store side; re-captured after a member re-bins).
+ * tiles of all members, each stage of the field step (current fold, the two
+ * B half steps and the E step, guard cells, window shift) is one launch over
+ * all members, and the whole step of the batch is one CUDA graph launch
+ * (captured once per store side; re-captured after a member re-bins or gains
+ * an antenna pulse).
  */
 typedef struct pic_batch pic_batch;
 
@@ -384,9 +387,11 @@ typedef struct pic_batch pic_batch;
  * comes from `alloc` (NULL: cudaMalloc); all work is enqueued on `stream`.
  * Members may have a moving window (move_window, open x1, front injection,
  * lasers and antennas added through their pic_batch_sim handles): each
- * shifts on its own steps, exactly as pic_step would move it; such a batch is
- * enqueued step by step instead of as a graph, because the members shift on
- * different steps.
+ * shifts on its own steps, exactly as pic_step would move it.  The values that
+ * change from step to step (shift flags, window corners, antenna times, first
+ * indices of fresh particles) are written on the host before each step into a
+ * pinned block that the step's first node copies to the device, so the same
+ * graph serves every step.
  * Errors: PIC_EINVAL for mismatched grids (message names the member),
  * PIC_EUNSUPPORTED for an r-z member (the batched step has no r-z solve),
  * PIC_ENOMEM, PIC_ECUDA, plus every error pic_init reports for a member. */

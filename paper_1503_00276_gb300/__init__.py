@@ -416,7 +416,8 @@ class _Member(Simulation):
 class Batch:
     """Many independent FP32 cell-offset simulations advanced together
     (pic_batch_init ... pic_batch_destroy): one persistent tile-kernel launch
-    for the particles of all members and one CUDA graph launch per step.
+    for the particles of all members, one launch per field stage for all
+    members, and one CUDA graph launch per step.
 
     ``members``: list of (grid, [species, ...]) with the same number of
     species each, or of (grid, [species, ...], laser) where laser is None, one

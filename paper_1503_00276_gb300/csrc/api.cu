@@ -1815,15 +1815,35 @@ struct pic_batch {
   cudaGraphExec_t exec[2] = {nullptr, nullptr};
   long long step = 0;
   long long nlaunch = 0;
-  // moving windows (members with move_window): the per-step shift flag of
-  // every member (host mirror pinned), and the dropped / created particle
-  // counters of every (member, species) gathered into one array per step
+  // moving windows (members with move_window): the dropped / created
+  // particle counters of every (member, species) gathered into one array per
+  // step
   bool moving = false;
-  int* d_shift = nullptr;
-  int* h_shift = nullptr;
   int** d_cnt_src = nullptr;  // [2 nent]: each entry's d_lost, d_kept
   int* d_cnt = nullptr;       // [2 nent]
   int* h_cnt = nullptr;       // pinned mirror
+  // the field step of all members, one launch per stage
+  BatchFieldTable ft{};
+  BatchFieldMember* d_fm = nullptr;
+  int* d_blk = nullptr;  // first blocks per member: interior, guard, shift-row launches ([nsims + 1] each)
+  int nblk_int = 0, nblk_guard = 0, nblk_rows = 0;
+  BatchZeroSeg* d_zseg[2] = {nullptr, nullptr};  // per input side: every current, every arrival counter
+  int* d_zblk[2] = {nullptr, nullptr};
+  int nzseg = 0;
+  int nzblk[2] = {0, 0};
+  void* d_ispec = nullptr;  // front-column injection records (moving windows)
+  int* d_iblk = nullptr;
+  int ninj_blk = 0;
+  // values of the next step read on the device (so that a captured step can
+  // be replayed): shift flag per member, the window's x1 corner after its
+  // shift per member, antenna time and x1 corner per member, first fresh
+  // particle index per entry; filled on the host before each step
+  unsigned char* h_dyn = nullptr;  // pinned
+  unsigned char* d_dyn = nullptr;
+  size_t dyn_bytes = 0, off_xinj = 0, off_ant = 0, off_first = 0;
+  long long ants_built = -1;  // antenna pulses of all members when the step was built
+  int* shift_flags() const { return reinterpret_cast<int*>(d_dyn); }
+  int* h_shift_flags() const { return reinterpret_cast<int*>(h_dyn); }
 };
 
 namespace {
@@ -1845,63 +1865,95 @@ void batch_drop_graphs(pic_batch* B) {
     }
 }
 
-// Everything one step enqueues for all simulations, store side p as input.
-// One step of every member on the batch's stream.  A batch with moving
-// windows is never captured (its members shift on different steps): the shift
-// flags of the step go to the device first, then after the batched particle
-// kernel every shifting member gets its fresh front column, field solve and
-// field shift as in one_step.
+long long batch_antennas(const pic_batch* B) {
+  long long n = 0;
+  for (const pic_sim* S : B->sims) n += S->n_ants;
+  return n;
+}
+
+// The next step's per-member values into the pinned block (read on the
+// device after the step's first copy): the moving-window decision as in
+// one_step, the window corner the fresh column is created at, the antenna time
+// and corner, and every entry's first fresh particle index.
+void batch_prepare(pic_batch* B) {
+  const int nsims = (int)B->sims.size();
+  int* shift = B->h_shift_flags();
+  double* xinj = reinterpret_cast<double*>(B->h_dyn + B->off_xinj);
+  double* ant = reinterpret_cast<double*>(B->h_dyn + B->off_ant);
+  long long* first = reinterpret_cast<long long*>(B->h_dyn + B->off_first);
+  for (int i = 0; i < nsims; ++i) {
+    const pic_sim* S = B->sims[i];
+    shift[i] = window_shift_due(S) ? 1 : 0;
+    xinj[i] = S->g.xmin[0] + S->g.dx[0];
+    ant[2 * i] = ((double)S->step + 0.5) * S->g.dt;
+    ant[2 * i + 1] = S->g.xmin[0];
+  }
+  for (size_t k = 0; k < B->ent.size(); ++k) first[k] = B->sims[B->ent[k].first]->sp[B->ent[k].second].created;
+}
+
+// The host's record of the step just taken: members that shifted moved their
+// window and used up their lattice places of the front column.
+void batch_after_step(pic_batch* B) {
+  const int* shift = B->h_shift_flags();
+  for (int i = 0; i < (int)B->sims.size(); ++i) {
+    if (!shift[i]) continue;
+    pic_sim* S = B->sims[i];
+    for (auto& sp : S->sp) sp.created += (long long)S->L.ny * S->L.nz * sp.ppc[0] * sp.ppc[1] * sp.ppc[2];
+    S->g.xmin[0] += S->g.dx[0];
+    ++S->shifts;
+  }
+}
+
+// Everything one step enqueues for all simulations, store side p as input:
+// the step's values to the device, then one launch per stage for all members
+// (currents and arrival counters cleared, the batched tile kernel, fresh front
+// columns, current fold, B half step, E step, B half step, window shift,
+// guards), per-member launches only for smoothing passes and antenna planes.
+// It reads nothing from the host after the first copy, so it can be captured.
 void batch_enqueue(pic_batch* B, int p) {
   const int nsims = (int)B->sims.size();
-  std::vector<char> shift(nsims, 0);
-  if (B->moving) {
-    for (int i = 0; i < nsims; ++i) B->h_shift[i] = shift[i] = window_shift_due(B->sims[i]) ? 1 : 0;
-    cudaMemcpyAsync(B->d_shift, B->h_shift, sizeof(int) * nsims, cudaMemcpyHostToDevice, B->s);
-  }
-  for (pic_sim* S : B->sims) cudaMemsetAsync(S->cur, 0, 3 * 4 * (size_t)S->L.plane, B->s);
-  for (auto& e : B->ent) {
-    SpeciesState& sp = B->sims[e.first]->sp[e.second];
-    cudaMemsetAsync(sp.side[1 - p].inc, 0, 4 * (size_t)sp.tg.ntiles, B->s);
-  }
-  tiled_push_batch(B->ndim, B->T, B->d_args[p], B->d_fmaps, B->d_jmaps, B->d_tile0, (int)B->ent.size(), B->d_work,
-                   B->grid, B->minb, B->s);
+  const int nent = (int)B->ent.size();
+  cudaMemcpyAsync(B->d_dyn, B->h_dyn, B->dyn_bytes, cudaMemcpyHostToDevice, B->s);
+  batch_zero(B->d_zseg[p], B->d_zblk[p], B->nzseg, B->nzblk[p], B->s);
+  tiled_push_batch(B->ndim, B->T, B->d_args[p], B->d_fmaps, B->d_jmaps, B->d_tile0, nent, B->d_work, B->grid,
+                   B->minb, B->s);
+  if (B->moving)
+    tiled_inject_batch(B->d_args[p], B->d_ispec, B->d_iblk, nent, B->ninj_blk, B->shift_flags(),
+                       reinterpret_cast<const double*>(B->d_dyn + B->off_xinj),
+                       reinterpret_cast<const long long*>(B->d_dyn + B->off_first), B->s);
+  batch_fold(B->ft, B->nblk_guard, B->s);
+  for (pic_sim* S : B->sims)  // smoothing passes, as field_step
+    for (int d = 0; d < S->ndim; ++d)
+      for (int pass = 0; pass < S->g.smooth_level[d]; ++pass) {
+        const double* w = S->g.smooth_w[d][pass];
+        for (int c = 0; c < 3; ++c)
+          smooth_pass<float>(S->L, cur_ptr<float>(S, c), reinterpret_cast<float*>(S->tmp), d, w[0], w[1], w[2],
+                             B->s);
+      }
+  batch_yee_b(B->ft, B->nblk_int, B->s);
   for (int i = 0; i < nsims; ++i) {
     pic_sim* S = B->sims[i];
-    if (shift[i]) {  // fresh plasma for the new front column, into the output side of this step
-      B->nlaunch += (long long)S->sp.size() + 2;  // injection per species, field shift and guards below
-      for (auto& sp : S->sp) {
-        const int out = 1 - sp.cur;
-        PushConst C = make_const(S, sp);
-        const long long cnt = (long long)S->L.ny * S->L.nz * sp.ppc[0] * sp.ppc[1] * sp.ppc[2];
-        const int nxs[3] = {S->L.nx, S->L.ny, S->L.nz};
-        tiled_inject(C, sp.tg, sp.side[out], sp.spill, sp.d_spill, sp.spill_cap, &S->dstat->status, nxs, sp.ppc,
-                     sp.uth, sp.ufl, sp.seed, sp.created, cnt, sp.has_prof ? &sp.prof : nullptr, sp.d_kept, B->s);
-        sp.created += cnt;
-      }
-    }
-    field_step<float>(S);
-    if (shift[i]) {  // every field value one cell back; zero front column
-      float* eb[6];
-      for (int c = 0; c < 6; ++c) eb[c] = fld_ptr<float>(S, c);
-      shift_x<float>(S->L, eb, 6, B->s);
-      fill_guards<float>(S->L, eb, 6, B->s);
-      S->g.xmin[0] += S->g.dx[0];
-      ++S->shifts;
-    }
+    if (S->n_ants > 0)
+      antenna_plane(S->L, S->d_ants, S->n_ants, 0.0, 0.0, S->d_inc, B->s,
+                    reinterpret_cast<const double*>(B->d_dyn + B->off_ant) + 2 * i);
   }
+  batch_yee_e(B->ft, B->nblk_int, B->s);
+  batch_yee_b(B->ft, B->nblk_int, B->s);
+  if (B->moving) batch_shift(B->ft, B->nblk_rows, B->s);
+  batch_fill(B->ft, B->nblk_guard, B->s);
   if (B->moving)
-    k_batch_gather_counts<<<(unsigned)((2 * B->ent.size() + 127) / 128), 128, 0, B->s>>>(B->d_cnt_src, B->d_cnt,
-                                                                                      (int)(2 * B->ent.size()));
+    k_batch_gather_counts<<<(unsigned)((2 * nent + 127) / 128), 128, 0, B->s>>>(B->d_cnt_src, B->d_cnt, 2 * nent);
 }
 
 long long batch_launches_per_step(const pic_batch* B) {
-  long long n = 1;
+  long long n = 6;  // clear, tile kernel, fold, B half, E, B half
+  n += B->nblk_guard > 0 ? 1 : 0;  // guards
+  if (B->moving) n += (B->ninj_blk > 0 ? 1 : 0) + 2;  // fresh columns, shift, counter gather
   for (const pic_sim* S : B->sims) {
-    n += 5;  // fold, B half, E, B half, fill
     for (int d = 0; d < S->ndim; ++d) n += 3 * (long long)S->g.smooth_level[d];
     if (S->n_ants > 0) n += 1;  // the antenna plane
   }
-  return n + (B->moving ? 1 : 0);  // the counter gather
+  return n;
 }
 
 pic_status batch_build(pic_batch* B) {
@@ -1924,7 +1976,7 @@ pic_status batch_build(pic_batch* B) {
       StatusWord* st = S->dstat;
       tiled_fill_args(args.data() + ab * k, C, sp.tg, sp.side[p], sp.side[1 - p], sp.spill, sp.d_spill,
                       sp.spill_cap, &st->status, S->L.open_x, S->moving ? sp.d_lost : nullptr,
-                      S->moving ? B->d_shift + B->ent[k].first : nullptr);
+                      S->moving ? B->shift_flags() + B->ent[k].first : nullptr);
       if (p == 0) {
         fme[k] = S->fmap;
         jme[k] = S->jmap;
@@ -1941,6 +1993,78 @@ pic_status batch_build(pic_batch* B) {
     set_error("pic_batch: tile shape not supported by the batched kernel");
     return PIC_EUNSUPPORTED;
   }
+  // the batched field step: one record and the first blocks per member
+  const int nsims = (int)B->sims.size();
+  std::vector<BatchFieldMember> fmem(nsims);
+  std::vector<int> blk(3 * (size_t)(nsims + 1), 0);
+  int* bi = blk.data();
+  int* bg = bi + nsims + 1;
+  int* br = bg + nsims + 1;
+  for (int i = 0; i < nsims; ++i) {
+    pic_sim* S = B->sims[i];
+    BatchFieldMember& m = fmem[i];
+    m.L = S->L;
+    for (int c = 0; c < 6; ++c) m.f[c] = fld_ptr<float>(S, c);
+    for (int c = 0; c < 3; ++c) m.j[c] = cur_ptr<float>(S, c);
+    const double dx3 = S->ndim == 3 ? S->g.dx[2] : 1.0;  // the constants yee_b_half / yee_e pass
+    m.h = (float)(S->g.dt / 2.0);
+    m.dt = (float)S->g.dt;
+    m.i1 = (float)(1.0 / S->g.dx[0]);
+    m.i2 = (float)(1.0 / S->g.dx[1]);
+    m.i3 = (float)(1.0 / dx3);
+    m.inc = S->n_ants > 0 ? S->d_inc : nullptr;
+    bi[i + 1] = bi[i] + batch_interior_blocks(S->L);
+    bg[i + 1] = bg[i] + batch_guard_blocks(S->L);
+    br[i + 1] = br[i] + batch_row_blocks(S->L);
+  }
+  B->nblk_int = bi[nsims];
+  B->nblk_guard = bg[nsims];
+  B->nblk_rows = br[nsims];
+  cudaMemcpyAsync(B->d_fm, fmem.data(), sizeof(BatchFieldMember) * nsims, cudaMemcpyHostToDevice, B->s);
+  cudaMemcpyAsync(B->d_blk, blk.data(), sizeof(int) * blk.size(), cudaMemcpyHostToDevice, B->s);
+  B->ft.m = B->d_fm;
+  B->ft.blk_int = B->d_blk;
+  B->ft.blk_guard = B->d_blk + nsims + 1;
+  B->ft.blk_rows = B->d_blk + 2 * (nsims + 1);
+  B->ft.shift = B->shift_flags();
+  B->ft.n = nsims;
+  // what each step clears, per input side: the currents, then the arrival
+  // counters of the output side
+  std::vector<BatchZeroSeg> zs(B->nzseg);
+  std::vector<int> zb(B->nzseg + 1);
+  for (int p = 0; p < 2; ++p) {
+    for (int i = 0; i < nsims; ++i) zs[i] = BatchZeroSeg{B->sims[i]->cur, 3 * (long long)B->sims[i]->L.plane};
+    for (int k = 0; k < n; ++k) {
+      SpeciesState& sp = B->sims[B->ent[k].first]->sp[B->ent[k].second];
+      zs[nsims + k] = BatchZeroSeg{sp.side[1 - p].inc, (long long)sp.tg.ntiles};
+    }
+    zb[0] = 0;
+    for (int q = 0; q < B->nzseg; ++q) zb[q + 1] = zb[q] + batch_zero_blocks(zs[q].words);
+    B->nzblk[p] = zb[B->nzseg];
+    cudaMemcpyAsync(B->d_zseg[p], zs.data(), sizeof(BatchZeroSeg) * zs.size(), cudaMemcpyHostToDevice, B->s);
+    cudaMemcpyAsync(B->d_zblk[p], zb.data(), sizeof(int) * zb.size(), cudaMemcpyHostToDevice, B->s);
+    if (cudaStreamSynchronize(B->s) != cudaSuccess) return cuda_check("pic_batch tables");  // zs reused
+  }
+  // the fresh front column of every entry of a moving member
+  if (B->moving) {
+    const size_t rb = tiled_inject_spec_bytes();
+    std::vector<unsigned char> rec(rb * n);
+    std::vector<int> ib(n + 1, 0);
+    for (int k = 0; k < n; ++k) {
+      pic_sim* S = B->sims[B->ent[k].first];
+      SpeciesState& sp = S->sp[B->ent[k].second];
+      const long long cnt = S->moving ? (long long)S->L.ny * S->L.nz * sp.ppc[0] * sp.ppc[1] * sp.ppc[2] : 0;
+      const int nxs[3] = {S->L.nx, S->L.ny, S->L.nz};
+      tiled_fill_inject(rec.data() + rb * k, make_const(S, sp), sp.tg, nxs, sp.ppc, sp.uth, sp.ufl, sp.seed,
+                        sp.has_prof ? &sp.prof : nullptr, sp.d_kept, B->ent[k].first, cnt);
+      ib[k + 1] = ib[k] + (int)((cnt + 255) / 256);
+    }
+    B->ninj_blk = ib[n];
+    cudaMemcpyAsync(B->d_ispec, rec.data(), rec.size(), cudaMemcpyHostToDevice, B->s);
+    cudaMemcpyAsync(B->d_iblk, ib.data(), sizeof(int) * ib.size(), cudaMemcpyHostToDevice, B->s);
+    if (cudaStreamSynchronize(B->s) != cudaSuccess) return cuda_check("pic_batch tables");
+  }
+  B->ants_built = batch_antennas(B);
   if (cudaStreamSynchronize(B->s) != cudaSuccess) return cuda_check("pic_batch tables");
   if (B->use_graph) {
     for (int p = 0; p < 2; ++p) {
@@ -2063,21 +2187,39 @@ pic_status pic_batch_init(int nsims, const pic_grid* grids, const pic_species* s
     return bail(PIC_ENOMEM);
   }
   for (pic_sim* S : B->sims) B->moving = B->moving || S->moving;
+  // batched field step tables and the per-step block (pinned mirror)
+  B->nzseg = nsims + n;
+  B->off_xinj = ((sizeof(int) * nsims + 7) / 8) * 8;
+  B->off_ant = B->off_xinj + sizeof(double) * nsims;
+  B->off_first = B->off_ant + 2 * sizeof(double) * nsims;
+  B->dyn_bytes = B->off_first + sizeof(long long) * n;
+  B->d_fm = (BatchFieldMember*)B->al.get(sizeof(BatchFieldMember) * nsims);
+  B->d_blk = (int*)B->al.get(sizeof(int) * 3 * (nsims + 1));
+  B->d_dyn = (unsigned char*)B->al.get(B->dyn_bytes);
+  bool ok = B->d_fm && B->d_blk && B->d_dyn;
+  for (int p = 0; p < 2; ++p) {
+    B->d_zseg[p] = (BatchZeroSeg*)B->al.get(sizeof(BatchZeroSeg) * B->nzseg);
+    B->d_zblk[p] = (int*)B->al.get(sizeof(int) * (B->nzseg + 1));
+    ok = ok && B->d_zseg[p] && B->d_zblk[p];
+  }
   if (B->moving) {
-    // members shift on different steps, so the step is not a fixed graph
-    B->use_graph = false;
-    B->d_shift = (int*)B->al.get(sizeof(int) * nsims);
+    B->d_ispec = B->al.get(tiled_inject_spec_bytes() * n);
+    B->d_iblk = (int*)B->al.get(sizeof(int) * (n + 1));
     B->d_cnt_src = (int**)B->al.get(sizeof(int*) * 2 * n);
     B->d_cnt = (int*)B->al.get(sizeof(int) * 2 * n);
-    if (!B->d_shift || !B->d_cnt_src || !B->d_cnt) {
-      set_error("pic_batch_init: out of device memory (window tables)");
-      return bail(PIC_ENOMEM);
-    }
-    if (cudaMallocHost(&B->h_shift, sizeof(int) * nsims) != cudaSuccess ||
-        cudaMallocHost(&B->h_cnt, sizeof(int) * 2 * n) != cudaSuccess) {
-      set_error("pic_batch_init: pinned host allocation failed");
-      return bail(PIC_ENOMEM);
-    }
+    ok = ok && B->d_ispec && B->d_iblk && B->d_cnt_src && B->d_cnt;
+  }
+  if (!ok) {
+    set_error("pic_batch_init: out of device memory (field and window tables)");
+    return bail(PIC_ENOMEM);
+  }
+  if (cudaMallocHost(&B->h_dyn, B->dyn_bytes) != cudaSuccess ||
+      (B->moving && cudaMallocHost(&B->h_cnt, sizeof(int) * 2 * n) != cudaSuccess)) {
+    set_error("pic_batch_init: pinned host allocation failed");
+    return bail(PIC_ENOMEM);
+  }
+  memset(B->h_dyn, 0, B->dyn_bytes);
+  if (B->moving) {
     std::vector<int*> src(2 * (size_t)n);
     for (int k = 0; k < n; ++k) {
       SpeciesState& sp = B->sims[B->ent[k].first]->sp[B->ent[k].second];
@@ -2085,7 +2227,6 @@ pic_status pic_batch_init(int nsims, const pic_grid* grids, const pic_species* s
       src[2 * k + 1] = sp.d_kept;
     }
     cudaMemcpyAsync(B->d_cnt_src, src.data(), sizeof(int*) * 2 * n, cudaMemcpyHostToDevice, B->s);
-    cudaMemsetAsync(B->d_shift, 0, sizeof(int) * nsims, B->s);
     if (cudaStreamSynchronize(B->s) != cudaSuccess) return bail(cuda_check("pic_batch_init"));
   }
   cudaMemsetAsync(B->d_stat, 0, sizeof(StatusWord) * nsims, B->s);
@@ -2123,11 +2264,12 @@ pic_status pic_batch_step(pic_batch* B, int nsteps) {
     }
   } join{B};
   for (int k = 0; k < nsteps; ++k) {
-    if (B->dirty) {
+    if (B->dirty || batch_antennas(B) != B->ants_built) {  // re-bin, or a pulse added through a member
       const pic_status st = batch_build(B);
       if (st != PIC_OK) return st;
     }
     const int p = B->sims[0]->sp[0].cur;
+    batch_prepare(B);  // the previous step has completed: the block is free
     if (B->use_graph) {
       if (cudaGraphLaunch(B->exec[p], B->s) != cudaSuccess) return cuda_check("pic_batch_step graph launch");
     } else {
@@ -2143,6 +2285,7 @@ pic_status pic_batch_step(pic_batch* B, int nsteps) {
     if (B->moving)
       cudaMemcpyAsync(B->h_cnt, B->d_cnt, sizeof(int) * 2 * B->ent.size(), cudaMemcpyDeviceToHost, B->s);
     if (cudaStreamSynchronize(B->s) != cudaSuccess) return cuda_check("pic_batch_step");
+    batch_after_step(B);
     if (B->moving)  // particles dropped through the open x1 side and created at the front
       for (size_t k = 0; k < B->ent.size(); ++k)
         B->sims[B->ent[k].first]->sp[B->ent[k].second].n += B->h_cnt[2 * k + 1] - B->h_cnt[2 * k];
@@ -2205,7 +2348,7 @@ pic_status pic_batch_destroy(pic_batch* B) {
   }
   B->al.release_all();
   if (B->h_stat) cudaFreeHost(B->h_stat);
-  if (B->h_shift) cudaFreeHost(B->h_shift);
+  if (B->h_dyn) cudaFreeHost(B->h_dyn);
   if (B->h_cnt) cudaFreeHost(B->h_cnt);
   if (B->ev_in) cudaEventDestroy(B->ev_in);
   if (B->ev_out) cudaEventDestroy(B->ev_out);

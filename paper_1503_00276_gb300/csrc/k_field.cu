@@ -82,8 +82,7 @@ struct PtrN {
 };
 
 template <typename T>
-__global__ void k_fill_guards(Layout L, PtrN<T, 6> P, int ncomp) {
-  const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+__device__ inline void fill_guard_at(const Layout& L, const PtrN<T, 6>& P, int ncomp, long long g) {
   int X, Y, Z;
   if (!guard_xyz(L, g, X, Y, Z)) return;
   const int i = X - L.gx, j = Y - L.gy, k = Z - L.gz;
@@ -96,13 +95,17 @@ __global__ void k_fill_guards(Layout L, PtrN<T, 6> P, int ncomp) {
   for (int c = 0; c < ncomp; ++c) P.c[c][dst] = P.c[c][src];
 }
 
+template <typename T>
+__global__ void k_fill_guards(Layout L, PtrN<T, 6> P, int ncomp) {
+  fill_guard_at<T>(L, P, ncomp, (long long)blockIdx.x * blockDim.x + threadIdx.x);
+}
+
 // Periodic boundary for the current: what the deposit put into a guard cell
 // belongs to the interior cell at the wrapped index (the node "communicates
 // with its own opposite boundary").  Several guard cells can map to one
 // interior cell (edges, corners), hence the atomics.
 template <typename T>
-__global__ void k_fold_guards(Layout L, PtrN<T, 6> P, int ncomp) {
-  const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+__device__ inline void fold_guard_at(const Layout& L, const PtrN<T, 6>& P, int ncomp, long long g) {
   int X, Y, Z;
   if (!guard_xyz(L, g, X, Y, Z)) return;
   const int i = X - L.gx, j = Y - L.gy, k = Z - L.gz;
@@ -114,6 +117,11 @@ __global__ void k_fold_guards(Layout L, PtrN<T, 6> P, int ncomp) {
     if (v != T(0) && !drop) atomicAdd(&P.c[c][dst], v);
     P.c[c][src] = T(0);
   }
+}
+
+template <typename T>
+__global__ void k_fold_guards(Layout L, PtrN<T, 6> P, int ncomp) {
+  fold_guard_at<T>(L, P, ncomp, (long long)blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 // ---------------------------------------------------------------- smoothing
@@ -199,10 +207,8 @@ __global__ void k_yee_e(Layout L, Ptr3<T> E, Ptr3<T> B, Ptr3<T> J, T dt, T dx1, 
 // FP32 forms of the two sweeps (the FP32 cell-offset path): multiplication by
 // 1/dx and explicit fused multiply-adds.  The FP64 sweeps above keep the
 // oracle's operation order (divisions, no contraction) for the FP64 parity.
-__global__ void k_yee_b_half_f32(Layout L, Ptr3<float> E, Ptr3<float> B, float h, float i1, float i2, float i3) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = blockIdx.y * blockDim.y + threadIdx.y;
-  const int k = blockIdx.z;
+__device__ inline void yee_b_f32_at(const Layout& L, const Ptr3<float>& E, const Ptr3<float>& B, float h, float i1,
+                                    float i2, float i3, int i, int j, int k) {
   if (i >= L.nx || j >= L.ny) return;
   const long long c = L.idx(i, j, k);
   const long long cx = c + (i + 1 == L.nx ? 1 - L.nx : 1);
@@ -227,11 +233,13 @@ __global__ void k_yee_b_half_f32(Layout L, Ptr3<float> E, Ptr3<float> B, float h
   B.c[2][c] = fmaf(-h, dE2d1 - dE1d2, B.c[2][c]);
 }
 
-__global__ void k_yee_e_f32(Layout L, Ptr3<float> E, Ptr3<float> B, Ptr3<float> J, float dt, float i1, float i2,
-                            float i3, const float* inc) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = blockIdx.y * blockDim.y + threadIdx.y;
-  const int k = blockIdx.z;
+__global__ void k_yee_b_half_f32(Layout L, Ptr3<float> E, Ptr3<float> B, float h, float i1, float i2, float i3) {
+  yee_b_f32_at(L, E, B, h, i1, i2, i3, blockIdx.x * blockDim.x + threadIdx.x, blockIdx.y * blockDim.y + threadIdx.y,
+               blockIdx.z);
+}
+
+__device__ inline void yee_e_f32_at(const Layout& L, const Ptr3<float>& E, const Ptr3<float>& B, const Ptr3<float>& J,
+                                    float dt, float i1, float i2, float i3, const float* inc, int i, int j, int k) {
   if (i >= L.nx || j >= L.ny) return;
   const long long c = L.idx(i, j, k);
   const long long cx = c - (i == 0 ? 1 - L.nx : 1);
@@ -260,13 +268,18 @@ __global__ void k_yee_e_f32(Layout L, Ptr3<float> E, Ptr3<float> B, Ptr3<float> 
   E.c[2][c] = fmaf(dt, dB2d1 - dB1d2 - __ldg(J.c[2] + c), E.c[2][c]);
 }
 
+__global__ void k_yee_e_f32(Layout L, Ptr3<float> E, Ptr3<float> B, Ptr3<float> J, float dt, float i1, float i2,
+                            float i3, const float* inc) {
+  yee_e_f32_at(L, E, B, J, dt, i1, i2, i3, inc, blockIdx.x * blockDim.x + threadIdx.x,
+               blockIdx.y * blockDim.y + threadIdx.y, blockIdx.z);
+}
+
 // Moving window: every field value one cell back in x1 (value at i <- value
 // at i + 1), zero in the new front column.  One warp per row; a row is read
 // ahead of where it is written.
 template <typename T>
-__global__ void k_shift_x(Layout L, PtrN<T, 6> P, int ncomp) {
+__device__ inline void shift_row(const Layout& L, const PtrN<T, 6>& P, int ncomp, long long row) {
   const int lane = threadIdx.x & 31;
-  const long long row = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const long long rows = (long long)ncomp * L.ny * L.nz;
   if (row >= rows) return;
   const int c = (int)(row / ((long long)L.ny * L.nz));
@@ -280,6 +293,11 @@ __global__ void k_shift_x(Layout L, PtrN<T, 6> P, int ncomp) {
     if (i < L.nx) f[i] = v;
     __syncwarp();
   }
+}
+
+template <typename T>
+__global__ void k_shift_x(Layout L, PtrN<T, 6> P, int ncomp) {
+  shift_row<T>(L, P, ncomp, (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5));
 }
 
 // Laser pulse added to the fields, each component at its staggered position.
@@ -597,10 +615,15 @@ void shift_x(const Layout& L, T* const* comps, int ncomp, cudaStream_t s) {
 // B2 and B3 of the antenna pulses just below the lower x1 boundary (x1 =
 // xlo1 - dx1/2) at time t, summed into inc[2][ny nz]: each pulse's front is
 // at xlo1 + (t - start); B3 = E2, B2 = -E3 of laser_amp at the B positions.
-__global__ void k_antenna_plane(Layout L, const LaserDev* P, int n, double t, double xlo1, float* inc) {
+__global__ void k_antenna_plane(Layout L, const LaserDev* P, int n, double t, double xlo1, const double* txlo,
+                                float* inc) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   const int k = blockIdx.y;
   if (j >= L.ny) return;
+  if (txlo) {  // read on the device (a step replayed from a graph)
+    t = txlo[0];
+    xlo1 = txlo[1];
+  }
   const double h3 = L.ndim == 3 ? 0.5 : 0.0;
   double b2 = 0.0, b3 = 0.0;
   for (int a = 0; a < n; ++a) {
@@ -648,9 +671,10 @@ void antenna_store(const double* p, void* dst) {
   std::memcpy(dst, &P, sizeof(P));
 }
 
-void antenna_plane(const Layout& L, const void* ants, int n, double t, double xlo1, float* inc, cudaStream_t s) {
+void antenna_plane(const Layout& L, const void* ants, int n, double t, double xlo1, float* inc, cudaStream_t s,
+                   const double* txlo) {
   k_antenna_plane<<<dim3((L.ny + 127) / 128, L.nz), 128, 0, s>>>(L, static_cast<const LaserDev*>(ants), n, t, xlo1,
-                                                                 inc);
+                                                                 txlo, inc);
 }
 
 template <typename T>
@@ -725,6 +749,108 @@ void unpack_interior(const Layout& L, const double* src, T* comp, cudaStream_t s
 template <typename T>
 void init_e_gauss_x1(const Layout& L, const double* rho, double rho_bg, double dx1, T* e1, cudaStream_t s) {
   k_gauss_x1<T><<<dim3((L.ny + 127) / 128, L.nz), 128, 0, s>>>(L, rho, rho_bg, dx1, e1);
+}
+
+// ------------------------------------------------------- batched field step
+// Every stage of the FP32 field step of many simulations in one launch: block
+// b belongs to the member m with blk[m] <= b < blk[m + 1] and runs the same
+// per-element code as the single-simulation kernels on its block of member m.
+__device__ inline int batch_member(const int* blk, int n, int b) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (__ldg(blk + mid) <= b)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo;
+}
+
+// interior blocks of 32 x 8 cells (one x3 plane), as interior_grid
+__device__ inline void batch_cell(const Layout& L, int lb, int& i, int& j, int& k) {
+  const int gx = (L.nx + 31) / 32, gy = (L.ny + 7) / 8;
+  const int bx = lb % gx, by = (lb / gx) % gy;
+  k = lb / (gx * gy);
+  i = bx * 32 + (threadIdx.x & 31);
+  j = by * 8 + (threadIdx.x >> 5);
+}
+
+__global__ void k_batch_zero(const BatchZeroSeg* seg, const int* blk, int n) {
+  const int m = batch_member(blk, n, blockIdx.x);
+  const BatchZeroSeg z = seg[m];
+  const long long w0 = ((long long)(blockIdx.x - blk[m]) * blockDim.x + threadIdx.x) * 4;
+  uint32_t* p = static_cast<uint32_t*>(z.p);
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+    if (w0 + q < z.words) p[w0 + q] = 0u;
+}
+
+__global__ void k_batch_fold(BatchFieldTable T) {
+  const int m = batch_member(T.blk_guard, T.n, blockIdx.x);
+  const BatchFieldMember& M = T.m[m];
+  PtrN<float, 6> P{};
+  for (int c = 0; c < 3; ++c) P.c[c] = M.j[c];
+  fold_guard_at<float>(M.L, P, 3, (long long)(blockIdx.x - T.blk_guard[m]) * blockDim.x + threadIdx.x);
+}
+
+__global__ void k_batch_fill(BatchFieldTable T) {
+  const int m = batch_member(T.blk_guard, T.n, blockIdx.x);
+  const BatchFieldMember& M = T.m[m];
+  PtrN<float, 6> P{};
+  for (int c = 0; c < 6; ++c) P.c[c] = M.f[c];
+  fill_guard_at<float>(M.L, P, 6, (long long)(blockIdx.x - T.blk_guard[m]) * blockDim.x + threadIdx.x);
+}
+
+__global__ void k_batch_yee_b(BatchFieldTable T) {
+  const int m = batch_member(T.blk_int, T.n, blockIdx.x);
+  const BatchFieldMember& M = T.m[m];
+  int i, j, k;
+  batch_cell(M.L, blockIdx.x - T.blk_int[m], i, j, k);
+  const Ptr3<float> E{{M.f[0], M.f[1], M.f[2]}}, B{{M.f[3], M.f[4], M.f[5]}};
+  yee_b_f32_at(M.L, E, B, M.h, M.i1, M.i2, M.i3, i, j, k);
+}
+
+__global__ void k_batch_yee_e(BatchFieldTable T) {
+  const int m = batch_member(T.blk_int, T.n, blockIdx.x);
+  const BatchFieldMember& M = T.m[m];
+  int i, j, k;
+  batch_cell(M.L, blockIdx.x - T.blk_int[m], i, j, k);
+  const Ptr3<float> E{{M.f[0], M.f[1], M.f[2]}}, B{{M.f[3], M.f[4], M.f[5]}}, J{{M.j[0], M.j[1], M.j[2]}};
+  yee_e_f32_at(M.L, E, B, J, M.dt, M.i1, M.i2, M.i3, M.inc, i, j, k);
+}
+
+__global__ void k_batch_shift(BatchFieldTable T) {
+  const int m = batch_member(T.blk_rows, T.n, blockIdx.x);
+  if (!T.shift[m]) return;  // this member does not move this step
+  const BatchFieldMember& M = T.m[m];
+  PtrN<float, 6> P{};
+  for (int c = 0; c < 6; ++c) P.c[c] = M.f[c];
+  shift_row<float>(M.L, P, 6, (long long)(blockIdx.x - T.blk_rows[m]) * (blockDim.x >> 5) + (threadIdx.x >> 5));
+}
+
+int batch_interior_blocks(const Layout& L) { return ((L.nx + 31) / 32) * ((L.ny + 7) / 8) * L.nz; }
+int batch_guard_blocks(const Layout& L) { return (int)((guard_count(L) + 255) / 256); }
+int batch_row_blocks(const Layout& L) { return (int)((6LL * L.ny * L.nz + 7) / 8); }
+int batch_zero_blocks(long long words) { return (int)((words + 1023) / 1024); }
+
+void batch_zero(const BatchZeroSeg* seg, const int* blk, int n, int nblk, cudaStream_t s) {
+  if (nblk > 0) k_batch_zero<<<nblk, 256, 0, s>>>(seg, blk, n);
+}
+void batch_fold(const BatchFieldTable& T, int nblk, cudaStream_t s) {
+  if (nblk > 0) k_batch_fold<<<nblk, 256, 0, s>>>(T);
+}
+void batch_fill(const BatchFieldTable& T, int nblk, cudaStream_t s) {
+  if (nblk > 0) k_batch_fill<<<nblk, 256, 0, s>>>(T);
+}
+void batch_yee_b(const BatchFieldTable& T, int nblk, cudaStream_t s) {
+  if (nblk > 0) k_batch_yee_b<<<nblk, 256, 0, s>>>(T);
+}
+void batch_yee_e(const BatchFieldTable& T, int nblk, cudaStream_t s) {
+  if (nblk > 0) k_batch_yee_e<<<nblk, 256, 0, s>>>(T);
+}
+void batch_shift(const BatchFieldTable& T, int nblk, cudaStream_t s) {
+  if (nblk > 0) k_batch_shift<<<nblk, 256, 0, s>>>(T);
 }
 
 #define PICGB_INST(T)                                                                                         \

@@ -1289,23 +1289,25 @@ struct InjectSpec {
   int* kept;             // particles created
 };
 
-__global__ void k_inject(TileArgs A, Tiles tg, InjectSpec J, long long count) {
-  const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= count) return;
+// Fresh particle k of the front column: first = global index of particle 0
+// (the lattice places created so far), xlo0 = the window's lower x1 corner
+// after its shift.
+__device__ inline void inject_one(const TileArgs& A, const int* T, const int* nt, const InjectSpec& J,
+                                  long long first, double xlo0, long long k) {
   const int ppc = J.ppc[0] * J.ppc[1] * J.ppc[2];
   const long long col = k / ppc;
   const int sub = (int)(k - col * ppc);
   const int cj = (int)(col % J.nx[1]), ck = (int)(col / J.nx[1]);
   const int si = sub % J.ppc[0], sj = (sub / J.ppc[0]) % J.ppc[1], sk = sub / (J.ppc[0] * J.ppc[1]);
-  const int ix = tg.nt[0] - 1, iy = cj / tg.T[1], iz = J.ndim == 3 ? ck / tg.T[2] : 0;
-  const int t = (iz * tg.nt[1] + iy) * tg.nt[0] + ix;
-  const int lx = J.nx[0] - 1 - ix * tg.T[0], ly = cj - iy * tg.T[1], lz = J.ndim == 3 ? ck - iz * tg.T[2] : 0;
+  const int ix = nt[0] - 1, iy = cj / T[1], iz = J.ndim == 3 ? ck / T[2] : 0;
+  const int t = (iz * nt[1] + iy) * nt[0] + ix;
+  const int lx = J.nx[0] - 1 - ix * T[0], ly = cj - iy * T[1], lz = J.ndim == 3 ? ck - iz * T[2] : 0;
   P q;
   q.cell = (uint32_t)lx | ((uint32_t)ly << 8) | ((uint32_t)lz << 16) | ((uint32_t)DIR_STAY << 24);
   q.o0 = (float)((si + 0.5) / J.ppc[0]);
   q.o1 = (float)((sj + 0.5) / J.ppc[1]);
   q.o2 = J.ndim == 3 ? (float)((sk + 0.5) / J.ppc[2]) : 0.f;
-  const unsigned long long g = (unsigned long long)(J.first + k);
+  const unsigned long long g = (unsigned long long)(first + k);
   float uu[3];
   for (int d = 0; d < 3; ++d)
     uu[d] = (float)(J.uth[d] != 0.0 ? J.ufl[d] + J.uth[d] * normal_dev(J.seed, 3ull * g + d) : J.ufl[d]);
@@ -1315,7 +1317,7 @@ __global__ void k_inject(TileArgs A, Tiles tg, InjectSpec J, long long count) {
   q.id = (int)g;
   q.w = 1.f;
   if (J.has_prof) {  // the profile at the particle's lab-frame position
-    const double x[3] = {J.xlo[0] + (J.nx[0] - 1 + (si + 0.5) / J.ppc[0]) * J.dx[0],
+    const double x[3] = {xlo0 + (J.nx[0] - 1 + (si + 0.5) / J.ppc[0]) * J.dx[0],
                          J.xlo[1] + (cj + (sj + 0.5) / J.ppc[1]) * J.dx[1],
                          J.ndim == 3 ? J.xlo[2] + (ck + (sk + 0.5) / J.ppc[2]) * J.dx[2] : 0.0};
     const double w = profile_weight(J.prof, x);
@@ -1333,6 +1335,38 @@ __global__ void k_inject(TileArgs A, Tiles tg, InjectSpec J, long long count) {
   } else {
     spill_put(A, t, q);
   }
+}
+
+__global__ void k_inject(TileArgs A, Tiles tg, InjectSpec J, long long count) {
+  const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < count) inject_one(A, tg.T, tg.nt, J, J.first, J.xlo[0], k);
+}
+
+// Batched form: entry e (a member and species) owns blocks [blk[e],
+// blk[e + 1]); a member that does not shift this step creates nothing.  The
+// per-step values (shift flag, window corner, first index) are read from
+// device memory, so the launch can be replayed from a graph.
+struct InjectBatchSpec {
+  InjectSpec J;
+  int T[3], nt[3];
+  int member;
+  long long count;
+};
+
+__global__ void k_inject_batch(const TileArgs* args, const InjectBatchSpec* spec, const int* blk, int n,
+                               const int* shift, const double* xlo0, const long long* first) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (blk[mid] <= (int)blockIdx.x)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  const InjectBatchSpec& S = spec[lo];
+  if (!shift[S.member]) return;
+  const long long k = (long long)(blockIdx.x - blk[lo]) * blockDim.x + threadIdx.x;
+  if (k < S.count) inject_one(args[lo], S.T, S.nt, S.J, first[lo], xlo0[S.member], k);
 }
 
 template <int NDIM, int TX, int TY, int TZ, int MINB, bool SORT = true, bool CYL = false, bool IDW = true>
@@ -1698,6 +1732,39 @@ void tiled_inject(const PushConst& C, const Tiles& tg, const TileSide& out, Flat
   if (prof) J.prof = *prof;
   J.kept = kept;
   k_inject<<<(unsigned)((count + 255) / 256), 256, 0, s>>>(A, tg, J, count);
+}
+
+size_t tiled_inject_spec_bytes() { return sizeof(InjectBatchSpec); }
+
+void tiled_fill_inject(void* dst, const PushConst& C, const Tiles& tg, const int nx[3], const int ppc[3],
+                       const double uth[3], const double ufl[3], unsigned long long seed, const ProfileDev* prof,
+                       int* kept, int member, long long count) {
+  InjectBatchSpec S{};
+  S.J.ndim = tg.ndim;
+  for (int d = 0; d < 3; ++d) {
+    S.J.nx[d] = nx[d];
+    S.J.ppc[d] = ppc[d];
+    S.J.uth[d] = uth[d];
+    S.J.ufl[d] = ufl[d];
+    S.J.xlo[d] = C.xmin[d];  // x1 is replaced by the step's value
+    S.J.dx[d] = C.dx[d];
+    S.T[d] = tg.T[d];
+    S.nt[d] = tg.nt[d];
+  }
+  S.J.seed = seed;
+  S.J.has_prof = prof != nullptr;
+  if (prof) S.J.prof = *prof;
+  S.J.kept = kept;
+  S.member = member;
+  S.count = count;
+  memcpy(dst, &S, sizeof(S));
+}
+
+void tiled_inject_batch(const void* args, const void* specs, const int* blk, int n, int nblk, const int* shift,
+                        const double* xlo0, const long long* first, cudaStream_t s) {
+  if (nblk > 0)
+    k_inject_batch<<<nblk, 256, 0, s>>>(static_cast<const TileArgs*>(args),
+                                        static_cast<const InjectBatchSpec*>(specs), blk, n, shift, xlo0, first);
 }
 
 void tiled_flatten(const Tiles& tg, const TileSide& in, const long long* out_off, Flat32 out, cudaStream_t s) {

@@ -43,7 +43,9 @@ template <typename T> void laser_add(const Layout& L, T* const* f, const double*
 // just below the lower x1 boundary at lab position xlo1 and time t into inc
 size_t antenna_bytes();
 void antenna_store(const double* p, void* dst);
-void antenna_plane(const Layout& L, const void* ants, int n, double t, double xlo1, float* inc, cudaStream_t s);
+// txlo non-null: t and xlo1 are read from txlo[0], txlo[1] on the device
+void antenna_plane(const Layout& L, const void* ants, int n, double t, double xlo1, float* inc, cudaStream_t s,
+                   const double* txlo = nullptr);
 template <typename T>
 void gauss_residual(const Layout& L, T* const* e, const double* rho, double rho_bg, const double dx[3], Diag64* acc,
                     cudaStream_t s);
@@ -52,6 +54,39 @@ template <typename T> void unpack_interior(const Layout& L, const double* src, T
 // E1 from the discrete Gauss law along x1, column by column (rho padded FP64).
 template <typename T> void init_e_gauss_x1(const Layout& L, const double* rho, double rho_bg, double dx1, T* e1,
                                            cudaStream_t s);
+
+// Batched FP32 field step (pic_batch): one launch per stage for all members.
+// Each table lists, per member, the first block of that member in the launch
+// (blk_*[n] = the total); the block counts per member are batch_*_blocks.
+struct BatchFieldMember {
+  Layout L;
+  float* f[6];            // E1..E3, B1..B3
+  float* j[3];
+  float h, dt, i1, i2, i3;  // dt / 2, dt and 1 / dx, as the single-simulation sweeps take them
+  const float* inc;       // antenna B plane below the lower x1 boundary, or null
+};
+struct BatchFieldTable {
+  const BatchFieldMember* m;
+  const int* blk_int;     // interior sweeps: blocks of 32 x 8 cells
+  const int* blk_guard;   // guard fill / fold: 256 guard cells per block
+  const int* blk_rows;    // window shift: 8 rows per block
+  const int* shift;       // [n] this step's shift flags (device)
+  int n;
+};
+struct BatchZeroSeg {     // words to clear: 4 per thread, 1024 per block
+  void* p;
+  long long words;
+};
+int batch_interior_blocks(const Layout& L);
+int batch_guard_blocks(const Layout& L);
+int batch_row_blocks(const Layout& L);
+int batch_zero_blocks(long long words);
+void batch_zero(const BatchZeroSeg* seg, const int* blk, int n, int nblk, cudaStream_t s);
+void batch_fold(const BatchFieldTable& T, int nblk, cudaStream_t s);
+void batch_fill(const BatchFieldTable& T, int nblk, cudaStream_t s);
+void batch_yee_b(const BatchFieldTable& T, int nblk, cudaStream_t s);
+void batch_yee_e(const BatchFieldTable& T, int nblk, cudaStream_t s);
+void batch_shift(const BatchFieldTable& T, int nblk, cudaStream_t s);
 
 // ----------------------------------------------------------------- particles
 struct PushConst {        // per-species constants of one step
@@ -196,6 +231,19 @@ void tiled_fill_args(void* dst, const PushConst& C, const Tiles& tg, const TileS
                      Flat32 spill, int* spill_count, long long spill_cap, int* status, int open_x, int* lost,
                      const int* shift_ptr);
 int tiled_batch_grid(int ndim, const int T[3], int total_tiles, int minb);
+// Batched front-column injection (moving windows): one record per table entry
+// (tiled_inject_spec_bytes bytes, written by tiled_fill_inject with the entry's
+// member index and lattice count); entry e owns blocks [blk[e], blk[e + 1]) of
+// 256 particles.  Per step, read on the device: shift[member], xlo0[member]
+// (the window's lower x1 corner after the shift) and first[e] (global index of
+// the entry's first fresh particle).  args: the entries' tile-kernel records
+// of the step (their output side receives the particles).
+size_t tiled_inject_spec_bytes();
+void tiled_fill_inject(void* dst, const PushConst& C, const Tiles& tg, const int nx[3], const int ppc[3],
+                       const double uth[3], const double ufl[3], unsigned long long seed, const ProfileDev* prof,
+                       int* kept, int member, long long count);
+void tiled_inject_batch(const void* args, const void* specs, const int* blk, int n, int nblk, const int* shift,
+                        const double* xlo0, const long long* first, cudaStream_t s);
 bool tiled_push_batch(int ndim, const int T[3], const void* args, const CUtensorMap* fmaps, const CUtensorMap* jmaps,
                       const int* tile0, int n, int* work, int grid, int minb, cudaStream_t s);
 void tiled_live(const Tiles& tg, const TileSide& in, int* live, cudaStream_t s);

@@ -62,8 +62,9 @@ def parse():
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-fp64", action="store_true")
     p.add_argument("--fp64-steps", type=int, default=3)
-    p.add_argument("--scan-steps", type=int, default=20,
-                   help="timed steps of the batched-scan comparison (64 runs, batched vs one by one)")
+    p.add_argument("--scan-steps", type=int, default=500,
+                   help="timed steps of the batched-scan comparison (64 wakefield runs, batched vs one by one; "
+                        "the scan's own length is 500)")
     p.add_argument("--no-scan", action="store_true")
     p.add_argument("--wake-steps", type=int, default=200,
                    help="timed steps of the 2D laser-wakefield workload (moving window)")

@@ -1107,10 +1107,11 @@ __global__ void k_global_to_flat(int ndim, Layout L, Tiles tg, PushConst C, cons
 
 // Charge density of one tile's particles (one block per tile).  Every stored
 // particle's cell is local to its tile, so its weights land on the tile's
-// (T+1)^d nodes.  A warp takes kRhoWarp consecutive slots, copied coalesced
-// into shared memory by cp.async; each lane then takes kRhoRun consecutive ones
-// (cell-sorted runs after the last sort) and sums the weights of consecutive
-// same-cell particles in registers (FP32).  Each run goes into a shared node
+// (T+1)^d nodes.  A warp takes kRhoWarp consecutive slots; each lane takes
+// kRhoRun consecutive ones (cell-sorted runs after the last sort), read as two
+// groups of four with one 128-bit load per array (four stayers: regions are
+// 16-byte aligned) or one by one (the last stayers, the arrivals), and sums
+// the weights of consecutive same-cell particles in registers (FP32).  Each run goes into a shared node
 // tile of 64-bit fixed-point sums in units of 2^-32, so the node sums do not
 // depend on the order of the adds (a node's sum must stay below 2^31 particle
 // weights).  The sums are kept as two 32-bit words added by 32-bit atomics: the
@@ -1124,13 +1125,10 @@ __global__ void k_global_to_flat(int ndim, Layout L, Tiles tg, PushConst C, cons
 constexpr int kRhoRun = 8;
 constexpr int kRhoWarp = 32 * kRhoRun;
 constexpr int kRhoThreads = 128;
-constexpr int kRhoPad = kRhoWarp + kRhoWarp / 32;  // one padding word per 32: conflict-free strided reads
 
 template <bool KIN>
 __global__ void __launch_bounds__(kRhoThreads) k_tiled_rho(Layout L, PushConst C, Tiles tg, TileSide in, double* rho,
                                                            Diag64* acc) {
-  constexpr int NA = KIN ? 8 : 5;  // staged arrays: cell, o1..o3, w[, u1..u3]
-  __shared__ float stg[kRhoThreads / 32][NA][kRhoPad];
   // node sums, fixed point in units of 2^-32: low words Rlo[nr], high words Rhi[nr]
   extern __shared__ unsigned int Rlo[];
   const int t = blockIdx.x;
@@ -1153,32 +1151,7 @@ __global__ void __launch_bounds__(kRhoThreads) k_tiled_rho(Layout L, PushConst C
   tile_origin(tg, t, o);
   __syncthreads();
   double kin = 0.0, live = 0.0;
-  float(*S)[kRhoPad] = stg[warp];
   for (int k0 = warp * kRhoWarp; k0 < n; k0 += (kRhoThreads / 32) * kRhoWarp) {
-    // coalesced: slot k0 + 32 m + lane into word p + p / 32 of each array,
-    // copied straight to shared memory so that all of them are in flight
-#pragma unroll
-    for (int m = 0; m < kRhoRun; ++m) {
-      const int p = 32 * m + lane, k = k0 + p, w = p + m;
-      if (k < n) {
-        const long long s = k < ns ? base + k : back + k;
-        cp_async4(&S[0][w], &in.p.cell[s]);
-        cp_async4(&S[1][w], &in.p.o[0][s]);
-        cp_async4(&S[2][w], &in.p.o[1][s]);
-        if (d3) cp_async4(&S[3][w], &in.p.o[2][s]);
-        if (has_w) cp_async4(&S[4][w], &in.p.w[s]);
-        if constexpr (KIN) {
-          cp_async4(&S[5][w], &in.p.u[0][s]);
-          cp_async4(&S[6][w], &in.p.u[1][s]);
-          cp_async4(&S[7][w], &in.p.u[2][s]);
-        }
-      } else {
-        S[0][w] = __uint_as_float(kHoleCell);
-      }
-    }
-    cp_async_commit();
-    cp_async_wait0();
-    __syncwarp();
     float accw[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     float kp = 0.f, lp = 0.f;  // this run's kinetic energy and charge
     int cur = -1;
@@ -1199,40 +1172,76 @@ __global__ void __launch_bounds__(kRhoThreads) k_tiled_rho(Layout L, PushConst C
           }
     };
 #pragma unroll
-    for (int j = 0; j < kRhoRun; ++j) {
-      const int p = kRhoRun * lane + j, w = p + p / 32;
-      const uint32_t cw = __float_as_uint(S[0][w]);
-      if (cw == kHoleCell) continue;
-      const int cell = (int)(cw & 0x00FFFFFFu);
-      if (cell != cur) {
-        if (cur >= 0) flush();
-        cur = cell;
-#pragma unroll
-        for (int q = 0; q < 8; ++q) accw[q] = 0.f;
-      }
-      const float e0 = S[1][w], e1 = S[2][w], e2 = d3 ? S[3][w] : 0.f, pw = has_w ? S[4][w] : 1.f;
-      if constexpr (KIN) {
-        const float ua = S[5][w], ub = S[6][w], uc = S[7][w];
-        const float u2 = fmaf(ua, ua, fmaf(ub, ub, uc * uc));
-        kp = fmaf(pw, u2 / (1.f + sqrtf(1.f + u2)), kp);
-        lp += pw;
-      }
-      const float f1[2] = {1.f - e0, e0}, f2[2] = {1.f - e1, e1}, f3[2] = {1.f - e2, e2};
-#pragma unroll
-      for (int c3 = 0; c3 < 2; ++c3)
-#pragma unroll
-        for (int c2 = 0; c2 < 2; ++c2) {
-          const float w23 = f2[c2] * (d3 ? f3[c3] : 1.f) * pw;
-#pragma unroll
-          for (int c1 = 0; c1 < 2; ++c1) accw[c3 * 4 + c2 * 2 + c1] = fmaf(f1[c1], w23, accw[c3 * 4 + c2 * 2 + c1]);
+    for (int h = 0; h < kRhoRun / 4; ++h) {
+      const int kb = k0 + kRhoRun * lane + 4 * h;  // this lane's next four slots
+      uint32_t cw[4];
+      float e0[4], e1[4], e2[4] = {0.f, 0.f, 0.f, 0.f}, pw[4] = {1.f, 1.f, 1.f, 1.f};
+      float ua[4] = {}, ub[4] = {}, uc[4] = {};
+      if (kb + 4 <= ns) {  // four stayers
+        const long long s = base + kb;
+        load_vec(in.p.cell + s, cw);
+        load_vec(in.p.o[0] + s, e0);
+        load_vec(in.p.o[1] + s, e1);
+        if (d3) load_vec(in.p.o[2] + s, e2);
+        if (has_w) load_vec(in.p.w + s, pw);
+        if constexpr (KIN) {
+          load_vec(in.p.u[0] + s, ua);
+          load_vec(in.p.u[1] + s, ub);
+          load_vec(in.p.u[2] + s, uc);
         }
+      } else {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int k = kb + j;
+          cw[j] = kHoleCell;
+          e0[j] = e1[j] = 0.f;
+          if (k < n) {
+            const long long s = k < ns ? base + k : back + k;
+            cw[j] = in.p.cell[s];
+            e0[j] = in.p.o[0][s];
+            e1[j] = in.p.o[1][s];
+            if (d3) e2[j] = in.p.o[2][s];
+            if (has_w) pw[j] = in.p.w[s];
+            if constexpr (KIN) {
+              ua[j] = in.p.u[0][s];
+              ub[j] = in.p.u[1][s];
+              uc[j] = in.p.u[2][s];
+            }
+          }
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        if (cw[j] == kHoleCell) continue;
+        const int cell = (int)(cw[j] & 0x00FFFFFFu);
+        if (cell != cur) {
+          if (cur >= 0) flush();
+          cur = cell;
+#pragma unroll
+          for (int q = 0; q < 8; ++q) accw[q] = 0.f;
+        }
+        if constexpr (KIN) {
+          const float u2 = fmaf(ua[j], ua[j], fmaf(ub[j], ub[j], uc[j] * uc[j]));
+          kp = fmaf(pw[j], u2 / (1.f + sqrtf(1.f + u2)), kp);
+          lp += pw[j];
+        }
+        const float f1[2] = {1.f - e0[j], e0[j]}, f2[2] = {1.f - e1[j], e1[j]}, f3[2] = {1.f - e2[j], e2[j]};
+#pragma unroll
+        for (int c3 = 0; c3 < 2; ++c3)
+#pragma unroll
+          for (int c2 = 0; c2 < 2; ++c2) {
+            const float w23 = f2[c2] * (d3 ? f3[c3] : 1.f) * pw[j];
+#pragma unroll
+            for (int c1 = 0; c1 < 2; ++c1)
+              accw[c3 * 4 + c2 * 2 + c1] = fmaf(f1[c1], w23, accw[c3 * 4 + c2 * 2 + c1]);
+          }
+      }
     }
     if (cur >= 0) flush();
     if constexpr (KIN) {
       kin += (double)kp;
       live += (double)lp;
     }
-    __syncwarp();
   }
   if constexpr (KIN) {
     __shared__ double red[2][kRhoThreads / 32];

@@ -1127,7 +1127,7 @@ constexpr int kRhoWarp = 32 * kRhoRun;
 constexpr int kRhoThreads = 128;
 
 template <bool KIN>
-__global__ void __launch_bounds__(kRhoThreads) k_tiled_rho(Layout L, PushConst C, Tiles tg, TileSide in, double* rho,
+__global__ void __launch_bounds__(kRhoThreads, 8) k_tiled_rho(Layout L, PushConst C, Tiles tg, TileSide in, double* rho,
                                                            Diag64* acc) {
   // node sums, fixed point in units of 2^-32: low words Rlo[nr], high words Rhi[nr]
   extern __shared__ unsigned int Rlo[];
@@ -1222,7 +1222,7 @@ __global__ void __launch_bounds__(kRhoThreads) k_tiled_rho(Layout L, PushConst C
         }
         if constexpr (KIN) {
           const float u2 = fmaf(ua[j], ua[j], fmaf(ub[j], ub[j], uc[j] * uc[j]));
-          kp = fmaf(pw[j], u2 / (1.f + sqrtf(1.f + u2)), kp);
+          kp = fmaf(pw[j], __fdividef(u2, 1.f + sqrtf(1.f + u2)), kp);  // 2 ulp: far below the gates
           lp += pw[j];
         }
         const float f1[2] = {1.f - e0[j], e0[j]}, f2[2] = {1.f - e1[j], e1[j]}, f3[2] = {1.f - e2[j], e2[j]};

@@ -13,7 +13,9 @@ CUDA graph launch per step.
   with and without moving windows;
 * wakefield members (windows moving at c that shift on different steps, open
   x1, front injection, in-box pulses and one antenna) against the same members
-  run alone and, for one member, the FP64 oracle, after 30 steps at 1e-4.
+  run alone and, for one member, the FP64 oracle, after 30 steps at 1e-4;
+* a mixed batch (moving and periodic members, one with current smoothing)
+  against its members run alone.
 """
 import os
 
@@ -247,4 +249,43 @@ def test_batch_of_wakefield_members_with_windows_matches_members_alone_and_oracl
         mref = np.max(np.abs(ref.fld[c]))
         if mref > 0:
             assert np.max(np.abs(m0.fields(name) - ref.fld[c])) < 1e-4 * mref, name
+    batch.close()
+
+
+def test_mixed_batch_of_windows_periodic_and_smoothed_members_matches_members_alone():
+    """One batch holding two wakefield members (one with an antenna pulse),
+    a periodic member and a periodic member whose current is smoothed (two
+    passes along x1, one along x2, launched per member inside the step's
+    graph): after 20 steps every member equals the same member run alone."""
+    import dataclasses
+
+    import paper_1503_00276_gb300 as pg
+    wake = _wake_members()
+    per = _members()
+    g_s, s_s = per[1]
+    g_s = dataclasses.replace(g_s, smooth_level=(2, 1, 0))
+    mem = [wake[0], per[0], wake[2], (g_s, s_s)]
+    n = 20
+    batch = pg.Batch(mem, track_ids=True)
+    batch.step(n)
+    # stages + fresh columns, shift, gather + one antenna + 3 smoothing passes x 3 components
+    assert batch.info()["launches"] == n * (7 + 3 + 1 + 9)
+    for i, m in enumerate(mem):
+        g, sps = m[0], m[1]
+        solo = pg.Simulation(g, sps, precision="fp32", tile=(32, 16), track_ids=True)
+        if len(m) > 2:
+            solo.add_laser(m[2])
+        solo.step(n)
+        b = batch.sim(i)
+        assert b.diag()["n_particles"] == solo.diag()["n_particles"]
+        if g.move_window:
+            _compare_window(b, solo, g.dx, 1e-4)
+        else:
+            _compare(b, solo, 1e-4)
+            for name in ("E1", "E2", "E3", "B1", "B2", "B3", "J1", "J2", "J3"):
+                f = solo.fields(name)
+                top = np.max(np.abs(f))
+                if top > 0:
+                    assert np.max(np.abs(b.fields(name) - f)) < 1e-4 * top, (i, name)
+        solo.close()
     batch.close()

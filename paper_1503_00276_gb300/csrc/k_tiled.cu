@@ -11,10 +11,13 @@
 //   * gather (eq. 2d-field-weighting-e3, 3D extension), Boris push
 //     (eq. momentum-update), position update (eq. 2d-position-update) and the
 //     TRISTAN / Villasenor-Buneman deposit run in FP32 on int cell + FP32 offset;
+//   * the tile's particles are read in chunks of 512 as one sequence, the
+//     stayers continued by the arrivals;
 //   * the current goes to a shared-memory tile: each thread adds the first
-//     in-cell piece of consecutive same-cell particles in registers and flushes
-//     once per cell; pieces after a face crossing (a few % of particles) are
-//     queued in shared memory and deposited by full warps;
+//     in-cell pieces of its two particles in registers, each warp then sums
+//     its lanes over runs of equal cells, and one lane per cell flushes;
+//     pieces after a face crossing (a few % of particles) are queued in
+//     shared memory and deposited by full warps;
 //   * each chunk of 512 advanced particles is counting-sorted by new cell in
 //     shared memory (keys only -- the particles stay in registers) and written
 //     to the front of the tile's region on the other store side; particles that

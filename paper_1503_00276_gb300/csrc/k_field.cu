@@ -274,6 +274,85 @@ __global__ void k_yee_e_f32(Layout L, Ptr3<float> E, Ptr3<float> B, Ptr3<float> 
                blockIdx.y * blockDim.y + threadIdx.y, blockIdx.z);
 }
 
+// 3D forms of the two FP32 sweeps that walk kZM planes of x3 per thread and
+// carry the x3 neighbour of one plane into the next in registers (the B half
+// step reads E at k + 1, the E step B at k - 1).  Every value is computed with
+// the expressions of yee_b_f32_at / yee_e_f32_at.
+constexpr int kZM = 8;
+
+__global__ void k_yee_b_half_f32_z(Layout L, Ptr3<float> E, Ptr3<float> B, float h, float i1, float i2, float i3) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int k0 = blockIdx.z * kZM;
+  if (i >= L.nx || j >= L.ny) return;
+  const long long pz = (long long)L.NX * L.NY;
+  const float* __restrict__ E1 = E.c[0];
+  const float* __restrict__ E2 = E.c[1];
+  const float* __restrict__ E3 = E.c[2];
+  const bool front = L.open_x && i + 1 == L.nx;
+  const long long dx1 = i + 1 == L.nx ? 1 - L.nx : 1;
+  const long long dy1 = j + 1 == L.ny ? (long long)(1 - L.ny) * L.NX : L.NX;
+  long long c = L.idx(i, j, k0);
+  float e1 = __ldg(E1 + c), e2 = __ldg(E2 + c);
+  const int k1 = min(k0 + kZM, L.nz);
+  for (int k = k0; k < k1; ++k) {
+    const long long cx = c + dx1, cy = c + dy1;
+    const long long cz = c + (k + 1 == L.nz ? (long long)(1 - L.nz) * pz : pz);
+    const float e3 = __ldg(E3 + c);
+    const float z1 = __ldg(E1 + cz), z2 = __ldg(E2 + cz);  // the next plane's e1, e2
+    const float dE3d2 = (__ldg(E3 + cy) - e3) * i2;
+    const float dE3d1 = ((front ? 0.f : __ldg(E3 + cx)) - e3) * i1;
+    const float dE2d1 = ((front ? 0.f : __ldg(E2 + cx)) - e2) * i1;
+    const float dE1d2 = (__ldg(E1 + cy) - e1) * i2;
+    const float dE2d3 = (z2 - e2) * i3;
+    const float dE1d3 = (z1 - e1) * i3;
+    B.c[0][c] = fmaf(-h, dE3d2 - dE2d3, B.c[0][c]);
+    B.c[1][c] = fmaf(-h, dE1d3 - dE3d1, B.c[1][c]);
+    B.c[2][c] = fmaf(-h, dE2d1 - dE1d2, B.c[2][c]);
+    e1 = z1;
+    e2 = z2;
+    c += pz;
+  }
+}
+
+__global__ void k_yee_e_f32_z(Layout L, Ptr3<float> E, Ptr3<float> B, Ptr3<float> J, float dt, float i1, float i2,
+                              float i3, const float* inc) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int k0 = blockIdx.z * kZM;
+  if (i >= L.nx || j >= L.ny) return;
+  const long long pz = (long long)L.NX * L.NY;
+  const float* __restrict__ B1 = B.c[0];
+  const float* __restrict__ B2 = B.c[1];
+  const float* __restrict__ B3 = B.c[2];
+  const bool back = L.open_x && i == 0;
+  const long long dx1 = i == 0 ? 1 - L.nx : 1;
+  const long long dy1 = j == 0 ? (long long)(1 - L.ny) * L.NX : L.NX;
+  long long c = L.idx(i, j, k0);
+  const long long cz0 = c - (k0 == 0 ? (long long)(1 - L.nz) * pz : pz);
+  float m1 = __ldg(B1 + cz0), m2 = __ldg(B2 + cz0);  // the previous plane's b1, b2
+  const int k1 = min(k0 + kZM, L.nz);
+  for (int k = k0; k < k1; ++k) {
+    const long long cx = c - dx1, cy = c - dy1;
+    const float b1 = __ldg(B1 + c), b2 = __ldg(B2 + c), b3 = __ldg(B3 + c);
+    const long long p = (long long)k * L.ny + j;  // this row in the incident planes
+    const float b3m = back ? (inc ? inc[(long long)L.ny * L.nz + p] : 0.f) : __ldg(B3 + cx);
+    const float b2m = back ? (inc ? inc[p] : 0.f) : __ldg(B2 + cx);
+    const float dB3d2 = (b3 - __ldg(B3 + cy)) * i2;
+    const float dB3d1 = (b3 - b3m) * i1;
+    const float dB2d1 = (b2 - b2m) * i1;
+    const float dB1d2 = (b1 - __ldg(B1 + cy)) * i2;
+    const float dB2d3 = (b2 - m2) * i3;
+    const float dB1d3 = (b1 - m1) * i3;
+    E.c[0][c] = fmaf(dt, dB3d2 - dB2d3 - __ldg(J.c[0] + c), E.c[0][c]);
+    E.c[1][c] = fmaf(dt, dB1d3 - dB3d1 - __ldg(J.c[1] + c), E.c[1][c]);
+    E.c[2][c] = fmaf(dt, dB2d1 - dB1d2 - __ldg(J.c[2] + c), E.c[2][c]);
+    m1 = b1;
+    m2 = b2;
+    c += pz;
+  }
+}
+
 // Moving window: every field value one cell back in x1 (value at i <- value
 // at i + 1), zero in the new front column.  One warp per row; a row is read
 // ahead of where it is written.
@@ -586,9 +665,14 @@ void smooth_pass(const Layout& L, T* comp, T* tmp, int dim, double w0, double w1
 template <typename T>
 void yee_b_half(const Layout& L, T* const* e, T* const* b, double dt, const double dx[3], cudaStream_t s) {
   Ptr3<T> E{{e[0], e[1], e[2]}}, B{{b[0], b[1], b[2]}};
-  if constexpr (sizeof(T) == 4)
-    k_yee_b_half_f32<<<interior_grid(L), kBlock, 0, s>>>(L, E, B, (float)(dt / 2.0), (float)(1.0 / dx[0]),
-                                                         (float)(1.0 / dx[1]), (float)(1.0 / dx[2]));
+  if constexpr (sizeof(T) == 4) {
+    if (L.ndim == 3)
+      k_yee_b_half_f32_z<<<dim3((L.nx + 31) / 32, (L.ny + 7) / 8, (L.nz + kZM - 1) / kZM), kBlock, 0, s>>>(
+          L, E, B, (float)(dt / 2.0), (float)(1.0 / dx[0]), (float)(1.0 / dx[1]), (float)(1.0 / dx[2]));
+    else
+      k_yee_b_half_f32<<<interior_grid(L), kBlock, 0, s>>>(L, E, B, (float)(dt / 2.0), (float)(1.0 / dx[0]),
+                                                           (float)(1.0 / dx[1]), (float)(1.0 / dx[2]));
+  }
   else
     k_yee_b_half<T><<<interior_grid(L), kBlock, 0, s>>>(L, E, B, (T)(dt / 2.0), (T)dx[0], (T)dx[1], (T)dx[2]);
 }
@@ -597,9 +681,14 @@ template <typename T>
 void yee_e(const Layout& L, T* const* e, T* const* b, T* const* j, double dt, const double dx[3], cudaStream_t s,
            const float* inc) {
   Ptr3<T> E{{e[0], e[1], e[2]}}, B{{b[0], b[1], b[2]}}, J{{j[0], j[1], j[2]}};
-  if constexpr (sizeof(T) == 4)
-    k_yee_e_f32<<<interior_grid(L), kBlock, 0, s>>>(L, E, B, J, (float)dt, (float)(1.0 / dx[0]),
-                                                    (float)(1.0 / dx[1]), (float)(1.0 / dx[2]), inc);
+  if constexpr (sizeof(T) == 4) {
+    if (L.ndim == 3)
+      k_yee_e_f32_z<<<dim3((L.nx + 31) / 32, (L.ny + 7) / 8, (L.nz + kZM - 1) / kZM), kBlock, 0, s>>>(
+          L, E, B, J, (float)dt, (float)(1.0 / dx[0]), (float)(1.0 / dx[1]), (float)(1.0 / dx[2]), inc);
+    else
+      k_yee_e_f32<<<interior_grid(L), kBlock, 0, s>>>(L, E, B, J, (float)dt, (float)(1.0 / dx[0]),
+                                                      (float)(1.0 / dx[1]), (float)(1.0 / dx[2]), inc);
+  }
   else
     k_yee_e<T><<<interior_grid(L), kBlock, 0, s>>>(L, E, B, J, (T)dt, (T)dx[0], (T)dx[1], (T)dx[2]);
 }

@@ -2169,6 +2169,14 @@ pic_status pic_batch_init(int nsims, const pic_grid* grids, const pic_species* s
     B->sims.push_back(S);
     for (int k = 0; k < nspecies; ++k) B->ent.push_back({i, k});
   }
+  // the particle launch takes work items in entry order: the densest entries
+  // (most particles per tile) first, so that their heavy tiles start early
+  // and the small tiles of sparse members fill the end of the launch
+  std::stable_sort(B->ent.begin(), B->ent.end(), [&](const std::pair<int, int>& a, const std::pair<int, int>& b) {
+    const SpeciesState& sa = B->sims[a.first]->sp[a.second];
+    const SpeciesState& sb = B->sims[b.first]->sp[b.second];
+    return (double)sa.n * sb.tg.ntiles > (double)sb.n * sa.tg.ntiles;
+  });
   const int n = (int)B->ent.size();
   B->d_args[0] = B->al.get(tiled_args_bytes() * n);
   B->d_args[1] = B->al.get(tiled_args_bytes() * n);

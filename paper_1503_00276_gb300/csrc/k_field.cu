@@ -354,7 +354,8 @@ __global__ void k_yee_e_f32_z(Layout L, Ptr3<float> E, Ptr3<float> B, Ptr3<float
 }
 
 // Moving window: every field value one cell back in x1 (value at i <- value
-// at i + 1), zero in the new front column.  One warp per row; a row is read
+// at i + 1), zero in the new front column.  One warp per row, 256 values per
+// round with every load of the round before its stores; a row is read
 // ahead of where it is written.
 template <typename T>
 __device__ inline void shift_row(const Layout& L, const PtrN<T, 6>& P, int ncomp, long long row) {
@@ -365,11 +366,22 @@ __device__ inline void shift_row(const Layout& L, const PtrN<T, 6>& P, int ncomp
   const long long r = row - (long long)c * L.ny * L.nz;
   const int j = (int)(r % L.ny), k = (int)(r / L.ny);
   T* f = P.c[c] + L.idx(0, j, k);
-  for (int b = 0; b < L.nx; b += 32) {
-    const int i = b + lane;
-    const T v = i + 1 < L.nx ? f[i + 1] : T(0);
+  // 256 values per round: all loads of a round are in flight before its
+  // stores, which only touch values the later rounds no longer read
+  constexpr int kR = 8;
+  for (int b = 0; b < L.nx; b += 32 * kR) {
+    T v[kR];
+#pragma unroll
+    for (int m = 0; m < kR; ++m) {
+      const int i = b + 32 * m + lane;
+      v[m] = i + 1 < L.nx ? f[i + 1] : T(0);
+    }
     __syncwarp();
-    if (i < L.nx) f[i] = v;
+#pragma unroll
+    for (int m = 0; m < kR; ++m) {
+      const int i = b + 32 * m + lane;
+      if (i < L.nx) f[i] = v[m];
+    }
     __syncwarp();
   }
 }

@@ -165,6 +165,7 @@ struct pic_sim {
   Diag64* dacc = nullptr;
   StatusWord* dstat = nullptr;
   StatusWord* hstat = nullptr;  // pinned
+  int* hcnt = nullptr;          // pinned: dropped / created particles per species, read with the status
   std::vector<SpeciesState> sp;
   CUtensorMap fmap{}, jmap{};
   long long step = 0;
@@ -1100,18 +1101,20 @@ pic_status one_step(pic_sim* S, bool check_now) {
   if (st != PIC_OK) return st;
   if (!check_now) return PIC_OK;
   cudaMemcpyAsync(S->hstat, S->dstat, sizeof(StatusWord), cudaMemcpyDeviceToHost, S->s);
+  // dropped (and injected) particles, read back with the status word
+  const bool counted = S->moving || (S->cyl && S->prec == PIC_FP32_CELLOFF);
+  if (counted)
+    for (size_t k = 0; k < S->sp.size(); ++k) {
+      cudaMemcpyAsync(S->hcnt + 2 * k, S->sp[k].d_lost, sizeof(int), cudaMemcpyDeviceToHost, S->s);
+      cudaMemcpyAsync(S->hcnt + 2 * k + 1, S->sp[k].d_kept, sizeof(int), cudaMemcpyDeviceToHost, S->s);
+      cudaMemsetAsync(S->sp[k].d_lost, 0, sizeof(int), S->s);
+      cudaMemsetAsync(S->sp[k].d_kept, 0, sizeof(int), S->s);
+    }
   if (cudaStreamSynchronize(S->s) != cudaSuccess) return cuda_check("step");
   const int flags = S->hstat->status;
   S->sticky_flags |= flags;
-  if (S->moving || (S->cyl && S->prec == PIC_FP32_CELLOFF))  // dropped (and injected) particles
-    for (auto& s : S->sp) {
-      int lost = 0, kept = 0;
-      cudaMemcpy(&lost, s.d_lost, sizeof(int), cudaMemcpyDeviceToHost);
-      cudaMemcpy(&kept, s.d_kept, sizeof(int), cudaMemcpyDeviceToHost);
-      cudaMemsetAsync(s.d_lost, 0, sizeof(int), S->s);
-      cudaMemsetAsync(s.d_kept, 0, sizeof(int), S->s);
-      s.n += kept - lost;
-    }
+  if (counted)
+    for (size_t k = 0; k < S->sp.size(); ++k) S->sp[k].n += S->hcnt[2 * k + 1] - S->hcnt[2 * k];
   if (flags & ST_SPILL) {
     if (flags & ST_SPILL_LOST) {
       set_error("particle spill list overflowed: particles were lost");
@@ -1221,6 +1224,7 @@ pic_status pic_destroy(pic_sim* S) {
   for (auto e : S->ev_pool) cudaEventDestroy(e);
   S->al.release_all();
   if (S->hstat) cudaFreeHost(S->hstat);
+  if (S->hcnt) cudaFreeHost(S->hcnt);
   delete S;
   return PIC_OK;
 }
@@ -1338,6 +1342,11 @@ pic_status init_sim(const pic_grid* grid, const pic_species* species, int nspeci
   S->dstat = (StatusWord*)S->al.get(sizeof(StatusWord));
   if (!S->fld || !S->cur || !S->tmp || !S->rho || !S->dense || !S->dacc || !S->dstat) {
     set_error("out of device memory (grid arrays)");
+    return bail(PIC_ENOMEM);
+  }
+  if (cudaMallocHost(&S->hcnt, sizeof(int) * 2 * (size_t)std::max(nspecies, 1)) != cudaSuccess) {
+    S->hcnt = nullptr;
+    set_error("pinned host allocation failed");
     return bail(PIC_ENOMEM);
   }
   if (cudaMallocHost(&S->hstat, sizeof(StatusWord)) != cudaSuccess) {

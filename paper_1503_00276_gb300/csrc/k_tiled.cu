@@ -1012,19 +1012,30 @@ __global__ void k_flatten(Tiles tg, TileSide in, const long long* out_off, Flat3
   }
 }
 
+// Tile counts and the scatter into the tile regions.  The flat input is
+// mostly grouped by tile (the loader's lattice order, a flattened store), so
+// the lanes of a warp that share a tile take their slots with one atomic
+// (match, then the leader adds the group's size and shares the base).  Every
+// block is a whole number of warps; lanes past n carry tile -1.
 __global__ void k_flat_count(Flat32 f, long long n, int ntiles, int* counts) {
   const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= n) return;
-  const int t = f.tile[k];
-  if (t >= 0 && t < ntiles) atomicAdd(&counts[t], 1);
+  int t = k < n ? f.tile[k] : -1;
+  if (t >= ntiles) t = -1;
+  const unsigned peers = __match_any_sync(0xffffffffu, t);
+  if (t >= 0 && (int)(threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&counts[t], __popc(peers));
 }
-
 __global__ void k_flat_scatter(Flat32 f, long long n, Tiles tg, int* cursor, Part32 out) {
   const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= n) return;
-  const int t = f.tile[k];
-  if (t < 0 || t >= tg.ntiles) return;
-  const int r = atomicAdd(&cursor[t], 1);
+  const int lane = threadIdx.x & 31;
+  int t = k < n ? f.tile[k] : -1;
+  if (t >= tg.ntiles) t = -1;
+  const unsigned peers = __match_any_sync(0xffffffffu, t);
+  const int leader = __ffs(peers) - 1;
+  int base = 0;
+  if (t >= 0 && lane == leader) base = atomicAdd(&cursor[t], __popc(peers));
+  base = __shfl_sync(0xffffffffu, base, leader);
+  if (t < 0) return;
+  const int r = base + __popc(peers & ((1u << lane) - 1u));
   if (r >= tg.cap[t]) return;  // capacities are sized from the same counts
   const long long s = tg.base[t] + r;
   out.cell[s] = f.cell[k];

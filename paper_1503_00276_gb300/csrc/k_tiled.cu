@@ -1347,8 +1347,18 @@ __device__ inline void inject_one(const TileArgs& A, const int* T, const int* nt
     if (!(J.prof.density * w > J.prof.den_min)) return;  // no particle where the density is this low
     q.w = (float)w;
   }
-  atomicAdd(J.kept, 1);
-  const int slot = atomicAdd(&A.out.inc[t], 1);
+  // the lanes still here are created; a warp's lanes mostly share a tile (a
+  // column's cells are consecutive), so each group takes its slots and adds to
+  // the count with one atomic
+  const unsigned act = __activemask();
+  const int lane = threadIdx.x & 31;
+  if (lane == __ffs(act) - 1) atomicAdd(J.kept, __popc(act));
+  const unsigned peers = __match_any_sync(act, t);
+  const int leader = __ffs(peers) - 1;
+  int base = 0;
+  if (lane == leader) base = atomicAdd(&A.out.inc[t], __popc(peers));
+  base = __shfl_sync(peers, base, leader);
+  const int slot = base + __popc(peers & ((1u << lane) - 1u));
   if (slot < A.res[t]) {
     const long long s = A.base[t] + A.cap[t] - 1 - slot;
     if (J.ndim == 3)

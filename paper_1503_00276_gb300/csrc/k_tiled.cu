@@ -222,6 +222,7 @@ __device__ inline int sort_and_store_lean(const TileArgs& A, int t, int tix, int
   const int nq = misc[5];
   __syncthreads();
   const int wsb = stay_ctr ? misc[4] : ws;
+  const bool agg = A.shift_ptr != nullptr || A.shift_x != 0;  // a window shift: many leavers
   {
     int p0 = 0, rs = 0;
 #pragma unroll
@@ -243,8 +244,38 @@ __device__ inline int sort_and_store_lean(const TileArgs& A, int t, int tix, int
             store_particle<NDIM>(A.out.p, base + pos, pp[r]);
           else
             spill_put(A, t, pp[r]);
-        } else if (k < G::NK) {
+        } else if (k < G::NK && !agg) {
           store_leaver<NDIM>(A, tix, tiy, tiz, pp[r], nb);
+        }
+      }
+    }
+  }
+  // leavers: the lanes bound for one neighbour tile take their arrival slots
+  // with one atomic (a window shift sends a tile's whole first cell column
+  // to the tile behind)
+  if (agg) {
+#pragma unroll
+    for (int r = 0; r < kPPT; ++r) {
+      const bool lv = r < nvalid && key[r] == G::NC;
+      const int dir = lv ? (int)(pp[r].cell >> 24) : -1;
+      const unsigned peers = __match_any_sync(0xffffffffu, dir);
+      if (lv) {
+        const int leader = __ffs(peers) - 1;
+        const int cnt = __popc(peers), rank = __popc(peers & ((1u << lane) - 1u));
+        const Nbr& nbr = nb[dir];
+        if (nbr.tile < 0) {  // left through an open x1 boundary
+          if (lane == leader) atomicAdd(A.lost, cnt);
+        } else {
+          int slot0 = 0;
+          if (lane == leader) slot0 = atomicAdd(&A.out.inc[nbr.tile], cnt);
+          slot0 = __shfl_sync(peers, slot0, leader);
+          const int slot = slot0 + rank;
+          P q2 = pp[r];
+          q2.cell = (q2.cell & 0x00FFFFFFu) | ((uint32_t)DIR_STAY << 24);
+          if (slot < nbr.res)
+            store_particle<NDIM>(A.out.p, nbr.base + nbr.cap - 1 - slot, q2);
+          else
+            spill_put(A, nbr.tile, q2);
         }
       }
     }

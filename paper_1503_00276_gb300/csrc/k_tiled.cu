@@ -21,8 +21,9 @@
 //   * each chunk of 512 advanced particles is counting-sorted by new cell in
 //     shared memory (keys only -- the particles stay in registers) and written
 //     to the front of the tile's region on the other store side; particles that
-//     left the tile are appended, with one global atomic each, to the back of
-//     their new tile's region there;
+//     left the tile are appended, with one global atomic each (one per warp
+//     and destination when a window shifts), to the back of their new tile's
+//     region there;
 //   * one TMA reduce-add flushes the shared current tile (with halo) into HBM.
 // The store is therefore re-binned by tile and re-sorted by cell every step
 // without a separate pass over HBM.

@@ -15,7 +15,9 @@ CUDA graph launch per step.
   x1, front injection, in-box pulses and one antenna) against the same members
   run alone and, for one member, the FP64 oracle, after 30 steps at 1e-4;
 * a mixed batch (moving and periodic members, one with current smoothing)
-  against its members run alone.
+  against its members run alone;
+* wakefield members that spill and are re-binned inside the batch, and a
+  batch whose second species is empty, against their members run alone.
 """
 import os
 
@@ -287,5 +289,47 @@ def test_mixed_batch_of_windows_periodic_and_smoothed_members_matches_members_al
                 top = np.max(np.abs(f))
                 if top > 0:
                     assert np.max(np.abs(b.fields(name) - f)) < 1e-4 * top, (i, name)
+        solo.close()
+    batch.close()
+
+
+def test_batch_rebins_wakefield_members_and_keeps_windows():
+    """Wakefield members with almost no spare slots in their tile regions
+    spill and are re-binned between steps inside the batch (re-sized regions,
+    tables and graph rebuilt); after 20 steps every member equals the same
+    member run alone with the same regions."""
+    import paper_1503_00276_gb300 as pg
+    mem = _wake_members()[:3]
+    n = 20
+    batch = pg.Batch(mem, track_ids=True, slack=1e-3)
+    batch.step(n)
+    assert any(batch.sim(i).diag()["error_flags"] & 2 for i in range(len(mem)))  # some member spilled
+    for i, (g, sps, las) in enumerate(mem):
+        solo = pg.Simulation(g, sps, precision="fp32", tile=(32, 16), track_ids=True, slack=1e-3)
+        solo.add_laser(las)
+        solo.step(n)
+        m = batch.sim(i)
+        assert m.diag()["error_flags"] & 1 == 0
+        assert m.n_particles() == solo.n_particles()
+        _compare_window(m, solo, g.dx, 1e-4)
+        solo.close()
+    batch.close()
+
+
+def test_batch_with_an_empty_species():
+    """Two species per member, the second one empty (a density profile that
+    is zero everywhere): the batch steps and equals the members run alone."""
+    import paper_1503_00276_gb300 as pg
+    zero = (np.array([0.0, 1.0]), np.array([0.0, 0.0]))
+    empty = workload.Species(rqm=1.0, ppc=(1, 1, 1), seed=5, profile=(zero, None, None), den_min=0.0)
+    mem = [(g, [s, empty]) for g, (s,) in _members()[:3]]
+    batch = pg.Batch(mem, track_ids=True)
+    batch.step(5)
+    for i, (g, sps) in enumerate(mem):
+        solo = pg.Simulation(g, sps, precision="fp32", tile=(32, 16), track_ids=True)
+        solo.step(5)
+        m = batch.sim(i)
+        assert m.n_particles(1) == 0
+        _compare(m, solo, 1e-4)
         solo.close()
     batch.close()
